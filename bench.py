@@ -1,0 +1,425 @@
+#!/usr/bin/env python
+"""Benchmark of the full-size frame: 32^3 -> 256^3 coarse-to-fine localization
+(Sec. 3.2) plus a 512x512 mesh-free render (Eq. 3), with the 257-1024-512-
+256-128-1 occupancy MLP and the 513-1024-512-256-128-3 colour MLP over
+256x128x128 feature maps.  One step = one frame.
+
+Prints ONE JSON line (rank 0).  `value` is frames/s over all ranks (each rank
+renders its own frames: independent replicas, no collective), measured with
+CUDA events around each step on the library's stream, L2 flushed between
+steps.  `e2e` repeats the measurement through the public API with the
+frame's feature maps copied in from pinned host memory and depth/colour/mask
+copied out every step.  `roofline` reports the dominant kernel class
+(hidden MLP layers) from the library's own per-launch CUDA-event timing over
+the same timed steps.
+
+--impl reference times the FP64 CPU oracle (the plain statement of the
+method) on the host cores instead, on a bounded sample of the same frame.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "frames/s & query pts/s at 256³ + 512² render, vs plain FP32 at IoU≥0.995"
+UNIT = "frames/s"
+L2_FLUSH_BYTES = 512 << 20
+COUNTS_FILE = os.path.join(ROOT, "tests", "golden", "full_frame_counts.txt")
+PROFILES = os.path.join(ROOT, "profiles")
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--precision", choices=("fp32",), default="fp32")
+    ap.add_argument("--query-points", type=int, default=1 << 20)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-clocks", action="store_true")
+    return ap.parse_args()
+
+
+def read_kv(path):
+    out = {}
+    if not os.path.exists(path):
+        return out
+    for line in open(path):
+        line = line.split("#", 1)[0].strip()
+        if "=" in line:
+            k, v = line.split("=", 1)
+            out[k.strip()] = v.strip()
+    return out
+
+
+def cpu_threads():
+    try:
+        from threadpoolctl import threadpool_info
+        n = [i.get("num_threads") for i in threadpool_info() if i.get("user_api") == "blas"]
+        if n and n[0]:
+            return int(n[0])
+    except Exception:
+        pass
+    return os.cpu_count() or 1
+
+
+# ------------------------------------------------------------------ clocks ---
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index, enabled=True):
+        self.proc = None
+        self.path = None
+        self.dev = device_index
+        if not enabled:
+            return
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={device_index}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append({"sm": float(parts[1]), "max": float(parts[2]),
+                             "power": float(parts[3]) if parts[3] not in ("[N/A]", "") else 0.0,
+                             "reasons": {"hw_slowdown": parts[5], "hw_thermal_slowdown": parts[6],
+                                         "sw_thermal_slowdown": parts[7], "sw_power_cap": parts[8]}})
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        reasons = sorted({k for r in rows for k, v in r["reasons"].items() if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(r["sm"] for r in rows),
+                "sm_max_mhz": max(r["max"] for r in rows),
+                "power_w_max": max(r["power"] for r in rows),
+                "samples": len(rows), "reasons": reasons}
+
+
+# --------------------------------------------------------------- roofline ---
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        return json.load(open(p)), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+            "sm_max_mhz": 2070.0}, "fallback"
+
+
+def fp32_simt_peak_tflops(sm_mhz):
+    # 152 SMs x 128 FP32 lanes x 2 flop (FFMA) per clock
+    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+def source_digest(files):
+    h = hashlib.sha256()
+    for f in files:
+        h.update(open(os.path.join(ROOT, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel_key, digest):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on
+    the current source (matching digest)."""
+    if not os.path.isdir(PROFILES):
+        return None
+    pat = re.compile(r"^traffic\[(\S+)\]\s*=\s*([0-9.eE+]+)\s+bytes/launch\s+source=(\w+)")
+    for f in sorted(os.listdir(PROFILES)):
+        if not f.endswith((".md", ".txt")):
+            continue
+        for line in open(os.path.join(PROFILES, f)):
+            m = pat.match(line.strip())
+            if m and m.group(1) == kernel_key and m.group(3) == digest:
+                return float(m.group(2))
+    return None
+
+
+# ----------------------------------------------------------------- oracle ---
+
+def oracle_frame(w):
+    """One full frame of the FP64 oracle; returns (seconds, counts)."""
+    import numpy as np
+    from oracle import field, localize, render
+    t0 = time.perf_counter()
+    lv = localize.hierarchical(lambda P: field.occupancy(w.occ_net, w.occ_map, w.calib, P),
+                               w.n0, w.num_levels)
+    rgb, depth, hit = render.render(lv[-1].values, w.render, w.col_net, w.occ_map, w.col_map,
+                                    w.calib)
+    dt = time.perf_counter() - t0
+    return dt, {"evals": int(sum(l.n_eval for l in lv)), "hits": int(np.count_nonzero(hit))}
+
+
+def run_reference(args, rank, world):
+    """FP64 oracle on the host cores: each step evaluates f_O at a bounded
+    sample of the frame's own level-0 nodes; frames/s is that rate divided by
+    the frame's f_O evaluations (colour pass, ray scan and set bookkeeping,
+    about a third of a full oracle frame, are not included)."""
+    if rank != 0:
+        return
+    import numpy as np
+    from oracle import field, localize
+    from paper_2007_13988_gb300 import synth
+    w = synth.full(0)
+    counts = read_kv(COUNTS_FILE)
+    evals_frame = int(counts.get("evals_total", 146108))
+    P_all = localize.grid_points(w.n0)
+    # size the sample so that warm-up + steps stay within ~2 minutes
+    probe = P_all[:2048]
+    t0 = time.perf_counter()
+    field.occupancy(w.occ_net, w.occ_map, w.calib, probe)
+    per_pt = (time.perf_counter() - t0) / len(probe)
+    budget = 120.0 / max(1, args.steps + args.warmup)
+    S = int(min(len(P_all), max(2048, budget / max(per_pt, 1e-9))))
+    P = P_all[:S]
+    for _ in range(args.warmup):
+        field.occupancy(w.occ_net, w.occ_map, w.calib, P)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        field.occupancy(w.occ_net, w.occ_map, w.calib, P)
+        times.append(time.perf_counter() - t0)
+    pts_per_s = S * len(times) / sum(times)
+    value = pts_per_s / evals_frame
+    cores = cpu_threads()
+    sample = (f"f_O (FP64, numpy) at {S} of the frame's 32^3 level-0 nodes per step, scaled by the "
+              f"frame's {evals_frame} f_O evaluations; colour, ray scan and set bookkeeping excluded")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000.0 * sum(times) / len(times), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(w, evals_frame, None),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def workload_config(w, evals, hits, precision="fp32"):
+    return {"workload": "one 512x512 frame: 32^3->256^3 hierarchical localization + 512^2 "
+                        "mesh-free render; f_O 257-1024-512-256-128-1 (skips at 2-4), "
+                        "f_T 513-1024-512-256-128-3; 256x128x128 FP32 feature maps",
+            "levels": f"{w.n0}->{w.n0 << (w.num_levels - 1)}", "render": w.render,
+            "precision": precision, "evals_per_frame": evals, "hits_per_frame": hits,
+            "l2": "flushed between timed steps (512 MB write, outside the step events)",
+            "parallelism": "replicas (independent frames per GPU)"}
+
+
+# -------------------------------------------------------------------- ours ---
+
+def run_ours(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+
+    from paper_2007_13988_gb300 import pifu, synth
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    w = synth.full(0)
+    ctx = pifu.pifu_create(pifu.blob_from_nets(w.occ_net, w.col_net))
+    stream = torch.cuda.Stream(device=dev)
+    R = w.render
+    with torch.cuda.stream(stream):
+        occ = torch.from_numpy(w.occ_map).to(dev)
+        col = torch.from_numpy(w.col_map).to(dev)
+        depth = torch.empty((R, R), dtype=torch.float32, device=dev)
+        rgb = torch.empty((R, R, 3), dtype=torch.float32, device=dev)
+        mask = torch.empty((R, R), dtype=torch.uint8, device=dev)
+        flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream.synchronize()
+
+    def frame():
+        vol = pifu.pifu_localize(ctx, occ, w.calib, w.n0, w.num_levels, stream=stream)
+        pifu.pifu_render(ctx, R, R, occ, col, w.calib, depth, rgb, mask, stream=stream)
+        return vol
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    for _ in range(args.warmup):
+        vol = frame()
+    stream.synchronize()
+    evals = int(vol.n_eval)
+    hits = int(mask.sum().item())
+
+    # ---- device-resident timed region --------------------------------------
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    clocks = ClockSampler(local_rank, enabled=not args.no_clocks)
+    barrier()
+    torch.cuda.synchronize()
+    pifu.pifu_profile(ctx, True)
+    for i in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        ev[i][0].record(stream)
+        frame()
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    prof = pifu.pifu_profile_read(ctx)
+    pifu.pifu_profile(ctx, False)
+    barrier()
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_s = sum(step_ms) / 1000.0
+    if world > 1:
+        t = torch.tensor([total_s], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_s = float(t.item())
+    value = world * args.steps / total_s
+
+    # ---- query points/s (raw field, inputs resident) -----------------------
+    Q = args.query_points
+    with torch.cuda.stream(stream):
+        pts = torch.from_numpy(synth.query_points(Q, seed=123)).to(dev)
+        qout = torch.empty(Q, dtype=torch.float32, device=dev)
+    stream.synchronize()
+    pifu.pifu_query(ctx, occ, w.calib, pts, qout, stream=stream)
+    qe = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+    n_q = 3
+    with torch.cuda.stream(stream):
+        flush.zero_()
+    qe[0].record(stream)
+    for _ in range(n_q):
+        pifu.pifu_query(ctx, occ, w.calib, pts, qout, stream=stream)
+    qe[1].record(stream)
+    stream.synchronize()
+    q_s = qe[0].elapsed_time(qe[1]) / 1000.0
+    query_pts_per_s = world * Q * n_q / q_s  # replicas: every rank queries its own batch
+
+    # ---- end to end through the public API with host buffers ---------------
+    h_occ = torch.from_numpy(w.occ_map).pin_memory()
+    h_col = torch.from_numpy(w.col_map).pin_memory()
+    h_depth = torch.empty((R, R), dtype=torch.float32).pin_memory()
+    h_rgb = torch.empty((R, R, 3), dtype=torch.float32).pin_memory()
+    h_mask = torch.empty((R, R), dtype=torch.uint8).pin_memory()
+    e2e_steps = max(3, min(args.steps, 10))
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        with torch.cuda.stream(stream):
+            occ.copy_(h_occ, non_blocking=True)
+            col.copy_(h_col, non_blocking=True)
+        frame()
+        with torch.cuda.stream(stream):
+            h_depth.copy_(depth, non_blocking=True)
+            h_rgb.copy_(rgb, non_blocking=True)
+            h_mask.copy_(mask, non_blocking=True)
+        stream.synchronize()
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([e2e_s], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_value = world * e2e_steps / e2e_s
+    h2d = h_occ.numel() * 4 + h_col.numel() * 4
+    d2h = h_depth.numel() * 4 + h_rgb.numel() * 4 + h_mask.numel()
+
+    pifu.pifu_destroy(ctx)
+    if rank != 0:
+        return
+
+    # ---- roofline of the dominant kernel class -----------------------------
+    peaks, peak_src = measured_peaks()
+    dom = max(prof, key=lambda k: prof[k]["ms"])
+    dk = prof["mlp_hidden"]
+    sm_mhz = peaks.get("sm_max_mhz", 2070.0)
+    peak = fp32_simt_peak_tflops(sm_mhz)
+    achieved = dk["flops"] / (dk["ms"] / 1000.0) / 1e12 if dk["ms"] > 0 else 0.0
+    digest = source_digest(["paper_2007_13988_gb300/csrc/mlp_f32.cu"])
+    traffic = recorded_traffic("sgemm_bias_lrelu", digest)
+    launches = sum(v["launches"] for v in prof.values())
+    roofline = {"bound": "alu", "kernel": "sgemm_bias_lrelu (hidden MLP layers, FP32 FFMA)",
+                "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "peak_source": f"FP32 SIMT: 152 SMs x 128 lanes x 2 flop x {sm_mhz:.0f} MHz "
+                               f"(sm_max_mhz from MEASURED_PEAKS.json, {peak_src})",
+                "traffic": None if traffic is None else traffic,
+                "avg_launch_ms": dk["ms"] / max(1, dk["launches"]),
+                "flops_per_launch": dk["flops"] / max(1, dk["launches"]),
+                "share_of_step": dk["ms"] / max(1e-9, sum(step_ms)),
+                "dominant_class": dom}
+    kernels = {k: {"launches": v["launches"] // max(1, args.steps),
+                   "ms_per_step": v["ms"] / max(1, args.steps)} for k, v in prof.items()}
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000.0 * total_s / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": workload_config(w, evals, hits),
+            "query_pts_per_s": query_pts_per_s,
+            "query": {"points": Q, "calls": n_q, "ms_per_call": 1000.0 * q_s / n_q},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h, "steps": e2e_steps},
+            "gpu_launches": launches,
+            "roofline": roofline,
+            "kernels": kernels,
+            "step_ms": {"min": min(step_ms), "median": statistics.median(step_ms),
+                        "max": max(step_ms)}}
+    if clk is not None:
+        line["clocks"] = clk
+    if world == 1 and not args.no_cpu_baseline:
+        t, cnt = oracle_frame(w)
+        line["cpu_baseline"] = {"value": 1.0 / t, "unit": UNIT, "cores": cpu_threads(),
+                                "kind": "oracle",
+                                "sample": f"one full frame of the FP64 oracle (numpy): "
+                                          f"{cnt['evals']} f_O + {cnt['hits']} f_T evaluations, "
+                                          f"localization bookkeeping and ray scan; {t:.1f} s"}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        torch.cuda.set_device(local_rank)
+        torch.distributed.init_process_group("nccl")
+    try:
+        run_ours(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch
+            torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,208 @@
+/*
+ * libpifu — C ABI of a GB300 (sm_103a) implementation of the pixel-aligned
+ * implicit occupancy field, its coarse-to-fine surface localization and
+ * mesh-free direct rendering, after Li et al., "Monocular Real-Time
+ * Volumetric Performance Capture" (arXiv 2007.13988):
+ *
+ *   Sec. 3.1, Eq. 1   O(P) = f_O(Phi(P_xy, g_O(I)), P_z)          occupancy
+ *   Sec. 3.1, Eq. 2   T(P) = f_T(Phi(P_xy, g_T), Phi(P_xy, g_O), P_z)  colour
+ *   Sec. 3.2          "Octree-based Robust Surface Localization"
+ *   Sec. 3.2, Eq. 3   "Mesh-free Rendering"
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Pointers named *_dev are CUDA device pointers owned by the caller; the
+ *   library never frees them and keeps none of them after a call returns.
+ *   Host pointers are read during the call only.
+ * - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *   stream).  Work is enqueued on it; the calls that need a host decision
+ *   (pifu_localize, pifu_render) synchronise it internally.
+ * - Every call returns a pifu_status.  Errors detectable on the host return
+ *   before any work is enqueued.  A CUDA error returns PIFU_ERR_CUDA and
+ *   leaves the context usable only if the CUDA context itself survived.
+ * - A context is bound to the device that was current at pifu_create and is
+ *   not thread-safe: one thread (or external serialisation) per context.
+ * - Feature maps are channel-last [H][W][C], C a multiple of 4, base
+ *   address 16-byte aligned.
+ * - Volume NDC is [-1, 1]^3.  A level of resolution N (cells per axis) has
+ *   N+1 nodes per axis at x_i = -1 + 2 i / N; node (i, j, k) has linear index
+ *   (k (N+1) + j) (N+1) + i (x fastest).
+ * - calib: 3x4 row-major affine map from volume NDC to the input view
+ *   (u, v, z_in); (u, v) index the feature map, z_in is the MLP's depth
+ *   input ("P_z" of Eq. 1).
+ */
+#ifndef PIFU_H
+#define PIFU_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pifu_ctx pifu_ctx;
+
+typedef enum {
+    PIFU_OK = 0,
+    PIFU_ERR_ARG = -1,            /* bad pointer, size, alignment or shape      */
+    PIFU_ERR_FORMAT = -2,         /* weight blob malformed                       */
+    PIFU_ERR_CUDA = -3,           /* a CUDA call failed                          */
+    PIFU_ERR_OOM = -4,            /* device allocation failed                    */
+    PIFU_ERR_NOT_CONVERGED = -5,  /* conflict loop hit pifu_levels.max_rounds    */
+    PIFU_ERR_TIMEOUT = -6,        /* a bounded device wait gave up               */
+    PIFU_ERR_STATE = -7,          /* call order violated (e.g. render first)     */
+    PIFU_ERR_UNSUPPORTED = -8     /* valid request outside what is implemented   */
+} pifu_status;
+
+typedef enum { PIFU_F32 = 0, PIFU_BF16 = 1 } pifu_dtype;
+
+/* MLP arithmetic.  FP32: plain single precision (SIMT FFMA).  The other
+ * values select tensor-core forms where the library provides them. */
+typedef enum { PIFU_PREC_FP32 = 0, PIFU_PREC_BF16 = 1, PIFU_PREC_MIXED = 2 } pifu_precision;
+
+/* A channel-last feature map g(I) in device memory: data[(j W + i) C + c]. */
+typedef struct {
+    const void* data;   /* device pointer, 16-byte aligned                    */
+    int32_t H, W, C;    /* H, W >= 1; C a multiple of 4                         */
+    int32_t dtype;      /* pifu_dtype                                          */
+} pifu_fmap;
+
+/* Coarse-to-fine schedule (Sec. 3.2): dense evaluation at n0 cells per axis,
+ * then num_levels-1 refinements doubling the resolution each time. */
+typedef struct {
+    int32_t n0;          /* power of two, >= 2                                 */
+    int32_t num_levels;  /* 1 .. 8; finest n0 << (num_levels-1) <= 512         */
+    int32_t precision;   /* pifu_precision                                     */
+    int32_t max_rounds;  /* cap on conflict rounds per level (<= 0: 4096)      */
+} pifu_levels;
+
+/* Target view of the render: the volume is aligned with it (Sec. 3.2), so
+ * pixel (i, j) looks along -z through x = (2i+1)/width - 1,
+ * y = (2j+1)/height - 1. */
+typedef struct {
+    int32_t width, height;
+    float background[3];  /* B of Eq. 3                                        */
+} pifu_camera;
+
+/* Result of pifu_localize: views into context memory, valid until the next
+ * pifu_localize or pifu_destroy on the same context.  Bitsets use one
+ * 32-bit word row per (k, j): bit i of row (k, j) is word
+ * (k (N+1) + j) row_words + (i >> 5), bit (i & 31); padding bits are 0. */
+typedef struct {
+    int32_t n;                    /* finest resolution (cells per axis)        */
+    int32_t num_levels;
+    int32_t row_words;            /* ceil((n+1) / 32)                          */
+    const uint32_t* occ_bits_dev; /* binarized finest level (o >= 0.5)         */
+    const uint32_t* eval_bits_dev;/* nodes the network evaluated at the finest */
+    const float* values_dev;      /* dense [(n+1)^3]; meaningful where the eval
+                                     bit is set (the network's occupancy)      */
+    int64_t n_eval;               /* network evaluations over all levels       */
+    int64_t evals_per_level[8];
+    int64_t candidates_per_level[8]; /* boundary candidates (before dilation)  */
+    int32_t conflict_rounds[8];
+} pifu_volume;
+
+/* Parse a weight blob (host memory, copied) holding the occupancy MLP f_O
+ * and the colour MLP f_T, and upload it to the current device.
+ * Blob format (little-endian): "PIFU", u32 version = 1, u32 n_nets = 2, then
+ * per net: u32 kind (0 occupancy/sigmoid, 1 colour/tanh), u32 d_in,
+ * u32 n_layers, f32 leaky slope, u32 widths[n_layers], u32 skip_mask
+ * (bit l: layer l reads [h_{l-1}, x]), then per layer f32 W[width][fan_in]
+ * row-major and f32 b[width].  Hidden widths must be multiples of 8 and the
+ * output width 1 (f_O) or 3 (f_T).  The blob is validated completely on the
+ * host before any CUDA call.  Errors: PIFU_ERR_FORMAT, PIFU_ERR_UNSUPPORTED
+ * (hidden width not a multiple of 8), PIFU_ERR_OOM, PIFU_ERR_CUDA,
+ * PIFU_ERR_ARG (null pointers). */
+int pifu_create(const void* weight_blob, size_t bytes, pifu_ctx** out);
+
+/* Release the context and all its device memory.  NULL is a no-op. */
+void pifu_destroy(pifu_ctx* ctx);
+
+/* Eq. 1 at m arbitrary points: occ_dev[p] = O(pts_dev[3p .. 3p+2]).
+ * pts_dev: device float32 [m][3] in volume NDC; occ_dev: device float32 [m].
+ * m = 0 is a no-op.  Asynchronous on `stream`. */
+int pifu_query(pifu_ctx* ctx, const pifu_fmap* occ_map, const float calib[12],
+               const float* pts_dev, int64_t m, float* occ_dev, void* stream);
+
+/* Eq. 2 at m points: rgb_dev[3p + c] = (tanh(f_T) + 1) / 2.  col_map may be
+ * NULL when f_T reads only [Phi(g_O), P_z]; otherwise its input is
+ * [Phi(g_T), Phi(g_O), P_z].  Asynchronous on `stream`. */
+int pifu_query_colour(pifu_ctx* ctx, const pifu_fmap* occ_map, const pifu_fmap* col_map,
+                      const float calib[12], const float* pts_dev, int64_t m,
+                      float* rgb_dev, void* stream);
+
+/* Sec. 3.2 coarse-to-fine localization of the 0.5 level set of Eq. 1.
+ * Level 0 is evaluated densely.  Every finer level binarizes the coarser one
+ * at 0.5, interpolates it tri-linearly onto the new nodes, evaluates the
+ * nodes whose interpolated value is neither 0 nor 1 together with their
+ * 26-neighbourhood, then repeatedly evaluates the unevaluated
+ * 26-neighbours of nodes whose binarized prediction disagrees with the
+ * binarized interpolation, until there are none.  Unevaluated nodes keep the
+ * interpolated 0/1.  Synchronises `stream` (the loop length is decided on
+ * the host).  *out receives views of the finest level and the counters.
+ * Errors: PIFU_ERR_ARG, PIFU_ERR_NOT_CONVERGED, PIFU_ERR_OOM, PIFU_ERR_CUDA,
+ * PIFU_ERR_UNSUPPORTED (precision not available). */
+int pifu_localize(pifu_ctx* ctx, const pifu_fmap* occ_map, const float calib[12],
+                  const pifu_levels* levels, void* stream, pifu_volume* out);
+
+/* Sec. 3.2 mesh-free render of the last localized volume (Eq. 3).  Each
+ * pixel's ray samples the bilinear (x, y) interpolation of the node values
+ * at every depth node from the observer (z = +1) backwards; the first sample
+ * >= 0.5 marks the surface, whose depth is the linear 0.5 crossing between it
+ * and the previous sample (z = +1 if it is the first).  Hit pixels get
+ * T(P(q), I) of Eq. 2, misses the background and mask 0.
+ * depth_dev: float32 [height][width] (NaN on misses); rgb_dev: float32
+ * [height][width][3]; mask_dev: uint8 [height][width].  Any of the three may
+ * be NULL if not wanted.  Requires a prior successful pifu_localize
+ * (PIFU_ERR_STATE otherwise).  Synchronises `stream`. */
+int pifu_render(pifu_ctx* ctx, const pifu_camera* cam, const pifu_fmap* occ_map,
+                const pifu_fmap* col_map, const float calib[12], void* stream,
+                float* depth_dev, float* rgb_dev, uint8_t* mask_dev);
+
+/* Copy the counters of the last pifu_localize into *out (host). */
+int pifu_sync_stats(pifu_ctx* ctx, pifu_volume* out);
+
+/* Static description of a status code. */
+const char* pifu_status_string(int status);
+
+/* Kernel classes counted and timed by the profiler. */
+typedef enum {
+    PIFU_K_GATHER = 0,      /* projection + bilinear gather (MLP input rows)      */
+    PIFU_K_MLP_HIDDEN = 1,  /* hidden MLP layers (the dense contraction)          */
+    PIFU_K_MLP_LAST = 2,    /* last MLP layer + activation + epilogue             */
+    PIFU_K_LEVEL = 3,       /* level set-up (dense set-up / classify, popcount)   */
+    PIFU_K_SELECT = 4,      /* 26-dilation, selection and compaction              */
+    PIFU_K_RENDER = 5,      /* ray first crossing                                 */
+    PIFU_K_COUNT = 6
+} pifu_kernel_class;
+
+/* Per-class totals since the last pifu_profile call.  `launches` counts
+ * every kernel launch of the class (always on).  `ms` sums CUDA-event
+ * durations measured on the launching stream around each launch (profiling
+ * on only).  `flops` and `bytes` are the ALGORITHMIC work of those launches
+ * (unpadded MLP shapes: 2 K N flops per point and layer; bitset, value and
+ * output bytes a launch must move at least), for roofline fractions. */
+typedef struct {
+    int64_t launches;
+    double ms;
+    double flops;
+    double bytes;
+} pifu_kernel_stats;
+
+/* Reset the counters and switch event timing on (enable != 0) or off. */
+int pifu_profile(pifu_ctx* ctx, int enable);
+
+/* Resolve pending timing events (waits for them) and copy the totals of all
+ * PIFU_K_COUNT classes into out[0 .. PIFU_K_COUNT). */
+int pifu_profile_read(pifu_ctx* ctx, pifu_kernel_stats* out);
+
+/* Text of the last CUDA error seen by this context ("" if none).  The
+ * pointer stays valid until the next call on the context. */
+const char* pifu_last_error(const pifu_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PIFU_H */

@@ -1,0 +1,210 @@
+// Plain FP32 form of the concatenation MLPs f_O and f_T (Sec. 3.1; Appendix,
+// "Pixel-aligned 3D Lifting", the "MLP" variant; the colour MLP's 1024-512-
+// 256-128-3 widths with skip connections, leaky-ReLU and tanh).
+//
+// Hidden layers run as a register-blocked SIMT SGEMM with the bias and the
+// leaky-ReLU fused into the epilogue.  A skip layer's input [h_{l-1}, x] is
+// never materialised: the K loop walks two segments, first h_{l-1}, then x,
+// against the matching column ranges of W_l.  The last layer (1 or 3
+// outputs) is a warp-per-point dot product fused with the activation and
+// with what the caller needs done with the result (store, scatter into a
+// localization level with conflict detection, or write pixels).
+//
+// This is the precision reference on the GPU (FFMA, float32 accumulation);
+// the roofline that bounds it is the FP32 SIMT FMA rate.
+#include "pifu_internal.h"
+
+namespace pifu {
+namespace {
+
+constexpr int BM = 128, BN = 128, BK = 8;
+
+__global__ void __launch_bounds__(256) sgemm_bias_lrelu_kernel(
+    int M, int N, const float* __restrict__ A1, int lda1, int K1, const float* __restrict__ A2,
+    int lda2, int K2, const float* __restrict__ W, int ldw, const float* __restrict__ bias,
+    float slope, float* __restrict__ Out, int ldo) {
+    __shared__ __align__(16) float As[2][BK][BM];
+    __shared__ __align__(16) float Bs[2][BK][BN];
+
+    const int tid = threadIdx.x;
+    const int bm = blockIdx.y * BM;
+    const int bn = blockIdx.x * BN;
+    const int nk1 = K1 / BK;
+    const int nk = nk1 + K2 / BK;
+
+    // global -> shared mapping: 128 rows x 8 k per tile, one float4 per thread
+    const int lrow = tid >> 1;
+    const int lk = (tid & 1) * 4;
+    const int gm = bm + lrow;
+    const int gn = bn + lrow;
+    const bool m_ok = gm < M;
+    const bool n_ok = gn < N;
+
+    float4 ra, rb;
+    auto load = [&](int kt) {
+        const float* src;
+        int kk;
+        int lda;
+        if (kt < nk1) {
+            src = A1; lda = lda1; kk = kt * BK;
+        } else {
+            src = A2; lda = lda2; kk = (kt - nk1) * BK;
+        }
+        ra = m_ok ? __ldg(reinterpret_cast<const float4*>(src + (int64_t)gm * lda + kk + lk))
+                  : make_float4(0.f, 0.f, 0.f, 0.f);
+        rb = n_ok ? __ldg(reinterpret_cast<const float4*>(W + (int64_t)gn * ldw + kt * BK + lk))
+                  : make_float4(0.f, 0.f, 0.f, 0.f);
+    };
+    auto store = [&](int buf) {
+        As[buf][lk + 0][lrow] = ra.x; As[buf][lk + 1][lrow] = ra.y;
+        As[buf][lk + 2][lrow] = ra.z; As[buf][lk + 3][lrow] = ra.w;
+        Bs[buf][lk + 0][lrow] = rb.x; Bs[buf][lk + 1][lrow] = rb.y;
+        Bs[buf][lk + 2][lrow] = rb.z; Bs[buf][lk + 3][lrow] = rb.w;
+    };
+
+    // compute mapping: 16 x 16 threads, each 8 x 8 outputs in two 4-wide halves
+    const int ty = tid >> 4;
+    const int tx = tid & 15;
+    float acc[8][8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+
+    if (nk > 0) {
+        load(0);
+        store(0);
+    }
+    __syncthreads();
+    for (int kt = 0; kt < nk; ++kt) {
+        const int cur = kt & 1;
+        if (kt + 1 < nk) load(kt + 1);
+#pragma unroll
+        for (int k = 0; k < BK; ++k) {
+            const float4 a0 = *reinterpret_cast<const float4*>(&As[cur][k][ty * 4]);
+            const float4 a1 = *reinterpret_cast<const float4*>(&As[cur][k][64 + ty * 4]);
+            const float4 b0 = *reinterpret_cast<const float4*>(&Bs[cur][k][tx * 4]);
+            const float4 b1 = *reinterpret_cast<const float4*>(&Bs[cur][k][64 + tx * 4]);
+            const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+            const float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+#pragma unroll
+                for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+        }
+        if (kt + 1 < nk) store(cur ^ 1);
+        __syncthreads();
+    }
+
+    // epilogue: bias + leaky-ReLU, float4 stores
+#pragma unroll
+    for (int hi = 0; hi < 2; ++hi) {
+        const int col = bn + hi * 64 + tx * 4;
+        if (col >= N) continue;
+        const float4 bb = *reinterpret_cast<const float4*>(bias + col);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int row = bm + (i < 4 ? ty * 4 + i : 64 + ty * 4 + (i - 4));
+            if (row >= M) continue;
+            float4 o;
+            o.x = acc[i][hi * 4 + 0] + bb.x;
+            o.y = acc[i][hi * 4 + 1] + bb.y;
+            o.z = acc[i][hi * 4 + 2] + bb.z;
+            o.w = acc[i][hi * 4 + 3] + bb.w;
+            o.x = o.x >= 0.f ? o.x : slope * o.x;
+            o.y = o.y >= 0.f ? o.y : slope * o.y;
+            o.z = o.z >= 0.f ? o.z : slope * o.z;
+            o.w = o.w >= 0.f ? o.w : slope * o.w;
+            *reinterpret_cast<float4*>(Out + (int64_t)row * ldo + col) = o;
+        }
+    }
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ float apply_act(int act, float t) {
+    if (act == ACT_SIGMOID) return 1.0f / (1.0f + expf(-t));
+    return 0.5f * (tanhf(t) + 1.0f);
+}
+
+__global__ void __launch_bounds__(256) last_layer_kernel(
+    int64_t p0, int64_t M, int n_out, const float* __restrict__ A1, int lda1, int K1,
+    const float* __restrict__ A2, int lda2, int K2, const float* __restrict__ W, int ldw,
+    const float* __restrict__ bias, Epilogue epi) {
+    const int lane = threadIdx.x & 31;
+    const int64_t lp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (lp >= M) return;  // whole warp exits together
+    float t[4] = {0.f, 0.f, 0.f, 0.f};
+    const float* a1 = A1 + lp * lda1;
+    const float* a2 = A2 + lp * lda2;
+    for (int k = lane; k < K1 + K2; k += 32) {
+        const float a = (k < K1) ? a1[k] : a2[k - K1];
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            if (j < n_out) t[j] = fmaf(a, W[(int64_t)j * ldw + k], t[j]);
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) t[j] = warp_sum(t[j]);
+    if (lane != 0) return;
+    const int64_t p = p0 + lp;
+    if (epi.mode == EPI_STORE) {
+        for (int j = 0; j < n_out; ++j) epi.out[p * n_out + j] = apply_act(epi.act, t[j] + bias[j]);
+    } else if (epi.mode == EPI_PIXELS) {
+        const int64_t pix = epi.pix[p];
+        for (int j = 0; j < n_out; ++j) epi.out[pix * 3 + j] = apply_act(epi.act, t[j] + bias[j]);
+    } else {
+        // Occupancy scattered into a localization level (Sec. 3.2): store the
+        // value, set the binarized bit, and flag a conflict when the
+        // binarized prediction differs from the binarized interpolation.
+        const float o = apply_act(ACT_SIGMOID, t[0] + bias[0]);
+        const int64_t idx = epi.list ? (int64_t)epi.list[p] : epi.base + p;
+        const LevelBits& lv = epi.lv;
+        lv.values[idx] = o;
+        const int64_t n1 = lv.N + 1;
+        const int64_t row = idx / n1;            // k (N+1) + j
+        const int i = (int)(idx - row * n1);
+        const int64_t w = row * lv.row_words + (i >> 5);
+        const uint32_t bit = 1u << (i & 31);
+        const bool ob = o >= kHalf;
+        if (lv.first_level) {
+            if (ob) atomicOr(&lv.bin[w], bit);
+        } else {
+            const bool tb = (lv.tent[w] & bit) != 0u;
+            if (ob != tb) {
+                atomicOr(&lv.conf[w], bit);
+                if (ob) atomicOr(&lv.bin[w], bit);
+                else atomicAnd(&lv.bin[w], ~bit);
+            }
+        }
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_sgemm_bias_lrelu(int M, int N, const float* A1, int lda1, int K1,
+                                    const float* A2, int lda2, int K2, const float* W, int ldw,
+                                    const float* bias, float slope, float* Out, int ldo,
+                                    cudaStream_t stream) {
+    if (M <= 0) return cudaSuccess;
+    dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM);
+    sgemm_bias_lrelu_kernel<<<grid, 256, 0, stream>>>(M, N, A1, lda1, K1, A2, lda2, K2, W, ldw,
+                                                      bias, slope, Out, ldo);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_last_layer(int64_t p0, int64_t M, int n_out, const float* A1, int lda1, int K1,
+                              const float* A2, int lda2, int K2, const float* W, int ldw,
+                              const float* bias, const Epilogue& epi, cudaStream_t stream) {
+    if (M <= 0) return cudaSuccess;
+    const int64_t threads = M * 32;
+    const int64_t blocks = (threads + 255) / 256;
+    last_layer_kernel<<<(unsigned)blocks, 256, 0, stream>>>(p0, M, n_out, A1, lda1, K1, A2, lda2,
+                                                           K2, W, ldw, bias, epi);
+    return cudaGetLastError();
+}
+
+}  // namespace pifu

@@ -1,0 +1,730 @@
+// C ABI of libpifu: weight-blob parsing, device memory, and the host side of
+// the coarse-to-fine localization loop and of the render (include/pifu.h).
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/pifu.h"
+#include "pifu_internal.h"
+
+using namespace pifu;
+
+namespace {
+
+constexpr int kMaxLevels = 8;
+constexpr int kMaxFine = 512;
+constexpr int64_t kChunk = 65536;   // points per MLP pass (bounds the activation workspace)
+
+struct DevLayer {
+    int n_out = 0;
+    int K1 = 0;     // columns reading h_{l-1}
+    int K2 = 0;     // columns reading x (padded to the gather's row width), 0 if none
+    int ldw = 0;    // K1 + K2
+    int fan_in = 0; // unpadded fan-in (algorithmic K)
+    float* W = nullptr;
+    float* b = nullptr;
+};
+
+struct DevNet {
+    int kind = 0;       // 0 occupancy (sigmoid), 1 colour (tanh01)
+    int d_in = 0;
+    int ldx = 0;        // gather row width: d_in rounded up to 8
+    float slope = 0.01f;
+    int max_hidden = 0;
+    std::vector<DevLayer> layers;
+};
+
+int round_up(int v, int m) { return (v + m - 1) / m * m; }
+
+// Launch counters (always on) and CUDA-event timing (when enabled) per
+// kernel class.
+struct Profiler {
+    bool on = false;
+    pifu_kernel_stats k[PIFU_K_COUNT] = {};
+    struct Pending {
+        int cls;
+        cudaEvent_t a, b;
+    };
+    std::vector<Pending> pending;
+    std::vector<cudaEvent_t> pool;
+
+    cudaEvent_t get() {
+        if (!pool.empty()) {
+            cudaEvent_t e = pool.back();
+            pool.pop_back();
+            return e;
+        }
+        cudaEvent_t e = nullptr;
+        cudaEventCreate(&e);
+        return e;
+    }
+    // Brackets one launch: call begin before, end after.
+    cudaEvent_t begin(cudaStream_t s) {
+        if (!on) return nullptr;
+        cudaEvent_t a = get();
+        cudaEventRecord(a, s);
+        return a;
+    }
+    void end(int cls, cudaEvent_t a, cudaStream_t s, double flops, double bytes) {
+        k[cls].launches += 1;
+        k[cls].flops += flops;
+        k[cls].bytes += bytes;
+        if (!on || !a) return;
+        cudaEvent_t b = get();
+        cudaEventRecord(b, s);
+        pending.push_back({cls, a, b});
+    }
+    cudaError_t resolve() {
+        cudaError_t err = cudaSuccess;
+        for (auto& p : pending) {
+            float ms = 0.f;
+            cudaError_t e = cudaEventSynchronize(p.b);
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, p.a, p.b);
+            if (e != cudaSuccess) err = e;
+            k[p.cls].ms += ms;
+            pool.push_back(p.a);
+            pool.push_back(p.b);
+        }
+        pending.clear();
+        return err;
+    }
+    void reset() {
+        resolve();
+        for (auto& x : k) x = pifu_kernel_stats{};
+    }
+    ~Profiler() {
+        for (auto& p : pending) {
+            pool.push_back(p.a);
+            pool.push_back(p.b);
+        }
+        for (auto e : pool) cudaEventDestroy(e);
+    }
+};
+
+}  // namespace
+
+struct pifu_ctx {
+    int device = 0;
+    DevNet net[2];
+    std::string last_error;
+    // MLP activation workspace
+    float* X = nullptr;
+    float* HA = nullptr;
+    float* HB = nullptr;
+    int64_t X_cap = 0, H_cap = 0;   // floats
+    // level workspace, sized for ws_N
+    int ws_N = 0;
+    uint32_t* cand = nullptr;
+    uint32_t* tent = nullptr;
+    uint32_t* bin[2] = {nullptr, nullptr};
+    uint32_t* eval = nullptr;
+    uint32_t* conf[2] = {nullptr, nullptr};
+    float* values = nullptr;
+    int* list = nullptr;
+    unsigned int* d_count = nullptr;
+    unsigned int* h_count = nullptr;          // pinned
+    unsigned long long* d_pop = nullptr;      // [kMaxLevels]
+    unsigned long long* h_pop = nullptr;      // pinned [kMaxLevels]
+    // render workspace
+    float* hit_xyz = nullptr;
+    int* hit_pix = nullptr;
+    int64_t hit_cap = 0;
+    // last localized volume
+    bool have_volume = false;
+    int vol_N = 0;
+    int vol_bin = 0;
+    pifu_volume stats{};
+    Profiler prof;
+};
+
+namespace {
+
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) { ok = false; return; }
+        if (prev != dev && cudaSetDevice(dev) != cudaSuccess) ok = false;
+    }
+    ~DeviceGuard() {
+        int cur;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+int fail_cuda(pifu_ctx* ctx, cudaError_t e) {
+    if (ctx) ctx->last_error = cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? PIFU_ERR_OOM : PIFU_ERR_CUDA;
+}
+
+#define CK(expr)                                      \
+    do {                                              \
+        cudaError_t e_ = (expr);                      \
+        if (e_ != cudaSuccess) return fail_cuda(ctx, e_); \
+    } while (0)
+
+template <typename T>
+cudaError_t dev_alloc(T** p, int64_t n) {
+    *p = nullptr;
+    if (n <= 0) return cudaSuccess;
+    return cudaMalloc(reinterpret_cast<void**>(p), (size_t)n * sizeof(T));
+}
+
+template <typename T>
+void dev_free(T*& p) {
+    if (p) cudaFree(p);
+    p = nullptr;
+}
+
+// ---- weight blob ------------------------------------------------------------
+
+struct Reader {
+    const uint8_t* p;
+    size_t n, off = 0;
+    bool get(void* dst, size_t bytes) {
+        if (off + bytes > n || off + bytes < off) return false;
+        std::memcpy(dst, p + off, bytes);
+        off += bytes;
+        return true;
+    }
+    bool u32(uint32_t& v) { return get(&v, 4); }
+    bool f32(float& v) { return get(&v, 4); }
+};
+
+// Host copy of one parsed net: per layer the repacked weights
+// [n_out][K1 | x padded to ldx] and the bias padded to a multiple of 4.
+struct HostNet {
+    DevNet shape;
+    std::vector<std::vector<float>> W, b;
+};
+
+int parse_net(Reader& rd, HostNet& hn, int want_kind) {
+    uint32_t kind, d_in, n_layers, skip_mask;
+    float slope;
+    if (!rd.u32(kind) || !rd.u32(d_in) || !rd.u32(n_layers) || !rd.f32(slope)) return PIFU_ERR_FORMAT;
+    if ((int)kind != want_kind || d_in == 0 || d_in > 4096 || n_layers == 0 || n_layers > 16)
+        return PIFU_ERR_FORMAT;
+    std::vector<uint32_t> widths(n_layers);
+    for (auto& w : widths)
+        if (!rd.u32(w) || w == 0 || w > 8192) return PIFU_ERR_FORMAT;
+    if (!rd.u32(skip_mask)) return PIFU_ERR_FORMAT;
+    const uint32_t n_out = widths[n_layers - 1];
+    if ((kind == 0 && n_out != 1) || (kind == 1 && n_out != 3)) return PIFU_ERR_FORMAT;
+    for (uint32_t l = 0; l + 1 < n_layers; ++l)
+        if (widths[l] % 8 != 0) return PIFU_ERR_UNSUPPORTED;
+    DevNet& net = hn.shape;
+    net.kind = (int)kind;
+    net.d_in = (int)d_in;
+    net.ldx = round_up((int)d_in, 8);
+    net.slope = slope;
+    net.layers.assign(n_layers, DevLayer{});
+    net.max_hidden = 0;
+    hn.W.assign(n_layers, {});
+    hn.b.assign(n_layers, {});
+    for (uint32_t l = 0; l < n_layers; ++l) {
+        const bool skip = (l > 0) && ((skip_mask >> l) & 1u);
+        const int prev = l == 0 ? 0 : (int)widths[l - 1];
+        const int fan_in = (l == 0 ? (int)d_in : prev) + (skip ? (int)d_in : 0);
+        DevLayer& L = net.layers[l];
+        L.n_out = (int)widths[l];
+        L.K1 = l == 0 ? 0 : prev;
+        L.K2 = (l == 0 || skip) ? net.ldx : 0;
+        L.ldw = L.K1 + L.K2;
+        L.fan_in = fan_in;
+        if (l + 1 < n_layers) net.max_hidden = std::max(net.max_hidden, L.n_out);
+        std::vector<float> w((size_t)L.n_out * fan_in), b(L.n_out);
+        if (!rd.get(w.data(), w.size() * 4) || !rd.get(b.data(), b.size() * 4)) return PIFU_ERR_FORMAT;
+        std::vector<float>& wp = hn.W[l];
+        wp.assign((size_t)L.n_out * L.ldw, 0.f);
+        for (int o = 0; o < L.n_out; ++o) {
+            const float* src = w.data() + (size_t)o * fan_in;
+            float* dst = wp.data() + (size_t)o * L.ldw;
+            if (l == 0) {
+                std::memcpy(dst, src, d_in * 4);
+            } else {
+                std::memcpy(dst, src, prev * 4);
+                if (skip) std::memcpy(dst + L.K1, src + prev, d_in * 4);
+            }
+        }
+        hn.b[l].assign(round_up(L.n_out, 4), 0.f);
+        std::memcpy(hn.b[l].data(), b.data(), L.n_out * 4);
+    }
+    return PIFU_OK;
+}
+
+int upload_net(pifu_ctx* ctx, const HostNet& hn, DevNet& net) {
+    net = hn.shape;
+    for (auto& L : net.layers) L.W = L.b = nullptr;
+    for (size_t l = 0; l < net.layers.size(); ++l) {
+        DevLayer& L = net.layers[l];
+        CK(dev_alloc(&L.W, (int64_t)hn.W[l].size()));
+        CK(dev_alloc(&L.b, (int64_t)hn.b[l].size()));
+        CK(cudaMemcpy(L.W, hn.W[l].data(), hn.W[l].size() * 4, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(L.b, hn.b[l].data(), hn.b[l].size() * 4, cudaMemcpyHostToDevice));
+    }
+    return PIFU_OK;
+}
+
+void free_net(DevNet& net) {
+    for (auto& L : net.layers) {
+        dev_free(L.W);
+        dev_free(L.b);
+    }
+    net.layers.clear();
+}
+
+// ---- workspaces -------------------------------------------------------------
+
+int ensure_mlp_ws(pifu_ctx* ctx) {
+    int64_t need_x = 0, need_h = 0;
+    for (const DevNet& n : ctx->net) {
+        need_x = std::max<int64_t>(need_x, kChunk * n.ldx);
+        need_h = std::max<int64_t>(need_h, kChunk * std::max(n.max_hidden, 8));
+    }
+    if (need_x > ctx->X_cap) {
+        dev_free(ctx->X);
+        CK(dev_alloc(&ctx->X, need_x));
+        ctx->X_cap = need_x;
+    }
+    if (need_h > ctx->H_cap) {
+        dev_free(ctx->HA);
+        dev_free(ctx->HB);
+        CK(dev_alloc(&ctx->HA, need_h));
+        CK(dev_alloc(&ctx->HB, need_h));
+        ctx->H_cap = need_h;
+    }
+    return PIFU_OK;
+}
+
+int ensure_level_ws(pifu_ctx* ctx, int N) {
+    if (N <= ctx->ws_N) return PIFU_OK;
+    uint32_t** bitsets[] = {&ctx->cand, &ctx->tent, &ctx->bin[0], &ctx->bin[1],
+                            &ctx->eval, &ctx->conf[0], &ctx->conf[1]};
+    for (auto b : bitsets) dev_free(*b);
+    dev_free(ctx->values);
+    dev_free(ctx->list);
+    ctx->ws_N = 0;
+    ctx->have_volume = false;
+    const int64_t words = words_of(N);
+    const int64_t nodes = (int64_t)(N + 1) * (N + 1) * (N + 1);
+    for (auto b : bitsets) {
+        CK(dev_alloc(b, words));
+        CK(cudaMemset(*b, 0, (size_t)words * 4));
+    }
+    CK(dev_alloc(&ctx->values, nodes));
+    CK(dev_alloc(&ctx->list, nodes));
+    ctx->ws_N = N;
+    return PIFU_OK;
+}
+
+int ensure_hit_ws(pifu_ctx* ctx, int64_t npix) {
+    if (npix <= ctx->hit_cap) return PIFU_OK;
+    dev_free(ctx->hit_xyz);
+    dev_free(ctx->hit_pix);
+    ctx->hit_cap = 0;
+    CK(dev_alloc(&ctx->hit_xyz, 3 * npix));
+    CK(dev_alloc(&ctx->hit_pix, npix));
+    ctx->hit_cap = npix;
+    return PIFU_OK;
+}
+
+// ---- argument checks ----------------------------------------------------------
+
+bool map_ok(const pifu_fmap* m) {
+    if (!m || !m->data) return false;
+    if (m->H < 1 || m->W < 1 || m->C < 4 || m->C % 4 != 0) return false;
+    if (m->H > 65536 || m->W > 65536) return false;
+    if ((reinterpret_cast<uintptr_t>(m->data) & 15u) != 0) return false;
+    return m->dtype == PIFU_F32 || m->dtype == PIFU_BF16;
+}
+
+Map to_map(const pifu_fmap* m) {
+    Map r{};
+    if (m) {
+        r.data = m->data;
+        r.H = m->H;
+        r.W = m->W;
+        r.C = m->C;
+        r.dtype = m->dtype;
+    }
+    return r;
+}
+
+Calib to_calib(const float* c) {
+    Calib r;
+    std::memcpy(r.c, c, sizeof(r.c));
+    return r;
+}
+
+bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
+
+// ---- the MLP over a point batch ---------------------------------------------------
+
+int run_mlp(pifu_ctx* ctx, const DevNet& net, const PointSrc& src, int64_t m, const Map& map0,
+            const Map& map1, const Calib& calib, const Epilogue& epi, cudaStream_t s) {
+    const int L = (int)net.layers.size();
+    Profiler& pr = ctx->prof;
+    for (int64_t p0 = 0; p0 < m; p0 += kChunk) {
+        const int64_t mc = std::min<int64_t>(kChunk, m - p0);
+        // gather: 4 taps x C channels read (L2), one padded row written
+        cudaEvent_t ev = pr.begin(s);
+        CK(launch_gather(src, p0, mc, calib, map0, map1, ctx->X, net.ldx, s));
+        pr.end(PIFU_K_GATHER, ev, s, 0.0,
+               (double)mc * (4.0 * (map0.C + map1.C) + net.ldx) * 4.0);
+        const float* h = nullptr;
+        int hw = 0;
+        for (int l = 0; l + 1 < L; ++l) {
+            const DevLayer& Ly = net.layers[l];
+            float* out = (l % 2 == 0) ? ctx->HA : ctx->HB;
+            ev = pr.begin(s);
+            CK(launch_sgemm_bias_lrelu((int)mc, Ly.n_out, h, hw, Ly.K1, ctx->X, net.ldx, Ly.K2, Ly.W,
+                                       Ly.ldw, Ly.b, net.slope, out, Ly.n_out, s));
+            pr.end(PIFU_K_MLP_HIDDEN, ev, s, 2.0 * mc * Ly.fan_in * Ly.n_out,
+                   4.0 * ((double)mc * (Ly.fan_in + Ly.n_out) + (double)Ly.n_out * (Ly.fan_in + 1)));
+            h = out;
+            hw = Ly.n_out;
+        }
+        const DevLayer& Ll = net.layers[L - 1];
+        ev = pr.begin(s);
+        CK(launch_last_layer(p0, mc, Ll.n_out, h, hw, Ll.K1, ctx->X, net.ldx, Ll.K2, Ll.W, Ll.ldw,
+                             Ll.b, epi, s));
+        pr.end(PIFU_K_MLP_LAST, ev, s, 2.0 * mc * Ll.fan_in * Ll.n_out,
+               4.0 * (double)mc * (Ll.fan_in + Ll.n_out));
+    }
+    return PIFU_OK;
+}
+
+int read_count(pifu_ctx* ctx, cudaStream_t s, unsigned int* out) {
+    CK(cudaMemcpyAsync(ctx->h_count, ctx->d_count, sizeof(unsigned int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    *out = *ctx->h_count;
+    return PIFU_OK;
+}
+
+}  // namespace
+
+// ============================================================================
+extern "C" {
+
+const char* pifu_status_string(int status) {
+    switch (status) {
+        case PIFU_OK: return "ok";
+        case PIFU_ERR_ARG: return "invalid argument";
+        case PIFU_ERR_FORMAT: return "malformed weight blob";
+        case PIFU_ERR_CUDA: return "CUDA error";
+        case PIFU_ERR_OOM: return "out of device memory";
+        case PIFU_ERR_NOT_CONVERGED: return "conflict loop did not converge within max_rounds";
+        case PIFU_ERR_TIMEOUT: return "bounded device wait timed out";
+        case PIFU_ERR_STATE: return "call order violated";
+        case PIFU_ERR_UNSUPPORTED: return "unsupported configuration";
+        default: return "unknown status";
+    }
+}
+
+const char* pifu_last_error(const pifu_ctx* ctx) {
+    return ctx ? ctx->last_error.c_str() : "";
+}
+
+int pifu_create(const void* weight_blob, size_t bytes, pifu_ctx** out) {
+    if (!out) return PIFU_ERR_ARG;
+    *out = nullptr;
+    if (!weight_blob) return PIFU_ERR_ARG;
+    // Parse and validate the whole blob on the host before touching CUDA.
+    Reader rd{static_cast<const uint8_t*>(weight_blob), bytes};
+    char magic[4];
+    uint32_t version, n_nets;
+    if (!rd.get(magic, 4) || std::memcmp(magic, "PIFU", 4) != 0) return PIFU_ERR_FORMAT;
+    if (!rd.u32(version) || version != 1 || !rd.u32(n_nets) || n_nets != 2) return PIFU_ERR_FORMAT;
+    HostNet hn[2];
+    int st = parse_net(rd, hn[0], 0);
+    if (st == PIFU_OK) st = parse_net(rd, hn[1], 1);
+    if (st == PIFU_OK && rd.off != rd.n) st = PIFU_ERR_FORMAT;
+    if (st != PIFU_OK) return st;
+    pifu_ctx* ctx = new pifu_ctx();
+    if (cudaGetDevice(&ctx->device) != cudaSuccess) {
+        delete ctx;
+        return PIFU_ERR_CUDA;
+    }
+    st = upload_net(ctx, hn[0], ctx->net[0]);
+    if (st == PIFU_OK) st = upload_net(ctx, hn[1], ctx->net[1]);
+    if (st == PIFU_OK) st = ensure_mlp_ws(ctx);
+    if (st == PIFU_OK) {
+        cudaError_t e = cudaMalloc(&ctx->d_count, sizeof(unsigned int));
+        if (e == cudaSuccess) e = cudaMalloc(&ctx->d_pop, kMaxLevels * sizeof(unsigned long long));
+        if (e == cudaSuccess) e = cudaHostAlloc(&ctx->h_count, sizeof(unsigned int), cudaHostAllocDefault);
+        if (e == cudaSuccess)
+            e = cudaHostAlloc(&ctx->h_pop, kMaxLevels * sizeof(unsigned long long), cudaHostAllocDefault);
+        if (e != cudaSuccess) st = fail_cuda(ctx, e);
+    }
+    if (st != PIFU_OK) {
+        pifu_destroy(ctx);
+        return st;
+    }
+    *out = ctx;
+    return PIFU_OK;
+}
+
+void pifu_destroy(pifu_ctx* ctx) {
+    if (!ctx) return;
+    DeviceGuard g(ctx->device);
+    free_net(ctx->net[0]);
+    free_net(ctx->net[1]);
+    dev_free(ctx->X);
+    dev_free(ctx->HA);
+    dev_free(ctx->HB);
+    uint32_t** bitsets[] = {&ctx->cand, &ctx->tent, &ctx->bin[0], &ctx->bin[1],
+                            &ctx->eval, &ctx->conf[0], &ctx->conf[1]};
+    for (auto b : bitsets) dev_free(*b);
+    dev_free(ctx->values);
+    dev_free(ctx->list);
+    dev_free(ctx->d_count);
+    dev_free(ctx->d_pop);
+    dev_free(ctx->hit_xyz);
+    dev_free(ctx->hit_pix);
+    if (ctx->h_count) cudaFreeHost(ctx->h_count);
+    if (ctx->h_pop) cudaFreeHost(ctx->h_pop);
+    delete ctx;
+}
+
+int pifu_query(pifu_ctx* ctx, const pifu_fmap* occ_map, const float calib[12],
+               const float* pts_dev, int64_t m, float* occ_dev, void* stream) {
+    if (!ctx || !calib || m < 0) return PIFU_ERR_ARG;
+    if (m == 0) return PIFU_OK;
+    if (!pts_dev || !occ_dev || !map_ok(occ_map)) return PIFU_ERR_ARG;
+    if (occ_map->dtype != PIFU_F32) return PIFU_ERR_UNSUPPORTED;
+    if (ctx->net[0].d_in != occ_map->C + 1) return PIFU_ERR_ARG;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return PIFU_ERR_CUDA;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    PointSrc src{PTS_XYZ, pts_dev, nullptr, 0, 0};
+    Epilogue epi{};
+    epi.mode = EPI_STORE;
+    epi.act = ACT_SIGMOID;
+    epi.out = occ_dev;
+    return run_mlp(ctx, ctx->net[0], src, m, to_map(occ_map), Map{}, to_calib(calib), epi, s);
+}
+
+int pifu_query_colour(pifu_ctx* ctx, const pifu_fmap* occ_map, const pifu_fmap* col_map,
+                      const float calib[12], const float* pts_dev, int64_t m, float* rgb_dev,
+                      void* stream) {
+    if (!ctx || !calib || m < 0) return PIFU_ERR_ARG;
+    if (m == 0) return PIFU_OK;
+    if (!pts_dev || !rgb_dev || !map_ok(occ_map) || (col_map && !map_ok(col_map))) return PIFU_ERR_ARG;
+    if (occ_map->dtype != PIFU_F32 || (col_map && col_map->dtype != PIFU_F32)) return PIFU_ERR_UNSUPPORTED;
+    const int c_t = col_map ? col_map->C : 0;
+    if (ctx->net[1].d_in != c_t + occ_map->C + 1) return PIFU_ERR_ARG;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return PIFU_ERR_CUDA;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    PointSrc src{PTS_XYZ, pts_dev, nullptr, 0, 0};
+    Epilogue epi{};
+    epi.mode = EPI_STORE;
+    epi.act = ACT_TANH01;
+    epi.out = rgb_dev;
+    const Map m0 = col_map ? to_map(col_map) : to_map(occ_map);
+    const Map m1 = col_map ? to_map(occ_map) : Map{};
+    return run_mlp(ctx, ctx->net[1], src, m, m0, m1, to_calib(calib), epi, s);
+}
+
+int pifu_localize(pifu_ctx* ctx, const pifu_fmap* occ_map, const float calib[12],
+                  const pifu_levels* lv, void* stream, pifu_volume* out) {
+    if (!ctx || !calib || !lv || !map_ok(occ_map)) return PIFU_ERR_ARG;
+    if (!is_pow2(lv->n0) || lv->n0 < 2 || lv->num_levels < 1 || lv->num_levels > kMaxLevels)
+        return PIFU_ERR_ARG;
+    const int64_t n_fine = (int64_t)lv->n0 << (lv->num_levels - 1);
+    if (n_fine > kMaxFine) return PIFU_ERR_ARG;
+    if (lv->precision != PIFU_PREC_FP32) return PIFU_ERR_UNSUPPORTED;
+    if (occ_map->dtype != PIFU_F32) return PIFU_ERR_UNSUPPORTED;
+    if (ctx->net[0].d_in != occ_map->C + 1) return PIFU_ERR_ARG;
+    const int max_rounds = lv->max_rounds > 0 ? lv->max_rounds : 4096;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return PIFU_ERR_CUDA;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    ctx->have_volume = false;
+    int st = ensure_level_ws(ctx, (int)n_fine);
+    if (st != PIFU_OK) return st;
+
+    pifu_volume vs{};
+    vs.num_levels = lv->num_levels;
+    const Map map = to_map(occ_map);
+    const Calib cal = to_calib(calib);
+    const DevNet& net = ctx->net[0];
+    CK(cudaMemsetAsync(ctx->d_pop, 0, kMaxLevels * sizeof(unsigned long long), s));
+
+    // level 0: dense evaluation of every node
+    int N = lv->n0;
+    int cur = 0;
+    {
+        cudaEvent_t ev = ctx->prof.begin(s);
+        CK(launch_dense_setup(N, ctx->cand, ctx->tent, ctx->bin[cur], ctx->eval, ctx->conf[0], s));
+        ctx->prof.end(PIFU_K_LEVEL, ev, s, 0.0, 5.0 * 4.0 * words_of(N));
+    }
+    {
+        const int64_t nodes = (int64_t)(N + 1) * (N + 1) * (N + 1);
+        PointSrc src{PTS_DENSE, nullptr, nullptr, 0, N};
+        Epilogue epi{};
+        epi.mode = EPI_LEVEL;
+        epi.list = nullptr;
+        epi.base = 0;
+        epi.lv = LevelBits{ctx->values, ctx->tent, ctx->bin[cur], ctx->conf[0], N, row_words_of(N), 1};
+        st = run_mlp(ctx, net, src, nodes, map, Map{}, cal, epi, s);
+        if (st != PIFU_OK) return st;
+        vs.evals_per_level[0] = nodes;
+        vs.n_eval = nodes;
+    }
+    // finer levels
+    for (int l = 1; l < lv->num_levels; ++l) {
+        const int prev = cur;
+        cur ^= 1;
+        N *= 2;
+        const int rw = row_words_of(N);
+        const double wbytes = 4.0 * words_of(N);
+        cudaEvent_t ev = ctx->prof.begin(s);
+        CK(launch_classify(ctx->bin[prev], N, ctx->cand, ctx->tent, ctx->bin[cur], ctx->eval,
+                           ctx->conf[0], s));
+        ctx->prof.end(PIFU_K_LEVEL, ev, s, 0.0, 4.0 * words_of(N / 2) + 5.0 * wbytes);
+        ev = ctx->prof.begin(s);
+        CK(launch_popcount(ctx->cand, words_of(N), ctx->d_pop + l, s));
+        ctx->prof.end(PIFU_K_LEVEL, ev, s, 0.0, wbytes);
+        // boundary candidates and their 1-ring
+        CK(cudaMemsetAsync(ctx->d_count, 0, sizeof(unsigned int), s));
+        ev = ctx->prof.begin(s);
+        CK(launch_dilate_select(ctx->cand, ctx->eval, ctx->conf[1], N, ctx->list, ctx->d_count, s));
+        unsigned int n = 0;
+        st = read_count(ctx, s, &n);
+        if (st != PIFU_OK) return st;
+        ctx->prof.end(PIFU_K_SELECT, ev, s, 0.0, 4.0 * wbytes + 4.0 * n);
+        int64_t level_evals = 0;
+        int q = 0;     // conflicts of the next evaluation go to conf[q]
+        int rounds = 0;
+        PointSrc src{PTS_LIST, nullptr, ctx->list, 0, N};
+        Epilogue epi{};
+        epi.mode = EPI_LEVEL;
+        epi.list = ctx->list;
+        while (n > 0) {
+            epi.lv = LevelBits{ctx->values, ctx->tent, ctx->bin[cur], ctx->conf[q], N, rw, 0};
+            st = run_mlp(ctx, net, src, n, map, Map{}, cal, epi, s);
+            if (st != PIFU_OK) return st;
+            level_evals += n;
+            // unevaluated 1-ring of this evaluation's conflicts
+            CK(cudaMemsetAsync(ctx->d_count, 0, sizeof(unsigned int), s));
+            ev = ctx->prof.begin(s);
+            CK(launch_dilate_select(ctx->conf[q], ctx->eval, ctx->conf[1 - q], N, ctx->list,
+                                    ctx->d_count, s));
+            st = read_count(ctx, s, &n);
+            if (st != PIFU_OK) return st;
+            ctx->prof.end(PIFU_K_SELECT, ev, s, 0.0, 4.0 * wbytes + 4.0 * n);
+            if (n > 0) {
+                if (rounds >= max_rounds) return PIFU_ERR_NOT_CONVERGED;
+                ++rounds;
+            }
+            q = 1 - q;
+        }
+        vs.evals_per_level[l] = level_evals;
+        vs.conflict_rounds[l] = rounds;
+        vs.n_eval += level_evals;
+    }
+    CK(cudaMemcpyAsync(ctx->h_pop, ctx->d_pop, kMaxLevels * sizeof(unsigned long long),
+                       cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    for (int l = 1; l < lv->num_levels; ++l) vs.candidates_per_level[l] = (int64_t)ctx->h_pop[l];
+    vs.n = N;
+    vs.row_words = row_words_of(N);
+    vs.occ_bits_dev = ctx->bin[cur];
+    vs.eval_bits_dev = ctx->eval;
+    vs.values_dev = ctx->values;
+    ctx->stats = vs;
+    ctx->have_volume = true;
+    ctx->vol_N = N;
+    ctx->vol_bin = cur;
+    if (out) *out = vs;
+    return PIFU_OK;
+}
+
+int pifu_render(pifu_ctx* ctx, const pifu_camera* cam, const pifu_fmap* occ_map,
+                const pifu_fmap* col_map, const float calib[12], void* stream, float* depth_dev,
+                float* rgb_dev, uint8_t* mask_dev) {
+    if (!ctx || !cam || !calib) return PIFU_ERR_ARG;
+    if (cam->width < 1 || cam->height < 1 || cam->width > 16384 || cam->height > 16384)
+        return PIFU_ERR_ARG;
+    if (!ctx->have_volume) return PIFU_ERR_STATE;
+    if (rgb_dev) {
+        if (!map_ok(occ_map) || (col_map && !map_ok(col_map))) return PIFU_ERR_ARG;
+        if (occ_map->dtype != PIFU_F32 || (col_map && col_map->dtype != PIFU_F32))
+            return PIFU_ERR_UNSUPPORTED;
+        const int c_t = col_map ? col_map->C : 0;
+        if (ctx->net[1].d_in != c_t + occ_map->C + 1) return PIFU_ERR_ARG;
+    }
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return PIFU_ERR_CUDA;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int64_t npix = (int64_t)cam->width * cam->height;
+    int st = ensure_hit_ws(ctx, npix);
+    if (st != PIFU_OK) return st;
+    RenderArgs a{};
+    a.width = cam->width;
+    a.height = cam->height;
+    a.N = ctx->vol_N;
+    a.row_words = row_words_of(ctx->vol_N);
+    a.values = ctx->values;
+    a.eval = ctx->eval;
+    a.bin = ctx->bin[ctx->vol_bin];
+    for (int c = 0; c < 3; ++c) a.bg[c] = cam->background[c];
+    a.depth = depth_dev;
+    a.rgb = rgb_dev;
+    a.mask = mask_dev;
+    a.hit_xyz = ctx->hit_xyz;
+    a.hit_pix = ctx->hit_pix;
+    a.hit_count = ctx->d_count;
+    CK(cudaMemsetAsync(ctx->d_count, 0, sizeof(unsigned int), s));
+    cudaEvent_t ev = ctx->prof.begin(s);
+    CK(launch_render_rays(a, s));
+    unsigned int n = 0;
+    st = read_count(ctx, s, &n);
+    if (st != PIFU_OK) return st;
+    {
+        // the volume once (two bitsets + the evaluated values) and the outputs
+        const double vol_bytes = 2.0 * 4.0 * words_of(ctx->vol_N) + 4.0 * (double)ctx->stats.evals_per_level[ctx->stats.num_levels - 1];
+        const double out_bytes = (double)npix * ((depth_dev ? 4 : 0) + (rgb_dev ? 12 : 0) + (mask_dev ? 1 : 0));
+        ctx->prof.end(PIFU_K_RENDER, ev, s, 0.0, vol_bytes + out_bytes + 16.0 * n);
+    }
+    if (!rgb_dev) return PIFU_OK;
+    if (n == 0) return PIFU_OK;
+    PointSrc src{PTS_XYZ, ctx->hit_xyz, nullptr, 0, 0};
+    Epilogue epi{};
+    epi.mode = EPI_PIXELS;
+    epi.act = ACT_TANH01;
+    epi.out = rgb_dev;
+    epi.pix = ctx->hit_pix;
+    const Map m0 = col_map ? to_map(col_map) : to_map(occ_map);
+    const Map m1 = col_map ? to_map(occ_map) : Map{};
+    return run_mlp(ctx, ctx->net[1], src, n, m0, m1, to_calib(calib), epi, s);
+}
+
+int pifu_profile(pifu_ctx* ctx, int enable) {
+    if (!ctx) return PIFU_ERR_ARG;
+    DeviceGuard g(ctx->device);
+    ctx->prof.reset();
+    ctx->prof.on = enable != 0;
+    return PIFU_OK;
+}
+
+int pifu_profile_read(pifu_ctx* ctx, pifu_kernel_stats* out) {
+    if (!ctx || !out) return PIFU_ERR_ARG;
+    DeviceGuard g(ctx->device);
+    cudaError_t e = ctx->prof.resolve();
+    if (e != cudaSuccess) return fail_cuda(ctx, e);
+    for (int i = 0; i < PIFU_K_COUNT; ++i) out[i] = ctx->prof.k[i];
+    return PIFU_OK;
+}
+
+int pifu_sync_stats(pifu_ctx* ctx, pifu_volume* out) {
+    if (!ctx || !out) return PIFU_ERR_ARG;
+    if (!ctx->have_volume) return PIFU_ERR_STATE;
+    *out = ctx->stats;
+    return PIFU_OK;
+}
+
+}  // extern "C"

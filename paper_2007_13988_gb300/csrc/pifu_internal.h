@@ -1,0 +1,129 @@
+// Internal declarations shared by the translation units of libpifu.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace pifu {
+
+constexpr float kHalf = 0.5f;
+
+// 3x4 calibration passed by value to kernels.
+struct Calib {
+    float c[12];
+};
+
+// A feature map as the kernels see it.
+struct Map {
+    const void* data;
+    int H, W, C;
+    int dtype;  // 0 f32, 1 bf16
+};
+
+// Where the points of an MLP batch come from.
+enum PointMode : int {
+    PTS_XYZ = 0,    // float32 [m][3] positions
+    PTS_LIST = 1,   // int32 node indices of a level with N cells per axis
+    PTS_DENSE = 2,  // node index = base + point number
+};
+
+struct PointSrc {
+    int mode;
+    const float* xyz;   // PTS_XYZ
+    const int* list;    // PTS_LIST
+    int64_t base;       // PTS_DENSE first node index
+    int N;              // grid modes: cells per axis
+};
+
+// What the last MLP layer does with its output.
+enum EpilogueMode : int {
+    EPI_STORE = 0,   // out[p * n_out + c] = act(t)
+    EPI_LEVEL = 1,   // scatter occupancy into a level (values, bits, conflicts)
+    EPI_PIXELS = 2,  // out[pix[p] * 3 + c] = act(t)
+};
+
+enum OutAct : int { ACT_SIGMOID = 0, ACT_TANH01 = 1 };
+
+struct LevelBits {
+    float* values;          // dense [(N+1)^3]
+    const uint32_t* tent;   // tentative binarized values (read-only during a level)
+    uint32_t* bin;          // working binarized values
+    uint32_t* conf;         // conflicts found by this evaluation
+    int N;
+    int row_words;
+    int first_level;        // 1: no tentative values, no conflicts
+};
+
+struct Epilogue {
+    int mode;
+    int act;
+    float* out;             // EPI_STORE / EPI_PIXELS
+    const int* pix;         // EPI_PIXELS pixel index per point
+    const int* list;        // EPI_LEVEL node index per point (null: dense from base)
+    int64_t base;           // EPI_LEVEL dense base
+    LevelBits lv;
+};
+
+// --- gather.cu -------------------------------------------------------------
+// X[p][0 .. ldx) = [Phi(map0), Phi(map1) (if C1 > 0), z_in, 0 ...] for the
+// points p in [p0, p0 + m).
+cudaError_t launch_gather(const PointSrc& src, int64_t p0, int64_t m, const Calib& calib,
+                          const Map& map0, const Map& map1, float* X, int ldx,
+                          cudaStream_t stream);
+
+// --- mlp_f32.cu ------------------------------------------------------------
+// Out[M][N] = lrelu(A1[M][K1] W[:, :K1]^T + A2[M][K2] W[:, K1:]^T + b);
+// K1, K2 multiples of 8; N a multiple of 4; ld* multiples of 4.
+cudaError_t launch_sgemm_bias_lrelu(int M, int N, const float* A1, int lda1, int K1,
+                                    const float* A2, int lda2, int K2, const float* W, int ldw,
+                                    const float* bias, float slope, float* Out, int ldo,
+                                    cudaStream_t stream);
+
+// Last layer (n_out <= 4 outputs) plus activation and epilogue, one warp per point.
+cudaError_t launch_last_layer(int64_t p0, int64_t M, int n_out, const float* A1, int lda1, int K1,
+                              const float* A2, int lda2, int K2, const float* W, int ldw,
+                              const float* bias, const Epilogue& epi, cudaStream_t stream);
+
+// --- localize.cu -----------------------------------------------------------
+__host__ __device__ inline int row_words_of(int N) { return (N + 1 + 31) / 32; }
+__host__ __device__ inline int64_t words_of(int N) {
+    return (int64_t)(N + 1) * (N + 1) * row_words_of(N);
+}
+
+// Level set-up from the binarized coarse level (N/2 cells): tentative bits,
+// candidate bits; clears eval, conf0 and the working bits (= tentative).
+cudaError_t launch_classify(const uint32_t* coarse_bin, int N, uint32_t* cand, uint32_t* tent,
+                            uint32_t* bin, uint32_t* eval, uint32_t* conf0, cudaStream_t stream);
+
+// Level-0 set-up: everything empty except eval = all nodes.
+cudaError_t launch_dense_setup(int N, uint32_t* cand, uint32_t* tent, uint32_t* bin,
+                               uint32_t* eval, uint32_t* conf0, cudaStream_t stream);
+
+// sel = dilate26(src) & ~eval; eval |= sel; clear[w] = 0 (if non-null);
+// append the node indices of sel to list at *count.
+cudaError_t launch_dilate_select(const uint32_t* src, uint32_t* eval, uint32_t* clear, int N,
+                                 int* list, unsigned int* count, cudaStream_t stream);
+
+// Population count of a bitset (for statistics) added into *count.
+cudaError_t launch_popcount(const uint32_t* bits, int64_t words, unsigned long long* count,
+                            cudaStream_t stream);
+
+// --- render.cu -------------------------------------------------------------
+struct RenderArgs {
+    int width, height;
+    int N, row_words;
+    const float* values;
+    const uint32_t* eval;
+    const uint32_t* bin;
+    float bg[3];
+    float* depth;         // may be null
+    float* rgb;           // may be null
+    uint8_t* mask;        // may be null
+    float* hit_xyz;       // [width*height][3] surface points of hits
+    int* hit_pix;         // pixel index per hit
+    unsigned int* hit_count;
+};
+cudaError_t launch_render_rays(const RenderArgs& a, cudaStream_t stream);
+
+}  // namespace pifu

@@ -1,0 +1,126 @@
+// Ray first crossing of the mesh-free render (Sec. 3.2, "Mesh-free
+// Rendering"): the volume is aligned with the target view, x/y with the
+// pixel axes and z with the rays, higher z nearer to the observer.
+//
+// One thread per pixel walks its ray from the observer (depth node N, z = +1)
+// backwards.  A sample is the bilinear (x, y) interpolation of the four node
+// columns around the pixel centre; a node's value is the network's occupancy
+// where the node was evaluated and its binarized 0/1 value elsewhere.  The
+// first sample >= 0.5 is the surface: the depth is the linear 0.5 crossing
+// between it and the previous sample (the two nodes "interpolated by the
+// predicted occupancy").  Empty space costs four bit tests per sample (the
+// evaluated and binarized bitsets of two node rows), so a miss reads only
+// bitsets.  Hits are appended (warp-aggregated) to a list of surface points
+// for the colour MLP; misses get the background of Eq. 3.
+#include <math.h>
+
+#include "pifu_internal.h"
+
+namespace pifu {
+namespace {
+
+// bits ix and ix+1 of a bitset row as bits 0 and 1 (ix + 1 <= N is in the row)
+__device__ __forceinline__ uint32_t two_bits(const uint32_t* __restrict__ rowp, int ix) {
+    uint32_t v = __ldg(rowp + (ix >> 5)) >> (ix & 31);
+    if ((ix & 31) == 31) v |= __ldg(rowp + (ix >> 5) + 1) << 1;
+    return v & 3u;
+}
+
+// Fine node coordinate of a pixel centre along one axis: (2i+1) N / (2 R) as
+// an integer part and an exact fraction (for power-of-two N and R).
+__device__ __forceinline__ void pixel_node(int i, int R, int N, int& i0, float& w) {
+    const long long num = (long long)(2 * i + 1) * N;
+    const long long den = 2LL * R;
+    long long q = num / den;
+    long long r = num - q * den;
+    if (q >= N) {  // cannot happen for i < R; keeps i0 + 1 <= N regardless
+        q = N - 1;
+        r = den;
+    }
+    i0 = (int)q;
+    w = (float)r / (float)den;
+}
+
+__global__ void __launch_bounds__(256) render_rays_kernel(RenderArgs a) {
+    const int64_t npix = (int64_t)a.width * a.height;
+    const int64_t pix = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    bool hit = false;
+    float zs = 0.f, px = 0.f, py = 0.f;
+    if (pix < npix) {
+        const int i = (int)(pix % a.width);
+        const int j = (int)(pix / a.width);
+        int ix0, iy0;
+        float wx, wy;
+        pixel_node(i, a.width, a.N, ix0, wx);
+        pixel_node(j, a.height, a.N, iy0, wy);
+        px = __fmaf_rn((float)(2 * i + 1), 1.0f / (float)a.width, -1.0f);
+        py = __fmaf_rn((float)(2 * j + 1), 1.0f / (float)a.height, -1.0f);
+        const int n1 = a.N + 1;
+        const int rw = a.row_words;
+        const float w00 = (1.f - wx) * (1.f - wy), w10 = wx * (1.f - wy);
+        const float w01 = (1.f - wx) * wy, w11 = wx * wy;
+        const float h = 2.0f / (float)a.N;
+        float vprev = 0.f;
+        for (int k = 0; k <= a.N; ++k) {
+            const int iz = a.N - k;
+            const int64_t row0 = (int64_t)iz * n1 + iy0;
+            const int64_t row1 = row0 + 1;
+            const uint32_t e0 = two_bits(a.eval + row0 * rw, ix0);
+            const uint32_t e1 = two_bits(a.eval + row1 * rw, ix0);
+            const uint32_t b0 = two_bits(a.bin + row0 * rw, ix0);
+            const uint32_t b1 = two_bits(a.bin + row1 * rw, ix0);
+            float v = 0.f;
+            if (e0 | e1 | b0 | b1) {
+                const float v00 = (e0 & 1u) ? a.values[row0 * n1 + ix0] : (float)(b0 & 1u);
+                const float v10 = (e0 & 2u) ? a.values[row0 * n1 + ix0 + 1] : (float)(b0 >> 1);
+                const float v01 = (e1 & 1u) ? a.values[row1 * n1 + ix0] : (float)(b1 & 1u);
+                const float v11 = (e1 & 2u) ? a.values[row1 * n1 + ix0 + 1] : (float)(b1 >> 1);
+                v = fmaf(w11, v11, fmaf(w01, v01, fmaf(w10, v10, w00 * v00)));
+            }
+            if (v >= kHalf) {
+                hit = true;
+                if (k == 0) {
+                    zs = 1.0f;
+                } else {
+                    const float t = (kHalf - vprev) / (v - vprev);
+                    const float zprev = __fmaf_rn(-(float)(k - 1), h, 1.0f);
+                    zs = zprev - t * h;
+                }
+                break;
+            }
+            vprev = v;
+        }
+        if (a.depth) a.depth[pix] = hit ? zs : __int_as_float(0x7fc00000);
+        if (a.mask) a.mask[pix] = hit ? 1 : 0;
+        if (a.rgb && !hit) {
+            a.rgb[pix * 3 + 0] = a.bg[0];
+            a.rgb[pix * 3 + 1] = a.bg[1];
+            a.rgb[pix * 3 + 2] = a.bg[2];
+        }
+    }
+    // warp-aggregated append of the hits
+    const unsigned ballot = __ballot_sync(0xffffffffu, hit);
+    if (ballot == 0u) return;
+    unsigned base = 0u;
+    if (lane == 0) base = atomicAdd(a.hit_count, (unsigned)__popc(ballot));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (hit) {
+        const unsigned pos = base + __popc(ballot & ((1u << lane) - 1u));
+        a.hit_xyz[3 * (int64_t)pos + 0] = px;
+        a.hit_xyz[3 * (int64_t)pos + 1] = py;
+        a.hit_xyz[3 * (int64_t)pos + 2] = zs;
+        a.hit_pix[pos] = (int)pix;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_render_rays(const RenderArgs& a, cudaStream_t stream) {
+    const int64_t npix = (int64_t)a.width * a.height;
+    if (npix <= 0) return cudaSuccess;
+    render_rays_kernel<<<(unsigned)((npix + 255) / 256), 256, 0, stream>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace pifu

@@ -1,0 +1,302 @@
+"""Thin Python binding of libpifu (include/pifu.h): the same entry points,
+argument marshalling only.  Every step of the path runs in the library's
+CUDA kernels; PyTorch supplies device memory and streams.
+
+Loading fails loudly when the library is missing or cannot be opened: there
+is no fallback of any kind.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import struct
+
+import numpy as np
+
+from . import build as _build
+
+PIFU_OK = 0
+PIFU_ERR_ARG = -1
+PIFU_ERR_FORMAT = -2
+PIFU_ERR_CUDA = -3
+PIFU_ERR_OOM = -4
+PIFU_ERR_NOT_CONVERGED = -5
+PIFU_ERR_TIMEOUT = -6
+PIFU_ERR_STATE = -7
+PIFU_ERR_UNSUPPORTED = -8
+
+PIFU_F32 = 0
+PIFU_BF16 = 1
+PIFU_PREC_FP32 = 0
+PIFU_PREC_BF16 = 1
+PIFU_PREC_MIXED = 2
+
+# Every symbol include/pifu.h declares.
+EXPORTS = ("pifu_create", "pifu_destroy", "pifu_query", "pifu_query_colour", "pifu_localize",
+           "pifu_render", "pifu_sync_stats", "pifu_status_string", "pifu_last_error",
+           "pifu_profile", "pifu_profile_read")
+
+KERNEL_CLASSES = ("gather", "mlp_hidden", "mlp_last", "level", "select", "render")
+
+
+class pifu_fmap(ctypes.Structure):
+    _fields_ = [("data", ctypes.c_void_p), ("H", ctypes.c_int32), ("W", ctypes.c_int32),
+                ("C", ctypes.c_int32), ("dtype", ctypes.c_int32)]
+
+
+class pifu_levels(ctypes.Structure):
+    _fields_ = [("n0", ctypes.c_int32), ("num_levels", ctypes.c_int32),
+                ("precision", ctypes.c_int32), ("max_rounds", ctypes.c_int32)]
+
+
+class pifu_camera(ctypes.Structure):
+    _fields_ = [("width", ctypes.c_int32), ("height", ctypes.c_int32),
+                ("background", ctypes.c_float * 3)]
+
+
+class pifu_volume(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("num_levels", ctypes.c_int32),
+                ("row_words", ctypes.c_int32),
+                ("occ_bits_dev", ctypes.c_void_p), ("eval_bits_dev", ctypes.c_void_p),
+                ("values_dev", ctypes.c_void_p), ("n_eval", ctypes.c_int64),
+                ("evals_per_level", ctypes.c_int64 * 8),
+                ("candidates_per_level", ctypes.c_int64 * 8),
+                ("conflict_rounds", ctypes.c_int32 * 8)]
+
+
+class pifu_kernel_stats(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_int64), ("ms", ctypes.c_double),
+                ("flops", ctypes.c_double), ("bytes", ctypes.c_double)]
+
+
+class PifuError(RuntimeError):
+    def __init__(self, status, what, detail=""):
+        self.status = status
+        msg = f"{what}: {_lib().pifu_status_string(status).decode()} ({status})"
+        if detail:
+            msg += f": {detail}"
+        super().__init__(msg)
+
+
+_LIB = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def _lib():
+    """Open libpifu.so (building it first if it is missing or stale)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = _build.build()
+    if not os.path.exists(path):
+        raise RuntimeError(f"libpifu not found at {path}")
+    lib = ctypes.CDLL(path)
+    P, I, I64, F = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_float
+    lib.pifu_create.argtypes = [P, ctypes.c_size_t, ctypes.POINTER(P)]
+    lib.pifu_create.restype = I
+    lib.pifu_destroy.argtypes = [P]
+    lib.pifu_destroy.restype = None
+    lib.pifu_query.argtypes = [P, ctypes.POINTER(pifu_fmap), ctypes.POINTER(F), P, I64, P, P]
+    lib.pifu_query.restype = I
+    lib.pifu_query_colour.argtypes = [P, ctypes.POINTER(pifu_fmap), ctypes.POINTER(pifu_fmap),
+                                      ctypes.POINTER(F), P, I64, P, P]
+    lib.pifu_query_colour.restype = I
+    lib.pifu_localize.argtypes = [P, ctypes.POINTER(pifu_fmap), ctypes.POINTER(F),
+                                  ctypes.POINTER(pifu_levels), P, ctypes.POINTER(pifu_volume)]
+    lib.pifu_localize.restype = I
+    lib.pifu_render.argtypes = [P, ctypes.POINTER(pifu_camera), ctypes.POINTER(pifu_fmap),
+                                ctypes.POINTER(pifu_fmap), ctypes.POINTER(F), P, P, P, P]
+    lib.pifu_render.restype = I
+    lib.pifu_sync_stats.argtypes = [P, ctypes.POINTER(pifu_volume)]
+    lib.pifu_sync_stats.restype = I
+    lib.pifu_status_string.argtypes = [I]
+    lib.pifu_status_string.restype = ctypes.c_char_p
+    lib.pifu_last_error.argtypes = [P]
+    lib.pifu_last_error.restype = ctypes.c_char_p
+    lib.pifu_profile.argtypes = [P, I]
+    lib.pifu_profile.restype = I
+    lib.pifu_profile_read.argtypes = [P, ctypes.POINTER(pifu_kernel_stats)]
+    lib.pifu_profile_read.restype = I
+    _LIB = lib
+    return lib
+
+
+def load():
+    """The opened ctypes library."""
+    return _lib()
+
+
+# --------------------------------------------------------------------------
+# Weight blob (format in include/pifu.h)
+# --------------------------------------------------------------------------
+
+def blob_from_nets(occ_net, col_net) -> bytes:
+    """Serialise the occupancy and colour MLPs into the library's blob."""
+    parts = [b"PIFU", struct.pack("<II", 1, 2)]
+    for kind, net in ((0, occ_net), (1, col_net)):
+        L = len(net.W)
+        skip_mask = 0
+        for l in net.skip:
+            skip_mask |= 1 << l
+        parts.append(struct.pack("<IIIf", kind, net.d_in, L, net.slope))
+        parts.append(struct.pack(f"<{L}I", *[w.shape[0] for w in net.W]))
+        parts.append(struct.pack("<I", skip_mask))
+        for W, b in zip(net.W, net.b):
+            parts.append(np.ascontiguousarray(W, dtype="<f4").tobytes())
+            parts.append(np.ascontiguousarray(b, dtype="<f4").tobytes())
+    return b"".join(parts)
+
+
+# --------------------------------------------------------------------------
+# Marshalling helpers
+# --------------------------------------------------------------------------
+
+def _ptr(t):
+    return ctypes.c_void_p(0 if t is None else t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def fmap(t):
+    """pifu_fmap describing a contiguous [H][W][C] CUDA tensor (float32/bf16)."""
+    import torch
+    if t is None:
+        return None
+    if not t.is_cuda or not t.is_contiguous() or t.dim() != 3:
+        raise ValueError("feature map must be a contiguous [H][W][C] CUDA tensor")
+    dt = {torch.float32: PIFU_F32, torch.bfloat16: PIFU_BF16}[t.dtype]
+    return pifu_fmap(t.data_ptr(), t.shape[0], t.shape[1], t.shape[2], dt)
+
+
+def _calib(c):
+    a = np.ascontiguousarray(np.asarray(c, dtype=np.float32).reshape(12))
+    return (ctypes.c_float * 12)(*a.tolist())
+
+
+def _check(status, what, ctx=None):
+    if status != PIFU_OK:
+        detail = ""
+        if ctx is not None and status in (PIFU_ERR_CUDA, PIFU_ERR_OOM):
+            detail = _lib().pifu_last_error(ctx).decode()
+        raise PifuError(status, what, detail)
+
+
+# --------------------------------------------------------------------------
+# Entry points (same names as the C ABI)
+# --------------------------------------------------------------------------
+
+def pifu_create(blob: bytes):
+    lib = _lib()
+    ctx = ctypes.c_void_p()
+    buf = ctypes.create_string_buffer(blob, len(blob))
+    _check(lib.pifu_create(buf, len(blob), ctypes.byref(ctx)), "pifu_create")
+    return ctx
+
+
+def pifu_destroy(ctx):
+    _lib().pifu_destroy(ctx)
+
+
+def pifu_query(ctx, occ_map, calib, pts, out, stream=None):
+    """out[p] = O(pts[p]) (Eq. 1); pts [m][3] and out [m] float32 CUDA tensors."""
+    m = pts.shape[0]
+    fm = fmap(occ_map)
+    st = _lib().pifu_query(ctx, ctypes.byref(fm), _calib(calib), _ptr(pts), m, _ptr(out),
+                           _stream(stream))
+    _check(st, "pifu_query", ctx)
+    return out
+
+
+def pifu_query_colour(ctx, occ_map, col_map, calib, pts, out, stream=None):
+    """out[p] = T(pts[p]) in [0, 1]^3 (Eq. 2); out [m][3]."""
+    m = pts.shape[0]
+    fo = fmap(occ_map)
+    fc = fmap(col_map)
+    st = _lib().pifu_query_colour(ctx, ctypes.byref(fo), ctypes.byref(fc) if fc else None,
+                                  _calib(calib), _ptr(pts), m, _ptr(out), _stream(stream))
+    _check(st, "pifu_query_colour", ctx)
+    return out
+
+
+def pifu_localize(ctx, occ_map, calib, n0, num_levels, precision=PIFU_PREC_FP32,
+                  max_rounds=0, stream=None) -> pifu_volume:
+    fm = fmap(occ_map)
+    lv = pifu_levels(n0, num_levels, precision, max_rounds)
+    vol = pifu_volume()
+    st = _lib().pifu_localize(ctx, ctypes.byref(fm), _calib(calib), ctypes.byref(lv),
+                              _stream(stream), ctypes.byref(vol))
+    _check(st, "pifu_localize", ctx)
+    return vol
+
+
+def pifu_render(ctx, width, height, occ_map, col_map, calib, depth=None, rgb=None, mask=None,
+                background=(0.0, 0.0, 0.0), stream=None):
+    cam = pifu_camera(width, height, (ctypes.c_float * 3)(*background))
+    fo = fmap(occ_map)
+    fc = fmap(col_map)
+    st = _lib().pifu_render(ctx, ctypes.byref(cam), ctypes.byref(fo) if fo else None,
+                            ctypes.byref(fc) if fc else None, _calib(calib), _stream(stream),
+                            _ptr(depth), _ptr(rgb), _ptr(mask))
+    _check(st, "pifu_render", ctx)
+
+
+def pifu_sync_stats(ctx) -> pifu_volume:
+    vol = pifu_volume()
+    _check(_lib().pifu_sync_stats(ctx, ctypes.byref(vol)), "pifu_sync_stats")
+    return vol
+
+
+def pifu_profile(ctx, enable: bool):
+    _check(_lib().pifu_profile(ctx, 1 if enable else 0), "pifu_profile", ctx)
+
+
+def pifu_profile_read(ctx) -> dict:
+    """{class name: {launches, ms, flops, bytes}} since the last pifu_profile."""
+    arr = (pifu_kernel_stats * len(KERNEL_CLASSES))()
+    _check(_lib().pifu_profile_read(ctx, arr), "pifu_profile_read", ctx)
+    return {n: {"launches": int(a.launches), "ms": float(a.ms), "flops": float(a.flops),
+                "bytes": float(a.bytes)} for n, a in zip(KERNEL_CLASSES, arr)}
+
+
+def pifu_status_string(status: int) -> str:
+    return _lib().pifu_status_string(status).decode()
+
+
+# --------------------------------------------------------------------------
+# Views of a localized volume (device tensors over context memory)
+# --------------------------------------------------------------------------
+
+def volume_tensors(vol: pifu_volume):
+    """(occ_bits, eval_bits, values) as CUDA tensors aliasing context memory
+    (valid until the next pifu_localize on the context)."""
+    import torch
+    n1 = vol.n + 1
+    words = n1 * n1 * vol.row_words
+
+    def view(ptr, count, dtype):
+        # wrap raw device memory through the CUDA array interface
+        class _A:
+            __cuda_array_interface__ = {"shape": (count,), "typestr": dtype, "data": (ptr, True),
+                                        "version": 3}
+        return torch.as_tensor(_A(), device="cuda")
+
+    occ = view(vol.occ_bits_dev, words, "<i4")
+    ev = view(vol.eval_bits_dev, words, "<i4")
+    val = view(vol.values_dev, n1 ** 3, "<f4")
+    return occ, ev, val
+
+
+def unpack_bits(words, n, row_words):
+    """Host bool array [n+1]^3 ([z][y][x]) from a bitset in the row layout."""
+    w = np.asarray(words, dtype=np.int32).view(np.uint32).reshape(n + 1, n + 1, row_words)
+    bits = np.unpackbits(w.view(np.uint8).reshape(n + 1, n + 1, row_words * 4), axis=2,
+                         bitorder="little")
+    return bits[:, :, :n + 1].astype(bool)
