@@ -284,7 +284,7 @@ def volume_tensors(vol: pifu_volume):
     def view(ptr, count, dtype):
         # wrap raw device memory through the CUDA array interface
         class _A:
-            __cuda_array_interface__ = {"shape": (count,), "typestr": dtype, "data": (ptr, True),
+            __cuda_array_interface__ = {"shape": (count,), "typestr": dtype, "data": (ptr, False),
                                         "version": 3}
         return torch.as_tensor(_A(), device="cuda")
 
