@@ -197,6 +197,36 @@ int pifu_profile(pifu_ctx* ctx, int enable);
  * PIFU_K_COUNT classes into out[0 .. PIFU_K_COUNT). */
 int pifu_profile_read(pifu_ctx* ctx, pifu_kernel_stats* out);
 
+/* Occupancy query that allocates nothing (the paper has no counterpart; this
+ * is a deployment aid).  It is meant for callers that cannot call cudaMalloc
+ * -- code embedded in an application whose own allocator owns all device
+ * memory, or running where device allocation is not permitted -- and so
+ * cannot create a context either (pifu_create allocates).
+ *
+ * Same result as pifu_query: occ_dev[p] = O(pts_dev[3p .. 3p+2]) (Eq. 1),
+ * with the occupancy MLP read from weight_blob_dev, a device copy of the
+ * weight blob (format as in pifu_create) placed by the caller in memory it
+ * owns (4-byte aligned, not modified).  weight_blob is the host copy of the
+ * same bytes, read for the layer shapes only.  pts_dev, occ_dev and the map
+ * are the caller's, as in pifu_query.  Asynchronous on `stream`.
+ *
+ * Scratch: the MLP activations use one fixed 16 MiB device array inside the
+ * library, which every GPU that loads the library holds until the process
+ * exits.  It bounds the points of one call: m <= 4194304 / (ldx + 2 h)
+ * with ldx = d_in rounded up to 8 and h the widest hidden layer (1,814
+ * points for the 257-1024-512-256-128-1 network, 14,169 for 33-128-64-1);
+ * a larger m returns PIFU_ERR_ARG before any work is enqueued.
+ * All calls share the array: calls that overlap on the GPU (other streams,
+ * other threads) race and must be serialised by the caller.  The first call
+ * on a device looks the array's device address up (cudaGetSymbolAddress)
+ * with that device current; make that first call before any stream capture.
+ * No call allocates memory, host or device.
+ * Errors: PIFU_ERR_ARG, PIFU_ERR_FORMAT, PIFU_ERR_UNSUPPORTED (bf16 map),
+ * PIFU_ERR_CUDA. */
+int pifu_query_noalloc(const void* weight_blob, size_t bytes, const void* weight_blob_dev,
+                       const pifu_fmap* occ_map, const float calib[12],
+                       const float* pts_dev, int64_t m, float* occ_dev, void* stream);
+
 /* Text of the last CUDA error seen by this context ("" if none).  The
  * pointer stays valid until the next call on the context. */
 const char* pifu_last_error(const pifu_ctx* ctx);

@@ -34,7 +34,7 @@ PIFU_PREC_MIXED = 2
 # Every symbol include/pifu.h declares.
 EXPORTS = ("pifu_create", "pifu_destroy", "pifu_query", "pifu_query_colour", "pifu_localize",
            "pifu_render", "pifu_sync_stats", "pifu_status_string", "pifu_last_error",
-           "pifu_profile", "pifu_profile_read")
+           "pifu_profile", "pifu_profile_read", "pifu_query_noalloc")
 
 KERNEL_CLASSES = ("gather", "mlp_hidden", "mlp_last", "level", "select", "render")
 
@@ -120,6 +120,9 @@ def _lib():
     lib.pifu_profile.restype = I
     lib.pifu_profile_read.argtypes = [P, ctypes.POINTER(pifu_kernel_stats)]
     lib.pifu_profile_read.restype = I
+    lib.pifu_query_noalloc.argtypes = [P, ctypes.c_size_t, P, ctypes.POINTER(pifu_fmap),
+                                       ctypes.POINTER(F), P, I64, P, P]
+    lib.pifu_query_noalloc.restype = I
     _LIB = lib
     return lib
 
@@ -252,6 +255,19 @@ def pifu_sync_stats(ctx) -> pifu_volume:
     vol = pifu_volume()
     _check(_lib().pifu_sync_stats(ctx, ctypes.byref(vol)), "pifu_sync_stats")
     return vol
+
+
+def pifu_query_noalloc(blob: bytes, blob_dev, occ_map, calib, pts, out, stream=None):
+    """pifu_query without a context and without any allocation by the
+    library: blob is the host weight blob, blob_dev a device copy of its
+    bytes owned by the caller (e.g. a uint8 CUDA tensor)."""
+    buf = ctypes.create_string_buffer(blob, len(blob))
+    fm = fmap(occ_map)
+    st = _lib().pifu_query_noalloc(buf, len(blob), _ptr(blob_dev), ctypes.byref(fm),
+                                   _calib(calib), _ptr(pts), pts.shape[0], _ptr(out),
+                                   _stream(stream))
+    _check(st, "pifu_query_noalloc")
+    return out
 
 
 def pifu_profile(ctx, enable: bool):
