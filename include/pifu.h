@@ -83,6 +83,7 @@ typedef struct {
 typedef struct {
     int32_t width, height;
     float background[3];  /* B of Eq. 3                                        */
+    int32_t precision;    /* pifu_precision of the colour MLP                   */
 } pifu_camera;
 
 /* Result of pifu_localize: views into context memory, valid until the next
@@ -124,6 +125,14 @@ void pifu_destroy(pifu_ctx* ctx);
  * m = 0 is a no-op.  Asynchronous on `stream`. */
 int pifu_query(pifu_ctx* ctx, const pifu_fmap* occ_map, const float calib[12],
                const float* pts_dev, int64_t m, float* occ_dev, void* stream);
+
+/* pifu_query with a choice of MLP arithmetic: PIFU_PREC_FP32 (plain, as
+ * pifu_query) or PIFU_PREC_BF16 (tcgen05 tensor cores: BF16 weights and
+ * activations, FP32 accumulation; hidden widths must be multiples of 64,
+ * else PIFU_ERR_UNSUPPORTED).  A bounded device wait that gave up is
+ * reported as PIFU_ERR_TIMEOUT by the next synchronising call. */
+int pifu_query_ex(pifu_ctx* ctx, const pifu_fmap* occ_map, const float calib[12],
+                  const float* pts_dev, int64_t m, float* occ_dev, int precision, void* stream);
 
 /* Eq. 2 at m points: rgb_dev[3p + c] = (tanh(f_T) + 1) / 2.  col_map may be
  * NULL when f_T reads only [Phi(g_O), P_z]; otherwise its input is

@@ -79,9 +79,23 @@ __device__ __forceinline__ float4 ld4(const float* p) {
     return __ldg(reinterpret_cast<const float4*>(p));
 }
 
+__device__ __forceinline__ void store4(float* X, float4 r) {
+    *reinterpret_cast<float4*>(X) = r;
+}
+
+__device__ __forceinline__ void store4(__nv_bfloat16* X, float4 r) {
+    const __nv_bfloat162 lo = __floats2bfloat162_rn(r.x, r.y);
+    const __nv_bfloat162 hi = __floats2bfloat162_rn(r.z, r.w);
+    uint2 v;
+    v.x = *reinterpret_cast<const uint32_t*>(&lo);
+    v.y = *reinterpret_cast<const uint32_t*>(&hi);
+    *reinterpret_cast<uint2*>(X) = v;
+}
+
+template <typename OutT>
 __global__ void __launch_bounds__(256) gather_kernel(PointSrc src, int64_t p0, int64_t m,
                                                      Calib calib, Map map0, Map map1,
-                                                     float* __restrict__ X, int ldx) {
+                                                     OutT* __restrict__ X, int ldx) {
     const int nq = ldx >> 2;
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= m * nq) return;
@@ -122,7 +136,7 @@ __global__ void __launch_bounds__(256) gather_kernel(PointSrc src, int64_t p0, i
     } else {
         r = make_float4(c == C0 + C1 ? __fadd_rn(zh, zl) : 0.f, 0.f, 0.f, 0.f);
     }
-    *reinterpret_cast<float4*>(X + lp * ldx + c) = r;
+    store4(X + lp * ldx + c, r);
 }
 
 }  // namespace
@@ -134,7 +148,20 @@ cudaError_t launch_gather(const PointSrc& src, int64_t p0, int64_t m, const Cali
     const int64_t total = m * (ldx / 4);
     const int threads = 256;
     const int64_t blocks = (total + threads - 1) / threads;
-    gather_kernel<<<(unsigned)blocks, threads, 0, stream>>>(src, p0, m, calib, map0, map1, X, ldx);
+    gather_kernel<float><<<(unsigned)blocks, threads, 0, stream>>>(src, p0, m, calib, map0, map1,
+                                                                  X, ldx);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather_bf16(const PointSrc& src, int64_t p0, int64_t m, const Calib& calib,
+                               const Map& map0, const Map& map1, __nv_bfloat16* X, int ldx,
+                               cudaStream_t stream) {
+    if (m <= 0) return cudaSuccess;
+    const int64_t total = m * (ldx / 4);
+    const int threads = 256;
+    const int64_t blocks = (total + threads - 1) / threads;
+    gather_kernel<__nv_bfloat16><<<(unsigned)blocks, threads, 0, stream>>>(src, p0, m, calib, map0,
+                                                                          map1, X, ldx);
     return cudaGetLastError();
 }
 

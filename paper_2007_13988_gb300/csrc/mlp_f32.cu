@@ -131,18 +131,22 @@ __device__ __forceinline__ float apply_act(int act, float t) {
     return 0.5f * (tanhf(t) + 1.0f);
 }
 
+__device__ __forceinline__ float to_f32(float v) { return v; }
+__device__ __forceinline__ float to_f32(__nv_bfloat16 v) { return __bfloat162float(v); }
+
+template <typename InT>
 __global__ void __launch_bounds__(256) last_layer_kernel(
-    int64_t p0, int64_t M, int n_out, const float* __restrict__ A1, int lda1, int K1,
-    const float* __restrict__ A2, int lda2, int K2, const float* __restrict__ W, int ldw,
+    int64_t p0, int64_t M, int n_out, const InT* __restrict__ A1, int lda1, int K1,
+    const InT* __restrict__ A2, int lda2, int K2, const float* __restrict__ W, int ldw,
     const float* __restrict__ bias, Epilogue epi) {
     const int lane = threadIdx.x & 31;
     const int64_t lp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (lp >= M) return;  // whole warp exits together
     float t[4] = {0.f, 0.f, 0.f, 0.f};
-    const float* a1 = A1 + lp * lda1;
-    const float* a2 = A2 + lp * lda2;
+    const InT* a1 = A1 + lp * lda1;
+    const InT* a2 = A2 + lp * lda2;
     for (int k = lane; k < K1 + K2; k += 32) {
-        const float a = (k < K1) ? a1[k] : a2[k - K1];
+        const float a = (k < K1) ? to_f32(a1[k]) : to_f32(a2[k - K1]);
 #pragma unroll
         for (int j = 0; j < 4; ++j)
             if (j < n_out) t[j] = fmaf(a, W[(int64_t)j * ldw + k], t[j]);
@@ -202,8 +206,20 @@ cudaError_t launch_last_layer(int64_t p0, int64_t M, int n_out, const float* A1,
     if (M <= 0) return cudaSuccess;
     const int64_t threads = M * 32;
     const int64_t blocks = (threads + 255) / 256;
-    last_layer_kernel<<<(unsigned)blocks, 256, 0, stream>>>(p0, M, n_out, A1, lda1, K1, A2, lda2,
-                                                           K2, W, ldw, bias, epi);
+    last_layer_kernel<float><<<(unsigned)blocks, 256, 0, stream>>>(p0, M, n_out, A1, lda1, K1, A2,
+                                                                  lda2, K2, W, ldw, bias, epi);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_last_layer_bf16(int64_t p0, int64_t M, int n_out, const __nv_bfloat16* A1,
+                                   int lda1, int K1, const __nv_bfloat16* A2, int lda2, int K2,
+                                   const float* W, int ldw, const float* bias, const Epilogue& epi,
+                                   cudaStream_t stream) {
+    if (M <= 0) return cudaSuccess;
+    const int64_t threads = M * 32;
+    const int64_t blocks = (threads + 255) / 256;
+    last_layer_kernel<__nv_bfloat16><<<(unsigned)blocks, 256, 0, stream>>>(
+        p0, M, n_out, A1, lda1, K1, A2, lda2, K2, W, ldw, bias, epi);
     return cudaGetLastError();
 }
 

@@ -27,6 +27,15 @@ struct DevLayer {
     float* b = nullptr;
 };
 
+// BF16 tensor-core form of a hidden layer: W as [n_out][Kw] BF16 with the x
+// segment zero-padded to whole 64-column K-blocks, and its tensor maps.
+struct TcLayer {
+    __nv_bfloat16* W = nullptr;
+    int Kw = 0, nk1 = 0, nk2 = 0, BN = 0;
+    CUtensorMap tmW{};
+    CUtensorMap tmA1{};   // the previous layer's BF16 output (l >= 1)
+};
+
 struct DevNet {
     int kind = 0;       // 0 occupancy (sigmoid), 1 colour (tanh01)
     int d_in = 0;
@@ -34,6 +43,9 @@ struct DevNet {
     float slope = 0.01f;
     int max_hidden = 0;
     std::vector<DevLayer> layers;
+    bool tc_ok = false;             // shapes allow the tensor-core form
+    std::vector<TcLayer> tc;        // hidden layers only
+    CUtensorMap tmX{};              // BF16 gather rows as the A operand
 };
 
 int round_up(int v, int m) { return (v + m - 1) / m * m; }
@@ -109,11 +121,13 @@ struct pifu_ctx {
     int device = 0;
     DevNet net[2];
     std::string last_error;
-    // MLP activation workspace
+    // MLP activation workspace (FP32 and BF16 forms)
     float* X = nullptr;
     float* HA = nullptr;
     float* HB = nullptr;
-    int64_t X_cap = 0, H_cap = 0;   // floats
+    int64_t X_cap = 0, H_cap = 0;   // elements
+    __nv_bfloat16* Xb = nullptr;
+    __nv_bfloat16* Hb[2] = {nullptr, nullptr};
     // level workspace, sized for ws_N
     int ws_N = 0;
     uint32_t* cand = nullptr;
@@ -123,8 +137,8 @@ struct pifu_ctx {
     uint32_t* conf[2] = {nullptr, nullptr};
     float* values = nullptr;
     int* list = nullptr;
-    unsigned int* d_count = nullptr;
-    unsigned int* h_count = nullptr;          // pinned
+    unsigned int* d_count = nullptr;          // [0] list length, [1] device error word
+    unsigned int* h_count = nullptr;          // pinned [2]
     unsigned long long* d_pop = nullptr;      // [kMaxLevels]
     unsigned long long* h_pop = nullptr;      // pinned [kMaxLevels]
     // render workspace
@@ -272,7 +286,9 @@ void free_net(DevNet& net) {
         dev_free(L.W);
         dev_free(L.b);
     }
+    for (auto& T : net.tc) dev_free(T.W);
     net.layers.clear();
+    net.tc.clear();
 }
 
 // ---- workspaces -------------------------------------------------------------
@@ -285,16 +301,69 @@ int ensure_mlp_ws(pifu_ctx* ctx) {
     }
     if (need_x > ctx->X_cap) {
         dev_free(ctx->X);
+        dev_free(ctx->Xb);
         CK(dev_alloc(&ctx->X, need_x));
+        CK(dev_alloc(&ctx->Xb, need_x));
         ctx->X_cap = need_x;
     }
     if (need_h > ctx->H_cap) {
         dev_free(ctx->HA);
         dev_free(ctx->HB);
+        dev_free(ctx->Hb[0]);
+        dev_free(ctx->Hb[1]);
         CK(dev_alloc(&ctx->HA, need_h));
         CK(dev_alloc(&ctx->HB, need_h));
+        CK(dev_alloc(&ctx->Hb[0], need_h));
+        CK(dev_alloc(&ctx->Hb[1], need_h));
         ctx->H_cap = need_h;
     }
+    return PIFU_OK;
+}
+
+// Tensor-core form of a net: BF16 weights and the tensor maps over them and
+// over the BF16 workspaces (which must already exist).  Nets whose hidden
+// widths are not multiples of 64 keep tc_ok = false.
+int build_tc(pifu_ctx* ctx, const HostNet& hn, DevNet& net) {
+    const int L = (int)net.layers.size();
+    net.tc_ok = false;
+    net.tc.assign(L > 1 ? L - 1 : 0, TcLayer{});
+    for (int l = 0; l + 1 < L; ++l)
+        if (net.layers[l].n_out % 64 != 0) return PIFU_OK;
+    const int k2pad = round_up(net.d_in, 64);
+    if (!tc_encode_2d_bf16(&net.tmX, ctx->Xb, (uint64_t)net.d_in, (uint64_t)kChunk,
+                           (uint64_t)net.ldx * 2, 64, 128))
+        return PIFU_ERR_CUDA;
+    for (int l = 0; l + 1 < L; ++l) {
+        const DevLayer& Ly = net.layers[l];
+        TcLayer& T = net.tc[l];
+        const bool has_x = Ly.K2 > 0;
+        T.nk1 = Ly.K1 / 64;
+        T.nk2 = has_x ? k2pad / 64 : 0;
+        T.Kw = Ly.K1 + (has_x ? k2pad : 0);
+        T.BN = Ly.n_out % 256 == 0 ? 256 : (Ly.n_out % 128 == 0 ? 128 : 64);
+        std::vector<__nv_bfloat16> wb((size_t)Ly.n_out * T.Kw, __float2bfloat16(0.f));
+        const std::vector<float>& wf = hn.W[l];   // [n_out][K1 | ldx]
+        for (int o = 0; o < Ly.n_out; ++o) {
+            for (int k = 0; k < Ly.K1; ++k)
+                wb[(size_t)o * T.Kw + k] = __float2bfloat16(wf[(size_t)o * Ly.ldw + k]);
+            if (has_x)
+                for (int k = 0; k < net.d_in; ++k)
+                    wb[(size_t)o * T.Kw + Ly.K1 + k] =
+                        __float2bfloat16(wf[(size_t)o * Ly.ldw + Ly.K1 + k]);
+        }
+        CK(dev_alloc(&T.W, (int64_t)wb.size()));
+        CK(cudaMemcpy(T.W, wb.data(), wb.size() * sizeof(__nv_bfloat16), cudaMemcpyHostToDevice));
+        if (!tc_encode_2d_bf16(&T.tmW, T.W, (uint64_t)T.Kw, (uint64_t)Ly.n_out, (uint64_t)T.Kw * 2,
+                               64, (uint32_t)T.BN))
+            return PIFU_ERR_CUDA;
+        if (l > 0) {
+            const __nv_bfloat16* src = ctx->Hb[(l - 1) % 2];
+            if (!tc_encode_2d_bf16(&T.tmA1, src, (uint64_t)Ly.K1, (uint64_t)kChunk,
+                                   (uint64_t)Ly.K1 * 2, 64, 128))
+                return PIFU_ERR_CUDA;
+        }
+    }
+    net.tc_ok = true;
     return PIFU_OK;
 }
 
@@ -362,8 +431,56 @@ bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
 
 // ---- the MLP over a point batch ---------------------------------------------------
 
+int run_mlp_tc(pifu_ctx* ctx, const DevNet& net, const PointSrc& src, int64_t m, const Map& map0,
+               const Map& map1, const Calib& calib, const Epilogue& epi, cudaStream_t s) {
+    if (!net.tc_ok) return PIFU_ERR_UNSUPPORTED;
+    const int L = (int)net.layers.size();
+    Profiler& pr = ctx->prof;
+    for (int64_t p0 = 0; p0 < m; p0 += kChunk) {
+        const int64_t mc = std::min<int64_t>(kChunk, m - p0);
+        cudaEvent_t ev = pr.begin(s);
+        CK(launch_gather_bf16(src, p0, mc, calib, map0, map1, ctx->Xb, net.ldx, s));
+        pr.end(PIFU_K_GATHER, ev, s, 0.0,
+               (double)mc * (4.0 * 4.0 * (map0.C + map1.C) + 2.0 * net.ldx));
+        for (int l = 0; l + 1 < L; ++l) {
+            const DevLayer& Ly = net.layers[l];
+            const TcLayer& T = net.tc[l];
+            TcLayerArgs a{};
+            a.tmA1 = l > 0 ? &T.tmA1 : &net.tmX;
+            a.tmA2 = &net.tmX;
+            a.tmW = &T.tmW;
+            a.nk1 = T.nk1;
+            a.nk2 = T.nk2;
+            a.M = (int)mc;
+            a.N = Ly.n_out;
+            a.BN = T.BN;
+            a.bias = Ly.b;
+            a.slope = net.slope;
+            a.out = ctx->Hb[l % 2];
+            a.ldo = Ly.n_out;
+            a.err = ctx->d_count + 1;
+            ev = pr.begin(s);
+            CK(launch_tc_linear(a, s));
+            pr.end(PIFU_K_MLP_HIDDEN, ev, s, 2.0 * mc * Ly.fan_in * Ly.n_out,
+                   2.0 * ((double)mc * (Ly.fan_in + Ly.n_out) + (double)Ly.n_out * Ly.fan_in));
+        }
+        const DevLayer& Ll = net.layers[L - 1];
+        const __nv_bfloat16* h = L > 1 ? ctx->Hb[(L - 2) % 2] : nullptr;
+        const int hw = L > 1 ? net.layers[L - 2].n_out : 0;
+        ev = pr.begin(s);
+        CK(launch_last_layer_bf16(p0, mc, Ll.n_out, h, hw, Ll.K1, ctx->Xb, net.ldx, Ll.K2, Ll.W,
+                                  Ll.ldw, Ll.b, epi, s));
+        pr.end(PIFU_K_MLP_LAST, ev, s, 2.0 * mc * Ll.fan_in * Ll.n_out,
+               2.0 * (double)mc * (Ll.fan_in + Ll.n_out));
+    }
+    return PIFU_OK;
+}
+
 int run_mlp(pifu_ctx* ctx, const DevNet& net, const PointSrc& src, int64_t m, const Map& map0,
-            const Map& map1, const Calib& calib, const Epilogue& epi, cudaStream_t s) {
+            const Map& map1, const Calib& calib, const Epilogue& epi, cudaStream_t s,
+            int precision = PIFU_PREC_FP32) {
+    if (precision == PIFU_PREC_BF16)
+        return run_mlp_tc(ctx, net, src, m, map0, map1, calib, epi, s);
     const int L = (int)net.layers.size();
     Profiler& pr = ctx->prof;
     for (int64_t p0 = 0; p0 < m; p0 += kChunk) {
@@ -396,10 +513,17 @@ int run_mlp(pifu_ctx* ctx, const DevNet& net, const PointSrc& src, int64_t m, co
     return PIFU_OK;
 }
 
+// Reads the list length and the device error word (set by a bounded wait
+// that gave up); a set error word is cleared and reported as a timeout.
 int read_count(pifu_ctx* ctx, cudaStream_t s, unsigned int* out) {
-    CK(cudaMemcpyAsync(ctx->h_count, ctx->d_count, sizeof(unsigned int), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(ctx->h_count, ctx->d_count, 2 * sizeof(unsigned int),
+                       cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
-    *out = *ctx->h_count;
+    *out = ctx->h_count[0];
+    if (ctx->h_count[1] != 0u) {
+        CK(cudaMemsetAsync(ctx->d_count + 1, 0, sizeof(unsigned int), s));
+        return PIFU_ERR_TIMEOUT;
+    }
     return PIFU_OK;
 }
 
@@ -450,10 +574,14 @@ int pifu_create(const void* weight_blob, size_t bytes, pifu_ctx** out) {
     st = upload_net(ctx, hn[0], ctx->net[0]);
     if (st == PIFU_OK) st = upload_net(ctx, hn[1], ctx->net[1]);
     if (st == PIFU_OK) st = ensure_mlp_ws(ctx);
+    if (st == PIFU_OK) st = build_tc(ctx, hn[0], ctx->net[0]);
+    if (st == PIFU_OK) st = build_tc(ctx, hn[1], ctx->net[1]);
     if (st == PIFU_OK) {
-        cudaError_t e = cudaMalloc(&ctx->d_count, sizeof(unsigned int));
+        cudaError_t e = cudaMalloc(&ctx->d_count, 2 * sizeof(unsigned int));
+        if (e == cudaSuccess) e = cudaMemset(ctx->d_count, 0, 2 * sizeof(unsigned int));
         if (e == cudaSuccess) e = cudaMalloc(&ctx->d_pop, kMaxLevels * sizeof(unsigned long long));
-        if (e == cudaSuccess) e = cudaHostAlloc(&ctx->h_count, sizeof(unsigned int), cudaHostAllocDefault);
+        if (e == cudaSuccess)
+            e = cudaHostAlloc(&ctx->h_count, 2 * sizeof(unsigned int), cudaHostAllocDefault);
         if (e == cudaSuccess)
             e = cudaHostAlloc(&ctx->h_pop, kMaxLevels * sizeof(unsigned long long), cudaHostAllocDefault);
         if (e != cudaSuccess) st = fail_cuda(ctx, e);
@@ -474,6 +602,9 @@ void pifu_destroy(pifu_ctx* ctx) {
     dev_free(ctx->X);
     dev_free(ctx->HA);
     dev_free(ctx->HB);
+    dev_free(ctx->Xb);
+    dev_free(ctx->Hb[0]);
+    dev_free(ctx->Hb[1]);
     uint32_t** bitsets[] = {&ctx->cand, &ctx->tent, &ctx->bin[0], &ctx->bin[1],
                             &ctx->eval, &ctx->conf[0], &ctx->conf[1]};
     for (auto b : bitsets) dev_free(*b);
@@ -490,7 +621,13 @@ void pifu_destroy(pifu_ctx* ctx) {
 
 int pifu_query(pifu_ctx* ctx, const pifu_fmap* occ_map, const float calib[12],
                const float* pts_dev, int64_t m, float* occ_dev, void* stream) {
+    return pifu_query_ex(ctx, occ_map, calib, pts_dev, m, occ_dev, PIFU_PREC_FP32, stream);
+}
+
+int pifu_query_ex(pifu_ctx* ctx, const pifu_fmap* occ_map, const float calib[12],
+                  const float* pts_dev, int64_t m, float* occ_dev, int precision, void* stream) {
     if (!ctx || !calib || m < 0) return PIFU_ERR_ARG;
+    if (precision != PIFU_PREC_FP32 && precision != PIFU_PREC_BF16) return PIFU_ERR_UNSUPPORTED;
     if (m == 0) return PIFU_OK;
     if (!pts_dev || !occ_dev || !map_ok(occ_map)) return PIFU_ERR_ARG;
     if (occ_map->dtype != PIFU_F32) return PIFU_ERR_UNSUPPORTED;
@@ -503,7 +640,8 @@ int pifu_query(pifu_ctx* ctx, const pifu_fmap* occ_map, const float calib[12],
     epi.mode = EPI_STORE;
     epi.act = ACT_SIGMOID;
     epi.out = occ_dev;
-    return run_mlp(ctx, ctx->net[0], src, m, to_map(occ_map), Map{}, to_calib(calib), epi, s);
+    return run_mlp(ctx, ctx->net[0], src, m, to_map(occ_map), Map{}, to_calib(calib), epi, s,
+                   precision);
 }
 
 int pifu_query_colour(pifu_ctx* ctx, const pifu_fmap* occ_map, const pifu_fmap* col_map,
@@ -535,7 +673,10 @@ int pifu_localize(pifu_ctx* ctx, const pifu_fmap* occ_map, const float calib[12]
         return PIFU_ERR_ARG;
     const int64_t n_fine = (int64_t)lv->n0 << (lv->num_levels - 1);
     if (n_fine > kMaxFine) return PIFU_ERR_ARG;
-    if (lv->precision != PIFU_PREC_FP32) return PIFU_ERR_UNSUPPORTED;
+    if (lv->precision != PIFU_PREC_FP32 && lv->precision != PIFU_PREC_BF16)
+        return PIFU_ERR_UNSUPPORTED;
+    if (lv->precision == PIFU_PREC_BF16 && !ctx->net[0].tc_ok) return PIFU_ERR_UNSUPPORTED;
+    const int prec = lv->precision;
     if (occ_map->dtype != PIFU_F32) return PIFU_ERR_UNSUPPORTED;
     if (ctx->net[0].d_in != occ_map->C + 1) return PIFU_ERR_ARG;
     const int max_rounds = lv->max_rounds > 0 ? lv->max_rounds : 4096;
@@ -569,7 +710,7 @@ int pifu_localize(pifu_ctx* ctx, const pifu_fmap* occ_map, const float calib[12]
         epi.list = nullptr;
         epi.base = 0;
         epi.lv = LevelBits{ctx->values, ctx->tent, ctx->bin[cur], ctx->conf[0], N, row_words_of(N), 1};
-        st = run_mlp(ctx, net, src, nodes, map, Map{}, cal, epi, s);
+        st = run_mlp(ctx, net, src, nodes, map, Map{}, cal, epi, s, prec);
         if (st != PIFU_OK) return st;
         vs.evals_per_level[0] = nodes;
         vs.n_eval = nodes;
@@ -605,7 +746,7 @@ int pifu_localize(pifu_ctx* ctx, const pifu_fmap* occ_map, const float calib[12]
         epi.list = ctx->list;
         while (n > 0) {
             epi.lv = LevelBits{ctx->values, ctx->tent, ctx->bin[cur], ctx->conf[q], N, rw, 0};
-            st = run_mlp(ctx, net, src, n, map, Map{}, cal, epi, s);
+            st = run_mlp(ctx, net, src, n, map, Map{}, cal, epi, s, prec);
             if (st != PIFU_OK) return st;
             level_evals += n;
             // unevaluated 1-ring of this evaluation's conflicts
@@ -628,7 +769,11 @@ int pifu_localize(pifu_ctx* ctx, const pifu_fmap* occ_map, const float calib[12]
     }
     CK(cudaMemcpyAsync(ctx->h_pop, ctx->d_pop, kMaxLevels * sizeof(unsigned long long),
                        cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
+    {
+        unsigned int dummy;
+        st = read_count(ctx, s, &dummy);   // synchronises and checks the error word
+        if (st != PIFU_OK) return st;
+    }
     for (int l = 1; l < lv->num_levels; ++l) vs.candidates_per_level[l] = (int64_t)ctx->h_pop[l];
     vs.n = N;
     vs.row_words = row_words_of(N);
@@ -650,6 +795,9 @@ int pifu_render(pifu_ctx* ctx, const pifu_camera* cam, const pifu_fmap* occ_map,
     if (cam->width < 1 || cam->height < 1 || cam->width > 16384 || cam->height > 16384)
         return PIFU_ERR_ARG;
     if (!ctx->have_volume) return PIFU_ERR_STATE;
+    if (cam->precision != PIFU_PREC_FP32 && cam->precision != PIFU_PREC_BF16)
+        return PIFU_ERR_UNSUPPORTED;
+    if (rgb_dev && cam->precision == PIFU_PREC_BF16 && !ctx->net[1].tc_ok) return PIFU_ERR_UNSUPPORTED;
     if (rgb_dev) {
         if (!map_ok(occ_map) || (col_map && !map_ok(col_map))) return PIFU_ERR_ARG;
         if (occ_map->dtype != PIFU_F32 || (col_map && col_map->dtype != PIFU_F32))
@@ -700,7 +848,7 @@ int pifu_render(pifu_ctx* ctx, const pifu_camera* cam, const pifu_fmap* occ_map,
     epi.pix = ctx->hit_pix;
     const Map m0 = col_map ? to_map(col_map) : to_map(occ_map);
     const Map m1 = col_map ? to_map(occ_map) : Map{};
-    return run_mlp(ctx, ctx->net[1], src, n, m0, m1, to_calib(calib), epi, s);
+    return run_mlp(ctx, ctx->net[1], src, n, m0, m1, to_calib(calib), epi, s, cam->precision);
 }
 
 int pifu_profile(pifu_ctx* ctx, int enable) {

@@ -3,6 +3,8 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <cuda.h>
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 namespace pifu {
@@ -72,6 +74,11 @@ cudaError_t launch_gather(const PointSrc& src, int64_t p0, int64_t m, const Cali
                           const Map& map0, const Map& map1, float* X, int ldx,
                           cudaStream_t stream);
 
+// Same rows in BF16 (the tensor-core MLP's A operand); ldx a multiple of 8.
+cudaError_t launch_gather_bf16(const PointSrc& src, int64_t p0, int64_t m, const Calib& calib,
+                               const Map& map0, const Map& map1, __nv_bfloat16* X, int ldx,
+                               cudaStream_t stream);
+
 // --- mlp_f32.cu ------------------------------------------------------------
 // Out[M][N] = lrelu(A1[M][K1] W[:, :K1]^T + A2[M][K2] W[:, K1:]^T + b);
 // K1, K2 multiples of 8; N a multiple of 4; ld* multiples of 4.
@@ -84,6 +91,35 @@ cudaError_t launch_sgemm_bias_lrelu(int M, int N, const float* A1, int lda1, int
 cudaError_t launch_last_layer(int64_t p0, int64_t M, int n_out, const float* A1, int lda1, int K1,
                               const float* A2, int lda2, int K2, const float* W, int ldw,
                               const float* bias, const Epilogue& epi, cudaStream_t stream);
+
+// Last layer reading BF16 activations (A1 = h, A2 = x rows), FP32 weights.
+cudaError_t launch_last_layer_bf16(int64_t p0, int64_t M, int n_out, const __nv_bfloat16* A1,
+                                   int lda1, int K1, const __nv_bfloat16* A2, int lda2, int K2,
+                                   const float* W, int ldw, const float* bias, const Epilogue& epi,
+                                   cudaStream_t stream);
+
+// --- mlp_tc.cu -------------------------------------------------------------
+// One hidden layer on the tensor cores (tcgen05, BF16 in, FP32 accumulate):
+// out[M][N] = lrelu([A1 | A2] W^T + b) in BF16.  A1 (nk1 K-blocks of 64)
+// and A2 (nk2 K-blocks) are 2-D tensor maps over BF16 rows, W a tensor map
+// over [N][64 (nk1 + nk2)] BF16; box 64 x 128 for A, 64 x BN for W, all
+// with the 128-byte swizzle.  N a multiple of BN (64, 128 or 256).
+struct TcLayerArgs {
+    const CUtensorMap* tmA1;
+    const CUtensorMap* tmA2;
+    const CUtensorMap* tmW;
+    int nk1, nk2, M, N, BN;
+    const float* bias;
+    float slope;
+    __nv_bfloat16* out;
+    int ldo;
+    unsigned int* err;
+};
+cudaError_t launch_tc_linear(const TcLayerArgs& a, cudaStream_t stream);
+
+// Encode a 2-D BF16 tensor map (128-byte swizzle, zero fill out of bounds).
+bool tc_encode_2d_bf16(void* map, const void* base, uint64_t cols, uint64_t rows,
+                       uint64_t row_stride_bytes, uint32_t box_cols, uint32_t box_rows);
 
 // --- localize.cu -----------------------------------------------------------
 __host__ __device__ inline int row_words_of(int N) { return (N + 1 + 31) / 32; }

@@ -34,7 +34,7 @@ PIFU_PREC_MIXED = 2
 # Every symbol include/pifu.h declares.
 EXPORTS = ("pifu_create", "pifu_destroy", "pifu_query", "pifu_query_colour", "pifu_localize",
            "pifu_render", "pifu_sync_stats", "pifu_status_string", "pifu_last_error",
-           "pifu_profile", "pifu_profile_read", "pifu_query_noalloc")
+           "pifu_profile", "pifu_profile_read", "pifu_query_noalloc", "pifu_query_ex")
 
 KERNEL_CLASSES = ("gather", "mlp_hidden", "mlp_last", "level", "select", "render")
 
@@ -51,7 +51,7 @@ class pifu_levels(ctypes.Structure):
 
 class pifu_camera(ctypes.Structure):
     _fields_ = [("width", ctypes.c_int32), ("height", ctypes.c_int32),
-                ("background", ctypes.c_float * 3)]
+                ("background", ctypes.c_float * 3), ("precision", ctypes.c_int32)]
 
 
 class pifu_volume(ctypes.Structure):
@@ -101,6 +101,8 @@ def _lib():
     lib.pifu_destroy.restype = None
     lib.pifu_query.argtypes = [P, ctypes.POINTER(pifu_fmap), ctypes.POINTER(F), P, I64, P, P]
     lib.pifu_query.restype = I
+    lib.pifu_query_ex.argtypes = [P, ctypes.POINTER(pifu_fmap), ctypes.POINTER(F), P, I64, P, I, P]
+    lib.pifu_query_ex.restype = I
     lib.pifu_query_colour.argtypes = [P, ctypes.POINTER(pifu_fmap), ctypes.POINTER(pifu_fmap),
                                       ctypes.POINTER(F), P, I64, P, P]
     lib.pifu_query_colour.restype = I
@@ -218,6 +220,16 @@ def pifu_query(ctx, occ_map, calib, pts, out, stream=None):
     return out
 
 
+def pifu_query_ex(ctx, occ_map, calib, pts, out, precision=PIFU_PREC_FP32, stream=None):
+    """pifu_query with a choice of MLP arithmetic (PIFU_PREC_FP32 / _BF16)."""
+    m = pts.shape[0]
+    fm = fmap(occ_map)
+    st = _lib().pifu_query_ex(ctx, ctypes.byref(fm), _calib(calib), _ptr(pts), m, _ptr(out),
+                              precision, _stream(stream))
+    _check(st, "pifu_query_ex", ctx)
+    return out
+
+
 def pifu_query_colour(ctx, occ_map, col_map, calib, pts, out, stream=None):
     """out[p] = T(pts[p]) in [0, 1]^3 (Eq. 2); out [m][3]."""
     m = pts.shape[0]
@@ -241,8 +253,8 @@ def pifu_localize(ctx, occ_map, calib, n0, num_levels, precision=PIFU_PREC_FP32,
 
 
 def pifu_render(ctx, width, height, occ_map, col_map, calib, depth=None, rgb=None, mask=None,
-                background=(0.0, 0.0, 0.0), stream=None):
-    cam = pifu_camera(width, height, (ctypes.c_float * 3)(*background))
+                background=(0.0, 0.0, 0.0), precision=PIFU_PREC_FP32, stream=None):
+    cam = pifu_camera(width, height, (ctypes.c_float * 3)(*background), precision)
     fo = fmap(occ_map)
     fc = fmap(col_map)
     st = _lib().pifu_render(ctx, ctypes.byref(cam), ctypes.byref(fo) if fo else None,

@@ -47,11 +47,12 @@ class Ctx:
             self.pifu.pifu_destroy(self.ctx)
             self.ctx = None
 
-    def query(self, P, calib=None):
+    def query(self, P, calib=None, precision=0):
         t = torch()
         pts = to_dev(np.asarray(P, np.float32))
         out = t.empty(len(P), dtype=t.float32, device="cuda")
-        self.pifu.pifu_query(self.ctx, self.occ, self.calib if calib is None else calib, pts, out)
+        self.pifu.pifu_query_ex(self.ctx, self.occ, self.calib if calib is None else calib, pts,
+                                out, precision)
         t.cuda.synchronize()
         return out.cpu().numpy().astype(np.float64)
 
@@ -82,7 +83,8 @@ class Ctx:
         v = np.where(e, v, np.nan)
         return b, e, v
 
-    def render(self, R, calib=None, background=(0.0, 0.0, 0.0), width=None, height=None):
+    def render(self, R, calib=None, background=(0.0, 0.0, 0.0), width=None, height=None,
+               precision=0):
         t = torch()
         W = R if width is None else width
         H = R if height is None else height
@@ -91,7 +93,7 @@ class Ctx:
         mask = t.empty((H, W), dtype=t.uint8, device="cuda")
         self.pifu.pifu_render(self.ctx, W, H, self.occ, self.col,
                               self.calib if calib is None else calib, depth, rgb, mask,
-                              background=background)
+                              background=background, precision=precision)
         t.cuda.synchronize()
         return (depth.cpu().numpy().astype(np.float64), rgb.cpu().numpy().astype(np.float64),
                 mask.cpu().numpy().astype(bool))
