@@ -45,7 +45,8 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
-    ap.add_argument("--precision", choices=("fp32",), default="fp32")
+    ap.add_argument("--precision", choices=("fp32", "bf16", "mixed"), default="mixed")
+    ap.add_argument("--no-plain", action="store_true", help="skip the plain FP32 comparison")
     ap.add_argument("--query-points", type=int, default=1 << 20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
@@ -170,8 +171,8 @@ def recorded_traffic(kernel_key, digest):
 
 # ----------------------------------------------------------------- oracle ---
 
-def oracle_frame(w):
-    """One full frame of the FP64 oracle; returns (seconds, counts)."""
+def oracle_frame(w, keep=False):
+    """One full frame of the FP64 oracle; returns (seconds, counts[, levels])."""
     import numpy as np
     from oracle import field, localize, render
     t0 = time.perf_counter()
@@ -180,7 +181,8 @@ def oracle_frame(w):
     rgb, depth, hit = render.render(lv[-1].values, w.render, w.col_net, w.occ_map, w.col_map,
                                     w.calib)
     dt = time.perf_counter() - t0
-    return dt, {"evals": int(sum(l.n_eval for l in lv)), "hits": int(np.count_nonzero(hit))}
+    counts = {"evals": int(sum(l.n_eval for l in lv)), "hits": int(np.count_nonzero(hit))}
+    return (dt, counts, lv) if keep else (dt, counts)
 
 
 def run_reference(args, rank, world):
@@ -221,14 +223,14 @@ def run_reference(args, rank, world):
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1000.0 * sum(times) / len(times), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": workload_config(w, evals_frame, None),
+            "config": workload_config(w, evals_frame, None, "fp64"),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
-def workload_config(w, evals, hits, precision="fp32"):
+def workload_config(w, evals, hits, precision="mixed"):
     return {"workload": "one 512x512 frame: 32^3->256^3 hierarchical localization + 512^2 "
                         "mesh-free render; f_O 257-1024-512-256-128-1 (skips at 2-4), "
                         "f_T 513-1024-512-256-128-3; 256x128x128 FP32 feature maps",
@@ -240,67 +242,112 @@ def workload_config(w, evals, hits, precision="fp32"):
 
 # -------------------------------------------------------------------- ours ---
 
+PREC = {"fp32": 0, "bf16": 1, "mixed": 2}
+
+
+class Frame:
+    """One workload on one device: context, resident inputs and outputs."""
+
+    def __init__(self, dev, stream):
+        import torch
+        from paper_2007_13988_gb300 import pifu, synth
+        self.pifu = pifu
+        self.w = w = synth.full(0)
+        self.ctx = pifu.pifu_create(pifu.blob_from_nets(w.occ_net, w.col_net))
+        self.stream = stream
+        self.dev = dev
+        R = w.render
+        with torch.cuda.stream(stream):
+            self.occ = torch.from_numpy(w.occ_map).to(dev)
+            self.col = torch.from_numpy(w.col_map).to(dev)
+            self.depth = torch.empty((R, R), dtype=torch.float32, device=dev)
+            self.rgb = torch.empty((R, R, 3), dtype=torch.float32, device=dev)
+            self.mask = torch.empty((R, R), dtype=torch.uint8, device=dev)
+            self.flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+        stream.synchronize()
+
+    def run(self, prec, margin=0.02):
+        w, p = self.w, self.pifu
+        vol = p.pifu_localize(self.ctx, self.occ, w.calib, w.n0, w.num_levels, precision=prec,
+                              margin=margin, stream=self.stream)
+        p.pifu_render(self.ctx, w.render, w.render, self.occ, self.col, w.calib, self.depth,
+                      self.rgb, self.mask, precision=1 if prec != 0 else 0, stream=self.stream)
+        return vol
+
+    def close(self):
+        self.pifu.pifu_destroy(self.ctx)
+
+
+def time_form(fr, prec, steps, warmup, world, clocks=None):
+    """Device-timed frames of one precision form; returns a dict."""
+    import torch
+    vol = None
+    for _ in range(max(1, warmup)):
+        vol = fr.run(prec)
+    fr.stream.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    fr.pifu.pifu_profile(fr.ctx, True)
+    for i in range(steps):
+        with torch.cuda.stream(fr.stream):
+            fr.flush.zero_()
+        ev[i][0].record(fr.stream)
+        vol = fr.run(prec)
+        ev[i][1].record(fr.stream)
+    torch.cuda.synchronize()
+    prof = fr.pifu.pifu_profile_read(fr.ctx)
+    fr.pifu.pifu_profile(fr.ctx, False)
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop() if clocks is not None else None
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_s = sum(step_ms) / 1000.0
+    if world > 1:
+        t = torch.tensor([total_s], device=fr.dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_s = float(t.item())
+    return {"value": world * steps / total_s, "ms_per_step": 1000.0 * total_s / steps,
+            "step_ms": step_ms, "prof": prof, "clocks": clk, "vol": vol,
+            "evals": int(vol.n_eval),
+            "rechecked": int(sum(vol.rechecked_per_level[i] for i in range(vol.num_levels))),
+            "hits": int(fr.mask.sum().item())}
+
+
 def run_ours(args, rank, world, local_rank):
     import numpy as np
     import torch
 
-    from paper_2007_13988_gb300 import pifu, synth
+    from paper_2007_13988_gb300 import synth
 
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
-    w = synth.full(0)
-    ctx = pifu.pifu_create(pifu.blob_from_nets(w.occ_net, w.col_net))
     stream = torch.cuda.Stream(device=dev)
+    fr = Frame(dev, stream)
+    pifu = fr.pifu
+    w = fr.w
     R = w.render
-    with torch.cuda.stream(stream):
-        occ = torch.from_numpy(w.occ_map).to(dev)
-        col = torch.from_numpy(w.col_map).to(dev)
-        depth = torch.empty((R, R), dtype=torch.float32, device=dev)
-        rgb = torch.empty((R, R, 3), dtype=torch.float32, device=dev)
-        mask = torch.empty((R, R), dtype=torch.uint8, device=dev)
-        flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
-    stream.synchronize()
+    prec = PREC[args.precision]
 
-    def frame():
-        vol = pifu.pifu_localize(ctx, occ, w.calib, w.n0, w.num_levels, stream=stream)
-        pifu.pifu_render(ctx, R, R, occ, col, w.calib, depth, rgb, mask, stream=stream)
-        return vol
-
-    def barrier():
-        if world > 1:
-            torch.distributed.barrier()
-
-    for _ in range(args.warmup):
-        vol = frame()
-    stream.synchronize()
-    evals = int(vol.n_eval)
-    hits = int(mask.sum().item())
-
-    # ---- device-resident timed region --------------------------------------
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(args.steps)]
-    clocks = ClockSampler(local_rank, enabled=not args.no_clocks)
-    barrier()
-    torch.cuda.synchronize()
-    pifu.pifu_profile(ctx, True)
-    for i in range(args.steps):
-        with torch.cuda.stream(stream):
-            flush.zero_()
-        ev[i][0].record(stream)
-        frame()
-        ev[i][1].record(stream)
-    torch.cuda.synchronize()
-    prof = pifu.pifu_profile_read(ctx)
-    pifu.pifu_profile(ctx, False)
-    barrier()
-    clk = clocks.stop()
-    step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_s = sum(step_ms) / 1000.0
-    if world > 1:
-        t = torch.tensor([total_s], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_s = float(t.item())
-    value = world * args.steps / total_s
+    # ---- headline form: device-resident timed region -----------------------
+    head = time_form(fr, prec, args.steps, args.warmup, world,
+                     ClockSampler(local_rank, enabled=not args.no_clocks))
+    head_rgb = fr.rgb.cpu().numpy()
+    head_b, head_vals = None, None
+    if rank == 0:
+        hv = head["vol"]
+        occ_b, ev_b, val = pifu.volume_tensors(hv)
+        head_b = pifu.unpack_bits(occ_b.cpu().numpy(), hv.n, hv.row_words)
+        head_e = pifu.unpack_bits(ev_b.cpu().numpy(), hv.n, hv.row_words)
+        v = val.cpu().numpy().astype(np.float64).reshape((hv.n + 1,) * 3)
+        head_vals = np.where(head_e, v, head_b.astype(np.float64))
+    # ---- the plain FP32 form on the same GPU, for the speedup ---------------
+    plain = None
+    if prec != 0 and not args.no_plain:
+        plain = time_form(fr, 0, max(3, min(args.steps, 10)), 2, world)
+        plain_rgb = fr.rgb.cpu().numpy()
 
     # ---- query points/s (raw field, inputs resident) -----------------------
     Q = args.query_points
@@ -308,18 +355,22 @@ def run_ours(args, rank, world, local_rank):
         pts = torch.from_numpy(synth.query_points(Q, seed=123)).to(dev)
         qout = torch.empty(Q, dtype=torch.float32, device=dev)
     stream.synchronize()
-    pifu.pifu_query(ctx, occ, w.calib, pts, qout, stream=stream)
-    qe = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-    n_q = 3
-    with torch.cuda.stream(stream):
-        flush.zero_()
-    qe[0].record(stream)
-    for _ in range(n_q):
-        pifu.pifu_query(ctx, occ, w.calib, pts, qout, stream=stream)
-    qe[1].record(stream)
-    stream.synchronize()
-    q_s = qe[0].elapsed_time(qe[1]) / 1000.0
-    query_pts_per_s = world * Q * n_q / q_s  # replicas: every rank queries its own batch
+
+    def query_rate(qprec):
+        pifu.pifu_query_ex(fr.ctx, fr.occ, w.calib, pts, qout, precision=qprec, stream=stream)
+        qe = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+        n_q = 3
+        with torch.cuda.stream(stream):
+            fr.flush.zero_()
+        qe[0].record(stream)
+        for _ in range(n_q):
+            pifu.pifu_query_ex(fr.ctx, fr.occ, w.calib, pts, qout, precision=qprec, stream=stream)
+        qe[1].record(stream)
+        stream.synchronize()
+        return world * Q * n_q / (qe[0].elapsed_time(qe[1]) / 1000.0)
+
+    q_head = query_rate(prec)
+    q_plain = query_rate(0) if prec != 0 else q_head
 
     # ---- end to end through the public API with host buffers ---------------
     h_occ = torch.from_numpy(w.occ_map).pin_memory()
@@ -328,18 +379,19 @@ def run_ours(args, rank, world, local_rank):
     h_rgb = torch.empty((R, R, 3), dtype=torch.float32).pin_memory()
     h_mask = torch.empty((R, R), dtype=torch.uint8).pin_memory()
     e2e_steps = max(3, min(args.steps, 10))
-    barrier()
+    if world > 1:
+        torch.distributed.barrier()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         with torch.cuda.stream(stream):
-            occ.copy_(h_occ, non_blocking=True)
-            col.copy_(h_col, non_blocking=True)
-        frame()
+            fr.occ.copy_(h_occ, non_blocking=True)
+            fr.col.copy_(h_col, non_blocking=True)
+        fr.run(prec)
         with torch.cuda.stream(stream):
-            h_depth.copy_(depth, non_blocking=True)
-            h_rgb.copy_(rgb, non_blocking=True)
-            h_mask.copy_(mask, non_blocking=True)
+            h_depth.copy_(fr.depth, non_blocking=True)
+            h_rgb.copy_(fr.rgb, non_blocking=True)
+            h_mask.copy_(fr.mask, non_blocking=True)
         stream.synchronize()
     e2e_s = time.perf_counter() - t0
     if world > 1:
@@ -349,55 +401,75 @@ def run_ours(args, rank, world, local_rank):
     e2e_value = world * e2e_steps / e2e_s
     h2d = h_occ.numel() * 4 + h_col.numel() * 4
     d2h = h_depth.numel() * 4 + h_rgb.numel() * 4 + h_mask.numel()
-
-    pifu.pifu_destroy(ctx)
+    fr.close()
     if rank != 0:
         return
 
-    # ---- roofline of the dominant kernel class -----------------------------
+    # ---- roofline of the dominant kernel class of the headline form --------
+    prof = head["prof"]
     peaks, peak_src = measured_peaks()
     dom = max(prof, key=lambda k: prof[k]["ms"])
     dk = prof["mlp_hidden"]
-    sm_mhz = peaks.get("sm_max_mhz", 2070.0)
-    peak = fp32_simt_peak_tflops(sm_mhz)
     achieved = dk["flops"] / (dk["ms"] / 1000.0) / 1e12 if dk["ms"] > 0 else 0.0
-    digest = source_digest(["paper_2007_13988_gb300/csrc/mlp_f32.cu"])
-    traffic = recorded_traffic("sgemm_bias_lrelu", digest)
-    launches = sum(v["launches"] for v in prof.values())
-    roofline = {"bound": "alu", "kernel": "sgemm_bias_lrelu (hidden MLP layers, FP32 FFMA)",
+    if prec == 0:
+        sm_mhz = peaks.get("sm_max_mhz", 2070.0)
+        peak = fp32_simt_peak_tflops(sm_mhz)
+        kname, bound, src = "sgemm_bias_lrelu", "alu", "paper_2007_13988_gb300/csrc/mlp_f32.cu"
+        peak_note = (f"FP32 SIMT: 152 SMs x 128 lanes x 2 flop x {sm_mhz:.0f} MHz "
+                     f"(sm_max_mhz, {peak_src})")
+    else:
+        peak = peaks.get("bf16_tflops", 1900.0)
+        kname, bound, src = "tc_linear_kernel", "tensor", "paper_2007_13988_gb300/csrc/mlp_tc.cu"
+        peak_note = f"dense BF16 cuBLAS burst, MEASURED_PEAKS.json ({peak_src})"
+    traffic = recorded_traffic(kname, source_digest([src]))
+    roofline = {"bound": bound, "kernel": kname + " (hidden MLP layers)",
                 "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "peak_source": f"FP32 SIMT: 152 SMs x 128 lanes x 2 flop x {sm_mhz:.0f} MHz "
-                               f"(sm_max_mhz from MEASURED_PEAKS.json, {peak_src})",
-                "traffic": None if traffic is None else traffic,
+                "peak_source": peak_note, "traffic": traffic,
                 "avg_launch_ms": dk["ms"] / max(1, dk["launches"]),
                 "flops_per_launch": dk["flops"] / max(1, dk["launches"]),
-                "share_of_step": dk["ms"] / max(1e-9, sum(step_ms)),
+                "share_of_step": dk["ms"] / max(1e-9, sum(head["step_ms"])),
                 "dominant_class": dom}
     kernels = {k: {"launches": v["launches"] // max(1, args.steps),
-                   "ms_per_step": v["ms"] / max(1, args.steps)} for k, v in prof.items()}
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1000.0 * total_s / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": workload_config(w, evals, hits),
-            "query_pts_per_s": query_pts_per_s,
-            "query": {"points": Q, "calls": n_q, "ms_per_call": 1000.0 * q_s / n_q},
+                   "ms_per_step": v["ms"] / max(1, args.steps),
+                   "achieved_gbs": (v["bytes"] / (v["ms"] / 1000.0) / 1e9) if v["ms"] > 0 else None}
+               for k, v in prof.items()}
+    launches = sum(v["launches"] for v in prof.values())
+    line = {"metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": {"fp32": "f32", "bf16": "bf16", "mixed": "bf16+f32"}[args.precision],
+            "data": "synthetic",
+            "config": workload_config(w, head["evals"], head["hits"], args.precision),
+            "query_pts_per_s": q_head,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "steps": e2e_steps},
-            "gpu_launches": launches,
-            "roofline": roofline,
-            "kernels": kernels,
-            "step_ms": {"min": min(step_ms), "median": statistics.median(step_ms),
-                        "max": max(step_ms)}}
-    if clk is not None:
-        line["clocks"] = clk
+            "gpu_launches": launches, "roofline": roofline, "kernels": kernels,
+            "step_ms": {"min": min(head["step_ms"]), "median": statistics.median(head["step_ms"]),
+                        "max": max(head["step_ms"])}}
+    if prec == 2:
+        line["config"]["margin"] = 0.02
+        line["config"]["rechecked_per_frame"] = head["rechecked"]
+    if plain is not None:
+        line["plain_fp32"] = {"value": plain["value"], "ms_per_step": plain["ms_per_step"],
+                              "query_pts_per_s": q_plain,
+                              "speedup_of_headline": head["value"] / plain["value"]}
+        d = plain_rgb.astype(np.float64) - head_rgb.astype(np.float64)
+        mse = float(np.mean(d * d))
+        line["accuracy"] = {"colour_psnr_vs_fp32_db": float("inf") if mse == 0 else
+                            10 * np.log10(1.0 / mse)}
+    if head["clocks"] is not None:
+        line["clocks"] = head["clocks"]
     if world == 1 and not args.no_cpu_baseline:
-        t, cnt = oracle_frame(w)
+        t, cnt, lv = oracle_frame(w, keep=True)
         line["cpu_baseline"] = {"value": 1.0 / t, "unit": UNIT, "cores": cpu_threads(),
                                 "kind": "oracle",
                                 "sample": f"one full frame of the FP64 oracle (numpy): "
                                           f"{cnt['evals']} f_O + {cnt['hits']} f_T evaluations, "
                                           f"localization bookkeeping and ray scan; {t:.1f} s"}
+        from oracle import metrics
+        acc = line.setdefault("accuracy", {})
+        acc["iou_vs_oracle"] = metrics.iou(head_b, lv[-1].binary)
+        acc["chamfer_vox_vs_oracle"] = metrics.chamfer_voxels(head_vals, lv[-1].values)
     print(json.dumps(line), flush=True)
 
 

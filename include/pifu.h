@@ -57,8 +57,10 @@ typedef enum {
 
 typedef enum { PIFU_F32 = 0, PIFU_BF16 = 1 } pifu_dtype;
 
-/* MLP arithmetic.  FP32: plain single precision (SIMT FFMA).  The other
- * values select tensor-core forms where the library provides them. */
+/* MLP arithmetic.  FP32: plain single precision (SIMT FFMA).  BF16: tcgen05
+ * tensor cores, BF16 weights and activations, FP32 accumulation.  MIXED:
+ * BF16, then every occupancy within `margin` of 0.5 evaluated again in FP32
+ * (the decision threshold is where low precision can change a result). */
 typedef enum { PIFU_PREC_FP32 = 0, PIFU_PREC_BF16 = 1, PIFU_PREC_MIXED = 2 } pifu_precision;
 
 /* A channel-last feature map g(I) in device memory: data[(j W + i) C + c]. */
@@ -75,6 +77,7 @@ typedef struct {
     int32_t num_levels;  /* 1 .. 8; finest n0 << (num_levels-1) <= 512         */
     int32_t precision;   /* pifu_precision                                     */
     int32_t max_rounds;  /* cap on conflict rounds per level (<= 0: 4096)      */
+    float margin;        /* MIXED: FP32 re-evaluation band |o - 0.5| < margin  */
 } pifu_levels;
 
 /* Target view of the render: the volume is aligned with it (Sec. 3.2), so
@@ -101,6 +104,7 @@ typedef struct {
     int64_t n_eval;               /* network evaluations over all levels       */
     int64_t evals_per_level[8];
     int64_t candidates_per_level[8]; /* boundary candidates (before dilation)  */
+    int64_t rechecked_per_level[8];  /* MIXED: evaluations redone in FP32       */
     int32_t conflict_rounds[8];
 } pifu_volume;
 
@@ -126,13 +130,15 @@ void pifu_destroy(pifu_ctx* ctx);
 int pifu_query(pifu_ctx* ctx, const pifu_fmap* occ_map, const float calib[12],
                const float* pts_dev, int64_t m, float* occ_dev, void* stream);
 
-/* pifu_query with a choice of MLP arithmetic: PIFU_PREC_FP32 (plain, as
- * pifu_query) or PIFU_PREC_BF16 (tcgen05 tensor cores: BF16 weights and
- * activations, FP32 accumulation; hidden widths must be multiples of 64,
- * else PIFU_ERR_UNSUPPORTED).  A bounded device wait that gave up is
- * reported as PIFU_ERR_TIMEOUT by the next synchronising call. */
+/* pifu_query with a choice of MLP arithmetic (pifu_precision).  BF16 and
+ * MIXED need hidden widths that are multiples of 64 (else
+ * PIFU_ERR_UNSUPPORTED); MIXED re-evaluates occupancies within `margin`
+ * (0 .. 0.5) of 0.5 in FP32 and synchronises the stream once per 65,536
+ * points.  A bounded device wait that gave up is reported as
+ * PIFU_ERR_TIMEOUT by the next synchronising call. */
 int pifu_query_ex(pifu_ctx* ctx, const pifu_fmap* occ_map, const float calib[12],
-                  const float* pts_dev, int64_t m, float* occ_dev, int precision, void* stream);
+                  const float* pts_dev, int64_t m, float* occ_dev, int precision, float margin,
+                  void* stream);
 
 /* Eq. 2 at m points: rgb_dev[3p + c] = (tanh(f_T) + 1) / 2.  col_map may be
  * NULL when f_T reads only [Phi(g_O), P_z]; otherwise its input is

@@ -58,10 +58,11 @@ __device__ __forceinline__ void texel_coord(float hi, float lo, int W, int& i0, 
 
 __device__ __forceinline__ void point_xyz(const PointSrc& src, int64_t p, float& x, float& y,
                                           float& z) {
-    if (src.mode == PTS_XYZ) {
-        x = src.xyz[3 * p + 0];
-        y = src.xyz[3 * p + 1];
-        z = src.xyz[3 * p + 2];
+    if (src.mode == PTS_XYZ || src.mode == PTS_XYZ_IDX) {
+        const int64_t q = src.mode == PTS_XYZ ? p : (int64_t)src.list[p];
+        x = src.xyz[3 * q + 0];
+        y = src.xyz[3 * q + 1];
+        z = src.xyz[3 * q + 2];
         return;
     }
     const int64_t idx = (src.mode == PTS_LIST) ? (int64_t)src.list[p] : src.base + p;

@@ -155,8 +155,20 @@ __global__ void __launch_bounds__(256) last_layer_kernel(
     for (int j = 0; j < 4; ++j) t[j] = warp_sum(t[j]);
     if (lane != 0) return;
     const int64_t p = p0 + lp;
+    if (epi.recheck) {
+        // mixed precision: defer occupancies close to the decision threshold
+        const float o = apply_act(ACT_SIGMOID, t[0] + bias[0]);
+        if (fabsf(o - kHalf) < epi.margin) {
+            const unsigned pos = atomicAdd(epi.recheck_count, 1u);
+            epi.recheck[pos] = epi.mode == EPI_LEVEL
+                                   ? (epi.list ? epi.list[p] : (int)(epi.base + p))
+                                   : (epi.pix ? epi.pix[p] : (int)p);
+            return;
+        }
+    }
     if (epi.mode == EPI_STORE) {
-        for (int j = 0; j < n_out; ++j) epi.out[p * n_out + j] = apply_act(epi.act, t[j] + bias[j]);
+        const int64_t q = epi.pix ? (int64_t)epi.pix[p] : p;
+        for (int j = 0; j < n_out; ++j) epi.out[q * n_out + j] = apply_act(epi.act, t[j] + bias[j]);
     } else if (epi.mode == EPI_PIXELS) {
         const int64_t pix = epi.pix[p];
         for (int j = 0; j < n_out; ++j) epi.out[pix * 3 + j] = apply_act(epi.act, t[j] + bias[j]);

@@ -137,6 +137,10 @@ struct pifu_ctx {
     uint32_t* conf[2] = {nullptr, nullptr};
     float* values = nullptr;
     int* list = nullptr;
+    int* recheck = nullptr;                   // mixed precision: points to redo in FP32
+    int64_t recheck_cap = 0;
+    unsigned int* d_recheck = nullptr;        // its length (device)
+    unsigned int* h_recheck = nullptr;        // pinned copy
     unsigned int* d_count = nullptr;          // [0] list length, [1] device error word
     unsigned int* h_count = nullptr;          // pinned [2]
     unsigned long long* d_pop = nullptr;      // [kMaxLevels]
@@ -384,6 +388,12 @@ int ensure_level_ws(pifu_ctx* ctx, int N) {
     }
     CK(dev_alloc(&ctx->values, nodes));
     CK(dev_alloc(&ctx->list, nodes));
+    if (nodes > ctx->recheck_cap) {
+        dev_free(ctx->recheck);
+        ctx->recheck_cap = 0;
+        CK(dev_alloc(&ctx->recheck, nodes));
+        ctx->recheck_cap = nodes;
+    }
     ctx->ws_N = N;
     return PIFU_OK;
 }
@@ -513,6 +523,52 @@ int run_mlp(pifu_ctx* ctx, const DevNet& net, const PointSrc& src, int64_t m, co
     return PIFU_OK;
 }
 
+// Mixed precision over one batch: the tensor-core BF16 pass commits every
+// occupancy farther than `margin` from 0.5 and queues the others (node
+// indices for a level, point numbers otherwise) on ctx->recheck; the queued
+// ones are then evaluated again in FP32 and committed.  One host read of the
+// queue length per batch.  *rechecked += the queue length.
+int read_recheck(pifu_ctx* ctx, cudaStream_t s, unsigned int* out);
+
+int run_mlp_mixed(pifu_ctx* ctx, const DevNet& net, const PointSrc& src, int64_t m,
+                  const Map& map0, const Map& map1, const Calib& calib, const Epilogue& epi,
+                  float margin, cudaStream_t s, int64_t* rechecked) {
+    if (m > ctx->recheck_cap) return PIFU_ERR_ARG;
+    CK(cudaMemsetAsync(ctx->d_recheck, 0, sizeof(unsigned int), s));
+    Epilogue e1 = epi;
+    e1.recheck = ctx->recheck;
+    e1.recheck_count = ctx->d_recheck;
+    e1.margin = margin;
+    int st = run_mlp_tc(ctx, net, src, m, map0, map1, calib, e1, s);
+    if (st != PIFU_OK) return st;
+    unsigned int n = 0;
+    st = read_recheck(ctx, s, &n);
+    if (st != PIFU_OK) return st;
+    if (rechecked) *rechecked += n;
+    if (n == 0) return PIFU_OK;
+    PointSrc s2 = src;
+    Epilogue e2 = epi;
+    if (epi.mode == EPI_LEVEL) {
+        s2.mode = PTS_LIST;
+        s2.list = ctx->recheck;
+        e2.list = ctx->recheck;
+    } else {
+        // EPI_STORE over positions: point numbers index the batch's arrays
+        s2.mode = PTS_XYZ_IDX;
+        s2.list = ctx->recheck;
+        e2.pix = ctx->recheck;
+    }
+    return run_mlp(ctx, net, s2, n, map0, map1, calib, e2, s, PIFU_PREC_FP32);
+}
+
+int read_recheck(pifu_ctx* ctx, cudaStream_t s, unsigned int* out) {
+    CK(cudaMemcpyAsync(ctx->h_recheck, ctx->d_recheck, sizeof(unsigned int),
+                       cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    *out = *ctx->h_recheck;
+    return PIFU_OK;
+}
+
 // Reads the list length and the device error word (set by a bounded wait
 // that gave up); a set error word is cleared and reported as a timeout.
 int read_count(pifu_ctx* ctx, cudaStream_t s, unsigned int* out) {
@@ -582,6 +638,11 @@ int pifu_create(const void* weight_blob, size_t bytes, pifu_ctx** out) {
         if (e == cudaSuccess) e = cudaMalloc(&ctx->d_pop, kMaxLevels * sizeof(unsigned long long));
         if (e == cudaSuccess)
             e = cudaHostAlloc(&ctx->h_count, 2 * sizeof(unsigned int), cudaHostAllocDefault);
+        if (e == cudaSuccess) e = cudaMalloc(&ctx->d_recheck, sizeof(unsigned int));
+        if (e == cudaSuccess)
+            e = cudaHostAlloc(&ctx->h_recheck, sizeof(unsigned int), cudaHostAllocDefault);
+        if (e == cudaSuccess) e = dev_alloc(&ctx->recheck, kChunk);
+        if (e == cudaSuccess) ctx->recheck_cap = kChunk;
         if (e == cudaSuccess)
             e = cudaHostAlloc(&ctx->h_pop, kMaxLevels * sizeof(unsigned long long), cudaHostAllocDefault);
         if (e != cudaSuccess) st = fail_cuda(ctx, e);
@@ -610,6 +671,9 @@ void pifu_destroy(pifu_ctx* ctx) {
     for (auto b : bitsets) dev_free(*b);
     dev_free(ctx->values);
     dev_free(ctx->list);
+    dev_free(ctx->recheck);
+    dev_free(ctx->d_recheck);
+    if (ctx->h_recheck) cudaFreeHost(ctx->h_recheck);
     dev_free(ctx->d_count);
     dev_free(ctx->d_pop);
     dev_free(ctx->hit_xyz);
@@ -621,13 +685,16 @@ void pifu_destroy(pifu_ctx* ctx) {
 
 int pifu_query(pifu_ctx* ctx, const pifu_fmap* occ_map, const float calib[12],
                const float* pts_dev, int64_t m, float* occ_dev, void* stream) {
-    return pifu_query_ex(ctx, occ_map, calib, pts_dev, m, occ_dev, PIFU_PREC_FP32, stream);
+    return pifu_query_ex(ctx, occ_map, calib, pts_dev, m, occ_dev, PIFU_PREC_FP32, 0.f, stream);
 }
 
 int pifu_query_ex(pifu_ctx* ctx, const pifu_fmap* occ_map, const float calib[12],
-                  const float* pts_dev, int64_t m, float* occ_dev, int precision, void* stream) {
+                  const float* pts_dev, int64_t m, float* occ_dev, int precision, float margin,
+                  void* stream) {
     if (!ctx || !calib || m < 0) return PIFU_ERR_ARG;
-    if (precision != PIFU_PREC_FP32 && precision != PIFU_PREC_BF16) return PIFU_ERR_UNSUPPORTED;
+    if (precision != PIFU_PREC_FP32 && precision != PIFU_PREC_BF16 && precision != PIFU_PREC_MIXED)
+        return PIFU_ERR_UNSUPPORTED;
+    if (precision == PIFU_PREC_MIXED && !(margin >= 0.f && margin <= 0.5f)) return PIFU_ERR_ARG;
     if (m == 0) return PIFU_OK;
     if (!pts_dev || !occ_dev || !map_ok(occ_map)) return PIFU_ERR_ARG;
     if (occ_map->dtype != PIFU_F32) return PIFU_ERR_UNSUPPORTED;
@@ -640,8 +707,22 @@ int pifu_query_ex(pifu_ctx* ctx, const pifu_fmap* occ_map, const float calib[12]
     epi.mode = EPI_STORE;
     epi.act = ACT_SIGMOID;
     epi.out = occ_dev;
-    return run_mlp(ctx, ctx->net[0], src, m, to_map(occ_map), Map{}, to_calib(calib), epi, s,
-                   precision);
+    if (precision != PIFU_PREC_FP32 && !ctx->net[0].tc_ok) return PIFU_ERR_UNSUPPORTED;
+    if (precision != PIFU_PREC_MIXED)
+        return run_mlp(ctx, ctx->net[0], src, m, to_map(occ_map), Map{}, to_calib(calib), epi, s,
+                       precision);
+    // mixed: batches of at most one workspace chunk, each BF16 then FP32 for
+    // the occupancies near 0.5 (synchronises the stream once per batch)
+    for (int64_t p0 = 0; p0 < m; p0 += kChunk) {
+        const int64_t mc = std::min<int64_t>(kChunk, m - p0);
+        PointSrc sb{PTS_XYZ, pts_dev + 3 * p0, nullptr, 0, 0};
+        Epilogue eb = epi;
+        eb.out = occ_dev + p0;
+        const int st = run_mlp_mixed(ctx, ctx->net[0], sb, mc, to_map(occ_map), Map{},
+                                     to_calib(calib), eb, margin, s, nullptr);
+        if (st != PIFU_OK) return st;
+    }
+    return PIFU_OK;
 }
 
 int pifu_query_colour(pifu_ctx* ctx, const pifu_fmap* occ_map, const pifu_fmap* col_map,
@@ -673,9 +754,12 @@ int pifu_localize(pifu_ctx* ctx, const pifu_fmap* occ_map, const float calib[12]
         return PIFU_ERR_ARG;
     const int64_t n_fine = (int64_t)lv->n0 << (lv->num_levels - 1);
     if (n_fine > kMaxFine) return PIFU_ERR_ARG;
-    if (lv->precision != PIFU_PREC_FP32 && lv->precision != PIFU_PREC_BF16)
+    if (lv->precision != PIFU_PREC_FP32 && lv->precision != PIFU_PREC_BF16 &&
+        lv->precision != PIFU_PREC_MIXED)
         return PIFU_ERR_UNSUPPORTED;
-    if (lv->precision == PIFU_PREC_BF16 && !ctx->net[0].tc_ok) return PIFU_ERR_UNSUPPORTED;
+    if (lv->precision != PIFU_PREC_FP32 && !ctx->net[0].tc_ok) return PIFU_ERR_UNSUPPORTED;
+    if (lv->precision == PIFU_PREC_MIXED && !(lv->margin >= 0.f && lv->margin <= 0.5f))
+        return PIFU_ERR_ARG;
     const int prec = lv->precision;
     if (occ_map->dtype != PIFU_F32) return PIFU_ERR_UNSUPPORTED;
     if (ctx->net[0].d_in != occ_map->C + 1) return PIFU_ERR_ARG;
@@ -710,7 +794,10 @@ int pifu_localize(pifu_ctx* ctx, const pifu_fmap* occ_map, const float calib[12]
         epi.list = nullptr;
         epi.base = 0;
         epi.lv = LevelBits{ctx->values, ctx->tent, ctx->bin[cur], ctx->conf[0], N, row_words_of(N), 1};
-        st = run_mlp(ctx, net, src, nodes, map, Map{}, cal, epi, s, prec);
+        st = prec == PIFU_PREC_MIXED
+                 ? run_mlp_mixed(ctx, net, src, nodes, map, Map{}, cal, epi, lv->margin, s,
+                                 &vs.rechecked_per_level[0])
+                 : run_mlp(ctx, net, src, nodes, map, Map{}, cal, epi, s, prec);
         if (st != PIFU_OK) return st;
         vs.evals_per_level[0] = nodes;
         vs.n_eval = nodes;
@@ -746,7 +833,10 @@ int pifu_localize(pifu_ctx* ctx, const pifu_fmap* occ_map, const float calib[12]
         epi.list = ctx->list;
         while (n > 0) {
             epi.lv = LevelBits{ctx->values, ctx->tent, ctx->bin[cur], ctx->conf[q], N, rw, 0};
-            st = run_mlp(ctx, net, src, n, map, Map{}, cal, epi, s, prec);
+            st = prec == PIFU_PREC_MIXED
+                     ? run_mlp_mixed(ctx, net, src, n, map, Map{}, cal, epi, lv->margin, s,
+                                     &vs.rechecked_per_level[l])
+                     : run_mlp(ctx, net, src, n, map, Map{}, cal, epi, s, prec);
             if (st != PIFU_OK) return st;
             level_evals += n;
             // unevaluated 1-ring of this evaluation's conflicts

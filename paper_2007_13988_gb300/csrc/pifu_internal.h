@@ -25,9 +25,10 @@ struct Map {
 
 // Where the points of an MLP batch come from.
 enum PointMode : int {
-    PTS_XYZ = 0,    // float32 [m][3] positions
-    PTS_LIST = 1,   // int32 node indices of a level with N cells per axis
-    PTS_DENSE = 2,  // node index = base + point number
+    PTS_XYZ = 0,     // float32 [m][3] positions
+    PTS_LIST = 1,    // int32 node indices of a level with N cells per axis
+    PTS_DENSE = 2,   // node index = base + point number
+    PTS_XYZ_IDX = 3, // positions xyz[list[p]] (a subset of a position array)
 };
 
 struct PointSrc {
@@ -40,7 +41,7 @@ struct PointSrc {
 
 // What the last MLP layer does with its output.
 enum EpilogueMode : int {
-    EPI_STORE = 0,   // out[p * n_out + c] = act(t)
+    EPI_STORE = 0,   // out[p * n_out + c] = act(t)   (p = pix[p] when pix is set)
     EPI_LEVEL = 1,   // scatter occupancy into a level (values, bits, conflicts)
     EPI_PIXELS = 2,  // out[pix[p] * 3 + c] = act(t)
 };
@@ -65,6 +66,12 @@ struct Epilogue {
     const int* list;        // EPI_LEVEL node index per point (null: dense from base)
     int64_t base;           // EPI_LEVEL dense base
     LevelBits lv;
+    // Mixed precision: occupancies within `margin` of 0.5 are not committed;
+    // their node index (EPI_LEVEL) or point number (EPI_STORE) is appended to
+    // recheck[] for re-evaluation in FP32.  Null recheck: commit everything.
+    int* recheck;
+    unsigned int* recheck_count;
+    float margin;
 };
 
 // --- gather.cu -------------------------------------------------------------

@@ -46,7 +46,8 @@ class pifu_fmap(ctypes.Structure):
 
 class pifu_levels(ctypes.Structure):
     _fields_ = [("n0", ctypes.c_int32), ("num_levels", ctypes.c_int32),
-                ("precision", ctypes.c_int32), ("max_rounds", ctypes.c_int32)]
+                ("precision", ctypes.c_int32), ("max_rounds", ctypes.c_int32),
+                ("margin", ctypes.c_float)]
 
 
 class pifu_camera(ctypes.Structure):
@@ -61,6 +62,7 @@ class pifu_volume(ctypes.Structure):
                 ("values_dev", ctypes.c_void_p), ("n_eval", ctypes.c_int64),
                 ("evals_per_level", ctypes.c_int64 * 8),
                 ("candidates_per_level", ctypes.c_int64 * 8),
+                ("rechecked_per_level", ctypes.c_int64 * 8),
                 ("conflict_rounds", ctypes.c_int32 * 8)]
 
 
@@ -101,7 +103,8 @@ def _lib():
     lib.pifu_destroy.restype = None
     lib.pifu_query.argtypes = [P, ctypes.POINTER(pifu_fmap), ctypes.POINTER(F), P, I64, P, P]
     lib.pifu_query.restype = I
-    lib.pifu_query_ex.argtypes = [P, ctypes.POINTER(pifu_fmap), ctypes.POINTER(F), P, I64, P, I, P]
+    lib.pifu_query_ex.argtypes = [P, ctypes.POINTER(pifu_fmap), ctypes.POINTER(F), P, I64, P, I, F,
+                                  P]
     lib.pifu_query_ex.restype = I
     lib.pifu_query_colour.argtypes = [P, ctypes.POINTER(pifu_fmap), ctypes.POINTER(pifu_fmap),
                                       ctypes.POINTER(F), P, I64, P, P]
@@ -220,12 +223,13 @@ def pifu_query(ctx, occ_map, calib, pts, out, stream=None):
     return out
 
 
-def pifu_query_ex(ctx, occ_map, calib, pts, out, precision=PIFU_PREC_FP32, stream=None):
-    """pifu_query with a choice of MLP arithmetic (PIFU_PREC_FP32 / _BF16)."""
+def pifu_query_ex(ctx, occ_map, calib, pts, out, precision=PIFU_PREC_FP32, margin=0.02,
+                  stream=None):
+    """pifu_query with a choice of MLP arithmetic (PIFU_PREC_FP32 / _BF16 / _MIXED)."""
     m = pts.shape[0]
     fm = fmap(occ_map)
     st = _lib().pifu_query_ex(ctx, ctypes.byref(fm), _calib(calib), _ptr(pts), m, _ptr(out),
-                              precision, _stream(stream))
+                              precision, margin, _stream(stream))
     _check(st, "pifu_query_ex", ctx)
     return out
 
@@ -242,9 +246,9 @@ def pifu_query_colour(ctx, occ_map, col_map, calib, pts, out, stream=None):
 
 
 def pifu_localize(ctx, occ_map, calib, n0, num_levels, precision=PIFU_PREC_FP32,
-                  max_rounds=0, stream=None) -> pifu_volume:
+                  max_rounds=0, margin=0.02, stream=None) -> pifu_volume:
     fm = fmap(occ_map)
-    lv = pifu_levels(n0, num_levels, precision, max_rounds)
+    lv = pifu_levels(n0, num_levels, precision, max_rounds, margin)
     vol = pifu_volume()
     st = _lib().pifu_localize(ctx, ctypes.byref(fm), _calib(calib), ctypes.byref(lv),
                               _stream(stream), ctypes.byref(vol))

@@ -47,12 +47,12 @@ class Ctx:
             self.pifu.pifu_destroy(self.ctx)
             self.ctx = None
 
-    def query(self, P, calib=None, precision=0):
+    def query(self, P, calib=None, precision=0, margin=0.02):
         t = torch()
         pts = to_dev(np.asarray(P, np.float32))
         out = t.empty(len(P), dtype=t.float32, device="cuda")
         self.pifu.pifu_query_ex(self.ctx, self.occ, self.calib if calib is None else calib, pts,
-                                out, precision)
+                                out, precision, margin)
         t.cuda.synchronize()
         return out.cpu().numpy().astype(np.float64)
 

@@ -128,3 +128,36 @@ def test_bf16_localization_iou(full):
     print("bf16 localization: IoU %.5f, evals %d (oracle %d)" % (iou, vol.n_eval,
                                                                 counts["evals_total"]))
     assert iou >= 0.97
+
+
+MIXED = 2
+
+
+def test_mixed_query_decisions_match_oracle(full):
+    # points on the finest grid near the figure, where o is close to 0.5
+    w = full.w
+    c = localize.node_coords(256)
+    rng = np.random.default_rng(9)
+    k, j, i = (rng.integers(0, 257, 60000) for _ in range(3))
+    P = np.stack([c[i], c[j], c[k]], 1)
+    o = field.occupancy(w.occ_net, w.occ_map, w.calib, P)
+    P = P[np.abs(o - 0.5) < 0.3][:3000].astype(np.float32)
+    want = field.occupancy(w.occ_net, w.occ_map, w.calib, P)
+    got = full.query(P, precision=MIXED)
+    near = np.abs(want - 0.5) < 0.015
+    # re-evaluated points carry FP32 accuracy; every decision matches
+    assert np.max(np.abs(got[near] - want[near])) <= 1e-4
+    assert np.array_equal(got >= 0.5, want >= 0.5)
+
+
+def test_mixed_localization_matches_oracle(full):
+    w = full.w
+    vol = full.localize(precision=MIXED, margin=0.02)
+    b, e, v = full.volume_host(vol)
+    lv = localize.hierarchical(lambda P: field.occupancy(w.occ_net, w.occ_map, w.calib, P),
+                               w.n0, w.num_levels)
+    iou = metrics.iou(b, lv[-1].binary)
+    sym = int(np.count_nonzero(e ^ lv[-1].evaluated))
+    print("mixed localization: IoU %.6f, eval symdiff %d, rechecked %s"
+          % (iou, sym, list(vol.rechecked_per_level)[:4]))
+    assert iou >= 0.999
