@@ -409,7 +409,7 @@ def run_ours(args, rank, world, local_rank):
     prof = head["prof"]
     peaks, peak_src = measured_peaks()
     dom = max(prof, key=lambda k: prof[k]["ms"])
-    dk = prof["mlp_hidden"]
+    dk = prof["mlp_hidden"] if prec != 0 else prof["mlp_f32"]
     achieved = dk["flops"] / (dk["ms"] / 1000.0) / 1e12 if dk["ms"] > 0 else 0.0
     if prec == 0:
         sm_mhz = peaks.get("sm_max_mhz", 2070.0)

@@ -184,12 +184,13 @@ const char* pifu_status_string(int status);
 /* Kernel classes counted and timed by the profiler. */
 typedef enum {
     PIFU_K_GATHER = 0,      /* projection + bilinear gather (MLP input rows)      */
-    PIFU_K_MLP_HIDDEN = 1,  /* hidden MLP layers (the dense contraction)          */
+    PIFU_K_MLP_HIDDEN = 1,  /* hidden MLP layers on the tensor cores (tcgen05)    */
     PIFU_K_MLP_LAST = 2,    /* last MLP layer + activation + epilogue             */
     PIFU_K_LEVEL = 3,       /* level set-up (dense set-up / classify, popcount)   */
     PIFU_K_SELECT = 4,      /* 26-dilation, selection and compaction              */
     PIFU_K_RENDER = 5,      /* ray first crossing                                 */
-    PIFU_K_COUNT = 6
+    PIFU_K_MLP_F32 = 6,     /* hidden MLP layers in FP32 (SIMT FFMA)              */
+    PIFU_K_COUNT = 7
 } pifu_kernel_class;
 
 /* Per-class totals since the last pifu_profile call.  `launches` counts

@@ -18,6 +18,7 @@ namespace pifu {
 namespace {
 
 constexpr int BM = 128, BN = 128, BK = 8;
+constexpr int kSmallM = kSplitMaxM;   // batches up to this many points use split-K
 
 __global__ void __launch_bounds__(256) sgemm_bias_lrelu_kernel(
     int M, int N, const float* __restrict__ A1, int lda1, int K1, const float* __restrict__ A2,
@@ -120,6 +121,117 @@ __global__ void __launch_bounds__(256) sgemm_bias_lrelu_kernel(
     }
 }
 
+// Small batches (a few points to a few thousand): the 128 x 128 tile above
+// leaves most SMs idle, and a CTA's K loop (up to 161 steps of 8) is a
+// chain of dependent global loads.  Here a 64-thread CTA computes a 32 x 32
+// tile (4 x 4 per thread) over one slice of K (blockIdx.z of gridDim.z) and
+// writes its partial sums to its own slice of `part`; a second kernel adds
+// the slices in a fixed order (deterministic, no atomics) and applies bias
+// and leaky-ReLU.  A batch of M points spreads over (M/32) (N/32) S CTAs.
+constexpr int SBM = 32, SBN = 32, SBK = 8;
+constexpr int kSplitSteps = 20;   // target K steps per slice
+
+__global__ void __launch_bounds__(64) sgemm_small_kernel(
+    int M, int N, const float* __restrict__ A1, int lda1, int K1, const float* __restrict__ A2,
+    int lda2, int K2, const float* __restrict__ W, int ldw, float* __restrict__ part,
+    int steps_per_slice) {
+    __shared__ __align__(16) float As[2][SBK][SBM];
+    __shared__ __align__(16) float Bs[2][SBK][SBN];
+    const int tid = threadIdx.x;
+    const int bm = blockIdx.y * SBM;
+    const int bn = blockIdx.x * SBN;
+    const int nk1 = K1 / SBK;
+    const int kt0 = blockIdx.z * steps_per_slice;
+    const int nk = min(nk1 + K2 / SBK, kt0 + steps_per_slice);
+    // one float4 of A and one of W per thread per K step: row tid/2, k (tid&1)*4
+    const int lrow = tid >> 1;
+    const int lk = (tid & 1) * 4;
+    const int gm = bm + lrow;
+    const int gn = bn + lrow;
+    float4 ra, rb;
+    auto load = [&](int kt) {
+        const float* src;
+        int kk, lda;
+        if (kt < nk1) {
+            src = A1; lda = lda1; kk = kt * SBK;
+        } else {
+            src = A2; lda = lda2; kk = (kt - nk1) * SBK;
+        }
+        ra = gm < M ? __ldg(reinterpret_cast<const float4*>(src + (int64_t)gm * lda + kk + lk))
+                    : make_float4(0.f, 0.f, 0.f, 0.f);
+        rb = gn < N ? __ldg(reinterpret_cast<const float4*>(W + (int64_t)gn * ldw + kt * SBK + lk))
+                    : make_float4(0.f, 0.f, 0.f, 0.f);
+    };
+    auto store = [&](int buf) {
+        As[buf][lk + 0][lrow] = ra.x; As[buf][lk + 1][lrow] = ra.y;
+        As[buf][lk + 2][lrow] = ra.z; As[buf][lk + 3][lrow] = ra.w;
+        Bs[buf][lk + 0][lrow] = rb.x; Bs[buf][lk + 1][lrow] = rb.y;
+        Bs[buf][lk + 2][lrow] = rb.z; Bs[buf][lk + 3][lrow] = rb.w;
+    };
+    const int ty = tid >> 3;   // rows ty*4 .. +3
+    const int tx = tid & 7;    // cols tx*4 .. +3
+    float acc[4][4] = {};
+    if (kt0 < nk) {
+        load(kt0);
+        store(0);
+    }
+    __syncthreads();
+    for (int kt = kt0; kt < nk; ++kt) {
+        const int cur = (kt - kt0) & 1;
+        if (kt + 1 < nk) load(kt + 1);
+#pragma unroll
+        for (int k = 0; k < SBK; ++k) {
+            const float4 a = *reinterpret_cast<const float4*>(&As[cur][k][ty * 4]);
+            const float4 b = *reinterpret_cast<const float4*>(&Bs[cur][k][tx * 4]);
+            const float av[4] = {a.x, a.y, a.z, a.w};
+            const float bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+        }
+        if (kt + 1 < nk) store(cur ^ 1);
+        __syncthreads();
+    }
+    const int col = bn + tx * 4;
+    if (col >= N) return;
+    float* slice = part + (int64_t)blockIdx.z * M * N;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int row = bm + ty * 4 + i;
+        if (row >= M) continue;
+        *reinterpret_cast<float4*>(slice + (int64_t)row * N + col) =
+            make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+    }
+}
+
+// out[m][n] = lrelu(bias[n] + sum over the S slices of part[s][m][n]), four
+// columns per thread, slices added in order.
+__global__ void __launch_bounds__(256) splitk_finish_kernel(int M, int N, int S,
+                                                            const float* __restrict__ part,
+                                                            const float* __restrict__ bias,
+                                                            float slope, float* __restrict__ Out,
+                                                            int ldo) {
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int nq = N / 4;
+    if (q >= (int64_t)M * nq) return;
+    const int row = (int)(q / nq);
+    const int col = (int)(q - (int64_t)row * nq) * 4;
+    float4 o = *reinterpret_cast<const float4*>(bias + col);
+    for (int z = 0; z < S; ++z) {
+        const float4 p = __ldg(reinterpret_cast<const float4*>(part + ((int64_t)z * M + row) * N + col));
+        o.x += p.x;
+        o.y += p.y;
+        o.z += p.z;
+        o.w += p.w;
+    }
+    o.x = o.x >= 0.f ? o.x : slope * o.x;
+    o.y = o.y >= 0.f ? o.y : slope * o.y;
+    o.z = o.z >= 0.f ? o.z : slope * o.z;
+    o.w = o.w >= 0.f ? o.w : slope * o.w;
+    *reinterpret_cast<float4*>(Out + (int64_t)row * ldo + col) = o;
+}
+
 __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -201,11 +313,30 @@ __global__ void __launch_bounds__(256) last_layer_kernel(
 
 }  // namespace
 
+int splitk_slices(int K1, int K2) {
+    const int steps = (K1 + K2) / SBK;
+    return steps <= 0 ? 1 : (steps + kSplitSteps - 1) / kSplitSteps;
+}
+
 cudaError_t launch_sgemm_bias_lrelu(int M, int N, const float* A1, int lda1, int K1,
                                     const float* A2, int lda2, int K2, const float* W, int ldw,
                                     const float* bias, float slope, float* Out, int ldo,
-                                    cudaStream_t stream) {
+                                    cudaStream_t stream, float* part) {
     if (M <= 0) return cudaSuccess;
+    if (M <= kSmallM && part) {
+        const int steps = (K1 + K2) / SBK;
+        const int S = splitk_slices(K1, K2);
+        const int per = (steps + S - 1) / S;
+        dim3 grid((N + SBN - 1) / SBN, (M + SBM - 1) / SBM, S);
+        sgemm_small_kernel<<<grid, 64, 0, stream>>>(M, N, A1, lda1, K1, A2, lda2, K2, W, ldw, part,
+                                                    per);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        const int64_t nthreads = (int64_t)M * (N / 4);
+        splitk_finish_kernel<<<(unsigned)((nthreads + 255) / 256), 256, 0, stream>>>(
+            M, N, S, part, bias, slope, Out, ldo);
+        return cudaGetLastError();
+    }
     dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM);
     sgemm_bias_lrelu_kernel<<<grid, 256, 0, stream>>>(M, N, A1, lda1, K1, A2, lda2, K2, W, ldw,
                                                       bias, slope, Out, ldo);

@@ -10,16 +10,24 @@
 // and from the X tensor map for the remaining nk2, against the matching
 // columns of W (whose x part is zero-padded to a whole K-block).
 //
-// One CTA computes a 128 x BN tile with 4 warps:
-//   warp 0 lane 0  TMA producer: A (128 x 64) and W (BN x 64) tiles into a
-//                  4-stage ring of 128B-swizzled shared-memory buffers;
-//   warp 1 lane 0  MMA issuer: 4 x tcgen05.mma (K = 16 each) per stage into
-//                  one TMEM accumulator of BN columns, tcgen05.commit frees
-//                  the stage;
-//   all 4 warps    epilogue: tcgen05.ld of their 32 TMEM lanes (= rows),
-//                  bias + leaky-ReLU, BF16 stores.
-// Every mbarrier wait is bounded; a wait that gives up sets *err and the CTA
-// still releases its tensor memory and returns.
+// Persistent, warp-specialised kernel: one CTA per SM walks the 128 x BN
+// output tiles (tile t covers rows 128 (t / (N/BN)), columns BN (t % (N/BN)),
+// so the CTAs working at one moment share A rows through L2).  10 warps:
+//   warp 0 lane 0   TMA producer: A (128 x 64) and W (BN x 64) tiles into a
+//                   4-stage ring of 128B-swizzled shared-memory buffers;
+//   warp 1          allocates 2 x BN TMEM columns; lane 0 issues 4 x
+//                   tcgen05.mma (K = 16) per stage into the accumulator of
+//                   the current tile (two accumulators, used alternately),
+//                   tcgen05.commit releases the stage and, after the last
+//                   K-block, hands the accumulator to the epilogue;
+//   warps 2 .. 9    epilogue, two warps per TMEM lane quadrant (the tile's
+//                   rows 32 (warp % 4) ..), each taking half of the columns:
+//                   tcgen05.ld 64 columns per wait, bias (staged in shared
+//                   memory once per CTA) + leaky-ReLU, BF16 stores, then
+//                   give the accumulator back -- overlapping the next
+//                   tile's main loop.
+// Every mbarrier wait is bounded; a wait that gives up sets *err, the role
+// stops, and the CTA still releases its tensor memory and returns.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
@@ -37,8 +45,26 @@ constexpr int TBK = 64;
 constexpr int TSTAGES = 4;
 constexpr uint32_t kWaitLimit = 1u << 20;   // polls; legitimate waits are microseconds
 
+constexpr int kMaxN = 1024;   // widest layer whose bias is staged in shared memory
+constexpr int kEpiWarps = 8;
+constexpr int kThreads = 64 + 32 * kEpiWarps;
+
 __host__ __device__ constexpr uint32_t tc_smem_bytes(int BN) {
-    return (uint32_t)TSTAGES * (TBM * TBK * 2 + BN * TBK * 2) + 1024 + 256;
+    // operand ring + 1024-byte alignment slack + barriers + staged bias
+    return (uint32_t)TSTAGES * (TBM * TBK * 2 + BN * TBK * 2) + 1024 + 256 + kMaxN * 4;
+}
+
+// 64 consecutive TMEM columns of the warp's 32 lanes: four x16 loads, one wait.
+__device__ __forceinline__ void tmem_ld64(uint32_t taddr, uint32_t (&r)[64]) {
+    uint32_t(&r0)[16] = *reinterpret_cast<uint32_t(*)[16]>(&r[0]);
+    uint32_t(&r1)[16] = *reinterpret_cast<uint32_t(*)[16]>(&r[16]);
+    uint32_t(&r2)[16] = *reinterpret_cast<uint32_t(*)[16]>(&r[32]);
+    uint32_t(&r3)[16] = *reinterpret_cast<uint32_t(*)[16]>(&r[48]);
+    tmem_ld16(taddr, r0);
+    tmem_ld16(taddr + 16, r1);
+    tmem_ld16(taddr + 32, r2);
+    tmem_ld16(taddr + 48, r3);
+    tmem_ld_wait();
 }
 
 __device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
@@ -47,120 +73,168 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
 }
 
 template <int BN>
-__global__ void __launch_bounds__(128, 1) tc_linear_kernel(
+__global__ void __launch_bounds__(kThreads, 1) tc_linear_kernel(
     const __grid_constant__ CUtensorMap tmA1, const __grid_constant__ CUtensorMap tmA2,
-    const __grid_constant__ CUtensorMap tmW, int nk1, int nk2, int M,
+    const __grid_constant__ CUtensorMap tmW, int nk1, int nk2, int M, int N,
     const float* __restrict__ bias, float slope, __nv_bfloat16* __restrict__ out, int ldo,
     unsigned int* __restrict__ err) {
     constexpr uint32_t A_BYTES = TBM * TBK * 2;
     constexpr uint32_t B_BYTES = BN * TBK * 2;
-    constexpr uint32_t TMEM_COLS = BN;   // 64, 128 or 256: a power of two >= 32
+    constexpr uint32_t TMEM_COLS = 2 * BN;   // two accumulators; 128, 256 or 512
     extern __shared__ uint8_t smem_raw[];
     uint8_t* sA = reinterpret_cast<uint8_t*>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
     uint8_t* sB = sA + TSTAGES * A_BYTES;
     uint64_t* full = reinterpret_cast<uint64_t*>(sB + TSTAGES * B_BYTES);
     uint64_t* empty = full + TSTAGES;
-    uint64_t* accf = empty + TSTAGES;
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(accf + 1);
+    uint64_t* accf = empty + TSTAGES;   // [2] accumulator ready for the epilogue
+    uint64_t* acce = accf + 2;          // [2] accumulator drained by the epilogue
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(acce + 2);
+    float* sbias = reinterpret_cast<float*>(reinterpret_cast<uint8_t*>(full) + 256);
 
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
-    const int m0 = blockIdx.y * TBM;
-    const int n0 = blockIdx.x * BN;
     const int nk = nk1 + nk2;
+    const int n_tn = N / BN;
+    const int n_tiles = ((M + TBM - 1) / TBM) * n_tn;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < TSTAGES; ++s) {
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
-        mbar_init(accf, 1);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&accf[b], 1);
+            mbar_init(&acce[b], kEpiWarps);   // one arrival per epilogue warp
+        }
         fence_mbar_init();
         if (nk1 > 0) prefetch_tmap(&tmA1);
         prefetch_tmap(&tmA2);
         prefetch_tmap(&tmW);
     }
-    if (warp == 0) tmem_alloc(tslot, TMEM_COLS);
+    for (int c = threadIdx.x; c < N; c += blockDim.x) sbias[c] = bias[c];
+    if (warp == 1) tmem_alloc(tslot, TMEM_COLS);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tslot;
 
     bool ok = true;
-    if (warp == 0 && lane == 0) {
-        // TMA producer
-        for (int kb = 0; kb < nk; ++kb) {
-            const int s = kb % TSTAGES;
-            const uint32_t u = (uint32_t)(kb / TSTAGES);
-            if (u > 0 && !mbar_wait(&empty[s], (u - 1) & 1u, kWaitLimit)) {
-                ok = false;
-                break;
+    if (warp == 0) {
+        if (lane == 0) {
+            // TMA producer
+            uint32_t g = 0;
+            for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
+                const int m0 = (t / n_tn) * TBM;
+                const int n0 = (t % n_tn) * BN;
+                for (int kb = 0; kb < nk; ++kb, ++g) {
+                    const uint32_t s = g % TSTAGES;
+                    const uint32_t u = g / TSTAGES;
+                    if (u > 0 && !mbar_wait(&empty[s], (u - 1) & 1u, kWaitLimit)) {
+                        ok = false;
+                        break;
+                    }
+                    mbar_arrive_expect_tx(&full[s], A_BYTES + B_BYTES);
+                    if (kb < nk1)
+                        tma_load_2d(sA + s * A_BYTES, &tmA1, kb * TBK, m0, &full[s]);
+                    else
+                        tma_load_2d(sA + s * A_BYTES, &tmA2, (kb - nk1) * TBK, m0, &full[s]);
+                    tma_load_2d(sB + s * B_BYTES, &tmW, kb * TBK, n0, &full[s]);
+                }
             }
-            mbar_arrive_expect_tx(&full[s], A_BYTES + B_BYTES);
-            if (kb < nk1)
-                tma_load_2d(sA + s * A_BYTES, &tmA1, kb * TBK, m0, &full[s]);
-            else
-                tma_load_2d(sA + s * A_BYTES, &tmA2, (kb - nk1) * TBK, m0, &full[s]);
-            tma_load_2d(sB + s * B_BYTES, &tmW, kb * TBK, n0, &full[s]);
         }
-    } else if (warp == 1 && lane == 0) {
-        // MMA issuer
-        constexpr uint32_t idesc = idesc_bf16_f32(TBM, BN);
-        for (int kb = 0; kb < nk; ++kb) {
-            const int s = kb % TSTAGES;
-            const uint32_t u = (uint32_t)(kb / TSTAGES);
-            if (!mbar_wait(&full[s], u & 1u, kWaitLimit)) {
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // MMA issuer
+            constexpr uint32_t idesc = idesc_bf16_f32(TBM, BN);
+            uint32_t g = 0, i = 0;
+            for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x, ++i) {
+                const uint32_t b = i & 1u, j = i >> 1;
+                if (j > 0 && !mbar_wait(&acce[b], (j - 1) & 1u, kWaitLimit)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t d = tmem + b * BN;
+                for (int kb = 0; kb < nk; ++kb, ++g) {
+                    const uint32_t s = g % TSTAGES;
+                    const uint32_t u = g / TSTAGES;
+                    if (!mbar_wait(&full[s], u & 1u, kWaitLimit)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t a0 = smem_u32(sA + s * A_BYTES);
+                    const uint32_t b0 = smem_u32(sB + s * B_BYTES);
+#pragma unroll
+                    for (int k = 0; k < TBK / 16; ++k)
+                        mma_bf16(d, desc_k_sw128(a0 + k * 32), desc_k_sw128(b0 + k * 32), idesc,
+                                 (kb | k) != 0 ? 1u : 0u);
+                    mma_commit(&empty[s]);
+                }
+                mma_commit(&accf[b]);   // also after an error, so the epilogue is released
+            }
+        }
+    } else {
+        // epilogue warps 2..9: TMEM lane quadrant q holds tile rows 32 q .. 32 q + 31;
+        // warps 2-5 take columns [0, BN/2), warps 6-9 columns [BN/2, BN)
+        constexpr int HALF = BN / 2;
+        const int q = warp & 3;
+        const int cbase = ((warp - 2) >> 2) * HALF;
+        uint32_t i = 0;
+        for (int t = blockIdx.x; t < n_tiles; t += gridDim.x, ++i) {
+            const uint32_t b = i & 1u, j = i >> 1;
+            const int m0 = (t / n_tn) * TBM;
+            const int n0 = (t % n_tn) * BN;
+            // warp-uniform: tcgen05.ld below is a .sync.aligned warp instruction
+            if (!__all_sync(0xffffffffu, mbar_wait(&accf[b], j & 1u, kWaitLimit))) {
                 ok = false;
                 break;
             }
             tc_fence_after();
-            const uint32_t a0 = smem_u32(sA + s * A_BYTES);
-            const uint32_t b0 = smem_u32(sB + s * B_BYTES);
-#pragma unroll
-            for (int k = 0; k < TBK / 16; ++k)
-                mma_bf16(tmem, desc_k_sw128(a0 + k * 32), desc_k_sw128(b0 + k * 32), idesc,
-                         (kb | k) != 0 ? 1u : 0u);
-            mma_commit(&empty[s]);
-        }
-        mma_commit(accf);   // also after an error, so the epilogue is released
-    }
-    __syncwarp();
-
-    // epilogue: TMEM lanes 32 warp .. 32 warp + 31 hold rows m0 + 32 warp + lane
-    // warp-uniform decision: tcgen05.ld below is a .sync.aligned warp instruction
-    const bool acc_ready = __all_sync(0xffffffffu, mbar_wait(accf, 0, kWaitLimit));
-    tc_fence_after();
-    if (acc_ready) {
-        const int row = m0 + warp * 32 + lane;
-        const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);
+            const int row = m0 + q * 32 + lane;
+            const uint32_t tl = tmem + ((uint32_t)(q * 32) << 16) + b * BN;
+            const float* bb = sbias + n0;
 #pragma unroll 1
-        for (int c0 = 0; c0 < BN; c0 += 16) {
-            uint32_t r[16];
-            tmem_ld16(tl + (uint32_t)c0, r);
-            tmem_ld_wait();
-            if (row < M) {
-                uint32_t pk[8];
-#pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    float a = __uint_as_float(r[2 * j]) + __ldg(bias + n0 + c0 + 2 * j);
-                    float b = __uint_as_float(r[2 * j + 1]) + __ldg(bias + n0 + c0 + 2 * j + 1);
-                    a = a >= 0.f ? a : slope * a;
-                    b = b >= 0.f ? b : slope * b;
-                    pk[j] = pack_bf16x2(a, b);
+            for (int c0 = cbase; c0 < cbase + HALF; c0 += 64) {
+                uint32_t r[64];
+                if (HALF >= 64) {
+                    tmem_ld64(tl + (uint32_t)c0, r);
+                } else {
+                    uint32_t(&r0)[16] = *reinterpret_cast<uint32_t(*)[16]>(&r[0]);
+                    uint32_t(&r1)[16] = *reinterpret_cast<uint32_t(*)[16]>(&r[16]);
+                    tmem_ld16(tl + (uint32_t)c0, r0);
+                    tmem_ld16(tl + (uint32_t)c0 + 16, r1);
+                    tmem_ld_wait();
                 }
-                uint4* dst = reinterpret_cast<uint4*>(out + (int64_t)row * ldo + n0 + c0);
-                dst[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
-                dst[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+                if (row < M) {
+                    constexpr int NC = HALF >= 64 ? 64 : HALF;
+                    uint4* dst = reinterpret_cast<uint4*>(out + (int64_t)row * ldo + n0 + c0);
+#pragma unroll
+                    for (int v = 0; v < NC / 8; ++v) {
+                        uint32_t pk[4];
+#pragma unroll
+                        for (int jj = 0; jj < 4; ++jj) {
+                            const int cc = v * 8 + 2 * jj;
+                            float a = __uint_as_float(r[cc]) + bb[c0 + cc];
+                            float c = __uint_as_float(r[cc + 1]) + bb[c0 + cc + 1];
+                            a = a >= 0.f ? a : slope * a;
+                            c = c >= 0.f ? c : slope * c;
+                            pk[jj] = pack_bf16x2(a, c);
+                        }
+                        dst[v] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                    }
+                }
             }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&acce[b]);
         }
-    } else {
-        ok = false;
     }
     if (!ok) atomicOr(err, 1u);
     tc_fence_before();
     __syncthreads();
-    if (warp == 0) tmem_dealloc(tmem, TMEM_COLS);
+    if (warp == 1) tmem_dealloc(tmem, TMEM_COLS);
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
@@ -178,8 +252,15 @@ cudaError_t launch_bn(const TcLayerArgs& a, cudaStream_t s) {
         if (e != cudaSuccess) return e;
         if (dev >= 0 && dev < 64) attr_set[dev] = true;
     }
-    dim3 grid(a.N / BN, (unsigned)((a.M + TBM - 1) / TBM));
-    tc_linear_kernel<BN><<<grid, 128, smem, s>>>(*a.tmA1, *a.tmA2, *a.tmW, a.nk1, a.nk2, a.M,
+    static int n_sm[64] = {};
+    if (dev >= 0 && dev < 64 && n_sm[dev] == 0) {
+        e = cudaDeviceGetAttribute(&n_sm[dev], cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return e;
+    }
+    const int sms = (dev >= 0 && dev < 64) ? n_sm[dev] : 148;
+    const long long tiles = (long long)(a.N / BN) * ((a.M + TBM - 1) / TBM);
+    const int grid = (int)(tiles < sms ? tiles : sms);
+    tc_linear_kernel<BN><<<grid, kThreads, smem, s>>>(*a.tmA1, *a.tmA2, *a.tmW, a.nk1, a.nk2, a.M, a.N,
                                                  a.bias, a.slope, a.out, a.ldo, a.err);
     return cudaGetLastError();
 }
@@ -211,6 +292,7 @@ bool tc_encode_2d_bf16(void* map, const void* base, uint64_t cols, uint64_t rows
 
 cudaError_t launch_tc_linear(const TcLayerArgs& a, cudaStream_t s) {
     if (a.M <= 0) return cudaSuccess;
+    if (a.N > kMaxN) return cudaErrorInvalidValue;
     switch (a.BN) {
         case 256: return launch_bn<256>(a, s);
         case 128: return launch_bn<128>(a, s);

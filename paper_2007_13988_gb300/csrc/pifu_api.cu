@@ -128,6 +128,8 @@ struct pifu_ctx {
     int64_t X_cap = 0, H_cap = 0;   // elements
     __nv_bfloat16* Xb = nullptr;
     __nv_bfloat16* Hb[2] = {nullptr, nullptr};
+    float* part = nullptr;            // split-K partial sums of small FP32 batches
+    int64_t part_cap = 0;
     // level workspace, sized for ws_N
     int ws_N = 0;
     uint32_t* cand = nullptr;
@@ -321,6 +323,16 @@ int ensure_mlp_ws(pifu_ctx* ctx) {
         CK(dev_alloc(&ctx->Hb[1], need_h));
         ctx->H_cap = need_h;
     }
+    int64_t need_p = 0;
+    for (const DevNet& n : ctx->net)
+        for (const DevLayer& L : n.layers)
+            need_p = std::max<int64_t>(need_p, (int64_t)splitk_slices(L.K1, L.K2) * kSplitMaxM *
+                                                   L.n_out);
+    if (need_p > ctx->part_cap) {
+        dev_free(ctx->part);
+        CK(dev_alloc(&ctx->part, need_p));
+        ctx->part_cap = need_p;
+    }
     return PIFU_OK;
 }
 
@@ -507,8 +519,8 @@ int run_mlp(pifu_ctx* ctx, const DevNet& net, const PointSrc& src, int64_t m, co
             float* out = (l % 2 == 0) ? ctx->HA : ctx->HB;
             ev = pr.begin(s);
             CK(launch_sgemm_bias_lrelu((int)mc, Ly.n_out, h, hw, Ly.K1, ctx->X, net.ldx, Ly.K2, Ly.W,
-                                       Ly.ldw, Ly.b, net.slope, out, Ly.n_out, s));
-            pr.end(PIFU_K_MLP_HIDDEN, ev, s, 2.0 * mc * Ly.fan_in * Ly.n_out,
+                                       Ly.ldw, Ly.b, net.slope, out, Ly.n_out, s, ctx->part));
+            pr.end(PIFU_K_MLP_F32, ev, s, 2.0 * mc * Ly.fan_in * Ly.n_out,
                    4.0 * ((double)mc * (Ly.fan_in + Ly.n_out) + (double)Ly.n_out * (Ly.fan_in + 1)));
             h = out;
             hw = Ly.n_out;
@@ -666,6 +678,7 @@ void pifu_destroy(pifu_ctx* ctx) {
     dev_free(ctx->Xb);
     dev_free(ctx->Hb[0]);
     dev_free(ctx->Hb[1]);
+    dev_free(ctx->part);
     uint32_t** bitsets[] = {&ctx->cand, &ctx->tent, &ctx->bin[0], &ctx->bin[1],
                             &ctx->eval, &ctx->conf[0], &ctx->conf[1]};
     for (auto b : bitsets) dev_free(*b);
@@ -820,10 +833,11 @@ int pifu_localize(pifu_ctx* ctx, const pifu_fmap* occ_map, const float calib[12]
         CK(cudaMemsetAsync(ctx->d_count, 0, sizeof(unsigned int), s));
         ev = ctx->prof.begin(s);
         CK(launch_dilate_select(ctx->cand, ctx->eval, ctx->conf[1], N, ctx->list, ctx->d_count, s));
+        ctx->prof.end(PIFU_K_SELECT, ev, s, 0.0, 4.0 * wbytes);
         unsigned int n = 0;
         st = read_count(ctx, s, &n);
         if (st != PIFU_OK) return st;
-        ctx->prof.end(PIFU_K_SELECT, ev, s, 0.0, 4.0 * wbytes + 4.0 * n);
+        ctx->prof.k[PIFU_K_SELECT].bytes += 4.0 * n;   // the list it wrote
         int64_t level_evals = 0;
         int q = 0;     // conflicts of the next evaluation go to conf[q]
         int rounds = 0;
@@ -844,9 +858,10 @@ int pifu_localize(pifu_ctx* ctx, const pifu_fmap* occ_map, const float calib[12]
             ev = ctx->prof.begin(s);
             CK(launch_dilate_select(ctx->conf[q], ctx->eval, ctx->conf[1 - q], N, ctx->list,
                                     ctx->d_count, s));
+            ctx->prof.end(PIFU_K_SELECT, ev, s, 0.0, 4.0 * wbytes);
             st = read_count(ctx, s, &n);
             if (st != PIFU_OK) return st;
-            ctx->prof.end(PIFU_K_SELECT, ev, s, 0.0, 4.0 * wbytes + 4.0 * n);
+            ctx->prof.k[PIFU_K_SELECT].bytes += 4.0 * n;
             if (n > 0) {
                 if (rounds >= max_rounds) return PIFU_ERR_NOT_CONVERGED;
                 ++rounds;
@@ -919,15 +934,18 @@ int pifu_render(pifu_ctx* ctx, const pifu_camera* cam, const pifu_fmap* occ_map,
     CK(cudaMemsetAsync(ctx->d_count, 0, sizeof(unsigned int), s));
     cudaEvent_t ev = ctx->prof.begin(s);
     CK(launch_render_rays(a, s));
+    {
+        // the volume once (two bitsets + the evaluated values) and the outputs
+        const double vol_bytes = 2.0 * 4.0 * words_of(ctx->vol_N) +
+                                 4.0 * (double)ctx->stats.evals_per_level[ctx->stats.num_levels - 1];
+        const double out_bytes =
+            (double)npix * ((depth_dev ? 4 : 0) + (rgb_dev ? 12 : 0) + (mask_dev ? 1 : 0));
+        ctx->prof.end(PIFU_K_RENDER, ev, s, 0.0, vol_bytes + out_bytes);
+    }
     unsigned int n = 0;
     st = read_count(ctx, s, &n);
     if (st != PIFU_OK) return st;
-    {
-        // the volume once (two bitsets + the evaluated values) and the outputs
-        const double vol_bytes = 2.0 * 4.0 * words_of(ctx->vol_N) + 4.0 * (double)ctx->stats.evals_per_level[ctx->stats.num_levels - 1];
-        const double out_bytes = (double)npix * ((depth_dev ? 4 : 0) + (rgb_dev ? 12 : 0) + (mask_dev ? 1 : 0));
-        ctx->prof.end(PIFU_K_RENDER, ev, s, 0.0, vol_bytes + out_bytes + 16.0 * n);
-    }
+    ctx->prof.k[PIFU_K_RENDER].bytes += 16.0 * n;   // the hit list
     if (!rgb_dev) return PIFU_OK;
     if (n == 0) return PIFU_OK;
     PointSrc src{PTS_XYZ, ctx->hit_xyz, nullptr, 0, 0};

@@ -88,11 +88,15 @@ cudaError_t launch_gather_bf16(const PointSrc& src, int64_t p0, int64_t m, const
 
 // --- mlp_f32.cu ------------------------------------------------------------
 // Out[M][N] = lrelu(A1[M][K1] W[:, :K1]^T + A2[M][K2] W[:, K1:]^T + b);
-// K1, K2 multiples of 8; N a multiple of 4; ld* multiples of 4.
+// K1, K2 multiples of 8; N a multiple of 4; ld* multiples of 4.  Batches of
+// at most kSplitMaxM points use split-K over `part`, a scratch array of
+// splitk_slices(K1, K2) * M * N floats (null: always the big-tile kernel).
+constexpr int kSplitMaxM = 8192;
+int splitk_slices(int K1, int K2);
 cudaError_t launch_sgemm_bias_lrelu(int M, int N, const float* A1, int lda1, int K1,
                                     const float* A2, int lda2, int K2, const float* W, int ldw,
                                     const float* bias, float slope, float* Out, int ldo,
-                                    cudaStream_t stream);
+                                    cudaStream_t stream, float* part);
 
 // Last layer (n_out <= 4 outputs) plus activation and epilogue, one warp per point.
 cudaError_t launch_last_layer(int64_t p0, int64_t M, int n_out, const float* A1, int lda1, int K1,

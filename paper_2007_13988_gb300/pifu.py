@@ -36,7 +36,7 @@ EXPORTS = ("pifu_create", "pifu_destroy", "pifu_query", "pifu_query_colour", "pi
            "pifu_render", "pifu_sync_stats", "pifu_status_string", "pifu_last_error",
            "pifu_profile", "pifu_profile_read", "pifu_query_noalloc", "pifu_query_ex")
 
-KERNEL_CLASSES = ("gather", "mlp_hidden", "mlp_last", "level", "select", "render")
+KERNEL_CLASSES = ("gather", "mlp_hidden", "mlp_last", "level", "select", "render", "mlp_f32")
 
 
 class pifu_fmap(ctypes.Structure):
