@@ -129,7 +129,7 @@ __global__ void __launch_bounds__(256) sgemm_bias_lrelu_kernel(
 // the slices in a fixed order (deterministic, no atomics) and applies bias
 // and leaky-ReLU.  A batch of M points spreads over (M/32) (N/32) S CTAs.
 constexpr int SBM = 32, SBN = 32, SBK = 8;
-constexpr int kSplitSteps = 20;   // target K steps per slice
+constexpr int kSplitSteps = 6;    // target K steps per slice (latency-bound: keep short)
 
 __global__ void __launch_bounds__(64) sgemm_small_kernel(
     int M, int N, const float* __restrict__ A1, int lda1, int K1, const float* __restrict__ A2,

@@ -16,6 +16,7 @@ namespace {
 constexpr int kMaxLevels = 8;
 constexpr int kMaxFine = 512;
 constexpr int64_t kChunk = 65536;   // points per MLP pass (bounds the activation workspace)
+constexpr int64_t kTinyBatch = 256; // mixed precision: batches this small run in FP32
 
 struct DevLayer {
     int n_out = 0;
@@ -151,6 +152,7 @@ struct pifu_ctx {
     float* hit_xyz = nullptr;
     int* hit_pix = nullptr;
     int64_t hit_cap = 0;
+    int* col_top = nullptr;       // render: per node column, highest non-empty depth
     // last localized volume
     bool have_volume = false;
     int vol_N = 0;
@@ -400,6 +402,8 @@ int ensure_level_ws(pifu_ctx* ctx, int N) {
     }
     CK(dev_alloc(&ctx->values, nodes));
     CK(dev_alloc(&ctx->list, nodes));
+    dev_free(ctx->col_top);
+    CK(dev_alloc(&ctx->col_top, (int64_t)(N + 1) * (N + 1)));
     if (nodes > ctx->recheck_cap) {
         dev_free(ctx->recheck);
         ctx->recheck_cap = 0;
@@ -546,6 +550,9 @@ int run_mlp_mixed(pifu_ctx* ctx, const DevNet& net, const PointSrc& src, int64_t
                   const Map& map0, const Map& map1, const Calib& calib, const Epilogue& epi,
                   float margin, cudaStream_t s, int64_t* rechecked) {
     if (m > ctx->recheck_cap) return PIFU_ERR_ARG;
+    // A tiny batch costs less in FP32 outright than in BF16 plus a re-check
+    // pass (both are latency-bound there); FP32 is the re-check's arithmetic.
+    if (m <= kTinyBatch) return run_mlp(ctx, net, src, m, map0, map1, calib, epi, s, PIFU_PREC_FP32);
     CK(cudaMemsetAsync(ctx->d_recheck, 0, sizeof(unsigned int), s));
     Epilogue e1 = epi;
     e1.recheck = ctx->recheck;
@@ -691,6 +698,7 @@ void pifu_destroy(pifu_ctx* ctx) {
     dev_free(ctx->d_pop);
     dev_free(ctx->hit_xyz);
     dev_free(ctx->hit_pix);
+    dev_free(ctx->col_top);
     if (ctx->h_count) cudaFreeHost(ctx->h_count);
     if (ctx->h_pop) cudaFreeHost(ctx->h_pop);
     delete ctx;
@@ -931,6 +939,7 @@ int pifu_render(pifu_ctx* ctx, const pifu_camera* cam, const pifu_fmap* occ_map,
     a.hit_xyz = ctx->hit_xyz;
     a.hit_pix = ctx->hit_pix;
     a.hit_count = ctx->d_count;
+    a.top = ctx->col_top;
     CK(cudaMemsetAsync(ctx->d_count, 0, sizeof(unsigned int), s));
     cudaEvent_t ev = ctx->prof.begin(s);
     CK(launch_render_rays(a, s));

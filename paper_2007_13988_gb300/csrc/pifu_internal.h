@@ -91,7 +91,7 @@ cudaError_t launch_gather_bf16(const PointSrc& src, int64_t p0, int64_t m, const
 // K1, K2 multiples of 8; N a multiple of 4; ld* multiples of 4.  Batches of
 // at most kSplitMaxM points use split-K over `part`, a scratch array of
 // splitk_slices(K1, K2) * M * N floats (null: always the big-tile kernel).
-constexpr int kSplitMaxM = 8192;
+constexpr int kSplitMaxM = 2048;
 int splitk_slices(int K1, int K2);
 cudaError_t launch_sgemm_bias_lrelu(int M, int N, const float* A1, int lda1, int K1,
                                     const float* A2, int lda2, int K2, const float* W, int ldw,
@@ -170,6 +170,7 @@ struct RenderArgs {
     float* hit_xyz;       // [width*height][3] surface points of hits
     int* hit_pix;         // pixel index per hit
     unsigned int* hit_count;
+    int* top;             // [(N+1)^2] scratch: highest non-empty depth node per column
 };
 cudaError_t launch_render_rays(const RenderArgs& a, cudaStream_t stream);
 

@@ -19,6 +19,30 @@
 namespace pifu {
 namespace {
 
+// Highest depth-node index k (z index, 0..N) at which node column (i, j) has
+// any evaluated or inside node: one thread per bitset word (k, j, word), one
+// atomicMax per set bit into top[j][i], which starts at -1 (empty column).
+__global__ void __launch_bounds__(256) column_top_kernel(int N, int row_words,
+                                                         const uint32_t* __restrict__ eval,
+                                                         const uint32_t* __restrict__ bin,
+                                                         int* __restrict__ top) {
+    const int n1 = N + 1;
+    const int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= (int64_t)n1 * n1 * row_words) return;
+    uint32_t bits = __ldg(eval + w) | __ldg(bin + w);
+    if (!bits) return;
+    const int wx = (int)(w % row_words);
+    const int64_t row = w / row_words;   // k (N+1) + j
+    const int j = (int)(row % n1);
+    const int k = (int)(row / n1);
+    int* t = top + (int64_t)j * n1 + wx * 32;
+    while (bits) {
+        const int b = __ffs(bits) - 1;
+        bits &= bits - 1u;
+        atomicMax(t + b, k);
+    }
+}
+
 // bits ix and ix+1 of a bitset row as bits 0 and 1 (ix + 1 <= N is in the row)
 __device__ __forceinline__ uint32_t two_bits(const uint32_t* __restrict__ rowp, int ix) {
     uint32_t v = __ldg(rowp + (ix >> 5)) >> (ix & 31);
@@ -61,8 +85,12 @@ __global__ void __launch_bounds__(256) render_rays_kernel(RenderArgs a) {
         const float w00 = (1.f - wx) * (1.f - wy), w10 = wx * (1.f - wy);
         const float w01 = (1.f - wx) * wy, w11 = wx * wy;
         const float h = 2.0f / (float)a.N;
+        // samples nearer the observer than every node of the four columns are 0
+        const int64_t c0 = (int64_t)iy0 * n1 + ix0;
+        const int ktop = max(max(a.top[c0], a.top[c0 + 1]), max(a.top[c0 + n1], a.top[c0 + n1 + 1]));
+        const int kstart = ktop < 0 ? a.N + 1 : a.N - ktop;
         float vprev = 0.f;
-        for (int k = 0; k <= a.N; ++k) {
+        for (int k = kstart; k <= a.N; ++k) {
             const int iz = a.N - k;
             const int64_t row0 = (int64_t)iz * n1 + iy0;
             const int64_t row1 = row0 + 1;
@@ -119,6 +147,14 @@ __global__ void __launch_bounds__(256) render_rays_kernel(RenderArgs a) {
 cudaError_t launch_render_rays(const RenderArgs& a, cudaStream_t stream) {
     const int64_t npix = (int64_t)a.width * a.height;
     if (npix <= 0) return cudaSuccess;
+    const int64_t n1 = a.N + 1;
+    cudaError_t e = cudaMemsetAsync(a.top, 0xff, (size_t)(n1 * n1) * sizeof(int), stream);   // -1
+    if (e != cudaSuccess) return e;
+    const int64_t nt = n1 * n1 * a.row_words;
+    column_top_kernel<<<(unsigned)((nt + 255) / 256), 256, 0, stream>>>(a.N, a.row_words, a.eval,
+                                                                        a.bin, a.top);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
     render_rays_kernel<<<(unsigned)((npix + 255) / 256), 256, 0, stream>>>(a);
     return cudaGetLastError();
 }
