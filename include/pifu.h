@@ -52,7 +52,9 @@ typedef enum {
     PIFU_ERR_NOT_CONVERGED = -5,  /* conflict loop hit pifu_levels.max_rounds    */
     PIFU_ERR_TIMEOUT = -6,        /* a bounded device wait gave up               */
     PIFU_ERR_STATE = -7,          /* call order violated (e.g. render first)     */
-    PIFU_ERR_UNSUPPORTED = -8     /* valid request outside what is implemented   */
+    PIFU_ERR_UNSUPPORTED = -8,    /* valid request outside what is implemented   */
+    PIFU_ERR_CAPACITY = -9        /* graph form: a device-side count exceeded a
+                                     fixed capacity (use pifu_localize/render)   */
 } pifu_status;
 
 typedef enum { PIFU_F32 = 0, PIFU_BF16 = 1 } pifu_dtype;

@@ -98,46 +98,55 @@ __global__ void __launch_bounds__(256) gather_kernel(PointSrc src, int64_t p0, i
                                                      Calib calib, Map map0, Map map1,
                                                      OutT* __restrict__ X, int ldx) {
     const int nq = ldx >> 2;
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= m * nq) return;
-    const int64_t lp = t / nq;
-    const int q = (int)(t - lp * nq);
-    const int c = q * 4;
-    float x, y, z;
-    point_xyz(src, p0 + lp, x, y, z);
-    float uh, ul, vh, vl, zh, zl;
-    affine_ff(calib.c + 0, x, y, z, uh, ul);
-    affine_ff(calib.c + 4, x, y, z, vh, vl);
-    affine_ff(calib.c + 8, x, y, z, zh, zl);
+    if (src.count) m = min(m, (int64_t)*src.count);
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < m * nq;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t lp = t / nq;
+        const int q = (int)(t - lp * nq);
+        const int c = q * 4;
+        float x, y, z;
+        point_xyz(src, p0 + lp, x, y, z);
+        float uh, ul, vh, vl, zh, zl;
+        affine_ff(calib.c + 0, x, y, z, uh, ul);
+        affine_ff(calib.c + 4, x, y, z, vh, vl);
+        affine_ff(calib.c + 8, x, y, z, zh, zl);
 
-    float4 r;
-    const int C0 = map0.C, C1 = map1.C;
-    if (c < C0 + C1) {
-        const Map& mp = (c < C0) ? map0 : map1;
-        const int cc = (c < C0) ? c : c - C0;
-        int i0, j0;
-        float a, b;
-        texel_coord(uh, ul, mp.W, i0, a);
-        texel_coord(vh, vl, mp.H, j0, b);
-        const int i1 = min(max(i0 + 1, 0), mp.W - 1);
-        const int j1 = min(max(j0 + 1, 0), mp.H - 1);
-        i0 = min(max(i0, 0), mp.W - 1);
-        j0 = min(max(j0, 0), mp.H - 1);
-        const float* F = static_cast<const float*>(mp.data);
-        const float4 f00 = ld4(F + ((int64_t)j0 * mp.W + i0) * mp.C + cc);
-        const float4 f10 = ld4(F + ((int64_t)j0 * mp.W + i1) * mp.C + cc);
-        const float4 f01 = ld4(F + ((int64_t)j1 * mp.W + i0) * mp.C + cc);
-        const float4 f11 = ld4(F + ((int64_t)j1 * mp.W + i1) * mp.C + cc);
-        const float w00 = (1.f - a) * (1.f - b), w10 = a * (1.f - b);
-        const float w01 = (1.f - a) * b, w11 = a * b;
-        r.x = fmaf(w11, f11.x, fmaf(w01, f01.x, fmaf(w10, f10.x, w00 * f00.x)));
-        r.y = fmaf(w11, f11.y, fmaf(w01, f01.y, fmaf(w10, f10.y, w00 * f00.y)));
-        r.z = fmaf(w11, f11.z, fmaf(w01, f01.z, fmaf(w10, f10.z, w00 * f00.z)));
-        r.w = fmaf(w11, f11.w, fmaf(w01, f01.w, fmaf(w10, f10.w, w00 * f00.w)));
-    } else {
-        r = make_float4(c == C0 + C1 ? __fadd_rn(zh, zl) : 0.f, 0.f, 0.f, 0.f);
+        float4 r;
+        const int C0 = map0.C, C1 = map1.C;
+        if (c < C0 + C1) {
+            const Map& mp = (c < C0) ? map0 : map1;
+            const int cc = (c < C0) ? c : c - C0;
+            int i0, j0;
+            float a, b;
+            texel_coord(uh, ul, mp.W, i0, a);
+            texel_coord(vh, vl, mp.H, j0, b);
+            const int i1 = min(max(i0 + 1, 0), mp.W - 1);
+            const int j1 = min(max(j0 + 1, 0), mp.H - 1);
+            i0 = min(max(i0, 0), mp.W - 1);
+            j0 = min(max(j0, 0), mp.H - 1);
+            const float* F = static_cast<const float*>(mp.data);
+            const float4 f00 = ld4(F + ((int64_t)j0 * mp.W + i0) * mp.C + cc);
+            const float4 f10 = ld4(F + ((int64_t)j0 * mp.W + i1) * mp.C + cc);
+            const float4 f01 = ld4(F + ((int64_t)j1 * mp.W + i0) * mp.C + cc);
+            const float4 f11 = ld4(F + ((int64_t)j1 * mp.W + i1) * mp.C + cc);
+            const float w00 = (1.f - a) * (1.f - b), w10 = a * (1.f - b);
+            const float w01 = (1.f - a) * b, w11 = a * b;
+            r.x = fmaf(w11, f11.x, fmaf(w01, f01.x, fmaf(w10, f10.x, w00 * f00.x)));
+            r.y = fmaf(w11, f11.y, fmaf(w01, f01.y, fmaf(w10, f10.y, w00 * f00.y)));
+            r.z = fmaf(w11, f11.z, fmaf(w01, f01.z, fmaf(w10, f10.z, w00 * f00.z)));
+            r.w = fmaf(w11, f11.w, fmaf(w01, f01.w, fmaf(w10, f10.w, w00 * f00.w)));
+        } else {
+            r = make_float4(c == C0 + C1 ? __fadd_rn(zh, zl) : 0.f, 0.f, 0.f, 0.f);
+        }
+        store4(X + lp * ldx + c, r);
     }
-    store4(X + lp * ldx + c, r);
+}
+
+// One thread per (point, 4 channels); a device-resident count gets a fixed,
+// SM-filling grid that strides over whatever the count turns out to be.
+inline unsigned gather_blocks(const PointSrc& src, int64_t total) {
+    const int64_t exact = (total + 255) / 256;
+    return (unsigned)(src.count ? (exact < 152 * 16 ? exact : 152 * 16) : exact);
 }
 
 }  // namespace
@@ -147,10 +156,8 @@ cudaError_t launch_gather(const PointSrc& src, int64_t p0, int64_t m, const Cali
                           cudaStream_t stream) {
     if (m <= 0) return cudaSuccess;
     const int64_t total = m * (ldx / 4);
-    const int threads = 256;
-    const int64_t blocks = (total + threads - 1) / threads;
-    gather_kernel<float><<<(unsigned)blocks, threads, 0, stream>>>(src, p0, m, calib, map0, map1,
-                                                                  X, ldx);
+    gather_kernel<float><<<gather_blocks(src, total), 256, 0, stream>>>(src, p0, m, calib, map0,
+                                                                       map1, X, ldx);
     return cudaGetLastError();
 }
 
@@ -159,10 +166,8 @@ cudaError_t launch_gather_bf16(const PointSrc& src, int64_t p0, int64_t m, const
                                cudaStream_t stream) {
     if (m <= 0) return cudaSuccess;
     const int64_t total = m * (ldx / 4);
-    const int threads = 256;
-    const int64_t blocks = (total + threads - 1) / threads;
-    gather_kernel<__nv_bfloat16><<<(unsigned)blocks, threads, 0, stream>>>(src, p0, m, calib, map0,
-                                                                          map1, X, ldx);
+    gather_kernel<__nv_bfloat16><<<gather_blocks(src, total), 256, 0, stream>>>(src, p0, m, calib,
+                                                                               map0, map1, X, ldx);
     return cudaGetLastError();
 }
 

@@ -178,6 +178,37 @@ __global__ void __launch_bounds__(256) popcount_kernel(const uint32_t* __restric
     if ((threadIdx.x & 31) == 0 && local) atomicAdd(count, local);
 }
 
+// Graph form: decides whether the conflict loop runs (another) round.  The
+// frontier `count` must be non-empty and fit the batch capacity; a round
+// beyond max_rounds ends the loop with the not-converged error bit.
+__global__ void loop_control_kernel(cudaGraphConditionalHandle h, const unsigned int* count,
+                                    unsigned int cap, unsigned int* rounds, int count_round,
+                                    int max_rounds, unsigned int* err) {
+    const unsigned int c = *count;
+    bool go = c > 0u;
+    if (go && c > cap) {
+        atomicOr(err, kErrCapacity);
+        go = false;
+    }
+    if (go && count_round) {
+        const unsigned int r = *rounds + 1u;
+        *rounds = r;
+        if ((int)r > max_rounds) {
+            atomicOr(err, kErrNotConverged);
+            go = false;
+        }
+    }
+    cudaGraphSetConditional(h, go ? 1u : 0u);
+}
+
+// *dst += *src, flagging a capacity error when *src exceeds cap.
+__global__ void accumulate_kernel(unsigned long long* dst, const unsigned int* src,
+                                  unsigned int cap, unsigned int* err) {
+    const unsigned int v = *src;
+    *dst += v;
+    if (v > cap) atomicOr(err, kErrCapacity);
+}
+
 inline unsigned blocks_for(int64_t n) { return (unsigned)((n + 255) / 256); }
 
 }  // namespace
@@ -200,6 +231,19 @@ cudaError_t launch_dilate_select(const uint32_t* src, uint32_t* eval, uint32_t* 
                                  int* list, unsigned int* count, cudaStream_t stream) {
     dilate_select_kernel<<<blocks_for(words_of(N)), 256, 0, stream>>>(src, eval, clear, N, list,
                                                                      count);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_loop_control(cudaGraphConditionalHandle h, const unsigned int* count,
+                                unsigned int cap, unsigned int* rounds, int count_round,
+                                int max_rounds, unsigned int* err, cudaStream_t stream) {
+    loop_control_kernel<<<1, 1, 0, stream>>>(h, count, cap, rounds, count_round, max_rounds, err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_accumulate(unsigned long long* dst, const unsigned int* src, unsigned int cap,
+                              unsigned int* err, cudaStream_t stream) {
+    accumulate_kernel<<<1, 1, 0, stream>>>(dst, src, cap, err);
     return cudaGetLastError();
 }
 

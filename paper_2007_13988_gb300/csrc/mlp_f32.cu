@@ -134,102 +134,120 @@ constexpr int kSplitSteps = 6;    // target K steps per slice (latency-bound: ke
 __global__ void __launch_bounds__(64) sgemm_small_kernel(
     int M, int N, const float* __restrict__ A1, int lda1, int K1, const float* __restrict__ A2,
     int lda2, int K2, const float* __restrict__ W, int ldw, float* __restrict__ part,
-    int steps_per_slice) {
+    int steps_per_slice, int S, const unsigned int* __restrict__ m_dev) {
+    // M is the capacity (and the slice stride of `part`); a device count
+    // narrows the rows actually computed.
+    const int Mc = M;
+    if (m_dev) M = min(M, (int)*m_dev);
     __shared__ __align__(16) float As[2][SBK][SBM];
     __shared__ __align__(16) float Bs[2][SBK][SBN];
     const int tid = threadIdx.x;
-    const int bm = blockIdx.y * SBM;
-    const int bn = blockIdx.x * SBN;
     const int nk1 = K1 / SBK;
-    const int kt0 = blockIdx.z * steps_per_slice;
-    const int nk = min(nk1 + K2 / SBK, kt0 + steps_per_slice);
+    const int tiles_n = (N + SBN - 1) / SBN;
+    const int tiles_m = (M + SBM - 1) / SBM;
+    const int64_t items = (int64_t)tiles_n * tiles_m * S;
     // one float4 of A and one of W per thread per K step: row tid/2, k (tid&1)*4
     const int lrow = tid >> 1;
     const int lk = (tid & 1) * 4;
-    const int gm = bm + lrow;
-    const int gn = bn + lrow;
-    float4 ra, rb;
-    auto load = [&](int kt) {
-        const float* src;
-        int kk, lda;
-        if (kt < nk1) {
-            src = A1; lda = lda1; kk = kt * SBK;
-        } else {
-            src = A2; lda = lda2; kk = (kt - nk1) * SBK;
-        }
-        ra = gm < M ? __ldg(reinterpret_cast<const float4*>(src + (int64_t)gm * lda + kk + lk))
-                    : make_float4(0.f, 0.f, 0.f, 0.f);
-        rb = gn < N ? __ldg(reinterpret_cast<const float4*>(W + (int64_t)gn * ldw + kt * SBK + lk))
-                    : make_float4(0.f, 0.f, 0.f, 0.f);
-    };
-    auto store = [&](int buf) {
-        As[buf][lk + 0][lrow] = ra.x; As[buf][lk + 1][lrow] = ra.y;
-        As[buf][lk + 2][lrow] = ra.z; As[buf][lk + 3][lrow] = ra.w;
-        Bs[buf][lk + 0][lrow] = rb.x; Bs[buf][lk + 1][lrow] = rb.y;
-        Bs[buf][lk + 2][lrow] = rb.z; Bs[buf][lk + 3][lrow] = rb.w;
-    };
     const int ty = tid >> 3;   // rows ty*4 .. +3
     const int tx = tid & 7;    // cols tx*4 .. +3
-    float acc[4][4] = {};
-    if (kt0 < nk) {
-        load(kt0);
-        store(0);
-    }
-    __syncthreads();
-    for (int kt = kt0; kt < nk; ++kt) {
-        const int cur = (kt - kt0) & 1;
-        if (kt + 1 < nk) load(kt + 1);
-#pragma unroll
-        for (int k = 0; k < SBK; ++k) {
-            const float4 a = *reinterpret_cast<const float4*>(&As[cur][k][ty * 4]);
-            const float4 b = *reinterpret_cast<const float4*>(&Bs[cur][k][tx * 4]);
-            const float av[4] = {a.x, a.y, a.z, a.w};
-            const float bv[4] = {b.x, b.y, b.z, b.w};
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-#pragma unroll
-                for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+    for (int64_t item = blockIdx.x; item < items; item += gridDim.x) {
+        const int z = (int)(item % S);
+        const int64_t tile = item / S;
+        const int bn = (int)(tile % tiles_n) * SBN;
+        const int bm = (int)(tile / tiles_n) * SBM;
+        const int kt0 = z * steps_per_slice;
+        const int nk = min(nk1 + K2 / SBK, kt0 + steps_per_slice);
+        const int gm = bm + lrow;
+        const int gn = bn + lrow;
+        float4 ra, rb;
+        auto load = [&](int kt) {
+            const float* src;
+            int kk, lda;
+            if (kt < nk1) {
+                src = A1; lda = lda1; kk = kt * SBK;
+            } else {
+                src = A2; lda = lda2; kk = (kt - nk1) * SBK;
+            }
+            ra = gm < M ? __ldg(reinterpret_cast<const float4*>(src + (int64_t)gm * lda + kk + lk))
+                        : make_float4(0.f, 0.f, 0.f, 0.f);
+            rb = gn < N ? __ldg(reinterpret_cast<const float4*>(W + (int64_t)gn * ldw + kt * SBK + lk))
+                        : make_float4(0.f, 0.f, 0.f, 0.f);
+        };
+        auto store = [&](int buf) {
+            As[buf][lk + 0][lrow] = ra.x; As[buf][lk + 1][lrow] = ra.y;
+            As[buf][lk + 2][lrow] = ra.z; As[buf][lk + 3][lrow] = ra.w;
+            Bs[buf][lk + 0][lrow] = rb.x; Bs[buf][lk + 1][lrow] = rb.y;
+            Bs[buf][lk + 2][lrow] = rb.z; Bs[buf][lk + 3][lrow] = rb.w;
+        };
+        float acc[4][4] = {};
+        if (kt0 < nk) {
+            load(kt0);
+            store(0);
         }
-        if (kt + 1 < nk) store(cur ^ 1);
         __syncthreads();
-    }
-    const int col = bn + tx * 4;
-    if (col >= N) return;
-    float* slice = part + (int64_t)blockIdx.z * M * N;
+        for (int kt = kt0; kt < nk; ++kt) {
+            const int cur = (kt - kt0) & 1;
+            if (kt + 1 < nk) load(kt + 1);
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const int row = bm + ty * 4 + i;
-        if (row >= M) continue;
-        *reinterpret_cast<float4*>(slice + (int64_t)row * N + col) =
-            make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+            for (int k = 0; k < SBK; ++k) {
+                const float4 a = *reinterpret_cast<const float4*>(&As[cur][k][ty * 4]);
+                const float4 b = *reinterpret_cast<const float4*>(&Bs[cur][k][tx * 4]);
+                const float av[4] = {a.x, a.y, a.z, a.w};
+                const float bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+            }
+            if (kt + 1 < nk) store(cur ^ 1);
+            __syncthreads();
+        }
+        const int col = bn + tx * 4;
+        if (col < N) {
+            float* slice = part + (int64_t)z * Mc * N;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int row = bm + ty * 4 + i;
+                if (row >= M) continue;
+                *reinterpret_cast<float4*>(slice + (int64_t)row * N + col) =
+                    make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+            }
+        }
     }
 }
 
 // out[m][n] = lrelu(bias[n] + sum over the S slices of part[s][m][n]), four
-// columns per thread, slices added in order.
+// columns per thread, slices added in order.  M is the slice stride; a
+// device count narrows the rows.
 __global__ void __launch_bounds__(256) splitk_finish_kernel(int M, int N, int S,
                                                             const float* __restrict__ part,
                                                             const float* __restrict__ bias,
                                                             float slope, float* __restrict__ Out,
-                                                            int ldo) {
-    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+                                                            int ldo,
+                                                            const unsigned int* __restrict__ m_dev) {
+    const int Mc = M;
+    if (m_dev) M = min(M, (int)*m_dev);
     const int nq = N / 4;
-    if (q >= (int64_t)M * nq) return;
-    const int row = (int)(q / nq);
-    const int col = (int)(q - (int64_t)row * nq) * 4;
-    float4 o = *reinterpret_cast<const float4*>(bias + col);
-    for (int z = 0; z < S; ++z) {
-        const float4 p = __ldg(reinterpret_cast<const float4*>(part + ((int64_t)z * M + row) * N + col));
-        o.x += p.x;
-        o.y += p.y;
-        o.z += p.z;
-        o.w += p.w;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < (int64_t)M * nq;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const int row = (int)(q / nq);
+        const int col = (int)(q - (int64_t)row * nq) * 4;
+        float4 o = *reinterpret_cast<const float4*>(bias + col);
+        for (int z = 0; z < S; ++z) {
+            const float4 p =
+                __ldg(reinterpret_cast<const float4*>(part + ((int64_t)z * Mc + row) * N + col));
+            o.x += p.x;
+            o.y += p.y;
+            o.z += p.z;
+            o.w += p.w;
+        }
+        o.x = o.x >= 0.f ? o.x : slope * o.x;
+        o.y = o.y >= 0.f ? o.y : slope * o.y;
+        o.z = o.z >= 0.f ? o.z : slope * o.z;
+        o.w = o.w >= 0.f ? o.w : slope * o.w;
+        *reinterpret_cast<float4*>(Out + (int64_t)row * ldo + col) = o;
     }
-    o.x = o.x >= 0.f ? o.x : slope * o.x;
-    o.y = o.y >= 0.f ? o.y : slope * o.y;
-    o.z = o.z >= 0.f ? o.z : slope * o.z;
-    o.w = o.w >= 0.f ? o.w : slope * o.w;
-    *reinterpret_cast<float4*>(Out + (int64_t)row * ldo + col) = o;
 }
 
 __device__ __forceinline__ float warp_sum(float v) {
@@ -246,27 +264,10 @@ __device__ __forceinline__ float apply_act(int act, float t) {
 __device__ __forceinline__ float to_f32(float v) { return v; }
 __device__ __forceinline__ float to_f32(__nv_bfloat16 v) { return __bfloat162float(v); }
 
-template <typename InT>
-__global__ void __launch_bounds__(256) last_layer_kernel(
-    int64_t p0, int64_t M, int n_out, const InT* __restrict__ A1, int lda1, int K1,
-    const InT* __restrict__ A2, int lda2, int K2, const float* __restrict__ W, int ldw,
-    const float* __restrict__ bias, Epilogue epi) {
-    const int lane = threadIdx.x & 31;
-    const int64_t lp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (lp >= M) return;  // whole warp exits together
-    float t[4] = {0.f, 0.f, 0.f, 0.f};
-    const InT* a1 = A1 + lp * lda1;
-    const InT* a2 = A2 + lp * lda2;
-    for (int k = lane; k < K1 + K2; k += 32) {
-        const float a = (k < K1) ? to_f32(a1[k]) : to_f32(a2[k - K1]);
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-            if (j < n_out) t[j] = fmaf(a, W[(int64_t)j * ldw + k], t[j]);
-    }
-#pragma unroll
-    for (int j = 0; j < 4; ++j) t[j] = warp_sum(t[j]);
-    if (lane != 0) return;
-    const int64_t p = p0 + lp;
+// The epilogue of one point (lane 0 of its warp): activation and where the
+// result goes.
+__device__ __forceinline__ void last_epilogue(const Epilogue& epi, int64_t p, int n_out,
+                                              const float (&t)[4], const float* __restrict__ bias) {
     if (epi.recheck) {
         // mixed precision: defer occupancies close to the decision threshold
         const float o = apply_act(ACT_SIGMOID, t[0] + bias[0]);
@@ -311,6 +312,35 @@ __global__ void __launch_bounds__(256) last_layer_kernel(
     }
 }
 
+// One warp per point (grid-stride over points; a device count narrows M).
+template <typename InT>
+__global__ void __launch_bounds__(256) last_layer_kernel(
+    int64_t p0, int64_t M, int n_out, const InT* __restrict__ A1, int lda1, int K1,
+    const InT* __restrict__ A2, int lda2, int K2, const float* __restrict__ W, int ldw,
+    const float* __restrict__ bias, Epilogue epi, const unsigned int* __restrict__ m_dev) {
+    const int lane = threadIdx.x & 31;
+    if (m_dev) M = min(M, (int64_t)*m_dev);
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t lp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; lp < M; lp += nwarps) {
+        float t[4] = {0.f, 0.f, 0.f, 0.f};
+        const InT* a1 = A1 + lp * lda1;
+        const InT* a2 = A2 + lp * lda2;
+        for (int k = lane; k < K1 + K2; k += 32) {
+            const float a = (k < K1) ? to_f32(a1[k]) : to_f32(a2[k - K1]);
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (j < n_out) t[j] = fmaf(a, W[(int64_t)j * ldw + k], t[j]);
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) t[j] = warp_sum(t[j]);
+        if (lane == 0) last_epilogue(epi, p0 + lp, n_out, t, bias);
+    }
+}
+
+inline unsigned fixed_or_exact(const unsigned int* m_dev, int64_t exact_blocks) {
+    return (unsigned)(m_dev ? (exact_blocks < 152 * 16 ? exact_blocks : 152 * 16) : exact_blocks);
+}
+
 }  // namespace
 
 int splitk_slices(int K1, int K2) {
@@ -321,22 +351,23 @@ int splitk_slices(int K1, int K2) {
 cudaError_t launch_sgemm_bias_lrelu(int M, int N, const float* A1, int lda1, int K1,
                                     const float* A2, int lda2, int K2, const float* W, int ldw,
                                     const float* bias, float slope, float* Out, int ldo,
-                                    cudaStream_t stream, float* part) {
+                                    cudaStream_t stream, float* part, const unsigned int* m_dev) {
     if (M <= 0) return cudaSuccess;
-    if (M <= kSmallM && part) {
+    if ((M <= kSmallM || m_dev) && part) {
         const int steps = (K1 + K2) / SBK;
         const int S = splitk_slices(K1, K2);
         const int per = (steps + S - 1) / S;
-        dim3 grid((N + SBN - 1) / SBN, (M + SBM - 1) / SBM, S);
-        sgemm_small_kernel<<<grid, 64, 0, stream>>>(M, N, A1, lda1, K1, A2, lda2, K2, W, ldw, part,
-                                                    per);
+        const int64_t items = (int64_t)((N + SBN - 1) / SBN) * ((M + SBM - 1) / SBM) * S;
+        sgemm_small_kernel<<<fixed_or_exact(m_dev, items), 64, 0, stream>>>(
+            M, N, A1, lda1, K1, A2, lda2, K2, W, ldw, part, per, S, m_dev);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         const int64_t nthreads = (int64_t)M * (N / 4);
-        splitk_finish_kernel<<<(unsigned)((nthreads + 255) / 256), 256, 0, stream>>>(
-            M, N, S, part, bias, slope, Out, ldo);
+        splitk_finish_kernel<<<fixed_or_exact(m_dev, (nthreads + 255) / 256), 256, 0, stream>>>(
+            M, N, S, part, bias, slope, Out, ldo, m_dev);
         return cudaGetLastError();
     }
+    if (m_dev) return cudaErrorInvalidValue;   // the big-tile kernel needs a host-known M
     dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM);
     sgemm_bias_lrelu_kernel<<<grid, 256, 0, stream>>>(M, N, A1, lda1, K1, A2, lda2, K2, W, ldw,
                                                       bias, slope, Out, ldo);
@@ -345,24 +376,23 @@ cudaError_t launch_sgemm_bias_lrelu(int M, int N, const float* A1, int lda1, int
 
 cudaError_t launch_last_layer(int64_t p0, int64_t M, int n_out, const float* A1, int lda1, int K1,
                               const float* A2, int lda2, int K2, const float* W, int ldw,
-                              const float* bias, const Epilogue& epi, cudaStream_t stream) {
+                              const float* bias, const Epilogue& epi, cudaStream_t stream,
+                              const unsigned int* m_dev) {
     if (M <= 0) return cudaSuccess;
-    const int64_t threads = M * 32;
-    const int64_t blocks = (threads + 255) / 256;
-    last_layer_kernel<float><<<(unsigned)blocks, 256, 0, stream>>>(p0, M, n_out, A1, lda1, K1, A2,
-                                                                  lda2, K2, W, ldw, bias, epi);
+    const int64_t blocks = (M * 32 + 255) / 256;
+    last_layer_kernel<float><<<fixed_or_exact(m_dev, blocks), 256, 0, stream>>>(
+        p0, M, n_out, A1, lda1, K1, A2, lda2, K2, W, ldw, bias, epi, m_dev);
     return cudaGetLastError();
 }
 
 cudaError_t launch_last_layer_bf16(int64_t p0, int64_t M, int n_out, const __nv_bfloat16* A1,
                                    int lda1, int K1, const __nv_bfloat16* A2, int lda2, int K2,
                                    const float* W, int ldw, const float* bias, const Epilogue& epi,
-                                   cudaStream_t stream) {
+                                   cudaStream_t stream, const unsigned int* m_dev) {
     if (M <= 0) return cudaSuccess;
-    const int64_t threads = M * 32;
-    const int64_t blocks = (threads + 255) / 256;
-    last_layer_kernel<__nv_bfloat16><<<(unsigned)blocks, 256, 0, stream>>>(
-        p0, M, n_out, A1, lda1, K1, A2, lda2, K2, W, ldw, bias, epi);
+    const int64_t blocks = (M * 32 + 255) / 256;
+    last_layer_kernel<__nv_bfloat16><<<fixed_or_exact(m_dev, blocks), 256, 0, stream>>>(
+        p0, M, n_out, A1, lda1, K1, A2, lda2, K2, W, ldw, bias, epi, m_dev);
     return cudaGetLastError();
 }
 

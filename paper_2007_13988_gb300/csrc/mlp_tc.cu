@@ -77,7 +77,8 @@ __global__ void __launch_bounds__(kThreads, 1) tc_linear_kernel(
     const __grid_constant__ CUtensorMap tmA1, const __grid_constant__ CUtensorMap tmA2,
     const __grid_constant__ CUtensorMap tmW, int nk1, int nk2, int M, int N,
     const float* __restrict__ bias, float slope, __nv_bfloat16* __restrict__ out, int ldo,
-    unsigned int* __restrict__ err) {
+    unsigned int* __restrict__ err, const unsigned int* __restrict__ m_dev) {
+    if (m_dev) M = min(M, (int)*m_dev);   // device-resident row count
     constexpr uint32_t A_BYTES = TBM * TBK * 2;
     constexpr uint32_t B_BYTES = BN * TBK * 2;
     constexpr uint32_t TMEM_COLS = 2 * BN;   // two accumulators; 128, 256 or 512
@@ -239,29 +240,46 @@ __global__ void __launch_bounds__(kThreads, 1) tc_linear_kernel(
 
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 
+// Per device: kernel attributes set (index by BN: 64, 128, 256) and SM count.
+bool g_attr_set[3][64] = {};
+int g_n_sm[64] = {};
+
+constexpr int bn_index(int BN) { return BN == 64 ? 0 : (BN == 128 ? 1 : 2); }
+
+template <int BN>
+cudaError_t ensure_attr(int dev) {
+    if (dev >= 0 && dev < 64 && g_attr_set[bn_index(BN)][dev]) return cudaSuccess;
+    const cudaError_t e = cudaFuncSetAttribute(
+        tc_linear_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem_bytes(BN));
+    if (e == cudaSuccess && dev >= 0 && dev < 64) g_attr_set[bn_index(BN)][dev] = true;
+    return e;
+}
+
+cudaError_t sm_count(int dev, int* out) {
+    if (dev >= 0 && dev < 64 && g_n_sm[dev] > 0) {
+        *out = g_n_sm[dev];
+        return cudaSuccess;
+    }
+    const cudaError_t e = cudaDeviceGetAttribute(out, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess && dev >= 0 && dev < 64) g_n_sm[dev] = *out;
+    return e;
+}
+
 template <int BN>
 cudaError_t launch_bn(const TcLayerArgs& a, cudaStream_t s) {
-    static bool attr_set[64] = {};   // per device ordinal
-    const uint32_t smem = tc_smem_bytes(BN);
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= 64 || !attr_set[dev]) {
-        e = cudaFuncSetAttribute(tc_linear_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem);
-        if (e != cudaSuccess) return e;
-        if (dev >= 0 && dev < 64) attr_set[dev] = true;
-    }
-    static int n_sm[64] = {};
-    if (dev >= 0 && dev < 64 && n_sm[dev] == 0) {
-        e = cudaDeviceGetAttribute(&n_sm[dev], cudaDevAttrMultiProcessorCount, dev);
-        if (e != cudaSuccess) return e;
-    }
-    const int sms = (dev >= 0 && dev < 64) ? n_sm[dev] : 148;
+    e = ensure_attr<BN>(dev);
+    if (e != cudaSuccess) return e;
+    int sms = 0;
+    e = sm_count(dev, &sms);
+    if (e != cudaSuccess) return e;
     const long long tiles = (long long)(a.N / BN) * ((a.M + TBM - 1) / TBM);
     const int grid = (int)(tiles < sms ? tiles : sms);
-    tc_linear_kernel<BN><<<grid, kThreads, smem, s>>>(*a.tmA1, *a.tmA2, *a.tmW, a.nk1, a.nk2, a.M, a.N,
-                                                 a.bias, a.slope, a.out, a.ldo, a.err);
+    tc_linear_kernel<BN><<<grid, kThreads, tc_smem_bytes(BN), s>>>(
+        *a.tmA1, *a.tmA2, *a.tmW, a.nk1, a.nk2, a.M, a.N, a.bias, a.slope, a.out, a.ldo, a.err,
+        a.m_dev);
     return cudaGetLastError();
 }
 
@@ -288,6 +306,16 @@ bool tc_encode_2d_bf16(void* map, const void* base, uint64_t cols, uint64_t rows
                                 CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS;
+}
+
+cudaError_t tc_prepare() {
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = ensure_attr<64>(dev);
+    if (e == cudaSuccess) e = ensure_attr<128>(dev);
+    if (e == cudaSuccess) e = ensure_attr<256>(dev);
+    if (e == cudaSuccess) e = sm_count(dev, &sms);
+    return e;
 }
 
 cudaError_t launch_tc_linear(const TcLayerArgs& a, cudaStream_t s) {

@@ -15,7 +15,9 @@ namespace {
 
 constexpr int kMaxLevels = 8;
 constexpr int kMaxFine = 512;
-constexpr int64_t kChunk = 65536;   // points per MLP pass (bounds the activation workspace)
+constexpr int64_t kChunk = 65536;    // points per FP32 MLP pass (bounds its activation workspace)
+constexpr int64_t kChunkTC = 262144; // points per tensor-core MLP pass (a whole 256^3 level)
+constexpr int64_t kRecheckCap = 8192; // graph form: FP32 re-checks per batch
 constexpr int64_t kTinyBatch = 256; // mixed precision: batches this small run in FP32
 
 struct DevLayer {
@@ -50,6 +52,32 @@ struct DevNet {
 };
 
 int round_up(int v, int m) { return (v + m - 1) / m * m; }
+
+// Everything a captured frame graph depends on; a call with the same key
+// relaunches the graph, any difference recaptures it.
+struct FrameKey {
+    const void* occ;
+    const void* col;
+    int oH, oW, oC, cH, cW, cC;
+    float calib[12];
+    int n0, num_levels, precision, max_rounds;
+    float margin;
+    int width, height, cam_precision;
+    float bg[3];
+    float* depth;
+    float* rgb;
+    uint8_t* mask;
+};
+
+// Device-side counters of a graph frame, copied to the host once at its end.
+struct GraphStats {
+    unsigned long long evals[8];
+    unsigned long long cands[8];
+    unsigned long long rechecked[8];
+    unsigned int rounds[8];
+    unsigned int err;
+    unsigned int pad;
+};
 
 // Launch counters (always on) and CUDA-event timing (when enabled) per
 // kernel class.
@@ -159,6 +187,17 @@ struct pifu_ctx {
     int vol_bin = 0;
     pifu_volume stats{};
     Profiler prof;
+    // graph form (pifu_frame)
+    bool g_valid = false;
+    FrameKey gkey{};
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    cudaStream_t cap_stream = nullptr;    // capture of the frame
+    cudaStream_t cap_stream2 = nullptr;   // capture of the loop bodies
+    GraphStats* d_gstats = nullptr;
+    GraphStats* h_gstats = nullptr;       // pinned
+    int64_t g_launches_fixed = 0;         // kernel launches outside the loops
+    int64_t g_launches_body[8] = {};      // kernel launches per loop iteration
 };
 
 namespace {
@@ -304,14 +343,14 @@ void free_net(DevNet& net) {
 int ensure_mlp_ws(pifu_ctx* ctx) {
     int64_t need_x = 0, need_h = 0;
     for (const DevNet& n : ctx->net) {
-        need_x = std::max<int64_t>(need_x, kChunk * n.ldx);
-        need_h = std::max<int64_t>(need_h, kChunk * std::max(n.max_hidden, 8));
+        need_x = std::max<int64_t>(need_x, n.ldx);
+        need_h = std::max<int64_t>(need_h, std::max(n.max_hidden, 8));
     }
-    if (need_x > ctx->X_cap) {
+    if (need_x > ctx->X_cap) {   // per-point widths; rows are kChunk (FP32) / kChunkTC (BF16)
         dev_free(ctx->X);
         dev_free(ctx->Xb);
-        CK(dev_alloc(&ctx->X, need_x));
-        CK(dev_alloc(&ctx->Xb, need_x));
+        CK(dev_alloc(&ctx->X, need_x * kChunk));
+        CK(dev_alloc(&ctx->Xb, need_x * kChunkTC));
         ctx->X_cap = need_x;
     }
     if (need_h > ctx->H_cap) {
@@ -319,16 +358,19 @@ int ensure_mlp_ws(pifu_ctx* ctx) {
         dev_free(ctx->HB);
         dev_free(ctx->Hb[0]);
         dev_free(ctx->Hb[1]);
-        CK(dev_alloc(&ctx->HA, need_h));
-        CK(dev_alloc(&ctx->HB, need_h));
-        CK(dev_alloc(&ctx->Hb[0], need_h));
-        CK(dev_alloc(&ctx->Hb[1], need_h));
+        CK(dev_alloc(&ctx->HA, need_h * kChunk));
+        CK(dev_alloc(&ctx->HB, need_h * kChunk));
+        CK(dev_alloc(&ctx->Hb[0], need_h * kChunkTC));
+        CK(dev_alloc(&ctx->Hb[1], need_h * kChunkTC));
         ctx->H_cap = need_h;
     }
+    // split-K partial sums: host-sized batches up to kSplitMaxM, device-sized
+    // re-check batches up to kRecheckCap
     int64_t need_p = 0;
     for (const DevNet& n : ctx->net)
         for (const DevLayer& L : n.layers)
-            need_p = std::max<int64_t>(need_p, (int64_t)splitk_slices(L.K1, L.K2) * kSplitMaxM *
+            need_p = std::max<int64_t>(need_p, (int64_t)splitk_slices(L.K1, L.K2) *
+                                                   std::max<int64_t>(kSplitMaxM, kRecheckCap) *
                                                    L.n_out);
     if (need_p > ctx->part_cap) {
         dev_free(ctx->part);
@@ -348,7 +390,7 @@ int build_tc(pifu_ctx* ctx, const HostNet& hn, DevNet& net) {
     for (int l = 0; l + 1 < L; ++l)
         if (net.layers[l].n_out % 64 != 0) return PIFU_OK;
     const int k2pad = round_up(net.d_in, 64);
-    if (!tc_encode_2d_bf16(&net.tmX, ctx->Xb, (uint64_t)net.d_in, (uint64_t)kChunk,
+    if (!tc_encode_2d_bf16(&net.tmX, ctx->Xb, (uint64_t)net.d_in, (uint64_t)kChunkTC,
                            (uint64_t)net.ldx * 2, 64, 128))
         return PIFU_ERR_CUDA;
     for (int l = 0; l + 1 < L; ++l) {
@@ -376,7 +418,7 @@ int build_tc(pifu_ctx* ctx, const HostNet& hn, DevNet& net) {
             return PIFU_ERR_CUDA;
         if (l > 0) {
             const __nv_bfloat16* src = ctx->Hb[(l - 1) % 2];
-            if (!tc_encode_2d_bf16(&T.tmA1, src, (uint64_t)Ly.K1, (uint64_t)kChunk,
+            if (!tc_encode_2d_bf16(&T.tmA1, src, (uint64_t)Ly.K1, (uint64_t)kChunkTC,
                                    (uint64_t)Ly.K1 * 2, 64, 128))
                 return PIFU_ERR_CUDA;
         }
@@ -457,13 +499,19 @@ bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
 
 // ---- the MLP over a point batch ---------------------------------------------------
 
-int run_mlp_tc(pifu_ctx* ctx, const DevNet& net, const PointSrc& src, int64_t m, const Map& map0,
-               const Map& map1, const Calib& calib, const Epilogue& epi, cudaStream_t s) {
+// m_dev (optional): the batch size is device-resident, at most m <= kChunkTC
+// (graph form); m is then only the capacity the launches are sized for.
+int run_mlp_tc(pifu_ctx* ctx, const DevNet& net, const PointSrc& src_in, int64_t m,
+               const Map& map0, const Map& map1, const Calib& calib, const Epilogue& epi,
+               cudaStream_t s, const unsigned int* m_dev = nullptr) {
     if (!net.tc_ok) return PIFU_ERR_UNSUPPORTED;
+    if (m_dev && m > kChunkTC) return PIFU_ERR_ARG;
+    PointSrc src = src_in;
+    src.count = m_dev;
     const int L = (int)net.layers.size();
     Profiler& pr = ctx->prof;
-    for (int64_t p0 = 0; p0 < m; p0 += kChunk) {
-        const int64_t mc = std::min<int64_t>(kChunk, m - p0);
+    for (int64_t p0 = 0; p0 < m; p0 += kChunkTC) {
+        const int64_t mc = std::min<int64_t>(kChunkTC, m - p0);
         cudaEvent_t ev = pr.begin(s);
         CK(launch_gather_bf16(src, p0, mc, calib, map0, map1, ctx->Xb, net.ldx, s));
         pr.end(PIFU_K_GATHER, ev, s, 0.0,
@@ -485,6 +533,7 @@ int run_mlp_tc(pifu_ctx* ctx, const DevNet& net, const PointSrc& src, int64_t m,
             a.out = ctx->Hb[l % 2];
             a.ldo = Ly.n_out;
             a.err = ctx->d_count + 1;
+            a.m_dev = m_dev;
             ev = pr.begin(s);
             CK(launch_tc_linear(a, s));
             pr.end(PIFU_K_MLP_HIDDEN, ev, s, 2.0 * mc * Ly.fan_in * Ly.n_out,
@@ -495,18 +544,22 @@ int run_mlp_tc(pifu_ctx* ctx, const DevNet& net, const PointSrc& src, int64_t m,
         const int hw = L > 1 ? net.layers[L - 2].n_out : 0;
         ev = pr.begin(s);
         CK(launch_last_layer_bf16(p0, mc, Ll.n_out, h, hw, Ll.K1, ctx->Xb, net.ldx, Ll.K2, Ll.W,
-                                  Ll.ldw, Ll.b, epi, s));
+                                  Ll.ldw, Ll.b, epi, s, m_dev));
         pr.end(PIFU_K_MLP_LAST, ev, s, 2.0 * mc * Ll.fan_in * Ll.n_out,
                2.0 * (double)mc * (Ll.fan_in + Ll.n_out));
     }
     return PIFU_OK;
 }
 
-int run_mlp(pifu_ctx* ctx, const DevNet& net, const PointSrc& src, int64_t m, const Map& map0,
+int run_mlp(pifu_ctx* ctx, const DevNet& net, const PointSrc& src_in, int64_t m, const Map& map0,
             const Map& map1, const Calib& calib, const Epilogue& epi, cudaStream_t s,
-            int precision = PIFU_PREC_FP32) {
+            int precision = PIFU_PREC_FP32, const unsigned int* m_dev = nullptr) {
     if (precision == PIFU_PREC_BF16)
-        return run_mlp_tc(ctx, net, src, m, map0, map1, calib, epi, s);
+        return run_mlp_tc(ctx, net, src_in, m, map0, map1, calib, epi, s, m_dev);
+    // a device-resident batch size uses the split-K kernels, sized for m <= kRecheckCap
+    if (m_dev && m > kRecheckCap) return PIFU_ERR_ARG;
+    PointSrc src = src_in;
+    src.count = m_dev;
     const int L = (int)net.layers.size();
     Profiler& pr = ctx->prof;
     for (int64_t p0 = 0; p0 < m; p0 += kChunk) {
@@ -523,7 +576,8 @@ int run_mlp(pifu_ctx* ctx, const DevNet& net, const PointSrc& src, int64_t m, co
             float* out = (l % 2 == 0) ? ctx->HA : ctx->HB;
             ev = pr.begin(s);
             CK(launch_sgemm_bias_lrelu((int)mc, Ly.n_out, h, hw, Ly.K1, ctx->X, net.ldx, Ly.K2, Ly.W,
-                                       Ly.ldw, Ly.b, net.slope, out, Ly.n_out, s, ctx->part));
+                                       Ly.ldw, Ly.b, net.slope, out, Ly.n_out, s, ctx->part,
+                                       m_dev));
             pr.end(PIFU_K_MLP_F32, ev, s, 2.0 * mc * Ly.fan_in * Ly.n_out,
                    4.0 * ((double)mc * (Ly.fan_in + Ly.n_out) + (double)Ly.n_out * (Ly.fan_in + 1)));
             h = out;
@@ -532,7 +586,7 @@ int run_mlp(pifu_ctx* ctx, const DevNet& net, const PointSrc& src, int64_t m, co
         const DevLayer& Ll = net.layers[L - 1];
         ev = pr.begin(s);
         CK(launch_last_layer(p0, mc, Ll.n_out, h, hw, Ll.K1, ctx->X, net.ldx, Ll.K2, Ll.W, Ll.ldw,
-                             Ll.b, epi, s));
+                             Ll.b, epi, s, m_dev));
         pr.end(PIFU_K_MLP_LAST, ev, s, 2.0 * mc * Ll.fan_in * Ll.n_out,
                4.0 * (double)mc * (Ll.fan_in + Ll.n_out));
     }
@@ -588,6 +642,12 @@ int read_recheck(pifu_ctx* ctx, cudaStream_t s, unsigned int* out) {
     return PIFU_OK;
 }
 
+int decode_err(unsigned int e) {
+    if (e & kErrCapacity) return PIFU_ERR_CAPACITY;
+    if (e & kErrNotConverged) return PIFU_ERR_NOT_CONVERGED;
+    return PIFU_ERR_TIMEOUT;
+}
+
 // Reads the list length and the device error word (set by a bounded wait
 // that gave up); a set error word is cleared and reported as a timeout.
 int read_count(pifu_ctx* ctx, cudaStream_t s, unsigned int* out) {
@@ -596,8 +656,9 @@ int read_count(pifu_ctx* ctx, cudaStream_t s, unsigned int* out) {
     CK(cudaStreamSynchronize(s));
     *out = ctx->h_count[0];
     if (ctx->h_count[1] != 0u) {
+        const unsigned int e = ctx->h_count[1];
         CK(cudaMemsetAsync(ctx->d_count + 1, 0, sizeof(unsigned int), s));
-        return PIFU_ERR_TIMEOUT;
+        return decode_err(e);
     }
     return PIFU_OK;
 }
@@ -618,6 +679,7 @@ const char* pifu_status_string(int status) {
         case PIFU_ERR_TIMEOUT: return "bounded device wait timed out";
         case PIFU_ERR_STATE: return "call order violated";
         case PIFU_ERR_UNSUPPORTED: return "unsupported configuration";
+        case PIFU_ERR_CAPACITY: return "a device-side count exceeded a fixed capacity of the graph form";
         default: return "unknown status";
     }
 }

@@ -11,6 +11,11 @@ namespace pifu {
 
 constexpr float kHalf = 0.5f;
 
+// Bits of the context's device error word.
+constexpr unsigned int kErrTimeout = 1u;       // a bounded device wait gave up
+constexpr unsigned int kErrNotConverged = 2u;  // graph form: conflict loop over max_rounds
+constexpr unsigned int kErrCapacity = 4u;      // graph form: a device count over its capacity
+
 // 3x4 calibration passed by value to kernels.
 struct Calib {
     float c[12];
@@ -37,6 +42,9 @@ struct PointSrc {
     const int* list;    // PTS_LIST
     int64_t base;       // PTS_DENSE first node index
     int N;              // grid modes: cells per axis
+    // Device-resident batch size: when set, a launch sized for m points
+    // processes min(*count, m) of them (graph form, no host read of counts).
+    const unsigned int* count;
 };
 
 // What the last MLP layer does with its output.
@@ -93,21 +101,25 @@ cudaError_t launch_gather_bf16(const PointSrc& src, int64_t p0, int64_t m, const
 // splitk_slices(K1, K2) * M * N floats (null: always the big-tile kernel).
 constexpr int kSplitMaxM = 2048;
 int splitk_slices(int K1, int K2);
+// m_dev (optional): device-resident row count, at most M; then M is only
+// the capacity (the slice stride of part) and the split-K kernels are used.
 cudaError_t launch_sgemm_bias_lrelu(int M, int N, const float* A1, int lda1, int K1,
                                     const float* A2, int lda2, int K2, const float* W, int ldw,
                                     const float* bias, float slope, float* Out, int ldo,
-                                    cudaStream_t stream, float* part);
+                                    cudaStream_t stream, float* part,
+                                    const unsigned int* m_dev = nullptr);
 
 // Last layer (n_out <= 4 outputs) plus activation and epilogue, one warp per point.
 cudaError_t launch_last_layer(int64_t p0, int64_t M, int n_out, const float* A1, int lda1, int K1,
                               const float* A2, int lda2, int K2, const float* W, int ldw,
-                              const float* bias, const Epilogue& epi, cudaStream_t stream);
+                              const float* bias, const Epilogue& epi, cudaStream_t stream,
+                              const unsigned int* m_dev = nullptr);
 
 // Last layer reading BF16 activations (A1 = h, A2 = x rows), FP32 weights.
 cudaError_t launch_last_layer_bf16(int64_t p0, int64_t M, int n_out, const __nv_bfloat16* A1,
                                    int lda1, int K1, const __nv_bfloat16* A2, int lda2, int K2,
                                    const float* W, int ldw, const float* bias, const Epilogue& epi,
-                                   cudaStream_t stream);
+                                   cudaStream_t stream, const unsigned int* m_dev = nullptr);
 
 // --- mlp_tc.cu -------------------------------------------------------------
 // One hidden layer on the tensor cores (tcgen05, BF16 in, FP32 accumulate):
@@ -125,8 +137,12 @@ struct TcLayerArgs {
     __nv_bfloat16* out;
     int ldo;
     unsigned int* err;
+    const unsigned int* m_dev;   // optional device-resident row count (<= M)
 };
 cudaError_t launch_tc_linear(const TcLayerArgs& a, cudaStream_t stream);
+// Set the tensor-core kernels' attributes on the current device (before a
+// stream capture: launches inside a capture then make no attribute calls).
+cudaError_t tc_prepare();
 
 // Encode a 2-D BF16 tensor map (128-byte swizzle, zero fill out of bounds).
 bool tc_encode_2d_bf16(void* map, const void* base, uint64_t cols, uint64_t rows,
@@ -151,6 +167,15 @@ cudaError_t launch_dense_setup(int N, uint32_t* cand, uint32_t* tent, uint32_t* 
 // append the node indices of sel to list at *count.
 cudaError_t launch_dilate_select(const uint32_t* src, uint32_t* eval, uint32_t* clear, int N,
                                  int* list, unsigned int* count, cudaStream_t stream);
+
+// Graph form: set the conditional handle to (*count > 0) within capacity
+// and round limits (count_round: this decision starts a conflict round).
+cudaError_t launch_loop_control(cudaGraphConditionalHandle h, const unsigned int* count,
+                                unsigned int cap, unsigned int* rounds, int count_round,
+                                int max_rounds, unsigned int* err, cudaStream_t stream);
+// *dst += *src; capacity error bit if *src > cap.
+cudaError_t launch_accumulate(unsigned long long* dst, const unsigned int* src, unsigned int cap,
+                              unsigned int* err, cudaStream_t stream);
 
 // Population count of a bitset (for statistics) added into *count.
 cudaError_t launch_popcount(const uint32_t* bits, int64_t words, unsigned long long* count,
