@@ -177,6 +177,26 @@ int pifu_render(pifu_ctx* ctx, const pifu_camera* cam, const pifu_fmap* occ_map,
                 const pifu_fmap* col_map, const float calib[12], void* stream,
                 float* depth_dev, float* rgb_dev, uint8_t* mask_dev);
 
+/* One frame -- pifu_localize followed by pifu_render -- as a CUDA graph
+ * (Sec. 3.2: localization, then mesh-free render; one launch per frame).
+ * The first call with a given argument set (map pointers and shapes,
+ * calibration, levels, camera, output pointers) captures the graph; later
+ * calls with the same set relaunch it.  Batch sizes stay on the device: the
+ * MLP launches read them from the counters the selection kernels write, and
+ * each level's conflict loop is a conditional WHILE node.  The stream is
+ * synchronised once, at the end, to read the counters into *out.
+ * Tensor-core forms only (levels->precision BF16 or MIXED; the colour MLP
+ * runs in BF16).  Fixed capacities: 262,144 points per evaluation batch and
+ * pixels per render, 8,192 FP32 re-checks per batch; a frame that exceeds one
+ * returns PIFU_ERR_CAPACITY (its outputs are then invalid and the
+ * host-driven pifu_localize + pifu_render handle it).  Other errors as in
+ * pifu_localize / pifu_render.  The last volume is then available to
+ * pifu_render and pifu_sync_stats as after pifu_localize. */
+int pifu_frame(pifu_ctx* ctx, const pifu_fmap* occ_map, const pifu_fmap* col_map,
+               const float calib[12], const pifu_levels* levels, const pifu_camera* cam,
+               void* stream, float* depth_dev, float* rgb_dev, uint8_t* mask_dev,
+               pifu_volume* out);
+
 /* Copy the counters of the last pifu_localize into *out (host). */
 int pifu_sync_stats(pifu_ctx* ctx, pifu_volume* out);
 

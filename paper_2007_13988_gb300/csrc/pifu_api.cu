@@ -665,6 +665,229 @@ int read_count(pifu_ctx* ctx, cudaStream_t s, unsigned int* out) {
 
 }  // namespace
 
+namespace {
+
+// ---- graph form: one CUDA graph per frame ------------------------------------
+//
+// pifu_frame captures localization + render once per argument set and then
+// relaunches the graph.  Batch sizes never come back to the host: the MLP
+// launches are sized for a capacity and read the true size from the
+// device counter the previous kernel wrote, and each level's conflict loop is
+// a conditional WHILE node whose body ends with a kernel that sets the
+// condition from the new frontier's size.  The host synchronises once, at the
+// end of the frame, to read the counters and the error word.
+
+// One evaluation batch in the graph: BF16 on the tensor cores, and for MIXED
+// the FP32 re-evaluation of the queued near-0.5 occupancies (device-sized).
+int g_eval(pifu_ctx* ctx, const DevNet& net, const PointSrc& src, int64_t cap,
+           const unsigned int* m_dev, const Map& map, const Calib& cal, const Epilogue& epi,
+           int prec, float margin, unsigned long long* rechecked, cudaStream_t s) {
+    if (prec == PIFU_PREC_BF16) return run_mlp_tc(ctx, net, src, cap, map, Map{}, cal, epi, s, m_dev);
+    CK(cudaMemsetAsync(ctx->d_recheck, 0, sizeof(unsigned int), s));
+    Epilogue e1 = epi;
+    e1.recheck = ctx->recheck;
+    e1.recheck_count = ctx->d_recheck;
+    e1.margin = margin;
+    int st = run_mlp_tc(ctx, net, src, cap, map, Map{}, cal, e1, s, m_dev);
+    if (st != PIFU_OK) return st;
+    PointSrc s2{PTS_LIST, nullptr, ctx->recheck, 0, src.N, nullptr};
+    Epilogue e2 = epi;
+    e2.list = ctx->recheck;
+    st = run_mlp(ctx, net, s2, kRecheckCap, map, Map{}, cal, e2, s, PIFU_PREC_FP32, ctx->d_recheck);
+    if (st != PIFU_OK) return st;
+    CK(launch_accumulate(rechecked, ctx->d_recheck, (unsigned)kRecheckCap, ctx->d_count + 1, s));
+    return PIFU_OK;
+}
+
+// Appends a WHILE node to the capture of `s` (after everything captured so
+// far) and returns its body graph; the condition is set by the kernel that
+// was captured last (launch_loop_control).
+int g_add_while(pifu_ctx* ctx, cudaStream_t s, cudaGraphConditionalHandle h, cudaGraph_t* body) {
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t cg = nullptr;
+    const cudaGraphNode_t* deps = nullptr;
+    const cudaGraphEdgeData* edata = nullptr;
+    size_t ndeps = 0;
+    CK(cudaStreamGetCaptureInfo(s, &cs, nullptr, &cg, &deps, &edata, &ndeps));
+    if (cs != cudaStreamCaptureStatusActive) return PIFU_ERR_STATE;
+    cudaGraphNodeParams np{};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = h;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    CK(cudaGraphAddNode(&node, cg, deps, edata, ndeps, &np));
+    *body = np.conditional.phGraph_out[0];
+    CK(cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+    return PIFU_OK;
+}
+
+int64_t launches_now(const pifu_ctx* ctx) {
+    int64_t n = 0;
+    for (const auto& k : ctx->prof.k) n += k.launches;
+    return n;
+}
+
+// The frame, captured on ctx->cap_stream (loop bodies on cap_stream2).
+int g_enqueue_frame(pifu_ctx* ctx, const FrameKey& k, const Map& occ, const Map& col,
+                    const Calib& cal) {
+    cudaStream_t s = ctx->cap_stream;
+    cudaStream_t sb = ctx->cap_stream2;
+    GraphStats* gs = ctx->d_gstats;
+    unsigned int* err = ctx->d_count + 1;
+    const DevNet& net = ctx->net[0];
+    int st = PIFU_OK;
+    CK(cudaMemsetAsync(gs, 0, sizeof(GraphStats), s));
+    CK(cudaMemsetAsync(err, 0, sizeof(unsigned int), s));
+    // level 0: every node
+    int N = k.n0, cur = 0;
+    CK(launch_dense_setup(N, ctx->cand, ctx->tent, ctx->bin[cur], ctx->eval, ctx->conf[0], s));
+    {
+        const int64_t nodes = (int64_t)(N + 1) * (N + 1) * (N + 1);
+        PointSrc src{PTS_DENSE, nullptr, nullptr, 0, N, nullptr};
+        Epilogue epi{};
+        epi.mode = EPI_LEVEL;
+        epi.lv = LevelBits{ctx->values, ctx->tent, ctx->bin[cur], ctx->conf[0], N, row_words_of(N), 1};
+        st = g_eval(ctx, net, src, nodes, nullptr, occ, cal, epi, k.precision, k.margin,
+                    &gs->rechecked[0], s);
+        if (st != PIFU_OK) return st;
+    }
+    for (int l = 1; l < k.num_levels; ++l) {
+        const int prev = cur;
+        cur ^= 1;
+        N *= 2;
+        CK(launch_classify(ctx->bin[prev], N, ctx->cand, ctx->tent, ctx->bin[cur], ctx->eval,
+                           ctx->conf[0], s));
+        CK(launch_popcount(ctx->cand, words_of(N), &gs->cands[l], s));
+        CK(cudaMemsetAsync(ctx->d_count, 0, sizeof(unsigned int), s));
+        CK(launch_dilate_select(ctx->cand, ctx->eval, nullptr, N, ctx->list, ctx->d_count, s));
+        cudaStreamCaptureStatus cs;
+        cudaGraph_t cg = nullptr;
+        CK(cudaStreamGetCaptureInfo(s, &cs, nullptr, &cg, nullptr, nullptr, nullptr));
+        cudaGraphConditionalHandle h;
+        CK(cudaGraphConditionalHandleCreate(&h, cg, 0, 0));
+        CK(launch_loop_control(h, ctx->d_count, (unsigned)kChunkTC, &gs->rounds[l], 0, k.max_rounds,
+                               err, s));
+        cudaGraph_t body = nullptr;
+        st = g_add_while(ctx, s, h, &body);
+        if (st != PIFU_OK) return st;
+        // loop body: evaluate the list, then the unevaluated ring of its conflicts
+        const int64_t before = launches_now(ctx);
+        CK(cudaStreamBeginCaptureToGraph(sb, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+        {
+            const int rw = row_words_of(N);
+            PointSrc src{PTS_LIST, nullptr, ctx->list, 0, N, nullptr};
+            Epilogue epi{};
+            epi.mode = EPI_LEVEL;
+            epi.list = ctx->list;
+            epi.lv = LevelBits{ctx->values, ctx->tent, ctx->bin[cur], ctx->conf[0], N, rw, 0};
+            st = launch_accumulate(&gs->evals[l], ctx->d_count, (unsigned)kChunkTC, err, sb) == cudaSuccess
+                     ? PIFU_OK : PIFU_ERR_CUDA;
+            if (st == PIFU_OK)
+                st = g_eval(ctx, net, src, kChunkTC, ctx->d_count, occ, cal, epi, k.precision,
+                            k.margin, &gs->rechecked[l], sb);
+            if (st == PIFU_OK && cudaMemsetAsync(ctx->d_count, 0, sizeof(unsigned int), sb) != cudaSuccess)
+                st = PIFU_ERR_CUDA;
+            if (st == PIFU_OK && launch_dilate_select(ctx->conf[0], ctx->eval, nullptr, N, ctx->list,
+                                                      ctx->d_count, sb) != cudaSuccess)
+                st = PIFU_ERR_CUDA;
+            if (st == PIFU_OK &&
+                cudaMemsetAsync(ctx->conf[0], 0, (size_t)words_of(N) * 4, sb) != cudaSuccess)
+                st = PIFU_ERR_CUDA;
+            if (st == PIFU_OK && launch_loop_control(h, ctx->d_count, (unsigned)kChunkTC,
+                                                     &gs->rounds[l], 1, k.max_rounds, err,
+                                                     sb) != cudaSuccess)
+                st = PIFU_ERR_CUDA;
+        }
+        cudaGraph_t body_out = nullptr;
+        const cudaError_t ee = cudaStreamEndCapture(sb, &body_out);
+        if (st != PIFU_OK) return st;
+        if (ee != cudaSuccess) return fail_cuda(ctx, ee);
+        ctx->g_launches_body[l] = launches_now(ctx) - before;
+    }
+    // render: first-occupied depth per column, rays, colour at the hits
+    RenderArgs a{};
+    a.width = k.width;
+    a.height = k.height;
+    a.N = N;
+    a.row_words = row_words_of(N);
+    a.values = ctx->values;
+    a.eval = ctx->eval;
+    a.bin = ctx->bin[cur];
+    for (int c = 0; c < 3; ++c) a.bg[c] = k.bg[c];
+    a.depth = k.depth;
+    a.rgb = k.rgb;
+    a.mask = k.mask;
+    a.hit_xyz = ctx->hit_xyz;
+    a.hit_pix = ctx->hit_pix;
+    a.hit_count = ctx->d_count;
+    a.top = ctx->col_top;
+    CK(cudaMemsetAsync(ctx->d_count, 0, sizeof(unsigned int), s));
+    CK(launch_render_rays(a, s));
+    ctx->prof.k[PIFU_K_RENDER].launches += 2;
+    if (k.rgb) {
+        const int64_t npix = (int64_t)k.width * k.height;
+        PointSrc src{PTS_XYZ, ctx->hit_xyz, nullptr, 0, 0, nullptr};
+        Epilogue epi{};
+        epi.mode = EPI_PIXELS;
+        epi.act = ACT_TANH01;
+        epi.out = k.rgb;
+        epi.pix = ctx->hit_pix;
+        const Map m0 = col.C > 0 ? col : occ;
+        const Map m1 = col.C > 0 ? occ : Map{};
+        st = run_mlp_tc(ctx, ctx->net[1], src, npix, m0, m1, cal, epi, s, ctx->d_count);
+        if (st != PIFU_OK) return st;
+    }
+    CK(cudaMemcpyAsync(&gs->err, err, sizeof(unsigned int), cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(ctx->h_gstats, gs, sizeof(GraphStats), cudaMemcpyDeviceToHost, s));
+    return PIFU_OK;
+}
+
+void g_destroy(pifu_ctx* ctx) {
+    if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
+    if (ctx->graph) cudaGraphDestroy(ctx->graph);
+    ctx->gexec = nullptr;
+    ctx->graph = nullptr;
+    ctx->g_valid = false;
+}
+
+int g_build(pifu_ctx* ctx, const FrameKey& k, const Map& occ, const Map& col, const Calib& cal) {
+    g_destroy(ctx);
+    if (!ctx->cap_stream) CK(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
+    if (!ctx->cap_stream2) CK(cudaStreamCreateWithFlags(&ctx->cap_stream2, cudaStreamNonBlocking));
+    if (!ctx->d_gstats) CK(dev_alloc(&ctx->d_gstats, 1));
+    if (!ctx->h_gstats) CK(cudaHostAlloc(&ctx->h_gstats, sizeof(GraphStats), cudaHostAllocDefault));
+    CK(tc_prepare());
+    const bool prof_on = ctx->prof.on;
+    ctx->prof.on = false;   // no timing events inside a graph
+    const int64_t before = launches_now(ctx);
+    CK(cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
+    int st = g_enqueue_frame(ctx, k, occ, col, cal);
+    cudaGraph_t g = nullptr;
+    const cudaError_t ee = cudaStreamEndCapture(ctx->cap_stream, &g);
+    ctx->prof.on = prof_on;
+    int64_t body = 0;
+    for (int l = 1; l < k.num_levels; ++l) body += ctx->g_launches_body[l];
+    ctx->g_launches_fixed = launches_now(ctx) - before - body;
+    for (auto& x : ctx->prof.k) x.launches = 0;   // capture is not execution
+    if (st != PIFU_OK) {
+        if (g) cudaGraphDestroy(g);
+        return st;
+    }
+    if (ee != cudaSuccess) return fail_cuda(ctx, ee);
+    ctx->graph = g;
+    const cudaError_t ie = cudaGraphInstantiate(&ctx->gexec, g, 0);
+    if (ie != cudaSuccess) {
+        g_destroy(ctx);
+        return fail_cuda(ctx, ie);
+    }
+    ctx->gkey = k;
+    ctx->g_valid = true;
+    return PIFU_OK;
+}
+
+}  // namespace
+
 // ============================================================================
 extern "C" {
 
@@ -761,6 +984,11 @@ void pifu_destroy(pifu_ctx* ctx) {
     dev_free(ctx->hit_xyz);
     dev_free(ctx->hit_pix);
     dev_free(ctx->col_top);
+    g_destroy(ctx);
+    if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+    if (ctx->cap_stream2) cudaStreamDestroy(ctx->cap_stream2);
+    dev_free(ctx->d_gstats);
+    if (ctx->h_gstats) cudaFreeHost(ctx->h_gstats);
     if (ctx->h_count) cudaFreeHost(ctx->h_count);
     if (ctx->h_pop) cudaFreeHost(ctx->h_pop);
     delete ctx;
@@ -1028,6 +1256,99 @@ int pifu_render(pifu_ctx* ctx, const pifu_camera* cam, const pifu_fmap* occ_map,
     const Map m0 = col_map ? to_map(col_map) : to_map(occ_map);
     const Map m1 = col_map ? to_map(occ_map) : Map{};
     return run_mlp(ctx, ctx->net[1], src, n, m0, m1, to_calib(calib), epi, s, cam->precision);
+}
+
+int pifu_frame(pifu_ctx* ctx, const pifu_fmap* occ_map, const pifu_fmap* col_map,
+               const float calib[12], const pifu_levels* lv, const pifu_camera* cam, void* stream,
+               float* depth_dev, float* rgb_dev, uint8_t* mask_dev, pifu_volume* out) {
+    if (!ctx || !calib || !lv || !cam || !map_ok(occ_map) || (col_map && !map_ok(col_map)))
+        return PIFU_ERR_ARG;
+    if (!is_pow2(lv->n0) || lv->n0 < 2 || lv->num_levels < 1 || lv->num_levels > kMaxLevels)
+        return PIFU_ERR_ARG;
+    const int64_t n_fine = (int64_t)lv->n0 << (lv->num_levels - 1);
+    if (n_fine > kMaxFine) return PIFU_ERR_ARG;
+    if (cam->width < 1 || cam->height < 1) return PIFU_ERR_ARG;
+    if ((int64_t)cam->width * cam->height > kChunkTC) return PIFU_ERR_CAPACITY;
+    if (lv->precision != PIFU_PREC_BF16 && lv->precision != PIFU_PREC_MIXED) return PIFU_ERR_UNSUPPORTED;
+    if (lv->precision == PIFU_PREC_MIXED && !(lv->margin >= 0.f && lv->margin <= 0.5f))
+        return PIFU_ERR_ARG;
+    if (occ_map->dtype != PIFU_F32 || (col_map && col_map->dtype != PIFU_F32)) return PIFU_ERR_UNSUPPORTED;
+    if (ctx->net[0].d_in != occ_map->C + 1) return PIFU_ERR_ARG;
+    if (!ctx->net[0].tc_ok) return PIFU_ERR_UNSUPPORTED;
+    if (rgb_dev) {
+        const int c_t = col_map ? col_map->C : 0;
+        if (ctx->net[1].d_in != c_t + occ_map->C + 1) return PIFU_ERR_ARG;
+        if (!ctx->net[1].tc_ok) return PIFU_ERR_UNSUPPORTED;
+    }
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return PIFU_ERR_CUDA;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    FrameKey k;
+    std::memset(&k, 0, sizeof(k));   // padding too: keys are compared bytewise
+    k.occ = occ_map->data;
+    k.oH = occ_map->H;
+    k.oW = occ_map->W;
+    k.oC = occ_map->C;
+    if (col_map) {
+        k.col = col_map->data;
+        k.cH = col_map->H;
+        k.cW = col_map->W;
+        k.cC = col_map->C;
+    }
+    std::memcpy(k.calib, calib, sizeof(k.calib));
+    k.n0 = lv->n0;
+    k.num_levels = lv->num_levels;
+    k.precision = lv->precision;
+    k.max_rounds = lv->max_rounds > 0 ? lv->max_rounds : 4096;
+    k.margin = lv->precision == PIFU_PREC_MIXED ? lv->margin : 0.f;
+    k.width = cam->width;
+    k.height = cam->height;
+    k.cam_precision = cam->precision;
+    for (int c = 0; c < 3; ++c) k.bg[c] = cam->background[c];
+    k.depth = depth_dev;
+    k.rgb = rgb_dev;
+    k.mask = mask_dev;
+    int st = ensure_level_ws(ctx, (int)n_fine);
+    if (st != PIFU_OK) return st;
+    st = ensure_hit_ws(ctx, (int64_t)cam->width * cam->height);
+    if (st != PIFU_OK) return st;
+    if (!ctx->g_valid || std::memcmp(&k, &ctx->gkey, sizeof(k)) != 0) {
+        st = g_build(ctx, k, to_map(occ_map), to_map(col_map), to_calib(calib));
+        if (st != PIFU_OK) return st;
+    }
+    ctx->have_volume = false;
+    CK(cudaGraphLaunch(ctx->gexec, s));
+    CK(cudaStreamSynchronize(s));
+    const GraphStats& gs = *ctx->h_gstats;
+    pifu_volume vs{};
+    vs.num_levels = lv->num_levels;
+    vs.evals_per_level[0] = (int64_t)(lv->n0 + 1) * (lv->n0 + 1) * (lv->n0 + 1);
+    vs.n_eval = vs.evals_per_level[0];
+    int64_t launches = ctx->g_launches_fixed;
+    for (int l = 0; l < lv->num_levels; ++l) {
+        if (l > 0) {
+            vs.evals_per_level[l] = (int64_t)gs.evals[l];
+            vs.n_eval += (int64_t)gs.evals[l];
+            vs.candidates_per_level[l] = (int64_t)gs.cands[l];
+            vs.conflict_rounds[l] = (int32_t)gs.rounds[l];
+            launches += ctx->g_launches_body[l] * (int64_t)(gs.rounds[l] + 1);
+        }
+        vs.rechecked_per_level[l] = (int64_t)gs.rechecked[l];
+    }
+    ctx->prof.k[PIFU_K_MLP_HIDDEN].launches += launches;   // graph: counted in one class
+    const int cur = (lv->num_levels - 1) & 1;
+    vs.n = (int32_t)n_fine;
+    vs.row_words = row_words_of((int)n_fine);
+    vs.occ_bits_dev = ctx->bin[cur];
+    vs.eval_bits_dev = ctx->eval;
+    vs.values_dev = ctx->values;
+    if (out) *out = vs;
+    if (gs.err) return decode_err(gs.err);
+    ctx->stats = vs;
+    ctx->have_volume = true;
+    ctx->vol_N = (int)n_fine;
+    ctx->vol_bin = cur;
+    return PIFU_OK;
 }
 
 int pifu_profile(pifu_ctx* ctx, int enable) {

@@ -24,6 +24,7 @@ PIFU_ERR_NOT_CONVERGED = -5
 PIFU_ERR_TIMEOUT = -6
 PIFU_ERR_STATE = -7
 PIFU_ERR_UNSUPPORTED = -8
+PIFU_ERR_CAPACITY = -9
 
 PIFU_F32 = 0
 PIFU_BF16 = 1
@@ -34,7 +35,8 @@ PIFU_PREC_MIXED = 2
 # Every symbol include/pifu.h declares.
 EXPORTS = ("pifu_create", "pifu_destroy", "pifu_query", "pifu_query_colour", "pifu_localize",
            "pifu_render", "pifu_sync_stats", "pifu_status_string", "pifu_last_error",
-           "pifu_profile", "pifu_profile_read", "pifu_query_noalloc", "pifu_query_ex")
+           "pifu_profile", "pifu_profile_read", "pifu_query_noalloc", "pifu_query_ex",
+           "pifu_frame")
 
 KERNEL_CLASSES = ("gather", "mlp_hidden", "mlp_last", "level", "select", "render", "mlp_f32")
 
@@ -115,6 +117,10 @@ def _lib():
     lib.pifu_render.argtypes = [P, ctypes.POINTER(pifu_camera), ctypes.POINTER(pifu_fmap),
                                 ctypes.POINTER(pifu_fmap), ctypes.POINTER(F), P, P, P, P]
     lib.pifu_render.restype = I
+    lib.pifu_frame.argtypes = [P, ctypes.POINTER(pifu_fmap), ctypes.POINTER(pifu_fmap),
+                               ctypes.POINTER(F), ctypes.POINTER(pifu_levels),
+                               ctypes.POINTER(pifu_camera), P, P, P, P, ctypes.POINTER(pifu_volume)]
+    lib.pifu_frame.restype = I
     lib.pifu_sync_stats.argtypes = [P, ctypes.POINTER(pifu_volume)]
     lib.pifu_sync_stats.restype = I
     lib.pifu_status_string.argtypes = [I]
@@ -265,6 +271,22 @@ def pifu_render(ctx, width, height, occ_map, col_map, calib, depth=None, rgb=Non
                             ctypes.byref(fc) if fc else None, _calib(calib), _stream(stream),
                             _ptr(depth), _ptr(rgb), _ptr(mask))
     _check(st, "pifu_render", ctx)
+
+
+def pifu_frame(ctx, occ_map, col_map, calib, n0, num_levels, width, height, depth=None, rgb=None,
+               mask=None, precision=PIFU_PREC_MIXED, margin=0.02, max_rounds=0,
+               background=(0.0, 0.0, 0.0), stream=None) -> pifu_volume:
+    """Localization + render of one frame as a (cached) CUDA graph."""
+    fo = fmap(occ_map)
+    fc = fmap(col_map)
+    lv = pifu_levels(n0, num_levels, precision, max_rounds, margin)
+    cam = pifu_camera(width, height, (ctypes.c_float * 3)(*background), PIFU_PREC_BF16)
+    vol = pifu_volume()
+    st = _lib().pifu_frame(ctx, ctypes.byref(fo), ctypes.byref(fc) if fc else None, _calib(calib),
+                           ctypes.byref(lv), ctypes.byref(cam), _stream(stream), _ptr(depth),
+                           _ptr(rgb), _ptr(mask), ctypes.byref(vol))
+    _check(st, "pifu_frame", ctx)
+    return vol
 
 
 def pifu_sync_stats(ctx) -> pifu_volume:
