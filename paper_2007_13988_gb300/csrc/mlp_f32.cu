@@ -13,6 +13,7 @@
 // This is the precision reference on the GPU (FFMA, float32 accumulation);
 // the roofline that bounds it is the FP32 SIMT FMA rate.
 #include "pifu_internal.h"
+#include "epilogue.cuh"
 
 namespace pifu {
 namespace {
@@ -256,61 +257,8 @@ __device__ __forceinline__ float warp_sum(float v) {
     return v;
 }
 
-__device__ __forceinline__ float apply_act(int act, float t) {
-    if (act == ACT_SIGMOID) return 1.0f / (1.0f + expf(-t));
-    return 0.5f * (tanhf(t) + 1.0f);
-}
-
 __device__ __forceinline__ float to_f32(float v) { return v; }
 __device__ __forceinline__ float to_f32(__nv_bfloat16 v) { return __bfloat162float(v); }
-
-// The epilogue of one point (lane 0 of its warp): activation and where the
-// result goes.
-__device__ __forceinline__ void last_epilogue(const Epilogue& epi, int64_t p, int n_out,
-                                              const float (&t)[4], const float* __restrict__ bias) {
-    if (epi.recheck) {
-        // mixed precision: defer occupancies close to the decision threshold
-        const float o = apply_act(ACT_SIGMOID, t[0] + bias[0]);
-        if (fabsf(o - kHalf) < epi.margin) {
-            const unsigned pos = atomicAdd(epi.recheck_count, 1u);
-            epi.recheck[pos] = epi.mode == EPI_LEVEL
-                                   ? (epi.list ? epi.list[p] : (int)(epi.base + p))
-                                   : (epi.pix ? epi.pix[p] : (int)p);
-            return;
-        }
-    }
-    if (epi.mode == EPI_STORE) {
-        const int64_t q = epi.pix ? (int64_t)epi.pix[p] : p;
-        for (int j = 0; j < n_out; ++j) epi.out[q * n_out + j] = apply_act(epi.act, t[j] + bias[j]);
-    } else if (epi.mode == EPI_PIXELS) {
-        const int64_t pix = epi.pix[p];
-        for (int j = 0; j < n_out; ++j) epi.out[pix * 3 + j] = apply_act(epi.act, t[j] + bias[j]);
-    } else {
-        // Occupancy scattered into a localization level (Sec. 3.2): store the
-        // value, set the binarized bit, and flag a conflict when the
-        // binarized prediction differs from the binarized interpolation.
-        const float o = apply_act(ACT_SIGMOID, t[0] + bias[0]);
-        const int64_t idx = epi.list ? (int64_t)epi.list[p] : epi.base + p;
-        const LevelBits& lv = epi.lv;
-        lv.values[idx] = o;
-        const int64_t n1 = lv.N + 1;
-        const int64_t row = idx / n1;            // k (N+1) + j
-        const int i = (int)(idx - row * n1);
-        const int64_t w = row * lv.row_words + (i >> 5);
-        const uint32_t bit = 1u << (i & 31);
-        const bool ob = o >= kHalf;
-        if (lv.first_level) {
-            if (ob) atomicOr(&lv.bin[w], bit);
-        } else {
-            const bool tb = (lv.tent[w] & bit) != 0u;
-            if (ob != tb) {
-                atomicOr(&lv.conf[w], bit);
-                if (ob) atomicOr(&lv.bin[w], bit);
-                else atomicAnd(&lv.bin[w], ~bit);
-            }
-        }
-    }
-}
 
 // One warp per point (grid-stride over points; a device count narrows M).
 template <typename InT>

@@ -32,6 +32,7 @@
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 
+#include "epilogue.cuh"
 #include "pifu_internal.h"
 #include "sm100.cuh"
 
@@ -49,9 +50,12 @@ constexpr int kMaxN = 1024;   // widest layer whose bias is staged in shared mem
 constexpr int kEpiWarps = 8;
 constexpr int kThreads = 64 + 32 * kEpiWarps;
 
+constexpr int kFuseFloats = 4 * 256 + 2 * 4 * TBM + 16;   // last-layer W, exchange, flags
+
 __host__ __device__ constexpr uint32_t tc_smem_bytes(int BN) {
-    // operand ring + 1024-byte alignment slack + barriers + staged bias
-    return (uint32_t)TSTAGES * (TBM * TBK * 2 + BN * TBK * 2) + 1024 + 256 + kMaxN * 4;
+    // operand ring + 1024-byte alignment slack + barriers + staged bias + fused last layer
+    return (uint32_t)TSTAGES * (TBM * TBK * 2 + BN * TBK * 2) + 1024 + 256 + kMaxN * 4 +
+           kFuseFloats * 4;
 }
 
 // 64 consecutive TMEM columns of the warp's 32 lanes: four x16 loads, one wait.
@@ -72,12 +76,12 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
     return *reinterpret_cast<const uint32_t*>(&h);
 }
 
-template <int BN>
+template <int BN, bool FUSE>
 __global__ void __launch_bounds__(kThreads, 1) tc_linear_kernel(
     const __grid_constant__ CUtensorMap tmA1, const __grid_constant__ CUtensorMap tmA2,
     const __grid_constant__ CUtensorMap tmW, int nk1, int nk2, int M, int N,
     const float* __restrict__ bias, float slope, __nv_bfloat16* __restrict__ out, int ldo,
-    unsigned int* __restrict__ err, const unsigned int* __restrict__ m_dev) {
+    unsigned int* __restrict__ err, const unsigned int* __restrict__ m_dev, FuseLast fl) {
     if (m_dev) M = min(M, (int)*m_dev);   // device-resident row count
     constexpr uint32_t A_BYTES = TBM * TBK * 2;
     constexpr uint32_t B_BYTES = BN * TBK * 2;
@@ -92,6 +96,9 @@ __global__ void __launch_bounds__(kThreads, 1) tc_linear_kernel(
     uint64_t* acce = accf + 2;          // [2] accumulator drained by the epilogue
     uint32_t* tslot = reinterpret_cast<uint32_t*>(acce + 2);
     float* sbias = reinterpret_cast<float*>(reinterpret_cast<uint8_t*>(full) + 256);
+    float* sW5 = sbias + kMaxN;              // fused last layer: [4][BN]
+    float* sxch = sW5 + 4 * 256;             // [2 buffers][4 outputs][128 rows] partial sums
+    volatile uint32_t* sflag = reinterpret_cast<volatile uint32_t*>(sxch + 2 * 4 * TBM);  // [2][4]
 
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
@@ -114,6 +121,11 @@ __global__ void __launch_bounds__(kThreads, 1) tc_linear_kernel(
         prefetch_tmap(&tmW);
     }
     for (int c = threadIdx.x; c < N; c += blockDim.x) sbias[c] = bias[c];
+    if (FUSE) {
+        for (int c = threadIdx.x; c < fl.n_out * BN; c += blockDim.x)
+            sW5[c] = fl.W[(int64_t)(c / BN) * fl.ldw + (c % BN)];
+        if (threadIdx.x < 8) sflag[threadIdx.x] = 0u;
+    }
     if (warp == 1) tmem_alloc(tslot, TMEM_COLS);
     tc_fence_before();
     __syncthreads();
@@ -196,6 +208,8 @@ __global__ void __launch_bounds__(kThreads, 1) tc_linear_kernel(
             const int row = m0 + q * 32 + lane;
             const uint32_t tl = tmem + ((uint32_t)(q * 32) << 16) + b * BN;
             const float* bb = sbias + n0;
+            const int half = (warp - 2) >> 2;
+            float part[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll 1
             for (int c0 = cbase; c0 < cbase + HALF; c0 += 64) {
                 uint32_t r[64];
@@ -208,8 +222,20 @@ __global__ void __launch_bounds__(kThreads, 1) tc_linear_kernel(
                     tmem_ld16(tl + (uint32_t)c0 + 16, r1);
                     tmem_ld_wait();
                 }
-                if (row < M) {
-                    constexpr int NC = HALF >= 64 ? 64 : HALF;
+                constexpr int NC = HALF >= 64 ? 64 : HALF;
+                if (FUSE) {
+                    // h rounded to BF16 (as the unfused path stores it), dotted
+                    // with the last layer's rows
+#pragma unroll
+                    for (int cc = 0; cc < NC; ++cc) {
+                        float a = __uint_as_float(r[cc]) + bb[c0 + cc];
+                        a = a >= 0.f ? a : slope * a;
+                        a = __bfloat162float(__float2bfloat16_rn(a));
+#pragma unroll
+                        for (int jo = 0; jo < 4; ++jo)
+                            if (jo < fl.n_out) part[jo] = fmaf(a, sW5[jo * BN + c0 + cc], part[jo]);
+                    }
+                } else if (row < M) {
                     uint4* dst = reinterpret_cast<uint4*>(out + (int64_t)row * ldo + n0 + c0);
 #pragma unroll
                     for (int v = 0; v < NC / 8; ++v) {
@@ -229,7 +255,47 @@ __global__ void __launch_bounds__(kThreads, 1) tc_linear_kernel(
             }
             tc_fence_before();
             __syncwarp();
-            if (lane == 0) mbar_arrive(&acce[b]);
+            if (!FUSE || half == 1) {
+                if (lane == 0) mbar_arrive(&acce[b]);
+            }
+            if (FUSE) {
+                // the column-half-1 warp of this lane quadrant publishes its
+                // partial sums; the half-0 warp adds them and finishes the row
+                float* xb = sxch + b * 4 * TBM;
+                const int rit = q * 32 + lane;
+                volatile uint32_t* flag = sflag + b * 4 + q;
+                if (half == 1) {
+#pragma unroll
+                    for (int jo = 0; jo < 4; ++jo)
+                        if (jo < fl.n_out) xb[jo * TBM + rit] = part[jo];
+                    __threadfence_block();
+                    __syncwarp();
+                    if (lane == 0) *flag = i + 1u;
+                } else {
+                    bool seen = true;
+                    if (lane == 0) {
+                        seen = false;
+                        for (uint32_t it = 0; it < kWaitLimit; ++it)
+                            if (*flag == i + 1u) {
+                                seen = true;
+                                break;
+                            }
+                    }
+                    seen = __shfl_sync(0xffffffffu, seen ? 1 : 0, 0) != 0;
+                    __threadfence_block();
+                    if (!seen) ok = false;
+                    if (seen && row < M) {
+                        float tt[4];
+#pragma unroll
+                        for (int jo = 0; jo < 4; ++jo)
+                            tt[jo] = jo < fl.n_out ? part[jo] + xb[jo * TBM + rit] : 0.f;
+                        last_epilogue(fl.epi, fl.p0 + row, fl.n_out, tt, fl.bias);
+                    }
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&acce[b]);   // after reading the exchange
+                    if (!seen) break;
+                }
+            }
         }
     }
     if (!ok) atomicOr(err, 1u);
@@ -249,8 +315,12 @@ constexpr int bn_index(int BN) { return BN == 64 ? 0 : (BN == 128 ? 1 : 2); }
 template <int BN>
 cudaError_t ensure_attr(int dev) {
     if (dev >= 0 && dev < 64 && g_attr_set[bn_index(BN)][dev]) return cudaSuccess;
-    const cudaError_t e = cudaFuncSetAttribute(
-        tc_linear_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem_bytes(BN));
+    cudaError_t e = cudaFuncSetAttribute(tc_linear_kernel<BN, false>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)tc_smem_bytes(BN));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(tc_linear_kernel<BN, true>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem_bytes(BN));
     if (e == cudaSuccess && dev >= 0 && dev < 64) g_attr_set[bn_index(BN)][dev] = true;
     return e;
 }
@@ -277,9 +347,16 @@ cudaError_t launch_bn(const TcLayerArgs& a, cudaStream_t s) {
     if (e != cudaSuccess) return e;
     const long long tiles = (long long)(a.N / BN) * ((a.M + TBM - 1) / TBM);
     const int grid = (int)(tiles < sms ? tiles : sms);
-    tc_linear_kernel<BN><<<grid, kThreads, tc_smem_bytes(BN), s>>>(
-        *a.tmA1, *a.tmA2, *a.tmW, a.nk1, a.nk2, a.M, a.N, a.bias, a.slope, a.out, a.ldo, a.err,
-        a.m_dev);
+    if (a.fuse) {
+        if (a.N != BN || a.fuse->n_out < 1 || a.fuse->n_out > 4) return cudaErrorInvalidValue;
+        tc_linear_kernel<BN, true><<<grid, kThreads, tc_smem_bytes(BN), s>>>(
+            *a.tmA1, *a.tmA2, *a.tmW, a.nk1, a.nk2, a.M, a.N, a.bias, a.slope, a.out, a.ldo,
+            a.err, a.m_dev, *a.fuse);
+    } else {
+        tc_linear_kernel<BN, false><<<grid, kThreads, tc_smem_bytes(BN), s>>>(
+            *a.tmA1, *a.tmA2, *a.tmW, a.nk1, a.nk2, a.M, a.N, a.bias, a.slope, a.out, a.ldo,
+            a.err, a.m_dev, FuseLast{});
+    }
     return cudaGetLastError();
 }
 

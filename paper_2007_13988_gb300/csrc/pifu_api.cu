@@ -516,6 +516,20 @@ int run_mlp_tc(pifu_ctx* ctx, const DevNet& net, const PointSrc& src_in, int64_t
         CK(launch_gather_bf16(src, p0, mc, calib, map0, map1, ctx->Xb, net.ldx, s));
         pr.end(PIFU_K_GATHER, ev, s, 0.0,
                (double)mc * (4.0 * 4.0 * (map0.C + map1.C) + 2.0 * net.ldx));
+        // the last layer rides in the last hidden layer's epilogue when that
+        // layer is one tile wide and the last layer reads only its output
+        const DevLayer& Ll = net.layers[L - 1];
+        const bool fuse = L > 1 && Ll.K2 == 0 && Ll.n_out <= 4 &&
+                          net.tc[L - 2].BN == net.layers[L - 2].n_out;
+        FuseLast fl{};
+        if (fuse) {
+            fl.W = Ll.W;
+            fl.ldw = Ll.ldw;
+            fl.bias = Ll.b;
+            fl.n_out = Ll.n_out;
+            fl.p0 = p0;
+            fl.epi = epi;
+        }
         for (int l = 0; l + 1 < L; ++l) {
             const DevLayer& Ly = net.layers[l];
             const TcLayer& T = net.tc[l];
@@ -534,19 +548,23 @@ int run_mlp_tc(pifu_ctx* ctx, const DevNet& net, const PointSrc& src_in, int64_t
             a.ldo = Ly.n_out;
             a.err = ctx->d_count + 1;
             a.m_dev = m_dev;
+            a.fuse = (fuse && l == L - 2) ? &fl : nullptr;
+            double flops = 2.0 * mc * Ly.fan_in * Ly.n_out;
+            if (a.fuse) flops += 2.0 * mc * Ll.fan_in * Ll.n_out;
             ev = pr.begin(s);
             CK(launch_tc_linear(a, s));
-            pr.end(PIFU_K_MLP_HIDDEN, ev, s, 2.0 * mc * Ly.fan_in * Ly.n_out,
+            pr.end(PIFU_K_MLP_HIDDEN, ev, s, flops,
                    2.0 * ((double)mc * (Ly.fan_in + Ly.n_out) + (double)Ly.n_out * Ly.fan_in));
         }
-        const DevLayer& Ll = net.layers[L - 1];
-        const __nv_bfloat16* h = L > 1 ? ctx->Hb[(L - 2) % 2] : nullptr;
-        const int hw = L > 1 ? net.layers[L - 2].n_out : 0;
-        ev = pr.begin(s);
-        CK(launch_last_layer_bf16(p0, mc, Ll.n_out, h, hw, Ll.K1, ctx->Xb, net.ldx, Ll.K2, Ll.W,
-                                  Ll.ldw, Ll.b, epi, s, m_dev));
-        pr.end(PIFU_K_MLP_LAST, ev, s, 2.0 * mc * Ll.fan_in * Ll.n_out,
-               2.0 * (double)mc * (Ll.fan_in + Ll.n_out));
+        if (!fuse) {
+            const __nv_bfloat16* h = L > 1 ? ctx->Hb[(L - 2) % 2] : nullptr;
+            const int hw = L > 1 ? net.layers[L - 2].n_out : 0;
+            ev = pr.begin(s);
+            CK(launch_last_layer_bf16(p0, mc, Ll.n_out, h, hw, Ll.K1, ctx->Xb, net.ldx, Ll.K2,
+                                      Ll.W, Ll.ldw, Ll.b, epi, s, m_dev));
+            pr.end(PIFU_K_MLP_LAST, ev, s, 2.0 * mc * Ll.fan_in * Ll.n_out,
+                   2.0 * (double)mc * (Ll.fan_in + Ll.n_out));
+        }
     }
     return PIFU_OK;
 }

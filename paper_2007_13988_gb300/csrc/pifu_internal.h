@@ -127,6 +127,18 @@ cudaError_t launch_last_layer_bf16(int64_t p0, int64_t M, int n_out, const __nv_
 // and A2 (nk2 K-blocks) are 2-D tensor maps over BF16 rows, W a tensor map
 // over [N][64 (nk1 + nk2)] BF16; box 64 x 128 for A, 64 x BN for W, all
 // with the 128-byte swizzle.  N a multiple of BN (64, 128 or 256).
+// The last layer fused into the epilogue of the last hidden tensor-core layer
+// (possible when one tile spans the hidden width and the last layer reads
+// only h): out = epilogue(W h + b) per row, h rounded to BF16 as stored.
+struct FuseLast {
+    const float* W;     // [n_out][ldw] FP32
+    int ldw;
+    const float* bias;
+    int n_out;          // <= 4
+    int64_t p0;         // point number of the batch's first row
+    Epilogue epi;
+};
+
 struct TcLayerArgs {
     const CUtensorMap* tmA1;
     const CUtensorMap* tmA2;
@@ -138,6 +150,7 @@ struct TcLayerArgs {
     int ldo;
     unsigned int* err;
     const unsigned int* m_dev;   // optional device-resident row count (<= M)
+    const FuseLast* fuse;        // optional: last layer fused (requires N == BN)
 };
 cudaError_t launch_tc_linear(const TcLayerArgs& a, cudaStream_t stream);
 // Set the tensor-core kernels' attributes on the current device (before a
