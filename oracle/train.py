@@ -1,0 +1,83 @@
+"""Training arithmetic of the distilled occupancy surrogate, in float64.
+
+The paper trains f_O with a binary cross-entropy loss (Sec. 3.1) and uses
+Adam for the texture network (Appendix, Training procedure).  The surrogate
+is an MLP of the same family (no skips): h_l = g(W_l h_{l-1} + b_l) with
+leaky-ReLU g, logit t = W_L h_{L-1} + b_L, target y in [0, 1] (the full
+network's occupancy), and the mean BCE over a batch of B points
+
+    L = (1/B) sum_b [ softplus(t_b) - y_b t_b ]
+      = (1/B) sum_b -[ y_b log s(t_b) + (1 - y_b) log(1 - s(t_b)) ],
+
+whose gradient with respect to t_b is (s(t_b) - y_b) / B.  Backward
+propagation is the chain rule layer by layer: dW_l = dZ_l^T H_{l-1},
+db_l = column sums of dZ_l, dH_{l-1} = dZ_l W_l, dZ_{l-1} = dH_{l-1} * g'(Z).
+
+Adam (Kingma & Ba): m = b1 m + (1-b1) g, v = b2 v + (1-b2) g^2,
+w -= lr (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps).
+
+Pins: tests/test_oracle_train.py (central finite differences of the loss;
+a hand-computed Adam step; BCE closed forms).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+F64 = np.float64
+
+
+def leaky(z, slope):
+    return np.where(z >= 0, z, slope * z)
+
+
+def leaky_grad(z, slope):
+    return np.where(z >= 0, 1.0, slope)
+
+
+def bce_with_logits(t, y):
+    """Mean BCE of logits t against targets y (numerically stable form)."""
+    t = np.asarray(t, F64)
+    y = np.asarray(y, F64)
+    return float(np.mean(np.logaddexp(0.0, t) - y * t))
+
+
+def forward(Ws, bs, X, slope):
+    """Pre-activations Z_l and activations H_l (H_0 = X); the last Z is the logit."""
+    H = [np.asarray(X, F64)]
+    Z = []
+    L = len(Ws)
+    for l in range(L):
+        z = H[-1] @ np.asarray(Ws[l], F64).T + np.asarray(bs[l], F64)
+        Z.append(z)
+        if l < L - 1:
+            H.append(leaky(z, slope))
+    return Z, H
+
+
+def loss_and_grads(Ws, bs, X, y, slope):
+    """Mean BCE loss and its gradients (dW_l, db_l) for one batch."""
+    Z, H = forward(Ws, bs, X, slope)
+    t = Z[-1][:, 0]
+    B = len(t)
+    loss = bce_with_logits(t, y)
+    s = 1.0 / (1.0 + np.exp(-t))
+    dz = ((s - np.asarray(y, F64)) / B)[:, None]
+    L = len(Ws)
+    dWs = [None] * L
+    dbs = [None] * L
+    for l in range(L - 1, -1, -1):
+        dWs[l] = dz.T @ H[l]
+        dbs[l] = dz.sum(axis=0)
+        if l > 0:
+            dh = dz @ np.asarray(Ws[l], F64)
+            dz = dh * leaky_grad(Z[l - 1], slope)
+    return loss, dWs, dbs
+
+
+def adam_step(w, g, m, v, t, lr, b1=0.9, b2=0.999, eps=1e-8):
+    """One Adam update (step number t >= 1); returns new (w, m, v)."""
+    m = b1 * m + (1 - b1) * g
+    v = b2 * v + (1 - b2) * g * g
+    mh = m / (1 - b1 ** t)
+    vh = v / (1 - b2 ** t)
+    return w - lr * mh / (np.sqrt(vh) + eps), m, v

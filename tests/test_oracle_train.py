@@ -1,0 +1,61 @@
+"""Pins of the oracle's training arithmetic (BCE loss of Sec. 3.1, Adam of
+the appendix) against central finite differences and hand-computed values."""
+import math
+
+import numpy as np
+
+from oracle import train
+
+
+def small_net(seed=0, dims=(7, 5, 4, 1)):
+    rng = np.random.default_rng(seed)
+    Ws = [rng.standard_normal((dims[i + 1], dims[i])) * 0.7 for i in range(len(dims) - 1)]
+    bs = [rng.standard_normal(dims[i + 1]) * 0.1 for i in range(len(dims) - 1)]
+    return Ws, bs
+
+
+def test_bce_closed_forms():
+    assert abs(train.bce_with_logits([0.0], [0.3]) - math.log(2.0)) < 1e-15
+    # y = 1: -log sigmoid(t)
+    assert abs(train.bce_with_logits([2.0], [1.0]) - math.log1p(math.exp(-2.0))) < 1e-15
+    # y = 0: -log(1 - sigmoid(t))
+    assert abs(train.bce_with_logits([-1.5], [0.0]) - math.log1p(math.exp(-1.5))) < 1e-15
+
+
+def test_gradients_match_central_differences():
+    Ws, bs = small_net(1)
+    rng = np.random.default_rng(2)
+    X = rng.standard_normal((9, 7))
+    y = rng.uniform(0, 1, 9)
+    slope = 0.01
+    loss, dWs, dbs = train.loss_and_grads(Ws, bs, X, y, slope)
+    h = 1e-6
+    for l in range(len(Ws)):
+        for idx in [(0, 0), (Ws[l].shape[0] - 1, Ws[l].shape[1] - 1), (0, Ws[l].shape[1] // 2)]:
+            Wp = [w.copy() for w in Ws]
+            Wm = [w.copy() for w in Ws]
+            Wp[l][idx] += h
+            Wm[l][idx] -= h
+            num = (train.loss_and_grads(Wp, bs, X, y, slope)[0]
+                   - train.loss_and_grads(Wm, bs, X, y, slope)[0]) / (2 * h)
+            assert abs(num - dWs[l][idx]) < 1e-8, (l, idx)
+        bp = [b.copy() for b in bs]
+        bm = [b.copy() for b in bs]
+        bp[l][0] += h
+        bm[l][0] -= h
+        num = (train.loss_and_grads(Ws, bp, X, y, slope)[0]
+               - train.loss_and_grads(Ws, bm, X, y, slope)[0]) / (2 * h)
+        assert abs(num - dbs[l][0]) < 1e-8
+
+
+def test_adam_first_steps_by_hand():
+    # Step 1: m = 0.1 g, v = 0.001 g^2, bias-corrected m_hat = g, v_hat = g^2,
+    # so the update is lr * g / (|g| + eps) = lr * sign(g) (up to eps).
+    w, m, v = train.adam_step(np.array([1.0, -2.0]), np.array([0.5, -4.0]), np.zeros(2),
+                              np.zeros(2), 1, lr=0.1)
+    np.testing.assert_allclose(w, [1.0 - 0.1, -2.0 + 0.1], atol=1e-7)
+    np.testing.assert_allclose(m, [0.05, -0.4])
+    np.testing.assert_allclose(v, [0.00025, 0.016])
+    # Step 2 with the same gradient: m_hat = g, v_hat = g^2 again.
+    w2, _, _ = train.adam_step(w, np.array([0.5, -4.0]), m, v, 2, lr=0.1)
+    np.testing.assert_allclose(w2, [1.0 - 0.2, -2.0 + 0.2], atol=1e-7)
