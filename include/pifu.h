@@ -80,6 +80,8 @@ typedef struct {
     int32_t precision;   /* pifu_precision                                     */
     int32_t max_rounds;  /* cap on conflict rounds per level (<= 0: 4096)      */
     float margin;        /* MIXED: FP32 re-evaluation band |o - 0.5| < margin  */
+    int32_t use_surrogate;    /* 1: coarse levels evaluate the trained f_S first  */
+    float surrogate_margin;   /* f_S occupancies within this of 0.5 fall back to f_O */
 } pifu_levels;
 
 /* Target view of the render: the volume is aligned with it (Sec. 3.2), so
@@ -107,6 +109,7 @@ typedef struct {
     int64_t evals_per_level[8];
     int64_t candidates_per_level[8]; /* boundary candidates (before dilation)  */
     int64_t rechecked_per_level[8];  /* MIXED: evaluations redone in FP32       */
+    int64_t fallback_per_level[8];   /* surrogate: evaluations redone by f_O    */
     int32_t conflict_rounds[8];
 } pifu_volume;
 
@@ -196,6 +199,49 @@ int pifu_frame(pifu_ctx* ctx, const pifu_fmap* occ_map, const pifu_fmap* col_map
                const float calib[12], const pifu_levels* levels, const pifu_camera* cam,
                void* stream, float* depth_dev, float* rgb_dev, uint8_t* mask_dev,
                pifu_volume* out);
+
+/* ---- Learned surrogate f_S (not in the paper) -------------------------------
+ * A small MLP of f_O's family, f_S: d_in -> h1 -> h2 -> 1 (leaky-ReLU,
+ * sigmoid, no skips), distilled from f_O and used by pifu_localize at the
+ * coarse levels (pifu_levels.use_surrogate): points whose f_S occupancy lies
+ * within surrogate_margin of 0.5 are evaluated again by f_O; the finest level
+ * always uses f_O.  Trained by the library's kernels: FP32 forward, the mean
+ * binary cross-entropy of Sec. 3.1 against f_O's occupancy, back-propagation
+ * and Adam (beta 0.9 / 0.999, eps 1e-8; the optimiser of the appendix).
+ * Parameters are exchanged in the blob's order: per layer W[n_out][fan_in]
+ * row-major, then b[n_out]. */
+
+/* Create (or re-create) f_S with Kaiming-uniform weights from `seed` and
+ * zero biases; h1, h2 multiples of 64 in 64 .. 1024. */
+int pifu_surrogate_init(pifu_ctx* ctx, int h1, int h2, uint64_t seed);
+
+/* Distillation tuples at m points: x_dev [m][ldx] float32 receives the rows
+ * f_O and f_S read ([Phi(g_O), P_z] zero-padded to ldx = d_in rounded up to
+ * 8), o_dev [m] f_O's occupancy in FP32.  Asynchronous on `stream`. */
+int pifu_surrogate_samples(pifu_ctx* ctx, const pifu_fmap* occ_map, const float calib[12],
+                           const float* pts_dev, int64_t m, float* x_dev, float* o_dev,
+                           void* stream);
+
+/* f_S's occupancy at m points (as pifu_query_ex, precision FP32 or BF16). */
+int pifu_surrogate_query(pifu_ctx* ctx, const pifu_fmap* occ_map, const float calib[12],
+                         const float* pts_dev, int64_t m, float* occ_dev, int precision,
+                         void* stream);
+
+/* Loss and gradient of f_S on one batch (x_dev [B][ldx], y_dev [B] targets in
+ * [0, 1]); grad_host (may be NULL) receives the gradient in the parameter
+ * order, loss_host the mean BCE.  Synchronises `stream`. */
+int pifu_surrogate_grad(pifu_ctx* ctx, const float* x_dev, const float* y_dev, int64_t B,
+                        float* grad_host, double* loss_host, void* stream);
+
+/* `steps` Adam steps with learning rate lr over consecutive batches of
+ * `batch` rows of (x_dev, y_dev) (m rows, wrapping around); loss_host[0] and
+ * [1] receive the first and the last batch loss.  Synchronises `stream`. */
+int pifu_surrogate_train(pifu_ctx* ctx, const float* x_dev, const float* y_dev, int64_t m,
+                         int batch, int steps, float lr, double* loss_host, void* stream);
+
+/* Copy f_S's n parameters to (set = 0) or from (set != 0) host memory;
+ * n must equal the parameter count. */
+int pifu_surrogate_params(pifu_ctx* ctx, float* host, int64_t n, int set);
 
 /* Copy the counters of the last pifu_localize into *out (host). */
 int pifu_sync_stats(pifu_ctx* ctx, pifu_volume* out);

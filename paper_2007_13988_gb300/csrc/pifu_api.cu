@@ -187,6 +187,27 @@ struct pifu_ctx {
     int vol_bin = 0;
     pifu_volume stats{};
     Profiler prof;
+    // learned surrogate f_S (d_in -> h1 -> h2 -> 1), FP32 master parameters
+    struct {
+        bool ready = false;
+        int h1 = 0, h2 = 0;
+        int64_t n = 0;                 // parameters in the padded device layout
+        int64_t off_w[3] = {}, off_b[3] = {};
+        float* params = nullptr;       // [W1 h1 x ldx | b1 | W2 h2 x h1 | b2 | W3 1 x h2 | b3]
+        float* grads = nullptr;
+        float* adam_m = nullptr;
+        float* adam_v = nullptr;
+        int step = 0;
+        int batch_cap = 0;
+        float *H1 = nullptr, *H2 = nullptr, *logit = nullptr, *g = nullptr, *dH1 = nullptr,
+              *dH2 = nullptr, *ones = nullptr;
+        double* d_loss = nullptr;
+        double* h_loss = nullptr;      // pinned
+    } sur;
+    DevNet snet;                       // f_S as the MLP runners see it
+    int* squeue = nullptr;             // surrogate fall-back queue (node indices)
+    unsigned int* d_squeue = nullptr;
+    unsigned int* h_squeue = nullptr;  // pinned
     // graph form (pifu_frame)
     bool g_valid = false;
     FrameKey gkey{};
@@ -448,8 +469,10 @@ int ensure_level_ws(pifu_ctx* ctx, int N) {
     CK(dev_alloc(&ctx->col_top, (int64_t)(N + 1) * (N + 1)));
     if (nodes > ctx->recheck_cap) {
         dev_free(ctx->recheck);
+        dev_free(ctx->squeue);
         ctx->recheck_cap = 0;
         CK(dev_alloc(&ctx->recheck, nodes));
+        CK(dev_alloc(&ctx->squeue, nodes));
         ctx->recheck_cap = nodes;
     }
     ctx->ws_N = N;
@@ -660,6 +683,39 @@ int read_recheck(pifu_ctx* ctx, cudaStream_t s, unsigned int* out) {
     return PIFU_OK;
 }
 
+// One evaluation batch of a level: the plain/BF16/MIXED network, or, at a
+// coarse level with the surrogate on, f_S first and f_O for the occupancies
+// f_S puts within `sur_margin` of 0.5 (one host read of that queue).
+int eval_level_batch(pifu_ctx* ctx, const PointSrc& src, int64_t n, const Map& map,
+                     const Calib& cal, const Epilogue& epi, int prec, float margin, bool surrogate,
+                     float sur_margin, cudaStream_t s, int64_t* rechecked, int64_t* fallback) {
+    const DevNet& fo = ctx->net[0];
+    if (!surrogate) {
+        return prec == PIFU_PREC_MIXED
+                   ? run_mlp_mixed(ctx, fo, src, n, map, Map{}, cal, epi, margin, s, rechecked)
+                   : run_mlp(ctx, fo, src, n, map, Map{}, cal, epi, s, prec);
+    }
+    if (n > ctx->recheck_cap) return PIFU_ERR_ARG;
+    CK(cudaMemsetAsync(ctx->d_squeue, 0, sizeof(unsigned int), s));
+    Epilogue es = epi;
+    es.recheck = ctx->squeue;
+    es.recheck_count = ctx->d_squeue;
+    es.margin = sur_margin;
+    int st = run_mlp(ctx, ctx->snet, src, n, map, Map{}, cal, es, s,
+                     prec == PIFU_PREC_FP32 || !ctx->snet.tc_ok ? PIFU_PREC_FP32 : PIFU_PREC_BF16);
+    if (st != PIFU_OK) return st;
+    CK(cudaMemcpyAsync(ctx->h_squeue, ctx->d_squeue, sizeof(unsigned int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    const unsigned int nf = *ctx->h_squeue;
+    if (fallback) *fallback += nf;
+    if (nf == 0) return PIFU_OK;
+    PointSrc sf{PTS_LIST, nullptr, ctx->squeue, 0, src.N, nullptr};
+    Epilogue ef = epi;
+    ef.list = ctx->squeue;
+    return eval_level_batch(ctx, sf, nf, map, cal, ef, prec, margin, false, 0.f, s, rechecked,
+                            nullptr);
+}
+
 int decode_err(unsigned int e) {
     if (e & kErrCapacity) return PIFU_ERR_CAPACITY;
     if (e & kErrNotConverged) return PIFU_ERR_NOT_CONVERGED;
@@ -684,6 +740,223 @@ int read_count(pifu_ctx* ctx, cudaStream_t s, unsigned int* out) {
 }  // namespace
 
 namespace {
+
+// ---- learned surrogate f_S ---------------------------------------------------
+//
+// Not in the paper: a small MLP of the same family, distilled from f_O on
+// (features, depth, occupancy) tuples that f_O itself produces, and used at
+// the coarse levels where only the side of 0.5 matters.  Occupancies it puts
+// within a margin of 0.5 fall back to f_O.  Training runs entirely in the
+// library's kernels (train.cu): FP32 forward, mean BCE, back-propagation,
+// Adam.
+
+uint64_t splitmix64(uint64_t& x) {
+    uint64_t z = (x += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+void sur_free(pifu_ctx* ctx) {
+    auto& S = ctx->sur;
+    dev_free(S.params);
+    dev_free(S.grads);
+    dev_free(S.adam_m);
+    dev_free(S.adam_v);
+    dev_free(S.H1);
+    dev_free(S.H2);
+    dev_free(S.logit);
+    dev_free(S.g);
+    dev_free(S.dH1);
+    dev_free(S.dH2);
+    dev_free(S.ones);
+    dev_free(S.d_loss);
+    if (S.h_loss) cudaFreeHost(S.h_loss);
+    S.h_loss = nullptr;
+    for (auto& T : ctx->snet.tc) dev_free(T.W);
+    ctx->snet.tc.clear();
+    ctx->snet.layers.clear();
+    ctx->snet.tc_ok = false;
+    S.ready = false;
+    S.batch_cap = 0;
+}
+
+// The FP32 runner's view of f_S (weights inside the flat parameter buffer).
+void sur_bind(pifu_ctx* ctx) {
+    auto& S = ctx->sur;
+    const DevNet& fo = ctx->net[0];
+    DevNet& n = ctx->snet;
+    n.kind = 0;
+    n.d_in = fo.d_in;
+    n.ldx = fo.ldx;
+    n.slope = fo.slope;
+    n.max_hidden = std::max(S.h1, S.h2);
+    n.layers.assign(3, DevLayer{});
+    const int widths[3] = {S.h1, S.h2, 1};
+    for (int l = 0; l < 3; ++l) {
+        DevLayer& L = n.layers[l];
+        L.n_out = widths[l];
+        L.K1 = l == 0 ? 0 : widths[l - 1];
+        L.K2 = l == 0 ? fo.ldx : 0;
+        L.ldw = L.K1 + L.K2;
+        L.fan_in = l == 0 ? fo.d_in : widths[l - 1];
+        L.W = S.params + S.off_w[l];
+        L.b = S.params + S.off_b[l];
+    }
+}
+
+// Rebuild the BF16 tensor-core form of f_S from its current parameters.
+int sur_build_tc(pifu_ctx* ctx) {
+    auto& S = ctx->sur;
+    DevNet& n = ctx->snet;
+    for (auto& T : n.tc) dev_free(T.W);
+    n.tc.clear();
+    std::vector<float> p((size_t)S.n);
+    CK(cudaMemcpy(p.data(), S.params, (size_t)S.n * 4, cudaMemcpyDeviceToHost));
+    HostNet hn;
+    hn.shape = n;
+    hn.W.resize(3);
+    hn.b.resize(3);
+    for (int l = 0; l < 3; ++l) {
+        const DevLayer& L = n.layers[l];
+        hn.W[l].assign(p.begin() + S.off_w[l], p.begin() + S.off_w[l] + (int64_t)L.n_out * L.ldw);
+        hn.b[l].assign(p.begin() + S.off_b[l], p.begin() + S.off_b[l] + round_up(L.n_out, 4));
+    }
+    return build_tc(ctx, hn, n);
+}
+
+int sur_init(pifu_ctx* ctx, int h1, int h2, uint64_t seed) {
+    sur_free(ctx);
+    auto& S = ctx->sur;
+    const DevNet& fo = ctx->net[0];
+    S.h1 = h1;
+    S.h2 = h2;
+    const int ldx = fo.ldx;
+    const int64_t sizes_w[3] = {(int64_t)h1 * ldx, (int64_t)h2 * h1, (int64_t)h2};
+    const int64_t sizes_b[3] = {round_up(h1, 4), round_up(h2, 4), 4};
+    int64_t off = 0;
+    for (int l = 0; l < 3; ++l) {
+        S.off_w[l] = off;
+        off += sizes_w[l];
+        S.off_b[l] = off;
+        off += sizes_b[l];
+    }
+    S.n = off;
+    // Kaiming-uniform weights (leaky-ReLU gain) from a splitmix64 stream,
+    // zero biases; padding columns stay zero.
+    std::vector<float> p((size_t)off, 0.f);
+    uint64_t st = seed;
+    const int fan[3] = {fo.d_in, h1, h2};
+    const int rows[3] = {h1, h2, 1};
+    const int ld[3] = {ldx, h1, h2};
+    for (int l = 0; l < 3; ++l) {
+        const double bound = std::sqrt(6.0 / fan[l]) / (l == 2 ? std::sqrt(2.0) : 1.0);
+        for (int r = 0; r < rows[l]; ++r)
+            for (int k = 0; k < fan[l]; ++k) {
+                const double u = (double)(splitmix64(st) >> 11) * (1.0 / 9007199254740992.0);
+                p[(size_t)(S.off_w[l] + (int64_t)r * ld[l] + k)] = (float)((2.0 * u - 1.0) * bound);
+            }
+    }
+    CK(dev_alloc(&S.params, off));
+    CK(dev_alloc(&S.grads, off));
+    CK(dev_alloc(&S.adam_m, off));
+    CK(dev_alloc(&S.adam_v, off));
+    CK(cudaMemcpy(S.params, p.data(), (size_t)off * 4, cudaMemcpyHostToDevice));
+    CK(cudaMemset(S.adam_m, 0, (size_t)off * 4));
+    CK(cudaMemset(S.adam_v, 0, (size_t)off * 4));
+    CK(dev_alloc(&S.d_loss, 1));
+    CK(cudaHostAlloc(&S.h_loss, sizeof(double), cudaHostAllocDefault));
+    S.step = 0;
+    S.ready = true;
+    sur_bind(ctx);
+    return sur_build_tc(ctx);
+}
+
+int sur_batch_ws(pifu_ctx* ctx, int B) {
+    auto& S = ctx->sur;
+    if (B <= S.batch_cap) return PIFU_OK;
+    float** bufs[] = {&S.H1, &S.H2, &S.logit, &S.g, &S.dH1, &S.dH2, &S.ones};
+    for (auto b : bufs) dev_free(*b);
+    S.batch_cap = 0;
+    CK(dev_alloc(&S.H1, (int64_t)B * S.h1));
+    CK(dev_alloc(&S.dH1, (int64_t)B * S.h1));
+    CK(dev_alloc(&S.H2, (int64_t)B * S.h2));
+    CK(dev_alloc(&S.dH2, (int64_t)B * S.h2));
+    CK(dev_alloc(&S.logit, B));
+    CK(dev_alloc(&S.g, B));
+    CK(dev_alloc(&S.ones, B));
+    CK(launch_fill(B, S.ones, 1.f, 0));
+    CK(cudaDeviceSynchronize());
+    S.batch_cap = B;
+    return PIFU_OK;
+}
+
+// Forward + backward of f_S on one batch (rows x: [B][ldx], targets y):
+// gradients into S.grads, mean BCE added to *S.d_loss.
+int sur_grad(pifu_ctx* ctx, const float* x, const float* y, int B, cudaStream_t s) {
+    auto& S = ctx->sur;
+    const int ldx = ctx->snet.ldx;
+    const float slope = ctx->snet.slope;
+    float* P = S.params;
+    float* G = S.grads;
+    const int h1 = S.h1, h2 = S.h2;
+    const int red = std::max(1, B / 256);   // reduction slices over the batch
+    // forward
+    CK(launch_gemm_strided(B, h1, ldx, x, ldx, 1, P + S.off_w[0], 1, ldx, S.H1, h1, 1, 0, s));
+    CK(launch_bias_lrelu(B, h1, S.H1, h1, P + S.off_b[0], slope, s));
+    CK(launch_gemm_strided(B, h2, h1, S.H1, h1, 1, P + S.off_w[1], 1, h1, S.H2, h2, 1, 0, s));
+    CK(launch_bias_lrelu(B, h2, S.H2, h2, P + S.off_b[1], slope, s));
+    CK(launch_gemm_strided(B, 1, h2, S.H2, h2, 1, P + S.off_w[2], 1, h2, S.logit, 1, 1, 0, s));
+    CK(launch_bce_grad(B, S.logit, P + S.off_b[2], y, S.g, S.d_loss, s));
+    // backward
+    CK(cudaMemsetAsync(G, 0, (size_t)S.n * 4, s));
+    // layer 3: dW3 = g^T H2, db3 = sum g, dH2 = g W3
+    CK(launch_gemm_strided(1, h2, B, S.g, 0, 1, S.H2, h2, 1, G + S.off_w[2], h2, red, 1, s));
+    CK(launch_gemm_strided(1, 1, B, S.g, 0, 1, S.ones, 1, 0, G + S.off_b[2], 1, red, 1, s));
+    CK(launch_gemm_strided(B, h2, 1, S.g, 1, 0, P + S.off_w[2], 0, 1, S.dH2, h2, 1, 0, s));
+    CK(launch_lrelu_backward((int64_t)B * h2, S.dH2, S.H2, slope, s));
+    // layer 2: dW2 = dZ2^T H1, db2 = column sums, dH1 = dZ2 W2
+    CK(launch_gemm_strided(h2, h1, B, S.dH2, 1, h2, S.H1, h1, 1, G + S.off_w[1], h1, red, 1, s));
+    CK(launch_gemm_strided(h2, 1, B, S.dH2, 1, h2, S.ones, 1, 0, G + S.off_b[1], 1, red, 1, s));
+    CK(launch_gemm_strided(B, h1, h2, S.dH2, h2, 1, P + S.off_w[1], h1, 1, S.dH1, h1, 1, 0, s));
+    CK(launch_lrelu_backward((int64_t)B * h1, S.dH1, S.H1, slope, s));
+    // layer 1: dW1 = dZ1^T X (padding columns of X are 0, so are theirs), db1
+    CK(launch_gemm_strided(h1, ldx, B, S.dH1, 1, h1, x, ldx, 1, G + S.off_w[0], ldx, red, 1, s));
+    CK(launch_gemm_strided(h1, 1, B, S.dH1, 1, h1, S.ones, 1, 0, G + S.off_b[0], 1, red, 1, s));
+    return PIFU_OK;
+}
+
+// Unpadded parameter layout (the blob's order): per layer W[n_out][fan_in], b.
+int64_t sur_unpadded_count(const pifu_ctx* ctx) {
+    const auto& S = ctx->sur;
+    const int fi = ctx->snet.d_in;
+    return (int64_t)S.h1 * fi + S.h1 + (int64_t)S.h2 * S.h1 + S.h2 + S.h2 + 1;
+}
+
+void sur_pack(const pifu_ctx* ctx, const std::vector<float>& padded, float* out) {
+    const auto& S = ctx->sur;
+    const DevNet& n = ctx->snet;
+    int64_t o = 0;
+    for (int l = 0; l < 3; ++l) {
+        const DevLayer& L = n.layers[l];
+        for (int r = 0; r < L.n_out; ++r)
+            for (int k = 0; k < L.fan_in; ++k) out[o++] = padded[(size_t)(S.off_w[l] + (int64_t)r * L.ldw + k)];
+        for (int r = 0; r < L.n_out; ++r) out[o++] = padded[(size_t)(S.off_b[l] + r)];
+    }
+}
+
+void sur_unpack(const pifu_ctx* ctx, const float* in, std::vector<float>& padded) {
+    const auto& S = ctx->sur;
+    const DevNet& n = ctx->snet;
+    padded.assign((size_t)S.n, 0.f);
+    int64_t o = 0;
+    for (int l = 0; l < 3; ++l) {
+        const DevLayer& L = n.layers[l];
+        for (int r = 0; r < L.n_out; ++r)
+            for (int k = 0; k < L.fan_in; ++k) padded[(size_t)(S.off_w[l] + (int64_t)r * L.ldw + k)] = in[o++];
+        for (int r = 0; r < L.n_out; ++r) padded[(size_t)(S.off_b[l] + r)] = in[o++];
+    }
+}
 
 // ---- graph form: one CUDA graph per frame ------------------------------------
 //
@@ -964,6 +1237,10 @@ int pifu_create(const void* weight_blob, size_t bytes, pifu_ctx** out) {
         if (e == cudaSuccess)
             e = cudaHostAlloc(&ctx->h_recheck, sizeof(unsigned int), cudaHostAllocDefault);
         if (e == cudaSuccess) e = dev_alloc(&ctx->recheck, kChunk);
+        if (e == cudaSuccess) e = dev_alloc(&ctx->squeue, kChunk);
+        if (e == cudaSuccess) e = cudaMalloc(&ctx->d_squeue, sizeof(unsigned int));
+        if (e == cudaSuccess)
+            e = cudaHostAlloc(&ctx->h_squeue, sizeof(unsigned int), cudaHostAllocDefault);
         if (e == cudaSuccess) ctx->recheck_cap = kChunk;
         if (e == cudaSuccess)
             e = cudaHostAlloc(&ctx->h_pop, kMaxLevels * sizeof(unsigned long long), cudaHostAllocDefault);
@@ -1003,6 +1280,10 @@ void pifu_destroy(pifu_ctx* ctx) {
     dev_free(ctx->hit_pix);
     dev_free(ctx->col_top);
     g_destroy(ctx);
+    sur_free(ctx);
+    dev_free(ctx->squeue);
+    dev_free(ctx->d_squeue);
+    if (ctx->h_squeue) cudaFreeHost(ctx->h_squeue);
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     if (ctx->cap_stream2) cudaStreamDestroy(ctx->cap_stream2);
     dev_free(ctx->d_gstats);
@@ -1090,6 +1371,9 @@ int pifu_localize(pifu_ctx* ctx, const pifu_fmap* occ_map, const float calib[12]
     if (lv->precision == PIFU_PREC_MIXED && !(lv->margin >= 0.f && lv->margin <= 0.5f))
         return PIFU_ERR_ARG;
     const int prec = lv->precision;
+    const bool use_sur = lv->use_surrogate != 0;
+    if (use_sur && (!ctx->sur.ready || !(lv->surrogate_margin >= 0.f && lv->surrogate_margin <= 0.5f)))
+        return use_sur && !ctx->sur.ready ? PIFU_ERR_STATE : PIFU_ERR_ARG;
     if (occ_map->dtype != PIFU_F32) return PIFU_ERR_UNSUPPORTED;
     if (ctx->net[0].d_in != occ_map->C + 1) return PIFU_ERR_ARG;
     const int max_rounds = lv->max_rounds > 0 ? lv->max_rounds : 4096;
@@ -1104,7 +1388,6 @@ int pifu_localize(pifu_ctx* ctx, const pifu_fmap* occ_map, const float calib[12]
     vs.num_levels = lv->num_levels;
     const Map map = to_map(occ_map);
     const Calib cal = to_calib(calib);
-    const DevNet& net = ctx->net[0];
     CK(cudaMemsetAsync(ctx->d_pop, 0, kMaxLevels * sizeof(unsigned long long), s));
 
     // level 0: dense evaluation of every node
@@ -1123,10 +1406,9 @@ int pifu_localize(pifu_ctx* ctx, const pifu_fmap* occ_map, const float calib[12]
         epi.list = nullptr;
         epi.base = 0;
         epi.lv = LevelBits{ctx->values, ctx->tent, ctx->bin[cur], ctx->conf[0], N, row_words_of(N), 1};
-        st = prec == PIFU_PREC_MIXED
-                 ? run_mlp_mixed(ctx, net, src, nodes, map, Map{}, cal, epi, lv->margin, s,
-                                 &vs.rechecked_per_level[0])
-                 : run_mlp(ctx, net, src, nodes, map, Map{}, cal, epi, s, prec);
+        st = eval_level_batch(ctx, src, nodes, map, cal, epi, prec, lv->margin,
+                              use_sur && lv->num_levels > 1, lv->surrogate_margin, s,
+                              &vs.rechecked_per_level[0], &vs.fallback_per_level[0]);
         if (st != PIFU_OK) return st;
         vs.evals_per_level[0] = nodes;
         vs.n_eval = nodes;
@@ -1163,10 +1445,9 @@ int pifu_localize(pifu_ctx* ctx, const pifu_fmap* occ_map, const float calib[12]
         epi.list = ctx->list;
         while (n > 0) {
             epi.lv = LevelBits{ctx->values, ctx->tent, ctx->bin[cur], ctx->conf[q], N, rw, 0};
-            st = prec == PIFU_PREC_MIXED
-                     ? run_mlp_mixed(ctx, net, src, n, map, Map{}, cal, epi, lv->margin, s,
-                                     &vs.rechecked_per_level[l])
-                     : run_mlp(ctx, net, src, n, map, Map{}, cal, epi, s, prec);
+            st = eval_level_batch(ctx, src, n, map, cal, epi, prec, lv->margin,
+                                  use_sur && l < lv->num_levels - 1, lv->surrogate_margin, s,
+                                  &vs.rechecked_per_level[l], &vs.fallback_per_level[l]);
             if (st != PIFU_OK) return st;
             level_evals += n;
             // unevaluated 1-ring of this evaluation's conflicts
@@ -1290,6 +1571,7 @@ int pifu_frame(pifu_ctx* ctx, const pifu_fmap* occ_map, const pifu_fmap* col_map
     if (lv->precision != PIFU_PREC_BF16 && lv->precision != PIFU_PREC_MIXED) return PIFU_ERR_UNSUPPORTED;
     if (lv->precision == PIFU_PREC_MIXED && !(lv->margin >= 0.f && lv->margin <= 0.5f))
         return PIFU_ERR_ARG;
+    if (lv->use_surrogate) return PIFU_ERR_UNSUPPORTED;   // host-driven form only
     if (occ_map->dtype != PIFU_F32 || (col_map && col_map->dtype != PIFU_F32)) return PIFU_ERR_UNSUPPORTED;
     if (ctx->net[0].d_in != occ_map->C + 1) return PIFU_ERR_ARG;
     if (!ctx->net[0].tc_ok) return PIFU_ERR_UNSUPPORTED;
@@ -1366,6 +1648,139 @@ int pifu_frame(pifu_ctx* ctx, const pifu_fmap* occ_map, const pifu_fmap* col_map
     ctx->have_volume = true;
     ctx->vol_N = (int)n_fine;
     ctx->vol_bin = cur;
+    return PIFU_OK;
+}
+
+int pifu_surrogate_init(pifu_ctx* ctx, int h1, int h2, uint64_t seed) {
+    if (!ctx || h1 < 64 || h2 < 64 || h1 % 64 || h2 % 64 || h1 > 1024 || h2 > 1024)
+        return PIFU_ERR_ARG;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return PIFU_ERR_CUDA;
+    return sur_init(ctx, h1, h2, seed);
+}
+
+int pifu_surrogate_samples(pifu_ctx* ctx, const pifu_fmap* occ_map, const float calib[12],
+                           const float* pts_dev, int64_t m, float* x_dev, float* o_dev,
+                           void* stream) {
+    if (!ctx || !calib || m < 0 || !map_ok(occ_map)) return PIFU_ERR_ARG;
+    if (m == 0) return PIFU_OK;
+    if (!pts_dev || !x_dev || !o_dev) return PIFU_ERR_ARG;
+    if (occ_map->dtype != PIFU_F32) return PIFU_ERR_UNSUPPORTED;
+    if (ctx->net[0].d_in != occ_map->C + 1) return PIFU_ERR_ARG;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return PIFU_ERR_CUDA;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const Map map = to_map(occ_map);
+    const Calib cal = to_calib(calib);
+    PointSrc src{PTS_XYZ, pts_dev, nullptr, 0, 0, nullptr};
+    // the rows f_S reads: [Phi(g_O), z, 0 ...] with the row width of f_O
+    for (int64_t p0 = 0; p0 < m; p0 += kChunk) {
+        const int64_t mc = std::min<int64_t>(kChunk, m - p0);
+        CK(launch_gather(src, p0, mc, cal, map, Map{}, x_dev + p0 * ctx->net[0].ldx,
+                         ctx->net[0].ldx, s));
+    }
+    // the targets: f_O's occupancy in FP32
+    Epilogue epi{};
+    epi.mode = EPI_STORE;
+    epi.act = ACT_SIGMOID;
+    epi.out = o_dev;
+    return run_mlp(ctx, ctx->net[0], src, m, map, Map{}, cal, epi, s, PIFU_PREC_FP32);
+}
+
+int pifu_surrogate_query(pifu_ctx* ctx, const pifu_fmap* occ_map, const float calib[12],
+                         const float* pts_dev, int64_t m, float* occ_dev, int precision,
+                         void* stream) {
+    if (!ctx || !calib || m < 0 || !map_ok(occ_map)) return PIFU_ERR_ARG;
+    if (!ctx->sur.ready) return PIFU_ERR_STATE;
+    if (m == 0) return PIFU_OK;
+    if (!pts_dev || !occ_dev) return PIFU_ERR_ARG;
+    if (precision != PIFU_PREC_FP32 && precision != PIFU_PREC_BF16) return PIFU_ERR_UNSUPPORTED;
+    if (precision == PIFU_PREC_BF16 && !ctx->snet.tc_ok) return PIFU_ERR_UNSUPPORTED;
+    if (occ_map->dtype != PIFU_F32) return PIFU_ERR_UNSUPPORTED;
+    if (ctx->snet.d_in != occ_map->C + 1) return PIFU_ERR_ARG;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return PIFU_ERR_CUDA;
+    PointSrc src{PTS_XYZ, pts_dev, nullptr, 0, 0, nullptr};
+    Epilogue epi{};
+    epi.mode = EPI_STORE;
+    epi.act = ACT_SIGMOID;
+    epi.out = occ_dev;
+    return run_mlp(ctx, ctx->snet, src, m, to_map(occ_map), Map{}, to_calib(calib), epi,
+                   static_cast<cudaStream_t>(stream), precision);
+}
+
+int pifu_surrogate_grad(pifu_ctx* ctx, const float* x_dev, const float* y_dev, int64_t B,
+                        float* grad_host, double* loss_host, void* stream) {
+    if (!ctx || !x_dev || !y_dev || B < 1 || B > (1 << 20)) return PIFU_ERR_ARG;
+    if (!ctx->sur.ready) return PIFU_ERR_STATE;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return PIFU_ERR_CUDA;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int st = sur_batch_ws(ctx, (int)B);
+    if (st != PIFU_OK) return st;
+    CK(cudaMemsetAsync(ctx->sur.d_loss, 0, sizeof(double), s));
+    st = sur_grad(ctx, x_dev, y_dev, (int)B, s);
+    if (st != PIFU_OK) return st;
+    CK(cudaMemcpyAsync(ctx->sur.h_loss, ctx->sur.d_loss, sizeof(double), cudaMemcpyDeviceToHost, s));
+    std::vector<float> gp((size_t)ctx->sur.n);
+    CK(cudaMemcpyAsync(gp.data(), ctx->sur.grads, (size_t)ctx->sur.n * 4, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (grad_host) sur_pack(ctx, gp, grad_host);
+    if (loss_host) *loss_host = *ctx->sur.h_loss;
+    return PIFU_OK;
+}
+
+int pifu_surrogate_train(pifu_ctx* ctx, const float* x_dev, const float* y_dev, int64_t m,
+                         int batch, int steps, float lr, double* loss_host, void* stream) {
+    if (!ctx || !x_dev || !y_dev || m < 1 || batch < 1 || batch > (1 << 20) || steps < 0 ||
+        !(lr > 0.f))
+        return PIFU_ERR_ARG;
+    if (!ctx->sur.ready) return PIFU_ERR_STATE;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return PIFU_ERR_CUDA;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    auto& S = ctx->sur;
+    const int B = (int)std::min<int64_t>(batch, m);
+    int st = sur_batch_ws(ctx, B);
+    if (st != PIFU_OK) return st;
+    const int64_t nb = m / B;   // whole batches; the samples are already in random order
+    double first = 0.0;
+    for (int it = 0; it < steps; ++it) {
+        const int64_t b0 = (int64_t)(it % nb) * B;
+        CK(cudaMemsetAsync(S.d_loss, 0, sizeof(double), s));
+        st = sur_grad(ctx, x_dev + b0 * ctx->snet.ldx, y_dev + b0, B, s);
+        if (st != PIFU_OK) return st;
+        CK(launch_adam(S.n, S.params, S.grads, S.adam_m, S.adam_v, lr, ++S.step, s));
+        if (it == 0) {
+            CK(cudaMemcpyAsync(S.h_loss, S.d_loss, sizeof(double), cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            first = *S.h_loss;
+        }
+    }
+    CK(cudaMemcpyAsync(S.h_loss, S.d_loss, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (loss_host) {
+        loss_host[0] = first;
+        loss_host[1] = *S.h_loss;
+    }
+    return sur_build_tc(ctx);   // inference form follows the new parameters
+}
+
+int pifu_surrogate_params(pifu_ctx* ctx, float* host, int64_t n, int set) {
+    if (!ctx) return PIFU_ERR_ARG;
+    if (!ctx->sur.ready) return PIFU_ERR_STATE;
+    if (!host || n != sur_unpadded_count(ctx)) return PIFU_ERR_ARG;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return PIFU_ERR_CUDA;
+    std::vector<float> p;
+    if (set) {
+        sur_unpack(ctx, host, p);
+        CK(cudaMemcpy(ctx->sur.params, p.data(), (size_t)ctx->sur.n * 4, cudaMemcpyHostToDevice));
+        return sur_build_tc(ctx);
+    }
+    p.resize((size_t)ctx->sur.n);
+    CK(cudaMemcpy(p.data(), ctx->sur.params, (size_t)ctx->sur.n * 4, cudaMemcpyDeviceToHost));
+    sur_pack(ctx, p, host);
     return PIFU_OK;
 }
 

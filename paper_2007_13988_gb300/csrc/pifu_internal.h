@@ -161,6 +161,24 @@ cudaError_t tc_prepare();
 bool tc_encode_2d_bf16(void* map, const void* base, uint64_t cols, uint64_t rows,
                        uint64_t row_stride_bytes, uint32_t box_cols, uint32_t box_rows);
 
+// --- train.cu --------------------------------------------------------------
+// C[m][n] (+)= sum_k A(m, k) B(k, n), A(m, k) = A[m a_m + k a_k],
+// B(k, n) = B[k b_k + n b_n], C row stride c_m; the reduction is split into
+// k_slices slices accumulated with atomicAdd (C must then start at zero).
+cudaError_t launch_gemm_strided(int M, int N, int K, const float* A, int64_t a_m, int64_t a_k,
+                                const float* B, int64_t b_k, int64_t b_n, float* C, int64_t c_m,
+                                int k_slices, int accumulate, cudaStream_t s);
+cudaError_t launch_bias_lrelu(int M, int N, float* Z, int ld, const float* bias, float slope,
+                              cudaStream_t s);
+// g[b] = (sigmoid(logit[b] + bias) - y[b]) / B; *loss += mean BCE.
+cudaError_t launch_bce_grad(int B, const float* logit, const float* bias, const float* y, float* g,
+                            double* loss, cudaStream_t s);
+cudaError_t launch_lrelu_backward(int64_t n, float* dH, const float* H, float slope,
+                                  cudaStream_t s);
+cudaError_t launch_adam(int64_t n, float* w, const float* g, float* m, float* v, float lr, int t,
+                        cudaStream_t s);
+cudaError_t launch_fill(int64_t n, float* p, float value, cudaStream_t s);
+
 // --- localize.cu -----------------------------------------------------------
 __host__ __device__ inline int row_words_of(int N) { return (N + 1 + 31) / 32; }
 __host__ __device__ inline int64_t words_of(int N) {

@@ -36,7 +36,8 @@ PIFU_PREC_MIXED = 2
 EXPORTS = ("pifu_create", "pifu_destroy", "pifu_query", "pifu_query_colour", "pifu_localize",
            "pifu_render", "pifu_sync_stats", "pifu_status_string", "pifu_last_error",
            "pifu_profile", "pifu_profile_read", "pifu_query_noalloc", "pifu_query_ex",
-           "pifu_frame")
+           "pifu_frame", "pifu_surrogate_init", "pifu_surrogate_samples", "pifu_surrogate_grad",
+           "pifu_surrogate_train", "pifu_surrogate_params", "pifu_surrogate_query")
 
 KERNEL_CLASSES = ("gather", "mlp_hidden", "mlp_last", "level", "select", "render", "mlp_f32")
 
@@ -49,7 +50,8 @@ class pifu_fmap(ctypes.Structure):
 class pifu_levels(ctypes.Structure):
     _fields_ = [("n0", ctypes.c_int32), ("num_levels", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("max_rounds", ctypes.c_int32),
-                ("margin", ctypes.c_float)]
+                ("margin", ctypes.c_float), ("use_surrogate", ctypes.c_int32),
+                ("surrogate_margin", ctypes.c_float)]
 
 
 class pifu_camera(ctypes.Structure):
@@ -65,6 +67,7 @@ class pifu_volume(ctypes.Structure):
                 ("evals_per_level", ctypes.c_int64 * 8),
                 ("candidates_per_level", ctypes.c_int64 * 8),
                 ("rechecked_per_level", ctypes.c_int64 * 8),
+                ("fallback_per_level", ctypes.c_int64 * 8),
                 ("conflict_rounds", ctypes.c_int32 * 8)]
 
 
@@ -121,6 +124,21 @@ def _lib():
                                ctypes.POINTER(F), ctypes.POINTER(pifu_levels),
                                ctypes.POINTER(pifu_camera), P, P, P, P, ctypes.POINTER(pifu_volume)]
     lib.pifu_frame.restype = I
+    U64, D = ctypes.c_uint64, ctypes.c_double
+    lib.pifu_surrogate_init.argtypes = [P, I, I, U64]
+    lib.pifu_surrogate_init.restype = I
+    lib.pifu_surrogate_samples.argtypes = [P, ctypes.POINTER(pifu_fmap), ctypes.POINTER(F), P, I64,
+                                           P, P, P]
+    lib.pifu_surrogate_samples.restype = I
+    lib.pifu_surrogate_query.argtypes = [P, ctypes.POINTER(pifu_fmap), ctypes.POINTER(F), P, I64,
+                                         P, I, P]
+    lib.pifu_surrogate_query.restype = I
+    lib.pifu_surrogate_grad.argtypes = [P, P, P, I64, ctypes.POINTER(F), ctypes.POINTER(D), P]
+    lib.pifu_surrogate_grad.restype = I
+    lib.pifu_surrogate_train.argtypes = [P, P, P, I64, I, I, F, ctypes.POINTER(D), P]
+    lib.pifu_surrogate_train.restype = I
+    lib.pifu_surrogate_params.argtypes = [P, ctypes.POINTER(F), I64, I]
+    lib.pifu_surrogate_params.restype = I
     lib.pifu_sync_stats.argtypes = [P, ctypes.POINTER(pifu_volume)]
     lib.pifu_sync_stats.restype = I
     lib.pifu_status_string.argtypes = [I]
@@ -252,9 +270,11 @@ def pifu_query_colour(ctx, occ_map, col_map, calib, pts, out, stream=None):
 
 
 def pifu_localize(ctx, occ_map, calib, n0, num_levels, precision=PIFU_PREC_FP32,
-                  max_rounds=0, margin=0.02, stream=None) -> pifu_volume:
+                  max_rounds=0, margin=0.02, use_surrogate=False, surrogate_margin=0.1,
+                  stream=None) -> pifu_volume:
     fm = fmap(occ_map)
-    lv = pifu_levels(n0, num_levels, precision, max_rounds, margin)
+    lv = pifu_levels(n0, num_levels, precision, max_rounds, margin, 1 if use_surrogate else 0,
+                     surrogate_margin)
     vol = pifu_volume()
     st = _lib().pifu_localize(ctx, ctypes.byref(fm), _calib(calib), ctypes.byref(lv),
                               _stream(stream), ctypes.byref(vol))
@@ -279,7 +299,7 @@ def pifu_frame(ctx, occ_map, col_map, calib, n0, num_levels, width, height, dept
     """Localization + render of one frame as a (cached) CUDA graph."""
     fo = fmap(occ_map)
     fc = fmap(col_map)
-    lv = pifu_levels(n0, num_levels, precision, max_rounds, margin)
+    lv = pifu_levels(n0, num_levels, precision, max_rounds, margin, 0, 0.0)
     cam = pifu_camera(width, height, (ctypes.c_float * 3)(*background), PIFU_PREC_BF16)
     vol = pifu_volume()
     st = _lib().pifu_frame(ctx, ctypes.byref(fo), ctypes.byref(fc) if fc else None, _calib(calib),
@@ -287,6 +307,60 @@ def pifu_frame(ctx, occ_map, col_map, calib, n0, num_levels, width, height, dept
                            _ptr(rgb), _ptr(mask), ctypes.byref(vol))
     _check(st, "pifu_frame", ctx)
     return vol
+
+
+def pifu_surrogate_init(ctx, h1=128, h2=64, seed=0):
+    _check(_lib().pifu_surrogate_init(ctx, h1, h2, seed), "pifu_surrogate_init", ctx)
+
+
+def pifu_surrogate_samples(ctx, occ_map, calib, pts, x_out, o_out, stream=None):
+    """Distillation tuples: x_out [m][row width of f_O] gathered rows, o_out [m]
+    f_O's FP32 occupancy at the points."""
+    fm = fmap(occ_map)
+    st = _lib().pifu_surrogate_samples(ctx, ctypes.byref(fm), _calib(calib), _ptr(pts),
+                                       pts.shape[0], _ptr(x_out), _ptr(o_out), _stream(stream))
+    _check(st, "pifu_surrogate_samples", ctx)
+
+
+def pifu_surrogate_query(ctx, occ_map, calib, pts, out, precision=PIFU_PREC_FP32, stream=None):
+    fm = fmap(occ_map)
+    st = _lib().pifu_surrogate_query(ctx, ctypes.byref(fm), _calib(calib), _ptr(pts),
+                                     pts.shape[0], _ptr(out), precision, _stream(stream))
+    _check(st, "pifu_surrogate_query", ctx)
+    return out
+
+
+def surrogate_param_count(h1, h2, d_in):
+    return h1 * d_in + h1 + h2 * h1 + h2 + h2 + 1
+
+
+def pifu_surrogate_grad(ctx, x, y, n_params, stream=None):
+    """(loss, gradient in the unpadded parameter layout) of one batch."""
+    g = (ctypes.c_float * n_params)()
+    loss = ctypes.c_double()
+    st = _lib().pifu_surrogate_grad(ctx, _ptr(x), _ptr(y), x.shape[0], g, ctypes.byref(loss),
+                                    _stream(stream))
+    _check(st, "pifu_surrogate_grad", ctx)
+    return loss.value, np.frombuffer(g, dtype=np.float32).copy()
+
+
+def pifu_surrogate_train(ctx, x, y, batch=4096, steps=1000, lr=1e-3, stream=None):
+    """Adam steps over consecutive batches; returns (first, last) batch loss."""
+    loss = (ctypes.c_double * 2)()
+    st = _lib().pifu_surrogate_train(ctx, _ptr(x), _ptr(y), x.shape[0], batch, steps, lr, loss,
+                                     _stream(stream))
+    _check(st, "pifu_surrogate_train", ctx)
+    return loss[0], loss[1]
+
+
+def pifu_surrogate_params(ctx, n_params, values=None):
+    """Get (values None) or set the surrogate's parameters (unpadded layout)."""
+    buf = (ctypes.c_float * n_params)()
+    if values is not None:
+        buf[:] = np.asarray(values, np.float32).tolist()
+    st = _lib().pifu_surrogate_params(ctx, buf, n_params, 0 if values is None else 1)
+    _check(st, "pifu_surrogate_params", ctx)
+    return None if values is not None else np.frombuffer(buf, dtype=np.float32).copy()
 
 
 def pifu_sync_stats(ctx) -> pifu_volume:

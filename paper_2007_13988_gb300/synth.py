@@ -259,6 +259,24 @@ def calib_yaw(deg: float, scale: float = 1.0) -> np.ndarray:
     return c.astype(np.float32)
 
 
+def distill_points(fig: Figure, n: int, seed: int, near_frac: float = 0.5,
+                   sigma: float = 0.02) -> np.ndarray:
+    """Training points for distillation: a fraction near the figure's surface
+    (a point on a random capsule's surface plus N(0, sigma) jitter, the
+    importance sampling PIFu trains with) and the rest uniform in [-1, 1]^3."""
+    rng = np.random.default_rng(seed)
+    n_near = int(n * near_frac)
+    k = rng.integers(0, len(fig.r), n_near)
+    t = rng.uniform(0, 1, n_near)[:, None]
+    axis = fig.a[k] + t * (fig.b[k] - fig.a[k])
+    u = rng.standard_normal((n_near, 3))
+    u /= np.linalg.norm(u, axis=1, keepdims=True)
+    near = axis + fig.r[k][:, None] * u + rng.normal(0, sigma, (n_near, 3))
+    uni = rng.uniform(-1, 1, (n - n_near, 3))
+    P = np.concatenate([near, uni], 0)
+    return np.clip(P[rng.permutation(n)], -1, 1).astype(np.float32)
+
+
 def query_points(n: int, seed: int) -> np.ndarray:
     """n points uniform in [-1, 1]^3, float32 [n, 3]."""
     rng = np.random.default_rng(seed)
