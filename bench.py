@@ -51,6 +51,11 @@ def parse_args():
     ap.add_argument("--query-points", type=int, default=1 << 20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
+    ap.add_argument("--surrogate", choices=("on", "off"), default="on",
+                    help="learned f_S at the coarse levels (trained before the timed region)")
+    ap.add_argument("--sur-figures", type=int, default=64)
+    ap.add_argument("--sur-tuples", type=int, default=10_000_000)
+    ap.add_argument("--sur-steps", type=int, default=6000)
     return ap.parse_args()
 
 
@@ -183,7 +188,7 @@ def oracle_frame(w, keep=False):
                                     w.calib)
     dt = time.perf_counter() - t0
     counts = {"evals": int(sum(l.n_eval for l in lv)), "hits": int(np.count_nonzero(hit))}
-    return (dt, counts, lv) if keep else (dt, counts)
+    return (dt, counts, (lv, rgb, hit)) if keep else (dt, counts)
 
 
 def run_reference(args, rank, world):
@@ -267,15 +272,16 @@ class Frame:
             self.flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
         stream.synchronize()
 
-    def run(self, prec, form="graph", margin=0.02):
+    def run(self, prec, form="graph", margin=0.02, sur_margin=None):
         w, p = self.w, self.pifu
+        sur = {} if sur_margin is None else {"use_surrogate": True, "surrogate_margin": sur_margin}
         if form == "graph" and prec != 0:
             # one CUDA graph per frame (captured on the first call)
             return p.pifu_frame(self.ctx, self.occ, self.col, w.calib, w.n0, w.num_levels,
                                 w.render, w.render, self.depth, self.rgb, self.mask,
-                                precision=prec, margin=margin, stream=self.stream)
+                                precision=prec, margin=margin, stream=self.stream, **sur)
         vol = p.pifu_localize(self.ctx, self.occ, w.calib, w.n0, w.num_levels, precision=prec,
-                              margin=margin, stream=self.stream)
+                              margin=margin, stream=self.stream, **sur)
         p.pifu_render(self.ctx, w.render, w.render, self.occ, self.col, w.calib, self.depth,
                       self.rgb, self.mask, precision=1 if prec != 0 else 0, stream=self.stream)
         return vol
@@ -284,12 +290,12 @@ class Frame:
         self.pifu.pifu_destroy(self.ctx)
 
 
-def time_form(fr, prec, steps, warmup, world, clocks=None, form="graph"):
+def time_form(fr, prec, steps, warmup, world, clocks=None, form="graph", sur_margin=None):
     """Device-timed frames of one precision form; returns a dict."""
     import torch
     vol = None
     for _ in range(max(1, warmup)):
-        vol = fr.run(prec, form)
+        vol = fr.run(prec, form, sur_margin=sur_margin)
     fr.stream.synchronize()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(steps)]
@@ -301,7 +307,7 @@ def time_form(fr, prec, steps, warmup, world, clocks=None, form="graph"):
         with torch.cuda.stream(fr.stream):
             fr.flush.zero_()
         ev[i][0].record(fr.stream)
-        vol = fr.run(prec, form)
+        vol = fr.run(prec, form, sur_margin=sur_margin)
         ev[i][1].record(fr.stream)
     torch.cuda.synchronize()
     prof = fr.pifu.pifu_profile_read(fr.ctx)
@@ -315,11 +321,39 @@ def time_form(fr, prec, steps, warmup, world, clocks=None, form="graph"):
         t = torch.tensor([total_s], device=fr.dev)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         total_s = float(t.item())
+    L = vol.num_levels
     return {"value": world * steps / total_s, "ms_per_step": 1000.0 * total_s / steps,
             "step_ms": step_ms, "prof": prof, "clocks": clk, "vol": vol,
             "evals": int(vol.n_eval),
-            "rechecked": int(sum(vol.rechecked_per_level[i] for i in range(vol.num_levels))),
+            "rechecked": int(sum(vol.rechecked_per_level[i] for i in range(L))),
+            "fallback": int(sum(vol.fallback_per_level[i] for i in range(L))),
+            "coarse_evals": int(sum(vol.evals_per_level[i] for i in range(L - 1))),
+            "evals_per_level": [int(vol.evals_per_level[i]) for i in range(L)],
+            "rounds": [int(vol.conflict_rounds[i]) for i in range(L)],
             "hits": int(fr.mask.sum().item())}
+
+
+def train_surrogate(fr, args):
+    """Distil f_S from f_O on the GPU (the library's own training kernels),
+    before any timed region; returns (margin, report)."""
+    import torch
+    from paper_2007_13988_gb300 import distill
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    per = max(1, args.sur_tuples // args.sur_figures)
+    x, y = distill.build_samples(fr.ctx, n_figures=args.sur_figures, per_figure=per, seed0=1000)
+    first, last = distill.train(fr.ctx, x, y, steps=args.sur_steps, batch=4096, lr=3e-3)
+    n = int(x.shape[0])
+    del x, y
+    torch.cuda.empty_cache()
+    margin, disagree = distill.calibrate_margin(fr.ctx, seeds=[2000, 2001], per_figure=200000)
+    torch.cuda.synchronize()
+    return margin, {"net": "257-128-64-1 (leaky-ReLU, sigmoid); BF16 tensor cores in the frame",
+                    "tuples": n, "figures": args.sur_figures, "steps": args.sur_steps,
+                    "batch": 4096, "lr": 3e-3, "loss_first": first, "loss_last": last,
+                    "margin": margin, "held_out_sign_disagreement": disagree,
+                    "train_s": time.perf_counter() - t0,
+                    "levels": "all but the finest (the finest level always runs f_O)"}
 
 
 def run_ours(args, rank, world, local_rank):
@@ -337,11 +371,18 @@ def run_ours(args, rank, world, local_rank):
     R = w.render
     prec = PREC[args.precision]
 
+    # ---- the learned surrogate, distilled before any timed region ----------
+    sur_margin, sur_report = None, None
+    if args.surrogate == "on" and prec != 0:
+        sur_margin, sur_report = train_surrogate(fr, args)
+
     # ---- headline form: device-resident timed region -----------------------
     form = args.form if prec != 0 else "host"
     head = time_form(fr, prec, args.steps, args.warmup, world,
-                     ClockSampler(local_rank, enabled=not args.no_clocks), form=form)
+                     ClockSampler(local_rank, enabled=not args.no_clocks), form=form,
+                     sur_margin=sur_margin)
     head_rgb = fr.rgb.cpu().numpy()
+    head_mask = fr.mask.cpu().numpy()
     head_b, head_vals = None, None
     if rank == 0:
         hv = head["vol"]
@@ -354,7 +395,12 @@ def run_ours(args, rank, world, local_rank):
     # classes of the same frame are timed on its host-driven form ------------
     prof_run = head
     if form == "graph":
-        prof_run = time_form(fr, prec, max(3, min(args.steps, 10)), 1, world, form="host")
+        prof_run = time_form(fr, prec, max(3, min(args.steps, 10)), 1, world, form="host",
+                             sur_margin=sur_margin)
+    # ---- the same form without the surrogate --------------------------------
+    no_sur = None
+    if sur_margin is not None:
+        no_sur = time_form(fr, prec, max(3, min(args.steps, 10)), 2, world, form=form)
     # ---- the plain FP32 form on the same GPU, for the speedup ---------------
     plain = None
     if prec != 0 and not args.no_plain:
@@ -399,7 +445,7 @@ def run_ours(args, rank, world, local_rank):
         with torch.cuda.stream(stream):
             fr.occ.copy_(h_occ, non_blocking=True)
             fr.col.copy_(h_col, non_blocking=True)
-        fr.run(prec, form)
+        fr.run(prec, form, sur_margin=sur_margin)
         with torch.cuda.stream(stream):
             h_depth.copy_(fr.depth, non_blocking=True)
             h_rgb.copy_(fr.rgb, non_blocking=True)
@@ -470,6 +516,19 @@ def run_ours(args, rank, world, local_rank):
     if prec == 2:
         line["config"]["margin"] = 0.02
         line["config"]["rechecked_per_frame"] = head["rechecked"]
+    line["config"]["surrogate"] = sur_margin is not None
+    line["config"]["evals_per_level"] = head["evals_per_level"]
+    line["config"]["conflict_rounds"] = head["rounds"]
+    if sur_report is not None:
+        sur_report["fallback_per_frame"] = head["fallback"]
+        sur_report["coarse_evals_per_frame"] = head["coarse_evals"]
+        sur_report["fallback_fraction"] = head["fallback"] / max(1, head["coarse_evals"])
+        line["surrogate"] = sur_report
+    if no_sur is not None:
+        line["without_surrogate"] = {"value": no_sur["value"], "ms_per_step": no_sur["ms_per_step"],
+                                     "evals_per_level": no_sur["evals_per_level"],
+                                     "conflict_rounds": no_sur["rounds"],
+                                     "speedup_of_headline": head["value"] / no_sur["value"]}
     if plain is not None:
         line["plain_fp32"] = {"value": plain["value"], "ms_per_step": plain["ms_per_step"],
                               "query_pts_per_s": q_plain,
@@ -481,7 +540,7 @@ def run_ours(args, rank, world, local_rank):
     if head["clocks"] is not None:
         line["clocks"] = head["clocks"]
     if world == 1 and not args.no_cpu_baseline:
-        t, cnt, lv = oracle_frame(w, keep=True)
+        t, cnt, (lv, o_rgb, o_hit) = oracle_frame(w, keep=True)
         line["cpu_baseline"] = {"value": 1.0 / t, "unit": UNIT, "cores": cpu_threads(),
                                 "kind": "oracle",
                                 "sample": f"one full frame of the FP64 oracle (numpy): "
@@ -491,6 +550,14 @@ def run_ours(args, rank, world, local_rank):
         acc = line.setdefault("accuracy", {})
         acc["iou_vs_oracle"] = metrics.iou(head_b, lv[-1].binary)
         acc["chamfer_vox_vs_oracle"] = metrics.chamfer_voxels(head_vals, lv[-1].values)
+        # colour at the pixels both renders hit (silhouette pixels that one of
+        # them misses are counted apart)
+        h_hit = head_mask.astype(bool)
+        both = h_hit & o_hit
+        d = head_rgb.astype(np.float64)[both] - o_rgb[both]
+        mse = float(np.mean(d * d)) if d.size else 0.0
+        acc["colour_psnr_vs_oracle_db"] = float("inf") if mse == 0 else 10 * np.log10(1.0 / mse)
+        acc["mask_disagreement_px"] = int(np.count_nonzero(h_hit != o_hit))
     print(json.dumps(line), flush=True)
 
 

@@ -62,6 +62,9 @@ struct FrameKey {
     float calib[12];
     int n0, num_levels, precision, max_rounds;
     float margin;
+    int use_surrogate;
+    float sur_margin;
+    uint64_t sur_version;          // f_S's tensor-core weights are rebuilt on change
     int width, height, cam_precision;
     float bg[3];
     float* depth;
@@ -74,6 +77,7 @@ struct GraphStats {
     unsigned long long evals[8];
     unsigned long long cands[8];
     unsigned long long rechecked[8];
+    unsigned long long fallback[8];
     unsigned int rounds[8];
     unsigned int err;
     unsigned int pad;
@@ -199,6 +203,7 @@ struct pifu_ctx {
         float* adam_v = nullptr;
         int step = 0;
         int batch_cap = 0;
+        uint64_t version = 0;          // bumped whenever the BF16 form is rebuilt
         float *H1 = nullptr, *H2 = nullptr, *logit = nullptr, *g = nullptr, *dH1 = nullptr,
               *dH2 = nullptr, *ones = nullptr;
         double* d_loss = nullptr;
@@ -809,6 +814,7 @@ void sur_bind(pifu_ctx* ctx) {
 int sur_build_tc(pifu_ctx* ctx) {
     auto& S = ctx->sur;
     DevNet& n = ctx->snet;
+    ++S.version;
     for (auto& T : n.tc) dev_free(T.W);
     n.tc.clear();
     std::vector<float> p((size_t)S.n);
@@ -970,9 +976,28 @@ void sur_unpack(const pifu_ctx* ctx, const float* in, std::vector<float>& padded
 
 // One evaluation batch in the graph: BF16 on the tensor cores, and for MIXED
 // the FP32 re-evaluation of the queued near-0.5 occupancies (device-sized).
+// With `sur`, f_S runs first and f_O takes the occupancies f_S put within
+// `sur_margin` of 0.5 (a device-sized queue; *fallback += its length).
 int g_eval(pifu_ctx* ctx, const DevNet& net, const PointSrc& src, int64_t cap,
            const unsigned int* m_dev, const Map& map, const Calib& cal, const Epilogue& epi,
-           int prec, float margin, unsigned long long* rechecked, cudaStream_t s) {
+           int prec, float margin, unsigned long long* rechecked, cudaStream_t s,
+           bool sur = false, float sur_margin = 0.f, unsigned long long* fallback = nullptr) {
+    if (sur) {
+        CK(cudaMemsetAsync(ctx->d_squeue, 0, sizeof(unsigned int), s));
+        Epilogue es = epi;
+        es.recheck = ctx->squeue;
+        es.recheck_count = ctx->d_squeue;
+        es.margin = sur_margin;
+        int st = run_mlp_tc(ctx, ctx->snet, src, cap, map, Map{}, cal, es, s, m_dev);
+        if (st != PIFU_OK) return st;
+        // a queue longer than one device-sized batch latches a capacity error
+        const int64_t qcap = std::min<int64_t>(cap, kChunkTC);
+        CK(launch_accumulate(fallback, ctx->d_squeue, (unsigned)qcap, ctx->d_count + 1, s));
+        PointSrc sf{PTS_LIST, nullptr, ctx->squeue, 0, src.N, nullptr};
+        Epilogue ef = epi;
+        ef.list = ctx->squeue;
+        return g_eval(ctx, net, sf, qcap, ctx->d_squeue, map, cal, ef, prec, margin, rechecked, s);
+    }
     if (prec == PIFU_PREC_BF16) return run_mlp_tc(ctx, net, src, cap, map, Map{}, cal, epi, s, m_dev);
     CK(cudaMemsetAsync(ctx->d_recheck, 0, sizeof(unsigned int), s));
     Epilogue e1 = epi;
@@ -1040,7 +1065,8 @@ int g_enqueue_frame(pifu_ctx* ctx, const FrameKey& k, const Map& occ, const Map&
         epi.mode = EPI_LEVEL;
         epi.lv = LevelBits{ctx->values, ctx->tent, ctx->bin[cur], ctx->conf[0], N, row_words_of(N), 1};
         st = g_eval(ctx, net, src, nodes, nullptr, occ, cal, epi, k.precision, k.margin,
-                    &gs->rechecked[0], s);
+                    &gs->rechecked[0], s, k.use_surrogate && k.num_levels > 1, k.sur_margin,
+                    &gs->fallback[0]);
         if (st != PIFU_OK) return st;
     }
     for (int l = 1; l < k.num_levels; ++l) {
@@ -1076,7 +1102,9 @@ int g_enqueue_frame(pifu_ctx* ctx, const FrameKey& k, const Map& occ, const Map&
                      ? PIFU_OK : PIFU_ERR_CUDA;
             if (st == PIFU_OK)
                 st = g_eval(ctx, net, src, kChunkTC, ctx->d_count, occ, cal, epi, k.precision,
-                            k.margin, &gs->rechecked[l], sb);
+                            k.margin, &gs->rechecked[l], sb,
+                            k.use_surrogate && l < k.num_levels - 1, k.sur_margin,
+                            &gs->fallback[l]);
             if (st == PIFU_OK && cudaMemsetAsync(ctx->d_count, 0, sizeof(unsigned int), sb) != cudaSuccess)
                 st = PIFU_ERR_CUDA;
             if (st == PIFU_OK && launch_dilate_select(ctx->conf[0], ctx->eval, nullptr, N, ctx->list,
@@ -1571,7 +1599,10 @@ int pifu_frame(pifu_ctx* ctx, const pifu_fmap* occ_map, const pifu_fmap* col_map
     if (lv->precision != PIFU_PREC_BF16 && lv->precision != PIFU_PREC_MIXED) return PIFU_ERR_UNSUPPORTED;
     if (lv->precision == PIFU_PREC_MIXED && !(lv->margin >= 0.f && lv->margin <= 0.5f))
         return PIFU_ERR_ARG;
-    if (lv->use_surrogate) return PIFU_ERR_UNSUPPORTED;   // host-driven form only
+    if (lv->use_surrogate) {
+        if (!ctx->sur.ready || !ctx->snet.tc_ok) return PIFU_ERR_STATE;
+        if (!(lv->surrogate_margin >= 0.f && lv->surrogate_margin <= 0.5f)) return PIFU_ERR_ARG;
+    }
     if (occ_map->dtype != PIFU_F32 || (col_map && col_map->dtype != PIFU_F32)) return PIFU_ERR_UNSUPPORTED;
     if (ctx->net[0].d_in != occ_map->C + 1) return PIFU_ERR_ARG;
     if (!ctx->net[0].tc_ok) return PIFU_ERR_UNSUPPORTED;
@@ -1601,6 +1632,11 @@ int pifu_frame(pifu_ctx* ctx, const pifu_fmap* occ_map, const pifu_fmap* col_map
     k.precision = lv->precision;
     k.max_rounds = lv->max_rounds > 0 ? lv->max_rounds : 4096;
     k.margin = lv->precision == PIFU_PREC_MIXED ? lv->margin : 0.f;
+    if (lv->use_surrogate) {
+        k.use_surrogate = 1;
+        k.sur_margin = lv->surrogate_margin;
+        k.sur_version = ctx->sur.version;
+    }
     k.width = cam->width;
     k.height = cam->height;
     k.cam_precision = cam->precision;
@@ -1634,6 +1670,7 @@ int pifu_frame(pifu_ctx* ctx, const pifu_fmap* occ_map, const pifu_fmap* col_map
             launches += ctx->g_launches_body[l] * (int64_t)(gs.rounds[l] + 1);
         }
         vs.rechecked_per_level[l] = (int64_t)gs.rechecked[l];
+        vs.fallback_per_level[l] = (int64_t)gs.fallback[l];
     }
     ctx->prof.k[PIFU_K_MLP_HIDDEN].launches += launches;   // graph: counted in one class
     const int cur = (lv->num_levels - 1) & 1;

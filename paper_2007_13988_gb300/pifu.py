@@ -295,11 +295,13 @@ def pifu_render(ctx, width, height, occ_map, col_map, calib, depth=None, rgb=Non
 
 def pifu_frame(ctx, occ_map, col_map, calib, n0, num_levels, width, height, depth=None, rgb=None,
                mask=None, precision=PIFU_PREC_MIXED, margin=0.02, max_rounds=0,
-               background=(0.0, 0.0, 0.0), stream=None) -> pifu_volume:
+               background=(0.0, 0.0, 0.0), stream=None, use_surrogate=False,
+               surrogate_margin=0.0) -> pifu_volume:
     """Localization + render of one frame as a (cached) CUDA graph."""
     fo = fmap(occ_map)
     fc = fmap(col_map)
-    lv = pifu_levels(n0, num_levels, precision, max_rounds, margin, 0, 0.0)
+    lv = pifu_levels(n0, num_levels, precision, max_rounds, margin, int(bool(use_surrogate)),
+                     surrogate_margin)
     cam = pifu_camera(width, height, (ctypes.c_float * 3)(*background), PIFU_PREC_BF16)
     vol = pifu_volume()
     st = _lib().pifu_frame(ctx, ctypes.byref(fo), ctypes.byref(fc) if fc else None, _calib(calib),

@@ -126,3 +126,33 @@ def test_surrogate_localization_gain(full, trained):
     assert iou >= 0.995
     # the gain: far fewer full-network evaluations at the coarse levels
     assert fallback < 0.5 * coarse_fo
+
+
+def test_surrogate_graph_frame_matches_host_path(full, trained):
+    """The graph form runs the same f_S / f_O decisions as the host-driven
+    form (device-sized fall-back queue instead of a host read)."""
+    import torch
+    first, last, margin, disagree = trained
+    w = full.w
+    host = full.localize(precision=pifu.PIFU_PREC_MIXED, use_surrogate=True,
+                         surrogate_margin=margin)
+    hb, he, hv = full.volume_host(host)
+    h_fallback = [int(host.fallback_per_level[i]) for i in range(w.num_levels)]
+    h_evals = [int(host.evals_per_level[i]) for i in range(w.num_levels)]
+    R = 512
+    depth = torch.empty((R, R), dtype=torch.float32, device="cuda")
+    rgb = torch.empty((R, R, 3), dtype=torch.float32, device="cuda")
+    mask = torch.empty((R, R), dtype=torch.uint8, device="cuda")
+    vol = pifu.pifu_frame(full.ctx, full.occ, full.col, w.calib, w.n0, w.num_levels, R, R,
+                          depth, rgb, mask, precision=pifu.PIFU_PREC_MIXED,
+                          use_surrogate=True, surrogate_margin=margin)
+    torch.cuda.synchronize()
+    gb, ge, gv = full.volume_host(vol)
+    assert [int(vol.fallback_per_level[i]) for i in range(w.num_levels)] == h_fallback
+    assert [int(vol.evals_per_level[i]) for i in range(w.num_levels)] == h_evals
+    assert h_fallback[-1] == 0          # the finest level never uses f_S
+    assert np.array_equal(gb, hb) and np.array_equal(ge, he)
+    # committed values: BF16 away from 0.5 in both forms, except that the host
+    # form evaluates a fall-back batch of at most 256 points in FP32 outright
+    np.testing.assert_allclose(gv[ge], hv[he], rtol=0, atol=0.03)
+
