@@ -189,7 +189,7 @@ int pifu_render(pifu_ctx* ctx, const pifu_camera* cam, const pifu_fmap* occ_map,
  * each level's conflict loop is a conditional WHILE node.  The stream is
  * synchronised once, at the end, to read the counters into *out.
  * Tensor-core forms only (levels->precision BF16 or MIXED; the colour MLP
- * runs in BF16).  Fixed capacities: 262,144 points per evaluation batch and
+ * runs in BF16).  Fixed capacities: 1,048,576 points per evaluation batch and
  * pixels per render, 8,192 FP32 re-checks per batch; a frame that exceeds one
  * returns PIFU_ERR_CAPACITY (its outputs are then invalid and the
  * host-driven pifu_localize + pifu_render handle it).  Other errors as in

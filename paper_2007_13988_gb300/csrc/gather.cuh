@@ -1,0 +1,121 @@
+// Device-side projection and bilinear sampling of the MLP input row
+// (Eq. 1 / Eq. 2, Sec. 3.1), shared by the gather kernels and the fused FP32
+// MLP kernel so that both assemble bit-identical rows.
+//
+// Precision: the texel coordinate s = u W/2 + (W-1)/2 has magnitude up to
+// W, so computing it in float32 and taking s - floor(s) would leave the
+// bilinear weight with an absolute error of ~ulp(W) (4e-6 at W = 128), which
+// a steep occupancy logit turns into a visible occupancy error.  Instead the
+// projection u = C [P, 1] is evaluated as an unevaluated float-float sum
+// (error-free products and sums) and the weight is formed directly as
+// fma(u_hi, W/2, (W-1)/2 - floor(s)) + u_lo W/2, whose only rounding is at
+// the weight's own magnitude (< 1).
+#pragma once
+
+#include "pifu_internal.h"
+
+namespace pifu {
+
+__device__ __forceinline__ void two_prod(float a, float b, float& p, float& e) {
+    p = __fmul_rn(a, b);
+    e = __fmaf_rn(a, b, -p);
+}
+
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// c0 x + c1 y + c2 z + c3 as hi + lo (|lo| <= ulp(hi) / 2 up to O(eps^2)).
+__device__ __forceinline__ void affine_ff(const float* c, float x, float y, float z,
+                                          float& hi, float& lo) {
+    float s = c[3], err = 0.f, p, e, t;
+    two_prod(c[0], x, p, e); two_sum(s, p, s, t); err = __fadd_rn(err, __fadd_rn(e, t));
+    two_prod(c[1], y, p, e); two_sum(s, p, s, t); err = __fadd_rn(err, __fadd_rn(e, t));
+    two_prod(c[2], z, p, e); two_sum(s, p, s, t); err = __fadd_rn(err, __fadd_rn(e, t));
+    hi = __fadd_rn(s, err);
+    lo = __fsub_rn(err, __fsub_rn(hi, s));
+}
+
+// Texel coordinate s = u W/2 + (W-1)/2 of u = hi + lo: integer part i0 and
+// fractional weight a (accurate to ~1e-7 absolute; may leave [0, 1) by that
+// much when s is within rounding of an integer, which keeps the sample
+// continuous).
+__device__ __forceinline__ void texel_coord(float hi, float lo, int W, int& i0, float& a) {
+    const float hw = 0.5f * (float)W;
+    const float off = hw - 0.5f;
+    const float sl = __fmul_rn(lo, hw);
+    const float s = __fmaf_rn(hi, hw, off);
+    const float fl = floorf(__fadd_rn(s, sl));
+    a = __fadd_rn(__fmaf_rn(hi, hw, __fsub_rn(off, fl)), sl);
+    i0 = (int)fmaxf(fminf(fl, (float)W + 1.f), -2.f);   // NaN -> W + 1 (clamped below)
+}
+
+__device__ __forceinline__ void point_xyz(const PointSrc& src, int64_t p, float& x, float& y,
+                                          float& z) {
+    if (src.mode == PTS_XYZ || src.mode == PTS_XYZ_IDX) {
+        const int64_t q = src.mode == PTS_XYZ ? p : (int64_t)src.list[p];
+        x = src.xyz[3 * q + 0];
+        y = src.xyz[3 * q + 1];
+        z = src.xyz[3 * q + 2];
+        return;
+    }
+    const int64_t idx = (src.mode == PTS_LIST) ? (int64_t)src.list[p] : src.base + p;
+    const int64_t n1 = src.N + 1;
+    const int i = (int)(idx % n1);
+    const int j = (int)((idx / n1) % n1);
+    const int k = (int)(idx / (n1 * n1));
+    const float h = 2.0f / (float)src.N;   // exact for power-of-two N
+    x = __fmaf_rn((float)i, h, -1.0f);
+    y = __fmaf_rn((float)j, h, -1.0f);
+    z = __fmaf_rn((float)k, h, -1.0f);
+}
+
+__device__ __forceinline__ float4 ld4(const float* p) {
+    return __ldg(reinterpret_cast<const float4*>(p));
+}
+
+// Channels c..c+3 of the MLP input row of point p: the bilinear sample of
+// map0 (channels [0, C0)) or map1 ([C0, C0 + C1)) at the point's projection,
+// then the projected depth at C0 + C1, then zero padding.
+__device__ __forceinline__ float4 gather_quad(const PointSrc& src, int64_t p, const Calib& calib,
+                                              const Map& map0, const Map& map1, int c) {
+    float x, y, z;
+    point_xyz(src, p, x, y, z);
+    float uh, ul, vh, vl, zh, zl;
+    affine_ff(calib.c + 0, x, y, z, uh, ul);
+    affine_ff(calib.c + 4, x, y, z, vh, vl);
+    affine_ff(calib.c + 8, x, y, z, zh, zl);
+
+    float4 r;
+    const int C0 = map0.C, C1 = map1.C;
+    if (c < C0 + C1) {
+        const Map& mp = (c < C0) ? map0 : map1;
+        const int cc = (c < C0) ? c : c - C0;
+        int i0, j0;
+        float a, b;
+        texel_coord(uh, ul, mp.W, i0, a);
+        texel_coord(vh, vl, mp.H, j0, b);
+        const int i1 = min(max(i0 + 1, 0), mp.W - 1);
+        const int j1 = min(max(j0 + 1, 0), mp.H - 1);
+        i0 = min(max(i0, 0), mp.W - 1);
+        j0 = min(max(j0, 0), mp.H - 1);
+        const float* F = static_cast<const float*>(mp.data);
+        const float4 f00 = ld4(F + ((int64_t)j0 * mp.W + i0) * mp.C + cc);
+        const float4 f10 = ld4(F + ((int64_t)j0 * mp.W + i1) * mp.C + cc);
+        const float4 f01 = ld4(F + ((int64_t)j1 * mp.W + i0) * mp.C + cc);
+        const float4 f11 = ld4(F + ((int64_t)j1 * mp.W + i1) * mp.C + cc);
+        const float w00 = (1.f - a) * (1.f - b), w10 = a * (1.f - b);
+        const float w01 = (1.f - a) * b, w11 = a * b;
+        r.x = fmaf(w11, f11.x, fmaf(w01, f01.x, fmaf(w10, f10.x, w00 * f00.x)));
+        r.y = fmaf(w11, f11.y, fmaf(w01, f01.y, fmaf(w10, f10.y, w00 * f00.y)));
+        r.z = fmaf(w11, f11.z, fmaf(w01, f01.z, fmaf(w10, f10.z, w00 * f00.z)));
+        r.w = fmaf(w11, f11.w, fmaf(w01, f01.w, fmaf(w10, f10.w, w00 * f00.w)));
+    } else {
+        r = make_float4(c == C0 + C1 ? __fadd_rn(zh, zl) : 0.f, 0.f, 0.f, 0.f);
+    }
+    return r;
+}
+
+}  // namespace pifu

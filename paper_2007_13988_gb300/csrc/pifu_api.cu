@@ -16,8 +16,9 @@ namespace {
 constexpr int kMaxLevels = 8;
 constexpr int kMaxFine = 512;
 constexpr int64_t kChunk = 65536;    // points per FP32 MLP pass (bounds its activation workspace)
-constexpr int64_t kChunkTC = 262144; // points per tensor-core MLP pass (a whole 256^3 level)
-constexpr int64_t kRecheckCap = 8192; // graph form: FP32 re-checks per batch
+constexpr int64_t kChunkTC = 1 << 20; // points per tensor-core MLP pass (a whole 512^3 level list)
+constexpr int64_t kRecheckCap = 8192; // graph form: FP32 re-checks per batch (split-K path)
+constexpr int64_t kFusedMaxM = 2048;   // host-sized FP32 batches up to this size: fused kernel
 constexpr int64_t kTinyBatch = 256; // mixed precision: batches this small run in FP32
 
 struct DevLayer {
@@ -52,6 +53,21 @@ struct DevNet {
 };
 
 int round_up(int v, int m) { return (v + m - 1) / m * m; }
+
+// The fused FP32 kernel's view of a network (nl = 0 if it has too many layers).
+FusedNet fused_of(const DevNet& n) {
+    FusedNet f{};
+    if (n.layers.size() > (size_t)kFusedMaxLayers) return f;
+    f.nl = (int)n.layers.size();
+    f.ldx = n.ldx;
+    f.max_hidden = round_up(std::max(n.max_hidden, 8), 4);
+    f.slope = n.slope;
+    for (int l = 0; l < f.nl; ++l) {
+        const DevLayer& L = n.layers[(size_t)l];
+        f.L[l] = FusedLayer{L.W, L.b, L.n_out, L.K1, L.K2, L.ldw};
+    }
+    return f;
+}
 
 // Everything a captured frame graph depends on; a call with the same key
 // relaunches the graph, any difference recaptures it.
@@ -602,12 +618,26 @@ int run_mlp(pifu_ctx* ctx, const DevNet& net, const PointSrc& src_in, int64_t m,
             int precision = PIFU_PREC_FP32, const unsigned int* m_dev = nullptr) {
     if (precision == PIFU_PREC_BF16)
         return run_mlp_tc(ctx, net, src_in, m, map0, map1, calib, epi, s, m_dev);
-    // a device-resident batch size uses the split-K kernels, sized for m <= kRecheckCap
-    if (m_dev && m > kRecheckCap) return PIFU_ERR_ARG;
     PointSrc src = src_in;
     src.count = m_dev;
     const int L = (int)net.layers.size();
     Profiler& pr = ctx->prof;
+    const FusedNet fz = fused_of(net);
+    if ((m_dev || m <= kFusedMaxM) && fused_ok(fz)) {
+        // the whole network in one launch (gather included)
+        double flops = 0.0, wbytes = 0.0;
+        for (const DevLayer& Ly : net.layers) {
+            flops += 2.0 * (double)m * Ly.fan_in * Ly.n_out;
+            wbytes += 4.0 * (double)Ly.n_out * (Ly.fan_in + 1);
+        }
+        cudaEvent_t ev = pr.begin(s);
+        CK(launch_mlp_fused(fz, src, 0, m, calib, map0, map1, epi, s));
+        pr.end(PIFU_K_MLP_F32, ev, s, flops,
+               wbytes + (double)m * 4.0 * (4.0 * (map0.C + map1.C) + net.layers[L - 1].n_out));
+        return PIFU_OK;
+    }
+    // a device-resident batch size uses the split-K kernels, sized for m <= kRecheckCap
+    if (m_dev && m > kRecheckCap) return PIFU_ERR_ARG;
     for (int64_t p0 = 0; p0 < m; p0 += kChunk) {
         const int64_t mc = std::min<int64_t>(kChunk, m - p0);
         // gather: 4 taps x C channels read (L2), one padded row written
@@ -1009,9 +1039,12 @@ int g_eval(pifu_ctx* ctx, const DevNet& net, const PointSrc& src, int64_t cap,
     PointSrc s2{PTS_LIST, nullptr, ctx->recheck, 0, src.N, nullptr};
     Epilogue e2 = epi;
     e2.list = ctx->recheck;
-    st = run_mlp(ctx, net, s2, kRecheckCap, map, Map{}, cal, e2, s, PIFU_PREC_FP32, ctx->d_recheck);
+    // the fused kernel takes any queue length (at most the batch's); the
+    // split-K path has a fixed capacity
+    const int64_t rcap = fused_ok(fused_of(net)) ? cap : kRecheckCap;
+    st = run_mlp(ctx, net, s2, rcap, map, Map{}, cal, e2, s, PIFU_PREC_FP32, ctx->d_recheck);
     if (st != PIFU_OK) return st;
-    CK(launch_accumulate(rechecked, ctx->d_recheck, (unsigned)kRecheckCap, ctx->d_count + 1, s));
+    CK(launch_accumulate(rechecked, ctx->d_recheck, (unsigned)rcap, ctx->d_count + 1, s));
     return PIFU_OK;
 }
 

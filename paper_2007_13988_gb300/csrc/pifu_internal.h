@@ -212,6 +212,27 @@ cudaError_t launch_accumulate(unsigned long long* dst, const unsigned int* src, 
 cudaError_t launch_popcount(const uint32_t* bits, int64_t words, unsigned long long* count,
                             cudaStream_t stream);
 
+// --- mlp_fused.cu ----------------------------------------------------------
+// The whole network in FP32 for a small (or device-sized) batch in one
+// launch: clusters of 8 CTAs, one 16-point tile per cluster at a time.
+constexpr int kFusedMaxLayers = 8;
+struct FusedLayer {
+    const float* W;   // [n_out][ldw]: K1 columns on h_{l-1}, then K2 on x
+    const float* b;
+    int n_out, K1, K2, ldw;
+};
+struct FusedNet {
+    FusedLayer L[kFusedMaxLayers];
+    int nl, ldx, max_hidden;
+    float slope;
+};
+// Whether the network's shape fits the fused kernel.
+bool fused_ok(const FusedNet& n);
+// Points p0 .. p0 + m - 1 of `src` (src.count: a device-resident m).
+cudaError_t launch_mlp_fused(const FusedNet& net, const PointSrc& src, int64_t p0, int64_t m,
+                             const Calib& calib, const Map& map0, const Map& map1,
+                             const Epilogue& epi, cudaStream_t stream);
+
 // --- render.cu -------------------------------------------------------------
 struct RenderArgs {
     int width, height;

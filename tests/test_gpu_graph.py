@@ -127,5 +127,5 @@ def test_graph_frame_tiny_and_not_converged():
 
 def test_graph_frame_capacity_is_checked(full):
     with pytest.raises(pifu.PifuError) as ei:
-        run_frame(full, 1024)   # 1024^2 pixels > 262,144
+        run_frame(full, 1025)   # 1025^2 pixels > 1,048,576
     assert ei.value.status == pifu.PIFU_ERR_CAPACITY
