@@ -47,6 +47,8 @@ def parse_args():
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--precision", choices=("fp32", "bf16", "mixed"), default="mixed")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP32 comparison")
+    ap.add_argument("--no-512", action="store_true",
+                    help="skip the 512^3 precision form (timing and accuracy vs the oracle)")
     ap.add_argument("--form", choices=("graph", "host"), default="graph")
     ap.add_argument("--query-points", type=int, default=1 << 20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -178,13 +180,13 @@ def recorded_traffic(kernel_key, digest):
 
 # ----------------------------------------------------------------- oracle ---
 
-def oracle_frame(w, keep=False):
+def oracle_frame(w, keep=False, levels=None):
     """One full frame of the FP64 oracle; returns (seconds, counts[, levels])."""
     import numpy as np
     from oracle import field, localize, render
     t0 = time.perf_counter()
     lv = localize.hierarchical(lambda P: field.occupancy(w.occ_net, w.occ_map, w.calib, P),
-                               w.n0, w.num_levels)
+                               w.n0, w.num_levels if levels is None else levels)
     rgb, depth, hit = render.render(lv[-1].values, w.render, w.col_net, w.occ_map, w.col_map,
                                     w.calib)
     dt = time.perf_counter() - t0
@@ -249,7 +251,9 @@ def workload_config(w, evals, hits, precision="mixed"):
 
 # -------------------------------------------------------------------- ours ---
 
-PREC = {"fp32": 0, "bf16": 1, "mixed": 2}
+PREC = {"fp32": 0, "bf16": 1, "mixed": 2, "fp8_mixed": 3, "fp8": 4}
+DTYPE = {"fp32": "f32", "bf16": "bf16", "mixed": "bf16+f32", "fp8_mixed": "e4m3+bf16+f32",
+         "fp8": "e4m3+bf16"}
 
 
 class Frame:
@@ -272,16 +276,19 @@ class Frame:
             self.mask = torch.empty((R, R), dtype=torch.uint8, device=dev)
             self.flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
         stream.synchronize()
+        # scales of the FP8 form from the frame's own dense coarsest grid
+        pifu.pifu_calibrate_fp8(self.ctx, self.occ, w.calib, w.n0, stream=stream)
 
-    def run(self, prec, form="graph", margin=0.02, sur_margin=None):
+    def run(self, prec, form="graph", margin=0.02, sur_margin=None, levels=None):
         w, p = self.w, self.pifu
+        L = w.num_levels if levels is None else levels
         sur = {} if sur_margin is None else {"use_surrogate": True, "surrogate_margin": sur_margin}
         if form == "graph" and prec != 0:
             # one CUDA graph per frame (captured on the first call)
-            return p.pifu_frame(self.ctx, self.occ, self.col, w.calib, w.n0, w.num_levels,
+            return p.pifu_frame(self.ctx, self.occ, self.col, w.calib, w.n0, L,
                                 w.render, w.render, self.depth, self.rgb, self.mask,
                                 precision=prec, margin=margin, stream=self.stream, **sur)
-        vol = p.pifu_localize(self.ctx, self.occ, w.calib, w.n0, w.num_levels, precision=prec,
+        vol = p.pifu_localize(self.ctx, self.occ, w.calib, w.n0, L, precision=prec,
                               margin=margin, stream=self.stream, **sur)
         p.pifu_render(self.ctx, w.render, w.render, self.occ, self.col, w.calib, self.depth,
                       self.rgb, self.mask, precision=1 if prec != 0 else 0, stream=self.stream)
@@ -291,12 +298,13 @@ class Frame:
         self.pifu.pifu_destroy(self.ctx)
 
 
-def time_form(fr, prec, steps, warmup, world, clocks=None, form="graph", sur_margin=None):
+def time_form(fr, prec, steps, warmup, world, clocks=None, form="graph", sur_margin=None,
+              levels=None):
     """Device-timed frames of one precision form; returns a dict."""
     import torch
     vol = None
     for _ in range(max(1, warmup)):
-        vol = fr.run(prec, form, sur_margin=sur_margin)
+        vol = fr.run(prec, form, sur_margin=sur_margin, levels=levels)
     fr.stream.synchronize()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(steps)]
@@ -308,7 +316,7 @@ def time_form(fr, prec, steps, warmup, world, clocks=None, form="graph", sur_mar
         with torch.cuda.stream(fr.stream):
             fr.flush.zero_()
         ev[i][0].record(fr.stream)
-        vol = fr.run(prec, form, sur_margin=sur_margin)
+        vol = fr.run(prec, form, sur_margin=sur_margin, levels=levels)
         ev[i][1].record(fr.stream)
     torch.cuda.synchronize()
     prof = fr.pifu.pifu_profile_read(fr.ctx)
@@ -332,6 +340,38 @@ def time_form(fr, prec, steps, warmup, world, clocks=None, form="graph", sur_mar
             "evals_per_level": [int(vol.evals_per_level[i]) for i in range(L)],
             "rounds": [int(vol.conflict_rounds[i]) for i in range(L)],
             "hits": int(fr.mask.sum().item())}
+
+
+def snapshot(fr, vol):
+    """Host copies of a frame's result: binarized fine grid, node values
+    (tentative 0/1 where not evaluated), colour and hit mask."""
+    import numpy as np
+    p = fr.pifu
+    occ_b, ev_b, val = p.volume_tensors(vol)
+    b = p.unpack_bits(occ_b.cpu().numpy(), vol.n, vol.row_words)
+    e = p.unpack_bits(ev_b.cpu().numpy(), vol.n, vol.row_words)
+    v = val.cpu().numpy().astype(np.float64).reshape((vol.n + 1,) * 3)
+    return {"b": b, "vals": np.where(e, v, b.astype(np.float64)), "rgb": fr.rgb.cpu().numpy(),
+            "mask": fr.mask.cpu().numpy().astype(bool)}
+
+
+def accuracy(snap, lv, o_rgb, o_hit, fp32_rgb=None):
+    """IoU / Chamfer of the fine grid and colour PSNR against the oracle's
+    frame (and PSNR against the plain FP32 render, if given)."""
+    import numpy as np
+    from oracle import metrics
+    both = snap["mask"] & o_hit
+    d = snap["rgb"].astype(np.float64)[both] - o_rgb[both]
+    mse = float(np.mean(d * d)) if d.size else 0.0
+    out = {"iou_vs_oracle": metrics.iou(snap["b"], lv[-1].binary),
+           "chamfer_vox_vs_oracle": metrics.chamfer_voxels(snap["vals"], lv[-1].values),
+           "colour_psnr_vs_oracle_db": float("inf") if mse == 0 else 10 * np.log10(1.0 / mse),
+           "mask_disagreement_px": int(np.count_nonzero(snap["mask"] != o_hit))}
+    if fp32_rgb is not None:
+        d = snap["rgb"].astype(np.float64) - fp32_rgb.astype(np.float64)
+        mse = float(np.mean(d * d))
+        out["colour_psnr_vs_fp32_db"] = float("inf") if mse == 0 else 10 * np.log10(1.0 / mse)
+    return out
 
 
 def train_surrogate(fr, args):
@@ -385,16 +425,7 @@ def run_ours(args, rank, world, local_rank):
     form = args.form if prec != 0 else "host"
     head = time_form(fr, prec, args.steps, args.warmup, world,
                      ClockSampler(local_rank, enabled=not args.no_clocks), form=form)
-    head_rgb = fr.rgb.cpu().numpy()
-    head_mask = fr.mask.cpu().numpy()
-    head_b, head_vals = None, None
-    if rank == 0:
-        hv = head["vol"]
-        occ_b, ev_b, val = pifu.volume_tensors(hv)
-        head_b = pifu.unpack_bits(occ_b.cpu().numpy(), hv.n, hv.row_words)
-        head_e = pifu.unpack_bits(ev_b.cpu().numpy(), hv.n, hv.row_words)
-        v = val.cpu().numpy().astype(np.float64).reshape((hv.n + 1,) * 3)
-        head_vals = np.where(head_e, v, head_b.astype(np.float64))
+    head_snap = snapshot(fr, head["vol"])
     # ---- per-kernel timing: a graph has no per-launch events, so the kernel
     # classes of the same frame are timed on its host-driven form ------------
     prof_run = head
@@ -405,19 +436,29 @@ def run_ours(args, rank, world, local_rank):
     if sur_margin is not None:
         sur = time_form(fr, prec, args.steps, args.warmup, world, form=form,
                         sur_margin=sur_margin)
-        sv = sur["vol"]
-        occ_b, ev_b, val = pifu.volume_tensors(sv)
-        sur_b = pifu.unpack_bits(occ_b.cpu().numpy(), sv.n, sv.row_words)
-        sur_e = pifu.unpack_bits(ev_b.cpu().numpy(), sv.n, sv.row_words)
-        v = val.cpu().numpy().astype(np.float64).reshape((sv.n + 1,) * 3)
-        sur_vals = np.where(sur_e, v, sur_b.astype(np.float64))
-        sur_rgb = fr.rgb.cpu().numpy()
-        sur_mask = fr.mask.cpu().numpy()
+        sur_snap = snapshot(fr, sur["vol"])
+    # ---- the other tensor-core precision forms of the same frame ------------
+    side_steps = max(3, min(args.steps, 10))
+    others = {}
+    if prec != 0:
+        for name in ("mixed", "fp8_mixed"):
+            if PREC[name] != prec:
+                r = time_form(fr, PREC[name], side_steps, 2, world, form=form)
+                others[name] = (r, snapshot(fr, r["vol"]))
     # ---- the plain FP32 form on the same GPU, for the speedup ---------------
     plain = None
     if prec != 0 and not args.no_plain:
-        plain = time_form(fr, 0, max(3, min(args.steps, 10)), 2, world)
+        plain = time_form(fr, 0, side_steps, 2, world)
         plain_rgb = fr.rgb.cpu().numpy()
+    # ---- the precision form at 512^3 (five levels from 32^3) ----------------
+    p512 = {}
+    if prec != 0 and not args.no_512:
+        L5 = w.num_levels + 1
+        for name in ("mixed", "fp8_mixed"):
+            r = time_form(fr, PREC[name], side_steps, 2, world, form=form, levels=L5)
+            p512[name] = (r, snapshot(fr, r["vol"]))
+        fp32_512 = time_form(fr, 0, 2, 1, world, levels=L5)
+        p512["fp32"] = (fp32_512, snapshot(fr, fp32_512["vol"]))
 
     # ---- query points/s (raw field, inputs resident) -----------------------
     Q = args.query_points
@@ -512,7 +553,7 @@ def run_ours(args, rank, world, local_rank):
     line = {"metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms_per_step"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": {"fp32": "f32", "bf16": "bf16", "mixed": "bf16+f32"}[args.precision],
+            "dtype": DTYPE[args.precision],
             "data": "synthetic",
             "config": workload_config(w, head["evals"], head["hits"], args.precision),
             "query_pts_per_s": q_head,
@@ -525,7 +566,7 @@ def run_ours(args, rank, world, local_rank):
                               else "host-driven (pifu_localize + pifu_render)")
     if form == "graph":
         line["host_driven"] = {"value": prof_run["value"], "ms_per_step": prof_run["ms_per_step"]}
-    if prec == 2:
+    if prec in (2, 3):
         line["config"]["margin"] = 0.02
         line["config"]["rechecked_per_frame"] = head["rechecked"]
     line["config"]["surrogate"] = False
@@ -547,10 +588,18 @@ def run_ours(args, rank, world, local_rank):
                               "speedup_of_headline": head["value"] / plain["value"]}
         if sur is not None:
             line["surrogate"]["speedup_over_plain_fp32"] = sur["value"] / plain["value"]
-        d = plain_rgb.astype(np.float64) - head_rgb.astype(np.float64)
+        d = plain_rgb.astype(np.float64) - head_snap["rgb"].astype(np.float64)
         mse = float(np.mean(d * d))
         line["accuracy"] = {"colour_psnr_vs_fp32_db": float("inf") if mse == 0 else
                             10 * np.log10(1.0 / mse)}
+    if others:
+        line["other_forms"] = {
+            name: {"value": r["value"], "unit": UNIT, "ms_per_step": r["ms_per_step"],
+                   "dtype": DTYPE[name], "rechecked_per_frame": r["rechecked"],
+                   "evals_per_frame": r["evals"], "conflict_rounds": r["rounds"],
+                   "speedup_over_headline": r["value"] / head["value"],
+                   "speedup_over_plain_fp32": r["value"] / plain["value"] if plain else None}
+            for name, (r, _) in others.items()}
     if head["clocks"] is not None:
         line["clocks"] = head["clocks"]
     if world == 1 and not args.no_cpu_baseline:
@@ -560,29 +609,35 @@ def run_ours(args, rank, world, local_rank):
                                 "sample": f"one full frame of the FP64 oracle (numpy): "
                                           f"{cnt['evals']} f_O + {cnt['hits']} f_T evaluations, "
                                           f"localization bookkeeping and ray scan; {t:.1f} s"}
-        from oracle import metrics
-        acc = line.setdefault("accuracy", {})
-        acc["iou_vs_oracle"] = metrics.iou(head_b, lv[-1].binary)
-        acc["chamfer_vox_vs_oracle"] = metrics.chamfer_voxels(head_vals, lv[-1].values)
         # colour at the pixels both renders hit (silhouette pixels that one of
         # them misses are counted apart)
-        h_hit = head_mask.astype(bool)
-        both = h_hit & o_hit
-        d = head_rgb.astype(np.float64)[both] - o_rgb[both]
-        mse = float(np.mean(d * d)) if d.size else 0.0
-        acc["colour_psnr_vs_oracle_db"] = float("inf") if mse == 0 else 10 * np.log10(1.0 / mse)
-        acc["mask_disagreement_px"] = int(np.count_nonzero(h_hit != o_hit))
+        line.setdefault("accuracy", {}).update(accuracy(head_snap, lv, o_rgb, o_hit))
         if sur is not None:
-            s_hit = sur_mask.astype(bool)
-            both = s_hit & o_hit
-            d = sur_rgb.astype(np.float64)[both] - o_rgb[both]
-            mse = float(np.mean(d * d)) if d.size else 0.0
-            line["surrogate"]["accuracy"] = {
-                "iou_vs_oracle": metrics.iou(sur_b, lv[-1].binary),
-                "chamfer_vox_vs_oracle": metrics.chamfer_voxels(sur_vals, lv[-1].values),
-                "colour_psnr_vs_oracle_db": float("inf") if mse == 0 else
-                10 * np.log10(1.0 / mse),
-                "mask_disagreement_px": int(np.count_nonzero(s_hit != o_hit))}
+            line["surrogate"]["accuracy"] = accuracy(sur_snap, lv, o_rgb, o_hit)
+        for name, (r, snap) in others.items():
+            line["other_forms"][name]["accuracy"] = accuracy(snap, lv, o_rgb, o_hit,
+                                                             plain_rgb if plain else None)
+    if p512:
+        out = {"workload": "the same frame at 512^3 effective resolution: 32^3 -> 512^3 "
+                           "(five levels) + 512^2 render, graph form",
+               "margin": 0.02}
+        base = p512["fp32"][0]
+        out["plain_fp32"] = {"value": base["value"], "ms_per_step": base["ms_per_step"],
+                             "form": "host-driven FP32", "evals_per_frame": base["evals"]}
+        for name in ("mixed", "fp8_mixed"):
+            r, _ = p512[name]
+            out[name] = {"value": r["value"], "unit": UNIT, "ms_per_step": r["ms_per_step"],
+                         "dtype": DTYPE[name], "speedup_over_plain_fp32": r["value"] / base["value"],
+                         "evals_per_frame": r["evals"], "rechecked_per_frame": r["rechecked"],
+                         "conflict_rounds": r["rounds"]}
+        if rank == 0:
+            t0 = time.perf_counter()
+            _, _, (lv5, o_rgb5, o_hit5) = oracle_frame(w, keep=True, levels=w.num_levels + 1)
+            out["oracle_s"] = time.perf_counter() - t0
+            for name in ("mixed", "fp8_mixed"):
+                out[name]["accuracy"] = accuracy(p512[name][1], lv5, o_rgb5, o_hit5,
+                                                 p512["fp32"][1]["rgb"])
+        line["precision_512"] = out
     print(json.dumps(line), flush=True)
 
 

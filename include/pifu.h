@@ -62,8 +62,20 @@ typedef enum { PIFU_F32 = 0, PIFU_BF16 = 1 } pifu_dtype;
 /* MLP arithmetic.  FP32: plain single precision (SIMT FFMA).  BF16: tcgen05
  * tensor cores, BF16 weights and activations, FP32 accumulation.  MIXED:
  * BF16, then every occupancy within `margin` of 0.5 evaluated again in FP32
- * (the decision threshold is where low precision can change a result). */
-typedef enum { PIFU_PREC_FP32 = 0, PIFU_PREC_BF16 = 1, PIFU_PREC_MIXED = 2 } pifu_precision;
+ * (the decision threshold is where low precision can change a result).
+ * FP8: as BF16, but f_O's leading hidden layers with at least 512 outputs
+ * (at full size the 1024- and 512-wide layers, 78% of its arithmetic) take
+ * E4M3 operands with per-output-channel weight scales and per-tensor
+ * activation scales (kind::f8f6f4, FP32 accumulation); needs
+ * pifu_calibrate_fp8 first.  FP8_MIXED: FP8, then the FP32 re-evaluation of
+ * MIXED.  The colour MLP runs in BF16 in the FP8 forms. */
+typedef enum {
+    PIFU_PREC_FP32 = 0,
+    PIFU_PREC_BF16 = 1,
+    PIFU_PREC_MIXED = 2,
+    PIFU_PREC_FP8_MIXED = 3,
+    PIFU_PREC_FP8 = 4
+} pifu_precision;
 
 /* A channel-last feature map g(I) in device memory: data[(j W + i) C + c]. */
 typedef struct {
@@ -79,7 +91,7 @@ typedef struct {
     int32_t num_levels;  /* 1 .. 8; finest n0 << (num_levels-1) <= 512         */
     int32_t precision;   /* pifu_precision                                     */
     int32_t max_rounds;  /* cap on conflict rounds per level (<= 0: 4096)      */
-    float margin;        /* MIXED: FP32 re-evaluation band |o - 0.5| < margin  */
+    float margin;        /* MIXED, FP8_MIXED: FP32 re-evaluation band |o - 0.5| < margin */
     int32_t use_surrogate;    /* 1: coarse levels evaluate the trained f_S first  */
     float surrogate_margin;   /* f_S occupancies within this of 0.5 fall back to f_O */
 } pifu_levels;
@@ -137,9 +149,10 @@ int pifu_query(pifu_ctx* ctx, const pifu_fmap* occ_map, const float calib[12],
 
 /* pifu_query with a choice of MLP arithmetic (pifu_precision).  BF16 and
  * MIXED need hidden widths that are multiples of 64 (else
- * PIFU_ERR_UNSUPPORTED); MIXED re-evaluates occupancies within `margin`
- * (0 .. 0.5) of 0.5 in FP32 and synchronises the stream once per 65,536
- * points.  A bounded device wait that gave up is reported as
+ * PIFU_ERR_UNSUPPORTED); the FP8 forms need pifu_calibrate_fp8 (else
+ * PIFU_ERR_STATE); MIXED and FP8_MIXED re-evaluate occupancies within
+ * `margin` (0 .. 0.5) of 0.5 in FP32 and synchronise the stream once per
+ * 65,536 points.  A bounded device wait that gave up is reported as
  * PIFU_ERR_TIMEOUT by the next synchronising call. */
 int pifu_query_ex(pifu_ctx* ctx, const pifu_fmap* occ_map, const float calib[12],
                   const float* pts_dev, int64_t m, float* occ_dev, int precision, float margin,
@@ -188,9 +201,9 @@ int pifu_render(pifu_ctx* ctx, const pifu_camera* cam, const pifu_fmap* occ_map,
  * MLP launches read them from the counters the selection kernels write, and
  * each level's conflict loop is a conditional WHILE node.  The stream is
  * synchronised once, at the end, to read the counters into *out.
- * Tensor-core forms only (levels->precision BF16 or MIXED; the colour MLP
- * runs in BF16).  Fixed capacities: 1,048,576 points per evaluation batch and
- * pixels per render, 8,192 FP32 re-checks per batch; a frame that exceeds one
+ * Tensor-core forms only (levels->precision BF16, MIXED, FP8 or FP8_MIXED;
+ * the colour MLP runs in BF16).  Fixed capacities: 1,048,576 points per
+ * evaluation batch and pixels per render; a frame that exceeds one
  * returns PIFU_ERR_CAPACITY (its outputs are then invalid and the
  * host-driven pifu_localize + pifu_render handle it).  Other errors as in
  * pifu_localize / pifu_render.  The last volume is then available to
@@ -199,6 +212,22 @@ int pifu_frame(pifu_ctx* ctx, const pifu_fmap* occ_map, const pifu_fmap* col_map
                const float calib[12], const pifu_levels* levels, const pifu_camera* cam,
                void* stream, float* depth_dev, float* rgb_dev, uint8_t* mask_dev,
                pifu_volume* out);
+
+/* ---- FP8 form of f_O (not in the paper) --------------------------------------
+ * Calibrates and builds the E4M3 layers used by PIFU_PREC_FP8 and
+ * PIFU_PREC_FP8_MIXED: f_O's input rows x and first hidden outputs are
+ * evaluated in FP32 at the (n0+1)^3 nodes of the dense coarsest grid of this
+ * feature map and calibration; the activation scales are their absolute
+ * maxima / 448 (the largest E4M3 value; larger values saturate), the weight
+ * scales the per-output-channel absolute maxima / 448 (the x columns of a
+ * layer that also reads h are first multiplied by s_x / s_h so that both
+ * segments share one accumulator scale).  The scales stay with the context
+ * until the next call.  Synchronises `stream`.
+ * Errors: PIFU_ERR_ARG (map/calibration/n0), PIFU_ERR_UNSUPPORTED (f_O has no
+ * tensor-core form, or no leading hidden layer with >= 512 outputs whose
+ * widths are multiples of 128), PIFU_ERR_CUDA / PIFU_ERR_OOM. */
+int pifu_calibrate_fp8(pifu_ctx* ctx, const pifu_fmap* occ_map, const float calib[12], int n0,
+                       void* stream);
 
 /* ---- Learned surrogate f_S (not in the paper) -------------------------------
  * A small MLP of f_O's family, f_S: d_in -> h1 -> h2 -> 1 (leaky-ReLU,

@@ -285,6 +285,18 @@ __global__ void __launch_bounds__(256) last_layer_kernel(
     }
 }
 
+// *out = max(*out, max |p[i]|) as float bits (non-negative floats order like
+// their bit patterns).
+__global__ void amax_kernel(const float* __restrict__ p, int64_t n, unsigned int* out) {
+    float v = 0.f;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        v = fmaxf(v, fabsf(p[i]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(v));
+}
+
 inline unsigned fixed_or_exact(const unsigned int* m_dev, int64_t exact_blocks) {
     return (unsigned)(m_dev ? (exact_blocks < 152 * 16 ? exact_blocks : 152 * 16) : exact_blocks);
 }
@@ -341,6 +353,13 @@ cudaError_t launch_last_layer_bf16(int64_t p0, int64_t M, int n_out, const __nv_
     const int64_t blocks = (M * 32 + 255) / 256;
     last_layer_kernel<__nv_bfloat16><<<fixed_or_exact(m_dev, blocks), 256, 0, stream>>>(
         p0, M, n_out, A1, lda1, K1, A2, lda2, K2, W, ldw, bias, epi, m_dev);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_amax(const float* p, int64_t n, unsigned int* out, cudaStream_t stream) {
+    if (n <= 0) return cudaSuccess;
+    const int64_t blocks = std::min<int64_t>((n + 255) / 256, 152 * 8);
+    amax_kernel<<<(unsigned)blocks, 256, 0, stream>>>(p, n, out);
     return cudaGetLastError();
 }
 

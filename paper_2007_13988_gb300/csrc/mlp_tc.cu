@@ -1,9 +1,15 @@
-// Tensor-core (tcgen05) form of one hidden MLP layer: BF16 operands, FP32
-// accumulation in tensor memory (Sec. 3.1's concatenation MLP, the "MLP"
-// variant of Table A1: 2.36 MFLOP per point at full size, a dense
-// contraction over a batch of points).
+// Tensor-core (tcgen05) form of one hidden MLP layer: BF16 or E4M3
+// operands, FP32 accumulation in tensor memory (Sec. 3.1's concatenation
+// MLP, the "MLP" variant of Table A1: 2.36 MFLOP per point at full size, a
+// dense contraction over a batch of points).
 //
-//   out[M][N] = lrelu( [H | X][M][K] * W[N][K]^T + b )        (BF16 out)
+//   out[M][N] = lrelu( s[n] ([H | X][M][K] * W[N][K]^T) + b )
+//
+// BF16 mode: s = 1, BF16 out.  E4M3 modes (kind::f8f6f4): the operands are
+// stored divided by their scales (per-tensor for activations, per output
+// channel for weights), s[n] multiplies the two back, and the output is BF16
+// or E4M3 again (multiplied by the next layer's inverse activation scale).
+// One K-block is 128 bytes of a row in both: 64 BF16 or 128 E4M3 values.
 //
 // The skip concatenation [h_{l-1}, x] is fused as two K segments: the TMA
 // producer fetches A tiles from the H tensor map for the first nk1 K-blocks
@@ -31,6 +37,7 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
 
 #include "epilogue.cuh"
 #include "pifu_internal.h"
@@ -53,8 +60,9 @@ constexpr int kThreads = 64 + 32 * kEpiWarps;
 constexpr int kFuseFloats = 4 * 256 + 2 * 4 * TBM + 16;   // last-layer W, exchange, flags
 
 __host__ __device__ constexpr uint32_t tc_smem_bytes(int BN) {
-    // operand ring + 1024-byte alignment slack + barriers + staged bias + fused last layer
-    return (uint32_t)TSTAGES * (TBM * TBK * 2 + BN * TBK * 2) + 1024 + 256 + kMaxN * 4 +
+    // operand ring + 1024-byte alignment slack + barriers + staged bias and
+    // column scales + fused last layer
+    return (uint32_t)TSTAGES * (TBM * TBK * 2 + BN * TBK * 2) + 1024 + 256 + 2 * kMaxN * 4 +
            kFuseFloats * 4;
 }
 
@@ -76,12 +84,22 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
     return *reinterpret_cast<const uint32_t*>(&h);
 }
 
-template <int BN, bool FUSE>
+// Four values rounded to E4M3 (saturating), first value in the lowest byte.
+__device__ __forceinline__ uint32_t pack_e4m3x4(float a, float b, float c, float d) {
+    const uint32_t lo = __nv_cvt_float2_to_fp8x2(make_float2(a, b), __NV_SATFINITE, __NV_E4M3);
+    const uint32_t hi = __nv_cvt_float2_to_fp8x2(make_float2(c, d), __NV_SATFINITE, __NV_E4M3);
+    return lo | (hi << 16);
+}
+
+template <int BN, bool FUSE, int MODE>
 __global__ void __launch_bounds__(kThreads, 1) tc_linear_kernel(
     const __grid_constant__ CUtensorMap tmA1, const __grid_constant__ CUtensorMap tmA2,
     const __grid_constant__ CUtensorMap tmW, int nk1, int nk2, int M, int N,
-    const float* __restrict__ bias, float slope, __nv_bfloat16* __restrict__ out, int ldo,
-    unsigned int* __restrict__ err, const unsigned int* __restrict__ m_dev, FuseLast fl) {
+    const float* __restrict__ bias, float slope, void* __restrict__ out_raw, int ldo,
+    unsigned int* __restrict__ err, const unsigned int* __restrict__ m_dev, FuseLast fl,
+    const float* __restrict__ colscale, float out_scale) {
+    static_assert(!(FUSE && MODE != TC_BF16), "the fused last layer reads BF16 activations");
+    constexpr int TBKE = MODE == TC_BF16 ? TBK : 2 * TBK;   // elements per 128-byte K-block
     if (m_dev) M = min(M, (int)*m_dev);   // device-resident row count
     constexpr uint32_t A_BYTES = TBM * TBK * 2;
     constexpr uint32_t B_BYTES = BN * TBK * 2;
@@ -96,7 +114,8 @@ __global__ void __launch_bounds__(kThreads, 1) tc_linear_kernel(
     uint64_t* acce = accf + 2;          // [2] accumulator drained by the epilogue
     uint32_t* tslot = reinterpret_cast<uint32_t*>(acce + 2);
     float* sbias = reinterpret_cast<float*>(reinterpret_cast<uint8_t*>(full) + 256);
-    float* sW5 = sbias + kMaxN;              // fused last layer: [4][BN]
+    float* scol = sbias + kMaxN;             // E4M3 modes: accumulator scale per column
+    float* sW5 = scol + kMaxN;               // fused last layer: [4][BN]
     float* sxch = sW5 + 4 * 256;             // [2 buffers][4 outputs][128 rows] partial sums
     volatile uint32_t* sflag = reinterpret_cast<volatile uint32_t*>(sxch + 2 * 4 * TBM);  // [2][4]
 
@@ -120,7 +139,10 @@ __global__ void __launch_bounds__(kThreads, 1) tc_linear_kernel(
         prefetch_tmap(&tmA2);
         prefetch_tmap(&tmW);
     }
-    for (int c = threadIdx.x; c < N; c += blockDim.x) sbias[c] = bias[c];
+    for (int c = threadIdx.x; c < N; c += blockDim.x) {
+        sbias[c] = bias[c];
+        scol[c] = MODE == TC_BF16 ? 1.f : colscale[c];
+    }
     if (FUSE) {
         for (int c = threadIdx.x; c < fl.n_out * BN; c += blockDim.x)
             sW5[c] = fl.W[(int64_t)(c / BN) * fl.ldw + (c % BN)];
@@ -149,17 +171,18 @@ __global__ void __launch_bounds__(kThreads, 1) tc_linear_kernel(
                     }
                     mbar_arrive_expect_tx(&full[s], A_BYTES + B_BYTES);
                     if (kb < nk1)
-                        tma_load_2d(sA + s * A_BYTES, &tmA1, kb * TBK, m0, &full[s]);
+                        tma_load_2d(sA + s * A_BYTES, &tmA1, kb * TBKE, m0, &full[s]);
                     else
-                        tma_load_2d(sA + s * A_BYTES, &tmA2, (kb - nk1) * TBK, m0, &full[s]);
-                    tma_load_2d(sB + s * B_BYTES, &tmW, kb * TBK, n0, &full[s]);
+                        tma_load_2d(sA + s * A_BYTES, &tmA2, (kb - nk1) * TBKE, m0, &full[s]);
+                    tma_load_2d(sB + s * B_BYTES, &tmW, kb * TBKE, n0, &full[s]);
                 }
             }
         }
     } else if (warp == 1) {
         if (lane == 0) {
             // MMA issuer
-            constexpr uint32_t idesc = idesc_bf16_f32(TBM, BN);
+            constexpr uint32_t idesc =
+                MODE == TC_BF16 ? idesc_bf16_f32(TBM, BN) : idesc_e4m3_f32(TBM, BN);
             uint32_t g = 0, i = 0;
             for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x, ++i) {
                 const uint32_t b = i & 1u, j = i >> 1;
@@ -179,10 +202,16 @@ __global__ void __launch_bounds__(kThreads, 1) tc_linear_kernel(
                     tc_fence_after();
                     const uint32_t a0 = smem_u32(sA + s * A_BYTES);
                     const uint32_t b0 = smem_u32(sB + s * B_BYTES);
+                    // 4 MMAs of 32 bytes of K each (16 BF16 or 32 E4M3 values)
 #pragma unroll
-                    for (int k = 0; k < TBK / 16; ++k)
-                        mma_bf16(d, desc_k_sw128(a0 + k * 32), desc_k_sw128(b0 + k * 32), idesc,
-                                 (kb | k) != 0 ? 1u : 0u);
+                    for (int k = 0; k < 4; ++k) {
+                        if (MODE == TC_BF16)
+                            mma_bf16(d, desc_k_sw128(a0 + k * 32), desc_k_sw128(b0 + k * 32),
+                                     idesc, (kb | k) != 0 ? 1u : 0u);
+                        else
+                            mma_e4m3(d, desc_k_sw128(a0 + k * 32), desc_k_sw128(b0 + k * 32),
+                                     idesc, (kb | k) != 0 ? 1u : 0u);
+                    }
                     mma_commit(&empty[s]);
                 }
                 mma_commit(&accf[b]);   // also after an error, so the epilogue is released
@@ -208,6 +237,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_linear_kernel(
             const int row = m0 + q * 32 + lane;
             const uint32_t tl = tmem + ((uint32_t)(q * 32) << 16) + b * BN;
             const float* bb = sbias + n0;
+            const float* sc = scol + n0;
             const int half = (warp - 2) >> 2;
             float part[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll 1
@@ -235,7 +265,28 @@ __global__ void __launch_bounds__(kThreads, 1) tc_linear_kernel(
                         for (int jo = 0; jo < 4; ++jo)
                             if (jo < fl.n_out) part[jo] = fmaf(a, sW5[jo * BN + c0 + cc], part[jo]);
                     }
+                } else if (row < M && MODE == TC_E4M3_E4M3) {
+                    uint8_t* out8 = static_cast<uint8_t*>(out_raw);
+                    uint4* dst = reinterpret_cast<uint4*>(out8 + (int64_t)row * ldo + n0 + c0);
+#pragma unroll
+                    for (int v = 0; v < NC / 16; ++v) {
+                        uint32_t pk[4];
+#pragma unroll
+                        for (int jj = 0; jj < 4; ++jj) {
+                            float e[4];
+#pragma unroll
+                            for (int t4 = 0; t4 < 4; ++t4) {
+                                const int cc = v * 16 + 4 * jj + t4;
+                                float a = fmaf(__uint_as_float(r[cc]), sc[c0 + cc], bb[c0 + cc]);
+                                a = a >= 0.f ? a : slope * a;
+                                e[t4] = a * out_scale;
+                            }
+                            pk[jj] = pack_e4m3x4(e[0], e[1], e[2], e[3]);
+                        }
+                        dst[v] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                    }
                 } else if (row < M) {
+                    __nv_bfloat16* out = static_cast<__nv_bfloat16*>(out_raw);
                     uint4* dst = reinterpret_cast<uint4*>(out + (int64_t)row * ldo + n0 + c0);
 #pragma unroll
                     for (int v = 0; v < NC / 8; ++v) {
@@ -243,8 +294,15 @@ __global__ void __launch_bounds__(kThreads, 1) tc_linear_kernel(
 #pragma unroll
                         for (int jj = 0; jj < 4; ++jj) {
                             const int cc = v * 8 + 2 * jj;
-                            float a = __uint_as_float(r[cc]) + bb[c0 + cc];
-                            float c = __uint_as_float(r[cc + 1]) + bb[c0 + cc + 1];
+                            float a, c;
+                            if (MODE == TC_BF16) {
+                                a = __uint_as_float(r[cc]) + bb[c0 + cc];
+                                c = __uint_as_float(r[cc + 1]) + bb[c0 + cc + 1];
+                            } else {
+                                a = fmaf(__uint_as_float(r[cc]), sc[c0 + cc], bb[c0 + cc]);
+                                c = fmaf(__uint_as_float(r[cc + 1]), sc[c0 + cc + 1],
+                                         bb[c0 + cc + 1]);
+                            }
                             a = a >= 0.f ? a : slope * a;
                             c = c >= 0.f ? c : slope * c;
                             pk[jj] = pack_bf16x2(a, c);
@@ -315,12 +373,14 @@ constexpr int bn_index(int BN) { return BN == 64 ? 0 : (BN == 128 ? 1 : 2); }
 template <int BN>
 cudaError_t ensure_attr(int dev) {
     if (dev >= 0 && dev < 64 && g_attr_set[bn_index(BN)][dev]) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(tc_linear_kernel<BN, false>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)tc_smem_bytes(BN));
+    const int bytes = (int)tc_smem_bytes(BN);
+    const cudaFuncAttribute at = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    cudaError_t e = cudaFuncSetAttribute(tc_linear_kernel<BN, false, TC_BF16>, at, bytes);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(tc_linear_kernel<BN, true, TC_BF16>, at, bytes);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(tc_linear_kernel<BN, true>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem_bytes(BN));
+        e = cudaFuncSetAttribute(tc_linear_kernel<BN, false, TC_E4M3_E4M3>, at, bytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(tc_linear_kernel<BN, false, TC_E4M3_BF16>, at, bytes);
     if (e == cudaSuccess && dev >= 0 && dev < 64) g_attr_set[bn_index(BN)][dev] = true;
     return e;
 }
@@ -347,23 +407,35 @@ cudaError_t launch_bn(const TcLayerArgs& a, cudaStream_t s) {
     if (e != cudaSuccess) return e;
     const long long tiles = (long long)(a.N / BN) * ((a.M + TBM - 1) / TBM);
     const int grid = (int)(tiles < sms ? tiles : sms);
+    const uint32_t smem = tc_smem_bytes(BN);
+    if (a.mode != TC_BF16 && (a.fuse || !a.colscale)) return cudaErrorInvalidValue;
     if (a.fuse) {
         if (a.N != BN || a.fuse->n_out < 1 || a.fuse->n_out > 4) return cudaErrorInvalidValue;
-        tc_linear_kernel<BN, true><<<grid, kThreads, tc_smem_bytes(BN), s>>>(
+        tc_linear_kernel<BN, true, TC_BF16><<<grid, kThreads, smem, s>>>(
             *a.tmA1, *a.tmA2, *a.tmW, a.nk1, a.nk2, a.M, a.N, a.bias, a.slope, a.out, a.ldo,
-            a.err, a.m_dev, *a.fuse);
+            a.err, a.m_dev, *a.fuse, nullptr, 1.f);
+    } else if (a.mode == TC_E4M3_E4M3) {
+        tc_linear_kernel<BN, false, TC_E4M3_E4M3><<<grid, kThreads, smem, s>>>(
+            *a.tmA1, *a.tmA2, *a.tmW, a.nk1, a.nk2, a.M, a.N, a.bias, a.slope, a.out, a.ldo,
+            a.err, a.m_dev, FuseLast{}, a.colscale, a.out_scale);
+    } else if (a.mode == TC_E4M3_BF16) {
+        tc_linear_kernel<BN, false, TC_E4M3_BF16><<<grid, kThreads, smem, s>>>(
+            *a.tmA1, *a.tmA2, *a.tmW, a.nk1, a.nk2, a.M, a.N, a.bias, a.slope, a.out, a.ldo,
+            a.err, a.m_dev, FuseLast{}, a.colscale, 1.f);
     } else {
-        tc_linear_kernel<BN, false><<<grid, kThreads, tc_smem_bytes(BN), s>>>(
+        tc_linear_kernel<BN, false, TC_BF16><<<grid, kThreads, smem, s>>>(
             *a.tmA1, *a.tmA2, *a.tmW, a.nk1, a.nk2, a.M, a.N, a.bias, a.slope, a.out, a.ldo,
-            a.err, a.m_dev, FuseLast{});
+            a.err, a.m_dev, FuseLast{}, nullptr, 1.f);
     }
     return cudaGetLastError();
 }
 
 }  // namespace
 
-bool tc_encode_2d_bf16(void* map, const void* base, uint64_t cols, uint64_t rows,
-                       uint64_t row_stride_bytes, uint32_t box_cols, uint32_t box_rows) {
+namespace {
+
+bool encode_2d(void* map, CUtensorMapDataType dtype, const void* base, uint64_t cols,
+               uint64_t rows, uint64_t row_stride_bytes, uint32_t box_cols, uint32_t box_rows) {
     if (!g_encode) {
         cudaDriverEntryPointQueryResult q;
         void* fn = nullptr;
@@ -377,12 +449,26 @@ bool tc_encode_2d_bf16(void* map, const void* base, uint64_t cols, uint64_t rows
     const cuuint64_t strides[1] = {row_stride_bytes};
     const cuuint32_t box[2] = {box_cols, box_rows};
     const cuuint32_t estr[2] = {1, 1};
-    const CUresult r = g_encode(static_cast<CUtensorMap*>(map), CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+    const CUresult r = g_encode(static_cast<CUtensorMap*>(map), dtype, 2,
                                 const_cast<void*>(base), dims, strides, box, estr,
                                 CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                                 CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+bool tc_encode_2d_bf16(void* map, const void* base, uint64_t cols, uint64_t rows,
+                       uint64_t row_stride_bytes, uint32_t box_cols, uint32_t box_rows) {
+    return encode_2d(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, base, cols, rows, row_stride_bytes,
+                     box_cols, box_rows);
+}
+
+bool tc_encode_2d_u8(void* map, const void* base, uint64_t cols, uint64_t rows,
+                     uint64_t row_stride_bytes, uint32_t box_cols, uint32_t box_rows) {
+    return encode_2d(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, base, cols, rows, row_stride_bytes,
+                     box_cols, box_rows);
 }
 
 cudaError_t tc_prepare() {

@@ -1,6 +1,7 @@
 // C ABI of libpifu: weight-blob parsing, device memory, and the host side of
 // the coarse-to-fine localization loop and of the render (include/pifu.h).
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -8,6 +9,8 @@
 
 #include "../../include/pifu.h"
 #include "pifu_internal.h"
+
+#include <cuda_fp8.h>
 
 using namespace pifu;
 
@@ -40,6 +43,18 @@ struct TcLayer {
     CUtensorMap tmA1{};   // the previous layer's BF16 output (l >= 1)
 };
 
+// E4M3 form of one of f_O's leading wide hidden layers: W divided by a
+// per-output-channel scale s_w[n] (the x columns first multiplied by
+// s_x / s_a), the accumulator multiplied back by colscale[n] = s_w[n] s_a.
+struct Fp8Layer {
+    uint8_t* W = nullptr;        // [n_out][Kw] E4M3 bytes, x segment zero-padded
+    float* colscale = nullptr;   // [n_out]
+    int Kw = 0, nk1 = 0, nk2 = 0, BN = 0;
+    float out_scale = 1.f;       // E4M3 output: 1 / s of the next layer's input
+    CUtensorMap tmW{};
+    CUtensorMap tmA1{};          // the previous layer's E4M3 output (layer >= 1)
+};
+
 struct DevNet {
     int kind = 0;       // 0 occupancy (sigmoid), 1 colour (tanh01)
     int d_in = 0;
@@ -50,7 +65,17 @@ struct DevNet {
     bool tc_ok = false;             // shapes allow the tensor-core form
     std::vector<TcLayer> tc;        // hidden layers only
     CUtensorMap tmX{};              // BF16 gather rows as the A operand
+    // FP8 form (pifu_calibrate_fp8): the first f8.size() hidden layers
+    bool f8_ok = false;
+    std::vector<Fp8Layer> f8;
+    float s_x = 0.f;                // per-tensor scale of the input rows
+    uint64_t f8_version = 0;        // bumped by every calibration
+    CUtensorMap tmX8{};             // E4M3 gather rows as the A operand
 };
+
+bool prec_f8(int p) { return p == PIFU_PREC_FP8 || p == PIFU_PREC_FP8_MIXED; }
+bool prec_mixed(int p) { return p == PIFU_PREC_MIXED || p == PIFU_PREC_FP8_MIXED; }
+bool prec_valid(int p) { return p >= PIFU_PREC_FP32 && p <= PIFU_PREC_FP8; }
 
 int round_up(int v, int m) { return (v + m - 1) / m * m; }
 
@@ -81,6 +106,7 @@ struct FrameKey {
     int use_surrogate;
     float sur_margin;
     uint64_t sur_version;          // f_S's tensor-core weights are rebuilt on change
+    uint64_t f8_version;           // f_O's E4M3 weights are rebuilt by calibration
     int width, height, cam_precision;
     float bg[3];
     float* depth;
@@ -177,6 +203,9 @@ struct pifu_ctx {
     int64_t X_cap = 0, H_cap = 0;   // elements
     __nv_bfloat16* Xb = nullptr;
     __nv_bfloat16* Hb[2] = {nullptr, nullptr};
+    uint8_t* X8 = nullptr;          // [kChunkTC][ldx8] E4M3 gather rows (FP8 forms):
+    int ldx8 = 0;                   //   x_hi at [0, kx8), x_lo at [kx8, 2 kx8)
+    int kx8 = 0;
     float* part = nullptr;            // split-K partial sums of small FP32 batches
     int64_t part_cap = 0;
     // level workspace, sized for ws_N
@@ -370,12 +399,22 @@ int upload_net(pifu_ctx* ctx, const HostNet& hn, DevNet& net) {
     return PIFU_OK;
 }
 
+void free_f8(DevNet& net) {
+    for (auto& Q : net.f8) {
+        dev_free(Q.W);
+        dev_free(Q.colscale);
+    }
+    net.f8.clear();
+    net.f8_ok = false;
+}
+
 void free_net(DevNet& net) {
     for (auto& L : net.layers) {
         dev_free(L.W);
         dev_free(L.b);
     }
     for (auto& T : net.tc) dev_free(T.W);
+    free_f8(net);
     net.layers.clear();
     net.tc.clear();
 }
@@ -469,6 +508,137 @@ int build_tc(pifu_ctx* ctx, const HostNet& hn, DevNet& net) {
     return PIFU_OK;
 }
 
+// ---- FP8 form of f_O ----------------------------------------------------------
+
+uint8_t e4m3_byte(float v) {
+    return (uint8_t)__nv_cvt_float_to_fp8(v, __NV_SATFINITE, __NV_E4M3);
+}
+
+// The E4M3 layers 0 .. F-1 of `net` from its FP32 weights (read back from the
+// device) and the activation scales: net.s_x for the input rows, s_h[l] for
+// h_l (the output of layer l, l < F-1).  The input rows enter as two E4M3
+// terms (x / s_x ~ hi + lo / 16), so a layer's x columns appear twice: once
+// against hi and once, divided by 16, against lo.
+int build_fp8(pifu_ctx* ctx, DevNet& net, int F, const std::vector<float>& s_h) {
+    free_f8(net);
+    const int kx8 = ctx->kx8;
+    const int nk2 = 2 * kx8 / 128;
+    if (!tc_encode_2d_u8(&net.tmX8, ctx->X8, (uint64_t)ctx->ldx8, (uint64_t)kChunkTC,
+                         (uint64_t)ctx->ldx8, 128, 128))
+        return PIFU_ERR_CUDA;
+    net.f8.assign((size_t)F, Fp8Layer{});
+    for (int l = 0; l < F; ++l) {
+        const DevLayer& Ly = net.layers[(size_t)l];
+        Fp8Layer& Q = net.f8[(size_t)l];
+        const bool has_x = Ly.K2 > 0;
+        Q.nk1 = Ly.K1 / 128;
+        Q.nk2 = has_x ? nk2 : 0;
+        Q.Kw = Ly.K1 + (has_x ? 2 * kx8 : 0);
+        Q.BN = net.tc[(size_t)l].BN;
+        const float s_a = l == 0 ? net.s_x : s_h[(size_t)l - 1];
+        const float xf = has_x ? net.s_x / s_a : 0.f;   // x columns in units of s_a
+        std::vector<float> wf((size_t)Ly.n_out * Ly.ldw);
+        CK(cudaMemcpy(wf.data(), Ly.W, wf.size() * 4, cudaMemcpyDeviceToHost));
+        std::vector<uint8_t> w8((size_t)Ly.n_out * Q.Kw, 0);
+        std::vector<float> cs((size_t)Ly.n_out);
+        for (int o = 0; o < Ly.n_out; ++o) {
+            const float* row = &wf[(size_t)o * Ly.ldw];
+            float amax = 0.f;
+            for (int k = 0; k < Ly.K1; ++k) amax = std::max(amax, std::fabs(row[k]));
+            if (has_x)
+                for (int k = 0; k < net.d_in; ++k)
+                    amax = std::max(amax, std::fabs(row[Ly.K1 + k] * xf));
+            const float sw = amax > 0.f ? amax / 448.f : 1.f;
+            uint8_t* dst = &w8[(size_t)o * Q.Kw];
+            for (int k = 0; k < Ly.K1; ++k) dst[k] = e4m3_byte(row[k] / sw);
+            if (has_x)
+                for (int k = 0; k < net.d_in; ++k) {
+                    dst[Ly.K1 + k] = e4m3_byte(row[Ly.K1 + k] * xf / sw);
+                    dst[Ly.K1 + kx8 + k] = e4m3_byte(row[Ly.K1 + k] * xf / (16.f * sw));
+                }
+            cs[(size_t)o] = sw * s_a;
+        }
+        CK(dev_alloc(&Q.W, (int64_t)w8.size()));
+        CK(dev_alloc(&Q.colscale, (int64_t)cs.size()));
+        CK(cudaMemcpy(Q.W, w8.data(), w8.size(), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(Q.colscale, cs.data(), cs.size() * 4, cudaMemcpyHostToDevice));
+        if (!tc_encode_2d_u8(&Q.tmW, Q.W, (uint64_t)Q.Kw, (uint64_t)Ly.n_out, (uint64_t)Q.Kw, 128,
+                             (uint32_t)Q.BN))
+            return PIFU_ERR_CUDA;
+        if (l > 0 && !tc_encode_2d_u8(&Q.tmA1, ctx->Hb[(l - 1) % 2], (uint64_t)Ly.K1,
+                                      (uint64_t)kChunkTC, (uint64_t)Ly.K1, 128, 128))
+            return PIFU_ERR_CUDA;
+        Q.out_scale = l + 1 < F ? 1.f / s_h[(size_t)l] : 1.f;
+    }
+    net.f8_ok = true;
+    ++net.f8_version;
+    return PIFU_OK;
+}
+
+// Activation scales from FP32 evaluations of the input rows and of h_0 ..
+// h_{F-2} at the (n0+1)^3 nodes of the dense grid, then build_fp8.
+int calibrate_fp8(pifu_ctx* ctx, const Map& map, const Calib& cal, int n0, cudaStream_t s) {
+    DevNet& net = ctx->net[0];
+    if (!net.tc_ok) return PIFU_ERR_UNSUPPORTED;
+    const int L = (int)net.layers.size();
+    int F = 0;   // the leading hidden layers with >= 512 outputs
+    while (F + 1 < L && net.layers[(size_t)F].n_out >= 512 &&
+           net.layers[(size_t)F].n_out % 128 == 0 && net.layers[(size_t)F].K1 % 128 == 0)
+        ++F;
+    if (F == 0) return PIFU_ERR_UNSUPPORTED;
+    // [x_hi | x_lo], each padded to whole 128-byte K-blocks; the padding
+    // stays zero (the gather writes only the first ldx bytes of each half)
+    const int kx8 = round_up(std::max(net.d_in, net.ldx), 128);
+    if (!ctx->X8 || ctx->ldx8 != 2 * kx8) {
+        dev_free(ctx->X8);
+        ctx->ldx8 = ctx->kx8 = 0;
+        CK(dev_alloc(&ctx->X8, (int64_t)2 * kx8 * kChunkTC));
+        CK(cudaMemset(ctx->X8, 0, (size_t)2 * kx8 * kChunkTC));
+        ctx->ldx8 = 2 * kx8;
+        ctx->kx8 = kx8;
+    }
+    unsigned int* d_amax = nullptr;
+    CK(cudaMalloc(&d_amax, sizeof(unsigned int) * (size_t)F));
+    cudaError_t e = cudaMemsetAsync(d_amax, 0, sizeof(unsigned int) * (size_t)F, s);
+    const int64_t nodes = (int64_t)(n0 + 1) * (n0 + 1) * (n0 + 1);
+    PointSrc src{PTS_DENSE, nullptr, nullptr, 0, n0, nullptr};
+    for (int64_t p0 = 0; p0 < nodes && e == cudaSuccess; p0 += kChunk) {
+        const int64_t mc = std::min<int64_t>(kChunk, nodes - p0);
+        e = launch_gather(src, p0, mc, cal, map, Map{}, ctx->X, net.ldx, s);
+        if (e == cudaSuccess) e = launch_amax(ctx->X, mc * net.ldx, d_amax, s);
+        const float* h = nullptr;
+        int hw = 0;
+        for (int l = 0; l + 1 < F && e == cudaSuccess; ++l) {
+            const DevLayer& Ly = net.layers[(size_t)l];
+            float* out = (l % 2 == 0) ? ctx->HA : ctx->HB;
+            e = launch_sgemm_bias_lrelu((int)mc, Ly.n_out, h, hw, Ly.K1, ctx->X, net.ldx, Ly.K2,
+                                        Ly.W, Ly.ldw, Ly.b, net.slope, out, Ly.n_out, s, nullptr,
+                                        nullptr);
+            if (e == cudaSuccess) e = launch_amax(out, mc * Ly.n_out, d_amax + 1 + l, s);
+            h = out;
+            hw = Ly.n_out;
+        }
+    }
+    std::vector<unsigned int> bits((size_t)F, 0u);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(bits.data(), d_amax, sizeof(unsigned int) * (size_t)F,
+                            cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(d_amax);
+    if (e != cudaSuccess) return fail_cuda(ctx, e);
+    auto scale = [](unsigned int b) {
+        float a;
+        std::memcpy(&a, &b, 4);
+        return a > 0.f && std::isfinite(a) ? a / 448.f : 1.f;
+    };
+    net.s_x = scale(bits[0]);
+    std::vector<float> s_h;
+    for (int l = 0; l + 1 < F; ++l) s_h.push_back(scale(bits[(size_t)l + 1]));
+    const int st = build_fp8(ctx, net, F, s_h);
+    if (st != PIFU_OK) free_f8(net);
+    return st;
+}
+
 int ensure_level_ws(pifu_ctx* ctx, int N) {
     if (N <= ctx->ws_N) return PIFU_OK;
     uint32_t** bitsets[] = {&ctx->cand, &ctx->tent, &ctx->bin[0], &ctx->bin[1],
@@ -547,8 +717,10 @@ bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
 // (graph form); m is then only the capacity the launches are sized for.
 int run_mlp_tc(pifu_ctx* ctx, const DevNet& net, const PointSrc& src_in, int64_t m,
                const Map& map0, const Map& map1, const Calib& calib, const Epilogue& epi,
-               cudaStream_t s, const unsigned int* m_dev = nullptr) {
+               cudaStream_t s, const unsigned int* m_dev = nullptr, bool f8 = false) {
     if (!net.tc_ok) return PIFU_ERR_UNSUPPORTED;
+    if (f8 && !net.f8_ok) return PIFU_ERR_STATE;
+    const int F = f8 ? (int)net.f8.size() : 0;   // leading E4M3 layers
     if (m_dev && m > kChunkTC) return PIFU_ERR_ARG;
     PointSrc src = src_in;
     src.count = m_dev;
@@ -557,9 +729,13 @@ int run_mlp_tc(pifu_ctx* ctx, const DevNet& net, const PointSrc& src_in, int64_t
     for (int64_t p0 = 0; p0 < m; p0 += kChunkTC) {
         const int64_t mc = std::min<int64_t>(kChunkTC, m - p0);
         cudaEvent_t ev = pr.begin(s);
-        CK(launch_gather_bf16(src, p0, mc, calib, map0, map1, ctx->Xb, net.ldx, s));
+        if (F > 0)
+            CK(launch_gather_dual(src, p0, mc, calib, map0, map1, ctx->Xb, net.ldx, ctx->X8,
+                                  ctx->ldx8, ctx->kx8, 1.f / net.s_x, s));
+        else
+            CK(launch_gather_bf16(src, p0, mc, calib, map0, map1, ctx->Xb, net.ldx, s));
         pr.end(PIFU_K_GATHER, ev, s, 0.0,
-               (double)mc * (4.0 * 4.0 * (map0.C + map1.C) + 2.0 * net.ldx));
+               (double)mc * (4.0 * 4.0 * (map0.C + map1.C) + (F > 0 ? 3.0 : 2.0) * net.ldx));
         // the last layer rides in the last hidden layer's epilogue when that
         // layer is one tile wide and the last layer reads only its output
         const DevLayer& Ll = net.layers[L - 1];
@@ -593,6 +769,21 @@ int run_mlp_tc(pifu_ctx* ctx, const DevNet& net, const PointSrc& src_in, int64_t
             a.err = ctx->d_count + 1;
             a.m_dev = m_dev;
             a.fuse = (fuse && l == L - 2) ? &fl : nullptr;
+            a.mode = TC_BF16;
+            if (l < F) {
+                // E4M3 operands; the last E4M3 layer hands BF16 to the next one
+                const Fp8Layer& Q = net.f8[(size_t)l];
+                a.tmA1 = l > 0 ? &Q.tmA1 : &net.tmX8;
+                a.tmA2 = &net.tmX8;
+                a.tmW = &Q.tmW;
+                a.nk1 = Q.nk1;
+                a.nk2 = Q.nk2;
+                a.BN = Q.BN;
+                a.mode = l + 1 < F ? TC_E4M3_E4M3 : TC_E4M3_BF16;
+                a.colscale = Q.colscale;
+                a.out_scale = Q.out_scale;
+                if (a.fuse) return PIFU_ERR_UNSUPPORTED;
+            }
             double flops = 2.0 * mc * Ly.fan_in * Ly.n_out;
             if (a.fuse) flops += 2.0 * mc * Ll.fan_in * Ll.n_out;
             ev = pr.begin(s);
@@ -616,8 +807,9 @@ int run_mlp_tc(pifu_ctx* ctx, const DevNet& net, const PointSrc& src_in, int64_t
 int run_mlp(pifu_ctx* ctx, const DevNet& net, const PointSrc& src_in, int64_t m, const Map& map0,
             const Map& map1, const Calib& calib, const Epilogue& epi, cudaStream_t s,
             int precision = PIFU_PREC_FP32, const unsigned int* m_dev = nullptr) {
-    if (precision == PIFU_PREC_BF16)
-        return run_mlp_tc(ctx, net, src_in, m, map0, map1, calib, epi, s, m_dev);
+    if (precision == PIFU_PREC_BF16 || precision == PIFU_PREC_FP8)
+        return run_mlp_tc(ctx, net, src_in, m, map0, map1, calib, epi, s, m_dev,
+                          precision == PIFU_PREC_FP8);
     PointSrc src = src_in;
     src.count = m_dev;
     const int L = (int)net.layers.size();
@@ -678,7 +870,7 @@ int read_recheck(pifu_ctx* ctx, cudaStream_t s, unsigned int* out);
 
 int run_mlp_mixed(pifu_ctx* ctx, const DevNet& net, const PointSrc& src, int64_t m,
                   const Map& map0, const Map& map1, const Calib& calib, const Epilogue& epi,
-                  float margin, cudaStream_t s, int64_t* rechecked) {
+                  float margin, cudaStream_t s, int64_t* rechecked, bool f8 = false) {
     if (m > ctx->recheck_cap) return PIFU_ERR_ARG;
     // A tiny batch costs less in FP32 outright than in BF16 plus a re-check
     // pass (both are latency-bound there); FP32 is the re-check's arithmetic.
@@ -688,7 +880,7 @@ int run_mlp_mixed(pifu_ctx* ctx, const DevNet& net, const PointSrc& src, int64_t
     e1.recheck = ctx->recheck;
     e1.recheck_count = ctx->d_recheck;
     e1.margin = margin;
-    int st = run_mlp_tc(ctx, net, src, m, map0, map1, calib, e1, s);
+    int st = run_mlp_tc(ctx, net, src, m, map0, map1, calib, e1, s, nullptr, f8);
     if (st != PIFU_OK) return st;
     unsigned int n = 0;
     st = read_recheck(ctx, s, &n);
@@ -726,8 +918,9 @@ int eval_level_batch(pifu_ctx* ctx, const PointSrc& src, int64_t n, const Map& m
                      float sur_margin, cudaStream_t s, int64_t* rechecked, int64_t* fallback) {
     const DevNet& fo = ctx->net[0];
     if (!surrogate) {
-        return prec == PIFU_PREC_MIXED
-                   ? run_mlp_mixed(ctx, fo, src, n, map, Map{}, cal, epi, margin, s, rechecked)
+        return prec_mixed(prec)
+                   ? run_mlp_mixed(ctx, fo, src, n, map, Map{}, cal, epi, margin, s, rechecked,
+                                   prec == PIFU_PREC_FP8_MIXED)
                    : run_mlp(ctx, fo, src, n, map, Map{}, cal, epi, s, prec);
     }
     if (n > ctx->recheck_cap) return PIFU_ERR_ARG;
@@ -1028,13 +1221,16 @@ int g_eval(pifu_ctx* ctx, const DevNet& net, const PointSrc& src, int64_t cap,
         ef.list = ctx->squeue;
         return g_eval(ctx, net, sf, qcap, ctx->d_squeue, map, cal, ef, prec, margin, rechecked, s);
     }
-    if (prec == PIFU_PREC_BF16) return run_mlp_tc(ctx, net, src, cap, map, Map{}, cal, epi, s, m_dev);
+    if (prec == PIFU_PREC_BF16 || prec == PIFU_PREC_FP8)
+        return run_mlp_tc(ctx, net, src, cap, map, Map{}, cal, epi, s, m_dev,
+                          prec == PIFU_PREC_FP8);
     CK(cudaMemsetAsync(ctx->d_recheck, 0, sizeof(unsigned int), s));
     Epilogue e1 = epi;
     e1.recheck = ctx->recheck;
     e1.recheck_count = ctx->d_recheck;
     e1.margin = margin;
-    int st = run_mlp_tc(ctx, net, src, cap, map, Map{}, cal, e1, s, m_dev);
+    int st = run_mlp_tc(ctx, net, src, cap, map, Map{}, cal, e1, s, m_dev,
+                        prec == PIFU_PREC_FP8_MIXED);
     if (st != PIFU_OK) return st;
     PointSrc s2{PTS_LIST, nullptr, ctx->recheck, 0, src.N, nullptr};
     Epilogue e2 = epi;
@@ -1326,6 +1522,7 @@ void pifu_destroy(pifu_ctx* ctx) {
     dev_free(ctx->Xb);
     dev_free(ctx->Hb[0]);
     dev_free(ctx->Hb[1]);
+    dev_free(ctx->X8);
     dev_free(ctx->part);
     uint32_t** bitsets[] = {&ctx->cand, &ctx->tent, &ctx->bin[0], &ctx->bin[1],
                             &ctx->eval, &ctx->conf[0], &ctx->conf[1]};
@@ -1363,9 +1560,8 @@ int pifu_query_ex(pifu_ctx* ctx, const pifu_fmap* occ_map, const float calib[12]
                   const float* pts_dev, int64_t m, float* occ_dev, int precision, float margin,
                   void* stream) {
     if (!ctx || !calib || m < 0) return PIFU_ERR_ARG;
-    if (precision != PIFU_PREC_FP32 && precision != PIFU_PREC_BF16 && precision != PIFU_PREC_MIXED)
-        return PIFU_ERR_UNSUPPORTED;
-    if (precision == PIFU_PREC_MIXED && !(margin >= 0.f && margin <= 0.5f)) return PIFU_ERR_ARG;
+    if (!prec_valid(precision)) return PIFU_ERR_UNSUPPORTED;
+    if (prec_mixed(precision) && !(margin >= 0.f && margin <= 0.5f)) return PIFU_ERR_ARG;
     if (m == 0) return PIFU_OK;
     if (!pts_dev || !occ_dev || !map_ok(occ_map)) return PIFU_ERR_ARG;
     if (occ_map->dtype != PIFU_F32) return PIFU_ERR_UNSUPPORTED;
@@ -1379,7 +1575,8 @@ int pifu_query_ex(pifu_ctx* ctx, const pifu_fmap* occ_map, const float calib[12]
     epi.act = ACT_SIGMOID;
     epi.out = occ_dev;
     if (precision != PIFU_PREC_FP32 && !ctx->net[0].tc_ok) return PIFU_ERR_UNSUPPORTED;
-    if (precision != PIFU_PREC_MIXED)
+    if (prec_f8(precision) && !ctx->net[0].f8_ok) return PIFU_ERR_STATE;
+    if (!prec_mixed(precision))
         return run_mlp(ctx, ctx->net[0], src, m, to_map(occ_map), Map{}, to_calib(calib), epi, s,
                        precision);
     // mixed: batches of at most one workspace chunk, each BF16 then FP32 for
@@ -1390,7 +1587,8 @@ int pifu_query_ex(pifu_ctx* ctx, const pifu_fmap* occ_map, const float calib[12]
         Epilogue eb = epi;
         eb.out = occ_dev + p0;
         const int st = run_mlp_mixed(ctx, ctx->net[0], sb, mc, to_map(occ_map), Map{},
-                                     to_calib(calib), eb, margin, s, nullptr);
+                                     to_calib(calib), eb, margin, s, nullptr,
+                                     precision == PIFU_PREC_FP8_MIXED);
         if (st != PIFU_OK) return st;
     }
     return PIFU_OK;
@@ -1425,11 +1623,10 @@ int pifu_localize(pifu_ctx* ctx, const pifu_fmap* occ_map, const float calib[12]
         return PIFU_ERR_ARG;
     const int64_t n_fine = (int64_t)lv->n0 << (lv->num_levels - 1);
     if (n_fine > kMaxFine) return PIFU_ERR_ARG;
-    if (lv->precision != PIFU_PREC_FP32 && lv->precision != PIFU_PREC_BF16 &&
-        lv->precision != PIFU_PREC_MIXED)
-        return PIFU_ERR_UNSUPPORTED;
+    if (!prec_valid(lv->precision)) return PIFU_ERR_UNSUPPORTED;
     if (lv->precision != PIFU_PREC_FP32 && !ctx->net[0].tc_ok) return PIFU_ERR_UNSUPPORTED;
-    if (lv->precision == PIFU_PREC_MIXED && !(lv->margin >= 0.f && lv->margin <= 0.5f))
+    if (prec_f8(lv->precision) && !ctx->net[0].f8_ok) return PIFU_ERR_STATE;
+    if (prec_mixed(lv->precision) && !(lv->margin >= 0.f && lv->margin <= 0.5f))
         return PIFU_ERR_ARG;
     const int prec = lv->precision;
     const bool use_sur = lv->use_surrogate != 0;
@@ -1629,8 +1826,9 @@ int pifu_frame(pifu_ctx* ctx, const pifu_fmap* occ_map, const pifu_fmap* col_map
     if (n_fine > kMaxFine) return PIFU_ERR_ARG;
     if (cam->width < 1 || cam->height < 1) return PIFU_ERR_ARG;
     if ((int64_t)cam->width * cam->height > kChunkTC) return PIFU_ERR_CAPACITY;
-    if (lv->precision != PIFU_PREC_BF16 && lv->precision != PIFU_PREC_MIXED) return PIFU_ERR_UNSUPPORTED;
-    if (lv->precision == PIFU_PREC_MIXED && !(lv->margin >= 0.f && lv->margin <= 0.5f))
+    if (!prec_valid(lv->precision) || lv->precision == PIFU_PREC_FP32) return PIFU_ERR_UNSUPPORTED;
+    if (prec_f8(lv->precision) && !ctx->net[0].f8_ok) return PIFU_ERR_STATE;
+    if (prec_mixed(lv->precision) && !(lv->margin >= 0.f && lv->margin <= 0.5f))
         return PIFU_ERR_ARG;
     if (lv->use_surrogate) {
         if (!ctx->sur.ready || !ctx->snet.tc_ok) return PIFU_ERR_STATE;
@@ -1664,7 +1862,8 @@ int pifu_frame(pifu_ctx* ctx, const pifu_fmap* occ_map, const pifu_fmap* col_map
     k.num_levels = lv->num_levels;
     k.precision = lv->precision;
     k.max_rounds = lv->max_rounds > 0 ? lv->max_rounds : 4096;
-    k.margin = lv->precision == PIFU_PREC_MIXED ? lv->margin : 0.f;
+    k.margin = prec_mixed(lv->precision) ? lv->margin : 0.f;
+    k.f8_version = prec_f8(lv->precision) ? ctx->net[0].f8_version : 0;
     if (lv->use_surrogate) {
         k.use_surrogate = 1;
         k.sur_margin = lv->surrogate_margin;
@@ -1719,6 +1918,18 @@ int pifu_frame(pifu_ctx* ctx, const pifu_fmap* occ_map, const pifu_fmap* col_map
     ctx->vol_N = (int)n_fine;
     ctx->vol_bin = cur;
     return PIFU_OK;
+}
+
+int pifu_calibrate_fp8(pifu_ctx* ctx, const pifu_fmap* occ_map, const float calib[12], int n0,
+                       void* stream) {
+    if (!ctx || !calib || !map_ok(occ_map) || n0 < 1 || n0 > 256) return PIFU_ERR_ARG;
+    if (occ_map->dtype != PIFU_F32) return PIFU_ERR_UNSUPPORTED;
+    if (ctx->net[0].d_in != occ_map->C + 1) return PIFU_ERR_ARG;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return PIFU_ERR_CUDA;
+    ctx->g_valid = false;   // a captured frame holds the previous scales
+    return calibrate_fp8(ctx, to_map(occ_map), to_calib(calib), n0,
+                         static_cast<cudaStream_t>(stream));
 }
 
 int pifu_surrogate_init(pifu_ctx* ctx, int h1, int h2, uint64_t seed) {

@@ -90,6 +90,14 @@ cudaError_t launch_gather(const PointSrc& src, int64_t p0, int64_t m, const Cali
                           cudaStream_t stream);
 
 // Same rows in BF16 (the tensor-core MLP's A operand); ldx a multiple of 8.
+// BF16 rows into X and, as two E4M3 terms of x inv_s (hi at byte c, lo =
+// 16 x the remainder at byte lo_off + c), into X8.
+cudaError_t launch_gather_dual(const PointSrc& src, int64_t p0, int64_t m, const Calib& calib,
+                               const Map& map0, const Map& map1, __nv_bfloat16* X, int ldx,
+                               uint8_t* X8, int ldx8, int lo_off, float inv_s,
+                               cudaStream_t stream);
+// *out = max(*out, max_i |p[i]|) with *out holding float bits.
+cudaError_t launch_amax(const float* p, int64_t n, unsigned int* out, cudaStream_t stream);
 cudaError_t launch_gather_bf16(const PointSrc& src, int64_t p0, int64_t m, const Calib& calib,
                                const Map& map0, const Map& map1, __nv_bfloat16* X, int ldx,
                                cudaStream_t stream);
@@ -139,18 +147,27 @@ struct FuseLast {
     Epilogue epi;
 };
 
+// Operand and output types of one tensor-core layer.
+enum TcMode : int {
+    TC_BF16 = 0,       // BF16 A and W, BF16 out
+    TC_E4M3_E4M3 = 1,  // E4M3 A and W, E4M3 out (scaled by out_scale)
+    TC_E4M3_BF16 = 2,  // E4M3 A and W, BF16 out
+};
 struct TcLayerArgs {
     const CUtensorMap* tmA1;
     const CUtensorMap* tmA2;
     const CUtensorMap* tmW;
-    int nk1, nk2, M, N, BN;
+    int nk1, nk2, M, N, BN;       // nk1, nk2: 128-byte K-blocks of the two A segments
     const float* bias;
     float slope;
-    __nv_bfloat16* out;
+    void* out;                    // [M][ldo] of the mode's output type
     int ldo;
     unsigned int* err;
     const unsigned int* m_dev;   // optional device-resident row count (<= M)
-    const FuseLast* fuse;        // optional: last layer fused (requires N == BN)
+    const FuseLast* fuse;        // optional: last layer fused (requires N == BN, TC_BF16)
+    int mode;                    // TcMode
+    const float* colscale;       // E4M3 modes: accumulator scale per output column
+    float out_scale;             // TC_E4M3_E4M3: output multiplied by this before rounding
 };
 cudaError_t launch_tc_linear(const TcLayerArgs& a, cudaStream_t stream);
 // Set the tensor-core kernels' attributes on the current device (before a
@@ -160,6 +177,9 @@ cudaError_t tc_prepare();
 // Encode a 2-D BF16 tensor map (128-byte swizzle, zero fill out of bounds).
 bool tc_encode_2d_bf16(void* map, const void* base, uint64_t cols, uint64_t rows,
                        uint64_t row_stride_bytes, uint32_t box_cols, uint32_t box_rows);
+// The same for 8-bit elements (E4M3 stored as bytes).
+bool tc_encode_2d_u8(void* map, const void* base, uint64_t cols, uint64_t rows,
+                     uint64_t row_stride_bytes, uint32_t box_cols, uint32_t box_rows);
 
 // --- train.cu --------------------------------------------------------------
 // C[m][n] (+)= sum_k A(m, k) B(k, n), A(m, k) = A[m a_m + k a_k],

@@ -31,13 +31,16 @@ PIFU_BF16 = 1
 PIFU_PREC_FP32 = 0
 PIFU_PREC_BF16 = 1
 PIFU_PREC_MIXED = 2
+PIFU_PREC_FP8_MIXED = 3
+PIFU_PREC_FP8 = 4
 
 # Every symbol include/pifu.h declares.
 EXPORTS = ("pifu_create", "pifu_destroy", "pifu_query", "pifu_query_colour", "pifu_localize",
            "pifu_render", "pifu_sync_stats", "pifu_status_string", "pifu_last_error",
            "pifu_profile", "pifu_profile_read", "pifu_query_noalloc", "pifu_query_ex",
            "pifu_frame", "pifu_surrogate_init", "pifu_surrogate_samples", "pifu_surrogate_grad",
-           "pifu_surrogate_train", "pifu_surrogate_params", "pifu_surrogate_query")
+           "pifu_surrogate_train", "pifu_surrogate_params", "pifu_surrogate_query",
+           "pifu_calibrate_fp8")
 
 KERNEL_CLASSES = ("gather", "mlp_hidden", "mlp_last", "level", "select", "render", "mlp_f32")
 
@@ -125,6 +128,8 @@ def _lib():
                                ctypes.POINTER(pifu_camera), P, P, P, P, ctypes.POINTER(pifu_volume)]
     lib.pifu_frame.restype = I
     U64, D = ctypes.c_uint64, ctypes.c_double
+    lib.pifu_calibrate_fp8.argtypes = [P, ctypes.POINTER(pifu_fmap), ctypes.POINTER(F), I, P]
+    lib.pifu_calibrate_fp8.restype = I
     lib.pifu_surrogate_init.argtypes = [P, I, I, U64]
     lib.pifu_surrogate_init.restype = I
     lib.pifu_surrogate_samples.argtypes = [P, ctypes.POINTER(pifu_fmap), ctypes.POINTER(F), P, I64,
@@ -309,6 +314,13 @@ def pifu_frame(ctx, occ_map, col_map, calib, n0, num_levels, width, height, dept
                            _ptr(rgb), _ptr(mask), ctypes.byref(vol))
     _check(st, "pifu_frame", ctx)
     return vol
+
+
+def pifu_calibrate_fp8(ctx, occ_map, calib, n0=32, stream=None):
+    """Scales and E4M3 weights of f_O's FP8 form from the dense n0^3 grid."""
+    fm = fmap(occ_map)
+    _check(_lib().pifu_calibrate_fp8(ctx, ctypes.byref(fm), _calib(calib), n0, _stream(stream)),
+           "pifu_calibrate_fp8", ctx)
 
 
 def pifu_surrogate_init(ctx, h1=128, h2=64, seed=0):

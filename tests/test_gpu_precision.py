@@ -81,3 +81,72 @@ def test_mixed_512_graph_frame(full, oracle512):
     print("mixed 512^3 graph render: mask agreement %.6f, colour PSNR %.1f dB" % (agree, psnr))
     assert agree >= 0.999
     assert psnr >= 40.0
+
+
+# ---- FP8 form: the 1024- and 512-wide layers in E4M3 ------------------------
+
+@pytest.fixture(scope="module")
+def fp8(full):
+    w = full.w
+    with pytest.raises(pifu.PifuError) as ei:
+        full.query(np.zeros((4, 3)), precision=pifu.PIFU_PREC_FP8)
+    assert ei.value.status == pifu.PIFU_ERR_STATE   # not calibrated yet
+    pifu.pifu_calibrate_fp8(full.ctx, full.occ, w.calib, w.n0)
+    return full
+
+
+def test_fp8_query_error_is_bounded(fp8):
+    """E4M3 operands (3 mantissa bits) in the two widest layers, the input
+    rows as two E4M3 terms: the error of the occupancy against FP64 is bounded
+    in distribution (a CPU emulation of the same rounding gives p99 0.026 on
+    the localization's points; with x as one E4M3 term it was 0.09), and the
+    FP32 re-evaluation of FP8_MIXED restores the plain tolerance near 0.5."""
+    w = fp8.w
+    P = synth.distill_points(w.fig, 20000, 99)
+    o = field.occupancy(w.occ_net, w.occ_map, w.calib, P)
+    o8 = fp8.query(P, precision=pifu.PIFU_PREC_FP8)
+    e = np.abs(o8 - o)
+    print("fp8 query: max %.4f p99 %.4f median %.5f" % (e.max(), np.quantile(e, 0.99),
+                                                        np.median(e)))
+    assert np.median(e) <= 0.01
+    assert np.quantile(e, 0.99) <= 0.06
+    assert e.max() <= 0.25
+    om = fp8.query(P, precision=pifu.PIFU_PREC_FP8_MIXED, margin=0.02)
+    near = np.abs(om - 0.5) < 0.02
+    assert np.max(np.abs(om[near] - o[near])) <= 1e-4
+
+
+def test_fp8_mixed_256_matches_oracle(fp8):
+    w = fp8.w
+    lv = localize.hierarchical(lambda P: field.occupancy(w.occ_net, w.occ_map, w.calib, P),
+                               w.n0, w.num_levels)
+    vol = fp8.localize(precision=pifu.PIFU_PREC_FP8_MIXED)
+    b, e, v = fp8.volume_host(vol)
+    iou = metrics.iou(b, lv[-1].binary)
+    ch = metrics.chamfer_voxels(filled(b, e, v), lv[-1].values)
+    print("fp8 mixed 256^3: IoU %.6f, Chamfer %.4f fine voxels, evaluations %d (oracle %d)"
+          % (iou, ch, vol.n_eval, sum(l.n_eval for l in lv)))
+    assert iou >= 0.995
+
+
+def test_fp8_mixed_512_graph_frame(fp8, oracle512):
+    import torch
+    lv, o_rgb, o_hit = oracle512
+    w = fp8.w
+    depth = torch.empty((R, R), dtype=torch.float32, device="cuda")
+    rgb = torch.empty((R, R, 3), dtype=torch.float32, device="cuda")
+    mask = torch.empty((R, R), dtype=torch.uint8, device="cuda")
+    vol = pifu.pifu_frame(fp8.ctx, fp8.occ, fp8.col, w.calib, w.n0, LEVELS, R, R, depth, rgb,
+                          mask, precision=pifu.PIFU_PREC_FP8_MIXED)
+    torch.cuda.synchronize()
+    b, e, v = fp8.volume_host(vol)
+    iou = metrics.iou(b, lv[-1].binary)
+    ch = metrics.chamfer_voxels(filled(b, e, v), lv[-1].values)
+    m = mask.cpu().numpy().astype(bool)
+    both = m & o_hit
+    d = rgb.cpu().numpy().astype(np.float64)[both] - o_rgb[both]
+    psnr = 10 * np.log10(1.0 / np.mean(d * d))
+    print("fp8 mixed 512^3 graph: IoU %.6f, Chamfer %.4f fine voxels, colour PSNR %.1f dB, "
+          "mask disagreement %d px" % (iou, ch, psnr, int(np.count_nonzero(m != o_hit))))
+    assert iou >= 0.995
+    assert psnr >= 40.0
