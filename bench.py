@@ -387,15 +387,15 @@ def train_surrogate(fr, args):
     n = int(x.shape[0])
     del x, y
     torch.cuda.empty_cache()
-    # a high quantile: a confident wrong decision at a coarse level costs
-    # extra conflict rounds at the next one
-    margin, disagree = distill.calibrate_margin(fr.ctx, seeds=[2000, 2001], per_figure=200000,
-                                                quantile=0.999)
+    # the largest held-out disagreement: a confident wrong decision at a
+    # coarse level costs extra conflict rounds at the next one
+    margin, disagree = distill.calibrate_margin(fr.ctx, seeds=[2000, 2001, 2002, 2003],
+                                                per_figure=200000, quantile=1.0)
     torch.cuda.synchronize()
     return margin, {"net": "257-128-64-1 (leaky-ReLU, sigmoid); BF16 tensor cores in the frame",
                     "tuples": n, "figures": args.sur_figures, "steps": args.sur_steps,
                     "batch": 4096, "lr": 3e-3, "loss_first": first, "loss_last": last,
-                    "margin": margin, "margin_quantile": 0.999,
+                    "margin": margin, "margin_quantile": 1.0,
                     "held_out_sign_disagreement": disagree,
                     "train_s": time.perf_counter() - t0,
                     "levels": "all but the finest (the finest level always runs f_O)"}

@@ -203,7 +203,8 @@ struct pifu_ctx {
     int64_t X_cap = 0, H_cap = 0;   // elements
     __nv_bfloat16* Xb = nullptr;
     __nv_bfloat16* Hb[2] = {nullptr, nullptr};
-    uint8_t* X8 = nullptr;          // [kChunkTC][ldx8] E4M3 gather rows (FP8 forms):
+    int64_t tc_rows = 0;            // rows of Xb, Hb[], X8 (grown on demand up to kChunkTC)
+    uint8_t* X8 = nullptr;          // [tc_rows][ldx8] E4M3 gather rows (FP8 forms):
     int ldx8 = 0;                   //   x_hi at [0, kx8), x_lo at [kx8, 2 kx8)
     int kx8 = 0;
     float* part = nullptr;            // split-K partial sums of small FP32 batches
@@ -427,22 +428,16 @@ int ensure_mlp_ws(pifu_ctx* ctx) {
         need_x = std::max<int64_t>(need_x, n.ldx);
         need_h = std::max<int64_t>(need_h, std::max(n.max_hidden, 8));
     }
-    if (need_x > ctx->X_cap) {   // per-point widths; rows are kChunk (FP32) / kChunkTC (BF16)
+    if (need_x > ctx->X_cap) {   // per-point widths; FP32 rows are kChunk points
         dev_free(ctx->X);
-        dev_free(ctx->Xb);
         CK(dev_alloc(&ctx->X, need_x * kChunk));
-        CK(dev_alloc(&ctx->Xb, need_x * kChunkTC));
         ctx->X_cap = need_x;
     }
     if (need_h > ctx->H_cap) {
         dev_free(ctx->HA);
         dev_free(ctx->HB);
-        dev_free(ctx->Hb[0]);
-        dev_free(ctx->Hb[1]);
         CK(dev_alloc(&ctx->HA, need_h * kChunk));
         CK(dev_alloc(&ctx->HB, need_h * kChunk));
-        CK(dev_alloc(&ctx->Hb[0], need_h * kChunkTC));
-        CK(dev_alloc(&ctx->Hb[1], need_h * kChunkTC));
         ctx->H_cap = need_h;
     }
     // split-K partial sums: host-sized batches up to kSplitMaxM, device-sized
@@ -464,6 +459,68 @@ int ensure_mlp_ws(pifu_ctx* ctx) {
 // Tensor-core form of a net: BF16 weights and the tensor maps over them and
 // over the BF16 workspaces (which must already exist).  Nets whose hidden
 // widths are not multiples of 64 keep tc_ok = false.
+// TMA maps of a network's activation operands (gather rows, previous layer
+// outputs) over the current tensor-core workspaces of tc_rows rows.
+int encode_act_maps(pifu_ctx* ctx, DevNet& net) {
+    if (!net.tc_ok || ctx->tc_rows == 0) return PIFU_OK;
+    const uint64_t rows = (uint64_t)ctx->tc_rows;
+    if (!tc_encode_2d_bf16(&net.tmX, ctx->Xb, (uint64_t)net.d_in, rows, (uint64_t)net.ldx * 2, 64,
+                           128))
+        return PIFU_ERR_CUDA;
+    for (size_t l = 1; l < net.tc.size(); ++l) {
+        const DevLayer& Ly = net.layers[l];
+        if (!tc_encode_2d_bf16(&net.tc[l].tmA1, ctx->Hb[(l - 1) % 2], (uint64_t)Ly.K1, rows,
+                               (uint64_t)Ly.K1 * 2, 64, 128))
+            return PIFU_ERR_CUDA;
+    }
+    if (net.f8_ok) {
+        if (!tc_encode_2d_u8(&net.tmX8, ctx->X8, (uint64_t)ctx->ldx8, rows, (uint64_t)ctx->ldx8,
+                             128, 128))
+            return PIFU_ERR_CUDA;
+        for (size_t l = 1; l < net.f8.size(); ++l) {
+            const DevLayer& Ly = net.layers[l];
+            if (!tc_encode_2d_u8(&net.f8[l].tmA1, ctx->Hb[(l - 1) % 2], (uint64_t)Ly.K1, rows,
+                                 (uint64_t)Ly.K1, 128, 128))
+                return PIFU_ERR_CUDA;
+        }
+    }
+    return PIFU_OK;
+}
+
+int encode_all_act_maps(pifu_ctx* ctx);
+
+// Grow the tensor-core workspaces to at least `rows` points (powers of two
+// from 65,536 up to kChunkTC).  Growing frees the old buffers (cudaFree waits
+// for the device) and invalidates a captured frame graph, which holds maps
+// of them; the graph form reserves kChunkTC rows before it captures.
+int ensure_tc_rows(pifu_ctx* ctx, int64_t rows) {
+    if (rows <= ctx->tc_rows) return PIFU_OK;
+    if (rows > kChunkTC) return PIFU_ERR_ARG;
+    int64_t cap = 65536;
+    while (cap < rows) cap *= 2;
+    cap = std::min<int64_t>(cap, kChunkTC);
+    int64_t need_x = 0, need_h = 0;
+    for (const DevNet& n : ctx->net) {
+        need_x = std::max<int64_t>(need_x, n.ldx);
+        need_h = std::max<int64_t>(need_h, std::max(n.max_hidden, 8));
+    }
+    ctx->g_valid = false;
+    dev_free(ctx->Xb);
+    dev_free(ctx->Hb[0]);
+    dev_free(ctx->Hb[1]);
+    dev_free(ctx->X8);
+    ctx->tc_rows = 0;
+    CK(dev_alloc(&ctx->Xb, need_x * cap));
+    CK(dev_alloc(&ctx->Hb[0], need_h * cap));
+    CK(dev_alloc(&ctx->Hb[1], need_h * cap));
+    if (ctx->ldx8 > 0) {
+        CK(dev_alloc(&ctx->X8, (int64_t)ctx->ldx8 * cap));
+        CK(cudaMemset(ctx->X8, 0, (size_t)ctx->ldx8 * cap));
+    }
+    ctx->tc_rows = cap;
+    return encode_all_act_maps(ctx);
+}
+
 int build_tc(pifu_ctx* ctx, const HostNet& hn, DevNet& net) {
     const int L = (int)net.layers.size();
     net.tc_ok = false;
@@ -471,9 +528,6 @@ int build_tc(pifu_ctx* ctx, const HostNet& hn, DevNet& net) {
     for (int l = 0; l + 1 < L; ++l)
         if (net.layers[l].n_out % 64 != 0) return PIFU_OK;
     const int k2pad = round_up(net.d_in, 64);
-    if (!tc_encode_2d_bf16(&net.tmX, ctx->Xb, (uint64_t)net.d_in, (uint64_t)kChunkTC,
-                           (uint64_t)net.ldx * 2, 64, 128))
-        return PIFU_ERR_CUDA;
     for (int l = 0; l + 1 < L; ++l) {
         const DevLayer& Ly = net.layers[l];
         TcLayer& T = net.tc[l];
@@ -497,15 +551,9 @@ int build_tc(pifu_ctx* ctx, const HostNet& hn, DevNet& net) {
         if (!tc_encode_2d_bf16(&T.tmW, T.W, (uint64_t)T.Kw, (uint64_t)Ly.n_out, (uint64_t)T.Kw * 2,
                                64, (uint32_t)T.BN))
             return PIFU_ERR_CUDA;
-        if (l > 0) {
-            const __nv_bfloat16* src = ctx->Hb[(l - 1) % 2];
-            if (!tc_encode_2d_bf16(&T.tmA1, src, (uint64_t)Ly.K1, (uint64_t)kChunkTC,
-                                   (uint64_t)Ly.K1 * 2, 64, 128))
-                return PIFU_ERR_CUDA;
-        }
     }
     net.tc_ok = true;
-    return PIFU_OK;
+    return encode_act_maps(ctx, net);
 }
 
 // ---- FP8 form of f_O ----------------------------------------------------------
@@ -523,9 +571,6 @@ int build_fp8(pifu_ctx* ctx, DevNet& net, int F, const std::vector<float>& s_h) 
     free_f8(net);
     const int kx8 = ctx->kx8;
     const int nk2 = 2 * kx8 / 128;
-    if (!tc_encode_2d_u8(&net.tmX8, ctx->X8, (uint64_t)ctx->ldx8, (uint64_t)kChunkTC,
-                         (uint64_t)ctx->ldx8, 128, 128))
-        return PIFU_ERR_CUDA;
     net.f8.assign((size_t)F, Fp8Layer{});
     for (int l = 0; l < F; ++l) {
         const DevLayer& Ly = net.layers[(size_t)l];
@@ -565,14 +610,11 @@ int build_fp8(pifu_ctx* ctx, DevNet& net, int F, const std::vector<float>& s_h) 
         if (!tc_encode_2d_u8(&Q.tmW, Q.W, (uint64_t)Q.Kw, (uint64_t)Ly.n_out, (uint64_t)Q.Kw, 128,
                              (uint32_t)Q.BN))
             return PIFU_ERR_CUDA;
-        if (l > 0 && !tc_encode_2d_u8(&Q.tmA1, ctx->Hb[(l - 1) % 2], (uint64_t)Ly.K1,
-                                      (uint64_t)kChunkTC, (uint64_t)Ly.K1, 128, 128))
-            return PIFU_ERR_CUDA;
         Q.out_scale = l + 1 < F ? 1.f / s_h[(size_t)l] : 1.f;
     }
     net.f8_ok = true;
     ++net.f8_version;
-    return PIFU_OK;
+    return encode_act_maps(ctx, net);
 }
 
 // Activation scales from FP32 evaluations of the input rows and of h_0 ..
@@ -589,11 +631,13 @@ int calibrate_fp8(pifu_ctx* ctx, const Map& map, const Calib& cal, int n0, cudaS
     // [x_hi | x_lo], each padded to whole 128-byte K-blocks; the padding
     // stays zero (the gather writes only the first ldx bytes of each half)
     const int kx8 = round_up(std::max(net.d_in, net.ldx), 128);
+    int st0 = ensure_tc_rows(ctx, 1);
+    if (st0 != PIFU_OK) return st0;
     if (!ctx->X8 || ctx->ldx8 != 2 * kx8) {
         dev_free(ctx->X8);
         ctx->ldx8 = ctx->kx8 = 0;
-        CK(dev_alloc(&ctx->X8, (int64_t)2 * kx8 * kChunkTC));
-        CK(cudaMemset(ctx->X8, 0, (size_t)2 * kx8 * kChunkTC));
+        CK(dev_alloc(&ctx->X8, (int64_t)2 * kx8 * ctx->tc_rows));
+        CK(cudaMemset(ctx->X8, 0, (size_t)2 * kx8 * ctx->tc_rows));
         ctx->ldx8 = 2 * kx8;
         ctx->kx8 = kx8;
     }
@@ -721,6 +765,10 @@ int run_mlp_tc(pifu_ctx* ctx, const DevNet& net, const PointSrc& src_in, int64_t
     if (!net.tc_ok) return PIFU_ERR_UNSUPPORTED;
     if (f8 && !net.f8_ok) return PIFU_ERR_STATE;
     const int F = f8 ? (int)net.f8.size() : 0;   // leading E4M3 layers
+    {
+        const int st = ensure_tc_rows(ctx, m_dev ? kChunkTC : std::min<int64_t>(m, kChunkTC));
+        if (st != PIFU_OK) return st;
+    }
     if (m_dev && m > kChunkTC) return PIFU_ERR_ARG;
     PointSrc src = src_in;
     src.count = m_dev;
@@ -1052,6 +1100,14 @@ int sur_build_tc(pifu_ctx* ctx) {
         hn.b[l].assign(p.begin() + S.off_b[l], p.begin() + S.off_b[l] + round_up(L.n_out, 4));
     }
     return build_tc(ctx, hn, n);
+}
+
+int encode_all_act_maps(pifu_ctx* ctx) {
+    for (DevNet& n : ctx->net) {
+        const int st = encode_act_maps(ctx, n);
+        if (st != PIFU_OK) return st;
+    }
+    return ctx->sur.ready ? encode_act_maps(ctx, ctx->snet) : PIFU_OK;
 }
 
 int sur_init(pifu_ctx* ctx, int h1, int h2, uint64_t seed) {
@@ -1406,6 +1462,11 @@ int g_build(pifu_ctx* ctx, const FrameKey& k, const Map& occ, const Map& col, co
     if (!ctx->d_gstats) CK(dev_alloc(&ctx->d_gstats, 1));
     if (!ctx->h_gstats) CK(cudaHostAlloc(&ctx->h_gstats, sizeof(GraphStats), cudaHostAllocDefault));
     CK(tc_prepare());
+    {
+        // device-sized batches: the workspaces must hold a whole capacity
+        const int st = ensure_tc_rows(ctx, kChunkTC);
+        if (st != PIFU_OK) return st;
+    }
     const bool prof_on = ctx->prof.on;
     ctx->prof.on = false;   // no timing events inside a graph
     const int64_t before = launches_now(ctx);
