@@ -81,7 +81,8 @@ typedef enum {
 typedef struct {
     const void* data;   /* device pointer, 16-byte aligned                    */
     int32_t H, W, C;    /* H, W >= 1; C a multiple of 4                         */
-    int32_t dtype;      /* pifu_dtype                                          */
+    int32_t dtype;      /* pifu_dtype: F32, or BF16 (read as float; storage    *
+                         * precision only -- the arithmetic is unchanged)      */
 } pifu_fmap;
 
 /* Coarse-to-fine schedule (Sec. 3.2): dense evaluation at n0 cells per axis,
@@ -212,6 +213,51 @@ int pifu_frame(pifu_ctx* ctx, const pifu_fmap* occ_map, const pifu_fmap* col_map
                const float calib[12], const pifu_levels* levels, const pifu_camera* cam,
                void* stream, float* depth_dev, float* rgb_dev, uint8_t* mask_dev,
                pifu_volume* out);
+
+/* ---- Lockstep batch of frames (not in the paper) ------------------------------
+ * Localization + render of B independent frames (1 <= B <= 64) that advance
+ * together.  Every level's set-up, dilation and compaction runs over all B
+ * frames at once.  Every evaluation batch is one device-sized list of
+ * (frame, node) keys for all frames, so one persistent tensor-core launch per
+ * MLP layer serves all B frames.  A level's conflict loop runs while any
+ * frame has a frontier (the rounds of the batch are those of its slowest
+ * frame).  Each frame's result equals what pifu_frame computes for it alone.
+ * The B frames' pipeline is one CUDA graph, captured per argument set: B, the
+ * maps' shapes and types, levels, camera and output pointers.  The map
+ * pointers and calibrations are read on the device, so consecutive batches
+ * with new maps relaunch the same graph.
+ *   occ_maps[f], col_maps[f]  frame f's maps (device pointers; the same shape
+ *                             and type for all f; col_maps may be null)
+ *   calibs                    B x 12 floats (host), frame f's calibration
+ *   depth_dev, rgb_dev, mask_dev  [B][height][width] (rgb x3) device outputs,
+ *                             each may be null
+ *   out                       B volumes (views into the context, valid until
+ *                             the next pifu_frames): per-level evaluation and
+ *                             candidate counts of each frame; conflict_rounds,
+ *                             rechecked_per_level and fallback_per_level are
+ *                             the batch's.
+ * Synchronises `stream` once.  Precisions and errors as pifu_frame;
+ * PIFU_ERR_CAPACITY when one round's keys exceed the batch capacity
+ * (B x 2^18 rounded up to a power of two, between 2^20 and 2^22) or
+ * B x width x height exceeds 2^22. */
+int pifu_frames(pifu_ctx* ctx, int B, const pifu_fmap* occ_maps, const pifu_fmap* col_maps,
+                const float* calibs, const pifu_levels* levels, const pifu_camera* cam,
+                void* stream, float* depth_dev, float* rgb_dev, uint8_t* mask_dev,
+                pifu_volume* out);
+
+/* ---- Tile autotuner (not in the paper) ----------------------------------------
+ * Times every tensor-core hidden layer of f_O and f_T (and of f_O's E4M3
+ * layers once calibrated) on a batch of `rows` points (128 .. 2^22) with each
+ * output tile width BN in {64, 128, 256} dividing its width (the layer into
+ * whose epilogue the last layer is fused keeps BN = its width), keeps the
+ * fastest, and invalidates captured graphs.  The contents of the activation
+ * workspaces are whatever they hold (only the timing matters).  Writes the
+ * chosen BN and the mean ms per launch of each tuned layer, in order (f_O
+ * layers, each E4M3 form before the BF16 form, then f_T), into bn_out /
+ * ms_out (up to n_max entries, either may be null) and their number into
+ * *n_layers.  Synchronises `stream`. */
+int pifu_autotune(pifu_ctx* ctx, int64_t rows, void* stream, int32_t* bn_out, double* ms_out,
+                  int n_max, int* n_layers);
 
 /* ---- FP8 form of f_O (not in the paper) --------------------------------------
  * Calibrates and builds the E4M3 layers used by PIFU_PREC_FP8 and

@@ -40,9 +40,21 @@ __device__ __forceinline__ void last_epilogue(const Epilogue& epi, int64_t p, in
         // value, set the binarized bit, and flag a conflict when the
         // binarized prediction differs from the binarized interpolation.
         const float o = apply_act(ACT_SIGMOID, t[0] + bias[0]);
-        const int64_t idx = epi.list ? (int64_t)epi.list[p] : epi.base + p;
+        int64_t idx = epi.list ? (int64_t)epi.list[p] : epi.base + p;
         const LevelBits& lv = epi.lv;
-        lv.values[idx] = o;
+        float* values = lv.values;
+        const uint32_t* tent = lv.tent;
+        uint32_t* bin = lv.bin;
+        uint32_t* conf = lv.conf;
+        if (lv.key_div) {   // several frames: key = frame * key_div + node
+            const int64_t f = idx / lv.key_div;
+            idx -= f * lv.key_div;
+            values += f * lv.slot_nodes;
+            tent += f * lv.slot_words;
+            bin += f * lv.slot_words;
+            conf += f * lv.slot_words;
+        }
+        values[idx] = o;
         const int64_t n1 = lv.N + 1;
         const int64_t row = idx / n1;            // k (N+1) + j
         const int i = (int)(idx - row * n1);
@@ -50,13 +62,13 @@ __device__ __forceinline__ void last_epilogue(const Epilogue& epi, int64_t p, in
         const uint32_t bit = 1u << (i & 31);
         const bool ob = o >= kHalf;
         if (lv.first_level) {
-            if (ob) atomicOr(&lv.bin[w], bit);
+            if (ob) atomicOr(&bin[w], bit);
         } else {
-            const bool tb = (lv.tent[w] & bit) != 0u;
+            const bool tb = (tent[w] & bit) != 0u;
             if (ob != tb) {
-                atomicOr(&lv.conf[w], bit);
-                if (ob) atomicOr(&lv.bin[w], bit);
-                else atomicAnd(&lv.bin[w], ~bit);
+                atomicOr(&conf[w], bit);
+                if (ob) atomicOr(&bin[w], bit);
+                else atomicAnd(&bin[w], ~bit);
             }
         }
     }

@@ -52,16 +52,26 @@ __device__ __forceinline__ void texel_coord(float hi, float lo, int W, int& i0, 
     i0 = (int)fmaxf(fminf(fl, (float)W + 1.f), -2.f);   // NaN -> W + 1 (clamped below)
 }
 
-__device__ __forceinline__ void point_xyz(const PointSrc& src, int64_t p, float& x, float& y,
-                                          float& z) {
+__device__ __forceinline__ float4 ld4(const float* p) {
+    return __ldg(reinterpret_cast<const float4*>(p));
+}
+
+// Position of point p; returns its frame (0 unless the source spans frames).
+__device__ __forceinline__ int point_xyz(const PointSrc& src, int64_t p, float& x, float& y,
+                                         float& z) {
     if (src.mode == PTS_XYZ || src.mode == PTS_XYZ_IDX) {
         const int64_t q = src.mode == PTS_XYZ ? p : (int64_t)src.list[p];
         x = src.xyz[3 * q + 0];
         y = src.xyz[3 * q + 1];
         z = src.xyz[3 * q + 2];
-        return;
+        return src.maps0 ? (int)((int64_t)src.keys[p] / src.slot_div) : 0;
     }
-    const int64_t idx = (src.mode == PTS_LIST) ? (int64_t)src.list[p] : src.base + p;
+    int64_t idx = (src.mode == PTS_LIST) ? (int64_t)src.list[p] : src.base + p;
+    int f = 0;
+    if (src.maps0) {
+        f = (int)(idx / src.slot_div);
+        idx -= (int64_t)f * src.slot_div;
+    }
     const int64_t n1 = src.N + 1;
     const int i = (int)(idx % n1);
     const int j = (int)((idx / n1) % n1);
@@ -70,19 +80,30 @@ __device__ __forceinline__ void point_xyz(const PointSrc& src, int64_t p, float&
     x = __fmaf_rn((float)i, h, -1.0f);
     y = __fmaf_rn((float)j, h, -1.0f);
     z = __fmaf_rn((float)k, h, -1.0f);
+    return f;
 }
 
-__device__ __forceinline__ float4 ld4(const float* p) {
-    return __ldg(reinterpret_cast<const float4*>(p));
+// Four consecutive channels of a texel as floats (FP32 or BF16 storage).
+__device__ __forceinline__ float4 tap4(const Map& mp, int64_t e) {
+    if (mp.dtype == 1) {
+        const uint2 v = __ldg(reinterpret_cast<const uint2*>(static_cast<const uint16_t*>(mp.data) + e));
+        return make_float4(__uint_as_float(v.x << 16), __uint_as_float(v.x & 0xffff0000u),
+                           __uint_as_float(v.y << 16), __uint_as_float(v.y & 0xffff0000u));
+    }
+    return ld4(static_cast<const float*>(mp.data) + e);
 }
 
 // Channels c..c+3 of the MLP input row of point p: the bilinear sample of
 // map0 (channels [0, C0)) or map1 ([C0, C0 + C1)) at the point's projection,
 // then the projected depth at C0 + C1, then zero padding.
-__device__ __forceinline__ float4 gather_quad(const PointSrc& src, int64_t p, const Calib& calib,
-                                              const Map& map0, const Map& map1, int c) {
+__device__ __forceinline__ float4 gather_quad(const PointSrc& src, int64_t p, const Calib& calib_in,
+                                              const Map& map0_in, const Map& map1_in, int c) {
     float x, y, z;
-    point_xyz(src, p, x, y, z);
+    const int f = point_xyz(src, p, x, y, z);
+    const bool multi = src.maps0 != nullptr;
+    const Calib& calib = multi ? src.calibs[f] : calib_in;
+    const Map map0 = multi ? src.maps0[f] : map0_in;
+    const Map map1 = multi ? (src.maps1 ? src.maps1[f] : Map{nullptr, 0, 0, 0, 0}) : map1_in;
     float uh, ul, vh, vl, zh, zl;
     affine_ff(calib.c + 0, x, y, z, uh, ul);
     affine_ff(calib.c + 4, x, y, z, vh, vl);
@@ -101,11 +122,10 @@ __device__ __forceinline__ float4 gather_quad(const PointSrc& src, int64_t p, co
         const int j1 = min(max(j0 + 1, 0), mp.H - 1);
         i0 = min(max(i0, 0), mp.W - 1);
         j0 = min(max(j0, 0), mp.H - 1);
-        const float* F = static_cast<const float*>(mp.data);
-        const float4 f00 = ld4(F + ((int64_t)j0 * mp.W + i0) * mp.C + cc);
-        const float4 f10 = ld4(F + ((int64_t)j0 * mp.W + i1) * mp.C + cc);
-        const float4 f01 = ld4(F + ((int64_t)j1 * mp.W + i0) * mp.C + cc);
-        const float4 f11 = ld4(F + ((int64_t)j1 * mp.W + i1) * mp.C + cc);
+        const float4 f00 = tap4(mp, ((int64_t)j0 * mp.W + i0) * mp.C + cc);
+        const float4 f10 = tap4(mp, ((int64_t)j0 * mp.W + i1) * mp.C + cc);
+        const float4 f01 = tap4(mp, ((int64_t)j1 * mp.W + i0) * mp.C + cc);
+        const float4 f11 = tap4(mp, ((int64_t)j1 * mp.W + i1) * mp.C + cc);
         const float w00 = (1.f - a) * (1.f - b), w10 = a * (1.f - b);
         const float w01 = (1.f - a) * b, w11 = a * b;
         r.x = fmaf(w11, f11.x, fmaf(w01, f01.x, fmaf(w10, f10.x, w00 * f00.x)));

@@ -10,6 +10,10 @@
 // warp-aggregated prefix sum of popcounts (one atomic per warp).  At 256^3 a
 // bitset is 2.4 MB; the whole level's bookkeeping touches ~15 MB, against
 // hundreds of MFLOP per evaluated point of MLP work.
+//
+// Several frames in lockstep: blockIdx.y is the frame; its bitsets start
+// `fslot` words (coarse: `cslot`) further, and the node keys it appends are
+// frame * slot_nodes + node, into one list for all frames.
 #include "pifu_internal.h"
 
 namespace pifu {
@@ -40,7 +44,17 @@ __global__ void __launch_bounds__(256) classify_kernel(const uint32_t* __restric
                                                        uint32_t* __restrict__ tent,
                                                        uint32_t* __restrict__ bin,
                                                        uint32_t* __restrict__ eval,
-                                                       uint32_t* __restrict__ conf0) {
+                                                       uint32_t* __restrict__ conf0,
+                                                       int64_t cslot, int64_t fslot) {
+    {
+        const int64_t f = blockIdx.y;
+        coarse += f * cslot;
+        cand += f * fslot;
+        tent += f * fslot;
+        bin += f * fslot;
+        eval += f * fslot;
+        conf0 += f * fslot;
+    }
     const int n1 = N + 1;
     const int rw = row_words_of(N);
     const int Nc = N / 2;
@@ -90,17 +104,18 @@ __global__ void __launch_bounds__(256) dense_setup_kernel(int N, uint32_t* __res
                                                           uint32_t* __restrict__ tent,
                                                           uint32_t* __restrict__ bin,
                                                           uint32_t* __restrict__ eval,
-                                                          uint32_t* __restrict__ conf0) {
+                                                          uint32_t* __restrict__ conf0,
+                                                          int64_t fslot) {
     const int n1 = N + 1;
     const int rw = row_words_of(N);
     const int64_t total = (int64_t)n1 * n1 * rw;
-    const int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (w >= total) return;
+    const int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x + blockIdx.y * fslot;
+    if (w - (int64_t)blockIdx.y * fslot >= total) return;
     cand[w] = 0u;
     tent[w] = 0u;
     bin[w] = 0u;
     conf0[w] = 0u;
-    eval[w] = valid_mask(N, (int)(w % rw));
+    eval[w] = valid_mask(N, (int)((w - (int64_t)blockIdx.y * fslot) % rw));
 }
 
 // sel = dilate26(src) & ~eval, restricted to the grid; eval |= sel; compact.
@@ -108,7 +123,14 @@ __global__ void __launch_bounds__(256) dilate_select_kernel(const uint32_t* __re
                                                             uint32_t* __restrict__ eval,
                                                             uint32_t* __restrict__ clear, int N,
                                                             int* __restrict__ list,
-                                                            unsigned int* __restrict__ count) {
+                                                            unsigned int* __restrict__ count,
+                                                            int64_t fslot, int64_t slot_nodes) {
+    {
+        const int64_t f = blockIdx.y;
+        src += f * fslot;
+        eval += f * fslot;
+        if (clear) clear += f * fslot;
+    }
     const int n1 = N + 1;
     const int rw = row_words_of(N);
     const int64_t total = (int64_t)n1 * n1 * rw;
@@ -156,7 +178,7 @@ __global__ void __launch_bounds__(256) dilate_select_kernel(const uint32_t* __re
     base = __shfl_sync(0xffffffffu, base, 31);
     if (n) {
         int pos = (int)base + incl - n;
-        const int64_t node0 = row * n1 + (int64_t)wx * 32;
+        const int64_t node0 = row * n1 + (int64_t)wx * 32 + (int64_t)blockIdx.y * slot_nodes;
         uint32_t s = sel;
         while (s) {
             const int b = __ffs(s) - 1;
@@ -168,7 +190,10 @@ __global__ void __launch_bounds__(256) dilate_select_kernel(const uint32_t* __re
 
 __global__ void __launch_bounds__(256) popcount_kernel(const uint32_t* __restrict__ bits,
                                                        int64_t words,
-                                                       unsigned long long* __restrict__ count) {
+                                                       unsigned long long* __restrict__ count,
+                                                       int64_t fslot) {
+    bits += (int64_t)blockIdx.y * fslot;   // frame blockIdx.y into count[blockIdx.y]
+    count += blockIdx.y;
     unsigned long long local = 0;
     for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < words;
          w += (int64_t)gridDim.x * blockDim.x)
@@ -214,23 +239,29 @@ inline unsigned blocks_for(int64_t n) { return (unsigned)((n + 255) / 256); }
 }  // namespace
 
 cudaError_t launch_classify(const uint32_t* coarse_bin, int N, uint32_t* cand, uint32_t* tent,
-                            uint32_t* bin, uint32_t* eval, uint32_t* conf0, cudaStream_t stream) {
-    classify_kernel<<<blocks_for(words_of(N)), 256, 0, stream>>>(coarse_bin, N, cand, tent, bin,
-                                                                eval, conf0);
+                            uint32_t* bin, uint32_t* eval, uint32_t* conf0, cudaStream_t stream,
+                            int slots, int64_t cslot, int64_t fslot) {
+    if (slots < 1 || slots > 65535) return cudaErrorInvalidValue;
+    classify_kernel<<<dim3(blocks_for(words_of(N)), (unsigned)slots), 256, 0, stream>>>(
+        coarse_bin, N, cand, tent, bin, eval, conf0, cslot, fslot);
     return cudaGetLastError();
 }
 
 cudaError_t launch_dense_setup(int N, uint32_t* cand, uint32_t* tent, uint32_t* bin,
-                               uint32_t* eval, uint32_t* conf0, cudaStream_t stream) {
-    dense_setup_kernel<<<blocks_for(words_of(N)), 256, 0, stream>>>(N, cand, tent, bin, eval,
-                                                                   conf0);
+                               uint32_t* eval, uint32_t* conf0, cudaStream_t stream, int slots,
+                               int64_t fslot) {
+    if (slots < 1 || slots > 65535) return cudaErrorInvalidValue;
+    dense_setup_kernel<<<dim3(blocks_for(words_of(N)), (unsigned)slots), 256, 0, stream>>>(
+        N, cand, tent, bin, eval, conf0, fslot);
     return cudaGetLastError();
 }
 
 cudaError_t launch_dilate_select(const uint32_t* src, uint32_t* eval, uint32_t* clear, int N,
-                                 int* list, unsigned int* count, cudaStream_t stream) {
-    dilate_select_kernel<<<blocks_for(words_of(N)), 256, 0, stream>>>(src, eval, clear, N, list,
-                                                                     count);
+                                 int* list, unsigned int* count, cudaStream_t stream, int slots,
+                                 int64_t fslot, int64_t slot_nodes) {
+    if (slots < 1 || slots > 65535) return cudaErrorInvalidValue;
+    dilate_select_kernel<<<dim3(blocks_for(words_of(N)), (unsigned)slots), 256, 0, stream>>>(
+        src, eval, clear, N, list, count, fslot, slot_nodes);
     return cudaGetLastError();
 }
 
@@ -248,8 +279,10 @@ cudaError_t launch_accumulate(unsigned long long* dst, const unsigned int* src, 
 }
 
 cudaError_t launch_popcount(const uint32_t* bits, int64_t words, unsigned long long* count,
-                            cudaStream_t stream) {
-    popcount_kernel<<<152 * 4, 256, 0, stream>>>(bits, words, count);
+                            cudaStream_t stream, int slots, int64_t fslot) {
+    if (slots < 1 || slots > 65535) return cudaErrorInvalidValue;
+    const unsigned gx = slots > 1 ? 152u : 152u * 4u;
+    popcount_kernel<<<dim3(gx, (unsigned)slots), 256, 0, stream>>>(bits, words, count, fslot);
     return cudaGetLastError();
 }
 

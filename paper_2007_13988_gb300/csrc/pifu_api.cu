@@ -20,6 +20,8 @@ constexpr int kMaxLevels = 8;
 constexpr int kMaxFine = 512;
 constexpr int64_t kChunk = 65536;    // points per FP32 MLP pass (bounds its activation workspace)
 constexpr int64_t kChunkTC = 1 << 20; // points per tensor-core MLP pass (a whole 512^3 level list)
+constexpr int64_t kTcRowsMax = 1 << 22; // device-sized batches of a lockstep frame batch
+constexpr int kMaxBatch = 64;           // frames of a lockstep batch
 constexpr int64_t kRecheckCap = 8192; // graph form: FP32 re-checks per batch (split-K path)
 constexpr int64_t kFusedMaxM = 2048;   // host-sized FP32 batches up to this size: fused kernel
 constexpr int64_t kTinyBatch = 256; // mixed precision: batches this small run in FP32
@@ -192,6 +194,69 @@ struct Profiler {
 
 }  // namespace
 
+// Device-side counters of a lockstep batch, copied to the host once at its end.
+struct BatchStats {
+    unsigned long long evals[8][kMaxBatch];   // per level and frame: evaluated nodes
+    unsigned long long cands[8][kMaxBatch];   // per level and frame: boundary candidates
+    unsigned long long keys[8];               // per level: keys evaluated, all frames
+    unsigned long long rechecked[8];
+    unsigned long long fallback[8];
+    unsigned int rounds[8];
+    unsigned int err;
+    unsigned int pad;
+};
+
+// Everything a captured batch graph depends on besides the map pointers and
+// calibrations (read on the device).
+struct BatchKey {
+    int B;
+    int oH, oW, oC, odt, cH, cW, cC, cdt;
+    int n0, num_levels, precision, max_rounds;
+    float margin;
+    int use_surrogate;
+    float sur_margin;
+    uint64_t sur_version;
+    uint64_t f8_version;
+    int width, height;
+    float bg[3];
+    float* depth;
+    float* rgb;
+    uint8_t* mask;
+};
+
+// Per-frame level state of a lockstep batch: B slots of the finest level's
+// size, so one slot stride serves every level.
+struct BatchWs {
+    int B = 0, N = 0;                  // allocated for B slots, finest N
+    int64_t slot_words = 0, slot_nodes = 0, cap = 0, npix = 0;
+    uint32_t* cand = nullptr;
+    uint32_t* tent = nullptr;
+    uint32_t* bin[2] = {nullptr, nullptr};
+    uint32_t* eval = nullptr;
+    uint32_t* conf = nullptr;
+    float* values = nullptr;
+    int* list = nullptr;               // [cap] keys frame * slot_nodes + node
+    int* recheck = nullptr;            // [cap]
+    int* squeue = nullptr;             // [cap]
+    int* col_top = nullptr;            // [B][(N+1)^2]
+    float* hit_xyz = nullptr;          // [B npix][3]
+    int* hit_pix = nullptr;            // [B npix]
+    Map* d_maps0 = nullptr;            // [kMaxBatch] device
+    Map* d_maps1 = nullptr;
+    Calib* d_calibs = nullptr;
+    Map* h_maps0 = nullptr;            // pinned staging
+    Map* h_maps1 = nullptr;
+    Calib* h_calibs = nullptr;
+    BatchStats* d_stats = nullptr;
+    BatchStats* h_stats = nullptr;     // pinned
+    bool g_valid = false;
+    BatchKey key{};
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int64_t launches_fixed = 0;
+    int64_t launches_body[8] = {};
+};
+
 struct pifu_ctx {
     int device = 0;
     DevNet net[2];
@@ -270,6 +335,8 @@ struct pifu_ctx {
     GraphStats* h_gstats = nullptr;       // pinned
     int64_t g_launches_fixed = 0;         // kernel launches outside the loops
     int64_t g_launches_body[8] = {};      // kernel launches per loop iteration
+    // lockstep frame batches (pifu_frames)
+    BatchWs batch;
 };
 
 namespace {
@@ -495,10 +562,10 @@ int encode_all_act_maps(pifu_ctx* ctx);
 // of them; the graph form reserves kChunkTC rows before it captures.
 int ensure_tc_rows(pifu_ctx* ctx, int64_t rows) {
     if (rows <= ctx->tc_rows) return PIFU_OK;
-    if (rows > kChunkTC) return PIFU_ERR_ARG;
+    if (rows > kTcRowsMax) return PIFU_ERR_ARG;
     int64_t cap = 65536;
     while (cap < rows) cap *= 2;
-    cap = std::min<int64_t>(cap, kChunkTC);
+    cap = std::min<int64_t>(cap, kTcRowsMax);
     int64_t need_x = 0, need_h = 0;
     for (const DevNet& n : ctx->net) {
         need_x = std::max<int64_t>(need_x, n.ldx);
@@ -765,17 +832,21 @@ int run_mlp_tc(pifu_ctx* ctx, const DevNet& net, const PointSrc& src_in, int64_t
     if (!net.tc_ok) return PIFU_ERR_UNSUPPORTED;
     if (f8 && !net.f8_ok) return PIFU_ERR_STATE;
     const int F = f8 ? (int)net.f8.size() : 0;   // leading E4M3 layers
+    // a device-resident count is a total: such a batch is one pass (the
+    // graph forms reserve its rows before capture); host-sized batches go in
+    // chunks of kChunkTC
+    const int64_t chunk = m_dev ? std::max<int64_t>(m, 1) : kChunkTC;
     {
-        const int st = ensure_tc_rows(ctx, m_dev ? kChunkTC : std::min<int64_t>(m, kChunkTC));
+        const int st = ensure_tc_rows(ctx, std::min<int64_t>(m, chunk));
         if (st != PIFU_OK) return st;
     }
-    if (m_dev && m > kChunkTC) return PIFU_ERR_ARG;
+    if (m_dev && m > kTcRowsMax) return PIFU_ERR_ARG;
     PointSrc src = src_in;
     src.count = m_dev;
     const int L = (int)net.layers.size();
     Profiler& pr = ctx->prof;
-    for (int64_t p0 = 0; p0 < m; p0 += kChunkTC) {
-        const int64_t mc = std::min<int64_t>(kChunkTC, m - p0);
+    for (int64_t p0 = 0; p0 < m; p0 += chunk) {
+        const int64_t mc = std::min<int64_t>(chunk, m - p0);
         cudaEvent_t ev = pr.begin(s);
         if (F > 0)
             CK(launch_gather_dual(src, p0, mc, calib, map0, map1, ctx->Xb, net.ldx, ctx->X8,
@@ -1270,9 +1341,13 @@ int g_eval(pifu_ctx* ctx, const DevNet& net, const PointSrc& src, int64_t cap,
         int st = run_mlp_tc(ctx, ctx->snet, src, cap, map, Map{}, cal, es, s, m_dev);
         if (st != PIFU_OK) return st;
         // a queue longer than one device-sized batch latches a capacity error
-        const int64_t qcap = std::min<int64_t>(cap, kChunkTC);
+        const int64_t qcap = std::min<int64_t>(cap, kTcRowsMax);
         CK(launch_accumulate(fallback, ctx->d_squeue, (unsigned)qcap, ctx->d_count + 1, s));
-        PointSrc sf{PTS_LIST, nullptr, ctx->squeue, 0, src.N, nullptr};
+        PointSrc sf = src;   // keeps the frames' maps of a lockstep batch
+        sf.mode = PTS_LIST;
+        sf.list = ctx->squeue;
+        sf.base = 0;
+        sf.count = nullptr;
         Epilogue ef = epi;
         ef.list = ctx->squeue;
         return g_eval(ctx, net, sf, qcap, ctx->d_squeue, map, cal, ef, prec, margin, rechecked, s);
@@ -1288,7 +1363,11 @@ int g_eval(pifu_ctx* ctx, const DevNet& net, const PointSrc& src, int64_t cap,
     int st = run_mlp_tc(ctx, net, src, cap, map, Map{}, cal, e1, s, m_dev,
                         prec == PIFU_PREC_FP8_MIXED);
     if (st != PIFU_OK) return st;
-    PointSrc s2{PTS_LIST, nullptr, ctx->recheck, 0, src.N, nullptr};
+    PointSrc s2 = src;   // keeps the frames' maps of a lockstep batch
+    s2.mode = PTS_LIST;
+    s2.list = ctx->recheck;
+    s2.base = 0;
+    s2.count = nullptr;
     Epilogue e2 = epi;
     e2.list = ctx->recheck;
     // the fused kernel takes any queue length (at most the batch's); the
@@ -1495,6 +1574,407 @@ int g_build(pifu_ctx* ctx, const FrameKey& k, const Map& occ, const Map& col, co
     return PIFU_OK;
 }
 
+// ---- lockstep batch of frames (pifu_frames) -----------------------------------
+//
+// B independent frames advance through the levels together: a level's set-up,
+// dilation and compaction run over all B frames' bitsets (grid.y = frame), and
+// every evaluation batch is one device-sized list of keys frame * slot_nodes +
+// node for all frames -- the work queue that one persistent tensor-core
+// launch per layer drains.  The conflict loop of a level runs while any frame
+// has a frontier.  Map pointers and calibrations are device arrays, written
+// before each launch, so a captured graph serves every batch of the same
+// shape.
+
+void batch_free(pifu_ctx* ctx) {
+    BatchWs& b = ctx->batch;
+    if (b.exec) cudaGraphExecDestroy(b.exec);
+    if (b.graph) cudaGraphDestroy(b.graph);
+    b.exec = nullptr;
+    b.graph = nullptr;
+    b.g_valid = false;
+    uint32_t** bits[] = {&b.cand, &b.tent, &b.bin[0], &b.bin[1], &b.eval, &b.conf};
+    for (auto p : bits) dev_free(*p);
+    dev_free(b.values);
+    dev_free(b.list);
+    dev_free(b.recheck);
+    dev_free(b.squeue);
+    dev_free(b.col_top);
+    dev_free(b.hit_xyz);
+    dev_free(b.hit_pix);
+    b.B = b.N = 0;
+    b.slot_words = b.slot_nodes = b.cap = b.npix = 0;
+}
+
+// Capacity of one device-sized batch for B frames: B x 2^18 keys rounded up
+// to a power of two, between 2^20 and kTcRowsMax.
+int64_t batch_cap(int B) {
+    int64_t c = 1 << 20;
+    while (c < (int64_t)B * (1 << 18) && c < kTcRowsMax) c *= 2;
+    return c;
+}
+
+int batch_ensure(pifu_ctx* ctx, int B, int N, int64_t npix) {
+    BatchWs& b = ctx->batch;
+    if (!b.d_maps0) {
+        CK(dev_alloc(&b.d_maps0, kMaxBatch));
+        CK(dev_alloc(&b.d_maps1, kMaxBatch));
+        CK(dev_alloc(&b.d_calibs, kMaxBatch));
+        CK(cudaHostAlloc(&b.h_maps0, sizeof(Map) * kMaxBatch, cudaHostAllocDefault));
+        CK(cudaHostAlloc(&b.h_maps1, sizeof(Map) * kMaxBatch, cudaHostAllocDefault));
+        CK(cudaHostAlloc(&b.h_calibs, sizeof(Calib) * kMaxBatch, cudaHostAllocDefault));
+        CK(dev_alloc(&b.d_stats, 1));
+        CK(cudaHostAlloc(&b.h_stats, sizeof(BatchStats), cudaHostAllocDefault));
+    }
+    if (b.B >= B && b.N == N && b.npix >= npix) return PIFU_OK;
+    const int Bn = std::max(B, b.B);
+    const int64_t np = std::max(npix, b.npix);
+    Map* keep[3] = {b.d_maps0, b.d_maps1, nullptr};
+    (void)keep;
+    batch_free(ctx);
+    const int64_t words = words_of(N);
+    const int64_t nodes = (int64_t)(N + 1) * (N + 1) * (N + 1);
+    if ((int64_t)Bn * nodes > 2147483647LL) return PIFU_ERR_ARG;   // int32 keys
+    uint32_t** bits[] = {&b.cand, &b.tent, &b.bin[0], &b.bin[1], &b.eval, &b.conf};
+    for (auto p : bits) {
+        CK(dev_alloc(p, words * Bn));
+        CK(cudaMemset(*p, 0, (size_t)(words * Bn) * 4));
+    }
+    const int64_t cap = batch_cap(Bn);
+    CK(dev_alloc(&b.values, nodes * Bn));
+    CK(dev_alloc(&b.list, cap));
+    CK(dev_alloc(&b.recheck, cap));
+    CK(dev_alloc(&b.squeue, cap));
+    CK(dev_alloc(&b.col_top, (int64_t)(N + 1) * (N + 1) * Bn));
+    CK(dev_alloc(&b.hit_xyz, 3 * np * Bn));
+    CK(dev_alloc(&b.hit_pix, np * Bn));
+    b.B = Bn;
+    b.N = N;
+    b.npix = np;
+    b.slot_words = words;
+    b.slot_nodes = nodes;
+    b.cap = cap;
+    return PIFU_OK;
+}
+
+// The batch's frame pipeline, captured on ctx->cap_stream (loop bodies on
+// cap_stream2).  g_eval's queues are pointed at the batch's for the capture.
+int g_enqueue_batch(pifu_ctx* ctx, const BatchKey& k) {
+    BatchWs& bw = ctx->batch;
+    cudaStream_t s = ctx->cap_stream;
+    cudaStream_t sb = ctx->cap_stream2;
+    BatchStats* gs = bw.d_stats;
+    unsigned int* err = ctx->d_count + 1;
+    const DevNet& net = ctx->net[0];
+    const int B = k.B;
+    const int64_t cap = bw.cap;
+    const int64_t fs = bw.slot_words, sn = bw.slot_nodes;
+    int st = PIFU_OK;
+    CK(cudaMemsetAsync(gs, 0, sizeof(BatchStats), s));
+    CK(cudaMemsetAsync(err, 0, sizeof(unsigned int), s));
+    int N = k.n0, cur = 0;
+    CK(launch_dense_setup(N, bw.cand, bw.tent, bw.bin[cur], bw.eval, bw.conf, s, B, fs));
+    const bool sur = k.use_surrogate != 0;
+    {
+        const int64_t nodes0 = (int64_t)(N + 1) * (N + 1) * (N + 1);
+        PointSrc src{PTS_DENSE, nullptr, nullptr, 0, N, nullptr};
+        src.maps0 = bw.d_maps0;
+        src.calibs = bw.d_calibs;
+        src.slot_div = nodes0;
+        Epilogue epi{};
+        epi.mode = EPI_LEVEL;
+        epi.lv = LevelBits{bw.values, bw.tent, bw.bin[cur], bw.conf, N, row_words_of(N), 1,
+                           nodes0, sn, fs};
+        if (B * nodes0 > cap) return PIFU_ERR_CAPACITY;
+        st = g_eval(ctx, net, src, B * nodes0, nullptr, Map{}, Calib{}, epi, k.precision, k.margin,
+                    &gs->rechecked[0], s, sur && k.num_levels > 1, k.sur_margin,
+                    &gs->fallback[0]);
+        if (st != PIFU_OK) return st;
+    }
+    for (int l = 1; l < k.num_levels; ++l) {
+        const int prev = cur;
+        cur ^= 1;
+        N *= 2;
+        CK(launch_classify(bw.bin[prev], N, bw.cand, bw.tent, bw.bin[cur], bw.eval, bw.conf, s, B,
+                           fs, fs));
+        CK(launch_popcount(bw.cand, words_of(N), &gs->cands[l][0], s, B, fs));
+        CK(cudaMemsetAsync(ctx->d_count, 0, sizeof(unsigned int), s));
+        CK(launch_dilate_select(bw.cand, bw.eval, nullptr, N, bw.list, ctx->d_count, s, B, fs, sn));
+        cudaStreamCaptureStatus cs;
+        cudaGraph_t cg = nullptr;
+        CK(cudaStreamGetCaptureInfo(s, &cs, nullptr, &cg, nullptr, nullptr, nullptr));
+        cudaGraphConditionalHandle h;
+        CK(cudaGraphConditionalHandleCreate(&h, cg, 0, 0));
+        CK(launch_loop_control(h, ctx->d_count, (unsigned)cap, &gs->rounds[l], 0, k.max_rounds,
+                               err, s));
+        cudaGraph_t body = nullptr;
+        st = g_add_while(ctx, s, h, &body);
+        if (st != PIFU_OK) return st;
+        const int64_t before = launches_now(ctx);
+        CK(cudaStreamBeginCaptureToGraph(sb, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+        {
+            const int rw = row_words_of(N);
+            PointSrc src{PTS_LIST, nullptr, bw.list, 0, N, nullptr};
+            src.maps0 = bw.d_maps0;
+            src.calibs = bw.d_calibs;
+            src.slot_div = sn;
+            Epilogue epi{};
+            epi.mode = EPI_LEVEL;
+            epi.list = bw.list;
+            epi.lv = LevelBits{bw.values, bw.tent, bw.bin[cur], bw.conf, N, rw, 0, sn, sn, fs};
+            st = launch_accumulate(&gs->keys[l], ctx->d_count, (unsigned)cap, err, sb) == cudaSuccess
+                     ? PIFU_OK : PIFU_ERR_CUDA;
+            if (st == PIFU_OK)
+                st = g_eval(ctx, net, src, cap, ctx->d_count, Map{}, Calib{}, epi, k.precision,
+                            k.margin, &gs->rechecked[l], sb, sur && l < k.num_levels - 1,
+                            k.sur_margin, &gs->fallback[l]);
+            if (st == PIFU_OK && cudaMemsetAsync(ctx->d_count, 0, sizeof(unsigned int), sb) != cudaSuccess)
+                st = PIFU_ERR_CUDA;
+            if (st == PIFU_OK && launch_dilate_select(bw.conf, bw.eval, nullptr, N, bw.list,
+                                                      ctx->d_count, sb, B, fs, sn) != cudaSuccess)
+                st = PIFU_ERR_CUDA;
+            if (st == PIFU_OK &&
+                cudaMemsetAsync(bw.conf, 0, (size_t)(fs * B) * 4, sb) != cudaSuccess)
+                st = PIFU_ERR_CUDA;
+            if (st == PIFU_OK && launch_loop_control(h, ctx->d_count, (unsigned)cap,
+                                                     &gs->rounds[l], 1, k.max_rounds, err,
+                                                     sb) != cudaSuccess)
+                st = PIFU_ERR_CUDA;
+        }
+        cudaGraph_t body_out = nullptr;
+        const cudaError_t ee = cudaStreamEndCapture(sb, &body_out);
+        if (st != PIFU_OK) return st;
+        if (ee != cudaSuccess) return fail_cuda(ctx, ee);
+        bw.launches_body[l] = launches_now(ctx) - before;
+        CK(launch_popcount(bw.eval, words_of(N), &gs->evals[l][0], s, B, fs));
+    }
+    // render all frames, then the colour MLP over all their hits
+    const int64_t npix = (int64_t)k.width * k.height;
+    RenderArgs a{};
+    a.width = k.width;
+    a.height = k.height;
+    a.N = N;
+    a.row_words = row_words_of(N);
+    a.values = bw.values;
+    a.eval = bw.eval;
+    a.bin = bw.bin[cur];
+    for (int c = 0; c < 3; ++c) a.bg[c] = k.bg[c];
+    a.depth = k.depth;
+    a.rgb = k.rgb;
+    a.mask = k.mask;
+    a.hit_xyz = bw.hit_xyz;
+    a.hit_pix = bw.hit_pix;
+    a.hit_count = ctx->d_count;
+    a.top = bw.col_top;
+    a.slots = B;
+    a.slot_nodes = sn;
+    a.slot_words = fs;
+    CK(cudaMemsetAsync(ctx->d_count, 0, sizeof(unsigned int), s));
+    CK(launch_render_rays(a, s));
+    ctx->prof.k[PIFU_K_RENDER].launches += 2;
+    if (k.rgb) {
+        PointSrc src{PTS_XYZ, bw.hit_xyz, nullptr, 0, 0, nullptr};
+        const bool col = k.cC > 0;
+        src.maps0 = col ? bw.d_maps1 : bw.d_maps0;   // colour maps first (Eq. 2)
+        src.maps1 = col ? bw.d_maps0 : nullptr;
+        src.calibs = bw.d_calibs;
+        src.keys = bw.hit_pix;
+        src.slot_div = npix;
+        Epilogue epi{};
+        epi.mode = EPI_PIXELS;
+        epi.act = ACT_TANH01;
+        epi.out = k.rgb;
+        epi.pix = bw.hit_pix;
+        if (B * npix > kTcRowsMax) return PIFU_ERR_CAPACITY;
+        st = run_mlp_tc(ctx, ctx->net[1], src, B * npix, Map{}, Map{}, Calib{}, epi, s,
+                        ctx->d_count);
+        if (st != PIFU_OK) return st;
+    }
+    CK(cudaMemcpyAsync(&gs->err, err, sizeof(unsigned int), cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(bw.h_stats, gs, sizeof(BatchStats), cudaMemcpyDeviceToHost, s));
+    return PIFU_OK;
+}
+
+int b_build(pifu_ctx* ctx, const BatchKey& k) {
+    BatchWs& bw = ctx->batch;
+    if (bw.exec) cudaGraphExecDestroy(bw.exec);
+    if (bw.graph) cudaGraphDestroy(bw.graph);
+    bw.exec = nullptr;
+    bw.graph = nullptr;
+    bw.g_valid = false;
+    if (!ctx->cap_stream) CK(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
+    if (!ctx->cap_stream2) CK(cudaStreamCreateWithFlags(&ctx->cap_stream2, cudaStreamNonBlocking));
+    CK(tc_prepare());
+    {
+        const int st = ensure_tc_rows(ctx, std::max<int64_t>(bw.cap, (int64_t)k.B * k.width * k.height));
+        if (st != PIFU_OK) return st;
+    }
+    // g_eval's queues are the context's; point them at the batch's for the capture
+    int* keep_recheck = ctx->recheck;
+    int* keep_squeue = ctx->squeue;
+    ctx->recheck = bw.recheck;
+    ctx->squeue = bw.squeue;
+    const bool prof_on = ctx->prof.on;
+    ctx->prof.on = false;
+    const int64_t before = launches_now(ctx);
+    int st = PIFU_OK;
+    cudaGraph_t g = nullptr;
+    cudaError_t ee = cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal);
+    if (ee == cudaSuccess) {
+        st = g_enqueue_batch(ctx, k);
+        ee = cudaStreamEndCapture(ctx->cap_stream, &g);
+    }
+    ctx->recheck = keep_recheck;
+    ctx->squeue = keep_squeue;
+    ctx->prof.on = prof_on;
+    int64_t body = 0;
+    for (int l = 1; l < k.num_levels; ++l) body += bw.launches_body[l];
+    bw.launches_fixed = launches_now(ctx) - before - body;
+    for (auto& x : ctx->prof.k) x.launches = 0;   // capture is not execution
+    if (st != PIFU_OK) {
+        if (g) cudaGraphDestroy(g);
+        return st;
+    }
+    if (ee != cudaSuccess) return fail_cuda(ctx, ee);
+    bw.graph = g;
+    const cudaError_t ie = cudaGraphInstantiate(&bw.exec, g, 0);
+    if (ie != cudaSuccess) {
+        cudaGraphDestroy(g);
+        bw.graph = nullptr;
+        return fail_cuda(ctx, ie);
+    }
+    bw.key = k;
+    bw.g_valid = true;
+    return PIFU_OK;
+}
+
+// ---- tile autotuner --------------------------------------------------------------
+//
+// Picks, per tensor-core hidden layer, the output tile width BN (64, 128 or
+// 256 columns of the 128-row tile) that runs fastest on a batch of `rows`
+// points, by timing each candidate with CUDA events.  The last hidden layer
+// keeps BN = its width when the last layer is fused into its epilogue.  The
+// chosen tile changes the weight tensor map's box, so captured graphs are
+// invalidated.
+
+int tune_layer(pifu_ctx* ctx, const TcLayerArgs& base, int n_out, bool fp8, CUtensorMap* tmW,
+               void* Wdev, int Kw, int* BN, cudaStream_t s, double* best_ms) {
+    const int cands[3] = {64, 128, 256};
+    int best = *BN;
+    double best_t = 1e30;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    int st = PIFU_OK;
+    for (int c : cands) {
+        if (n_out % c != 0 || st != PIFU_OK) continue;
+        const bool ok = fp8 ? tc_encode_2d_u8(tmW, Wdev, (uint64_t)Kw, (uint64_t)n_out, (uint64_t)Kw,
+                                              128, (uint32_t)c)
+                            : tc_encode_2d_bf16(tmW, Wdev, (uint64_t)Kw, (uint64_t)n_out,
+                                                (uint64_t)Kw * 2, 64, (uint32_t)c);
+        if (!ok) {
+            st = PIFU_ERR_CUDA;
+            break;
+        }
+        TcLayerArgs a = base;
+        a.BN = c;
+        a.tmW = tmW;
+        float ms = 0.f;
+        cudaError_t e = launch_tc_linear(a, s);   // warm-up
+        if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+        for (int r = 0; r < 3 && e == cudaSuccess; ++r) e = launch_tc_linear(a, s);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e != cudaSuccess) {
+            st = fail_cuda(ctx, e);
+            break;
+        }
+        if (ms < best_t) {
+            best_t = ms;
+            best = c;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != PIFU_OK) return st;
+    *best_ms = best_t / 3.0;
+    *BN = best;
+    const bool ok = fp8 ? tc_encode_2d_u8(tmW, Wdev, (uint64_t)Kw, (uint64_t)n_out, (uint64_t)Kw, 128,
+                                          (uint32_t)best)
+                        : tc_encode_2d_bf16(tmW, Wdev, (uint64_t)Kw, (uint64_t)n_out,
+                                            (uint64_t)Kw * 2, 64, (uint32_t)best);
+    return ok ? PIFU_OK : PIFU_ERR_CUDA;
+}
+
+int autotune(pifu_ctx* ctx, int64_t rows, cudaStream_t s, int32_t* bn_out, double* ms_out,
+             int n_max, int* n_done) {
+    int st = ensure_tc_rows(ctx, rows);
+    if (st != PIFU_OK) return st;
+    CK(tc_prepare());
+    int n = 0;
+    auto record = [&](int bn, double ms) {
+        if (n < n_max) {
+            if (bn_out) bn_out[n] = bn;
+            if (ms_out) ms_out[n] = ms;
+        }
+        ++n;
+    };
+    for (int which = 0; which < 2; ++which) {
+        DevNet& net = ctx->net[which];
+        if (!net.tc_ok) continue;
+        const int L = (int)net.layers.size();
+        for (int l = 0; l + 1 < L; ++l) {
+            const DevLayer& Ly = net.layers[(size_t)l];
+            const bool fused_last = l == L - 2 && net.layers[(size_t)L - 1].K2 == 0 &&
+                                    net.layers[(size_t)L - 1].n_out <= 4;
+            TcLayerArgs a{};
+            a.M = (int)rows;
+            a.N = Ly.n_out;
+            a.bias = Ly.b;
+            a.slope = net.slope;
+            a.out = ctx->Hb[l % 2];
+            a.ldo = Ly.n_out;
+            a.err = ctx->d_count + 1;
+            a.mode = TC_BF16;
+            const bool f8 = net.f8_ok && l < (int)net.f8.size();
+            if (f8) {
+                Fp8Layer& Q = net.f8[(size_t)l];
+                a.tmA1 = l > 0 ? &Q.tmA1 : &net.tmX8;
+                a.tmA2 = &net.tmX8;
+                a.nk1 = Q.nk1;
+                a.nk2 = Q.nk2;
+                a.mode = l + 1 < (int)net.f8.size() ? TC_E4M3_E4M3 : TC_E4M3_BF16;
+                a.colscale = Q.colscale;
+                a.out_scale = Q.out_scale;
+                double ms = 0.0;
+                st = tune_layer(ctx, a, Ly.n_out, true, &Q.tmW, Q.W, Q.Kw, &Q.BN, s, &ms);
+                if (st != PIFU_OK) return st;
+                record(Q.BN, ms);
+            }
+            TcLayer& T = net.tc[(size_t)l];
+            if (fused_last) {
+                record(T.BN, 0.0);   // kept: the fused last layer needs BN = n_out
+                continue;
+            }
+            a.tmA1 = l > 0 ? &T.tmA1 : &net.tmX;
+            a.tmA2 = &net.tmX;
+            a.nk1 = T.nk1;
+            a.nk2 = T.nk2;
+            a.mode = TC_BF16;
+            a.colscale = nullptr;
+            a.out_scale = 1.f;
+            double ms = 0.0;
+            st = tune_layer(ctx, a, Ly.n_out, false, &T.tmW, T.W, T.Kw, &T.BN, s, &ms);
+            if (st != PIFU_OK) return st;
+            record(T.BN, ms);
+        }
+    }
+    ctx->g_valid = false;
+    ctx->batch.g_valid = false;
+    if (n_done) *n_done = n;
+    return PIFU_OK;
+}
+
 }  // namespace
 
 // ============================================================================
@@ -1575,6 +2055,18 @@ int pifu_create(const void* weight_blob, size_t bytes, pifu_ctx** out) {
 void pifu_destroy(pifu_ctx* ctx) {
     if (!ctx) return;
     DeviceGuard g(ctx->device);
+    batch_free(ctx);
+    {
+        BatchWs& bw = ctx->batch;
+        dev_free(bw.d_maps0);
+        dev_free(bw.d_maps1);
+        dev_free(bw.d_calibs);
+        dev_free(bw.d_stats);
+        if (bw.h_maps0) cudaFreeHost(bw.h_maps0);
+        if (bw.h_maps1) cudaFreeHost(bw.h_maps1);
+        if (bw.h_calibs) cudaFreeHost(bw.h_calibs);
+        if (bw.h_stats) cudaFreeHost(bw.h_stats);
+    }
     free_net(ctx->net[0]);
     free_net(ctx->net[1]);
     dev_free(ctx->X);
@@ -1625,7 +2117,6 @@ int pifu_query_ex(pifu_ctx* ctx, const pifu_fmap* occ_map, const float calib[12]
     if (prec_mixed(precision) && !(margin >= 0.f && margin <= 0.5f)) return PIFU_ERR_ARG;
     if (m == 0) return PIFU_OK;
     if (!pts_dev || !occ_dev || !map_ok(occ_map)) return PIFU_ERR_ARG;
-    if (occ_map->dtype != PIFU_F32) return PIFU_ERR_UNSUPPORTED;
     if (ctx->net[0].d_in != occ_map->C + 1) return PIFU_ERR_ARG;
     DeviceGuard g(ctx->device);
     if (!g.ok) return PIFU_ERR_CUDA;
@@ -1661,7 +2152,6 @@ int pifu_query_colour(pifu_ctx* ctx, const pifu_fmap* occ_map, const pifu_fmap* 
     if (!ctx || !calib || m < 0) return PIFU_ERR_ARG;
     if (m == 0) return PIFU_OK;
     if (!pts_dev || !rgb_dev || !map_ok(occ_map) || (col_map && !map_ok(col_map))) return PIFU_ERR_ARG;
-    if (occ_map->dtype != PIFU_F32 || (col_map && col_map->dtype != PIFU_F32)) return PIFU_ERR_UNSUPPORTED;
     const int c_t = col_map ? col_map->C : 0;
     if (ctx->net[1].d_in != c_t + occ_map->C + 1) return PIFU_ERR_ARG;
     DeviceGuard g(ctx->device);
@@ -1693,7 +2183,6 @@ int pifu_localize(pifu_ctx* ctx, const pifu_fmap* occ_map, const float calib[12]
     const bool use_sur = lv->use_surrogate != 0;
     if (use_sur && (!ctx->sur.ready || !(lv->surrogate_margin >= 0.f && lv->surrogate_margin <= 0.5f)))
         return use_sur && !ctx->sur.ready ? PIFU_ERR_STATE : PIFU_ERR_ARG;
-    if (occ_map->dtype != PIFU_F32) return PIFU_ERR_UNSUPPORTED;
     if (ctx->net[0].d_in != occ_map->C + 1) return PIFU_ERR_ARG;
     const int max_rounds = lv->max_rounds > 0 ? lv->max_rounds : 4096;
     DeviceGuard g(ctx->device);
@@ -1821,8 +2310,6 @@ int pifu_render(pifu_ctx* ctx, const pifu_camera* cam, const pifu_fmap* occ_map,
     if (rgb_dev && cam->precision == PIFU_PREC_BF16 && !ctx->net[1].tc_ok) return PIFU_ERR_UNSUPPORTED;
     if (rgb_dev) {
         if (!map_ok(occ_map) || (col_map && !map_ok(col_map))) return PIFU_ERR_ARG;
-        if (occ_map->dtype != PIFU_F32 || (col_map && col_map->dtype != PIFU_F32))
-            return PIFU_ERR_UNSUPPORTED;
         const int c_t = col_map ? col_map->C : 0;
         if (ctx->net[1].d_in != c_t + occ_map->C + 1) return PIFU_ERR_ARG;
     }
@@ -1895,7 +2382,6 @@ int pifu_frame(pifu_ctx* ctx, const pifu_fmap* occ_map, const pifu_fmap* col_map
         if (!ctx->sur.ready || !ctx->snet.tc_ok) return PIFU_ERR_STATE;
         if (!(lv->surrogate_margin >= 0.f && lv->surrogate_margin <= 0.5f)) return PIFU_ERR_ARG;
     }
-    if (occ_map->dtype != PIFU_F32 || (col_map && col_map->dtype != PIFU_F32)) return PIFU_ERR_UNSUPPORTED;
     if (ctx->net[0].d_in != occ_map->C + 1) return PIFU_ERR_ARG;
     if (!ctx->net[0].tc_ok) return PIFU_ERR_UNSUPPORTED;
     if (rgb_dev) {
@@ -1984,13 +2470,143 @@ int pifu_frame(pifu_ctx* ctx, const pifu_fmap* occ_map, const pifu_fmap* col_map
 int pifu_calibrate_fp8(pifu_ctx* ctx, const pifu_fmap* occ_map, const float calib[12], int n0,
                        void* stream) {
     if (!ctx || !calib || !map_ok(occ_map) || n0 < 1 || n0 > 256) return PIFU_ERR_ARG;
-    if (occ_map->dtype != PIFU_F32) return PIFU_ERR_UNSUPPORTED;
     if (ctx->net[0].d_in != occ_map->C + 1) return PIFU_ERR_ARG;
     DeviceGuard g(ctx->device);
     if (!g.ok) return PIFU_ERR_CUDA;
     ctx->g_valid = false;   // a captured frame holds the previous scales
     return calibrate_fp8(ctx, to_map(occ_map), to_calib(calib), n0,
                          static_cast<cudaStream_t>(stream));
+}
+
+int pifu_frames(pifu_ctx* ctx, int B, const pifu_fmap* occ_maps, const pifu_fmap* col_maps,
+                const float* calibs, const pifu_levels* lv, const pifu_camera* cam, void* stream,
+                float* depth_dev, float* rgb_dev, uint8_t* mask_dev, pifu_volume* out) {
+    if (!ctx || B < 1 || B > kMaxBatch || !occ_maps || !calibs || !lv || !cam)
+        return PIFU_ERR_ARG;
+    const pifu_fmap& o0 = occ_maps[0];
+    for (int f = 0; f < B; ++f) {
+        const pifu_fmap& o = occ_maps[f];
+        if (!map_ok(&o) || o.H != o0.H || o.W != o0.W || o.C != o0.C || o.dtype != o0.dtype)
+            return PIFU_ERR_ARG;
+        if (col_maps) {
+            const pifu_fmap& c = col_maps[f];
+            if (!map_ok(&c) || c.H != col_maps[0].H || c.W != col_maps[0].W ||
+                c.C != col_maps[0].C || c.dtype != col_maps[0].dtype)
+                return PIFU_ERR_ARG;
+        }
+    }
+    if (!is_pow2(lv->n0) || lv->n0 < 2 || lv->num_levels < 1 || lv->num_levels > kMaxLevels)
+        return PIFU_ERR_ARG;
+    const int64_t n_fine = (int64_t)lv->n0 << (lv->num_levels - 1);
+    if (n_fine > kMaxFine) return PIFU_ERR_ARG;
+    if (cam->width < 1 || cam->height < 1) return PIFU_ERR_ARG;
+    const int64_t npix = (int64_t)cam->width * cam->height;
+    if ((int64_t)B * npix > kTcRowsMax) return PIFU_ERR_CAPACITY;
+    if (!prec_valid(lv->precision) || lv->precision == PIFU_PREC_FP32) return PIFU_ERR_UNSUPPORTED;
+    if (prec_f8(lv->precision) && !ctx->net[0].f8_ok) return PIFU_ERR_STATE;
+    if (prec_mixed(lv->precision) && !(lv->margin >= 0.f && lv->margin <= 0.5f))
+        return PIFU_ERR_ARG;
+    if (lv->use_surrogate) {
+        if (!ctx->sur.ready || !ctx->snet.tc_ok) return PIFU_ERR_STATE;
+        if (!(lv->surrogate_margin >= 0.f && lv->surrogate_margin <= 0.5f)) return PIFU_ERR_ARG;
+    }
+    if (ctx->net[0].d_in != o0.C + 1) return PIFU_ERR_ARG;
+    if (!ctx->net[0].tc_ok) return PIFU_ERR_UNSUPPORTED;
+    if (rgb_dev) {
+        const int c_t = col_maps ? col_maps[0].C : 0;
+        if (ctx->net[1].d_in != c_t + o0.C + 1) return PIFU_ERR_ARG;
+        if (!ctx->net[1].tc_ok) return PIFU_ERR_UNSUPPORTED;
+    }
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return PIFU_ERR_CUDA;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int st = batch_ensure(ctx, B, (int)n_fine, npix);
+    if (st != PIFU_OK) return st;
+    BatchWs& bw = ctx->batch;
+    BatchKey k;
+    std::memset(&k, 0, sizeof(k));   // padding too: keys are compared bytewise
+    k.B = B;
+    k.oH = o0.H;
+    k.oW = o0.W;
+    k.oC = o0.C;
+    k.odt = o0.dtype;
+    if (col_maps) {
+        k.cH = col_maps[0].H;
+        k.cW = col_maps[0].W;
+        k.cC = col_maps[0].C;
+        k.cdt = col_maps[0].dtype;
+    }
+    k.n0 = lv->n0;
+    k.num_levels = lv->num_levels;
+    k.precision = lv->precision;
+    k.max_rounds = lv->max_rounds > 0 ? lv->max_rounds : 4096;
+    k.margin = prec_mixed(lv->precision) ? lv->margin : 0.f;
+    if (lv->use_surrogate) {
+        k.use_surrogate = 1;
+        k.sur_margin = lv->surrogate_margin;
+        k.sur_version = ctx->sur.version;
+    }
+    k.f8_version = prec_f8(lv->precision) ? ctx->net[0].f8_version : 0;
+    k.width = cam->width;
+    k.height = cam->height;
+    for (int c = 0; c < 3; ++c) k.bg[c] = cam->background[c];
+    k.depth = depth_dev;
+    k.rgb = rgb_dev;
+    k.mask = mask_dev;
+    if (!bw.g_valid || std::memcmp(&k, &bw.key, sizeof(k)) != 0) {
+        st = b_build(ctx, k);
+        if (st != PIFU_OK) return st;
+    }
+    // this batch's maps and calibrations, read by the graph's kernels
+    for (int f = 0; f < B; ++f) {
+        bw.h_maps0[f] = to_map(&occ_maps[f]);
+        bw.h_maps1[f] = col_maps ? to_map(&col_maps[f]) : Map{};
+        bw.h_calibs[f] = to_calib(calibs + 12 * f);
+    }
+    CK(cudaMemcpyAsync(bw.d_maps0, bw.h_maps0, sizeof(Map) * B, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(bw.d_maps1, bw.h_maps1, sizeof(Map) * B, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(bw.d_calibs, bw.h_calibs, sizeof(Calib) * B, cudaMemcpyHostToDevice, s));
+    ctx->have_volume = false;
+    CK(cudaGraphLaunch(bw.exec, s));
+    CK(cudaStreamSynchronize(s));
+    const BatchStats& gs = *bw.h_stats;
+    const int64_t nodes0 = (int64_t)(lv->n0 + 1) * (lv->n0 + 1) * (lv->n0 + 1);
+    int64_t launches = bw.launches_fixed;
+    for (int l = 1; l < lv->num_levels; ++l) launches += bw.launches_body[l] * (int64_t)(gs.rounds[l] + 1);
+    ctx->prof.k[PIFU_K_MLP_HIDDEN].launches += launches;   // graph: counted in one class
+    const int cur = (lv->num_levels - 1) & 1;
+    for (int f = 0; f < B && out; ++f) {
+        pifu_volume vs{};
+        vs.num_levels = lv->num_levels;
+        vs.n = (int32_t)n_fine;
+        vs.row_words = row_words_of((int)n_fine);
+        vs.occ_bits_dev = bw.bin[cur] + f * bw.slot_words;
+        vs.eval_bits_dev = bw.eval + f * bw.slot_words;
+        vs.values_dev = bw.values + f * bw.slot_nodes;
+        vs.evals_per_level[0] = nodes0;
+        vs.n_eval = nodes0;
+        for (int l = 0; l < lv->num_levels; ++l) {
+            if (l > 0) {
+                vs.evals_per_level[l] = (int64_t)gs.evals[l][f];
+                vs.n_eval += (int64_t)gs.evals[l][f];
+                vs.candidates_per_level[l] = (int64_t)gs.cands[l][f];
+                vs.conflict_rounds[l] = (int32_t)gs.rounds[l];
+            }
+            vs.rechecked_per_level[l] = (int64_t)gs.rechecked[l];
+            vs.fallback_per_level[l] = (int64_t)gs.fallback[l];
+        }
+        out[f] = vs;
+    }
+    if (gs.err) return decode_err(gs.err);
+    return PIFU_OK;
+}
+
+int pifu_autotune(pifu_ctx* ctx, int64_t rows, void* stream, int32_t* bn_out, double* ms_out,
+                  int n_max, int* n_layers) {
+    if (!ctx || rows < 128 || rows > kTcRowsMax || n_max < 0) return PIFU_ERR_ARG;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return PIFU_ERR_CUDA;
+    return autotune(ctx, rows, static_cast<cudaStream_t>(stream), bn_out, ms_out, n_max, n_layers);
 }
 
 int pifu_surrogate_init(pifu_ctx* ctx, int h1, int h2, uint64_t seed) {
@@ -2007,7 +2623,6 @@ int pifu_surrogate_samples(pifu_ctx* ctx, const pifu_fmap* occ_map, const float 
     if (!ctx || !calib || m < 0 || !map_ok(occ_map)) return PIFU_ERR_ARG;
     if (m == 0) return PIFU_OK;
     if (!pts_dev || !x_dev || !o_dev) return PIFU_ERR_ARG;
-    if (occ_map->dtype != PIFU_F32) return PIFU_ERR_UNSUPPORTED;
     if (ctx->net[0].d_in != occ_map->C + 1) return PIFU_ERR_ARG;
     DeviceGuard g(ctx->device);
     if (!g.ok) return PIFU_ERR_CUDA;
@@ -2038,7 +2653,6 @@ int pifu_surrogate_query(pifu_ctx* ctx, const pifu_fmap* occ_map, const float ca
     if (!pts_dev || !occ_dev) return PIFU_ERR_ARG;
     if (precision != PIFU_PREC_FP32 && precision != PIFU_PREC_BF16) return PIFU_ERR_UNSUPPORTED;
     if (precision == PIFU_PREC_BF16 && !ctx->snet.tc_ok) return PIFU_ERR_UNSUPPORTED;
-    if (occ_map->dtype != PIFU_F32) return PIFU_ERR_UNSUPPORTED;
     if (ctx->snet.d_in != occ_map->C + 1) return PIFU_ERR_ARG;
     DeviceGuard g(ctx->device);
     if (!g.ok) return PIFU_ERR_CUDA;

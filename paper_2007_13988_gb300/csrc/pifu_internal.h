@@ -45,6 +45,15 @@ struct PointSrc {
     // Device-resident batch size: when set, a launch sized for m points
     // processes min(*count, m) of them (graph form, no host read of counts).
     const unsigned int* count;
+    // Several frames in one batch (lockstep form), when maps0 is set: a
+    // point's key is list[p] (PTS_LIST), base + p (PTS_DENSE) or keys[p]
+    // (PTS_XYZ); its frame is key / slot_div, whose maps and calibration
+    // replace the launch's, and in the grid modes its node is key % slot_div.
+    const Map* maps0;
+    const Map* maps1;     // may be null
+    const Calib* calibs;
+    const int* keys;      // PTS_XYZ
+    int64_t slot_div;
 };
 
 // What the last MLP layer does with its output.
@@ -64,6 +73,12 @@ struct LevelBits {
     int N;
     int row_words;
     int first_level;        // 1: no tentative values, no conflicts
+    // Several frames (lockstep form): a node key is frame * key_div + node,
+    // and frame f's arrays start f slot_nodes values / f slot_words words
+    // further.
+    int64_t key_div;        // 0: one frame
+    int64_t slot_nodes;
+    int64_t slot_words;
 };
 
 struct Epilogue {
@@ -207,17 +222,23 @@ __host__ __device__ inline int64_t words_of(int N) {
 
 // Level set-up from the binarized coarse level (N/2 cells): tentative bits,
 // candidate bits; clears eval, conf0 and the working bits (= tentative).
+// Several frames: `slots` of them, bitsets cslot (coarse) / fslot (fine)
+// words apart.
 cudaError_t launch_classify(const uint32_t* coarse_bin, int N, uint32_t* cand, uint32_t* tent,
-                            uint32_t* bin, uint32_t* eval, uint32_t* conf0, cudaStream_t stream);
+                            uint32_t* bin, uint32_t* eval, uint32_t* conf0, cudaStream_t stream,
+                            int slots = 1, int64_t cslot = 0, int64_t fslot = 0);
 
 // Level-0 set-up: everything empty except eval = all nodes.
 cudaError_t launch_dense_setup(int N, uint32_t* cand, uint32_t* tent, uint32_t* bin,
-                               uint32_t* eval, uint32_t* conf0, cudaStream_t stream);
+                               uint32_t* eval, uint32_t* conf0, cudaStream_t stream,
+                               int slots = 1, int64_t fslot = 0);
 
 // sel = dilate26(src) & ~eval; eval |= sel; clear[w] = 0 (if non-null);
 // append the node indices of sel to list at *count.
+// Several frames: one list for all, keys frame * slot_nodes + node.
 cudaError_t launch_dilate_select(const uint32_t* src, uint32_t* eval, uint32_t* clear, int N,
-                                 int* list, unsigned int* count, cudaStream_t stream);
+                                 int* list, unsigned int* count, cudaStream_t stream,
+                                 int slots = 1, int64_t fslot = 0, int64_t slot_nodes = 0);
 
 // Graph form: set the conditional handle to (*count > 0) within capacity
 // and round limits (count_round: this decision starts a conflict round).
@@ -229,8 +250,9 @@ cudaError_t launch_accumulate(unsigned long long* dst, const unsigned int* src, 
                               unsigned int* err, cudaStream_t stream);
 
 // Population count of a bitset (for statistics) added into *count.
+// Several frames: count[f] += popcount of frame f's bitset.
 cudaError_t launch_popcount(const uint32_t* bits, int64_t words, unsigned long long* count,
-                            cudaStream_t stream);
+                            cudaStream_t stream, int slots = 1, int64_t fslot = 0);
 
 // --- mlp_fused.cu ----------------------------------------------------------
 // The whole network in FP32 for a small (or device-sized) batch in one
@@ -268,6 +290,11 @@ struct RenderArgs {
     int* hit_pix;         // pixel index per hit
     unsigned int* hit_count;
     int* top;             // [(N+1)^2] scratch: highest non-empty depth node per column
+    // Several frames (lockstep form): frame f's volume starts f slot_nodes
+    // values / f slot_words words further, its outputs f width*height pixels
+    // further, and its hits carry pixel keys f width*height + pixel.
+    int slots;            // 0 or 1: one frame
+    int64_t slot_nodes, slot_words;
 };
 cudaError_t launch_render_rays(const RenderArgs& a, cudaStream_t stream);
 

@@ -25,8 +25,14 @@ namespace {
 __global__ void __launch_bounds__(256) column_top_kernel(int N, int row_words,
                                                          const uint32_t* __restrict__ eval,
                                                          const uint32_t* __restrict__ bin,
-                                                         int* __restrict__ top) {
+                                                         int* __restrict__ top, int64_t slot_words) {
     const int n1 = N + 1;
+    {
+        const int64_t f = blockIdx.y;   // frame of a lockstep batch
+        eval += f * slot_words;
+        bin += f * slot_words;
+        top += f * (int64_t)n1 * n1;
+    }
     const int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (w >= (int64_t)n1 * n1 * row_words) return;
     uint32_t bits = __ldg(eval + w) | __ldg(bin + w);
@@ -69,6 +75,16 @@ __global__ void __launch_bounds__(256) render_rays_kernel(RenderArgs a) {
     const int64_t npix = (int64_t)a.width * a.height;
     const int64_t pix = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int lane = threadIdx.x & 31;
+    const int64_t frame = blockIdx.y;   // frame of a lockstep batch (0: one frame)
+    if (frame > 0) {
+        a.values += frame * a.slot_nodes;
+        a.eval += frame * a.slot_words;
+        a.bin += frame * a.slot_words;
+        a.top += frame * (int64_t)(a.N + 1) * (a.N + 1);
+        if (a.depth) a.depth += frame * npix;
+        if (a.mask) a.mask += frame * npix;
+        if (a.rgb) a.rgb += frame * npix * 3;
+    }
     bool hit = false;
     float zs = 0.f, px = 0.f, py = 0.f;
     if (pix < npix) {
@@ -138,7 +154,7 @@ __global__ void __launch_bounds__(256) render_rays_kernel(RenderArgs a) {
         a.hit_xyz[3 * (int64_t)pos + 0] = px;
         a.hit_xyz[3 * (int64_t)pos + 1] = py;
         a.hit_xyz[3 * (int64_t)pos + 2] = zs;
-        a.hit_pix[pos] = (int)pix;
+        a.hit_pix[pos] = (int)(frame * npix + pix);
     }
 }
 
@@ -148,14 +164,17 @@ cudaError_t launch_render_rays(const RenderArgs& a, cudaStream_t stream) {
     const int64_t npix = (int64_t)a.width * a.height;
     if (npix <= 0) return cudaSuccess;
     const int64_t n1 = a.N + 1;
-    cudaError_t e = cudaMemsetAsync(a.top, 0xff, (size_t)(n1 * n1) * sizeof(int), stream);   // -1
+    const int slots = a.slots > 1 ? a.slots : 1;
+    if (slots > 65535 || (int64_t)slots * npix > 2147483647LL) return cudaErrorInvalidValue;
+    cudaError_t e =
+        cudaMemsetAsync(a.top, 0xff, (size_t)(n1 * n1 * slots) * sizeof(int), stream);   // -1
     if (e != cudaSuccess) return e;
     const int64_t nt = n1 * n1 * a.row_words;
-    column_top_kernel<<<(unsigned)((nt + 255) / 256), 256, 0, stream>>>(a.N, a.row_words, a.eval,
-                                                                        a.bin, a.top);
+    column_top_kernel<<<dim3((unsigned)((nt + 255) / 256), (unsigned)slots), 256, 0, stream>>>(
+        a.N, a.row_words, a.eval, a.bin, a.top, a.slot_words);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    render_rays_kernel<<<(unsigned)((npix + 255) / 256), 256, 0, stream>>>(a);
+    render_rays_kernel<<<dim3((unsigned)((npix + 255) / 256), (unsigned)slots), 256, 0, stream>>>(a);
     return cudaGetLastError();
 }
 

@@ -40,7 +40,7 @@ EXPORTS = ("pifu_create", "pifu_destroy", "pifu_query", "pifu_query_colour", "pi
            "pifu_profile", "pifu_profile_read", "pifu_query_noalloc", "pifu_query_ex",
            "pifu_frame", "pifu_surrogate_init", "pifu_surrogate_samples", "pifu_surrogate_grad",
            "pifu_surrogate_train", "pifu_surrogate_params", "pifu_surrogate_query",
-           "pifu_calibrate_fp8")
+           "pifu_calibrate_fp8", "pifu_frames", "pifu_autotune")
 
 KERNEL_CLASSES = ("gather", "mlp_hidden", "mlp_last", "level", "select", "render", "mlp_f32")
 
@@ -128,6 +128,13 @@ def _lib():
                                ctypes.POINTER(pifu_camera), P, P, P, P, ctypes.POINTER(pifu_volume)]
     lib.pifu_frame.restype = I
     U64, D = ctypes.c_uint64, ctypes.c_double
+    lib.pifu_frames.argtypes = [P, I, ctypes.POINTER(pifu_fmap), ctypes.POINTER(pifu_fmap),
+                                ctypes.POINTER(F), ctypes.POINTER(pifu_levels),
+                                ctypes.POINTER(pifu_camera), P, P, P, P, ctypes.POINTER(pifu_volume)]
+    lib.pifu_frames.restype = I
+    lib.pifu_autotune.argtypes = [P, I64, P, ctypes.POINTER(ctypes.c_int32),
+                                  ctypes.POINTER(ctypes.c_double), I, ctypes.POINTER(I)]
+    lib.pifu_autotune.restype = I
     lib.pifu_calibrate_fp8.argtypes = [P, ctypes.POINTER(pifu_fmap), ctypes.POINTER(F), I, P]
     lib.pifu_calibrate_fp8.restype = I
     lib.pifu_surrogate_init.argtypes = [P, I, I, U64]
@@ -314,6 +321,38 @@ def pifu_frame(ctx, occ_map, col_map, calib, n0, num_levels, width, height, dept
                            _ptr(rgb), _ptr(mask), ctypes.byref(vol))
     _check(st, "pifu_frame", ctx)
     return vol
+
+
+def pifu_frames(ctx, occ_maps, col_maps, calibs, n0, num_levels, width, height, depth=None,
+                rgb=None, mask=None, precision=PIFU_PREC_MIXED, margin=0.02, max_rounds=0,
+                background=(0.0, 0.0, 0.0), stream=None, use_surrogate=False,
+                surrogate_margin=0.0):
+    """B frames in lockstep as one (cached) CUDA graph; returns B volumes.
+    occ_maps / col_maps: sequences of device tensors (col_maps may be None),
+    calibs: B calibrations; depth/rgb/mask: [B][H][W](x3) device tensors."""
+    B = len(occ_maps)
+    fo = (pifu_fmap * B)(*[fmap(m) for m in occ_maps])
+    fc = (pifu_fmap * B)(*[fmap(m) for m in col_maps]) if col_maps is not None else None
+    cal = np.ascontiguousarray(np.asarray(calibs, np.float32).reshape(B, 12))
+    cal_p = cal.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+    lv = pifu_levels(n0, num_levels, precision, max_rounds, margin, int(bool(use_surrogate)),
+                     surrogate_margin)
+    cam = pifu_camera(width, height, (ctypes.c_float * 3)(*background), PIFU_PREC_BF16)
+    vols = (pifu_volume * B)()
+    st = _lib().pifu_frames(ctx, B, fo, fc, cal_p, ctypes.byref(lv), ctypes.byref(cam),
+                            _stream(stream), _ptr(depth), _ptr(rgb), _ptr(mask), vols)
+    _check(st, "pifu_frames", ctx)
+    return list(vols)
+
+
+def pifu_autotune(ctx, rows, stream=None, n_max=32):
+    """Tile widths chosen per tensor-core layer: list of (BN, ms per launch)."""
+    bn = (ctypes.c_int32 * n_max)()
+    ms = (ctypes.c_double * n_max)()
+    n = ctypes.c_int(0)
+    _check(_lib().pifu_autotune(ctx, int(rows), _stream(stream), bn, ms, n_max, ctypes.byref(n)),
+           "pifu_autotune", ctx)
+    return [(int(bn[i]), float(ms[i])) for i in range(min(n.value, n_max))]
 
 
 def pifu_calibrate_fp8(ctx, occ_map, calib, n0=32, stream=None):

@@ -238,6 +238,64 @@ def colour_map(fig: Figure, H: int, W: int, C: int, seed: int) -> np.ndarray:
 
 
 # --------------------------------------------------------------------------
+# Video stream: seeded figures animated by per-frame joint perturbations
+# --------------------------------------------------------------------------
+
+class StreamFigure:
+    """One animated subject of a stream: its seed, scale and per-joint phases."""
+
+    def __init__(self, seed: int, scale: float, frames: int, amp: float = 0.03):
+        self.seed = seed
+        self.scale = scale
+        self.frames = frames
+        self.amp = amp
+        self.phase = np.random.default_rng(seed + 7).uniform(0.0, 2.0 * np.pi,
+                                                              size=(len(_JOINTS), 3))
+        self._noise_o = None
+        self._noise_t = None
+
+    def figure(self, t: int) -> Figure:
+        """The figure at frame t: joints moved by amp sin(2 pi t / frames + phase)."""
+        perturb = self.amp * np.sin(2.0 * np.pi * t / self.frames + self.phase)
+        return capsule_figure(self.seed, scale=self.scale, jitter=0.04, perturb=perturb)
+
+    def texture(self, H: int = 128, W: int = 128, C: int = 256):
+        """(g_O, g_T) of frame 0; their N(0, 1) channels 3.. are the subject's
+        fixed texture for every frame."""
+        if self._noise_o is None or self._noise_o.shape != (H, W, C):
+            self._noise_o = feature_map(self.figure(0), H, W, C, self.seed)
+            self._noise_t = colour_map(self.figure(0), H, W, C, self.seed)
+        return self._noise_o, self._noise_t
+
+    def geometry(self, t: int, H: int = 128, W: int = 128):
+        """Channels 0-2 of g_O (front depth, back depth, mask) and of g_T
+        (colour) at frame t, as [H][W][3] float32 arrays."""
+        fig = self.figure(t)
+        uu, vv = texel_centres(H, W)
+        front, back, hit = z_ray_figure(fig, uu, vv)
+        geo = np.stack([front, back, hit.astype(np.float32)], axis=-1).astype(np.float32)
+        return geo, colour_map(fig, H, W, 3, self.seed)
+
+    def maps(self, t: int, H: int = 128, W: int = 128, C: int = 256):
+        """(g_O, g_T) float32 maps of frame t: the fixed texture with the
+        frame's geometry and colour channels."""
+        g_o, g_t = (m.copy() for m in self.texture(H, W, C))
+        geo, col = self.geometry(t, H, W)
+        g_o[:, :, :3] = geo
+        g_t[:, :, :3] = col
+        return g_o, g_t
+
+
+def stream(n_figures: int = 8, frames: int = 64, seed: int = 100,
+           scale_range=(0.5, 1.3)) -> list:
+    """The subjects of a video stream: independent seeded figures with scales
+    uniform in scale_range (so their surface-cell fractions differ)."""
+    rng = np.random.default_rng(seed)
+    scales = rng.uniform(scale_range[0], scale_range[1], size=n_figures)
+    return [StreamFigure(seed + 1000 * (i + 1), float(scales[i]), frames) for i in range(n_figures)]
+
+
+# --------------------------------------------------------------------------
 # Calibration and query points
 # --------------------------------------------------------------------------
 
