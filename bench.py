@@ -47,6 +47,11 @@ def parse_args():
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--precision", choices=("fp32", "bf16", "mixed"), default="mixed")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP32 comparison")
+    ap.add_argument("--no-stream", action="store_true",
+                    help="skip the batched video-stream workload")
+    ap.add_argument("--batch", type=int, default=8, help="frames per lockstep batch (stream)")
+    ap.add_argument("--stream-subjects", type=int, default=8)
+    ap.add_argument("--stream-frames", type=int, default=64)
     ap.add_argument("--no-512", action="store_true",
                     help="skip the 512^3 precision form (timing and accuracy vs the oracle)")
     ap.add_argument("--form", choices=("graph", "host"), default="graph")
@@ -401,6 +406,142 @@ def train_surrogate(fr, args):
                     "levels": "all but the finest (the finest level always runs f_O)"}
 
 
+def run_stream(fr, args, world, sur_margin):
+    """The video-stream workload: subjects x frames animated figures with BF16
+    maps, in lockstep batches of args.batch frames (one CUDA graph each).
+    Returns a dict for the JSON line (rank-local timings)."""
+    import numpy as np
+    import torch
+    from concurrent.futures import ThreadPoolExecutor
+    from paper_2007_13988_gb300 import synth
+    pifu, w, dev, s = fr.pifu, fr.w, fr.dev, fr.stream
+    subj = synth.stream(n_figures=args.stream_subjects, frames=args.stream_frames, seed=100)
+    H = W = 128
+    C = 256
+    t0 = time.perf_counter()
+    occ, col = [], []
+    with torch.cuda.stream(s):
+        for sj in subj:
+            g_o, g_t = sj.texture(H, W, C)
+            base_o = torch.from_numpy(g_o).to(dev).to(torch.bfloat16)
+            base_t = torch.from_numpy(g_t).to(dev).to(torch.bfloat16)
+            with ThreadPoolExecutor(8) as ex:
+                geo = list(ex.map(lambda t: sj.geometry(t, H, W), range(args.stream_frames)))
+            fo, ft = [], []
+            for g, cc in geo:
+                m_o = base_o.clone()
+                m_o[:, :, :3] = torch.from_numpy(g).to(dev).to(torch.bfloat16)
+                m_t = base_t.clone()
+                m_t[:, :, :3] = torch.from_numpy(cc).to(dev).to(torch.bfloat16)
+                fo.append(m_o)
+                ft.append(m_t)
+            occ.append(fo)
+            col.append(ft)
+    s.synchronize()
+    gen_s = time.perf_counter() - t0
+    B = args.batch
+    n_subj, n_frames = len(subj), args.stream_frames
+    # frame order: frame t of every subject, then t + 1 ...
+    order = [(i, t) for t in range(n_frames) for i in range(n_subj)]
+    batches = [order[k:k + B] for k in range(0, len(order), B) if len(order[k:k + B]) == B]
+    R = w.render
+    depth = torch.empty((B, R, R), dtype=torch.float32, device=dev)
+    rgb = torch.empty((B, R, R, 3), dtype=torch.float32, device=dev)
+    mask = torch.empty((B, R, R), dtype=torch.uint8, device=dev)
+    calibs = [w.calib] * B
+    # FP8 scales from the stream's own first frame; tiles for a level-0 batch
+    pifu.pifu_calibrate_fp8(fr.ctx, occ[0][0], w.calib, w.n0, stream=s)
+    tuned = pifu.pifu_autotune(fr.ctx, B * (w.n0 + 1) ** 3, stream=s)
+
+    def run(prec, sur):
+        kw = {"use_surrogate": True, "surrogate_margin": sur} if sur is not None else {}
+        lat, vols = [], None
+        for rep in range(2):   # first pass: capture + warm-up
+            lat = []
+            for bt in batches:
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                with torch.cuda.stream(s):
+                    fr.flush.zero_()
+                e0.record(s)
+                vols = pifu.pifu_frames(fr.ctx, [occ[i][t] for i, t in bt],
+                                        [col[i][t] for i, t in bt], calibs, w.n0, w.num_levels,
+                                        R, R, depth, rgb, mask, precision=prec, stream=s, **kw)
+                e1.record(s)
+                e1.synchronize()
+                lat.append(e0.elapsed_time(e1))
+        total_s = sum(lat) / 1000.0
+        n = len(batches) * B
+        return {"value": world * n / total_s, "unit": UNIT, "frames": n,
+                "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                "batch_ms_min": min(lat), "batch_ms_max": max(lat),
+                "rounds_last_batch": [int(vols[0].conflict_rounds[l]) for l in range(w.num_levels)],
+                "evals_per_frame_mean": float(np.mean([v.n_eval for v in vols]))}
+
+    def run_single(prec):
+        # the same frames one graph launch each (pifu_frame), for comparison
+        lat = []
+        for rep in range(2):
+            lat = []
+            for i, t in order[:len(batches) * B]:
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(s)
+                pifu.pifu_frame(fr.ctx, occ[i][t], col[i][t], w.calib, w.n0, w.num_levels, R, R,
+                                depth[0], rgb[0], mask[0], precision=prec, stream=s)
+                e1.record(s)
+                e1.synchronize()
+                lat.append(e0.elapsed_time(e1))
+        return {"value": world * len(lat) / (sum(lat) / 1000.0), "unit": UNIT,
+                "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99))}
+
+    out = {"workload": f"{n_subj} subjects x {n_frames} frames (scales "
+                       f"{min(x.scale for x in subj):.2f}-{max(x.scale for x in subj):.2f}, joints "
+                       f"animated per frame), 256x128x128 BF16 maps per frame, 32^3->256^3 + "
+                       f"512^2 render per frame",
+           "batch": B, "form": "pifu_frames: lockstep batches, one CUDA graph",
+           "latency": "per frame = its batch's device time (all frames of a batch finish "
+                      "together); p50/p99 over batches",
+           "map_generation_s": gen_s, "autotuned_tiles": [bn for bn, _ in tuned],
+           "count_readings": {"subjects_x_frames": n_subj * n_frames,
+                              "frames_total_alternative": n_frames}}
+    prec8 = PREC["fp8_mixed"]
+    if sur_margin is not None:
+        out["fp8_mixed_surrogate"] = run(prec8, sur_margin)
+        out["value"] = out["fp8_mixed_surrogate"]["value"]
+    out["fp8_mixed"] = run(prec8, None)
+    out["mixed"] = run(PREC["mixed"], None)
+    out.setdefault("value", out["fp8_mixed"]["value"])
+    out["single_frame_graphs_mixed"] = run_single(PREC["mixed"])
+    out["unit"] = UNIT
+    return out, (occ, col, subj)
+
+
+def stream_accuracy(fr, args, stream_inputs):
+    """FP8_MIXED volumes of two stream frames (the first subject's first frame
+    and the largest subject's middle frame) against the FP64 oracle on the
+    same BF16-rounded maps."""
+    import numpy as np
+    from oracle import field, localize, metrics
+    pifu, w = fr.pifu, fr.w
+    occ, col, subj = stream_inputs
+    big = max(range(len(subj)), key=lambda i: subj[i].scale)
+    samples = []
+    for i, t in ((0, 0), (big, args.stream_frames // 2)):
+        m_r = occ[i][t].float().cpu().numpy().astype(np.float64)
+        lvs = localize.hierarchical(lambda P: field.occupancy(w.occ_net, m_r, w.calib, P), w.n0,
+                                    w.num_levels)
+        vol = pifu.pifu_frames(fr.ctx, [occ[i][t]], [col[i][t]], [w.calib], w.n0, w.num_levels,
+                               w.render, w.render, precision=PREC["fp8_mixed"],
+                               stream=fr.stream)[0]
+        b = pifu.unpack_bits(pifu.volume_tensors(vol)[0].cpu().numpy(), vol.n, vol.row_words)
+        samples.append({"subject": i, "frame": t, "scale": subj[i].scale,
+                        "iou_fp8_mixed_vs_oracle": metrics.iou(b, lvs[-1].binary),
+                        "inside_fraction": float(np.mean(lvs[-1].binary)),
+                        "evaluated_fraction_finest": lvs[-1].n_eval / lvs[-1].binary.size})
+    return samples
+
+
 def run_ours(args, rank, world, local_rank):
     import numpy as np
     import torch
@@ -459,6 +600,13 @@ def run_ours(args, rank, world, local_rank):
             p512[name] = (r, snapshot(fr, r["vol"]))
         fp32_512 = time_form(fr, 0, 2, 1, world, levels=L5)
         p512["fp32"] = (fp32_512, snapshot(fr, fp32_512["vol"]))
+
+    # ---- the video stream in lockstep batches ----------------------------------
+    stream_out, stream_inputs = None, None
+    if prec != 0 and not args.no_stream:
+        stream_out, stream_inputs = run_stream(fr, args, world, sur_margin)
+        if rank == 0 and not args.no_cpu_baseline:
+            stream_out["accuracy_samples"] = stream_accuracy(fr, args, stream_inputs)
 
     # ---- query points/s (raw field, inputs resident) -----------------------
     Q = args.query_points
@@ -617,6 +765,8 @@ def run_ours(args, rank, world, local_rank):
         for name, (r, snap) in others.items():
             line["other_forms"][name]["accuracy"] = accuracy(snap, lv, o_rgb, o_hit,
                                                              plain_rgb if plain else None)
+    if stream_out is not None:
+        line["stream"] = stream_out
     if p512:
         out = {"workload": "the same frame at 512^3 effective resolution: 32^3 -> 512^3 "
                            "(five levels) + 512^2 render, graph form",
