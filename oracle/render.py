@@ -90,3 +90,95 @@ def render(values, R, col_net, occ_map, col_map, calib, background=(0.0, 0.0, 0.
         P = np.stack([c[ii], c[jj], depth[jj, ii]], axis=1)
         rgb[jj, ii] = _field.colour(col_net, occ_map, col_map, calib, P)
     return rgb, depth, hit
+
+
+# ---- the paper's view-culled final level (Sec. 3.2, "Mesh-free Rendering") ----
+#
+# Reading used: the render's pixel columns are the final level's columns (the
+# grid's x, y are the pixel axes): pixel (i, j) at its centre, depth nodes
+# z_k = 1 - 2k/N_f (k = 0 nearest) of the final level, N_f = 2 N_c where N_c
+# is the last localized level.  Steps, in the paper's order:
+#  1. upsample the binarized level N_c by tri-linear interpolation to every
+#     (pixel, depth node): the tentative value T;
+#  2. argmax along the ray: O_max = max_k T, i_max = the smallest k reaching it;
+#  3. if O_max = 1, the nodes behind i_max (k > i_max) are shadow nodes;
+#  4. the remaining nodes with an interpolated value strictly between 0 and 1
+#     (the ambiguous band around 0.5) are evaluated with the network; every
+#     other node keeps T (0 or 1, or its fraction behind the shadow line);
+#  5. binarize (>= 0.5) and argmax again; a pixel hits when some node is
+#     inside, and its surface lies between the nodes i_max - 1 and i_max,
+#     interpolated linearly by their values (z = 1 when i_max = 0);
+#  6. Eq. 3 colours the surface point.
+
+
+def tentative_columns(coarse_binary, R, N_f):
+    """T [R, R, N_f + 1]: tri-linear interpolation of the binarized level
+    (bool [N_c+1]^3, [z][y][x]) at pixel centres and final-level depth nodes
+    (k counted from the observer)."""
+    N_c = coarse_binary.shape[0] - 1
+    B = np.asarray(coarse_binary, dtype=F64)
+    Vc = ray_columns(B, R)                   # [j, i, kc], kc = coarse depth from the observer
+    zk = 1.0 - 2.0 * np.arange(N_f + 1, dtype=F64) / N_f
+    fz = (1.0 - zk) * N_c / 2.0              # coarse depth coordinate from the observer
+    k0 = np.minimum(np.floor(fz).astype(np.int64), N_c - 1)
+    wz = fz - k0
+    return (1.0 - wz)[None, None, :] * Vc[:, :, k0] + wz[None, None, :] * Vc[:, :, k0 + 1]
+
+
+def culled_final_level(field, coarse_binary, R, N_f=None):
+    """The view-culled final level.  field(P [m, 3]) -> occupancy [m].
+
+    Returns a dict: depth [R, R] (NaN on misses), hit [R, R] bool, values
+    [R, R, N_f+1] (network output where evaluated, else T), evaluated
+    [R, R, N_f+1] bool, shadow [R, R, N_f+1] bool, T, i_max [R, R] (-1 on
+    misses), n_eval."""
+    N_c = coarse_binary.shape[0] - 1
+    if N_f is None:
+        N_f = 2 * N_c
+    T = tentative_columns(coarse_binary, R, N_f)
+    # 2. argmax along the ray (smallest index among the maxima)
+    o_max = T.max(axis=2)
+    i_max = np.argmax(T >= o_max[..., None], axis=2)
+    # 3. shadow nodes
+    k = np.arange(N_f + 1)[None, None, :]
+    shadow = (o_max[..., None] >= 1.0) & (k > i_max[..., None])
+    # 4. evaluate the non-shadow ambiguous nodes
+    ev = (~shadow) & (T > 0.0) & (T < 1.0)
+    values = T.copy()
+    jj, ii, kk = np.nonzero(ev)
+    c = pixel_centres(R)
+    zk = 1.0 - 2.0 * np.arange(N_f + 1, dtype=F64) / N_f
+    if len(jj):
+        P = np.stack([c[ii], c[jj], zk[kk]], axis=1)
+        values[jj, ii, kk] = field(P)
+    # 5. binarize, argmax again, crossing
+    inside = values >= 0.5
+    hit = inside.any(axis=2)
+    first = np.where(hit, np.argmax(inside, axis=2), -1)
+    depth = np.full((R, R), np.nan)
+    hj, hi = np.nonzero(hit)
+    hk = first[hj, hi]
+    at0 = hk == 0
+    depth[hj[at0], hi[at0]] = 1.0
+    nj, ni, nk = hj[~at0], hi[~at0], hk[~at0]
+    v0 = values[nj, ni, nk - 1]
+    v1 = values[nj, ni, nk]
+    t = (0.5 - v0) / (v1 - v0)
+    depth[nj, ni] = zk[nk - 1] + t * (zk[nk] - zk[nk - 1])
+    return {"depth": depth, "hit": hit, "values": values, "evaluated": ev, "shadow": shadow,
+            "T": T, "i_max": first, "n_eval": int(ev.sum())}
+
+
+def render_culled(field, coarse_binary, R, col_net, occ_map, col_map, calib,
+                  background=(0.0, 0.0, 0.0), N_f=None):
+    """Eq. 3 over the view-culled final level: (rgb, depth, hit, result dict)."""
+    res = culled_final_level(field, coarse_binary, R, N_f)
+    depth, hit = res["depth"], res["hit"]
+    rgb = np.empty((R, R, 3), dtype=F64)
+    rgb[:] = np.asarray(background, dtype=F64)
+    c = pixel_centres(R)
+    jj, ii = np.nonzero(hit)
+    if len(jj):
+        P = np.stack([c[ii], c[jj], depth[jj, ii]], axis=1)
+        rgb[jj, ii] = _field.colour(col_net, occ_map, col_map, calib, P)
+    return rgb, depth, hit, res

@@ -106,3 +106,110 @@ def test_render_colours_the_surface_point():
     np.testing.assert_allclose(rgb[:, :, 0], np.broadcast_to((np.tanh(c)[None, :] + 1) / 2, (R, R)), atol=1e-12)
     np.testing.assert_allclose(rgb[:, :, 1], (np.tanh(-0.3046875) + 1) / 2, atol=1e-12)
     np.testing.assert_allclose(rgb[:, :, 2], 0.5)
+
+
+# ---- view-culled final level -------------------------------------------------
+
+def capsule_setup(n0, levels):
+    fig = synth.capsule_figure(0)
+    n_f = n0 << levels                # the final level doubles the last localized one
+    tau = 0.5 * 2.0 / n_f
+    f = lambda P: field.capsule_occupancy(fig.a, fig.b, fig.r, P, tau)
+    lv = localize.hierarchical(f, n0, levels)
+    return fig, f, lv, n_f
+
+
+def test_culled_plane_crossing_closed_form():
+    """A half-space, occupancy 0.5 + s (z0 - z) clipped to [0, 1].  Along a
+    ray the upsampled binarized level is 0, then 1/2 at the one fine node
+    between the coarse outside and inside nodes, then 1: that node is the only
+    one evaluated, and the crossing interpolates its value with its
+    neighbour's tentative 0 or 1."""
+    z0, slope = 0.2109375, 3.0
+    f = lambda P: np.clip(0.5 + slope * (z0 - P[:, 2]), 0.0, 1.0)
+    N_c, R = 16, 16
+    N_f = 2 * N_c
+    h = 2.0 / N_f
+    coarse = plane_volume(N_c, z0, slope) >= 0.5
+    res = render.culled_final_level(f, coarse, R)
+    assert res["hit"].all()
+    assert (res["evaluated"].sum(axis=2) == 1).all()
+    zc = localize.node_coords(N_c)
+    z_in = zc[coarse[:, 0, 0]].max()          # nearest coarse inside node
+    z_m = z_in + h                              # the fine node between it and the outside one
+    o_m = 0.5 + slope * (z0 - z_m)
+    if o_m >= 0.5:
+        want = (z_m + h) - (0.5 / o_m) * h      # between tentative 0 and o_m
+    else:
+        want = z_m - (0.5 - o_m) / (1.0 - o_m) * h   # between o_m and tentative 1
+    np.testing.assert_allclose(res["depth"], want, atol=1e-13)
+
+
+def test_culled_invariants():
+    fig, f, lv, n_f = capsule_setup(8, 3)
+    R = n_f
+    res = render.culled_final_level(f, lv[-1].binary, R)
+    T, ev, sh = res["T"], res["evaluated"], res["shadow"]
+    # nothing behind the first fully inside tentative node is evaluated
+    assert not (ev & sh).any()
+    # only ambiguous (fractional) tentative nodes are evaluated
+    assert ((T[ev] > 0) & (T[ev] < 1)).all()
+    # shadow nodes start right after the nearest node with T = 1
+    o_max = T.max(axis=2)
+    jj, ii = np.nonzero(o_max >= 1)
+    for j, i in zip(jj[:200], ii[:200]):
+        first_one = int(np.argmax(T[j, i] >= 1))
+        assert not sh[j, i, :first_one + 1].any() and sh[j, i, first_one + 1:].all()
+    # a hit's first inside node is preceded only by outside nodes
+    v = res["values"]
+    hj, hi = np.nonzero(res["hit"])
+    for j, i in zip(hj[:500], hi[:500]):
+        k = res["i_max"][j, i]
+        assert v[j, i, k] >= 0.5 and (v[j, i, :k] < 0.5).all()
+    # far fewer evaluations than the dense final level
+    assert res["n_eval"] < 0.05 * T.size
+
+
+@pytest.mark.parametrize("n0,levels", [(8, 3), (16, 2)])
+def test_culled_depth_matches_ray_capsule_intersection(n0, levels):
+    fig, f, lv, n_f = capsule_setup(n0, levels)
+    R = n_f
+    res = render.culled_final_level(f, lv[-1].binary, R)
+    depth, hit = res["depth"], res["hit"]
+    c = render.pixel_centres(R)
+    uu, vv = np.meshgrid(c, c, indexing="xy")
+    front, _, ahit = synth.z_ray_figure(fig, uu, vv)
+    both = hit & ahit
+    assert both.sum() > 0.9 * ahit.sum()
+    assert np.abs(depth[both] - front[both]).max() <= 2.0 / n_f
+
+
+def test_culled_matches_dense_columns():
+    """Brute force: the network at every node of every pixel column, then the
+    first inside node.  Where the coarse level is right the culled level finds
+    the same first inside node (its one evaluated node per ray decides which
+    side of it the surface lies), and its depth is within one fine voxel of
+    the dense linear crossing."""
+    fig, f, lv, n_f = capsule_setup(8, 3)
+    R = n_f
+    res = render.culled_final_level(f, lv[-1].binary, R)
+    c = render.pixel_centres(R)
+    zk = 1 - 2 * np.arange(n_f + 1) / n_f
+    jj, ii, kk = np.meshgrid(np.arange(R), np.arange(R), np.arange(n_f + 1), indexing="ij")
+    P = np.stack([c[ii.ravel()], c[jj.ravel()], zk[kk.ravel()]], axis=1)
+    dense = f(P).reshape(R, R, n_f + 1)
+    inside = dense >= 0.5
+    dhit = inside.any(axis=2)
+    assert np.mean(dhit == res["hit"]) >= 0.995
+    both = dhit & res["hit"]
+    kd = np.argmax(inside, axis=2)
+    assert np.mean(kd[both] == res["i_max"][both]) >= 0.99
+    zd = np.full(dense.shape[:2], np.nan)
+    for j, i in zip(*np.nonzero(both)):
+        k = kd[j, i]
+        if k == 0:
+            zd[j, i] = 1.0
+        else:
+            tt = (0.5 - dense[j, i, k - 1]) / (dense[j, i, k] - dense[j, i, k - 1])
+            zd[j, i] = zk[k - 1] + tt * (zk[k] - zk[k - 1])
+    assert np.nanmax(np.abs(zd[both] - res["depth"][both])) <= 2.0 / n_f
