@@ -99,11 +99,23 @@ typedef struct {
 
 /* Target view of the render: the volume is aligned with it (Sec. 3.2), so
  * pixel (i, j) looks along -z through x = (2i+1)/width - 1,
- * y = (2j+1)/height - 1. */
+ * y = (2j+1)/height - 1.
+ * final_level 0: the ray samples the localized volume (N cells) at its depth
+ * nodes, bilinearly between the four node columns around the pixel.
+ * final_level 1: the paper's view-culled final level at twice the localized
+ * resolution (Sec. 3.2; square power-of-two images): along each pixel column
+ * the binarized localized level is upsampled tri-linearly to the 2N + 1
+ * depth nodes of the next level; the nodes behind the nearest fully inside
+ * one are shadow nodes; the remaining ambiguous nodes (0 < upsampled < 1) are
+ * evaluated with f_O in the localization's arithmetic; the first inside node
+ * after binarization and its predecessor give the surface.  No conflict loop
+ * runs at this level.  The evaluations are counted in the volume's
+ * evals_per_level[num_levels]. */
 typedef struct {
     int32_t width, height;
     float background[3];  /* B of Eq. 3                                        */
     int32_t precision;    /* pifu_precision of the colour MLP                   */
+    int32_t final_level;  /* 0 or 1 (see above)                                 */
 } pifu_camera;
 
 /* Result of pifu_localize: views into context memory, valid until the next

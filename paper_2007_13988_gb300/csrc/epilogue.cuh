@@ -23,7 +23,7 @@ __device__ __forceinline__ void last_epilogue(const Epilogue& epi, int64_t p, in
         const float o = apply_act(ACT_SIGMOID, t[0] + bias[0]);
         if (fabsf(o - kHalf) < epi.margin) {
             const unsigned pos = atomicAdd(epi.recheck_count, 1u);
-            epi.recheck[pos] = epi.mode == EPI_LEVEL
+            epi.recheck[pos] = (epi.mode == EPI_LEVEL || epi.mode == EPI_COLUMN)
                                    ? (epi.list ? epi.list[p] : (int)(epi.base + p))
                                    : (epi.pix ? epi.pix[p] : (int)p);
             return;
@@ -32,6 +32,9 @@ __device__ __forceinline__ void last_epilogue(const Epilogue& epi, int64_t p, in
     if (epi.mode == EPI_STORE) {
         const int64_t q = epi.pix ? (int64_t)epi.pix[p] : p;
         for (int j = 0; j < n_out; ++j) epi.out[q * n_out + j] = apply_act(epi.act, t[j] + bias[j]);
+    } else if (epi.mode == EPI_COLUMN) {
+        epi.out[epi.list ? (int64_t)epi.list[p] : epi.base + p] =
+            apply_act(ACT_SIGMOID, t[0] + bias[0]);
     } else if (epi.mode == EPI_PIXELS) {
         const int64_t pix = epi.pix[p];
         for (int j = 0; j < n_out; ++j) epi.out[pix * 3 + j] = apply_act(epi.act, t[j] + bias[j]);

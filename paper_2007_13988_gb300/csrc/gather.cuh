@@ -66,6 +66,20 @@ __device__ __forceinline__ int point_xyz(const PointSrc& src, int64_t p, float& 
         z = src.xyz[3 * q + 2];
         return src.maps0 ? (int)((int64_t)src.keys[p] / src.slot_div) : 0;
     }
+    if (src.mode == PTS_COLUMN) {
+        // key = pixel (N + 1) + k; pixel centre (2i+1)/width - 1, depth 1 - 2k/N
+        const int64_t key = (int64_t)src.list[p];
+        const int64_t n1 = src.N + 1;
+        const int64_t pix = key / n1;
+        const int k = (int)(key - pix * n1);
+        const int i = (int)(pix % src.width);
+        const int j = (int)(pix / src.width);
+        const float inv = 1.0f / (float)src.width;   // exact for power-of-two widths
+        x = __fmaf_rn((float)(2 * i + 1), inv, -1.0f);
+        y = __fmaf_rn((float)(2 * j + 1), inv, -1.0f);
+        z = __fmaf_rn(-(float)k, 2.0f / (float)src.N, 1.0f);
+        return 0;
+    }
     int64_t idx = (src.mode == PTS_LIST) ? (int64_t)src.list[p] : src.base + p;
     int f = 0;
     if (src.maps0) {

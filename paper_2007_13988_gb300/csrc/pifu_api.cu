@@ -109,7 +109,7 @@ struct FrameKey {
     float sur_margin;
     uint64_t sur_version;          // f_S's tensor-core weights are rebuilt on change
     uint64_t f8_version;           // f_O's E4M3 weights are rebuilt by calibration
-    int width, height, cam_precision;
+    int width, height, cam_precision, final_level;
     float bg[3];
     float* depth;
     float* rgb;
@@ -118,6 +118,7 @@ struct FrameKey {
 
 // Device-side counters of a graph frame, copied to the host once at its end.
 struct GraphStats {
+    unsigned long long culled;   // view-culled final level: candidates evaluated
     unsigned long long evals[8];
     unsigned long long cands[8];
     unsigned long long rechecked[8];
@@ -296,6 +297,12 @@ struct pifu_ctx {
     int* hit_pix = nullptr;
     int64_t hit_cap = 0;
     int* col_top = nullptr;       // render: per node column, highest non-empty depth
+    // view-culled final level: candidate keys and their occupancies
+    int* cull_list = nullptr;
+    float* cull_values = nullptr;
+    int64_t cull_cap = 0, cull_vals_cap = 0;
+    int vol_prec = 0;             // arithmetic of the last localization
+    float vol_margin = 0.f;
     // last localized volume
     bool have_volume = false;
     int vol_N = 0;
@@ -1008,8 +1015,9 @@ int run_mlp_mixed(pifu_ctx* ctx, const DevNet& net, const PointSrc& src, int64_t
     if (n == 0) return PIFU_OK;
     PointSrc s2 = src;
     Epilogue e2 = epi;
-    if (epi.mode == EPI_LEVEL) {
-        s2.mode = PTS_LIST;
+    if (epi.mode == EPI_LEVEL || epi.mode == EPI_COLUMN) {
+        // the queue holds keys of the same kind as the batch's
+        s2.mode = epi.mode == EPI_COLUMN ? PTS_COLUMN : PTS_LIST;
         s2.list = ctx->recheck;
         e2.list = ctx->recheck;
     } else {
@@ -1061,6 +1069,37 @@ int eval_level_batch(pifu_ctx* ctx, const PointSrc& src, int64_t n, const Map& m
     ef.list = ctx->squeue;
     return eval_level_batch(ctx, sf, nf, map, cal, ef, prec, margin, false, 0.f, s, rechecked,
                             nullptr);
+}
+
+// View-culled final level workspaces: candidate keys (16 per pixel) and the
+// dense per-(pixel, depth node) occupancy store (touched only at candidates).
+int ensure_cull_ws(pifu_ctx* ctx, int64_t npix, int Nc) {
+    const int64_t cap = npix * 16;
+    const int64_t vals = npix * (2 * (int64_t)Nc + 1);
+    if (cap > ctx->cull_cap) {
+        dev_free(ctx->cull_list);
+        ctx->cull_cap = 0;
+        CK(dev_alloc(&ctx->cull_list, cap));
+        ctx->cull_cap = cap;
+    }
+    if (vals > ctx->cull_vals_cap) {
+        dev_free(ctx->cull_values);
+        ctx->cull_vals_cap = 0;
+        CK(dev_alloc(&ctx->cull_values, vals));
+        ctx->cull_vals_cap = vals;
+    }
+    return PIFU_OK;
+}
+
+// One host-sized evaluation batch in the given arithmetic (FP32, the tensor-
+// core forms, or those with the FP32 re-check).
+int eval_batch(pifu_ctx* ctx, const PointSrc& src, int64_t n, const Map& map, const Calib& cal,
+               const Epilogue& epi, int prec, float margin, cudaStream_t s) {
+    const DevNet& fo = ctx->net[0];
+    if (prec_mixed(prec))
+        return run_mlp_mixed(ctx, fo, src, n, map, Map{}, cal, epi, margin, s, nullptr,
+                             prec == PIFU_PREC_FP8_MIXED);
+    return run_mlp(ctx, fo, src, n, map, Map{}, cal, epi, s, prec);
 }
 
 int decode_err(unsigned int e) {
@@ -1364,7 +1403,7 @@ int g_eval(pifu_ctx* ctx, const DevNet& net, const PointSrc& src, int64_t cap,
                         prec == PIFU_PREC_FP8_MIXED);
     if (st != PIFU_OK) return st;
     PointSrc s2 = src;   // keeps the frames' maps of a lockstep batch
-    s2.mode = PTS_LIST;
+    s2.mode = src.mode == PTS_COLUMN ? PTS_COLUMN : PTS_LIST;   // the queue holds keys
     s2.list = ctx->recheck;
     s2.base = 0;
     s2.count = nullptr;
@@ -1487,6 +1526,60 @@ int g_enqueue_frame(pifu_ctx* ctx, const FrameKey& k, const Map& occ, const Map&
         if (st != PIFU_OK) return st;
         if (ee != cudaSuccess) return fail_cuda(ctx, ee);
         ctx->g_launches_body[l] = launches_now(ctx) - before;
+    }
+    if (k.final_level) {
+        // the view-culled final level at 2 N depth nodes, then colour
+        CullArgs c{};
+        c.width = k.width;
+        c.height = k.height;
+        c.Nc = N;
+        c.row_words = row_words_of(N);
+        c.bin = ctx->bin[cur];
+        c.list = ctx->cull_list;
+        c.count = ctx->d_count;
+        c.cap = (unsigned)std::min<int64_t>(ctx->cull_cap, kChunkTC);
+        c.err = err;
+        c.values = ctx->cull_values;
+        for (int q = 0; q < 3; ++q) c.bg[q] = k.bg[q];
+        c.depth = k.depth;
+        c.rgb = k.rgb;
+        c.mask = k.mask;
+        c.hit_xyz = ctx->hit_xyz;
+        c.hit_pix = ctx->hit_pix;
+        c.hit_count = ctx->d_count;
+        c.top = ctx->col_top;
+        CK(cudaMemsetAsync(ctx->d_count, 0, sizeof(unsigned int), s));
+        CK(launch_cull_select(c, s));
+        CK(launch_accumulate(&gs->culled, ctx->d_count, c.cap, err, s));
+        PointSrc src{PTS_COLUMN, nullptr, ctx->cull_list, 0, 2 * N, nullptr};
+        src.width = k.width;
+        Epilogue epi{};
+        epi.mode = EPI_COLUMN;
+        epi.out = ctx->cull_values;
+        epi.list = ctx->cull_list;
+        const int lf = std::min(k.num_levels, kMaxLevels - 1);
+        st = g_eval(ctx, net, src, (int64_t)c.cap, ctx->d_count, occ, cal, epi, k.precision,
+                    k.margin, &gs->rechecked[lf], s);
+        if (st != PIFU_OK) return st;
+        CK(cudaMemsetAsync(ctx->d_count, 0, sizeof(unsigned int), s));
+        CK(launch_cull_final(c, s));
+        ctx->prof.k[PIFU_K_RENDER].launches += 3;
+        if (k.rgb) {
+            const int64_t npix = (int64_t)k.width * k.height;
+            PointSrc hs{PTS_XYZ, ctx->hit_xyz, nullptr, 0, 0, nullptr};
+            Epilogue he{};
+            he.mode = EPI_PIXELS;
+            he.act = ACT_TANH01;
+            he.out = k.rgb;
+            he.pix = ctx->hit_pix;
+            const Map m0 = col.C > 0 ? col : occ;
+            const Map m1 = col.C > 0 ? occ : Map{};
+            st = run_mlp_tc(ctx, ctx->net[1], hs, npix, m0, m1, cal, he, s, ctx->d_count);
+            if (st != PIFU_OK) return st;
+        }
+        CK(cudaMemcpyAsync(&gs->err, err, sizeof(unsigned int), cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemcpyAsync(ctx->h_gstats, gs, sizeof(GraphStats), cudaMemcpyDeviceToHost, s));
+        return PIFU_OK;
     }
     // render: first-occupied depth per column, rays, colour at the hits
     RenderArgs a{};
@@ -2294,6 +2387,8 @@ int pifu_localize(pifu_ctx* ctx, const pifu_fmap* occ_map, const float calib[12]
     ctx->have_volume = true;
     ctx->vol_N = N;
     ctx->vol_bin = cur;
+    ctx->vol_prec = prec;
+    ctx->vol_margin = lv->margin;
     if (out) *out = vs;
     return PIFU_OK;
 }
@@ -2313,12 +2408,79 @@ int pifu_render(pifu_ctx* ctx, const pifu_camera* cam, const pifu_fmap* occ_map,
         const int c_t = col_map ? col_map->C : 0;
         if (ctx->net[1].d_in != c_t + occ_map->C + 1) return PIFU_ERR_ARG;
     }
+    if (cam->final_level != 0 &&
+        (cam->final_level != 1 || cam->width != cam->height || !is_pow2(cam->width) ||
+         !map_ok(occ_map) || ctx->net[0].d_in != occ_map->C + 1))
+        return PIFU_ERR_ARG;
     DeviceGuard g(ctx->device);
     if (!g.ok) return PIFU_ERR_CUDA;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const int64_t npix = (int64_t)cam->width * cam->height;
     int st = ensure_hit_ws(ctx, npix);
     if (st != PIFU_OK) return st;
+    unsigned int n = 0;
+    if (cam->final_level) {
+        // view-culled final level (Sec. 3.2) at 2 N depth nodes of the pixel columns
+        const int Nc = ctx->vol_N;
+        st = ensure_cull_ws(ctx, npix, Nc);
+        if (st != PIFU_OK) return st;
+        CullArgs c{};
+        c.width = cam->width;
+        c.height = cam->height;
+        c.Nc = Nc;
+        c.row_words = row_words_of(Nc);
+        c.bin = ctx->bin[ctx->vol_bin];
+        c.list = ctx->cull_list;
+        c.count = ctx->d_count;
+        c.cap = (unsigned)ctx->cull_cap;
+        c.err = ctx->d_count + 1;
+        c.values = ctx->cull_values;
+        for (int q = 0; q < 3; ++q) c.bg[q] = cam->background[q];
+        c.depth = depth_dev;
+        c.rgb = rgb_dev;
+        c.mask = mask_dev;
+        c.hit_xyz = ctx->hit_xyz;
+        c.hit_pix = ctx->hit_pix;
+        c.hit_count = ctx->d_count;
+        c.top = ctx->col_top;
+        CK(cudaMemsetAsync(ctx->d_count, 0, sizeof(unsigned int), s));
+        cudaEvent_t ev = ctx->prof.begin(s);
+        CK(launch_cull_select(c, s));
+        ctx->prof.end(PIFU_K_SELECT, ev, s, 0.0, 4.0 * words_of(Nc) + 4.0 * npix);
+        unsigned int nc = 0;
+        st = read_count(ctx, s, &nc);
+        if (st != PIFU_OK) return st;
+        if (nc > 0) {
+            PointSrc src{PTS_COLUMN, nullptr, ctx->cull_list, 0, 2 * Nc, nullptr};
+            src.width = cam->width;
+            Epilogue epi{};
+            epi.mode = EPI_COLUMN;
+            epi.out = ctx->cull_values;
+            epi.list = ctx->cull_list;
+            st = eval_batch(ctx, src, nc, to_map(occ_map), to_calib(calib), epi, ctx->vol_prec,
+                            ctx->vol_margin, s);
+            if (st != PIFU_OK) return st;
+        }
+        if (ctx->stats.num_levels < kMaxLevels)
+            ctx->stats.evals_per_level[ctx->stats.num_levels] = nc;
+        CK(cudaMemsetAsync(ctx->d_count, 0, sizeof(unsigned int), s));
+        ev = ctx->prof.begin(s);
+        CK(launch_cull_final(c, s));
+        ctx->prof.end(PIFU_K_RENDER, ev, s, 0.0, 4.0 * words_of(Nc) + 4.0 * nc + 17.0 * npix);
+        st = read_count(ctx, s, &n);
+        if (st != PIFU_OK) return st;
+        ctx->prof.k[PIFU_K_RENDER].bytes += 16.0 * n;   // the hit list
+        if (!rgb_dev || n == 0) return PIFU_OK;
+        PointSrc hs{PTS_XYZ, ctx->hit_xyz, nullptr, 0, 0};
+        Epilogue he{};
+        he.mode = EPI_PIXELS;
+        he.act = ACT_TANH01;
+        he.out = rgb_dev;
+        he.pix = ctx->hit_pix;
+        const Map m0 = col_map ? to_map(col_map) : to_map(occ_map);
+        const Map m1 = col_map ? to_map(occ_map) : Map{};
+        return run_mlp(ctx, ctx->net[1], hs, n, m0, m1, to_calib(calib), he, s, cam->precision);
+    }
     RenderArgs a{};
     a.width = cam->width;
     a.height = cam->height;
@@ -2346,7 +2508,6 @@ int pifu_render(pifu_ctx* ctx, const pifu_camera* cam, const pifu_fmap* occ_map,
             (double)npix * ((depth_dev ? 4 : 0) + (rgb_dev ? 12 : 0) + (mask_dev ? 1 : 0));
         ctx->prof.end(PIFU_K_RENDER, ev, s, 0.0, vol_bytes + out_bytes);
     }
-    unsigned int n = 0;
     st = read_count(ctx, s, &n);
     if (st != PIFU_OK) return st;
     ctx->prof.k[PIFU_K_RENDER].bytes += 16.0 * n;   // the hit list
@@ -2374,6 +2535,9 @@ int pifu_frame(pifu_ctx* ctx, const pifu_fmap* occ_map, const pifu_fmap* col_map
     if (n_fine > kMaxFine) return PIFU_ERR_ARG;
     if (cam->width < 1 || cam->height < 1) return PIFU_ERR_ARG;
     if ((int64_t)cam->width * cam->height > kChunkTC) return PIFU_ERR_CAPACITY;
+    if (cam->final_level != 0 &&
+        (cam->final_level != 1 || cam->width != cam->height || !is_pow2(cam->width)))
+        return PIFU_ERR_ARG;
     if (!prec_valid(lv->precision) || lv->precision == PIFU_PREC_FP32) return PIFU_ERR_UNSUPPORTED;
     if (prec_f8(lv->precision) && !ctx->net[0].f8_ok) return PIFU_ERR_STATE;
     if (prec_mixed(lv->precision) && !(lv->margin >= 0.f && lv->margin <= 0.5f))
@@ -2419,6 +2583,7 @@ int pifu_frame(pifu_ctx* ctx, const pifu_fmap* occ_map, const pifu_fmap* col_map
     k.width = cam->width;
     k.height = cam->height;
     k.cam_precision = cam->precision;
+    k.final_level = cam->final_level;
     for (int c = 0; c < 3; ++c) k.bg[c] = cam->background[c];
     k.depth = depth_dev;
     k.rgb = rgb_dev;
@@ -2427,6 +2592,10 @@ int pifu_frame(pifu_ctx* ctx, const pifu_fmap* occ_map, const pifu_fmap* col_map
     if (st != PIFU_OK) return st;
     st = ensure_hit_ws(ctx, (int64_t)cam->width * cam->height);
     if (st != PIFU_OK) return st;
+    if (cam->final_level) {
+        st = ensure_cull_ws(ctx, (int64_t)cam->width * cam->height, (int)n_fine);
+        if (st != PIFU_OK) return st;
+    }
     if (!ctx->g_valid || std::memcmp(&k, &ctx->gkey, sizeof(k)) != 0) {
         st = g_build(ctx, k, to_map(occ_map), to_map(col_map), to_calib(calib));
         if (st != PIFU_OK) return st;
@@ -2458,12 +2627,16 @@ int pifu_frame(pifu_ctx* ctx, const pifu_fmap* occ_map, const pifu_fmap* col_map
     vs.occ_bits_dev = ctx->bin[cur];
     vs.eval_bits_dev = ctx->eval;
     vs.values_dev = ctx->values;
+    if (cam->final_level && lv->num_levels < kMaxLevels)
+        vs.evals_per_level[lv->num_levels] = (int64_t)gs.culled;   // the culled final level
     if (out) *out = vs;
     if (gs.err) return decode_err(gs.err);
     ctx->stats = vs;
     ctx->have_volume = true;
     ctx->vol_N = (int)n_fine;
     ctx->vol_bin = cur;
+    ctx->vol_prec = lv->precision;
+    ctx->vol_margin = lv->margin;
     return PIFU_OK;
 }
 
@@ -2500,6 +2673,7 @@ int pifu_frames(pifu_ctx* ctx, int B, const pifu_fmap* occ_maps, const pifu_fmap
     const int64_t n_fine = (int64_t)lv->n0 << (lv->num_levels - 1);
     if (n_fine > kMaxFine) return PIFU_ERR_ARG;
     if (cam->width < 1 || cam->height < 1) return PIFU_ERR_ARG;
+    if (cam->final_level) return PIFU_ERR_UNSUPPORTED;   // lockstep batches ray-march the volume
     const int64_t npix = (int64_t)cam->width * cam->height;
     if ((int64_t)B * npix > kTcRowsMax) return PIFU_ERR_CAPACITY;
     if (!prec_valid(lv->precision) || lv->precision == PIFU_PREC_FP32) return PIFU_ERR_UNSUPPORTED;

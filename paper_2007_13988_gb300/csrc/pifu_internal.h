@@ -34,6 +34,8 @@ enum PointMode : int {
     PTS_LIST = 1,    // int32 node indices of a level with N cells per axis
     PTS_DENSE = 2,   // node index = base + point number
     PTS_XYZ_IDX = 3, // positions xyz[list[p]] (a subset of a position array)
+    PTS_COLUMN = 4,  // view-culled final level: key list[p] = pixel (N+1) + k, the point
+                     // at pixel (i, j) of a width x width image and depth node k of N cells
 };
 
 struct PointSrc {
@@ -54,6 +56,7 @@ struct PointSrc {
     const Calib* calibs;
     const int* keys;      // PTS_XYZ
     int64_t slot_div;
+    int width;            // PTS_COLUMN: pixels per image side
 };
 
 // What the last MLP layer does with its output.
@@ -61,6 +64,7 @@ enum EpilogueMode : int {
     EPI_STORE = 0,   // out[p * n_out + c] = act(t)   (p = pix[p] when pix is set)
     EPI_LEVEL = 1,   // scatter occupancy into a level (values, bits, conflicts)
     EPI_PIXELS = 2,  // out[pix[p] * 3 + c] = act(t)
+    EPI_COLUMN = 3,  // out[key] = occupancy, key = list[p] (view-culled final level)
 };
 
 enum OutAct : int { ACT_SIGMOID = 0, ACT_TANH01 = 1 };
@@ -297,5 +301,35 @@ struct RenderArgs {
     int64_t slot_nodes, slot_words;
 };
 cudaError_t launch_render_rays(const RenderArgs& a, cudaStream_t stream);
+
+// View-culled final level (Sec. 3.2): the render's pixel columns at the N_f =
+// 2 N_c depth nodes of the level after the last localized one (N_c cells,
+// binarized bits `bin`).  Per pixel the binarized level is upsampled
+// tri-linearly along the column (tentative T); nodes behind the nearest
+// T = 1 node are shadow nodes; the non-shadow nodes with 0 < T < 1 are the
+// candidates.
+struct CullArgs {
+    int width, height;     // square images only: width == height
+    int Nc, row_words;     // the localized level
+    const uint32_t* bin;
+    int* list;             // candidates' keys pixel (N_f + 1) + k
+    unsigned int* count;   // appended at *count
+    unsigned int cap;      // list capacity: beyond it the error word gets kErrCapacity
+    unsigned int* err;
+    const float* values;   // [width*height][N_f + 1]: the candidates' occupancies
+    float bg[3];
+    float* depth;          // may be null
+    float* rgb;            // may be null
+    uint8_t* mask;         // may be null
+    float* hit_xyz;
+    int* hit_pix;
+    unsigned int* hit_count;
+    int* top;              // [(Nc+1)^2] scratch: highest set depth node per column
+};
+// Candidates of every pixel into list (warp-aggregated).
+cudaError_t launch_cull_select(const CullArgs& a, cudaStream_t stream);
+// Second argmax over T and the evaluated candidates, the crossing, outputs
+// and the hit list for the colour MLP.
+cudaError_t launch_cull_final(const CullArgs& a, cudaStream_t stream);
 
 }  // namespace pifu

@@ -179,3 +179,198 @@ cudaError_t launch_render_rays(const RenderArgs& a, cudaStream_t stream) {
 }
 
 }  // namespace pifu
+
+// ---- view-culled final level (Sec. 3.2) ----------------------------------------
+
+namespace pifu {
+namespace {
+
+// The binarized localized level along one pixel column: the bilinear (x, y)
+// weights of the four node columns around the pixel centre, and the column
+// value at a coarse depth node counted from the observer.  Exact in float for
+// power-of-two sizes (dyadic weights, sums of at most four of them).
+struct CullColumn {
+    const uint32_t* bin;
+    int Nc, rw, ix0, iy0;
+    float w00, w10, w01, w11;
+
+    __device__ __forceinline__ float coarse(int kc) const {
+        const int iz = Nc - kc;
+        const int64_t row0 = (int64_t)iz * (Nc + 1) + iy0;
+        const uint32_t b0 = two_bits(bin + row0 * rw, ix0);
+        const uint32_t b1 = two_bits(bin + (row0 + 1) * rw, ix0);
+        return w00 * (float)(b0 & 1u) + w10 * (float)(b0 >> 1) + w01 * (float)(b1 & 1u) +
+               w11 * (float)(b1 >> 1);
+    }
+};
+
+__device__ __forceinline__ CullColumn cull_column(const CullArgs& a, int i, int j) {
+    CullColumn c;
+    c.bin = a.bin;
+    c.Nc = a.Nc;
+    c.rw = a.row_words;
+    float wx, wy;
+    pixel_node(i, a.width, a.Nc, c.ix0, wx);
+    pixel_node(j, a.height, a.Nc, c.iy0, wy);
+    c.w00 = (1.f - wx) * (1.f - wy);
+    c.w10 = wx * (1.f - wy);
+    c.w01 = (1.f - wx) * wy;
+    c.w11 = wx * wy;
+    return c;
+}
+
+// Walks the fine depth nodes k = 0 .. 2 Nc of a column in order, with the
+// tentative value T_k (coarse node k/2, or the mean of its two neighbours for
+// odd k), stopping after the first T = 1 (the nodes behind it are shadow
+// nodes).  visit(k, T) is called for every non-shadow node.  Returns the
+// number of nodes walked.
+template <typename F>
+__device__ __forceinline__ void walk_column(const CullColumn& c, int kc_start, F&& visit) {
+    float prev = 0.f;   // coarse nodes before kc_start are empty (value 0)
+    for (int kc = kc_start; kc <= c.Nc; ++kc) {
+        const float v = c.coarse(kc);
+        if (kc > 0) {
+            const float t = 0.5f * (prev + v);
+            if (!visit(2 * kc - 1, t)) return;
+        }
+        if (!visit(2 * kc, v)) return;
+        prev = v;
+    }
+}
+
+__device__ __forceinline__ int cull_start(const CullArgs& a, const int* top, const CullColumn& c) {
+    const int n1 = a.Nc + 1;
+    const int64_t c0 = (int64_t)c.iy0 * n1 + c.ix0;
+    const int ktop = max(max(top[c0], top[c0 + 1]), max(top[c0 + n1], top[c0 + n1 + 1]));
+    return ktop < 0 ? -1 : a.Nc - ktop;   // first coarse depth node (from the observer) that may be set
+}
+
+__global__ void __launch_bounds__(256) cull_select_kernel(CullArgs a) {
+    const int* __restrict__ top = a.top;
+    const int64_t npix = (int64_t)a.width * a.height;
+    const int64_t pix = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const int64_t n1f = 2 * (int64_t)a.Nc + 1;
+    int n = 0;
+    CullColumn c{};
+    int ks = -1;
+    if (pix < npix) {
+        c = cull_column(a, (int)(pix % a.width), (int)(pix / a.width));
+        ks = cull_start(a, top, c);
+        if (ks >= 0)
+            walk_column(c, ks, [&](int, float t) {
+                if (t >= 1.f) return false;
+                if (t > 0.f) ++n;
+                return true;
+            });
+    }
+    int incl = n;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+    }
+    const int warp_total = __shfl_sync(0xffffffffu, incl, 31);
+    unsigned int base = 0u;
+    if (lane == 31 && warp_total > 0) base = atomicAdd(a.count, (unsigned int)warp_total);
+    base = __shfl_sync(0xffffffffu, base, 31);
+    if (n) {
+        unsigned int pos = base + (unsigned int)(incl - n);
+        if (pos + (unsigned int)n > a.cap) {
+            atomicOr(a.err, kErrCapacity);   // the list would overflow: drop this column
+            return;
+        }
+        walk_column(c, ks, [&](int k, float t) {
+            if (t >= 1.f) return false;
+            if (t > 0.f) a.list[pos++] = (int)(pix * n1f + k);
+            return true;
+        });
+    }
+}
+
+__global__ void __launch_bounds__(256) cull_final_kernel(CullArgs a) {
+    const int* __restrict__ top = a.top;
+    const int64_t npix = (int64_t)a.width * a.height;
+    const int64_t pix = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const int64_t n1f = 2 * (int64_t)a.Nc + 1;
+    bool hit = false;
+    float zs = 0.f, px = 0.f, py = 0.f;
+    if (pix < npix) {
+        const int i = (int)(pix % a.width);
+        const int j = (int)(pix / a.width);
+        px = __fmaf_rn((float)(2 * i + 1), 1.0f / (float)a.width, -1.0f);
+        py = __fmaf_rn((float)(2 * j + 1), 1.0f / (float)a.height, -1.0f);
+        const CullColumn c = cull_column(a, i, j);
+        const int ks = cull_start(a, top, c);
+        if (ks >= 0) {
+            const float h = 1.0f / (float)a.Nc;   // fine node spacing 2 / (2 Nc)
+            const float* vals = a.values + pix * n1f;
+            float vprev = 0.f;
+            walk_column(c, ks, [&](int k, float t) {
+                const float v = (t > 0.f && t < 1.f) ? vals[k] : t;   // evaluated candidates
+                if (v >= kHalf) {
+                    hit = true;
+                    if (k == 0) {
+                        zs = 1.0f;
+                    } else {
+                        const float u = (kHalf - vprev) / (v - vprev);
+                        const float zprev = __fmaf_rn(-(float)(k - 1), h, 1.0f);
+                        zs = zprev - u * h;
+                    }
+                    return false;
+                }
+                vprev = v;
+                return true;
+            });
+        }
+        if (a.depth) a.depth[pix] = hit ? zs : __int_as_float(0x7fc00000);
+        if (a.mask) a.mask[pix] = hit ? 1 : 0;
+        if (a.rgb && !hit) {
+            a.rgb[pix * 3 + 0] = a.bg[0];
+            a.rgb[pix * 3 + 1] = a.bg[1];
+            a.rgb[pix * 3 + 2] = a.bg[2];
+        }
+    }
+    const unsigned ballot = __ballot_sync(0xffffffffu, hit);
+    if (ballot == 0u) return;
+    unsigned base = 0u;
+    if (lane == 0) base = atomicAdd(a.hit_count, (unsigned)__popc(ballot));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (hit) {
+        const unsigned pos = base + __popc(ballot & ((1u << lane) - 1u));
+        a.hit_xyz[3 * (int64_t)pos + 0] = px;
+        a.hit_xyz[3 * (int64_t)pos + 1] = py;
+        a.hit_xyz[3 * (int64_t)pos + 2] = zs;
+        a.hit_pix[pos] = (int)pix;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_cull_select(const CullArgs& a, cudaStream_t stream) {
+    const int64_t npix = (int64_t)a.width * a.height;
+    if (npix <= 0) return cudaSuccess;
+    if (a.width != a.height || a.Nc < 1 || (2 * (int64_t)a.Nc + 1) * npix > 2147483647LL)
+        return cudaErrorInvalidValue;
+    // highest set depth node of every column of the localized level (bin only)
+    const int64_t n1 = a.Nc + 1;
+    cudaError_t e = cudaMemsetAsync(a.top, 0xff, (size_t)(n1 * n1) * sizeof(int), stream);
+    if (e != cudaSuccess) return e;
+    const int64_t nt = n1 * n1 * a.row_words;
+    column_top_kernel<<<dim3((unsigned)((nt + 255) / 256), 1u), 256, 0, stream>>>(
+        a.Nc, a.row_words, a.bin, a.bin, a.top, 0);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    cull_select_kernel<<<(unsigned)((npix + 255) / 256), 256, 0, stream>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cull_final(const CullArgs& a, cudaStream_t stream) {
+    const int64_t npix = (int64_t)a.width * a.height;
+    if (npix <= 0) return cudaSuccess;
+    cull_final_kernel<<<(unsigned)((npix + 255) / 256), 256, 0, stream>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace pifu

@@ -59,7 +59,8 @@ class pifu_levels(ctypes.Structure):
 
 class pifu_camera(ctypes.Structure):
     _fields_ = [("width", ctypes.c_int32), ("height", ctypes.c_int32),
-                ("background", ctypes.c_float * 3), ("precision", ctypes.c_int32)]
+                ("background", ctypes.c_float * 3), ("precision", ctypes.c_int32),
+                ("final_level", ctypes.c_int32)]
 
 
 class pifu_volume(ctypes.Structure):
@@ -295,8 +296,9 @@ def pifu_localize(ctx, occ_map, calib, n0, num_levels, precision=PIFU_PREC_FP32,
 
 
 def pifu_render(ctx, width, height, occ_map, col_map, calib, depth=None, rgb=None, mask=None,
-                background=(0.0, 0.0, 0.0), precision=PIFU_PREC_FP32, stream=None):
-    cam = pifu_camera(width, height, (ctypes.c_float * 3)(*background), precision)
+                background=(0.0, 0.0, 0.0), precision=PIFU_PREC_FP32, stream=None,
+                final_level=0):
+    cam = pifu_camera(width, height, (ctypes.c_float * 3)(*background), precision, final_level)
     fo = fmap(occ_map)
     fc = fmap(col_map)
     st = _lib().pifu_render(ctx, ctypes.byref(cam), ctypes.byref(fo) if fo else None,
@@ -308,13 +310,14 @@ def pifu_render(ctx, width, height, occ_map, col_map, calib, depth=None, rgb=Non
 def pifu_frame(ctx, occ_map, col_map, calib, n0, num_levels, width, height, depth=None, rgb=None,
                mask=None, precision=PIFU_PREC_MIXED, margin=0.02, max_rounds=0,
                background=(0.0, 0.0, 0.0), stream=None, use_surrogate=False,
-               surrogate_margin=0.0) -> pifu_volume:
+               surrogate_margin=0.0, final_level=0) -> pifu_volume:
     """Localization + render of one frame as a (cached) CUDA graph."""
     fo = fmap(occ_map)
     fc = fmap(col_map)
     lv = pifu_levels(n0, num_levels, precision, max_rounds, margin, int(bool(use_surrogate)),
                      surrogate_margin)
-    cam = pifu_camera(width, height, (ctypes.c_float * 3)(*background), PIFU_PREC_BF16)
+    cam = pifu_camera(width, height, (ctypes.c_float * 3)(*background), PIFU_PREC_BF16,
+                      final_level)
     vol = pifu_volume()
     st = _lib().pifu_frame(ctx, ctypes.byref(fo), ctypes.byref(fc) if fc else None, _calib(calib),
                            ctypes.byref(lv), ctypes.byref(cam), _stream(stream), _ptr(depth),

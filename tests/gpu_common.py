@@ -84,7 +84,7 @@ class Ctx:
         return b, e, v
 
     def render(self, R, calib=None, background=(0.0, 0.0, 0.0), width=None, height=None,
-               precision=0):
+               precision=0, final_level=0):
         t = torch()
         W = R if width is None else width
         H = R if height is None else height
@@ -93,7 +93,8 @@ class Ctx:
         mask = t.empty((H, W), dtype=t.uint8, device="cuda")
         self.pifu.pifu_render(self.ctx, W, H, self.occ, self.col,
                               self.calib if calib is None else calib, depth, rgb, mask,
-                              background=background, precision=precision)
+                              background=background, precision=precision,
+                              final_level=final_level)
         t.cuda.synchronize()
         return (depth.cpu().numpy().astype(np.float64), rgb.cpu().numpy().astype(np.float64),
                 mask.cpu().numpy().astype(bool))
