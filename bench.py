@@ -52,6 +52,8 @@ def parse_args():
     ap.add_argument("--batch", type=int, default=8, help="frames per lockstep batch (stream)")
     ap.add_argument("--stream-subjects", type=int, default=8)
     ap.add_argument("--stream-frames", type=int, default=64)
+    ap.add_argument("--no-culled", action="store_true",
+                    help="skip the paper's view-culled final level render")
     ap.add_argument("--no-512", action="store_true",
                     help="skip the 512^3 precision form (timing and accuracy vs the oracle)")
     ap.add_argument("--form", choices=("graph", "host"), default="graph")
@@ -284,7 +286,7 @@ class Frame:
         # scales of the FP8 form from the frame's own dense coarsest grid
         pifu.pifu_calibrate_fp8(self.ctx, self.occ, w.calib, w.n0, stream=stream)
 
-    def run(self, prec, form="graph", margin=0.02, sur_margin=None, levels=None):
+    def run(self, prec, form="graph", margin=0.02, sur_margin=None, levels=None, final_level=0):
         w, p = self.w, self.pifu
         L = w.num_levels if levels is None else levels
         sur = {} if sur_margin is None else {"use_surrogate": True, "surrogate_margin": sur_margin}
@@ -292,24 +294,26 @@ class Frame:
             # one CUDA graph per frame (captured on the first call)
             return p.pifu_frame(self.ctx, self.occ, self.col, w.calib, w.n0, L,
                                 w.render, w.render, self.depth, self.rgb, self.mask,
-                                precision=prec, margin=margin, stream=self.stream, **sur)
+                                precision=prec, margin=margin, stream=self.stream,
+                                final_level=final_level, **sur)
         vol = p.pifu_localize(self.ctx, self.occ, w.calib, w.n0, L, precision=prec,
                               margin=margin, stream=self.stream, **sur)
         p.pifu_render(self.ctx, w.render, w.render, self.occ, self.col, w.calib, self.depth,
-                      self.rgb, self.mask, precision=1 if prec != 0 else 0, stream=self.stream)
-        return vol
+                      self.rgb, self.mask, precision=1 if prec != 0 else 0, stream=self.stream,
+                      final_level=final_level)
+        return p.pifu_sync_stats(self.ctx) if final_level else vol
 
     def close(self):
         self.pifu.pifu_destroy(self.ctx)
 
 
 def time_form(fr, prec, steps, warmup, world, clocks=None, form="graph", sur_margin=None,
-              levels=None):
+              levels=None, final_level=0):
     """Device-timed frames of one precision form; returns a dict."""
     import torch
     vol = None
     for _ in range(max(1, warmup)):
-        vol = fr.run(prec, form, sur_margin=sur_margin, levels=levels)
+        vol = fr.run(prec, form, sur_margin=sur_margin, levels=levels, final_level=final_level)
     fr.stream.synchronize()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(steps)]
@@ -321,7 +325,7 @@ def time_form(fr, prec, steps, warmup, world, clocks=None, form="graph", sur_mar
         with torch.cuda.stream(fr.stream):
             fr.flush.zero_()
         ev[i][0].record(fr.stream)
-        vol = fr.run(prec, form, sur_margin=sur_margin, levels=levels)
+        vol = fr.run(prec, form, sur_margin=sur_margin, levels=levels, final_level=final_level)
         ev[i][1].record(fr.stream)
     torch.cuda.synchronize()
     prof = fr.pifu.pifu_profile_read(fr.ctx)
@@ -591,6 +595,14 @@ def run_ours(args, rank, world, local_rank):
     if prec != 0 and not args.no_plain:
         plain = time_form(fr, 0, side_steps, 2, world)
         plain_rgb = fr.rgb.cpu().numpy()
+    # ---- the paper's view-culled final level: 512 depth nodes at 512^2 -------
+    culled = None
+    if prec != 0 and not args.no_culled:
+        culled = time_form(fr, prec, args.steps, args.warmup, world, form=form, final_level=1)
+        culled["snap"] = snapshot(fr, culled["vol"])
+        fr_depth_culled = fr.depth.cpu().numpy().astype(np.float64)
+        culled_plain = time_form(fr, 0, 2, 1, world, final_level=1)
+        culled["plain"] = culled_plain
     # ---- the precision form at 512^3 (five levels from 32^3) ----------------
     p512 = {}
     if prec != 0 and not args.no_512:
@@ -765,6 +777,38 @@ def run_ours(args, rank, world, local_rank):
         for name, (r, snap) in others.items():
             line["other_forms"][name]["accuracy"] = accuracy(snap, lv, o_rgb, o_hit,
                                                              plain_rgb if plain else None)
+    if culled is not None:
+        L = w.num_levels
+        cv = culled["vol"]
+        line["culled_final_level"] = {
+            "form": "the paper's view-culled final level (Sec. 3.2): 32^3 -> 256^3 localized, "
+                    "then 513 depth nodes per pixel column of the 512^2 image, shadow nodes "
+                    "culled, ambiguous nodes evaluated, no conflict loop; graph form",
+            "value": culled["value"], "unit": UNIT, "ms_per_step": culled["ms_per_step"],
+            "localized_evals_per_frame": int(sum(cv.evals_per_level[i] for i in range(L))),
+            "culled_level_evals_per_frame": int(cv.evals_per_level[L]),
+            "plain_fp32": {"value": culled["plain"]["value"],
+                           "ms_per_step": culled["plain"]["ms_per_step"]},
+            "speedup_over_plain_fp32": culled["value"] / culled["plain"]["value"]}
+        if world == 1 and not args.no_cpu_baseline:
+            from oracle import field, render as orender
+            f = lambda P: field.occupancy(w.occ_net, w.occ_map, w.calib, P)
+            t0 = time.perf_counter()
+            o_rgb2, o_depth2, o_hit2, res = orender.render_culled(f, lv[-1].binary, w.render,
+                                                                  w.col_net, w.occ_map, w.col_map,
+                                                                  w.calib)
+            sn = culled["snap"]
+            both = sn["mask"] & o_hit2
+            d = sn["rgb"].astype(np.float64)[both] - o_rgb2[both]
+            mse = float(np.mean(d * d)) if d.size else 0.0
+            line["culled_final_level"]["accuracy"] = {
+                "iou_vs_oracle": accuracy(sn, lv, o_rgb, o_hit)["iou_vs_oracle"],
+                "mask_agreement_vs_oracle_culled": float(np.mean(sn["mask"] == o_hit2)),
+                "depth_max_abs_vs_oracle_culled": float(np.nanmax(np.abs(
+                    fr_depth_culled[both] - o_depth2[both]))) if both.any() else None,
+                "colour_psnr_vs_oracle_culled_db": float("inf") if mse == 0 else
+                10 * np.log10(1.0 / mse),
+                "oracle_culled_evals": res["n_eval"], "oracle_s": time.perf_counter() - t0}
     if stream_out is not None:
         line["stream"] = stream_out
     if p512:
