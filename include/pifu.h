@@ -233,7 +233,10 @@ int pifu_frame(pifu_ctx* ctx, const pifu_fmap* occ_map, const pifu_fmap* col_map
  * (frame, node) keys for all frames, so one persistent tensor-core launch per
  * MLP layer serves all B frames.  A level's conflict loop runs while any
  * frame has a frontier (the rounds of the batch are those of its slowest
- * frame).  Each frame's result equals what pifu_frame computes for it alone.
+ * frame).  Each frame's binarized volume and evaluated set equal what
+ * pifu_frame computes for it alone; its values agree to BF16 rounding (a
+ * round of at most 256 points, which the MIXED forms evaluate in FP32
+ * outright, can be tiny in one form and not in the other).
  * The B frames' pipeline is one CUDA graph, captured per argument set: B, the
  * maps' shapes and types, levels, camera and output pointers.  The map
  * pointers and calibrations are read on the device, so consecutive batches

@@ -226,6 +226,15 @@ __global__ void loop_control_kernel(cudaGraphConditionalHandle h, const unsigned
     cudaGraphSetConditional(h, go ? 1u : 0u);
 }
 
+// Graph form: picks one of two conditional branches from a device-resident
+// batch size: hs for 1 .. threshold points, hl above.
+__global__ void branch_kernel(cudaGraphConditionalHandle hs, cudaGraphConditionalHandle hl,
+                              const unsigned int* count, unsigned int threshold) {
+    const unsigned int c = *count;
+    cudaGraphSetConditional(hs, (c > 0u && c <= threshold) ? 1u : 0u);
+    cudaGraphSetConditional(hl, c > threshold ? 1u : 0u);
+}
+
 // *dst += *src, flagging a capacity error when *src exceeds cap.
 __global__ void accumulate_kernel(unsigned long long* dst, const unsigned int* src,
                                   unsigned int cap, unsigned int* err) {
@@ -269,6 +278,12 @@ cudaError_t launch_loop_control(cudaGraphConditionalHandle h, const unsigned int
                                 unsigned int cap, unsigned int* rounds, int count_round,
                                 int max_rounds, unsigned int* err, cudaStream_t stream) {
     loop_control_kernel<<<1, 1, 0, stream>>>(h, count, cap, rounds, count_round, max_rounds, err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_branch(cudaGraphConditionalHandle hs, cudaGraphConditionalHandle hl,
+                          const unsigned int* count, unsigned int threshold, cudaStream_t stream) {
+    branch_kernel<<<1, 1, 0, stream>>>(hs, hl, count, threshold);
     return cudaGetLastError();
 }
 

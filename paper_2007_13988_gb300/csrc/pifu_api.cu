@@ -338,6 +338,7 @@ struct pifu_ctx {
     cudaGraphExec_t gexec = nullptr;
     cudaStream_t cap_stream = nullptr;    // capture of the frame
     cudaStream_t cap_stream2 = nullptr;   // capture of the loop bodies
+    cudaStream_t cap_stream3 = nullptr;   // capture of conditional branches
     GraphStats* d_gstats = nullptr;
     GraphStats* h_gstats = nullptr;       // pinned
     int64_t g_launches_fixed = 0;         // kernel launches outside the loops
@@ -1363,6 +1364,9 @@ void sur_unpack(const pifu_ctx* ctx, const float* in, std::vector<float>& padded
 // condition from the new frontier's size.  The host synchronises once, at the
 // end of the frame, to read the counters and the error word.
 
+int g_add_cond(pifu_ctx* ctx, cudaStream_t s, cudaGraphConditionalHandle h,
+               cudaGraphConditionalNodeType type, cudaGraph_t* body);
+
 // One evaluation batch in the graph: BF16 on the tensor cores, and for MIXED
 // the FP32 re-evaluation of the queued near-0.5 occupancies (device-sized).
 // With `sur`, f_S runs first and f_O takes the occupancies f_S put within
@@ -1394,6 +1398,35 @@ int g_eval(pifu_ctx* ctx, const DevNet& net, const PointSrc& src, int64_t cap,
     if (prec == PIFU_PREC_BF16 || prec == PIFU_PREC_FP8)
         return run_mlp_tc(ctx, net, src, cap, map, Map{}, cal, epi, s, m_dev,
                           prec == PIFU_PREC_FP8);
+    if (m_dev && ctx->cap_stream3 && s != ctx->cap_stream3) {
+        // A device-sized batch of at most kTinyBatch points goes straight to
+        // FP32 (one fused launch), as in the host-driven form; the tensor-core
+        // pass and its re-check run above that.  Two IF nodes, set on the device.
+        cudaStreamCaptureStatus cs;
+        cudaGraph_t cg = nullptr;
+        CK(cudaStreamGetCaptureInfo(s, &cs, nullptr, &cg, nullptr, nullptr, nullptr));
+        cudaGraphConditionalHandle hs, hl;
+        CK(cudaGraphConditionalHandleCreate(&hs, cg, 0, 0));
+        CK(cudaGraphConditionalHandleCreate(&hl, cg, 0, 0));
+        CK(launch_branch(hs, hl, m_dev, (unsigned)kTinyBatch, s));
+        cudaStream_t s3 = ctx->cap_stream3;
+        for (int br = 0; br < 2; ++br) {
+            cudaGraph_t body = nullptr;
+            int st = g_add_cond(ctx, s, br == 0 ? hs : hl, cudaGraphCondTypeIf, &body);
+            if (st != PIFU_OK) return st;
+            CK(cudaStreamBeginCaptureToGraph(s3, body, nullptr, nullptr, 0,
+                                             cudaStreamCaptureModeThreadLocal));
+            if (br == 0)
+                st = run_mlp(ctx, net, src, cap, map, Map{}, cal, epi, s3, PIFU_PREC_FP32, m_dev);
+            else
+                st = g_eval(ctx, net, src, cap, m_dev, map, cal, epi, prec, margin, rechecked, s3);
+            cudaGraph_t out = nullptr;
+            const cudaError_t ee = cudaStreamEndCapture(s3, &out);
+            if (st != PIFU_OK) return st;
+            if (ee != cudaSuccess) return fail_cuda(ctx, ee);
+        }
+        return PIFU_OK;
+    }
     CK(cudaMemsetAsync(ctx->d_recheck, 0, sizeof(unsigned int), s));
     Epilogue e1 = epi;
     e1.recheck = ctx->recheck;
@@ -1421,7 +1454,17 @@ int g_eval(pifu_ctx* ctx, const DevNet& net, const PointSrc& src, int64_t cap,
 // Appends a WHILE node to the capture of `s` (after everything captured so
 // far) and returns its body graph; the condition is set by the kernel that
 // was captured last (launch_loop_control).
+int g_add_cond(pifu_ctx* ctx, cudaStream_t s, cudaGraphConditionalHandle h,
+               cudaGraphConditionalNodeType type, cudaGraph_t* body);
+
 int g_add_while(pifu_ctx* ctx, cudaStream_t s, cudaGraphConditionalHandle h, cudaGraph_t* body) {
+    return g_add_cond(ctx, s, h, cudaGraphCondTypeWhile, body);
+}
+
+// Appends a conditional node of `type` to the capture of `s` (after
+// everything captured so far) and returns its body graph.
+int g_add_cond(pifu_ctx* ctx, cudaStream_t s, cudaGraphConditionalHandle h,
+               cudaGraphConditionalNodeType type, cudaGraph_t* body) {
     cudaStreamCaptureStatus cs;
     cudaGraph_t cg = nullptr;
     const cudaGraphNode_t* deps = nullptr;
@@ -1432,7 +1475,7 @@ int g_add_while(pifu_ctx* ctx, cudaStream_t s, cudaGraphConditionalHandle h, cud
     cudaGraphNodeParams np{};
     np.type = cudaGraphNodeTypeConditional;
     np.conditional.handle = h;
-    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.type = type;
     np.conditional.size = 1;
     cudaGraphNode_t node;
     CK(cudaGraphAddNode(&node, cg, deps, edata, ndeps, &np));
@@ -1631,6 +1674,7 @@ int g_build(pifu_ctx* ctx, const FrameKey& k, const Map& occ, const Map& col, co
     g_destroy(ctx);
     if (!ctx->cap_stream) CK(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
     if (!ctx->cap_stream2) CK(cudaStreamCreateWithFlags(&ctx->cap_stream2, cudaStreamNonBlocking));
+    if (!ctx->cap_stream3) CK(cudaStreamCreateWithFlags(&ctx->cap_stream3, cudaStreamNonBlocking));
     if (!ctx->d_gstats) CK(dev_alloc(&ctx->d_gstats, 1));
     if (!ctx->h_gstats) CK(cudaHostAlloc(&ctx->h_gstats, sizeof(GraphStats), cudaHostAllocDefault));
     CK(tc_prepare());
@@ -1896,6 +1940,7 @@ int b_build(pifu_ctx* ctx, const BatchKey& k) {
     bw.g_valid = false;
     if (!ctx->cap_stream) CK(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
     if (!ctx->cap_stream2) CK(cudaStreamCreateWithFlags(&ctx->cap_stream2, cudaStreamNonBlocking));
+    if (!ctx->cap_stream3) CK(cudaStreamCreateWithFlags(&ctx->cap_stream3, cudaStreamNonBlocking));
     CK(tc_prepare());
     {
         const int st = ensure_tc_rows(ctx, std::max<int64_t>(bw.cap, (int64_t)k.B * k.width * k.height));
@@ -2190,6 +2235,7 @@ void pifu_destroy(pifu_ctx* ctx) {
     if (ctx->h_squeue) cudaFreeHost(ctx->h_squeue);
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     if (ctx->cap_stream2) cudaStreamDestroy(ctx->cap_stream2);
+    if (ctx->cap_stream3) cudaStreamDestroy(ctx->cap_stream3);
     dev_free(ctx->d_gstats);
     if (ctx->h_gstats) cudaFreeHost(ctx->h_gstats);
     if (ctx->h_count) cudaFreeHost(ctx->h_count);

@@ -249,6 +249,9 @@ cudaError_t launch_dilate_select(const uint32_t* src, uint32_t* eval, uint32_t* 
 cudaError_t launch_loop_control(cudaGraphConditionalHandle h, const unsigned int* count,
                                 unsigned int cap, unsigned int* rounds, int count_round,
                                 int max_rounds, unsigned int* err, cudaStream_t stream);
+// Graph form: set hs for 1 .. threshold points in *count, hl above.
+cudaError_t launch_branch(cudaGraphConditionalHandle hs, cudaGraphConditionalHandle hl,
+                          const unsigned int* count, unsigned int threshold, cudaStream_t stream);
 // *dst += *src; capacity error bit if *src > cap.
 cudaError_t launch_accumulate(unsigned long long* dst, const unsigned int* src, unsigned int cap,
                               unsigned int* err, cudaStream_t stream);
