@@ -44,6 +44,7 @@ __device__ __forceinline__ void last_epilogue(const Epilogue& epi, int64_t p, in
         // binarized prediction differs from the binarized interpolation.
         const float o = apply_act(ACT_SIGMOID, t[0] + bias[0]);
         int64_t idx = epi.list ? (int64_t)epi.list[p] : epi.base + p;
+        const int key = (int)idx;
         const LevelBits& lv = epi.lv;
         float* values = lv.values;
         const uint32_t* tent = lv.tent;
@@ -72,6 +73,11 @@ __device__ __forceinline__ void last_epilogue(const Epilogue& epi, int64_t p, in
                 atomicOr(&conf[w], bit);
                 if (ob) atomicOr(&bin[w], bit);
                 else atomicAnd(&bin[w], ~bit);
+                if (lv.clist) {
+                    const unsigned int pos = atomicAdd(lv.ccount, 1u);
+                    if (pos < lv.ccap) lv.clist[pos] = key;
+                    else atomicOr(lv.err, kErrCapacity);
+                }
             }
         }
     }

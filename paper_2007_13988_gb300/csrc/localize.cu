@@ -226,6 +226,62 @@ __global__ void loop_control_kernel(cudaGraphConditionalHandle h, const unsigned
     cudaGraphSetConditional(h, go ? 1u : 0u);
 }
 
+// One thread per (conflict, neighbour) pair; warp-aggregated append.
+__global__ void __launch_bounds__(256) expand_conflicts_kernel(
+    const int* __restrict__ clist, const unsigned int* __restrict__ ccount, unsigned int max_c,
+    int N, uint32_t* __restrict__ eval, int64_t key_div, int64_t slot_words,
+    int* __restrict__ list, unsigned int* __restrict__ count, unsigned int cap,
+    unsigned int* __restrict__ err) {
+    const unsigned int nc = min(*ccount, max_c);
+    const int n1 = N + 1;
+    const int rw = row_words_of(N);
+    const int lane = threadIdx.x & 31;
+    const int64_t total = (int64_t)nc * 26;
+    // whole warps iterate together (ballots below)
+    for (int64_t base_t = (int64_t)blockIdx.x * blockDim.x; base_t < total;
+         base_t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t t = base_t + threadIdx.x;
+        bool fresh = false;
+        int64_t nkey = 0;
+        if (t < total) {
+            const int64_t c = t / 26;
+            int nb = (int)(t - c * 26);
+            nb += nb >= 13 ? 1 : 0;                // skip the centre of the 3x3x3 block
+            const int dx = nb % 3 - 1, dy = (nb / 3) % 3 - 1, dz = nb / 9 - 1;
+            int64_t key = clist[c];
+            int64_t f = 0;
+            if (key_div) {
+                f = key / key_div;
+                key -= f * key_div;
+            }
+            const int64_t row = key / n1;           // k (N+1) + j
+            const int i = (int)(key - row * n1) + dx;
+            const int j = (int)(row % n1) + dy;
+            const int k = (int)(row / n1) + dz;
+            if (i >= 0 && i <= N && j >= 0 && j <= N && k >= 0 && k <= N) {
+                const int64_t r2 = (int64_t)k * n1 + j;
+                uint32_t* wptr = eval + f * slot_words + r2 * rw + (i >> 5);
+                const uint32_t bit = 1u << (i & 31);
+                if (!(*wptr & bit)) {
+                    const uint32_t old = atomicOr(wptr, bit);
+                    fresh = !(old & bit);
+                }
+                nkey = f * (key_div ? key_div : 0) + r2 * n1 + i;
+            }
+        }
+        const unsigned ballot = __ballot_sync(0xffffffffu, fresh);
+        if (ballot == 0u) continue;
+        unsigned int b = 0u;
+        if (lane == 0) b = atomicAdd(count, (unsigned int)__popc(ballot));
+        b = __shfl_sync(0xffffffffu, b, 0);
+        if (fresh) {
+            const unsigned int pos = b + __popc(ballot & ((1u << lane) - 1u));
+            if (pos < cap) list[pos] = (int)nkey;
+            else atomicOr(err, kErrCapacity);
+        }
+    }
+}
+
 // Graph form: picks one of two conditional branches from a device-resident
 // batch size: hs for 1 .. threshold points, hl above.
 __global__ void branch_kernel(cudaGraphConditionalHandle hs, cudaGraphConditionalHandle hl,
@@ -278,6 +334,18 @@ cudaError_t launch_loop_control(cudaGraphConditionalHandle h, const unsigned int
                                 unsigned int cap, unsigned int* rounds, int count_round,
                                 int max_rounds, unsigned int* err, cudaStream_t stream) {
     loop_control_kernel<<<1, 1, 0, stream>>>(h, count, cap, rounds, count_round, max_rounds, err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_expand_conflicts(const int* clist, const unsigned int* ccount,
+                                    unsigned int max_c, int N, uint32_t* eval, int64_t key_div,
+                                    int64_t slot_words, int* list, unsigned int* count,
+                                    unsigned int cap, unsigned int* err, cudaStream_t stream) {
+    if (max_c == 0) return cudaSuccess;
+    const int64_t total = (int64_t)max_c * 26;
+    const int64_t blocks = std::min<int64_t>((total + 255) / 256, 152 * 8);
+    expand_conflicts_kernel<<<(unsigned)blocks, 256, 0, stream>>>(
+        clist, ccount, max_c, N, eval, key_div, slot_words, list, count, cap, err);
     return cudaGetLastError();
 }
 

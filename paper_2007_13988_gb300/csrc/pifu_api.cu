@@ -339,6 +339,9 @@ struct pifu_ctx {
     cudaStream_t cap_stream = nullptr;    // capture of the frame
     cudaStream_t cap_stream2 = nullptr;   // capture of the loop bodies
     cudaStream_t cap_stream3 = nullptr;   // capture of conditional branches
+    int* clist = nullptr;                 // graph form: conflicts of a round (keys)
+    unsigned int* d_ccount = nullptr;
+    int64_t clist_cap = 0;
     GraphStats* d_gstats = nullptr;
     GraphStats* h_gstats = nullptr;       // pinned
     int64_t g_launches_fixed = 0;         // kernel launches outside the loops
@@ -1103,6 +1106,18 @@ int eval_batch(pifu_ctx* ctx, const PointSrc& src, int64_t n, const Map& map, co
     return run_mlp(ctx, fo, src, n, map, Map{}, cal, epi, s, prec);
 }
 
+// Conflict list of the graph forms' rounds (keys), at least `cap` entries.
+int ensure_clist(pifu_ctx* ctx, int64_t cap) {
+    if (!ctx->d_ccount) CK(dev_alloc(&ctx->d_ccount, 1));
+    if (cap > ctx->clist_cap) {
+        dev_free(ctx->clist);
+        ctx->clist_cap = 0;
+        CK(dev_alloc(&ctx->clist, cap));
+        ctx->clist_cap = cap;
+    }
+    return PIFU_OK;
+}
+
 int decode_err(unsigned int e) {
     if (e & kErrCapacity) return PIFU_ERR_CAPACITY;
     if (e & kErrNotConverged) return PIFU_ERR_NOT_CONVERGED;
@@ -1544,8 +1559,17 @@ int g_enqueue_frame(pifu_ctx* ctx, const FrameKey& k, const Map& occ, const Map&
             epi.mode = EPI_LEVEL;
             epi.list = ctx->list;
             epi.lv = LevelBits{ctx->values, ctx->tent, ctx->bin[cur], ctx->conf[0], N, rw, 0};
+            // the round's conflicts as a list: the next frontier is their
+            // unevaluated 26-neighbours, found in work proportional to them
+            epi.lv.clist = ctx->clist;
+            epi.lv.ccount = ctx->d_ccount;
+            epi.lv.ccap = (unsigned)ctx->clist_cap;
+            epi.lv.err = err;
             st = launch_accumulate(&gs->evals[l], ctx->d_count, (unsigned)kChunkTC, err, sb) == cudaSuccess
                      ? PIFU_OK : PIFU_ERR_CUDA;
+            if (st == PIFU_OK &&
+                cudaMemsetAsync(ctx->d_ccount, 0, sizeof(unsigned int), sb) != cudaSuccess)
+                st = PIFU_ERR_CUDA;
             if (st == PIFU_OK)
                 st = g_eval(ctx, net, src, kChunkTC, ctx->d_count, occ, cal, epi, k.precision,
                             k.margin, &gs->rechecked[l], sb,
@@ -1553,11 +1577,10 @@ int g_enqueue_frame(pifu_ctx* ctx, const FrameKey& k, const Map& occ, const Map&
                             &gs->fallback[l]);
             if (st == PIFU_OK && cudaMemsetAsync(ctx->d_count, 0, sizeof(unsigned int), sb) != cudaSuccess)
                 st = PIFU_ERR_CUDA;
-            if (st == PIFU_OK && launch_dilate_select(ctx->conf[0], ctx->eval, nullptr, N, ctx->list,
-                                                      ctx->d_count, sb) != cudaSuccess)
-                st = PIFU_ERR_CUDA;
             if (st == PIFU_OK &&
-                cudaMemsetAsync(ctx->conf[0], 0, (size_t)words_of(N) * 4, sb) != cudaSuccess)
+                launch_expand_conflicts(ctx->clist, ctx->d_ccount, (unsigned)kChunkTC, N, ctx->eval,
+                                        0, 0, ctx->list, ctx->d_count, (unsigned)kChunkTC, err,
+                                        sb) != cudaSuccess)
                 st = PIFU_ERR_CUDA;
             if (st == PIFU_OK && launch_loop_control(h, ctx->d_count, (unsigned)kChunkTC,
                                                      &gs->rounds[l], 1, k.max_rounds, err,
@@ -1676,6 +1699,10 @@ int g_build(pifu_ctx* ctx, const FrameKey& k, const Map& occ, const Map& col, co
     if (!ctx->cap_stream2) CK(cudaStreamCreateWithFlags(&ctx->cap_stream2, cudaStreamNonBlocking));
     if (!ctx->cap_stream3) CK(cudaStreamCreateWithFlags(&ctx->cap_stream3, cudaStreamNonBlocking));
     if (!ctx->d_gstats) CK(dev_alloc(&ctx->d_gstats, 1));
+    {
+        const int st = ensure_clist(ctx, kChunkTC);
+        if (st != PIFU_OK) return st;
+    }
     if (!ctx->h_gstats) CK(cudaHostAlloc(&ctx->h_gstats, sizeof(GraphStats), cudaHostAllocDefault));
     CK(tc_prepare());
     {
@@ -1858,19 +1885,25 @@ int g_enqueue_batch(pifu_ctx* ctx, const BatchKey& k) {
             epi.mode = EPI_LEVEL;
             epi.list = bw.list;
             epi.lv = LevelBits{bw.values, bw.tent, bw.bin[cur], bw.conf, N, rw, 0, sn, sn, fs};
+            epi.lv.clist = ctx->clist;
+            epi.lv.ccount = ctx->d_ccount;
+            epi.lv.ccap = (unsigned)ctx->clist_cap;
+            epi.lv.err = err;
             st = launch_accumulate(&gs->keys[l], ctx->d_count, (unsigned)cap, err, sb) == cudaSuccess
                      ? PIFU_OK : PIFU_ERR_CUDA;
+            if (st == PIFU_OK &&
+                cudaMemsetAsync(ctx->d_ccount, 0, sizeof(unsigned int), sb) != cudaSuccess)
+                st = PIFU_ERR_CUDA;
             if (st == PIFU_OK)
                 st = g_eval(ctx, net, src, cap, ctx->d_count, Map{}, Calib{}, epi, k.precision,
                             k.margin, &gs->rechecked[l], sb, sur && l < k.num_levels - 1,
                             k.sur_margin, &gs->fallback[l]);
             if (st == PIFU_OK && cudaMemsetAsync(ctx->d_count, 0, sizeof(unsigned int), sb) != cudaSuccess)
                 st = PIFU_ERR_CUDA;
-            if (st == PIFU_OK && launch_dilate_select(bw.conf, bw.eval, nullptr, N, bw.list,
-                                                      ctx->d_count, sb, B, fs, sn) != cudaSuccess)
-                st = PIFU_ERR_CUDA;
             if (st == PIFU_OK &&
-                cudaMemsetAsync(bw.conf, 0, (size_t)(fs * B) * 4, sb) != cudaSuccess)
+                launch_expand_conflicts(ctx->clist, ctx->d_ccount, (unsigned)cap, N, bw.eval, sn,
+                                        fs, bw.list, ctx->d_count, (unsigned)cap, err,
+                                        sb) != cudaSuccess)
                 st = PIFU_ERR_CUDA;
             if (st == PIFU_OK && launch_loop_control(h, ctx->d_count, (unsigned)cap,
                                                      &gs->rounds[l], 1, k.max_rounds, err,
@@ -1941,6 +1974,10 @@ int b_build(pifu_ctx* ctx, const BatchKey& k) {
     if (!ctx->cap_stream) CK(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
     if (!ctx->cap_stream2) CK(cudaStreamCreateWithFlags(&ctx->cap_stream2, cudaStreamNonBlocking));
     if (!ctx->cap_stream3) CK(cudaStreamCreateWithFlags(&ctx->cap_stream3, cudaStreamNonBlocking));
+    {
+        const int st = ensure_clist(ctx, bw.cap);
+        if (st != PIFU_OK) return st;
+    }
     CK(tc_prepare());
     {
         const int st = ensure_tc_rows(ctx, std::max<int64_t>(bw.cap, (int64_t)k.B * k.width * k.height));
@@ -2236,6 +2273,8 @@ void pifu_destroy(pifu_ctx* ctx) {
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     if (ctx->cap_stream2) cudaStreamDestroy(ctx->cap_stream2);
     if (ctx->cap_stream3) cudaStreamDestroy(ctx->cap_stream3);
+    dev_free(ctx->clist);
+    dev_free(ctx->d_ccount);
     dev_free(ctx->d_gstats);
     if (ctx->h_gstats) cudaFreeHost(ctx->h_gstats);
     if (ctx->h_count) cudaFreeHost(ctx->h_count);

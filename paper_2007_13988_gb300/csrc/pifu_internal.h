@@ -83,6 +83,12 @@ struct LevelBits {
     int64_t key_div;        // 0: one frame
     int64_t slot_nodes;
     int64_t slot_words;
+    // Optional: the keys of the conflicts found are also appended here (the
+    // sparse expansion of the next conflict round reads them).
+    int* clist;
+    unsigned int* ccount;
+    unsigned int ccap;      // beyond it the error word gets kErrCapacity
+    unsigned int* err;
 };
 
 struct Epilogue {
@@ -249,6 +255,17 @@ cudaError_t launch_dilate_select(const uint32_t* src, uint32_t* eval, uint32_t* 
 cudaError_t launch_loop_control(cudaGraphConditionalHandle h, const unsigned int* count,
                                 unsigned int cap, unsigned int* rounds, int count_round,
                                 int max_rounds, unsigned int* err, cudaStream_t stream);
+// Sparse conflict expansion (Sec. 3.2's conflict rounds): for every key in
+// clist[0 .. *ccount) (frame * key_div + node of an N-cell level), every
+// 26-neighbour inside the grid whose evaluated bit was clear gets it set and
+// is appended to list at *count (at most cap; beyond it kErrCapacity).  The
+// same set as dilate26(conflicts) & ~evaluated, in work proportional to the
+// conflicts.  Launched for up to max_c conflicts (a device-resident count).
+cudaError_t launch_expand_conflicts(const int* clist, const unsigned int* ccount,
+                                    unsigned int max_c, int N, uint32_t* eval, int64_t key_div,
+                                    int64_t slot_words, int* list, unsigned int* count,
+                                    unsigned int cap, unsigned int* err, cudaStream_t stream);
+
 // Graph form: set hs for 1 .. threshold points in *count, hl above.
 cudaError_t launch_branch(cudaGraphConditionalHandle hs, cudaGraphConditionalHandle hl,
                           const unsigned int* count, unsigned int threshold, cudaStream_t stream);
