@@ -100,7 +100,6 @@ __global__ void __launch_bounds__(kThreads, 1) tc_linear_kernel(
     const float* __restrict__ colscale, float out_scale) {
     static_assert(!(FUSE && MODE != TC_BF16), "the fused last layer reads BF16 activations");
     constexpr int TBKE = MODE == TC_BF16 ? TBK : 2 * TBK;   // elements per 128-byte K-block
-    if (m_dev) M = min(M, (int)*m_dev);   // device-resident row count
     constexpr uint32_t A_BYTES = TBM * TBK * 2;
     constexpr uint32_t B_BYTES = BN * TBK * 2;
     constexpr uint32_t TMEM_COLS = 2 * BN;   // two accumulators; 128, 256 or 512
@@ -123,8 +122,9 @@ __global__ void __launch_bounds__(kThreads, 1) tc_linear_kernel(
     const int lane = threadIdx.x & 31;
     const int nk = nk1 + nk2;
     const int n_tn = N / BN;
-    const int n_tiles = ((M + TBM - 1) / TBM) * n_tn;
 
+    // Prologue: everything here depends only on the weights, so with a
+    // programmatic dependent launch it overlaps the previous kernel's tail.
     if (threadIdx.x == 0) {
         for (int s = 0; s < TSTAGES; ++s) {
             mbar_init(&full[s], 1);
@@ -153,6 +153,10 @@ __global__ void __launch_bounds__(kThreads, 1) tc_linear_kernel(
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tslot;
+    // the activations and the device-resident row count come from earlier kernels
+    griddep_wait();
+    if (m_dev) M = min(M, (int)*m_dev);
+    const int n_tiles = ((M + TBM - 1) / TBM) * n_tn;
 
     bool ok = true;
     if (warp == 0) {
@@ -409,25 +413,35 @@ cudaError_t launch_bn(const TcLayerArgs& a, cudaStream_t s) {
     const int grid = (int)(tiles < sms ? tiles : sms);
     const uint32_t smem = tc_smem_bytes(BN);
     if (a.mode != TC_BF16 && (a.fuse || !a.colscale)) return cudaErrorInvalidValue;
+    // programmatic dependent launch: the prologue overlaps the previous kernel
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    const float* noscale = nullptr;
     if (a.fuse) {
         if (a.N != BN || a.fuse->n_out < 1 || a.fuse->n_out > 4) return cudaErrorInvalidValue;
-        tc_linear_kernel<BN, true, TC_BF16><<<grid, kThreads, smem, s>>>(
-            *a.tmA1, *a.tmA2, *a.tmW, a.nk1, a.nk2, a.M, a.N, a.bias, a.slope, a.out, a.ldo,
-            a.err, a.m_dev, *a.fuse, nullptr, 1.f);
-    } else if (a.mode == TC_E4M3_E4M3) {
-        tc_linear_kernel<BN, false, TC_E4M3_E4M3><<<grid, kThreads, smem, s>>>(
-            *a.tmA1, *a.tmA2, *a.tmW, a.nk1, a.nk2, a.M, a.N, a.bias, a.slope, a.out, a.ldo,
-            a.err, a.m_dev, FuseLast{}, a.colscale, a.out_scale);
-    } else if (a.mode == TC_E4M3_BF16) {
-        tc_linear_kernel<BN, false, TC_E4M3_BF16><<<grid, kThreads, smem, s>>>(
-            *a.tmA1, *a.tmA2, *a.tmW, a.nk1, a.nk2, a.M, a.N, a.bias, a.slope, a.out, a.ldo,
-            a.err, a.m_dev, FuseLast{}, a.colscale, 1.f);
-    } else {
-        tc_linear_kernel<BN, false, TC_BF16><<<grid, kThreads, smem, s>>>(
-            *a.tmA1, *a.tmA2, *a.tmW, a.nk1, a.nk2, a.M, a.N, a.bias, a.slope, a.out, a.ldo,
-            a.err, a.m_dev, FuseLast{}, nullptr, 1.f);
+        return cudaLaunchKernelEx(&cfg, tc_linear_kernel<BN, true, TC_BF16>, *a.tmA1, *a.tmA2,
+                                  *a.tmW, a.nk1, a.nk2, a.M, a.N, a.bias, a.slope, a.out, a.ldo,
+                                  a.err, a.m_dev, *a.fuse, noscale, 1.f);
     }
-    return cudaGetLastError();
+    if (a.mode == TC_E4M3_E4M3)
+        return cudaLaunchKernelEx(&cfg, tc_linear_kernel<BN, false, TC_E4M3_E4M3>, *a.tmA1,
+                                  *a.tmA2, *a.tmW, a.nk1, a.nk2, a.M, a.N, a.bias, a.slope, a.out,
+                                  a.ldo, a.err, a.m_dev, FuseLast{}, a.colscale, a.out_scale);
+    if (a.mode == TC_E4M3_BF16)
+        return cudaLaunchKernelEx(&cfg, tc_linear_kernel<BN, false, TC_E4M3_BF16>, *a.tmA1,
+                                  *a.tmA2, *a.tmW, a.nk1, a.nk2, a.M, a.N, a.bias, a.slope, a.out,
+                                  a.ldo, a.err, a.m_dev, FuseLast{}, a.colscale, 1.f);
+    return cudaLaunchKernelEx(&cfg, tc_linear_kernel<BN, false, TC_BF16>, *a.tmA1, *a.tmA2,
+                              *a.tmW, a.nk1, a.nk2, a.M, a.N, a.bias, a.slope, a.out, a.ldo,
+                              a.err, a.m_dev, FuseLast{}, noscale, 1.f);
 }
 
 }  // namespace

@@ -52,6 +52,15 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32
     return false;
 }
 
+// ---- programmatic dependent launch ---------------------------------------------
+
+// Wait until the grid this one depends on (launched before it with
+// programmatic stream serialization) has completed and its writes are
+// visible; returns at once when there is no such dependency.
+__device__ __forceinline__ void griddep_wait() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
 // ---- TMA ----------------------------------------------------------------------
 
 // 2-D tiled bulk tensor load into shared memory, completion counted in bytes
