@@ -81,3 +81,49 @@ def adam_step(w, g, m, v, t, lr, b1=0.9, b2=0.999, eps=1e-8):
     mh = m / (1 - b1 ** t)
     vh = v / (1 - b2 ** t)
     return w - lr * mh / (np.sqrt(vh) + eps), m, v
+
+
+# ---- point OHEM (Sec. 3.3, Eq. 6) ----------------------------------------------
+#
+# Each training point m carries the inverse of its sampling probability,
+#     P^-1_pt(m) = 1 / (exp(-L_BCE(m) / alpha_p) + beta_p),
+# recomputed from its binary cross-entropy whenever it is in a mini-batch and
+# used, after normalisation, as the probability of drawing it again.  The
+# draws use uniforms from splitmix64 (Steele, Lea and Flood; the constants of
+# the published generator), one 64-bit output per (seed, step, draw) counter,
+# and inverse-CDF search on the float64 prefix sums of the weights.
+
+MASK64 = (1 << 64) - 1
+
+
+def ohem_inverse_probability(loss, alpha=0.7, beta=0.0):
+    """Eq. 6 for points."""
+    loss = np.asarray(loss, F64)
+    return 1.0 / (np.exp(-loss / alpha) + beta)
+
+
+def splitmix64_next(state):
+    """One step of splitmix64: (new state, output)."""
+    state = (state + 0x9E3779B97F4A7C15) & MASK64
+    z = state
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & MASK64
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & MASK64
+    return state, z ^ (z >> 31)
+
+
+def draw_uniform(seed, step, i):
+    """Uniform in [0, 1) for draw i of step `step`: the first splitmix64 output
+    from the state seed ^ (step << 32) ^ i, top 53 bits."""
+    state = (seed ^ ((step & 0xFFFFFFFF) << 32) ^ i) & MASK64
+    _, z = splitmix64_next(state)
+    return (z >> 11) * (1.0 / 9007199254740992.0)
+
+
+def ohem_sample(weights, seed, step, B):
+    """B indices drawn with probability proportional to weights."""
+    w = np.asarray(weights, F64)
+    cdf = np.cumsum(w)
+    total = cdf[-1]
+    u = np.array([draw_uniform(seed, step, i) for i in range(B)]) * total
+    idx = np.searchsorted(cdf, u, side="right")
+    return np.minimum(idx, len(w) - 1)

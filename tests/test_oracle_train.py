@@ -59,3 +59,29 @@ def test_adam_first_steps_by_hand():
     # Step 2 with the same gradient: m_hat = g, v_hat = g^2 again.
     w2, _, _ = train.adam_step(w, np.array([0.5, -4.0]), m, v, 2, lr=0.1)
     np.testing.assert_allclose(w2, [1.0 - 0.2, -2.0 + 0.2], atol=1e-7)
+
+
+def test_ohem_eq6_closed_forms():
+    # beta = 0: the inverse probability is exp(L / alpha); L = 0 gives 1 / (1 + beta)
+    L = np.array([0.0, 0.35, 0.7, 1.4])
+    np.testing.assert_allclose(train.ohem_inverse_probability(L, 0.7, 0.0), np.exp(L / 0.7),
+                               rtol=1e-15)
+    assert abs(train.ohem_inverse_probability([0.0], 0.7, 10.0)[0] - 1.0 / 11.0) < 1e-16
+    # harder points (larger loss) are drawn more often
+    assert np.all(np.diff(train.ohem_inverse_probability(L, 0.7, 0.0)) > 0)
+
+
+def test_splitmix64_published_outputs():
+    # the generator's first outputs from state 0 (published reference values)
+    s, z = train.splitmix64_next(0)
+    assert z == 0xE220A8397B1DCDAF
+    s, z = train.splitmix64_next(s)
+    assert z == 0x6E789E6AA1B965F4
+
+
+def test_ohem_sampling_frequencies():
+    w = np.array([1.0, 2.0, 7.0, 0.0, 10.0])
+    idx = train.ohem_sample(w, seed=3, step=5, B=20000)
+    freq = np.bincount(idx, minlength=len(w)) / len(idx)
+    np.testing.assert_allclose(freq, w / w.sum(), atol=0.015)
+    assert freq[3] == 0.0
