@@ -329,6 +329,28 @@ int pifu_surrogate_grad(pifu_ctx* ctx, const float* x_dev, const float* y_dev, i
 int pifu_surrogate_train(pifu_ctx* ctx, const float* x_dev, const float* y_dev, int64_t m,
                          int batch, int steps, float lr, double* loss_host, void* stream);
 
+/* Point OHEM (Sec. 3.3, Eq. 6) for f_S's training tuples: every tuple m
+ * carries w_m = 1 / (exp(-L_BCE(m) / alpha) + beta), the inverse of its
+ * sampling probability, recomputed from its loss whenever it is in a batch;
+ * batches are drawn with probability w_m / sum w (inverse-CDF search of the
+ * float64 prefix sums, one splitmix64 uniform per draw from the counter
+ * seed ^ (step << 32) ^ draw, top 53 bits).
+ * pifu_surrogate_ohem_init: weights of m tuples set to 1 (after
+ * pifu_surrogate_init, which drops them).  pifu_surrogate_ohem_weights:
+ * host copy of the m weights (set = 0) or upload (set = 1).
+ * pifu_surrogate_ohem_sample: B indices into idx_dev by the current weights
+ * for (seed, step).  pifu_surrogate_train_ohem: as pifu_surrogate_train with
+ * the batches drawn so, re-weighting each drawn tuple from its loss under the
+ * parameters before that step's Adam update; needs the weights for the same
+ * m.  The paper's constants are alpha = 0.7, beta = 0. */
+int pifu_surrogate_ohem_init(pifu_ctx* ctx, int64_t m);
+int pifu_surrogate_ohem_weights(pifu_ctx* ctx, float* host, int64_t n, int set);
+int pifu_surrogate_ohem_sample(pifu_ctx* ctx, uint64_t seed, int step, int B, int* idx_dev,
+                               void* stream);
+int pifu_surrogate_train_ohem(pifu_ctx* ctx, const float* x_dev, const float* y_dev, int64_t m,
+                              int batch, int steps, float lr, float alpha, float beta,
+                              uint64_t seed, double* loss_host, void* stream);
+
 /* Copy f_S's n parameters to (set = 0) or from (set != 0) host memory;
  * n must equal the parameter count. */
 int pifu_surrogate_params(pifu_ctx* ctx, float* host, int64_t n, int set);

@@ -326,6 +326,16 @@ struct pifu_ctx {
               *dH2 = nullptr, *ones = nullptr;
         double* d_loss = nullptr;
         double* h_loss = nullptr;      // pinned
+        // point OHEM (Eq. 6): per-tuple weights and the sampled batch
+        int64_t ohem_m = 0;
+        float* ohem_w = nullptr;
+        double* ohem_cdf = nullptr;
+        double* ohem_sums = nullptr;
+        int ohem_B = 0;
+        float* xb = nullptr;
+        float* yb = nullptr;
+        int* ib = nullptr;
+        float* per_loss = nullptr;
     } sur;
     DevNet snet;                       // f_S as the MLP runners see it
     int* squeue = nullptr;             // surrogate fall-back queue (node indices)
@@ -1118,6 +1128,36 @@ int ensure_clist(pifu_ctx* ctx, int64_t cap) {
     return PIFU_OK;
 }
 
+// Point OHEM state for m tuples (weights 1) and a sampled batch of B rows.
+int ohem_ensure(pifu_ctx* ctx, int64_t m, int B, bool reset) {
+    auto& S = ctx->sur;
+    if (m != S.ohem_m) {
+        dev_free(S.ohem_w);
+        dev_free(S.ohem_cdf);
+        dev_free(S.ohem_sums);
+        S.ohem_m = 0;
+        CK(dev_alloc(&S.ohem_w, m));
+        CK(dev_alloc(&S.ohem_cdf, m));
+        CK(dev_alloc(&S.ohem_sums, ohem_scan_blocks(m)));
+        S.ohem_m = m;
+        reset = true;
+    }
+    if (reset) CK(launch_fill(m, S.ohem_w, 1.0f, nullptr));
+    if (B > S.ohem_B) {
+        dev_free(S.xb);
+        dev_free(S.yb);
+        dev_free(S.ib);
+        dev_free(S.per_loss);
+        S.ohem_B = 0;
+        CK(dev_alloc(&S.xb, (int64_t)B * ctx->snet.ldx));
+        CK(dev_alloc(&S.yb, B));
+        CK(dev_alloc(&S.ib, B));
+        CK(dev_alloc(&S.per_loss, B));
+        S.ohem_B = B;
+    }
+    return PIFU_OK;
+}
+
 int decode_err(unsigned int e) {
     if (e & kErrCapacity) return PIFU_ERR_CAPACITY;
     if (e & kErrNotConverged) return PIFU_ERR_NOT_CONVERGED;
@@ -1181,6 +1221,15 @@ void sur_free(pifu_ctx* ctx) {
     ctx->snet.tc_ok = false;
     S.ready = false;
     S.batch_cap = 0;
+    dev_free(S.ohem_w);
+    dev_free(S.ohem_cdf);
+    dev_free(S.ohem_sums);
+    dev_free(S.xb);
+    dev_free(S.yb);
+    dev_free(S.ib);
+    dev_free(S.per_loss);
+    S.ohem_m = 0;
+    S.ohem_B = 0;
 }
 
 // The FP32 runner's view of f_S (weights inside the flat parameter buffer).
@@ -1304,7 +1353,8 @@ int sur_batch_ws(pifu_ctx* ctx, int B) {
 
 // Forward + backward of f_S on one batch (rows x: [B][ldx], targets y):
 // gradients into S.grads, mean BCE added to *S.d_loss.
-int sur_grad(pifu_ctx* ctx, const float* x, const float* y, int B, cudaStream_t s) {
+int sur_grad(pifu_ctx* ctx, const float* x, const float* y, int B, cudaStream_t s,
+             float* per_loss = nullptr) {
     auto& S = ctx->sur;
     const int ldx = ctx->snet.ldx;
     const float slope = ctx->snet.slope;
@@ -1318,7 +1368,7 @@ int sur_grad(pifu_ctx* ctx, const float* x, const float* y, int B, cudaStream_t 
     CK(launch_gemm_strided(B, h2, h1, S.H1, h1, 1, P + S.off_w[1], 1, h1, S.H2, h2, 1, 0, s));
     CK(launch_bias_lrelu(B, h2, S.H2, h2, P + S.off_b[1], slope, s));
     CK(launch_gemm_strided(B, 1, h2, S.H2, h2, 1, P + S.off_w[2], 1, h2, S.logit, 1, 1, 0, s));
-    CK(launch_bce_grad(B, S.logit, P + S.off_b[2], y, S.g, S.d_loss, s));
+    CK(launch_bce_grad(B, S.logit, P + S.off_b[2], y, S.g, S.d_loss, s, per_loss));
     // backward
     CK(cudaMemsetAsync(G, 0, (size_t)S.n * 4, s));
     // layer 3: dW3 = g^T H2, db3 = sum g, dH2 = g W3
@@ -2979,6 +3029,86 @@ int pifu_surrogate_train(pifu_ctx* ctx, const float* x_dev, const float* y_dev, 
         loss_host[1] = *S.h_loss;
     }
     return sur_build_tc(ctx);   // inference form follows the new parameters
+}
+
+int pifu_surrogate_ohem_init(pifu_ctx* ctx, int64_t m) {
+    if (!ctx || m < 1 || m > ((int64_t)1 << 31) - 1) return PIFU_ERR_ARG;
+    if (!ctx->sur.ready) return PIFU_ERR_STATE;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return PIFU_ERR_CUDA;
+    int st = ohem_ensure(ctx, m, 1, true);
+    if (st != PIFU_OK) return st;
+    CK(cudaDeviceSynchronize());
+    return PIFU_OK;
+}
+
+int pifu_surrogate_ohem_weights(pifu_ctx* ctx, float* host, int64_t n, int set) {
+    if (!ctx || !host) return PIFU_ERR_ARG;
+    auto& S = ctx->sur;
+    if (!S.ohem_w) return PIFU_ERR_STATE;
+    if (n != S.ohem_m) return PIFU_ERR_ARG;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return PIFU_ERR_CUDA;
+    CK(cudaMemcpy(set ? (void*)S.ohem_w : (void*)host, set ? (const void*)host : (const void*)S.ohem_w,
+                  (size_t)n * 4, set ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToHost));
+    return PIFU_OK;
+}
+
+int pifu_surrogate_ohem_sample(pifu_ctx* ctx, uint64_t seed, int step, int B, int* idx_dev,
+                               void* stream) {
+    if (!ctx || !idx_dev || B < 1 || step < 0) return PIFU_ERR_ARG;
+    auto& S = ctx->sur;
+    if (!S.ohem_w) return PIFU_ERR_STATE;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return PIFU_ERR_CUDA;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    CK(launch_ohem_sample(S.ohem_w, S.ohem_m, S.ohem_cdf, S.ohem_sums, seed, (uint32_t)step, B,
+                          idx_dev, s));
+    CK(cudaStreamSynchronize(s));
+    return PIFU_OK;
+}
+
+int pifu_surrogate_train_ohem(pifu_ctx* ctx, const float* x_dev, const float* y_dev, int64_t m,
+                              int batch, int steps, float lr, float alpha, float beta,
+                              uint64_t seed, double* loss_host, void* stream) {
+    if (!ctx || !x_dev || !y_dev || m < 1 || batch < 1 || batch > (1 << 20) || steps < 0 ||
+        !(lr > 0.f) || !(alpha > 0.f) || !(beta >= 0.f))
+        return PIFU_ERR_ARG;
+    auto& S = ctx->sur;
+    if (!S.ready) return PIFU_ERR_STATE;
+    if (S.ohem_m != m) return PIFU_ERR_STATE;   // pifu_surrogate_ohem_init(m) first
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return PIFU_ERR_CUDA;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int B = batch;
+    int st = sur_batch_ws(ctx, B);
+    if (st == PIFU_OK) st = ohem_ensure(ctx, m, B, false);
+    if (st != PIFU_OK) return st;
+    const int ldx = ctx->snet.ldx;
+    double first = 0.0;
+    for (int it = 0; it < steps; ++it) {
+        // draw the batch by the current weights, train on it, re-weight it
+        CK(launch_ohem_sample(S.ohem_w, m, S.ohem_cdf, S.ohem_sums, seed, (uint32_t)it, B, S.ib,
+                              s));
+        CK(launch_gather_rows(x_dev, y_dev, ldx, S.ib, B, S.xb, S.yb, s));
+        CK(cudaMemsetAsync(S.d_loss, 0, sizeof(double), s));
+        st = sur_grad(ctx, S.xb, S.yb, B, s, S.per_loss);
+        if (st != PIFU_OK) return st;
+        CK(launch_ohem_update(S.ohem_w, S.ib, S.per_loss, B, alpha, beta, s));
+        CK(launch_adam(S.n, S.params, S.grads, S.adam_m, S.adam_v, lr, ++S.step, s));
+        if (it == 0) {
+            CK(cudaMemcpyAsync(S.h_loss, S.d_loss, sizeof(double), cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            first = *S.h_loss;
+        }
+    }
+    CK(cudaMemcpyAsync(S.h_loss, S.d_loss, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (loss_host) {
+        loss_host[0] = first;
+        loss_host[1] = *S.h_loss;
+    }
+    return sur_build_tc(ctx);
 }
 
 int pifu_surrogate_params(pifu_ctx* ctx, float* host, int64_t n, int set) {

@@ -215,9 +215,20 @@ cudaError_t launch_gemm_strided(int M, int N, int K, const float* A, int64_t a_m
                                 int k_slices, int accumulate, cudaStream_t s);
 cudaError_t launch_bias_lrelu(int M, int N, float* Z, int ld, const float* bias, float slope,
                               cudaStream_t s);
-// g[b] = (sigmoid(logit[b] + bias) - y[b]) / B; *loss += mean BCE.
+// g[b] = (sigmoid(logit[b] + bias) - y[b]) / B; *loss += mean BCE;
+// per_loss[b] = sample b's BCE (if non-null).
 cudaError_t launch_bce_grad(int B, const float* logit, const float* bias, const float* y, float* g,
-                            double* loss, cudaStream_t s);
+                            double* loss, cudaStream_t s, float* per_loss = nullptr);
+// Point OHEM: B indices drawn with probability proportional to w[0 .. m)
+// (cdf: m doubles, sums: ohem_scan_blocks(m) doubles of scratch).
+int64_t ohem_scan_blocks(int64_t m);
+cudaError_t launch_ohem_sample(const float* w, int64_t m, double* cdf, double* sums,
+                               uint64_t seed, uint32_t step, int B, int* idx, cudaStream_t s);
+cudaError_t launch_gather_rows(const float* x, const float* y, int ld, const int* idx, int B,
+                               float* xb, float* yb, cudaStream_t s);
+// w[idx[b]] = 1 / (exp(-loss[b] / alpha) + beta) (Eq. 6).
+cudaError_t launch_ohem_update(float* w, const int* idx, const float* loss, int B, float alpha,
+                               float beta, cudaStream_t s);
 cudaError_t launch_lrelu_backward(int64_t n, float* dH, const float* H, float slope,
                                   cudaStream_t s);
 cudaError_t launch_adam(int64_t n, float* w, const float* g, float* m, float* v, float lr, int t,

@@ -79,10 +79,11 @@ __global__ void bias_lrelu_kernel(int M, int N, float* __restrict__ Z, int ld,
     Z[(int64_t)m * ld + n] = z >= 0.f ? z : slope * z;
 }
 
-// g[b] = (sigmoid(t_b + bias) - y_b) / B and loss += softplus(t) - y t.
+// g[b] = (sigmoid(t_b + bias) - y_b) / B and loss += softplus(t) - y t
+// (per_loss[b] = that sample's loss, if set).
 __global__ void bce_grad_kernel(int B, const float* __restrict__ logit, const float* __restrict__ bias,
                                 const float* __restrict__ y, float* __restrict__ g,
-                                double* __restrict__ loss) {
+                                double* __restrict__ loss, float* __restrict__ per_loss) {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     double l = 0.0;
     if (b < B) {
@@ -93,6 +94,7 @@ __global__ void bce_grad_kernel(int B, const float* __restrict__ logit, const fl
         const double td = (double)t;
         const double sp = td > 0 ? td + log1p(exp(-td)) : log1p(exp(td));
         l = sp - (double)y[b] * td;
+        if (per_loss) per_loss[b] = (float)l;
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) l += __shfl_xor_sync(0xffffffffu, l, o);
@@ -119,6 +121,127 @@ __global__ void adam_kernel(int64_t n, float* __restrict__ w, const float* __res
     m[i] = mi;
     v[i] = vi;
     w[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+}
+
+// ---- point OHEM (Sec. 3.3, Eq. 6) ----------------------------------------------
+//
+// Sampling probability proportional to w = 1 / (exp(-L_BCE / alpha) + beta):
+// an inclusive FP64 prefix sum of w (blocks of kScanPer elements, then the
+// block totals, then their offsets), one splitmix64 uniform per draw from the
+// counter seed ^ (step << 32) ^ draw, and an upper-bound search of u * total.
+
+constexpr int kScanThreads = 256;
+constexpr int kScanEach = 16;
+constexpr int kScanPer = kScanThreads * kScanEach;
+
+__device__ __forceinline__ double warp_incl_scan(double v, int lane) {
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const double t = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += t;
+    }
+    return v;
+}
+
+// Inclusive scan of vals[0 .. n) in one block of kScanThreads threads, each
+// owning `each` consecutive values; returns the block total.
+template <typename Load, typename Store>
+__device__ __forceinline__ double block_scan(int64_t n, int each, Load&& load, Store&& store) {
+    __shared__ double warp_tot[kScanThreads / 32];
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const int64_t i0 = (int64_t)t * each;
+    double run = 0.0;
+    for (int k = 0; k < each; ++k)
+        if (i0 + k < n) run += load(i0 + k);
+    const double incl = warp_incl_scan(run, lane);
+    if (lane == 31) warp_tot[warp] = incl;
+    __syncthreads();
+    double woff = 0.0, total = 0.0;
+    for (int q = 0; q < kScanThreads / 32; ++q) {
+        if (q < warp) woff += warp_tot[q];
+        total += warp_tot[q];
+    }
+    double acc = woff + incl - run;   // exclusive prefix of this thread
+    for (int k = 0; k < each; ++k)
+        if (i0 + k < n) {
+            const double v = load(i0 + k);
+            acc += v;
+            store(i0 + k, acc, v);       // inclusive prefix and the element
+        }
+    __syncthreads();
+    return total;
+}
+
+__global__ void __launch_bounds__(kScanThreads) scan_blocks_kernel(const float* __restrict__ w,
+                                                                   int64_t m, double* __restrict__ cdf,
+                                                                   double* __restrict__ sums) {
+    const int64_t base = (int64_t)blockIdx.x * kScanPer;
+    const int64_t n = min((int64_t)kScanPer, m - base);
+    const double tot = block_scan(
+        n, kScanEach, [&](int64_t i) { return (double)w[base + i]; },
+        [&](int64_t i, double incl, double) { cdf[base + i] = incl; });
+    if (threadIdx.x == 0) sums[blockIdx.x] = tot;
+}
+
+// Exclusive offsets of the block totals, in place (one block).
+__global__ void __launch_bounds__(kScanThreads) scan_sums_kernel(double* __restrict__ sums,
+                                                                 int64_t nb) {
+    const int each = (int)((nb + kScanThreads - 1) / kScanThreads);
+    block_scan(
+        nb, each, [&](int64_t i) { return sums[i]; },
+        [&](int64_t i, double incl, double v) { sums[i] = incl - v; });   // exclusive
+}
+
+__global__ void add_offsets_kernel(double* __restrict__ cdf, int64_t m,
+                                   const double* __restrict__ offs) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < m) cdf[i] += offs[i / kScanPer];
+}
+
+__device__ __forceinline__ uint64_t splitmix64_out(uint64_t state) {
+    uint64_t z = state + 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+__global__ void ohem_sample_kernel(const double* __restrict__ cdf, int64_t m, uint64_t seed,
+                                   uint32_t step, int B, int* __restrict__ idx) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B) return;
+    const uint64_t z = splitmix64_out(seed ^ ((uint64_t)step << 32) ^ (uint64_t)b);
+    const double u = (double)(z >> 11) * (1.0 / 9007199254740992.0) * cdf[m - 1];
+    int64_t lo = 0, hi = m;   // first i with cdf[i] > u
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (cdf[mid] > u) hi = mid;
+        else lo = mid + 1;
+    }
+    idx[b] = (int)min(lo, m - 1);
+}
+
+// xb[b] = x[idx[b]] (rows of ld floats), yb[b] = y[idx[b]].
+__global__ void gather_rows_kernel(const float* __restrict__ x, const float* __restrict__ y, int ld,
+                                   const int* __restrict__ idx, int B, float* __restrict__ xb,
+                                   float* __restrict__ yb) {
+    const int nq = ld >> 2;
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)B * nq) return;
+    const int b = (int)(t / nq);
+    const int q = (int)(t - (int64_t)b * nq);
+    const int64_t r = idx[b];
+    reinterpret_cast<float4*>(xb + (int64_t)b * ld)[q] =
+        reinterpret_cast<const float4*>(x + r * ld)[q];
+    if (q == 0) yb[b] = y[r];
+}
+
+// w[idx[b]] = 1 / (exp(-L_b / alpha) + beta), kept in [1e-30, 1e30].
+__global__ void ohem_update_kernel(float* __restrict__ w, const int* __restrict__ idx,
+                                   const float* __restrict__ loss, int B, float alpha, float beta) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B) return;
+    const float v = 1.0f / (expf(-loss[b] / alpha) + beta);
+    w[idx[b]] = fminf(fmaxf(v, 1e-30f), 1e30f);
 }
 
 __global__ void fill_kernel(int64_t n, float* __restrict__ p, float value) {
@@ -152,8 +275,8 @@ cudaError_t launch_bias_lrelu(int M, int N, float* Z, int ld, const float* bias,
 }
 
 cudaError_t launch_bce_grad(int B, const float* logit, const float* bias, const float* y, float* g,
-                            double* loss, cudaStream_t s) {
-    bce_grad_kernel<<<nblk(B), 256, 0, s>>>(B, logit, bias, y, g, loss);
+                            double* loss, cudaStream_t s, float* per_loss) {
+    bce_grad_kernel<<<nblk(B), 256, 0, s>>>(B, logit, bias, y, g, loss, per_loss);
     return cudaGetLastError();
 }
 
@@ -168,6 +291,30 @@ cudaError_t launch_adam(int64_t n, float* w, const float* g, float* m, float* v,
     const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
     const float c1 = 1.f - powf(b1, (float)t), c2 = 1.f - powf(b2, (float)t);
     adam_kernel<<<nblk(n), 256, 0, s>>>(n, w, g, m, v, lr, b1, b2, eps, c1, c2);
+    return cudaGetLastError();
+}
+
+int64_t ohem_scan_blocks(int64_t m) { return (m + kScanPer - 1) / kScanPer; }
+
+cudaError_t launch_ohem_sample(const float* w, int64_t m, double* cdf, double* sums,
+                               uint64_t seed, uint32_t step, int B, int* idx, cudaStream_t s) {
+    const int64_t nb = ohem_scan_blocks(m);
+    scan_blocks_kernel<<<(unsigned)nb, kScanThreads, 0, s>>>(w, m, cdf, sums);
+    scan_sums_kernel<<<1, kScanThreads, 0, s>>>(sums, nb);
+    add_offsets_kernel<<<nblk(m), 256, 0, s>>>(cdf, m, sums);
+    ohem_sample_kernel<<<nblk(B), 256, 0, s>>>(cdf, m, seed, step, B, idx);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather_rows(const float* x, const float* y, int ld, const int* idx, int B,
+                               float* xb, float* yb, cudaStream_t s) {
+    gather_rows_kernel<<<nblk((int64_t)B * (ld / 4)), 256, 0, s>>>(x, y, ld, idx, B, xb, yb);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ohem_update(float* w, const int* idx, const float* loss, int B, float alpha,
+                               float beta, cudaStream_t s) {
+    ohem_update_kernel<<<nblk(B), 256, 0, s>>>(w, idx, loss, B, alpha, beta);
     return cudaGetLastError();
 }
 

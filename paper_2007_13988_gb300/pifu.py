@@ -40,7 +40,9 @@ EXPORTS = ("pifu_create", "pifu_destroy", "pifu_query", "pifu_query_colour", "pi
            "pifu_profile", "pifu_profile_read", "pifu_query_noalloc", "pifu_query_ex",
            "pifu_frame", "pifu_surrogate_init", "pifu_surrogate_samples", "pifu_surrogate_grad",
            "pifu_surrogate_train", "pifu_surrogate_params", "pifu_surrogate_query",
-           "pifu_calibrate_fp8", "pifu_frames", "pifu_autotune")
+           "pifu_calibrate_fp8", "pifu_frames", "pifu_autotune", "pifu_surrogate_ohem_init",
+           "pifu_surrogate_ohem_weights", "pifu_surrogate_ohem_sample",
+           "pifu_surrogate_train_ohem")
 
 KERNEL_CLASSES = ("gather", "mlp_hidden", "mlp_last", "level", "select", "render", "mlp_f32")
 
@@ -150,6 +152,15 @@ def _lib():
     lib.pifu_surrogate_grad.restype = I
     lib.pifu_surrogate_train.argtypes = [P, P, P, I64, I, I, F, ctypes.POINTER(D), P]
     lib.pifu_surrogate_train.restype = I
+    lib.pifu_surrogate_ohem_init.argtypes = [P, I64]
+    lib.pifu_surrogate_ohem_init.restype = I
+    lib.pifu_surrogate_ohem_weights.argtypes = [P, ctypes.POINTER(F), I64, I]
+    lib.pifu_surrogate_ohem_weights.restype = I
+    lib.pifu_surrogate_ohem_sample.argtypes = [P, U64, I, I, P, P]
+    lib.pifu_surrogate_ohem_sample.restype = I
+    lib.pifu_surrogate_train_ohem.argtypes = [P, P, P, I64, I, I, F, F, F, U64,
+                                              ctypes.POINTER(D), P]
+    lib.pifu_surrogate_train_ohem.restype = I
     lib.pifu_surrogate_params.argtypes = [P, ctypes.POINTER(F), I64, I]
     lib.pifu_surrogate_params.restype = I
     lib.pifu_sync_stats.argtypes = [P, ctypes.POINTER(pifu_volume)]
@@ -356,6 +367,35 @@ def pifu_autotune(ctx, rows, stream=None, n_max=32):
     _check(_lib().pifu_autotune(ctx, int(rows), _stream(stream), bn, ms, n_max, ctypes.byref(n)),
            "pifu_autotune", ctx)
     return [(int(bn[i]), float(ms[i])) for i in range(min(n.value, n_max))]
+
+
+def pifu_surrogate_ohem_init(ctx, m):
+    _check(_lib().pifu_surrogate_ohem_init(ctx, int(m)), "pifu_surrogate_ohem_init", ctx)
+
+
+def pifu_surrogate_ohem_weights(ctx, n, values=None):
+    """Read the n OHEM weights (values None) or upload them."""
+    buf = np.ascontiguousarray(np.zeros(n, np.float32) if values is None else
+                               np.asarray(values, np.float32))
+    ptr = buf.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+    _check(_lib().pifu_surrogate_ohem_weights(ctx, ptr, n, 0 if values is None else 1),
+           "pifu_surrogate_ohem_weights", ctx)
+    return buf
+
+
+def pifu_surrogate_ohem_sample(ctx, seed, step, idx, stream=None):
+    """Draw idx.shape[0] indices (int32 CUDA tensor) by the current weights."""
+    _check(_lib().pifu_surrogate_ohem_sample(ctx, seed, step, idx.shape[0], _ptr(idx),
+                                             _stream(stream)), "pifu_surrogate_ohem_sample", ctx)
+
+
+def pifu_surrogate_train_ohem(ctx, x, y, batch=4096, steps=100, lr=1e-3, alpha=0.7, beta=0.0,
+                              seed=0, stream=None):
+    loss = (ctypes.c_double * 2)()
+    _check(_lib().pifu_surrogate_train_ohem(ctx, _ptr(x), _ptr(y), x.shape[0], batch, steps, lr,
+                                            alpha, beta, seed, loss, _stream(stream)),
+           "pifu_surrogate_train_ohem", ctx)
+    return float(loss[0]), float(loss[1])
 
 
 def pifu_calibrate_fp8(ctx, occ_map, calib, n0=32, stream=None):
