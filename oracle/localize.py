@@ -176,3 +176,71 @@ def hierarchical(field, n0, num_levels):
     for _ in range(num_levels - 1):
         levels.append(refine(field, levels[-1]))
     return levels
+
+
+# ---- the octree baselines of Fig. 3 (Sec. 3.2) ---------------------------------
+#
+# Two subdivision rules the paper compares against, each dense at the coarsest
+# level and one pass per finer level (no dilation, no conflict rounds):
+#  * binarized octree (the subdivision of the occupancy-network paper cited
+#    there): binarize the coarser level, interpolate tri-linearly, evaluate
+#    the nodes whose interpolated value is neither 0 nor 1 (the cells whose
+#    corners straddle the boundary); every other node keeps its 0 / 1 value;
+#  * threshold subdivision: for every fine node, the coarse values it
+#    interpolates from (its 1, 2, 4 or 8 coarse corners, continuous values);
+#    evaluate it when their maximum absolute deviation from their mean exceeds
+#    the threshold, else give it that mean (tri-linear interpolation).
+# The acceleration factor of Fig. 3 divides the brute-force node count by the
+# evaluated count.
+
+
+def corner_mean_deviation(coarse_vals):
+    """(mean, deviation) for every node of the next level: the mean of the
+    coarse values it interpolates from and their maximum absolute deviation
+    from that mean."""
+    c = np.asarray(coarse_vals, dtype=F64)
+    Nc = c.shape[0] - 1
+    idx = np.arange(2 * Nc + 1)
+    lo, hi = idx // 2, (idx + 1) // 2
+    mean = upsample_tentative(c)
+    dev = np.zeros_like(mean)
+    for kz in (lo, hi):
+        for jy in (lo, hi):
+            for ix in (lo, hi):
+                dev = np.maximum(dev, np.abs(c[np.ix_(kz, jy, ix)] - mean))
+    return mean, dev
+
+
+def octree_binarized(field, n0, num_levels):
+    """Binarized-octree baseline; returns the levels."""
+    levels = [dense(field, n0)]
+    for _ in range(num_levels - 1):
+        coarse = levels[-1]
+        N = 2 * coarse.N
+        T = upsample_tentative(coarse.values >= 0.5)
+        ev = (T > 0.0) & (T < 1.0)
+        values = T.copy()
+        n = evaluate_mask(field, N, ev, values)
+        levels.append(Level(N=N, values=values, evaluated=ev, tentative=T, selected=ev,
+                            n_eval=n, conflict_rounds=0))
+    return levels
+
+
+def octree_threshold(field, n0, num_levels, threshold):
+    """Threshold-subdivision baseline; returns the levels."""
+    levels = [dense(field, n0)]
+    for _ in range(num_levels - 1):
+        coarse = levels[-1]
+        N = 2 * coarse.N
+        mean, dev = corner_mean_deviation(coarse.values)
+        ev = dev > threshold
+        values = mean.copy()
+        n = evaluate_mask(field, N, ev, values)
+        levels.append(Level(N=N, values=values, evaluated=ev, tentative=mean, selected=ev,
+                            n_eval=n, conflict_rounds=0))
+    return levels
+
+
+def acceleration_factor(levels):
+    """Brute-force evaluations at the finest level / evaluations made."""
+    return (levels[-1].N + 1) ** 3 / sum(l.n_eval for l in levels)

@@ -158,3 +158,67 @@ def test_isolated_thin_capsule_is_missed():
     d = localize.dense(f, 32)
     assert d.binary.sum() > 0
     assert lv[-1].binary.sum() == 0
+
+
+# ---- octree baselines (Fig. 3) ---------------------------------------------------
+
+def affine_field(P):
+    return 0.31 + 0.27 * P[:, 0] - 0.19 * P[:, 1] + 0.11 * P[:, 2]
+
+
+def test_threshold_octree_affine_field_closed_forms():
+    # tri-linear interpolation reproduces an affine field exactly
+    n0, L = 4, 3
+    big = localize.octree_threshold(affine_field, n0, L, threshold=10.0)
+    assert [l.n_eval for l in big] == [(n0 + 1) ** 3, 0, 0]
+    P = localize.grid_points(n0 << (L - 1))
+    np.testing.assert_allclose(big[-1].values.ravel(), affine_field(P), atol=1e-14)
+    # threshold 0: every node between coarse nodes deviates (the gradient
+    # is non-zero on every axis), nodes on coarse nodes do not
+    zero = localize.octree_threshold(affine_field, n0, L, threshold=0.0)
+    for l in zero[1:]:
+        assert l.n_eval == (l.N + 1) ** 3 - (l.N // 2 + 1) ** 3
+
+
+def test_binarized_octree_single_inside_node():
+    # one inside coarse node: exactly the fine nodes of the 8 cells around it
+    # other than itself (its own fine node interpolates to 1, its
+    # neighbours to fractions, everything else to 0) are evaluated
+    n0 = 4
+    centre = np.array([0.0, 0.0, 0.0])
+    f = lambda P: (np.abs(P - centre).max(axis=1) < 0.1).astype(np.float64)
+    lv = localize.octree_binarized(f, n0, 2)
+    ev = lv[1].evaluated
+    k, j, i = np.nonzero(ev)
+    assert len(k) == 26                      # the 3x3x3 block around fine node (4, 4, 4), less it
+    assert set(map(tuple, np.stack([k, j, i], 1) - 4)) == {
+        (a, b, c) for a in (-1, 0, 1) for b in (-1, 0, 1) for c in (-1, 0, 1)} - {(0, 0, 0)}
+
+
+def test_fig3_ordering_on_capsules():
+    """On the capsule figure (32^3 -> 64^3 from 16^3): the method keeps the
+    brute-force result, the binarized octree loses surface, and the
+    threshold subdivision trades evaluations for accuracy monotonically."""
+    from oracle import metrics
+    n0, L = 16, 3
+    fig = synth.capsule_figure(0)
+    tau = 0.5 * 2.0 / (n0 << (L - 1))
+    f = lambda P: field.capsule_occupancy(fig.a, fig.b, fig.r, P, tau)
+    brute = localize.dense(f, n0 << (L - 1))
+    ours = localize.hierarchical(f, n0, L)
+    binz = localize.octree_binarized(f, n0, L)
+    iou = lambda lv: metrics.iou(lv[-1].binary, brute.binary)
+    assert iou(ours) == 1.0
+    assert iou(binz) < iou(ours)
+    accel, ious = [], []
+    for thr in (0.05, 0.08, 0.12, 0.2, 0.3, 0.4):
+        lv = localize.octree_threshold(f, n0, L, thr)
+        accel.append(localize.acceleration_factor(lv))
+        ious.append(iou(lv))
+    assert all(a < b for a, b in zip(accel, accel[1:]))      # higher threshold, fewer evaluations
+    assert ious[0] >= ious[-1]
+    # at the threshold that evaluates about as many nodes as the method,
+    # the method is more accurate
+    a_ours = localize.acceleration_factor(ours)
+    k = int(np.argmin([abs(a - a_ours) for a in accel]))
+    assert ious[k] < 1.0
