@@ -56,6 +56,8 @@ def parse_args():
                     help="skip the paper's view-culled final level render")
     ap.add_argument("--no-512", action="store_true",
                     help="skip the 512^3 precision form (timing and accuracy vs the oracle)")
+    ap.add_argument("--no-octree", action="store_true",
+                    help="skip the Fig. 3 comparison with the two octree baselines")
     ap.add_argument("--form", choices=("graph", "host"), default="graph")
     ap.add_argument("--query-points", type=int, default=1 << 20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -259,6 +261,7 @@ def workload_config(w, evals, hits, precision="mixed"):
 # -------------------------------------------------------------------- ours ---
 
 PREC = {"fp32": 0, "bf16": 1, "mixed": 2, "fp8_mixed": 3, "fp8": 4}
+PREC_NAME = {v: k for k, v in PREC.items()}
 DTYPE = {"fp32": "f32", "bf16": "bf16", "mixed": "bf16+f32", "fp8_mixed": "e4m3+bf16+f32",
          "fp8": "e4m3+bf16"}
 
@@ -349,6 +352,70 @@ def time_form(fr, prec, steps, warmup, world, clocks=None, form="graph", sur_mar
             "evals_per_level": [int(vol.evals_per_level[i]) for i in range(L)],
             "rounds": [int(vol.conflict_rounds[i]) for i in range(L)],
             "hits": int(fr.mask.sum().item())}
+
+
+def octree_tradeoff(fr, prec, reps=3):
+    """Fig. 3: for the method and the two octree baselines, the acceleration
+    factor (brute-force evaluations / evaluations), the IoU of the binarized
+    finest grid against the brute-force dense grid in the same arithmetic,
+    and the localization time (host-driven form, device-timed)."""
+    import numpy as np
+    import torch
+    p, w = fr.pifu, fr.w
+    N = w.n0 << (w.num_levels - 1)
+
+    def timed(n0, L, **kw):
+        run = lambda: p.pifu_localize(fr.ctx, fr.occ, w.calib, n0, L, precision=prec,
+                                      stream=fr.stream, **kw)
+        vol = run()
+        ms = []
+        for _ in range(reps):
+            e = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+            with torch.cuda.stream(fr.stream):
+                fr.flush.zero_()
+            e[0].record(fr.stream)
+            vol = run()
+            e[1].record(fr.stream)
+            fr.stream.synchronize()
+            ms.append(e[0].elapsed_time(e[1]))
+        occ, _, _ = p.volume_tensors(vol)
+        b = p.unpack_bits(occ.cpu().numpy(), vol.n, vol.row_words)
+        return int(vol.n_eval), float(np.median(ms)), b
+
+    from scipy import ndimage
+    cell = (N // w.n0) ** 3
+
+    def main_body(b):
+        # 26-connected components of at least one coarsest cell's volume
+        lab, _ = ndimage.label(b, structure=np.ones((3, 3, 3)))
+        sz = np.bincount(lab.ravel())
+        sz[0] = 0
+        return sz[lab] >= cell
+
+    def iou(a, b):
+        return float(np.count_nonzero(a & b)) / max(1, int(np.count_nonzero(a | b)))
+
+    n_b, ms_b, bb = timed(N, 1)
+    body_bb = main_body(bb)
+
+    def entry(n0, L, **kw):
+        n, ms, b = timed(n0, L, **kw)
+        return {"acceleration": (N + 1) ** 3 / n, "iou_vs_brute_force": iou(b, bb),
+                "main_body_iou_vs_brute_force": iou(main_body(b), body_bb), "evals": n,
+                "localize_ms": ms, "time_speedup_vs_brute_force": ms_b / ms}
+
+    out = {"workload": f"{w.n0}^3 -> {N}^3 localization of the full-size frame, "
+                       f"{DTYPE[PREC_NAME[prec]]} arithmetic, host-driven form",
+           "brute_force": {"evals": n_b, "localize_ms": ms_b},
+           "method": entry(w.n0, w.num_levels),
+           "binarized_octree": entry(w.n0, w.num_levels, subdivision=p.PIFU_SUBDIV_BINARIZED)}
+    out["threshold_octree"] = {
+        str(t): entry(w.n0, w.num_levels, subdivision=p.PIFU_SUBDIV_THRESHOLD, threshold=t)
+        for t in (0.01, 0.02, 0.03, 0.05, 0.08, 0.12, 0.2, 0.3, 0.4)}
+    out["notes"] = ("thresholds 0.05 .. 0.4 are Fig. 3's, 0.01 .. 0.03 extend the curve to the "
+                    "method's evaluation count; main body: 26-connected inside components of at "
+                    f"least one coarsest cell ({cell} voxels)")
+    return out
 
 
 def snapshot(fr, vol):
@@ -613,6 +680,10 @@ def run_ours(args, rank, world, local_rank):
         fp32_512 = time_form(fr, 0, 2, 1, world, levels=L5)
         p512["fp32"] = (fp32_512, snapshot(fr, fp32_512["vol"]))
 
+    # ---- Fig. 3: the method against the two octree baselines -----------------
+    fig3 = None
+    if not args.no_octree:
+        fig3 = octree_tradeoff(fr, prec)
     # ---- the video stream in lockstep batches ----------------------------------
     stream_out, stream_inputs = None, None
     if prec != 0 and not args.no_stream:
@@ -809,6 +880,8 @@ def run_ours(args, rank, world, local_rank):
                 "colour_psnr_vs_oracle_culled_db": float("inf") if mse == 0 else
                 10 * np.log10(1.0 / mse),
                 "oracle_culled_evals": res["n_eval"], "oracle_s": time.perf_counter() - t0}
+    if fig3 is not None:
+        line["fig3_octree_baselines"] = fig3
     if stream_out is not None:
         line["stream"] = stream_out
     if p512:

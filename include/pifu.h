@@ -95,7 +95,27 @@ typedef struct {
     float margin;        /* MIXED, FP8_MIXED: FP32 re-evaluation band |o - 0.5| < margin */
     int32_t use_surrogate;    /* 1: coarse levels evaluate the trained f_S first  */
     float surrogate_margin;   /* f_S occupancies within this of 0.5 fall back to f_O */
+    int32_t subdivision;      /* pifu_subdivision (0: the method of Sec. 3.2)     */
+    float threshold;          /* PIFU_SUBDIV_THRESHOLD: deviation threshold >= 0  */
 } pifu_levels;
+
+/* Rule that picks the nodes of a finer level to evaluate (pifu_localize
+ * only; the graph forms take METHOD alone).  The two octree baselines the
+ * paper compares against in Fig. 3 run one evaluation pass per level, with
+ * no dilation and no conflict rounds:
+ *  BINARIZED  evaluate the nodes whose tri-linear interpolation of the
+ *             binarized coarser level is neither 0 nor 1; the others keep
+ *             that 0 / 1;
+ *  THRESHOLD  give every node the tri-linear interpolation of the coarser
+ *             level's continuous values and evaluate it when those corner
+ *             values deviate from their mean by more than `threshold`
+ *             (values_dev then holds a value at every node).
+ * The acceleration factor of Fig. 3 is (n + 1)^3 / pifu_volume.n_eval. */
+typedef enum {
+    PIFU_SUBDIV_METHOD = 0,
+    PIFU_SUBDIV_BINARIZED = 1,
+    PIFU_SUBDIV_THRESHOLD = 2
+} pifu_subdivision;
 
 /* Target view of the render: the volume is aligned with it (Sec. 3.2), so
  * pixel (i, j) looks along -z through x = (2i+1)/width - 1,

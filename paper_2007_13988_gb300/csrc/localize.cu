@@ -119,12 +119,14 @@ __global__ void __launch_bounds__(256) dense_setup_kernel(int N, uint32_t* __res
 }
 
 // sel = dilate26(src) & ~eval, restricted to the grid; eval |= sel; compact.
+// radius 0: sel = src & ~eval (no dilation; the binarized-octree baseline).
 __global__ void __launch_bounds__(256) dilate_select_kernel(const uint32_t* __restrict__ src,
                                                             uint32_t* __restrict__ eval,
                                                             uint32_t* __restrict__ clear, int N,
                                                             int* __restrict__ list,
                                                             unsigned int* __restrict__ count,
-                                                            int64_t fslot, int64_t slot_nodes) {
+                                                            int64_t fslot, int64_t slot_nodes,
+                                                            int radius) {
     {
         const int64_t f = blockIdx.y;
         src += f * fslot;
@@ -144,11 +146,11 @@ __global__ void __launch_bounds__(256) dilate_select_kernel(const uint32_t* __re
         row = w / rw;
         const int j = (int)(row % n1);
         const int k = (int)(row / n1);
-        uint32_t acc = 0u;
-        for (int dk = -1; dk <= 1; ++dk) {
+        uint32_t acc = radius ? 0u : src[w];
+        for (int dk = -radius; dk <= radius; ++dk) {
             const int kk = k + dk;
             if (kk < 0 || kk > N) continue;
-            for (int dj = -1; dj <= 1; ++dj) {
+            for (int dj = -1; dj <= 1 && radius; ++dj) {
                 const int jj = j + dj;
                 if (jj < 0 || jj > N) continue;
                 const uint32_t* r = src + ((int64_t)kk * n1 + jj) * rw;
@@ -185,6 +187,66 @@ __global__ void __launch_bounds__(256) dilate_select_kernel(const uint32_t* __re
             s &= s - 1u;
             list[pos++] = (int)(node0 + b);
         }
+    }
+}
+
+// Threshold subdivision, the second octree baseline of Fig. 3: every fine
+// node takes the mean of the continuous coarse values at its 1, 2, 4 or 8
+// coarse corners (their tri-linear interpolation) and is selected for
+// evaluation when the largest absolute deviation of those values from the
+// mean exceeds `thr`.  One warp per bitset word, lane b on node 32 wx + b:
+// the value store is coalesced and the word's bits come from ballots.
+// coarse: the dense (N/2 + 1)^3 values of the coarser level.
+__global__ void __launch_bounds__(256) threshold_select_kernel(
+    const float* __restrict__ coarse, int N, float thr, float* __restrict__ values,
+    uint32_t* __restrict__ tent, uint32_t* __restrict__ bin, uint32_t* __restrict__ eval,
+    uint32_t* __restrict__ conf0, int* __restrict__ list, unsigned int* __restrict__ count) {
+    const int n1 = N + 1;
+    const int rw = row_words_of(N);
+    const int nc1 = N / 2 + 1;
+    const int64_t total = (int64_t)n1 * n1 * rw;
+    const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (w >= total) return;                  // whole warps only (blockDim % 32 == 0)
+    const int wx = (int)(w % rw);
+    const int64_t row = w / rw;
+    const int j = (int)(row % n1);
+    const int k = (int)(row / n1);
+    const int i = wx * 32 + lane;
+    const bool valid = i <= N;
+    float mean = 0.f, dev = 0.f;
+    if (valid) {
+        const int kc[2] = {k >> 1, (k + 1) >> 1};
+        const int jc[2] = {j >> 1, (j + 1) >> 1};
+        const int ic[2] = {i >> 1, (i + 1) >> 1};
+        const int nz = 1 + (k & 1), ny = 1 + (j & 1), nx = 1 + (i & 1);
+        float c[8];
+        int n = 0;
+        float sum = 0.f;
+        for (int a = 0; a < nz; ++a)
+            for (int b = 0; b < ny; ++b)
+                for (int d = 0; d < nx; ++d) {
+                    c[n] = coarse[((int64_t)kc[a] * nc1 + jc[b]) * nc1 + ic[d]];
+                    sum += c[n++];
+                }
+        mean = sum / (float)n;               // n is 1, 2, 4 or 8: an exact scaling
+        for (int m = 0; m < n; ++m) dev = fmaxf(dev, fabsf(c[m] - mean));
+        values[row * n1 + i] = mean;
+    }
+    const bool sel = valid && dev > thr;
+    const uint32_t sbits = __ballot_sync(0xffffffffu, sel);
+    const uint32_t tbits = __ballot_sync(0xffffffffu, valid && mean >= kHalf);
+    if (lane == 0) {
+        tent[w] = tbits;
+        bin[w] = tbits;
+        eval[w] = sbits;
+        conf0[w] = 0u;
+    }
+    if (sbits) {
+        unsigned int base = 0u;
+        if (lane == 0) base = atomicAdd(count, (unsigned int)__popc(sbits));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (sel) list[base + __popc(sbits & ((1u << lane) - 1u))] = (int)(row * n1 + i);
     }
 }
 
@@ -326,7 +388,24 @@ cudaError_t launch_dilate_select(const uint32_t* src, uint32_t* eval, uint32_t* 
                                  int64_t fslot, int64_t slot_nodes) {
     if (slots < 1 || slots > 65535) return cudaErrorInvalidValue;
     dilate_select_kernel<<<dim3(blocks_for(words_of(N)), (unsigned)slots), 256, 0, stream>>>(
-        src, eval, clear, N, list, count, fslot, slot_nodes);
+        src, eval, clear, N, list, count, fslot, slot_nodes, 1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_select(const uint32_t* src, uint32_t* eval, int N, int* list,
+                          unsigned int* count, cudaStream_t stream) {
+    dilate_select_kernel<<<blocks_for(words_of(N)), 256, 0, stream>>>(src, eval, nullptr, N, list,
+                                                                    count, 0, 0, 0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_threshold_select(const float* coarse, int N, float thr, float* values,
+                                    uint32_t* tent, uint32_t* bin, uint32_t* eval,
+                                    uint32_t* conf0, int* list, unsigned int* count,
+                                    cudaStream_t stream) {
+    const int64_t threads = words_of(N) * 32;
+    threshold_select_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, stream>>>(
+        coarse, N, thr, values, tent, bin, eval, conf0, list, count);
     return cudaGetLastError();
 }
 

@@ -300,6 +300,8 @@ struct pifu_ctx {
     // view-culled final level: candidate keys and their occupancies
     int* cull_list = nullptr;
     float* cull_values = nullptr;
+    float* prev_values = nullptr;         // threshold subdivision: the coarser level's values
+    int64_t prev_cap = 0;
     int64_t cull_cap = 0, cull_vals_cap = 0;
     int vol_prec = 0;             // arithmetic of the last localization
     float vol_margin = 0.f;
@@ -799,6 +801,15 @@ int ensure_level_ws(pifu_ctx* ctx, int N) {
         ctx->recheck_cap = nodes;
     }
     ctx->ws_N = N;
+    return PIFU_OK;
+}
+
+int ensure_prev_values(pifu_ctx* ctx, int64_t n) {
+    if (n <= ctx->prev_cap) return PIFU_OK;
+    dev_free(ctx->prev_values);
+    ctx->prev_cap = 0;
+    CK(dev_alloc(&ctx->prev_values, n));
+    ctx->prev_cap = n;
     return PIFU_OK;
 }
 
@@ -2306,6 +2317,7 @@ void pifu_destroy(pifu_ctx* ctx) {
                             &ctx->eval, &ctx->conf[0], &ctx->conf[1]};
     for (auto b : bitsets) dev_free(*b);
     dev_free(ctx->values);
+    dev_free(ctx->prev_values);
     dev_free(ctx->list);
     dev_free(ctx->recheck);
     dev_free(ctx->d_recheck);
@@ -2412,6 +2424,11 @@ int pifu_localize(pifu_ctx* ctx, const pifu_fmap* occ_map, const float calib[12]
     if (use_sur && (!ctx->sur.ready || !(lv->surrogate_margin >= 0.f && lv->surrogate_margin <= 0.5f)))
         return use_sur && !ctx->sur.ready ? PIFU_ERR_STATE : PIFU_ERR_ARG;
     if (ctx->net[0].d_in != occ_map->C + 1) return PIFU_ERR_ARG;
+    const int subdiv = lv->subdivision;
+    if (subdiv < PIFU_SUBDIV_METHOD || subdiv > PIFU_SUBDIV_THRESHOLD) return PIFU_ERR_ARG;
+    if (subdiv == PIFU_SUBDIV_THRESHOLD && !(lv->threshold >= 0.f && lv->threshold <= 1.f))
+        return PIFU_ERR_ARG;
+    if (subdiv != PIFU_SUBDIV_METHOD && use_sur) return PIFU_ERR_UNSUPPORTED;
     const int max_rounds = lv->max_rounds > 0 ? lv->max_rounds : 4096;
     DeviceGuard g(ctx->device);
     if (!g.ok) return PIFU_ERR_CUDA;
@@ -2456,22 +2473,60 @@ int pifu_localize(pifu_ctx* ctx, const pifu_fmap* occ_map, const float calib[12]
         N *= 2;
         const int rw = row_words_of(N);
         const double wbytes = 4.0 * words_of(N);
-        cudaEvent_t ev = ctx->prof.begin(s);
-        CK(launch_classify(ctx->bin[prev], N, ctx->cand, ctx->tent, ctx->bin[cur], ctx->eval,
-                           ctx->conf[0], s));
-        ctx->prof.end(PIFU_K_LEVEL, ev, s, 0.0, 4.0 * words_of(N / 2) + 5.0 * wbytes);
-        ev = ctx->prof.begin(s);
-        CK(launch_popcount(ctx->cand, words_of(N), ctx->d_pop + l, s));
-        ctx->prof.end(PIFU_K_LEVEL, ev, s, 0.0, wbytes);
-        // boundary candidates and their 1-ring
-        CK(cudaMemsetAsync(ctx->d_count, 0, sizeof(unsigned int), s));
-        ev = ctx->prof.begin(s);
-        CK(launch_dilate_select(ctx->cand, ctx->eval, ctx->conf[1], N, ctx->list, ctx->d_count, s));
-        ctx->prof.end(PIFU_K_SELECT, ev, s, 0.0, 4.0 * wbytes);
+        cudaEvent_t ev;
+        if (subdiv == PIFU_SUBDIV_THRESHOLD) {
+            // the coarser level's continuous values, read while this level's
+            // are written
+            const int64_t nc = (int64_t)(N / 2 + 1) * (N / 2 + 1) * (N / 2 + 1);
+            st = ensure_prev_values(ctx, nc);
+            if (st != PIFU_OK) return st;
+            CK(cudaMemcpyAsync(ctx->prev_values, ctx->values, (size_t)nc * 4,
+                               cudaMemcpyDeviceToDevice, s));
+            CK(cudaMemsetAsync(ctx->d_count, 0, sizeof(unsigned int), s));
+            ev = ctx->prof.begin(s);
+            CK(launch_threshold_select(ctx->prev_values, N, lv->threshold, ctx->values, ctx->tent,
+                                       ctx->bin[cur], ctx->eval, ctx->conf[0], ctx->list,
+                                       ctx->d_count, s));
+            ctx->prof.end(PIFU_K_SELECT, ev, s, 0.0,
+                          4.0 * nc + 4.0 * (double)(N + 1) * (N + 1) * (N + 1) + 4.0 * wbytes);
+            CK(launch_popcount(ctx->eval, words_of(N), ctx->d_pop + l, s));
+        } else {
+            ev = ctx->prof.begin(s);
+            CK(launch_classify(ctx->bin[prev], N, ctx->cand, ctx->tent, ctx->bin[cur], ctx->eval,
+                               ctx->conf[0], s));
+            ctx->prof.end(PIFU_K_LEVEL, ev, s, 0.0, 4.0 * words_of(N / 2) + 5.0 * wbytes);
+            ev = ctx->prof.begin(s);
+            CK(launch_popcount(ctx->cand, words_of(N), ctx->d_pop + l, s));
+            ctx->prof.end(PIFU_K_LEVEL, ev, s, 0.0, wbytes);
+            CK(cudaMemsetAsync(ctx->d_count, 0, sizeof(unsigned int), s));
+            ev = ctx->prof.begin(s);
+            if (subdiv == PIFU_SUBDIV_BINARIZED)   // the candidates alone
+                CK(launch_select(ctx->cand, ctx->eval, N, ctx->list, ctx->d_count, s));
+            else                                   // boundary candidates and their 1-ring
+                CK(launch_dilate_select(ctx->cand, ctx->eval, ctx->conf[1], N, ctx->list,
+                                        ctx->d_count, s));
+            ctx->prof.end(PIFU_K_SELECT, ev, s, 0.0, 4.0 * wbytes);
+        }
         unsigned int n = 0;
         st = read_count(ctx, s, &n);
         if (st != PIFU_OK) return st;
         ctx->prof.k[PIFU_K_SELECT].bytes += 4.0 * n;   // the list it wrote
+        if (subdiv != PIFU_SUBDIV_METHOD) {
+            // octree baselines: one pass, no conflict rounds
+            if (n > 0) {
+                PointSrc src{PTS_LIST, nullptr, ctx->list, 0, N};
+                Epilogue epi{};
+                epi.mode = EPI_LEVEL;
+                epi.list = ctx->list;
+                epi.lv = LevelBits{ctx->values, ctx->tent, ctx->bin[cur], ctx->conf[0], N, rw, 0};
+                st = eval_level_batch(ctx, src, n, map, cal, epi, prec, lv->margin, false, 0.f, s,
+                                      &vs.rechecked_per_level[l], &vs.fallback_per_level[l]);
+                if (st != PIFU_OK) return st;
+            }
+            vs.evals_per_level[l] = n;
+            vs.n_eval += n;
+            continue;
+        }
         int64_t level_evals = 0;
         int q = 0;     // conflicts of the next evaluation go to conf[q]
         int rounds = 0;
@@ -2674,6 +2729,7 @@ int pifu_frame(pifu_ctx* ctx, const pifu_fmap* occ_map, const pifu_fmap* col_map
         (cam->final_level != 1 || cam->width != cam->height || !is_pow2(cam->width)))
         return PIFU_ERR_ARG;
     if (!prec_valid(lv->precision) || lv->precision == PIFU_PREC_FP32) return PIFU_ERR_UNSUPPORTED;
+    if (lv->subdivision != PIFU_SUBDIV_METHOD) return PIFU_ERR_UNSUPPORTED;
     if (prec_f8(lv->precision) && !ctx->net[0].f8_ok) return PIFU_ERR_STATE;
     if (prec_mixed(lv->precision) && !(lv->margin >= 0.f && lv->margin <= 0.5f))
         return PIFU_ERR_ARG;
@@ -2812,6 +2868,7 @@ int pifu_frames(pifu_ctx* ctx, int B, const pifu_fmap* occ_maps, const pifu_fmap
     const int64_t npix = (int64_t)cam->width * cam->height;
     if ((int64_t)B * npix > kTcRowsMax) return PIFU_ERR_CAPACITY;
     if (!prec_valid(lv->precision) || lv->precision == PIFU_PREC_FP32) return PIFU_ERR_UNSUPPORTED;
+    if (lv->subdivision != PIFU_SUBDIV_METHOD) return PIFU_ERR_UNSUPPORTED;
     if (prec_f8(lv->precision) && !ctx->net[0].f8_ok) return PIFU_ERR_STATE;
     if (prec_mixed(lv->precision) && !(lv->margin >= 0.f && lv->margin <= 0.5f))
         return PIFU_ERR_ARG;

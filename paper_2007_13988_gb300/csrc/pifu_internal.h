@@ -261,6 +261,20 @@ cudaError_t launch_dilate_select(const uint32_t* src, uint32_t* eval, uint32_t* 
                                  int* list, unsigned int* count, cudaStream_t stream,
                                  int slots = 1, int64_t fslot = 0, int64_t slot_nodes = 0);
 
+// src & ~eval (no dilation); eval |= it; append the node indices to list.
+cudaError_t launch_select(const uint32_t* src, uint32_t* eval, int N, int* list,
+                          unsigned int* count, cudaStream_t stream);
+
+// Threshold subdivision (octree baseline of Fig. 3) of an N-cell level from
+// the dense continuous values of the N/2-cell level: values = the tri-linear
+// interpolation of the coarse values; tent = bin = (values >= 1/2);
+// eval = the nodes whose coarse corners deviate from their mean by more
+// than thr, also appended to list at *count; conf0 cleared.
+cudaError_t launch_threshold_select(const float* coarse, int N, float thr, float* values,
+                                    uint32_t* tent, uint32_t* bin, uint32_t* eval,
+                                    uint32_t* conf0, int* list, unsigned int* count,
+                                    cudaStream_t stream);
+
 // Graph form: set the conditional handle to (*count > 0) within capacity
 // and round limits (count_round: this decision starts a conflict round).
 cudaError_t launch_loop_control(cudaGraphConditionalHandle h, const unsigned int* count,

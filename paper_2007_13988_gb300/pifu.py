@@ -33,6 +33,9 @@ PIFU_PREC_BF16 = 1
 PIFU_PREC_MIXED = 2
 PIFU_PREC_FP8_MIXED = 3
 PIFU_PREC_FP8 = 4
+PIFU_SUBDIV_METHOD = 0
+PIFU_SUBDIV_BINARIZED = 1
+PIFU_SUBDIV_THRESHOLD = 2
 
 # Every symbol include/pifu.h declares.
 EXPORTS = ("pifu_create", "pifu_destroy", "pifu_query", "pifu_query_colour", "pifu_localize",
@@ -56,7 +59,8 @@ class pifu_levels(ctypes.Structure):
     _fields_ = [("n0", ctypes.c_int32), ("num_levels", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("max_rounds", ctypes.c_int32),
                 ("margin", ctypes.c_float), ("use_surrogate", ctypes.c_int32),
-                ("surrogate_margin", ctypes.c_float)]
+                ("surrogate_margin", ctypes.c_float), ("subdivision", ctypes.c_int32),
+                ("threshold", ctypes.c_float)]
 
 
 class pifu_camera(ctypes.Structure):
@@ -295,10 +299,12 @@ def pifu_query_colour(ctx, occ_map, col_map, calib, pts, out, stream=None):
 
 def pifu_localize(ctx, occ_map, calib, n0, num_levels, precision=PIFU_PREC_FP32,
                   max_rounds=0, margin=0.02, use_surrogate=False, surrogate_margin=0.1,
-                  stream=None) -> pifu_volume:
+                  stream=None, subdivision=PIFU_SUBDIV_METHOD, threshold=0.0) -> pifu_volume:
+    """subdivision: PIFU_SUBDIV_METHOD (Sec. 3.2), or one of the octree
+    baselines of Fig. 3 (BINARIZED; THRESHOLD with `threshold`)."""
     fm = fmap(occ_map)
     lv = pifu_levels(n0, num_levels, precision, max_rounds, margin, 1 if use_surrogate else 0,
-                     surrogate_margin)
+                     surrogate_margin, subdivision, threshold)
     vol = pifu_volume()
     st = _lib().pifu_localize(ctx, ctypes.byref(fm), _calib(calib), ctypes.byref(lv),
                               _stream(stream), ctypes.byref(vol))
