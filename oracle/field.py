@@ -16,9 +16,15 @@ Readings where the paper is silent (each also listed in the design notes):
   states LeakyReLU for f_T without a slope), sigmoid on f_O's output, tanh on
   f_T's output mapped to [0, 1] as (t + 1) / 2.
 
+* The paper's final f_O (Appendix) lifts the feature with conditional batch
+  normalization and takes the depth as a soft one-hot vector (Eq. 7, Eq. 8):
+  ``soft_z`` and ``cbn_mlp``.
+
 Pins: tests/test_oracle_field.py (texel-centre sampling returns stored values,
 a map linear in (u, v) is reproduced exactly, border clamping, MLP against an
-explicit per-neuron loop, the Table A1 flop count).
+explicit per-neuron loop, the Table A1 flop count; SoftZ closed forms,
+batch-normalization statistics, a hand-built CBN network, the constructed
+CBN network's closed form).
 """
 from __future__ import annotations
 
@@ -90,15 +96,54 @@ def sigmoid(t):
     return 1.0 / (1.0 + np.exp(-t))
 
 
+def soft_z(pz, n):
+    """Soft one-hot depth Z (Appendix, "Depth Representation", Eq. 7): with
+    P'_z = (P_z + 1) / 2 and x = (n - 1) P'_z, Z_i = 1 + floor(x) - x at
+    i = floor(x), x - floor(x) at i = floor(x) + 1, 0 elsewhere.
+    Readings: P'_z is clamped to [0, 1] (Eq. 7 is stated for -1 <= P_z <= 1);
+    at P'_z = 1 the second index is n, whose weight is 0, and is dropped."""
+    p = np.clip(0.5 * (np.asarray(pz, dtype=F64) + 1.0), 0.0, 1.0)
+    x = (n - 1) * p
+    i = np.floor(x).astype(np.int64)
+    Z = np.zeros((len(p), n), dtype=F64)
+    rows = np.arange(len(p))
+    Z[rows, i] = 1.0 + i - x
+    k = i + 1 < n
+    Z[rows[k], i[k] + 1] = x[k] - i[k]
+    return Z
+
+
+def cbn_mlp(net, c, Z):
+    """The CBN lifting of the Appendix ("Pixel-aligned 3D Lifting", Eq. 8) in
+    float64; returns the logit.  h_0 = Wz Z + bz; block i normalizes its
+    input with the running statistics, f = gamma_i(c) (h - mu_i) /
+    sqrt(var_i + eps) + beta_i(c) with gamma_i(c) = Gg_i c + gg_i and
+    beta_i(c) = Gb_i c + gb_i, applies ReLU, then its linear layer."""
+    c = np.asarray(c, dtype=F64)
+    h = np.asarray(Z, dtype=F64) @ np.asarray(net.Wz, F64).T + np.asarray(net.bz, F64)
+    for i in range(net.n_blocks):
+        norm = (h - np.asarray(net.mu[i], F64)) / np.sqrt(np.asarray(net.var[i], F64) + net.eps)
+        gamma = c @ np.asarray(net.Gg[i], F64).T + np.asarray(net.gg[i], F64)
+        beta = c @ np.asarray(net.Gb[i], F64).T + np.asarray(net.gb[i], F64)
+        a = np.maximum(gamma * norm + beta, 0.0)
+        h = a @ np.asarray(net.W[i], F64).T + np.asarray(net.b[i], F64)
+    return h
+
+
 def occupancy_logit(net, occ_map, calib, P, chunk=8192):
-    """Pre-sigmoid value of f_O at points P [M, 3] (Eq. 1)."""
+    """Pre-sigmoid value of f_O at points P [M, 3] (Eq. 1): the concatenation
+    MLP on [phi, P_z], or (a network of kind "cbn") the CBN lifting
+    conditioned on phi with the SoftZ depth."""
     P = np.asarray(P, dtype=F64).reshape(-1, 3)
     out = np.empty(len(P), dtype=F64)
     for s in range(0, len(P), chunk):
         u, v, z = project(calib, P[s:s + chunk])
         phi = sample_bilinear(occ_map, u, v)
-        x = np.concatenate([phi, z[:, None]], axis=1)
-        out[s:s + chunk] = mlp(net, x)[:, 0]
+        if getattr(net, "kind", "mlp") == "cbn":
+            out[s:s + chunk] = cbn_mlp(net, phi, soft_z(z, net.n_z))[:, 0]
+        else:
+            x = np.concatenate([phi, z[:, None]], axis=1)
+            out[s:s + chunk] = mlp(net, x)[:, 0]
     return out
 
 

@@ -501,6 +501,178 @@ def colour_net(d_in: int, widths, skip, seed: int) -> Net:
     return Net(d_in=d_in, widths=widths, skip=tuple(skip), W=Ws, b=bs, out_act="tanh01")
 
 
+@dataclasses.dataclass
+class CbnNet:
+    """f_O of the paper's final model (Appendix, "Depth Representation" and
+    "Pixel-aligned 3D Lifting"): the depth P_z enters as its soft one-hot
+    vector Z of ``n_z`` channels (Eq. 7) through a linear layer of ``width``
+    outputs, followed by ``n_blocks`` blocks of conditional batch
+    normalization (Eq. 8) with gamma(c) = Gg c + gg and beta(c) = Gb c + gb
+    linear in the pixel-aligned feature c, ReLU, and a linear layer; the last
+    block's linear layer has one output, the logit.  mu / var are the
+    normalization's running statistics (inference)."""
+
+    C: int
+    n_z: int
+    width: int
+    Wz: np.ndarray          # [width][n_z]
+    bz: np.ndarray          # [width]
+    Gg: list                # per block [width][C]
+    gg: list                # per block [width]
+    Gb: list                # per block [width][C]
+    gb: list                # per block [width]
+    mu: list                # per block [width]
+    var: list               # per block [width]
+    W: list                 # per block [width][width], the last [1][width]
+    b: list                 # per block [width], the last [1]
+    eps: float = 1e-5
+    out_act: str = "sigmoid"
+    kind: str = "cbn"
+
+    @property
+    def n_blocks(self) -> int:
+        return len(self.W)
+
+    @property
+    def n_params(self) -> int:
+        arrs = [self.Wz, self.bz] + self.Gg + self.gg + self.Gb + self.gb + self.W + self.b
+        return sum(a.size for a in arrs)
+
+    def flops_per_point(self) -> int:
+        mats = [self.Wz] + self.Gg + self.Gb + self.W
+        return sum(2 * m.shape[0] * m.shape[1] for m in mats)
+
+
+def occupancy_cbn_net(C: int, seed: int, logit_scale: float, width: int = 128,
+                      n_blocks: int = 5, n_z: int = 64, noise_logit: float = 0.25,
+                      carriers: int = 8, mask_gain: float = 1.0) -> CbnNet:
+    """Constructed CBN + SoftZ occupancy network whose 0.5 level set follows
+    the figure: its logit is ``logit_scale * M`` plus a texel-scale random
+    perturbation, M = min(f - z, z - b, mask_gain (mask - 1/2)) as in
+    ``occupancy_net``.
+
+    Conditional batch normalization acts channel by channel, so a carrier unit
+    of block i reads channel u of h_{i-1} (normalized with the running
+    statistics) scaled by a constant gamma, plus beta(c), linear in the
+    feature; ReLU pairs carry values as in ``occupancy_net`` (slope 0:
+    r(t) - r(-t) = t, r(t) + r(-t) = |t|):
+
+    * the SoftZ layer gives z exactly on the channels whose Wz row is
+      zeta (2 j / (n_z - 1) - 1) (the two weights of Z sum to 1 and their
+      centroid is (n_z - 1) P'_z);
+    * block 1 carries A = f - b and Cm = mask_gain (mask - 1/2) through beta
+      alone and B = f + b - 2z through gamma z + beta;
+    * the linear layer after it forms S = m + Cm and D = m - Cm,
+      m = A/2 - |B|/2, block 2 carries them, and M = S/2 - |D|/2;
+    * blocks 3 .. n_blocks pass M on; the last linear layer reads it out.
+
+    Every unit pair is replicated ``carriers`` times with gains in [0.5, 1.5];
+    the other units are random (gamma near 1, small beta(c), Kaiming linear
+    layers, running statistics mu in [-0.2, 0.2], var in [0.5, 1.5])."""
+    rng = np.random.default_rng(seed)
+    R = carriers
+    K = width
+    assert 6 * R <= K and n_blocks >= 3
+    relu_gain = math.sqrt(2.0)
+    Wz = _kaiming_uniform(rng, K, n_z, relu_gain)
+    bz = rng.uniform(-0.1, 0.1, size=K)
+    Gg, gg, Gb, gb, mu, var, W, b = [], [], [], [], [], [], [], []
+    for i in range(n_blocks):
+        Gg.append(0.1 * rng.uniform(-1, 1, size=(K, C)) * math.sqrt(3.0 / C))
+        gg.append(np.ones(K))
+        Gb.append(0.1 * rng.uniform(-1, 1, size=(K, C)) * math.sqrt(3.0 / C))
+        gb.append(rng.uniform(-0.1, 0.1, size=K))
+        mu.append(rng.uniform(-0.2, 0.2, size=K))
+        var.append(rng.uniform(0.5, 1.5, size=K))
+        if i < n_blocks - 1:
+            W.append(_kaiming_uniform(rng, K, K, relu_gain))
+            b.append(rng.uniform(-0.1, 0.1, size=K))
+        else:
+            W.append(np.zeros((1, K)))
+            b.append(np.zeros(1))
+    # float32 running statistics: the construction's constants use the
+    # stored values
+    mu = [m.astype(np.float32).astype(np.float64) for m in mu]
+    var = [v.astype(np.float32).astype(np.float64) for v in var]
+    scale = [1.0 / np.sqrt(v + 1e-5) for v in var]
+
+    def constant_gamma(i, u, gamma, beta):
+        Gg[i][u, :] = 0.0
+        gg[i][u] = gamma
+        Gb[i][u, :] = 0.0
+        gb[i][u] = beta
+
+    def readouts(first, gains):
+        """Signed and magnitude read-outs (length K) of the R pairs at units
+        first .. first + 2R (first R the + units)."""
+        signed = np.zeros(K)
+        mag = np.zeros(K)
+        for r in range(R):
+            signed[first + r] = 1.0 / (gains[r] * R)
+            signed[first + R + r] = -1.0 / (gains[r] * R)
+            mag[first + r] = 1.0 / (gains[r] * R)
+            mag[first + R + r] = 1.0 / (gains[r] * R)
+        return signed, mag
+
+    # block 0 (the first CBN block)
+    gA, gB, gC = (rng.uniform(0.5, 1.5, size=R) for _ in range(3))
+    for r in range(R):
+        for sgn, off in ((1.0, 0), (-1.0, R)):
+            u = off + r                       # A = f - b through beta
+            constant_gamma(0, u, 0.0, 0.0)
+            Gb[0][u, 0], Gb[0][u, 1] = sgn * gA[r], -sgn * gA[r]
+            u = 2 * R + off + r               # B = f + b - 2z
+            zeta = rng.uniform(0.5, 1.5)
+            Wz[u, :] = zeta * (2.0 * np.arange(n_z) / (n_z - 1) - 1.0)
+            bz[u] = 0.0
+            gam = -2.0 * sgn * gB[r] / (scale[0][u] * zeta)
+            constant_gamma(0, u, gam, -2.0 * sgn * gB[r] * mu[0][u] / zeta)
+            Gb[0][u, 0], Gb[0][u, 1] = sgn * gB[r], sgn * gB[r]
+            u = 4 * R + off + r               # Cm = mask_gain (mask - 1/2)
+            constant_gamma(0, u, 0.0, -0.5 * sgn * gC[r] * mask_gain)
+            Gb[0][u, 2] = sgn * gC[r] * mask_gain
+    A_s, _ = readouts(0, gA)
+    _, B_m = readouts(2 * R, gB)
+    C_s, _ = readouts(4 * R, gC)
+    m_lin = 0.5 * A_s - 0.5 * B_m
+    forms = [m_lin + C_s, m_lin - C_s]        # S, D over block 0's units
+
+    def carry(i, form_rows):
+        """Linear layer i - 1 writes each form of form_rows onto 2R channels
+        (gains lambda); block i carries it in R +/- pairs; returns the
+        read-out gains."""
+        gains = []
+        for q, form in enumerate(form_rows):
+            g = rng.uniform(0.5, 1.5, size=R)
+            gains.append(g)
+            for r in range(R):
+                for sgn, off in ((1.0, 0), (-1.0, R)):
+                    u = 2 * R * q + off + r
+                    lam = rng.uniform(0.5, 1.5)
+                    W[i - 1][u, :] = lam * form
+                    b[i - 1][u] = 0.0
+                    constant_gamma(i, u, sgn * g[r] / (scale[i][u] * lam),
+                                   sgn * g[r] * mu[i][u] / lam)
+        return gains
+
+    gS, gD = carry(1, forms)
+    S_s, _ = readouts(0, gS)
+    _, D_m = readouts(2 * R, gD)
+    M_lin = 0.5 * S_s - 0.5 * D_m
+    for i in range(2, n_blocks):
+        (gM,) = carry(i, [M_lin])
+        M_lin, _ = readouts(0, gM)
+    n_rand = K - 2 * R
+    proj = rng.uniform(-1.0, 1.0, size=n_rand) * math.sqrt(3.0 / n_rand)
+    W[-1][0, :] = logit_scale * M_lin
+    W[-1][0, 2 * R:] += noise_logit * proj
+    f32 = lambda a: np.ascontiguousarray(a, dtype=np.float32)
+    return CbnNet(C=C, n_z=n_z, width=K, Wz=f32(Wz), bz=f32(bz), Gg=[f32(a) for a in Gg],
+                  gg=[f32(a) for a in gg], Gb=[f32(a) for a in Gb], gb=[f32(a) for a in gb],
+                  mu=[f32(a) for a in mu], var=[f32(a) for a in var], W=[f32(a) for a in W],
+                  b=[f32(a) for a in b])
+
+
 # --------------------------------------------------------------------------
 # Workload presets
 # --------------------------------------------------------------------------
@@ -547,3 +719,25 @@ def full(seed: int = 0, calib=None, num_levels: int = 4, n0: int = 32, render: i
     return Workload(f"full {n0}^3->{n_fine}^3, {render}^2 render, C=256 FP32", fig, occ, col,
                     calib_identity() if calib is None else calib, onet, cnet,
                     n0=n0, num_levels=num_levels, render=render)
+
+
+def tiny_cbn(seed: int = 0, calib=None) -> Workload:
+    """The tiny workload with the CBN + SoftZ f_O (C = 32, width 64, four
+    blocks, n_z = 64), levels 16 -> 32 -> 64, 64x64 render."""
+    w = tiny(seed, calib)
+    w.occ_net = occupancy_cbn_net(32, seed + 12, logit_scale=0.65 * 64, width=64, n_blocks=4,
+                                  carriers=4)
+    w.name = "tiny CBN+SoftZ 16^3->64^3, 64^2 render, C=32 FP32"
+    return w
+
+
+def full_cbn(seed: int = 0, calib=None, num_levels: int = 4, n0: int = 32,
+             render: int = 512) -> Workload:
+    """The full-size frame with the paper's final f_O: SoftZ (64) -> 128, five
+    CBN blocks of 128 channels conditioned on the 256-channel feature, one
+    output; the colour MLP and the maps are those of ``full``."""
+    w = full(seed, calib, num_levels, n0, render)
+    n_fine = n0 << (num_levels - 1)
+    w.occ_net = occupancy_cbn_net(256, seed + 12, logit_scale=0.65 * n_fine)
+    w.name = f"full CBN+SoftZ {n0}^3->{n_fine}^3, {render}^2 render, C=256 FP32"
+    return w

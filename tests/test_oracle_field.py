@@ -207,3 +207,152 @@ def test_colour_input_order():
     net = _Net(6, [Wt], [np.zeros(3)])
     rgb = field.colour(net, O, T, synth.calib_identity(), np.array([[0.0, 0.0, 0.75]]))
     np.testing.assert_allclose(rgb[0], (np.tanh([0.25, -0.5, 0.75]) + 1) / 2, atol=1e-15)
+
+
+# ---- CBN + SoftZ (Appendix, Eq. 7 and Eq. 8) ------------------------------------
+
+def test_soft_z_closed_forms():
+    n = 64
+    # Eq. 7's two weights are the linear "hat" basis of the n nodes x = 0..n-1
+    # at x = (n - 1) (P_z + 1) / 2: Z_i = max(0, 1 - |x - i|)
+    pz = np.concatenate([np.linspace(-1, 1, 1001), [-1.0, 1.0, 0.0]])
+    Z = field.soft_z(pz, n)
+    x = (n - 1) * (pz + 1) / 2
+    hat = np.maximum(0.0, 1.0 - np.abs(x[:, None] - np.arange(n)[None, :]))
+    np.testing.assert_allclose(Z, hat, rtol=0, atol=1e-12)
+    np.testing.assert_allclose(Z.sum(axis=1), 1.0, atol=1e-12)
+    assert np.count_nonzero(Z, axis=1).max() <= 2
+    # the centroid recovers the depth: sum_i (2 i / (n - 1) - 1) Z_i = P_z
+    np.testing.assert_allclose(Z @ (2 * np.arange(n) / (n - 1) - 1), pz, atol=1e-12)
+    # end points and the midpoint, worked by hand
+    assert Z[-3, 0] == 1.0 and Z[-2, n - 1] == 1.0
+    assert Z[-1, 31] == 0.5 and Z[-1, 32] == 0.5
+    # outside [-1, 1] the depth is clamped (reading)
+    np.testing.assert_array_equal(field.soft_z([1.5, -3.0], n), field.soft_z([1.0, -1.0], n))
+    # a small case by hand: n = 5, P_z = -0.5 -> x = 1 exactly; P_z = 0.25 -> x = 2.5
+    Z5 = field.soft_z([-0.5, 0.25], 5)
+    np.testing.assert_array_equal(Z5, [[0, 1, 0, 0, 0], [0, 0, 0.5, 0.5, 0]])
+
+
+class _Cbn:
+    def __init__(self, **kw):
+        self.__dict__.update(kw)
+        self.kind = "cbn"
+        self.n_blocks = len(self.W)
+
+
+def test_cbn_hand_built():
+    """Two channels, one-dimensional feature c, n_z = 3, two blocks, worked
+    by hand.  var = 1e-5 makes eps matter (scale 1/sqrt(2e-5))."""
+    net = _Cbn(C=1, n_z=3, width=2, eps=1e-5,
+               Wz=np.array([[1.0, 2.0, 3.0], [0.0, 0.0, 1.0]]), bz=np.array([0.5, -1.0]),
+               Gg=[np.array([[1.0], [0.0]]), np.array([[0.0], [2.0]])],
+               gg=[np.array([0.0, 1.0]), np.array([1.0, 0.5])],
+               Gb=[np.array([[0.0], [1.0]]), np.array([[-1.0], [0.0]])],
+               gb=[np.array([0.25, 0.0]), np.array([0.0, 0.1])],
+               mu=[np.array([1.0, -1.0]), np.array([0.0, 2.0])],
+               var=[np.array([3.0 - 1e-5, 1e-5]), np.array([1.0 - 1e-5, 4.0 - 1e-5])],
+               W=[np.array([[1.0, -1.0], [2.0, 0.0]]), np.array([[1.0, 1.0]])],
+               b=[np.array([0.0, 1.0]), np.array([-0.5])])
+    c = np.array([[2.0]])
+    Z = np.array([[0.0, 0.5, 0.5]])
+    # h0 = [1*0 + 2*.5 + 3*.5 + .5, .5 - 1] = [3, -0.5]
+    # block 0: norm = [(3 - 1)/sqrt(3), (-0.5 + 1)/sqrt(2e-5)]
+    #          gamma = [2, 1], beta = [0.25, 2]
+    n0 = (3.0 - 1.0) / math.sqrt(3.0)
+    n1 = 0.5 / math.sqrt(2e-5)
+    a = [max(2 * n0 + 0.25, 0.0), max(1 * n1 + 2.0, 0.0)]
+    h1 = [a[0] - a[1], 2 * a[0] + 1.0]
+    # block 1: norm = [h1_0 / 1, (h1_1 - 2) / 2]; gamma = [1, 4.5]; beta = [-2, 0.1]
+    a2 = [max(1.0 * h1[0] - 2.0, 0.0), max(4.5 * (h1[1] - 2.0) / 2.0 + 0.1, 0.0)]
+    want = a2[0] + a2[1] - 0.5
+    assert abs(field.cbn_mlp(net, c, Z)[0, 0] - want) <= 1e-12 * max(1.0, abs(want))
+    # a second input where the first channel's ReLU cuts: c = -1
+    # block 0: gamma = [-1, 1], beta = [0.25, -1]
+    c = np.array([[-1.0]])
+    a = [max(-1 * n0 + 0.25, 0.0), max(1 * n1 - 1.0, 0.0)]
+    h1 = [a[0] - a[1], 2 * a[0] + 1.0]
+    # block 1: gamma = [1, 2 (-1) + 0.5] = [1, -1.5]; beta = [1, 0.1]
+    a2 = [max(1.0 * h1[0] + 1.0, 0.0), max(-1.5 * (h1[1] - 2.0) / 2.0 + 0.1, 0.0)]
+    want = a2[0] + a2[1] - 0.5
+    assert abs(field.cbn_mlp(net, c, Z)[0, 0] - want) <= 1e-12 * max(1.0, abs(want))
+
+
+def test_cbn_batch_statistics():
+    """With the running statistics equal to a batch's own mean and variance,
+    gamma(c) = 1 and beta(c) = 0, the normalized batch has mean 0 and
+    variance var / (var + eps) per channel (read through a ReLU-free pair:
+    r(t) - r(-t) = t)."""
+    rng = np.random.default_rng(4)
+    n_z, K, C, M = 8, 3, 4, 4000
+    Wz = rng.standard_normal((K, n_z))
+    bz = rng.standard_normal(K)
+    Z = field.soft_z(rng.uniform(-1, 1, M), n_z)
+    h0 = Z @ Wz.T + bz
+    mu, var = h0.mean(axis=0), h0.var(axis=0)
+    # block 0 duplicates each channel with gamma +1 / -1; its linear layer
+    # takes the difference of each pair (= the normalized value)
+    Wz2 = np.concatenate([Wz, Wz])
+    net = _Cbn(C=C, n_z=n_z, width=2 * K, eps=1e-5, Wz=Wz2, bz=np.concatenate([bz, bz]),
+               Gg=[np.zeros((2 * K, C)), np.zeros((1, 2 * K))],
+               gg=[np.concatenate([np.ones(K), -np.ones(K)]), np.ones(1)],
+               Gb=[np.zeros((2 * K, C)), np.zeros((1, 2 * K))], gb=[np.zeros(2 * K), np.zeros(1)],
+               mu=[np.concatenate([mu, mu]), np.zeros(1)],
+               var=[np.concatenate([var, var]), np.ones(1)],
+               W=[np.concatenate([np.eye(K), -np.eye(K)], axis=1)], b=[np.zeros(K)])
+    net.n_blocks = 1
+    out = field.cbn_mlp(net, rng.standard_normal((M, C)), Z)
+    np.testing.assert_allclose(out.mean(axis=0), 0.0, atol=1e-12)
+    np.testing.assert_allclose(out.var(axis=0), var / (var + 1e-5), rtol=1e-12)
+
+
+@pytest.mark.parametrize("C,width,n_blocks,R", [(16, 64, 3, 4), (256, 128, 5, 8)])
+def test_constructed_cbn_network_computes_closed_form(C, width, n_blocks, R):
+    # logit = scale * min(f - z, z - b, mask - 1/2) by construction (ReLU pair
+    # identities, constant gamma compensating the running statistics, the
+    # SoftZ centroid).  The oracle's forward pass must reproduce it.
+    net = synth.occupancy_cbn_net(C, seed=6, logit_scale=7.0, width=width, n_blocks=n_blocks,
+                                  noise_logit=0.0, carriers=R)
+    rng = np.random.default_rng(9)
+    n = 500
+    c = rng.standard_normal((n, C))
+    c[:, 0] = rng.uniform(-1, 1, n)
+    c[:, 1] = c[:, 0] - rng.uniform(0, 0.6, n)
+    c[:, 2] = rng.uniform(0, 1, n)
+    z = rng.uniform(-1, 1, n)
+    f, b, m = c[:, 0], c[:, 1], c[:, 2]
+    want = 7.0 * np.minimum(np.minimum(f - z, z - b), m - 0.5)
+    got = field.cbn_mlp(net, c, field.soft_z(z, net.n_z))[:, 0]
+    np.testing.assert_allclose(got, want, rtol=0, atol=5e-5)
+
+
+def test_cbn_full_size_cost():
+    """Shapes of the paper's final f_O under the reading of the design notes:
+    SoftZ 64 -> 128, five CBN blocks of 128 channels conditioned on the
+    256-channel feature, 128-wide linear layers, one output.  Table A1 quotes
+    3.0 GFLOPS per 4096 calls; this reading costs 3.29 (the input layer and
+    the 128-wide linear layers cannot be dropped without contradicting the
+    text), within 10%."""
+    net = synth.occupancy_cbn_net(256, seed=0, logit_scale=1.0)
+    f = net.flops_per_point()
+    assert f == 2 * (64 * 128 + 5 * 2 * 256 * 128 + 4 * 128 * 128 + 128)
+    assert abs(f * 4096 / 1e9 - 3.0) / 3.0 < 0.10
+
+
+def test_cbn_occupancy_end_to_end_closed_form_at_texel_centres():
+    # the CBN + SoftZ f_O built to compute scale * min(f - z, z - b, mask - 1/2)
+    # (noise off), through projection, sampling and SoftZ at texel centres:
+    # pins the conditioning on phi and the depth path through Eq. 7
+    w = synth.tiny(0)
+    net = synth.occupancy_cbn_net(32, seed=4, logit_scale=9.0, width=64, n_blocks=4,
+                                  noise_logit=0.0, carriers=4)
+    rng = np.random.default_rng(5)
+    i = rng.integers(0, 64, 300)
+    j = rng.integers(0, 64, 300)
+    z = rng.uniform(-1, 1, 300)
+    u, v = texel_uv(i, j, 64, 64)
+    P = np.stack([u, v, z], 1)
+    F = w.occ_map.astype(np.float64)
+    want = 9.0 * np.minimum(np.minimum(F[j, i, 0] - z, z - F[j, i, 1]), F[j, i, 2] - 0.5)
+    got = field.occupancy(net, w.occ_map, w.calib, P)
+    np.testing.assert_allclose(got, 1 / (1 + np.exp(-want)), rtol=0, atol=1e-5)
