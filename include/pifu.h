@@ -165,7 +165,20 @@ typedef struct {
  * u32 n_layers, f32 leaky slope, u32 widths[n_layers], u32 skip_mask
  * (bit l: layer l reads [h_{l-1}, x]), then per layer f32 W[width][fan_in]
  * row-major and f32 b[width].  Hidden widths must be multiples of 8 and the
- * output width 1 (f_O) or 3 (f_T).  The blob is validated completely on the
+ * output width 1 (f_O) or 3 (f_T).
+ * The occupancy net may instead be the paper's final CBN + SoftZ network
+ * (Appendix, "Depth Representation", Eq. 7, and "Pixel-aligned 3D
+ * Lifting", Eq. 8): u32 kind = 2, u32 C (feature channels), u32 n_z (SoftZ
+ * channels), u32 K (width), u32 n_blocks, f32 eps, then f32 Wz[K][n_z],
+ * bz[K], and per block Gg[K][C], gg[K], Gb[K][C], gb[K], mu[K], var[K]
+ * (running statistics), W[K_out][K], b[K_out] with K_out = K except 1 for
+ * the last block.  The network computes h = Wz Z + bz, then per block
+ * a = ReLU((Gg c + gg) (h - mu) / sqrt(var + eps) + Gb c + gb), h = W a + b,
+ * and O = sigmoid(h).  Limits: C and K multiples of 8, n_z >= 2,
+ * n_blocks 1 .. 8.  Such a context serves pifu_query, pifu_query_ex (FP32,
+ * BF16, MIXED), pifu_localize and pifu_render (FP32, BF16, MIXED, no
+ * surrogate); the FP8 forms, the surrogate and the graph forms return
+ * PIFU_ERR_UNSUPPORTED.  The blob is validated completely on the
  * host before any CUDA call.  Errors: PIFU_ERR_FORMAT, PIFU_ERR_UNSUPPORTED
  * (hidden width not a multiple of 8), PIFU_ERR_OOM, PIFU_ERR_CUDA,
  * PIFU_ERR_ARG (null pointers). */

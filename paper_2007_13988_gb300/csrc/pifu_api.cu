@@ -75,6 +75,15 @@ struct DevNet {
     CUtensorMap tmX8{};             // E4M3 gather rows as the A operand
 };
 
+constexpr int kNetCbn = 2;   // DevNet.kind of the CBN + SoftZ occupancy network
+
+// Device copy of the CBN + SoftZ occupancy network (statistics folded).
+struct CbnDev {
+    bool ready = false;
+    std::vector<float*> bufs;   // every allocation, freed together
+    CbnF32 f32{};
+};
+
 bool prec_f8(int p) { return p == PIFU_PREC_FP8 || p == PIFU_PREC_FP8_MIXED; }
 bool prec_mixed(int p) { return p == PIFU_PREC_MIXED || p == PIFU_PREC_FP8_MIXED; }
 bool prec_valid(int p) { return p >= PIFU_PREC_FP32 && p <= PIFU_PREC_FP8; }
@@ -261,6 +270,7 @@ struct BatchWs {
 struct pifu_ctx {
     int device = 0;
     DevNet net[2];
+    CbnDev cbn;           // net[0].kind == kNetCbn: the occupancy network
     std::string last_error;
     // MLP activation workspace (FP32 and BF16 forms)
     float* X = nullptr;
@@ -475,6 +485,123 @@ int parse_net(Reader& rd, HostNet& hn, int want_kind) {
         std::memcpy(hn.b[l].data(), b.data(), L.n_out * 4);
     }
     return PIFU_OK;
+}
+
+// Host copy of the CBN + SoftZ occupancy network with every block's running
+// statistics folded into the linear layer before it: with
+// s_i = 1 / sqrt(var_i + eps), block i's normalized input is
+// s_i (W a + b - mu_i) = (s_i W) a + s_i (b - mu_i).
+struct HostCbn {
+    int C = 0, n_z = 0, K = 0, nb = 0;
+    std::vector<float> WzT, bz, Gt, g0, WT, bl, wlast, blast;
+};
+
+int parse_cbn(Reader& rd, HostCbn& h) {
+    uint32_t kind, C, n_z, K, nb;
+    float eps;
+    if (!rd.u32(kind) || !rd.u32(C) || !rd.u32(n_z) || !rd.u32(K) || !rd.u32(nb) || !rd.f32(eps))
+        return PIFU_ERR_FORMAT;
+    if (kind != (uint32_t)kNetCbn || C == 0 || C > 4096 || n_z < 2 || n_z > 4096 || K == 0 ||
+        K > 1024 || nb == 0 || nb > 8 || !(eps >= 0.f && eps < 1.f))
+        return PIFU_ERR_FORMAT;
+    if (C % 8 != 0 || K % 8 != 0) return PIFU_ERR_UNSUPPORTED;
+    auto vec = [&rd](std::vector<float>& v, size_t n) {
+        v.resize(n);
+        return rd.get(v.data(), n * 4);
+    };
+    std::vector<float> Wz, bz;
+    if (!vec(Wz, (size_t)K * n_z) || !vec(bz, K)) return PIFU_ERR_FORMAT;
+    std::vector<std::vector<float>> Gg(nb), gg(nb), Gb(nb), gb(nb), mu(nb), var(nb), W(nb), b(nb);
+    for (uint32_t i = 0; i < nb; ++i) {
+        const size_t kout = i + 1 < nb ? K : 1;
+        if (!vec(Gg[i], (size_t)K * C) || !vec(gg[i], K) || !vec(Gb[i], (size_t)K * C) ||
+            !vec(gb[i], K) || !vec(mu[i], K) || !vec(var[i], K) || !vec(W[i], kout * K) ||
+            !vec(b[i], kout))
+            return PIFU_ERR_FORMAT;
+        for (float v : var[i])
+            if (!(v + eps > 0.f) || !std::isfinite(v)) return PIFU_ERR_FORMAT;
+    }
+    std::vector<std::vector<double>> sc(nb, std::vector<double>(K));
+    for (uint32_t i = 0; i < nb; ++i)
+        for (uint32_t k = 0; k < K; ++k) sc[i][k] = 1.0 / std::sqrt((double)var[i][k] + (double)eps);
+    h.C = (int)C;
+    h.n_z = (int)n_z;
+    h.K = (int)K;
+    h.nb = (int)nb;
+    h.WzT.assign((size_t)n_z * K, 0.f);
+    h.bz.assign(K, 0.f);
+    for (uint32_t k = 0; k < K; ++k) {
+        for (uint32_t j = 0; j < n_z; ++j)
+            h.WzT[(size_t)j * K + k] = (float)(sc[0][k] * Wz[(size_t)k * n_z + j]);
+        h.bz[k] = (float)(sc[0][k] * ((double)bz[k] - mu[0][k]));
+    }
+    const size_t K2 = 2 * (size_t)K;
+    h.Gt.assign(nb * C * K2, 0.f);
+    h.g0.assign(nb * K2, 0.f);
+    for (uint32_t i = 0; i < nb; ++i)
+        for (size_t o = 0; o < K2; ++o) {
+            const bool gam = o < K;
+            const std::vector<float>& G = gam ? Gg[i] : Gb[i];
+            const size_t row = gam ? o : o - K;
+            for (uint32_t c = 0; c < C; ++c) h.Gt[(i * C + c) * K2 + o] = G[row * C + c];
+            h.g0[i * K2 + o] = gam ? gg[i][row] : gb[i][row];
+        }
+    h.WT.assign((size_t)(nb - 1) * K * K, 0.f);
+    h.bl.assign((size_t)(nb - 1) * K, 0.f);
+    for (uint32_t i = 0; i + 1 < nb; ++i)
+        for (uint32_t o = 0; o < K; ++o) {
+            const double s1 = sc[i + 1][o];
+            for (uint32_t k = 0; k < K; ++k)
+                h.WT[((size_t)i * K + k) * K + o] = (float)(s1 * W[i][(size_t)o * K + k]);
+            h.bl[(size_t)i * K + o] = (float)(s1 * ((double)b[i][o] - mu[i + 1][o]));
+        }
+    h.wlast = W[nb - 1];
+    h.blast = {b[nb - 1][0], 0.f, 0.f, 0.f};
+    return PIFU_OK;
+}
+
+int upload_cbn(pifu_ctx* ctx, const HostCbn& h) {
+    CbnDev& d = ctx->cbn;
+    auto up = [&d](const std::vector<float>& v, const float** dst) -> cudaError_t {
+        float* p = nullptr;
+        cudaError_t e = dev_alloc(&p, (int64_t)std::max<size_t>(v.size(), 1));
+        if (e != cudaSuccess) return e;
+        d.bufs.push_back(p);
+        *dst = p;
+        return v.empty() ? cudaSuccess
+                         : cudaMemcpy(p, v.data(), v.size() * 4, cudaMemcpyHostToDevice);
+    };
+    CbnF32& f = d.f32;
+    CK(up(h.WzT, &f.WzT));
+    CK(up(h.bz, &f.bz));
+    CK(up(h.Gt, &f.Gt));
+    CK(up(h.g0, &f.g0));
+    CK(up(h.WT, &f.WT));
+    CK(up(h.bl, &f.bl));
+    CK(up(h.wlast, &f.wlast));
+    CK(up(h.blast, &f.blast));
+    f.C = h.C;
+    f.n_z = h.n_z;
+    f.K = h.K;
+    f.nb = h.nb;
+    if (!cbn_f32_ok(f)) return PIFU_ERR_UNSUPPORTED;
+    // the occupancy slot's shape: the depth is one input scalar as for the
+    // concatenation network; no layers of its own
+    DevNet& net = ctx->net[0];
+    net = DevNet{};
+    net.kind = kNetCbn;
+    net.d_in = h.C + 1;
+    net.ldx = round_up(h.C + 1, 8);
+    net.max_hidden = h.K;
+    d.ready = true;
+    return PIFU_OK;
+}
+
+void free_cbn(CbnDev& d) {
+    for (float* p : d.bufs) dev_free(p);
+    d.bufs.clear();
+    d.f32 = CbnF32{};
+    d.ready = false;
 }
 
 int upload_net(pifu_ctx* ctx, const HostNet& hn, DevNet& net) {
@@ -958,6 +1085,21 @@ int run_mlp_tc(pifu_ctx* ctx, const DevNet& net, const PointSrc& src_in, int64_t
 int run_mlp(pifu_ctx* ctx, const DevNet& net, const PointSrc& src_in, int64_t m, const Map& map0,
             const Map& map1, const Calib& calib, const Epilogue& epi, cudaStream_t s,
             int precision = PIFU_PREC_FP32, const unsigned int* m_dev = nullptr) {
+    if (net.kind == kNetCbn) {
+        if (precision != PIFU_PREC_FP32)
+            return run_mlp_tc(ctx, net, src_in, m, map0, map1, calib, epi, s, m_dev,
+                              precision == PIFU_PREC_FP8);
+        if (m_dev) return PIFU_ERR_UNSUPPORTED;
+        const CbnF32& f = ctx->cbn.f32;
+        const double flops = 2.0 * (double)m *
+                             ((double)f.n_z * f.K + 2.0 * f.nb * f.C * f.K +
+                              (double)(f.nb - 1) * f.K * f.K + f.K);
+        const double wbytes = 4.0 * ((double)f.n_z * f.K + f.nb * (2.0 * f.C * f.K + f.K * f.K));
+        cudaEvent_t ev = ctx->prof.begin(s);
+        CK(launch_cbn_f32(f, src_in, m, calib, map0, epi, s));
+        ctx->prof.end(PIFU_K_MLP_F32, ev, s, flops, wbytes + (double)m * 4.0 * (4.0 * map0.C + 1));
+        return PIFU_OK;
+    }
     if (precision == PIFU_PREC_BF16 || precision == PIFU_PREC_FP8)
         return run_mlp_tc(ctx, net, src_in, m, map0, map1, calib, epi, s, m_dev,
                           precision == PIFU_PREC_FP8);
@@ -2247,7 +2389,11 @@ int pifu_create(const void* weight_blob, size_t bytes, pifu_ctx** out) {
     if (!rd.get(magic, 4) || std::memcmp(magic, "PIFU", 4) != 0) return PIFU_ERR_FORMAT;
     if (!rd.u32(version) || version != 1 || !rd.u32(n_nets) || n_nets != 2) return PIFU_ERR_FORMAT;
     HostNet hn[2];
-    int st = parse_net(rd, hn[0], 0);
+    HostCbn hc;
+    uint32_t kind0 = 0;
+    if (rd.off + 4 <= rd.n) std::memcpy(&kind0, rd.p + rd.off, 4);
+    const bool cbn = kind0 == (uint32_t)kNetCbn;
+    int st = cbn ? parse_cbn(rd, hc) : parse_net(rd, hn[0], 0);
     if (st == PIFU_OK) st = parse_net(rd, hn[1], 1);
     if (st == PIFU_OK && rd.off != rd.n) st = PIFU_ERR_FORMAT;
     if (st != PIFU_OK) return st;
@@ -2256,10 +2402,10 @@ int pifu_create(const void* weight_blob, size_t bytes, pifu_ctx** out) {
         delete ctx;
         return PIFU_ERR_CUDA;
     }
-    st = upload_net(ctx, hn[0], ctx->net[0]);
+    st = cbn ? upload_cbn(ctx, hc) : upload_net(ctx, hn[0], ctx->net[0]);
     if (st == PIFU_OK) st = upload_net(ctx, hn[1], ctx->net[1]);
     if (st == PIFU_OK) st = ensure_mlp_ws(ctx);
-    if (st == PIFU_OK) st = build_tc(ctx, hn[0], ctx->net[0]);
+    if (st == PIFU_OK && !cbn) st = build_tc(ctx, hn[0], ctx->net[0]);
     if (st == PIFU_OK) st = build_tc(ctx, hn[1], ctx->net[1]);
     if (st == PIFU_OK) {
         cudaError_t e = cudaMalloc(&ctx->d_count, 2 * sizeof(unsigned int));
@@ -2304,6 +2450,7 @@ void pifu_destroy(pifu_ctx* ctx) {
         if (bw.h_stats) cudaFreeHost(bw.h_stats);
     }
     free_net(ctx->net[0]);
+    free_cbn(ctx->cbn);
     free_net(ctx->net[1]);
     dev_free(ctx->X);
     dev_free(ctx->HA);
@@ -2354,6 +2501,7 @@ int pifu_query_ex(pifu_ctx* ctx, const pifu_fmap* occ_map, const float calib[12]
                   void* stream) {
     if (!ctx || !calib || m < 0) return PIFU_ERR_ARG;
     if (!prec_valid(precision)) return PIFU_ERR_UNSUPPORTED;
+    if (ctx->net[0].kind == kNetCbn && prec_f8(precision)) return PIFU_ERR_UNSUPPORTED;
     if (prec_mixed(precision) && !(margin >= 0.f && margin <= 0.5f)) return PIFU_ERR_ARG;
     if (m == 0) return PIFU_OK;
     if (!pts_dev || !occ_dev || !map_ok(occ_map)) return PIFU_ERR_ARG;
@@ -2429,6 +2577,7 @@ int pifu_localize(pifu_ctx* ctx, const pifu_fmap* occ_map, const float calib[12]
     if (subdiv == PIFU_SUBDIV_THRESHOLD && !(lv->threshold >= 0.f && lv->threshold <= 1.f))
         return PIFU_ERR_ARG;
     if (subdiv != PIFU_SUBDIV_METHOD && use_sur) return PIFU_ERR_UNSUPPORTED;
+    if (ctx->net[0].kind == kNetCbn && (use_sur || prec_f8(prec))) return PIFU_ERR_UNSUPPORTED;
     const int max_rounds = lv->max_rounds > 0 ? lv->max_rounds : 4096;
     DeviceGuard g(ctx->device);
     if (!g.ok) return PIFU_ERR_CUDA;
@@ -2730,6 +2879,7 @@ int pifu_frame(pifu_ctx* ctx, const pifu_fmap* occ_map, const pifu_fmap* col_map
         return PIFU_ERR_ARG;
     if (!prec_valid(lv->precision) || lv->precision == PIFU_PREC_FP32) return PIFU_ERR_UNSUPPORTED;
     if (lv->subdivision != PIFU_SUBDIV_METHOD) return PIFU_ERR_UNSUPPORTED;
+    if (ctx->net[0].kind == kNetCbn) return PIFU_ERR_UNSUPPORTED;
     if (prec_f8(lv->precision) && !ctx->net[0].f8_ok) return PIFU_ERR_STATE;
     if (prec_mixed(lv->precision) && !(lv->margin >= 0.f && lv->margin <= 0.5f))
         return PIFU_ERR_ARG;
@@ -2835,6 +2985,7 @@ int pifu_calibrate_fp8(pifu_ctx* ctx, const pifu_fmap* occ_map, const float cali
                        void* stream) {
     if (!ctx || !calib || !map_ok(occ_map) || n0 < 1 || n0 > 256) return PIFU_ERR_ARG;
     if (ctx->net[0].d_in != occ_map->C + 1) return PIFU_ERR_ARG;
+    if (ctx->net[0].kind == kNetCbn) return PIFU_ERR_UNSUPPORTED;
     DeviceGuard g(ctx->device);
     if (!g.ok) return PIFU_ERR_CUDA;
     ctx->g_valid = false;   // a captured frame holds the previous scales
@@ -2869,6 +3020,7 @@ int pifu_frames(pifu_ctx* ctx, int B, const pifu_fmap* occ_maps, const pifu_fmap
     if ((int64_t)B * npix > kTcRowsMax) return PIFU_ERR_CAPACITY;
     if (!prec_valid(lv->precision) || lv->precision == PIFU_PREC_FP32) return PIFU_ERR_UNSUPPORTED;
     if (lv->subdivision != PIFU_SUBDIV_METHOD) return PIFU_ERR_UNSUPPORTED;
+    if (ctx->net[0].kind == kNetCbn) return PIFU_ERR_UNSUPPORTED;
     if (prec_f8(lv->precision) && !ctx->net[0].f8_ok) return PIFU_ERR_STATE;
     if (prec_mixed(lv->precision) && !(lv->margin >= 0.f && lv->margin <= 0.5f))
         return PIFU_ERR_ARG;

@@ -196,7 +196,17 @@ def load():
 def blob_from_nets(occ_net, col_net) -> bytes:
     """Serialise the occupancy and colour MLPs into the library's blob."""
     parts = [b"PIFU", struct.pack("<II", 1, 2)]
+    f4 = lambda a: np.ascontiguousarray(a, dtype="<f4").tobytes()
     for kind, net in ((0, occ_net), (1, col_net)):
+        if getattr(net, "kind", "mlp") == "cbn":
+            # kind 2: the CBN + SoftZ occupancy network
+            parts.append(struct.pack("<IIIIIf", 2, net.C, net.n_z, net.width, net.n_blocks,
+                                     net.eps))
+            parts += [f4(net.Wz), f4(net.bz)]
+            for i in range(net.n_blocks):
+                parts += [f4(net.Gg[i]), f4(net.gg[i]), f4(net.Gb[i]), f4(net.gb[i]),
+                          f4(net.mu[i]), f4(net.var[i]), f4(net.W[i]), f4(net.b[i])]
+            continue
         L = len(net.W)
         skip_mask = 0
         for l in net.skip:
