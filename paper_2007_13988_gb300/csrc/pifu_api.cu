@@ -82,6 +82,11 @@ struct CbnDev {
     bool ready = false;
     std::vector<float*> bufs;   // every allocation, freed together
     CbnF32 f32{};
+    // tensor-core form
+    bool tc_ok = false;
+    __nv_bfloat16* Gbf = nullptr;   // [nb 2K][C]
+    __nv_bfloat16* Wbf = nullptr;   // [(nb - 1) K][K] (or a dummy row block when nb = 1)
+    CUtensorMap tmG{}, tmW{}, tmX{};
 };
 
 bool prec_f8(int p) { return p == PIFU_PREC_FP8 || p == PIFU_PREC_FP8_MIXED; }
@@ -585,6 +590,33 @@ int upload_cbn(pifu_ctx* ctx, const HostCbn& h) {
     f.K = h.K;
     f.nb = h.nb;
     if (!cbn_f32_ok(f)) return PIFU_ERR_UNSUPPORTED;
+    if (cbn_tc_ok(h.C, h.K, h.nb)) {
+        // BF16 weights in the MMA's K-major B layout: rows are outputs
+        const size_t K2 = 2 * (size_t)h.K;
+        std::vector<__nv_bfloat16> G((size_t)h.nb * K2 * h.C);
+        for (int i = 0; i < h.nb; ++i)
+            for (size_t o = 0; o < K2; ++o)
+                for (int c = 0; c < h.C; ++c)
+                    G[((size_t)i * K2 + o) * h.C + c] =
+                        __float2bfloat16_rn(h.Gt[((size_t)i * h.C + c) * K2 + o]);
+        const int nw = std::max(h.nb - 1, 1);
+        std::vector<__nv_bfloat16> W((size_t)nw * h.K * h.K, __float2bfloat16_rn(0.f));
+        for (int i = 0; i + 1 < h.nb; ++i)
+            for (int o = 0; o < h.K; ++o)
+                for (int k = 0; k < h.K; ++k)
+                    W[((size_t)i * h.K + o) * h.K + k] =
+                        __float2bfloat16_rn(h.WT[((size_t)i * h.K + k) * h.K + o]);
+        CK(dev_alloc(&d.Gbf, (int64_t)G.size()));
+        CK(dev_alloc(&d.Wbf, (int64_t)W.size()));
+        CK(cudaMemcpy(d.Gbf, G.data(), G.size() * 2, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(d.Wbf, W.data(), W.size() * 2, cudaMemcpyHostToDevice));
+        if (!tc_encode_2d_bf16(&d.tmG, d.Gbf, (uint64_t)h.C, (uint64_t)h.nb * K2,
+                               (uint64_t)h.C * 2, 64, (uint32_t)K2) ||
+            !tc_encode_2d_bf16(&d.tmW, d.Wbf, (uint64_t)h.K, (uint64_t)nw * h.K,
+                               (uint64_t)h.K * 2, 64, (uint32_t)h.K))
+            return PIFU_ERR_CUDA;
+        d.tc_ok = true;
+    }
     // the occupancy slot's shape: the depth is one input scalar as for the
     // concatenation network; no layers of its own
     DevNet& net = ctx->net[0];
@@ -593,6 +625,7 @@ int upload_cbn(pifu_ctx* ctx, const HostCbn& h) {
     net.d_in = h.C + 1;
     net.ldx = round_up(h.C + 1, 8);
     net.max_hidden = h.K;
+    net.tc_ok = d.tc_ok;
     d.ready = true;
     return PIFU_OK;
 }
@@ -600,6 +633,9 @@ int upload_cbn(pifu_ctx* ctx, const HostCbn& h) {
 void free_cbn(CbnDev& d) {
     for (float* p : d.bufs) dev_free(p);
     d.bufs.clear();
+    dev_free(d.Gbf);
+    dev_free(d.Wbf);
+    d.tc_ok = false;
     d.f32 = CbnF32{};
     d.ready = false;
 }
@@ -679,7 +715,7 @@ int ensure_mlp_ws(pifu_ctx* ctx) {
 // TMA maps of a network's activation operands (gather rows, previous layer
 // outputs) over the current tensor-core workspaces of tc_rows rows.
 int encode_act_maps(pifu_ctx* ctx, DevNet& net) {
-    if (!net.tc_ok || ctx->tc_rows == 0) return PIFU_OK;
+    if (!net.tc_ok || ctx->tc_rows == 0 || net.kind == kNetCbn) return PIFU_OK;
     const uint64_t rows = (uint64_t)ctx->tc_rows;
     if (!tc_encode_2d_bf16(&net.tmX, ctx->Xb, (uint64_t)net.d_in, rows, (uint64_t)net.ldx * 2, 64,
                            128))
@@ -985,9 +1021,15 @@ bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
 
 // m_dev (optional): the batch size is device-resident, at most m <= kChunkTC
 // (graph form); m is then only the capacity the launches are sized for.
+int run_cbn_tc(pifu_ctx* ctx, const PointSrc& src, int64_t m, const Map& map, const Calib& calib,
+               const Epilogue& epi, cudaStream_t s);
 int run_mlp_tc(pifu_ctx* ctx, const DevNet& net, const PointSrc& src_in, int64_t m,
                const Map& map0, const Map& map1, const Calib& calib, const Epilogue& epi,
                cudaStream_t s, const unsigned int* m_dev = nullptr, bool f8 = false) {
+    if (net.kind == kNetCbn) {
+        if (f8 || m_dev) return PIFU_ERR_UNSUPPORTED;
+        return run_cbn_tc(ctx, src_in, m, map0, calib, epi, s);
+    }
     if (!net.tc_ok) return PIFU_ERR_UNSUPPORTED;
     if (f8 && !net.f8_ok) return PIFU_ERR_STATE;
     const int F = f8 ? (int)net.f8.size() : 0;   // leading E4M3 layers
@@ -1078,6 +1120,52 @@ int run_mlp_tc(pifu_ctx* ctx, const DevNet& net, const PointSrc& src_in, int64_t
             pr.end(PIFU_K_MLP_LAST, ev, s, 2.0 * mc * Ll.fan_in * Ll.n_out,
                    2.0 * (double)mc * (Ll.fan_in + Ll.n_out));
         }
+    }
+    return PIFU_OK;
+}
+
+// The CBN + SoftZ network on the tensor cores over a host-sized batch, in
+// passes of at most kChunkTC points: gather (BF16 features, FP32 depth), then
+// the whole network in one launch.
+int run_cbn_tc(pifu_ctx* ctx, const PointSrc& src, int64_t m, const Map& map, const Calib& calib,
+               const Epilogue& epi, cudaStream_t s) {
+    CbnDev& d = ctx->cbn;
+    if (!d.tc_ok) return PIFU_ERR_UNSUPPORTED;
+    const CbnF32& f = d.f32;
+    {
+        const int st = ensure_tc_rows(ctx, std::min<int64_t>(m, kChunkTC));
+        if (st != PIFU_OK) return st;
+    }
+    float* zbuf = reinterpret_cast<float*>(ctx->Hb[0]);
+    const CbnTcMaps maps{&d.tmX, &d.tmG, &d.tmW};
+    Profiler& pr = ctx->prof;
+    const double flops_pt = 2.0 * ((double)f.n_z * f.K + 2.0 * f.nb * f.C * f.K +
+                                   (double)(f.nb - 1) * f.K * f.K + f.K);
+    for (int64_t p0 = 0; p0 < m; p0 += kChunkTC) {
+        const int64_t mc = std::min<int64_t>(kChunkTC, m - p0);
+        cudaEvent_t ev = pr.begin(s);
+        CK(launch_cbn_gather(src, p0, mc, calib, map, ctx->Xb, f.C, zbuf, s));
+        pr.end(PIFU_K_GATHER, ev, s, 0.0, (double)mc * (4.0 * 4.0 * map.C + 2.0 * f.C + 4.0));
+        CbnTcArgs a{};
+        a.zbuf = zbuf;
+        a.WzT = f.WzT;
+        a.bz = f.bz;
+        a.g0 = f.g0;
+        a.bl = f.bl;
+        a.wlast = f.wlast;
+        a.blast = f.blast;
+        a.C = f.C;
+        a.n_z = f.n_z;
+        a.K = f.K;
+        a.nb = f.nb;
+        a.M = (int)mc;
+        a.p0 = p0;
+        a.err = ctx->d_count + 1;
+        a.epi = epi;
+        ev = pr.begin(s);
+        CK(launch_cbn_tc(maps, a, s));
+        pr.end(PIFU_K_MLP_HIDDEN, ev, s, flops_pt * (double)mc,
+               2.0 * (double)mc * f.C + 2.0 * f.nb * (2.0 * f.C * f.K + (double)f.K * f.K));
     }
     return PIFU_OK;
 }
@@ -1435,6 +1523,11 @@ int encode_all_act_maps(pifu_ctx* ctx) {
         const int st = encode_act_maps(ctx, n);
         if (st != PIFU_OK) return st;
     }
+    CbnDev& cb = ctx->cbn;
+    if (cb.tc_ok && ctx->tc_rows > 0 &&
+        !tc_encode_2d_bf16(&cb.tmX, ctx->Xb, (uint64_t)cb.f32.C, (uint64_t)ctx->tc_rows,
+                           (uint64_t)cb.f32.C * 2, 64, 128))
+        return PIFU_ERR_CUDA;
     return ctx->sur.ready ? encode_act_maps(ctx, ctx->snet) : PIFU_OK;
 }
 

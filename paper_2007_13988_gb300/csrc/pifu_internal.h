@@ -345,6 +345,35 @@ bool cbn_f32_ok(const CbnF32& net);
 cudaError_t launch_cbn_f32(const CbnF32& net, const PointSrc& src, int64_t m, const Calib& calib,
                            const Map& map, const Epilogue& epi, cudaStream_t stream);
 
+// --- cbn_tc.cu -------------------------------------------------------------
+// The CBN + SoftZ network on tcgen05 tensor cores (BF16 operands, FP32
+// accumulation): one persistent kernel runs all blocks per 128-point tile.
+struct CbnTcArgs {
+    const float* zbuf;    // [M] projected depth of each row (FP32)
+    const float* WzT;     // FP32 folded input layer, as CbnF32
+    const float* bz;
+    const float* g0;      // nb x [2K]: [gg; gb]
+    const float* bl;      // (nb - 1) x [K]
+    const float* wlast;   // [K]
+    const float* blast;   // [4]
+    int C, n_z, K, nb;
+    int M;                // rows of this pass
+    int64_t p0;           // point number of row 0 (for the epilogue)
+    unsigned int* err;    // device error word
+    Epilogue epi;
+};
+struct CbnTcMaps {
+    const CUtensorMap* tmX;   // BF16 feature rows [rows][C], box 64 x 128
+    const CUtensorMap* tmG;   // BF16 [nb 2K][C] = [Gg; Gb] per block, box 64 x 2K
+    const CUtensorMap* tmW;   // BF16 [(nb - 1) K][K] folded linear layers, box 64 x K
+};
+bool cbn_tc_ok(int C, int K, int nb);
+// X[r][0 .. C) = BF16 feature of point p0 + r, z[r] = its projected depth.
+cudaError_t launch_cbn_gather(const PointSrc& src, int64_t p0, int64_t m, const Calib& calib,
+                              const Map& map, __nv_bfloat16* X, int C, float* z,
+                              cudaStream_t stream);
+cudaError_t launch_cbn_tc(const CbnTcMaps& maps, const CbnTcArgs& args, cudaStream_t stream);
+
 // --- render.cu -------------------------------------------------------------
 struct RenderArgs {
     int width, height;

@@ -117,3 +117,133 @@ def test_cbn_refused_forms(tiny):
         pifu.pifu_frame(tiny.ctx, tiny.occ, tiny.col, w.calib, w.n0, w.num_levels, 64, 64, d, rgb,
                         m, precision=pifu.PIFU_PREC_MIXED)
     assert ei.value.status == pifu.PIFU_ERR_UNSUPPORTED
+
+
+# ---- tensor-core (tcgen05, BF16 operands, FP32 accumulation) form ---------------
+
+BF16, MIXED = pifu.PIFU_PREC_BF16, pifu.PIFU_PREC_MIXED
+
+
+def bf16_round(a):
+    """Round to the nearest BF16 (ties to even), returned as float64."""
+    a = np.asarray(a, dtype=np.float32)
+    u = a.view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def emulate_tc(net, c, z):
+    """The kernel's arithmetic in float64: statistics folded into the linear
+    layers as the library folds them (products in double, stored in FP32,
+    MMA operands in BF16), BF16 features and block outputs a, FP32 epilogue
+    values, the last layer on the unrounded a."""
+    f64 = np.float64
+    eps = f64(np.float32(net.eps))
+    s = [1.0 / np.sqrt(np.asarray(v, f64) + eps) for v in net.var]
+    WzT = (s[0][:, None] * np.asarray(net.Wz, f64)).astype(np.float32).astype(f64)
+    bz = (s[0] * (np.asarray(net.bz, f64) - np.asarray(net.mu[0], f64))).astype(np.float32)
+    p = np.clip(0.5 * (z + 1.0), 0.0, 1.0)
+    x = (net.n_z - 1) * p
+    i = np.minimum(np.floor(x).astype(int), net.n_z - 2)
+    t = x - i
+    n = (1 - t)[:, None] * WzT[:, i].T + t[:, None] * WzT[:, i + 1].T + bz.astype(f64)
+    cb = bf16_round(c)
+    for blk in range(net.n_blocks):
+        g = cb @ bf16_round(net.Gg[blk]).T + np.asarray(net.gg[blk], f64)
+        b = cb @ bf16_round(net.Gb[blk]).T + np.asarray(net.gb[blk], f64)
+        a = np.maximum(g * n + b, 0.0)
+        if blk + 1 == net.n_blocks:
+            logit = a @ np.asarray(net.W[blk], f64)[0] + f64(net.b[blk][0])
+            return 1.0 / (1.0 + np.exp(-logit))
+        W = bf16_round((s[blk + 1][:, None] * np.asarray(net.W[blk], f64)).astype(np.float32))
+        bl = (s[blk + 1] * (np.asarray(net.b[blk], f64) - np.asarray(net.mu[blk + 1], f64)))
+        n = bf16_round(a) @ W.T + bl.astype(np.float32).astype(f64)
+
+
+@pytest.mark.parametrize("K,m", [(64, 1), (64, 300), (128, 3001)])
+def test_cbn_tc_matches_bf16_emulation(K, m):
+    """Hand-sized CBN networks (C = 128: two K-blocks of features; three
+    blocks) on BF16-valued maps at texel centres and depths on a 1/64 grid, so
+    the kernel's inputs are exact; ragged tile counts."""
+    C, n_z, nb = 128, 64, 3
+    rng = np.random.default_rng(11 + K)
+    u = lambda *sh: rng.uniform(-1, 1, sh)
+    net = synth.CbnNet(
+        C=C, n_z=n_z, width=K,
+        Wz=u(K, n_z).astype(np.float32), bz=(0.1 * u(K)).astype(np.float32),
+        Gg=[bf16_round(0.1 * u(K, C)).astype(np.float32) for _ in range(nb)],
+        gg=[(1 + 0.1 * u(K)).astype(np.float32) for _ in range(nb)],
+        Gb=[bf16_round(0.1 * u(K, C)).astype(np.float32) for _ in range(nb)],
+        gb=[(0.1 * u(K)).astype(np.float32) for _ in range(nb)],
+        mu=[(0.2 * u(K)).astype(np.float32) for _ in range(nb)],
+        var=[rng.uniform(0.5, 1.5, K).astype(np.float32) for _ in range(nb)],
+        W=[(u(K, K) * np.sqrt(6.0 / K)).astype(np.float32) for _ in range(nb - 1)]
+          + [(u(1, K) * np.sqrt(3.0 / K)).astype(np.float32)],
+        b=[(0.1 * u(K)).astype(np.float32) for _ in range(nb - 1)] + [np.zeros(1, np.float32)])
+    w = synth.tiny(0)
+    H = W = 32
+    fmap = bf16_round(rng.standard_normal((H, W, C))).astype(np.float32)
+    w.occ_map = np.ascontiguousarray(fmap)
+    w.occ_net = net
+    w.col_net = synth.colour_net(C + 1, (64, 3), (), 5)
+    c = Ctx(w)
+    try:
+        i = rng.integers(0, W, m)
+        j = rng.integers(0, H, m)
+        z = rng.integers(-64, 65, m) / 64.0
+        P = np.stack([(2 * i + 1) / W - 1, (2 * j + 1) / H - 1, z], 1).astype(np.float32)
+        want = emulate_tc(net, fmap[j, i].astype(np.float64), z)
+        got = c.query(P, precision=BF16)
+        err = np.abs(got - want)
+        print("CBN tc K=%d m=%d: max %.2e mean %.2e" % (K, m, err.max(), err.mean()))
+        # differences only from FP32-vs-FP64 accumulation order flipping a
+        # BF16 rounding of a block output
+        assert err.max() <= 2e-3
+        assert err.mean() <= 1e-4
+    finally:
+        c.close()
+
+
+def test_cbn_bf16_query_against_oracle(full):
+    w = full.w
+    P = synth.query_points(4000, seed=24)
+    want = occ_oracle(w, P)
+    got = full.query(P, precision=BF16)
+    err = np.abs(got - want)
+    print("CBN bf16 occupancy error vs oracle: max %.3g mean %.3g" % (err.max(), err.mean()))
+    assert err.mean() <= 5e-3
+    assert np.count_nonzero((got >= 0.5) != (want >= 0.5)) <= 0.01 * len(P)
+
+
+def test_cbn_mixed_query_decisions_match_oracle(full):
+    w = full.w
+    c = localize.node_coords(256)
+    rng = np.random.default_rng(25)
+    k, j, i = (rng.integers(0, 257, 60000) for _ in range(3))
+    P = np.stack([c[i], c[j], c[k]], 1)
+    o = occ_oracle(w, P)
+    P = P[np.abs(o - 0.5) < 0.3][:3000].astype(np.float32)
+    want = occ_oracle(w, P)
+    got = full.query(P, precision=MIXED)
+    near = np.abs(want - 0.5) < 0.015
+    assert np.max(np.abs(got[near] - want[near])) <= OCC_TOL
+    assert np.array_equal(got >= 0.5, want >= 0.5)
+
+
+@pytest.fixture(scope="module")
+def full_levels(full):
+    w = full.w
+    return localize.hierarchical(lambda P: occ_oracle(w, P), w.n0, w.num_levels)
+
+
+def test_cbn_mixed_localization_256(full, full_levels):
+    from oracle import metrics
+    vol = full.localize(precision=MIXED, margin=0.02)
+    b, e, v = full.volume_host(vol)
+    iou = metrics.iou(b, full_levels[-1].binary)
+    print("CBN mixed 32^3 -> 256^3: IoU %.6f, evals %d (oracle %d), rechecked %s"
+          % (iou, vol.n_eval, sum(l.n_eval for l in full_levels), list(vol.rechecked_per_level)[:4]))
+    assert iou >= 0.999
+    vb = full.localize(precision=BF16)
+    bb, _, _ = full.volume_host(vb)
+    assert metrics.iou(bb, full_levels[-1].binary) >= 0.97
