@@ -56,6 +56,8 @@ def parse_args():
                     help="skip the paper's view-culled final level render")
     ap.add_argument("--no-512", action="store_true",
                     help="skip the 512^3 precision form (timing and accuracy vs the oracle)")
+    ap.add_argument("--no-cbn", action="store_true",
+                    help="skip the CBN + SoftZ occupancy network (the paper's final f_O)")
     ap.add_argument("--no-octree", action="store_true",
                     help="skip the Fig. 3 comparison with the two octree baselines")
     ap.add_argument("--form", choices=("graph", "host"), default="graph")
@@ -418,6 +420,28 @@ def octree_tradeoff(fr, prec, reps=3):
     return out
 
 
+def cbn_form(fr, args, world):
+    """The paper's final f_O (CBN + SoftZ, Appendix, Eq. 7 and Eq. 8) on the
+    same frame and maps: the host-driven MIXED and plain FP32 forms (the
+    graph forms take the concatenation network), device-timed like the
+    headline, with the CBN kernel's own roofline."""
+    from paper_2007_13988_gb300 import synth
+    p = fr.pifu
+    wc = synth.full_cbn(0)
+    ctx = p.pifu_create(p.blob_from_nets(wc.occ_net, wc.col_net))
+    saved = fr.ctx, fr.w
+    fr.ctx, fr.w = ctx, wc
+    try:
+        side = max(3, min(args.steps, 10))
+        mixed = time_form(fr, PREC["mixed"], args.steps, args.warmup, world, form="host")
+        mixed["snap"] = snapshot(fr, mixed["vol"])
+        plain = time_form(fr, 0, side, 2, world, form="host")
+    finally:
+        fr.ctx, fr.w = saved
+        p.pifu_destroy(ctx)
+    return wc, mixed, plain
+
+
 def snapshot(fr, vol):
     """Host copies of a frame's result: binarized fine grid, node values
     (tentative 0/1 where not evaluated), colour and hit mask."""
@@ -684,6 +708,10 @@ def run_ours(args, rank, world, local_rank):
     fig3 = None
     if not args.no_octree:
         fig3 = octree_tradeoff(fr, prec)
+    # ---- the paper's final f_O: CBN + SoftZ -------------------------------------
+    cbn = None
+    if prec != 0 and not args.no_cbn:
+        cbn = cbn_form(fr, args, world)
     # ---- the video stream in lockstep batches ----------------------------------
     stream_out, stream_inputs = None, None
     if prec != 0 and not args.no_stream:
@@ -882,6 +910,37 @@ def run_ours(args, rank, world, local_rank):
                 "oracle_culled_evals": res["n_eval"], "oracle_s": time.perf_counter() - t0}
     if fig3 is not None:
         line["fig3_octree_baselines"] = fig3
+    if cbn is not None:
+        wc, cm, cp = cbn
+        ck = cm["prof"]["cbn_tc"]
+        c_ach = ck["flops"] / (ck["ms"] / 1000.0) / 1e12 if ck["ms"] > 0 else 0.0
+        c_peak = peaks.get("bf16_tflops", 1900.0)
+        out = {"form": "the paper's final f_O, CBN + SoftZ (SoftZ 64 -> 128, five CBN blocks "
+                       "of 128 channels conditioned on the 256-channel feature), "
+                       "32^3 -> 256^3 + 512^2 render, host-driven MIXED",
+               "value": cm["value"], "unit": UNIT, "ms_per_step": cm["ms_per_step"],
+               "evals_per_frame": cm["evals"], "rechecked_per_frame": cm["rechecked"],
+               "conflict_rounds": cm["rounds"],
+               "f_O_gflop_per_frame": cm["evals"] * wc.occ_net.flops_per_point() / 1e9,
+               "plain_fp32": {"value": cp["value"], "ms_per_step": cp["ms_per_step"]},
+               "speedup_over_plain_fp32": cm["value"] / cp["value"],
+               "speedup_over_headline_host_driven": cm["value"] / prof_run["value"],
+               "kernel_roofline": {
+                   "kernel": "cbn_tc_kernel (whole f_O per 128-point tile)", "bound": "tensor",
+                   "achieved": c_ach, "peak": c_peak, "unit": "TFLOP/s",
+                   "frac": c_ach / c_peak, "peak_source": "dense BF16 cuBLAS burst, "
+                   "MEASURED_PEAKS.json",
+                   "launches_per_step": ck["launches"] / max(1, len(cm["step_ms"])),
+                   "ms_per_step": ck["ms"] / max(1, len(cm["step_ms"]))},
+               "kernels": {k: {"launches": v["launches"] // max(1, len(cm["step_ms"])),
+                               "ms_per_step": v["ms"] / max(1, len(cm["step_ms"]))}
+                           for k, v in cm["prof"].items() if v["launches"]}}
+        if world == 1 and not args.no_cpu_baseline:
+            t0 = time.perf_counter()
+            _, _, (lvc, o_rgbc, o_hitc) = oracle_frame(wc, keep=True)
+            out["accuracy"] = accuracy(cm["snap"], lvc, o_rgbc, o_hitc)
+            out["oracle_s"] = time.perf_counter() - t0
+        line["cbn_softz"] = out
     if stream_out is not None:
         line["stream"] = stream_out
     if p512:

@@ -403,7 +403,8 @@ typedef enum {
     PIFU_K_SELECT = 4,      /* 26-dilation, selection and compaction              */
     PIFU_K_RENDER = 5,      /* ray first crossing                                 */
     PIFU_K_MLP_F32 = 6,     /* hidden MLP layers in FP32 (SIMT FFMA)              */
-    PIFU_K_COUNT = 7
+    PIFU_K_CBN_TC = 7,      /* the CBN + SoftZ occupancy network on tcgen05       */
+    PIFU_K_COUNT = 8
 } pifu_kernel_class;
 
 /* Per-class totals since the last pifu_profile call.  `launches` counts

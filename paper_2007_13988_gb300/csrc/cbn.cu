@@ -1,6 +1,6 @@
 // The paper's final occupancy network (Appendix, "Depth Representation",
 // Eq. 7, and "Pixel-aligned 3D Lifting", Eq. 8) in FP32: the depth enters as
-// its soft one-hot vector Z, the pixel-aligned feature c conditions five
+// its soft one-hot vector Z, the pixel-aligned feature c conditions the
 // blocks of conditional batch normalization:
 //
 //   h_0 = Wz Z + bz;  per block i:
@@ -13,25 +13,43 @@
 // non-zero weights, so the input layer is a linear interpolation of two
 // columns of the folded Wz.
 //
-// One CTA walks 32-point tiles: it gathers the tile's features into shared
-// memory (channel-major, so every thread of a GEMM step reads the same
-// values), then per block computes the 2K gamma/beta outputs, the ReLU, and
-// the K outputs of the next linear layer, and finally the logit with one warp
-// per point.  Weights are stored input-major, so a warp's loads of one input
-// row are contiguous.  This is the reference arithmetic of the CBN network:
-// the plain FP32 form, the re-evaluation of the MIXED form and small batches.
+// Conditional batch normalization acts channel by channel, which sets the
+// work split: a cluster of kS CTAs owns a tile of kP points, and CTA r owns
+// channels [r Kc, (r + 1) Kc) (Kc = K / kS) in every block.  For its channels
+// it computes gamma and beta (a 2 Kc x C slice of the contraction over the
+// feature), the normalized input n (its slice of the previous linear layer),
+// and a, which it stores into every CTA's copy of the full a through
+// distributed shared memory; one cluster barrier per block publishes a, and
+// the next linear layer's slice reads all of it.  The tile's features are
+// gathered once per cluster (each CTA a slice of the channels, broadcast the
+// same way).  Each CTA's weight slice of a block (C x 2 Kc + K x Kc floats,
+// contiguous on the host) is loaded into registers during the previous
+// block's arithmetic and stored into a shared-memory double buffer, so the
+// inner loops read shared memory only.
+//
+// This is the reference arithmetic of the CBN network: the plain FP32 form,
+// the re-evaluation of the MIXED form and small batches, whose latency the
+// cluster split keeps low (a tile's arithmetic and weights are spread over
+// kS SMs).  The only waits are hardware cluster barriers, which every CTA of
+// a cluster reaches the same number of times.
+#include <cooperative_groups.h>
+
 #include <algorithm>
 
 #include "epilogue.cuh"
 #include "gather.cuh"
 
+namespace cg = cooperative_groups;
+
 namespace pifu {
 namespace {
 
-constexpr int kP = kCbnTile;       // points per tile
+constexpr int kS = kCbnCluster;    // CTAs per cluster
+constexpr int kP = 32;             // points per tile
 constexpr int kLd = kP + 4;        // row stride of the [channel][point] arrays
 constexpr int kThreads = 256;
-constexpr int kPG = 16;            // points per GEMM work item
+constexpr int kPG = 4;             // points per GEMM work item
+constexpr int kPf = kCbnPrefetch;  // float4 registers of the weight prefetch per thread
 
 // SoftZ of Eq. 7 for depth z: lower index i (<= n_z - 2) and the weight t of
 // index i + 1 (Z_i = 1 - t).  P'_z is clamped to [0, 1]; at P'_z = 1 the pair
@@ -43,142 +61,235 @@ __device__ __forceinline__ void soft_z(float z, int n_z, int& i, float& t) {
     t = x - (float)i;
 }
 
-// out[o][p] = bias[o] + sum_k WT[k][o] in[k][p] for o < n_out, p < kP;
-// in / out are [channel][kLd] shared-memory arrays.
-__device__ __forceinline__ void tile_gemm(const float* __restrict__ WT,
-                                          const float* __restrict__ bias, int n_in, int n_out,
-                                          const float* in, float* out) {
+// out[o][p] = bias[o] + sum_k W[k][o] in[k][p] for o < n_out, p < kP; W is
+// [n_in][n_out] and in / out are [channel][kLd], all in shared memory.  A
+// warp's work items share their points (broadcast reads) and take
+// consecutive outputs (conflict-free weight reads).
+__device__ __forceinline__ void tile_gemm(const float* W, const float* __restrict__ bias,
+                                          int n_in, int n_out, const float* in, float* out) {
     const int items = n_out * (kP / kPG);
     for (int it = threadIdx.x; it < items; it += blockDim.x) {
         const int o = it % n_out;
         const int g = it / n_out;
-        float acc[kPG];
-#pragma unroll
-        for (int j = 0; j < kPG; ++j) acc[j] = 0.f;
+        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
         const float* ip = in + g * kPG;
-        const float* wp = WT + o;
-#pragma unroll 4
+#pragma unroll 8
         for (int k = 0; k < n_in; ++k) {
-            const float w = __ldg(wp + (int64_t)k * n_out);
-            const float4* a = reinterpret_cast<const float4*>(ip + k * kLd);
-#pragma unroll
-            for (int q = 0; q < kPG / 4; ++q) {
-                const float4 v = a[q];
-                acc[4 * q + 0] = fmaf(w, v.x, acc[4 * q + 0]);
-                acc[4 * q + 1] = fmaf(w, v.y, acc[4 * q + 1]);
-                acc[4 * q + 2] = fmaf(w, v.z, acc[4 * q + 2]);
-                acc[4 * q + 3] = fmaf(w, v.w, acc[4 * q + 3]);
-            }
+            const float w = W[k * n_out + o];
+            const float4 v = *reinterpret_cast<const float4*>(ip + k * kLd);
+            acc.x = fmaf(w, v.x, acc.x);
+            acc.y = fmaf(w, v.y, acc.y);
+            acc.z = fmaf(w, v.z, acc.z);
+            acc.w = fmaf(w, v.w, acc.w);
         }
         const float b = __ldg(bias + o);
         float* op = out + o * kLd + g * kPG;
-#pragma unroll
-        for (int j = 0; j < kPG; ++j) op[j] = acc[j] + b;
+        op[0] = acc.x + b;
+        op[1] = acc.y + b;
+        op[2] = acc.z + b;
+        op[3] = acc.w + b;
     }
 }
 
-__global__ void __launch_bounds__(kThreads) cbn_f32_kernel(CbnF32 net, PointSrc src, int64_t m,
-                                                           Calib calib, Map map, Epilogue epi) {
-    extern __shared__ __align__(16) float sm[];
-    const int C = net.C, K = net.K;
-    float* cS = sm;                       // [C][kLd] features
-    float* nS = cS + C * kLd;             // [K][kLd] normalized block input
-    float* gS = nS + K * kLd;             // [2K][kLd] gamma | beta; a overwrites gamma
-    float* tS = gS + 2 * K * kLd;         // [kP] SoftZ weight of the upper index
-    int* iS = reinterpret_cast<int*>(tS + kP);   // [kP] SoftZ lower index
+// Weight slice of block `blk` for CTA r: the gamma/beta part (C x 2Kc), then
+// the linear part (K x Kc) unless blk is the last block.
+struct Slice {
+    const float4* g;
+    const float4* w;
+    int ng, nw;   // float4 counts
+};
+
+__device__ __forceinline__ Slice slice_of(const CbnF32& net, int blk, int r) {
+    const int Kc = net.K / kS;
+    const int64_t gsz = (int64_t)net.C * 2 * Kc, wsz = (int64_t)net.K * Kc;
+    Slice s;
+    s.g = reinterpret_cast<const float4*>(net.GS + ((int64_t)blk * kS + r) * gsz);
+    s.ng = (int)(gsz / 4);
+    const bool lin = blk + 1 < net.nb;
+    s.w = lin ? reinterpret_cast<const float4*>(net.WS + ((int64_t)blk * kS + r) * wsz) : nullptr;
+    s.nw = lin ? (int)(wsz / 4) : 0;
+    return s;
+}
+
+__device__ __forceinline__ void prefetch(const Slice& s, float4 (&pf)[kPf]) {
+#pragma unroll
+    for (int i = 0; i < kPf; ++i) {
+        const int e = threadIdx.x + i * kThreads;
+        if (e < s.ng) pf[i] = __ldg(s.g + e);
+        else if (e < s.ng + s.nw) pf[i] = __ldg(s.w + (e - s.ng));
+    }
+}
+
+__device__ __forceinline__ void commit(const Slice& s, const float4 (&pf)[kPf], float* buf) {
+    float4* b4 = reinterpret_cast<float4*>(buf);
+#pragma unroll
+    for (int i = 0; i < kPf; ++i) {
+        const int e = threadIdx.x + i * kThreads;
+        if (e < s.ng + s.nw) b4[e] = pf[i];
+    }
+}
+
+__global__ void __cluster_dims__(kS, 1, 1) __launch_bounds__(kThreads, 1)
+    cbn_f32_kernel(CbnF32 net, PointSrc src, int64_t m, Calib calib, Map map, Epilogue epi) {
+    cg::cluster_group cl = cg::this_cluster();
+    const int r = (int)cl.block_rank();
+    const int64_t cid = blockIdx.x / kS;
+    const int64_t ncl = gridDim.x / kS;
+    const int C = net.C, K = net.K, nb = net.nb;
+    const int Kc = K / kS, K2c = 2 * Kc;
+    const int slice = C * K2c + K * Kc;           // floats of one weight buffer
+    extern __shared__ float4 smem4[];
+    float* cS = reinterpret_cast<float*>(smem4);   // [C][kLd] features
+    float* aS = cS + C * kLd;                      // [2][K][kLd] a of all channels
+    float* nS = aS + 2 * K * kLd;                  // [Kc][kLd] normalized input, own channels
+    float* gS = nS + Kc * kLd;                     // [2Kc][kLd] gamma | beta, own channels
+    float* wS = gS + K2c * kLd;                    // [2][slice] weight double buffer
+    float* tS = wS + 2 * slice;                    // [kP] SoftZ weight of the upper index
+    int* iS = reinterpret_cast<int*>(tS + kP);     // [kP] SoftZ lower index
     const Map none{nullptr, 0, 0, 0, 0};
-    const int nq = C / 4 + 1;             // feature quads + the depth quad
+
+    if (src.count) m = min(m, (int64_t)*src.count);
     const int64_t ntiles = (m + kP - 1) / kP;
-    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    float4 pf[kPf];
+    {
+        const Slice s0 = slice_of(net, 0, r);
+        prefetch(s0, pf);
+        commit(s0, pf, wS);
+    }
+    __syncthreads();
+    const int qpr = C / 4 / kS;   // feature quads each CTA gathers per point
+    int64_t q = 0;                // blocks done by this cluster (buffer parity)
+    for (int64_t tile = cid; tile < ntiles; tile += ncl) {
         const int64_t p0 = tile * kP;
         const int np = (int)(m - p0 < (int64_t)kP ? m - p0 : (int64_t)kP);
-        for (int w = threadIdx.x; w < kP * nq; w += blockDim.x) {
-            const int p = w % kP;
-            const int q = w / kP;
+        // features: CTA r gathers quads [r qpr, (r + 1) qpr) of every point
+        // and stores them into every CTA's copy; every CTA takes the depth
+        for (int e = threadIdx.x; e < kP * qpr; e += kThreads) {
+            const int p = e % kP;
+            const int qd = r * qpr + e / kP;
             float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (p < np) v = gather_quad(src, p0 + p, calib, map, none, 4 * q);
-            if (q < C / 4) {
-                cS[(4 * q + 0) * kLd + p] = v.x;
-                cS[(4 * q + 1) * kLd + p] = v.y;
-                cS[(4 * q + 2) * kLd + p] = v.z;
-                cS[(4 * q + 3) * kLd + p] = v.w;
-            } else {
-                int i;
-                float t;
-                soft_z(v.x, net.n_z, i, t);
-                iS[p] = i;
-                tS[p] = t;
-            }
-        }
-        __syncthreads();
-        // normalized input of block 0: (1 - t) Wz'[:, i] + t Wz'[:, i + 1] + bz'
-        for (int w = threadIdx.x; w < K * kP; w += blockDim.x) {
-            const int k = w / kP;
-            const int p = w % kP;
-            const int i = iS[p];
-            const float t = tS[p];
-            const float lo = __ldg(net.WzT + (int64_t)i * K + k);
-            const float hi = __ldg(net.WzT + (int64_t)(i + 1) * K + k);
-            nS[k * kLd + p] = fmaf(t, hi, fmaf(1.0f - t, lo, __ldg(net.bz + k)));
-        }
-        __syncthreads();
-        for (int blk = 0; blk < net.nb; ++blk) {
-            tile_gemm(net.Gt + (int64_t)blk * C * 2 * K, net.g0 + (int64_t)blk * 2 * K, C, 2 * K,
-                      cS, gS);
-            __syncthreads();
-            for (int w = threadIdx.x; w < K * kP; w += blockDim.x) {
-                const int k = w / kP;
-                const int p = w % kP;
-                const int e = k * kLd + p;
-                gS[e] = fmaxf(fmaf(gS[e], nS[e], gS[K * kLd + e]), 0.0f);
-            }
-            __syncthreads();
-            if (blk + 1 < net.nb) {
-                tile_gemm(net.WT + (int64_t)blk * K * K, net.bl + (int64_t)blk * K, K, K, gS, nS);
-                __syncthreads();
-            }
-        }
-        // logit = wlast . a + blast, one warp per point
-        const int warp = threadIdx.x >> 5;
-        const int lane = threadIdx.x & 31;
-        for (int p = warp; p < np; p += blockDim.x >> 5) {
-            float acc = 0.f;
-            for (int k = lane; k < K; k += 32) acc = fmaf(__ldg(net.wlast + k), gS[k * kLd + p], acc);
+            if (p < np) v = gather_quad(src, p0 + p, calib, map, none, 4 * qd);
+            float* dst = cS + 4 * qd * kLd + p;
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-            if (lane == 0) {
-                const float t[4] = {acc, 0.f, 0.f, 0.f};
-                last_epilogue(epi, p0 + p, 1, t, net.blast);
+            for (int d = 0; d < kS; ++d) {
+                float* rd = cl.map_shared_rank(dst, (unsigned)d);
+                rd[0] = v.x;
+                rd[kLd] = v.y;
+                rd[2 * kLd] = v.z;
+                rd[3 * kLd] = v.w;
             }
         }
-        __syncthreads();
+        if (threadIdx.x < kP) {
+            const int p = threadIdx.x;
+            float z = 0.f;
+            if (p < np) z = gather_quad(src, p0 + p, calib, map, none, C).x;
+            int i;
+            float t;
+            soft_z(z, net.n_z, i, t);
+            iS[p] = i;
+            tS[p] = t;
+        }
+        cl.sync();
+        // normalized input of block 0 for the own channels
+        for (int e = threadIdx.x; e < Kc * kP; e += kThreads) {
+            const int j = e / kP;
+            const int p = e % kP;
+            const int k = r * Kc + j;
+            const float lo = __ldg(net.WzT + (int64_t)iS[p] * K + k);
+            const float hi = __ldg(net.WzT + (int64_t)(iS[p] + 1) * K + k);
+            nS[j * kLd + p] = fmaf(tS[p], hi, fmaf(1.0f - tS[p], lo, __ldg(net.bz + k)));
+        }
+        for (int blk = 0; blk < nb; ++blk, ++q) {
+            const float* wb = wS + (q & 1) * slice;
+            // the next block's weight slice travels while this block computes
+            const bool more = blk + 1 < nb || tile + ncl < ntiles;
+            const Slice sn = slice_of(net, blk + 1 < nb ? blk + 1 : 0, r);
+            if (more) prefetch(sn, pf);
+            __syncthreads();   // nS, the weights of this block
+            tile_gemm(wb, net.g0S + ((int64_t)blk * kS + r) * K2c, C, K2c, cS, gS);
+            __syncthreads();
+            float* aq = aS + (q & 1) * K * kLd;
+            for (int e = threadIdx.x; e < Kc * kP; e += kThreads) {
+                const int j = e / kP;
+                const int p = e % kP;
+                const float a = fmaxf(fmaf(gS[j * kLd + p], nS[j * kLd + p], gS[(Kc + j) * kLd + p]),
+                                      0.0f);
+                float* dst = aq + (r * Kc + j) * kLd + p;
+#pragma unroll
+                for (int d = 0; d < kS; ++d) *cl.map_shared_rank(dst, (unsigned)d) = a;
+            }
+            cl.sync();
+            if (blk + 1 < nb) {
+                tile_gemm(wb + C * K2c, net.blS + ((int64_t)blk * kS + r) * Kc, K, Kc, aq, nS);
+            } else {
+                // logits: CTA r takes points r, r + kS, ...
+                const int lane = threadIdx.x & 31;
+                for (int p = r + kS * (threadIdx.x >> 5); p < np; p += kS * (kThreads / 32)) {
+                    float acc = 0.f;
+                    for (int k = lane; k < K; k += 32) acc = fmaf(__ldg(net.wlast + k), aq[k * kLd + p], acc);
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+                    if (lane == 0) {
+                        const float t[4] = {acc, 0.f, 0.f, 0.f};
+                        last_epilogue(epi, p0 + p, 1, t, net.blast);
+                    }
+                }
+            }
+            __syncthreads();   // every read of this block's weights is done
+            if (more) commit(sn, pf, wS + ((q + 1) & 1) * slice);
+        }
     }
 }
 
 size_t smem_bytes(const CbnF32& net) {
-    return (size_t)(net.C + 3 * net.K) * kLd * 4 + 2 * kP * 4;
+    const int Kc = net.K / kS;
+    const size_t slice = (size_t)net.C * 2 * Kc + (size_t)net.K * Kc;
+    return ((size_t)(net.C + 2 * net.K + 3 * Kc) * kLd + 2 * slice + 2 * kP) * 4;
+}
+
+int max_clusters(const CbnF32& net) {
+    static int cached = -1;
+    static size_t cached_smem = 0;
+    const size_t smem = smem_bytes(net);
+    if (cached >= 0 && cached_smem == smem) return cached;
+    if (cudaFuncSetAttribute(cbn_f32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem) != cudaSuccess)
+        return 0;
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(kS);
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = smem;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, cbn_f32_kernel, &cfg) != cudaSuccess) n = 0;
+    cached_smem = smem;
+    return cached = n;
 }
 
 }  // namespace
 
 bool cbn_f32_ok(const CbnF32& net) {
-    return net.C % 4 == 0 && net.C >= 4 && net.K >= 1 && net.n_z >= 2 && net.nb >= 1 &&
-           smem_bytes(net) <= 227 * 1024;
+    if (net.C < 4 * kS || net.C % (4 * kS) != 0 || net.K % (4 * kS) != 0 || net.K < 4 * kS ||
+        net.n_z < 2 || net.nb < 1)
+        return false;
+    const int Kc = net.K / kS;
+    const int slice = net.C * 2 * Kc + net.K * Kc;
+    return slice <= 4 * kPf * kThreads && smem_bytes(net) <= 227 * 1024;
 }
 
 cudaError_t launch_cbn_f32(const CbnF32& net, const PointSrc& src, int64_t m, const Calib& calib,
                            const Map& map, const Epilogue& epi, cudaStream_t stream) {
     if (m <= 0) return cudaSuccess;
     if (!cbn_f32_ok(net)) return cudaErrorInvalidValue;
-    const size_t smem = smem_bytes(net);
-    cudaError_t e = cudaFuncSetAttribute(cbn_f32_kernel,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
+    const int ncl = max_clusters(net);
+    if (ncl <= 0) return cudaErrorInvalidConfiguration;
     const int64_t tiles = (m + kP - 1) / kP;
-    const int per_sm = smem <= 113 * 1024 ? 2 : 1;
-    const int64_t grid = std::min<int64_t>(tiles, 152 * per_sm);
-    cbn_f32_kernel<<<(unsigned)grid, kThreads, smem, stream>>>(net, src, m, calib, map, epi);
-    return cudaGetLastError();
+    const int64_t grid_cl = src.count ? ncl : std::min<int64_t>(tiles, ncl);
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3((unsigned)(grid_cl * kS));
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = smem_bytes(net);
+    cfg.stream = stream;
+    return cudaLaunchKernelEx(&cfg, cbn_f32_kernel, net, src, m, calib, map, epi);
 }
 
 }  // namespace pifu

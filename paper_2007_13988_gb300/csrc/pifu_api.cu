@@ -82,6 +82,8 @@ struct CbnDev {
     bool ready = false;
     std::vector<float*> bufs;   // every allocation, freed together
     CbnF32 f32{};
+    const float* g0 = nullptr;   // nb x [2K] (tensor-core epilogue)
+    const float* bl = nullptr;   // (nb - 1) x [K]
     // tensor-core form
     bool tc_ok = false;
     __nv_bfloat16* Gbf = nullptr;   // [nb 2K][C]
@@ -499,6 +501,7 @@ int parse_net(Reader& rd, HostNet& hn, int want_kind) {
 struct HostCbn {
     int C = 0, n_z = 0, K = 0, nb = 0;
     std::vector<float> WzT, bz, Gt, g0, WT, bl, wlast, blast;
+    std::vector<float> GS, g0S, WS, blS;   // the FP32 kernel's per-CTA slices
 };
 
 int parse_cbn(Reader& rd, HostCbn& h) {
@@ -562,6 +565,30 @@ int parse_cbn(Reader& rd, HostCbn& h) {
         }
     h.wlast = W[nb - 1];
     h.blast = {b[nb - 1][0], 0.f, 0.f, 0.f};
+    // slices of the cluster kernel: CTA r owns channels [r Kc, (r + 1) Kc)
+    if (K % kCbnCluster == 0) {
+        const size_t S = kCbnCluster, Kc = K / S, K2c = 2 * Kc;
+        h.GS.assign(nb * S * C * K2c, 0.f);
+        h.g0S.assign(nb * S * K2c, 0.f);
+        for (size_t i = 0; i < nb; ++i)
+            for (size_t r = 0; r < S; ++r)
+                for (size_t j = 0; j < K2c; ++j) {
+                    const size_t o = j < Kc ? r * Kc + j : K + r * Kc + (j - Kc);
+                    for (size_t c = 0; c < C; ++c)
+                        h.GS[((i * S + r) * C + c) * K2c + j] = h.Gt[(i * C + c) * K2 + o];
+                    h.g0S[(i * S + r) * K2c + j] = h.g0[i * K2 + o];
+                }
+        h.WS.assign((nb - 1) * S * K * Kc, 0.f);
+        h.blS.assign((nb - 1) * S * Kc, 0.f);
+        for (size_t i = 0; i + 1 < nb; ++i)
+            for (size_t r = 0; r < S; ++r)
+                for (size_t j = 0; j < Kc; ++j) {
+                    const size_t o = r * Kc + j;
+                    for (size_t k = 0; k < K; ++k)
+                        h.WS[((i * S + r) * K + k) * Kc + j] = h.WT[(i * K + k) * K + o];
+                    h.blS[(i * S + r) * Kc + j] = h.bl[i * K + o];
+                }
+    }
     return PIFU_OK;
 }
 
@@ -579,12 +606,14 @@ int upload_cbn(pifu_ctx* ctx, const HostCbn& h) {
     CbnF32& f = d.f32;
     CK(up(h.WzT, &f.WzT));
     CK(up(h.bz, &f.bz));
-    CK(up(h.Gt, &f.Gt));
-    CK(up(h.g0, &f.g0));
-    CK(up(h.WT, &f.WT));
-    CK(up(h.bl, &f.bl));
+    CK(up(h.GS, &f.GS));
+    CK(up(h.g0S, &f.g0S));
+    CK(up(h.WS, &f.WS));
+    CK(up(h.blS, &f.blS));
     CK(up(h.wlast, &f.wlast));
     CK(up(h.blast, &f.blast));
+    CK(up(h.g0, &d.g0));
+    CK(up(h.bl, &d.bl));
     f.C = h.C;
     f.n_z = h.n_z;
     f.K = h.K;
@@ -637,6 +666,7 @@ void free_cbn(CbnDev& d) {
     dev_free(d.Wbf);
     d.tc_ok = false;
     d.f32 = CbnF32{};
+    d.g0 = d.bl = nullptr;
     d.ready = false;
 }
 
@@ -1150,8 +1180,8 @@ int run_cbn_tc(pifu_ctx* ctx, const PointSrc& src, int64_t m, const Map& map, co
         a.zbuf = zbuf;
         a.WzT = f.WzT;
         a.bz = f.bz;
-        a.g0 = f.g0;
-        a.bl = f.bl;
+        a.g0 = d.g0;
+        a.bl = d.bl;
         a.wlast = f.wlast;
         a.blast = f.blast;
         a.C = f.C;
@@ -1164,7 +1194,7 @@ int run_cbn_tc(pifu_ctx* ctx, const PointSrc& src, int64_t m, const Map& map, co
         a.epi = epi;
         ev = pr.begin(s);
         CK(launch_cbn_tc(maps, a, s));
-        pr.end(PIFU_K_MLP_HIDDEN, ev, s, flops_pt * (double)mc,
+        pr.end(PIFU_K_CBN_TC, ev, s, flops_pt * (double)mc,
                2.0 * (double)mc * f.C + 2.0 * f.nb * (2.0 * f.C * f.K + (double)f.K * f.K));
     }
     return PIFU_OK;

@@ -327,21 +327,26 @@ cudaError_t launch_mlp_fused(const FusedNet& net, const PointSrc& src, int64_t p
 // --- cbn.cu --------------------------------------------------------------
 // The CBN + SoftZ occupancy network (Appendix, Eq. 7 and Eq. 8) in FP32, with
 // each block's running statistics folded into the linear layer before it.
-constexpr int kCbnTile = 32;   // points per CTA tile of the FP32 kernel
+// Clusters of kCbnCluster CTAs; CTA r of a cluster owns channels
+// [r Kc, (r + 1) Kc), Kc = K / kCbnCluster, and its weight slices are
+// contiguous.
+constexpr int kCbnCluster = 8;
+constexpr int kCbnPrefetch = 12;   // float4 per thread: a slice holds <= 12 x 256 float4
 struct CbnF32 {
     const float* WzT;    // [n_z][K]: s_0 Wz, transposed
     const float* bz;     // [K]: s_0 (bz - mu_0)
-    const float* Gt;     // nb x [C][2K]: [Gg; Gb] transposed
-    const float* g0;     // nb x [2K]: [gg; gb]
-    const float* WT;     // (nb - 1) x [K][K]: s_{i+1} W_i, transposed
-    const float* bl;     // (nb - 1) x [K]: s_{i+1} (b_i - mu_{i+1})
+    const float* GS;     // nb x kCbnCluster x [C][2Kc]: gamma then beta columns of the slice
+    const float* g0S;    // nb x kCbnCluster x [2Kc]: gg then gb of the slice
+    const float* WS;     // (nb - 1) x kCbnCluster x [K][Kc]: s_{i+1} W_i, the slice's outputs
+    const float* blS;    // (nb - 1) x kCbnCluster x [Kc]: s_{i+1} (b_i - mu_{i+1})
     const float* wlast;  // [K]
     const float* blast;  // [4] (one value, padded)
     int C, n_z, K, nb;
 };
 bool cbn_f32_ok(const CbnF32& net);
-// Occupancy logits of points 0 .. m - 1 of `src` through the level / store
-// epilogue (the feature is map's bilinear sample, the depth its projection).
+// Occupancy logits of points 0 .. m - 1 of `src` (src.count: a device-resident
+// m) through the level / store epilogue; the feature is map's bilinear
+// sample, the depth its projection.
 cudaError_t launch_cbn_f32(const CbnF32& net, const PointSrc& src, int64_t m, const Calib& calib,
                            const Map& map, const Epilogue& epi, cudaStream_t stream);
 

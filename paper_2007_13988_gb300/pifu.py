@@ -47,7 +47,8 @@ EXPORTS = ("pifu_create", "pifu_destroy", "pifu_query", "pifu_query_colour", "pi
            "pifu_surrogate_ohem_weights", "pifu_surrogate_ohem_sample",
            "pifu_surrogate_train_ohem")
 
-KERNEL_CLASSES = ("gather", "mlp_hidden", "mlp_last", "level", "select", "render", "mlp_f32")
+KERNEL_CLASSES = ("gather", "mlp_hidden", "mlp_last", "level", "select", "render", "mlp_f32",
+                  "cbn_tc")
 
 
 class pifu_fmap(ctypes.Structure):
