@@ -364,25 +364,33 @@ __global__ void __launch_bounds__(kThreads, 1) cbn_tc_kernel(
 
 // SoftZ depth and BF16 feature rows of points p0 .. p0 + m - 1: row r of X
 // holds the C channels of point p0 + r; z[r] its projected depth (FP32).
+// One thread per (point, 4 quads): the projection and taps once per group.
 __global__ void __launch_bounds__(256) cbn_gather_kernel(PointSrc src, int64_t p0, int64_t m,
                                                          Calib calib, Map map,
                                                          __nv_bfloat16* __restrict__ X, int C,
                                                          float* __restrict__ z) {
-    const int nq = C / 4 + 1;
-    const int64_t total = m * nq;
+    const uint32_t nq = (uint32_t)C / 4 + 1;          // feature quads + the depth quad
+    const uint32_t ng = (nq + 3) / 4;
+    const int64_t total = m * ng;   // < 2^32: at most 2^20 rows of at most 257 groups
     const Map none{nullptr, 0, 0, 0, 0};
     for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < total;
          w += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t r = w / nq;
-        const int qd = (int)(w - r * nq);
-        const float4 v = gather_quad(src, p0 + r, calib, map, none, 4 * qd);
-        if (qd < C / 4) {
-            uint2 pk;
-            pk.x = pack2(v.x, v.y);
-            pk.y = pack2(v.z, v.w);
-            *reinterpret_cast<uint2*>(X + r * C + 4 * qd) = pk;
-        } else {
-            z[r] = v.x;
+        const uint32_t r = (uint32_t)w / ng;
+        const uint32_t q0 = ((uint32_t)w - r * ng) * 4;
+        const PointSample ps = sample_point(src, p0 + r, calib, map, none);
+#pragma unroll
+        for (uint32_t j = 0; j < 4; ++j) {
+            const uint32_t qd = q0 + j;
+            if (qd >= nq) break;
+            const float4 v = sample_quad(ps, 4 * (int)qd);
+            if (qd < (uint32_t)C / 4) {
+                uint2 pk;
+                pk.x = pack2(v.x, v.y);
+                pk.y = pack2(v.z, v.w);
+                *reinterpret_cast<uint2*>(X + (int64_t)r * C + 4 * qd) = pk;
+            } else {
+                z[r] = v.x;
+            }
         }
     }
 }
@@ -423,7 +431,7 @@ cudaError_t launch_cbn_gather(const PointSrc& src, int64_t p0, int64_t m, const 
                               const Map& map, __nv_bfloat16* X, int C, float* z,
                               cudaStream_t stream) {
     if (m <= 0) return cudaSuccess;
-    const int64_t total = m * (C / 4 + 1);
+    const int64_t total = m * ((C / 4 + 1 + 3) / 4);
     const int64_t blocks = std::min<int64_t>((total + 255) / 256, 152 * 16);
     cbn_gather_kernel<<<(unsigned)blocks, 256, 0, stream>>>(src, p0, m, calib, map, X, C, z);
     return cudaGetLastError();

@@ -2,9 +2,9 @@
 // and Eq. 2 (Sec. 3.1): x = [Phi(P_xy, g(I)) ..., P_z].
 //
 // Layout: feature maps are channel-last [H][W][C], so the C channels of one
-// texel are one contiguous run; a thread owns one point and four channels
-// and issues one 16-byte load per bilinear tap, and consecutive threads of a
-// warp read consecutive 16-byte pieces of the same texel row (coalesced).
+// texel are one contiguous run; a thread owns one point and 16 channels and
+// issues four 16-byte loads per bilinear tap, and consecutive threads of a
+// warp read consecutive 64-byte pieces of the same texel row (coalesced).
 // The 16.8 MB full-size map stays resident in the 129 MB L2 across a frame.
 //
 // Projection and sampling arithmetic: gather.cuh.
@@ -28,18 +28,29 @@ __device__ __forceinline__ void store4(__nv_bfloat16* X, float4 r) {
     *reinterpret_cast<uint2*>(X) = v;
 }
 
+// One thread per (point, group of kQPT quads): the projection and the tap
+// positions are computed once per group, then the group's 4 kQPT taps are
+// independent 16-byte loads; consecutive threads take consecutive groups of
+// the same texel rows (64 contiguous bytes each).
+constexpr uint32_t kQPT = 4;
+
 template <typename OutT>
 __global__ void __launch_bounds__(256) gather_kernel(PointSrc src, int64_t p0, int64_t m,
                                                      Calib calib, Map map0, Map map1,
                                                      OutT* __restrict__ X, int ldx) {
-    const int nq = ldx >> 2;
+    const uint32_t nq = (uint32_t)ldx >> 2;
+    const uint32_t ng = (nq + kQPT - 1) / kQPT;
     if (src.count) m = min(m, (int64_t)*src.count);
-    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < m * nq;
+    // m ng < 2^32 (at most 2^22 rows of at most 33 groups): 32-bit division
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < m * ng;
          t += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t lp = t / nq;
-        const int q = (int)(t - lp * nq);
-        const int c = q * 4;
-        store4(X + lp * ldx + c, gather_quad(src, p0 + lp, calib, map0, map1, c));
+        const uint32_t lp = (uint32_t)t / ng;
+        const uint32_t q0 = ((uint32_t)t - lp * ng) * kQPT;
+        const PointSample ps = sample_point(src, p0 + lp, calib, map0, map1);
+        OutT* row = X + (int64_t)lp * ldx;
+#pragma unroll
+        for (uint32_t j = 0; j < kQPT; ++j)
+            if (q0 + j < nq) store4(row + 4 * (q0 + j), sample_quad(ps, 4 * (int)(q0 + j)));
     }
 }
 
@@ -52,14 +63,14 @@ __global__ void __launch_bounds__(256) gather_dual_kernel(PointSrc src, int64_t 
                                                           __nv_bfloat16* __restrict__ X, int ldx,
                                                           uint8_t* __restrict__ X8, int ldx8,
                                                           int lo_off, float inv_s) {
-    const int nq = ldx >> 2;
+    const uint32_t nq = (uint32_t)ldx >> 2;
     if (src.count) m = min(m, (int64_t)*src.count);
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < m * nq;
          t += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t lp = t / nq;
-        const int c = (int)(t - lp * nq) * 4;
+        const uint32_t lp = (uint32_t)t / nq;
+        const int c = (int)((uint32_t)t - lp * nq) * 4;
         const float4 r = gather_quad(src, p0 + lp, calib, map0, map1, c);
-        store4(X + lp * ldx + c, r);
+        store4(X + (int64_t)lp * ldx + c, r);
         const float v[4] = {r.x * inv_s, r.y * inv_s, r.z * inv_s, r.w * inv_s};
         uint32_t hw = 0, lw = 0;
 #pragma unroll
@@ -69,7 +80,7 @@ __global__ void __launch_bounds__(256) gather_dual_kernel(PointSrc src, int64_t 
             hw |= (uint32_t)h.__x << (8 * j);
             lw |= (uint32_t)l.__x << (8 * j);
         }
-        uint8_t* row = X8 + lp * ldx8;
+        uint8_t* row = X8 + (int64_t)lp * ldx8;
         *reinterpret_cast<uint32_t*>(row + c) = hw;
         *reinterpret_cast<uint32_t*>(row + lo_off + c) = lw;
     }
@@ -88,7 +99,7 @@ cudaError_t launch_gather(const PointSrc& src, int64_t p0, int64_t m, const Cali
                           const Map& map0, const Map& map1, float* X, int ldx,
                           cudaStream_t stream) {
     if (m <= 0) return cudaSuccess;
-    const int64_t total = m * (ldx / 4);
+    const int64_t total = m * ((ldx / 4 + kQPT - 1) / kQPT);
     gather_kernel<float><<<gather_blocks(src, total), 256, 0, stream>>>(src, p0, m, calib, map0,
                                                                        map1, X, ldx);
     return cudaGetLastError();
@@ -98,7 +109,7 @@ cudaError_t launch_gather_bf16(const PointSrc& src, int64_t p0, int64_t m, const
                                const Map& map0, const Map& map1, __nv_bfloat16* X, int ldx,
                                cudaStream_t stream) {
     if (m <= 0) return cudaSuccess;
-    const int64_t total = m * (ldx / 4);
+    const int64_t total = m * ((ldx / 4 + kQPT - 1) / kQPT);
     gather_kernel<__nv_bfloat16><<<gather_blocks(src, total), 256, 0, stream>>>(src, p0, m, calib,
                                                                                map0, map1, X, ldx);
     return cudaGetLastError();

@@ -57,6 +57,8 @@ __device__ __forceinline__ float4 ld4(const float* p) {
 }
 
 // Position of point p; returns its frame (0 unless the source spans frames).
+// Node indices and keys are below 2^31 (int32 lists; (N + 1)^3 <= 513^3), so
+// they are decoded with 32-bit unsigned divisions.
 __device__ __forceinline__ int point_xyz(const PointSrc& src, int64_t p, float& x, float& y,
                                          float& z) {
     if (src.mode == PTS_XYZ || src.mode == PTS_XYZ_IDX) {
@@ -64,32 +66,36 @@ __device__ __forceinline__ int point_xyz(const PointSrc& src, int64_t p, float& 
         x = src.xyz[3 * q + 0];
         y = src.xyz[3 * q + 1];
         z = src.xyz[3 * q + 2];
-        return src.maps0 ? (int)((int64_t)src.keys[p] / src.slot_div) : 0;
+        return src.maps0 ? (int)((uint32_t)src.keys[p] / (uint32_t)src.slot_div) : 0;
     }
     if (src.mode == PTS_COLUMN) {
         // key = pixel (N + 1) + k; pixel centre (2i+1)/width - 1, depth 1 - 2k/N
-        const int64_t key = (int64_t)src.list[p];
-        const int64_t n1 = src.N + 1;
-        const int64_t pix = key / n1;
+        const uint32_t key = (uint32_t)src.list[p];
+        const uint32_t n1 = (uint32_t)src.N + 1u;
+        const uint32_t pix = key / n1;
         const int k = (int)(key - pix * n1);
-        const int i = (int)(pix % src.width);
-        const int j = (int)(pix / src.width);
+        const uint32_t wd = (uint32_t)src.width;
+        const int j = (int)(pix / wd);
+        const int i = (int)(pix - (uint32_t)j * wd);
         const float inv = 1.0f / (float)src.width;   // exact for power-of-two widths
         x = __fmaf_rn((float)(2 * i + 1), inv, -1.0f);
         y = __fmaf_rn((float)(2 * j + 1), inv, -1.0f);
         z = __fmaf_rn(-(float)k, 2.0f / (float)src.N, 1.0f);
         return 0;
     }
-    int64_t idx = (src.mode == PTS_LIST) ? (int64_t)src.list[p] : src.base + p;
+    uint32_t idx = (src.mode == PTS_LIST) ? (uint32_t)src.list[p] : (uint32_t)(src.base + p);
     int f = 0;
     if (src.maps0) {
-        f = (int)(idx / src.slot_div);
-        idx -= (int64_t)f * src.slot_div;
+        const uint32_t sd = (uint32_t)src.slot_div;
+        f = (int)(idx / sd);
+        idx -= (uint32_t)f * sd;
     }
-    const int64_t n1 = src.N + 1;
-    const int i = (int)(idx % n1);
-    const int j = (int)((idx / n1) % n1);
-    const int k = (int)(idx / (n1 * n1));
+    const uint32_t n1 = (uint32_t)src.N + 1u;
+    const uint32_t row = idx / n1;             // k (N + 1) + j
+    const int i = (int)(idx - row * n1);
+    const uint32_t kk = row / n1;
+    const int j = (int)(row - kk * n1);
+    const int k = (int)kk;
     const float h = 2.0f / (float)src.N;   // exact for power-of-two N
     x = __fmaf_rn((float)i, h, -1.0f);
     y = __fmaf_rn((float)j, h, -1.0f);
@@ -107,9 +113,84 @@ __device__ __forceinline__ float4 tap4(const Map& mp, int64_t e) {
     return ld4(static_cast<const float*>(mp.data) + e);
 }
 
-// Channels c..c+3 of the MLP input row of point p: the bilinear sample of
-// map0 (channels [0, C0)) or map1 ([C0, C0 + C1)) at the point's projection,
-// then the projected depth at C0 + C1, then zero padding.
+// A point's projection, the frame's maps and the four bilinear taps of
+// each map: everything its channels share.
+struct PointSample {
+    Map map0, map1;
+    float zh, zl;                  // projected depth as hi + lo
+    int64_t e0[4], e1[4];          // tap element offsets (channel 0) in map0 / map1
+    float w0[4], w1[4];            // bilinear weights w00, w10, w01, w11 of each map
+};
+
+__device__ __forceinline__ void taps_of(const Map& mp, float uh, float ul, float vh, float vl,
+                                        int64_t (&e)[4], float (&w)[4]) {
+    int i0, j0;
+    float a, b;
+    texel_coord(uh, ul, mp.W, i0, a);
+    texel_coord(vh, vl, mp.H, j0, b);
+    const int i1 = min(max(i0 + 1, 0), mp.W - 1);
+    const int j1 = min(max(j0 + 1, 0), mp.H - 1);
+    i0 = min(max(i0, 0), mp.W - 1);
+    j0 = min(max(j0, 0), mp.H - 1);
+    e[0] = ((int64_t)j0 * mp.W + i0) * mp.C;
+    e[1] = ((int64_t)j0 * mp.W + i1) * mp.C;
+    e[2] = ((int64_t)j1 * mp.W + i0) * mp.C;
+    e[3] = ((int64_t)j1 * mp.W + i1) * mp.C;
+    w[0] = (1.f - a) * (1.f - b);
+    w[1] = a * (1.f - b);
+    w[2] = (1.f - a) * b;
+    w[3] = a * b;
+}
+
+__device__ __forceinline__ PointSample sample_point(const PointSrc& src, int64_t p,
+                                                    const Calib& calib_in, const Map& map0_in,
+                                                    const Map& map1_in) {
+    PointSample ps;
+    float x, y, z;
+    const int f = point_xyz(src, p, x, y, z);
+    const bool multi = src.maps0 != nullptr;
+    // by value: a reference that may name the kernel's parameter would put
+    // the parameter in local memory
+    const Calib calib = multi ? src.calibs[f] : calib_in;
+    ps.map0 = multi ? src.maps0[f] : map0_in;
+    ps.map1 = multi ? (src.maps1 ? src.maps1[f] : Map{nullptr, 0, 0, 0, 0}) : map1_in;
+    float uh, ul, vh, vl;
+    affine_ff(calib.c + 0, x, y, z, uh, ul);
+    affine_ff(calib.c + 4, x, y, z, vh, vl);
+    affine_ff(calib.c + 8, x, y, z, ps.zh, ps.zl);
+    if (ps.map0.C > 0) taps_of(ps.map0, uh, ul, vh, vl, ps.e0, ps.w0);
+    if (ps.map1.C > 0) taps_of(ps.map1, uh, ul, vh, vl, ps.e1, ps.w1);
+    return ps;
+}
+
+// Channels c..c+3 of the sampled point's MLP input row: the bilinear sample
+// of map0 (channels [0, C0)) or map1 ([C0, C0 + C1)), then the projected
+// depth at C0 + C1, then zero padding.
+__device__ __forceinline__ float4 sample_quad(const PointSample& ps, int c) {
+    const int C0 = ps.map0.C, C1 = ps.map1.C;
+    if (c >= C0 + C1) return make_float4(c == C0 + C1 ? __fadd_rn(ps.zh, ps.zl) : 0.f, 0.f, 0.f, 0.f);
+    // selections by value (constant indices keep the arrays in registers)
+    const bool first = c < C0;
+    const Map& mp = first ? ps.map0 : ps.map1;
+    const int64_t cc = first ? c : c - C0;
+    const float4 f00 = tap4(mp, (first ? ps.e0[0] : ps.e1[0]) + cc);
+    const float4 f10 = tap4(mp, (first ? ps.e0[1] : ps.e1[1]) + cc);
+    const float4 f01 = tap4(mp, (first ? ps.e0[2] : ps.e1[2]) + cc);
+    const float4 f11 = tap4(mp, (first ? ps.e0[3] : ps.e1[3]) + cc);
+    const float w00 = first ? ps.w0[0] : ps.w1[0], w10 = first ? ps.w0[1] : ps.w1[1];
+    const float w01 = first ? ps.w0[2] : ps.w1[2], w11 = first ? ps.w0[3] : ps.w1[3];
+    float4 r;
+    r.x = fmaf(w11, f11.x, fmaf(w01, f01.x, fmaf(w10, f10.x, w00 * f00.x)));
+    r.y = fmaf(w11, f11.y, fmaf(w01, f01.y, fmaf(w10, f10.y, w00 * f00.y)));
+    r.z = fmaf(w11, f11.z, fmaf(w01, f01.z, fmaf(w10, f10.z, w00 * f00.z)));
+    r.w = fmaf(w11, f11.w, fmaf(w01, f01.w, fmaf(w10, f10.w, w00 * f00.w)));
+    return r;
+}
+
+// Channels c..c+3 of the MLP input row of point p (one quad on its own,
+// the same arithmetic as sample_point + sample_quad; written out so that
+// only the map holding channel c is touched, which keeps the register count
+// of the kernels that inline it next to their hot loops).
 __device__ __forceinline__ float4 gather_quad(const PointSrc& src, int64_t p, const Calib& calib_in,
                                               const Map& map0_in, const Map& map1_in, int c) {
     float x, y, z;
