@@ -5,10 +5,13 @@
 // small to fill the GPU, where the chain gather -> one GEMM per layer -> last
 // layer would be ten dependent launches of a few microseconds of work each.
 //
-// Work split: a cluster of kCL CTAs owns a tile of kFP points.  Every CTA
+// Work split: a cluster of CL CTAs owns a tile of kFP points (CL = 8, the
+// portable cluster size, or 16 for host-sized batches of at most as many
+// tiles as 16-CTA clusters fit on the GPU at once: half the arithmetic and
+// weight traffic per SM, so a small batch finishes sooner).  Every CTA
 // assembles the tile's input rows itself (projection + bilinear sample, the
 // same device code as the gather kernel), then for each hidden layer computes
-// its 1/kCL share of the output neurons for all kFP points and stores that
+// its 1/CL share of the output neurons for all kFP points and stores that
 // slice into every CTA's copy of the layer output through distributed shared
 // memory; one cluster barrier per layer publishes it.  The weights are read
 // once per tile per cluster (each CTA reads its own rows), from L2.
@@ -20,7 +23,7 @@
 // partial sums meet in shared memory, in a fixed order (deterministic).
 //
 // Shape rules (checked on the host, fused_ok): hidden widths n_out with
-// n_out / kCL a power of two in [8, 512]; K1, K2, ldw multiples of 4; at
+// n_out / CL a power of two in [8, 512]; K1, K2, ldw multiples of 4; at
 // most 4 outputs in the last layer; 16-byte aligned weights and biases.
 //
 // No waits other than the hardware cluster barrier, which every CTA of a
@@ -38,6 +41,7 @@ namespace {
 
 constexpr int kFP = 16;     // points per cluster tile
 constexpr int kCL = 8;      // CTAs per cluster (portable cluster size)
+constexpr int kCLWide = 16; // CTAs per cluster for small host-sized batches (non-portable)
 constexpr int kFT = 256;    // threads per CTA
 constexpr int kNW = kFT / 32;
 constexpr int kNJ = 8;      // neurons per warp task
@@ -68,7 +72,7 @@ __device__ __forceinline__ void load_wq(float4 (&w)[kNJ], const float* __restric
         w[j] = kq < Kq ? ld4(wrow + (int64_t)j * ldw + 4 * kq) : make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
-// One hidden layer of the tile: this CTA's S = n_out / kCL neurons, stored
+// One hidden layer of the tile: this CTA's S = n_out / CL neurons, stored
 // into every CTA's `out` ([kFP][n_out]), then a cluster barrier.
 //
 // A warp task is kNJ consecutive neurons over one of KW interleaved K-splits;
@@ -79,12 +83,13 @@ __device__ __forceinline__ void load_wq(float4 (&w)[kNJ], const float* __restric
 // summed over the lanes by recursive halving (each step exchanges half of the
 // values), which leaves lane l the sums of point l/2, neurons 4 (l & 1) ..
 // + 3; K-splits meet in shared memory in a fixed order.
+template <int CL>
 __device__ __forceinline__ void fused_layer(const FusedLayer& Ly, float slope,
                                             const float* __restrict__ in,
                                             const float* __restrict__ xs, int ldx,
                                             float* out, float* __restrict__ red, unsigned rank,
                                             cg::cluster_group& cl) {
-    const int S = Ly.n_out / kCL;
+    const int S = Ly.n_out / CL;
     const int groups = S / kNJ;
     const int KW = groups >= kNW ? 1 : kNW / groups;
     const int warp = threadIdx.x >> 5;
@@ -154,19 +159,21 @@ __device__ __forceinline__ void fused_layer(const FusedLayer& Ly, float slope,
         s.w = lrelu(s.w + b.w, slope);
         float* dst = out + p * Ly.n_out + (int)rank * S + j;
 #pragma unroll
-        for (int r = 0; r < kCL; ++r)
+        for (int r = 0; r < CL; ++r)
             *reinterpret_cast<float4*>(cl.map_shared_rank(dst, (unsigned)r)) = s;
     }
     cl.sync();
 }
 
-__global__ void __cluster_dims__(kCL, 1, 1) __launch_bounds__(kFT, 1)
+// Launched with a cluster dimension of CL (launch attribute).
+template <int CL>
+__global__ void __launch_bounds__(kFT, 1)
     mlp_fused_kernel(FusedNet net, PointSrc src, int64_t p0, int64_t m, Calib calib, Map map0,
                      Map map1, Epilogue epi) {
     cg::cluster_group cl = cg::this_cluster();
     const unsigned rank = cl.block_rank();
-    const int64_t cid = blockIdx.x / kCL;
-    const int64_t ncl = gridDim.x / kCL;
+    const int64_t cid = blockIdx.x / CL;
+    const int64_t ncl = gridDim.x / CL;
     extern __shared__ float4 smem4[];
     float* xs = reinterpret_cast<float*>(smem4);   // [kFP][ldx]
     float* hb0 = xs + kFP * net.ldx;               // [kFP][<= max_hidden]
@@ -179,36 +186,36 @@ __global__ void __cluster_dims__(kCL, 1, 1) __launch_bounds__(kFT, 1)
     if (src.count) m = min(m, (int64_t)*src.count);
     const int nq = net.ldx >> 2;
     const int64_t ntiles = (m + kFP - 1) / kFP;
-    constexpr int kPerRank = kFP / kCL;   // points each CTA gathers
+    constexpr int kPerRank = kFP / CL;   // points each CTA gathers
     for (int64_t tile = cid; tile < ntiles; tile += ncl) {
         const int64_t t0 = tile * kFP;
         const int np = (int)(m - t0 < kFP ? m - t0 : kFP);
-        // input rows: CTA `rank` assembles points rank, rank + kCL, ... and
+        // input rows: CTA `rank` assembles points rank, rank + CL, ... and
         // stores them into every CTA's copy
         for (int e = threadIdx.x; e < kPerRank * nq; e += kFT) {
             const int i = e / nq;
             const int c = (e - i * nq) * 4;
-            const int p = (int)rank + kCL * i;
+            const int p = (int)rank + CL * i;
             const float4 r = p < np ? gather_quad(src, p0 + t0 + p, calib, map0, map1, c)
                                     : make_float4(0.f, 0.f, 0.f, 0.f);
             float* dst = xs + p * net.ldx + c;
 #pragma unroll
-            for (int q = 0; q < kCL; ++q)
+            for (int q = 0; q < CL; ++q)
                 *reinterpret_cast<float4*>(cl.map_shared_rank(dst, (unsigned)q)) = r;
         }
         cl.sync();
         const float* in = nullptr;
         for (int l = 0; l + 1 < net.nl; ++l) {
             float* out = (l & 1) ? hb1 : hb0;
-            fused_layer(net.L[l], net.slope, in, xs, net.ldx, out, red, rank, cl);
+            fused_layer<CL>(net.L[l], net.slope, in, xs, net.ldx, out, red, rank, cl);
             in = out;
         }
-        // last layer and epilogue: CTA `rank` takes points rank, rank + kCL, ...
+        // last layer and epilogue: CTA `rank` takes points rank, rank + CL, ...
         {
             const int K = Ll.K1 + Ll.K2;
             const int lane = threadIdx.x & 31;
             const int w = threadIdx.x >> 5;
-            const int p = (int)rank + kCL * w;
+            const int p = (int)rank + CL * w;
             if (w < kPerRank && p < np) {
                 float acc[4] = {0.f, 0.f, 0.f, 0.f};
                 for (int k = lane; k < K; k += 32) {
@@ -228,19 +235,64 @@ __global__ void __cluster_dims__(kCL, 1, 1) __launch_bounds__(kFT, 1)
 
 bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
+template <int CL>
 int max_clusters() {
     static int cached = -1;
     if (cached >= 0) return cached;
-    if (cudaFuncSetAttribute(mlp_fused_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if (cudaFuncSetAttribute(mlp_fused_kernel<CL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)kSmemBytes) != cudaSuccess)
         return cached = 0;
+    if (CL > 8 && cudaFuncSetAttribute(mlp_fused_kernel<CL>,
+                                       cudaFuncAttributeNonPortableClusterSizeAllowed,
+                                       1) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return cached = 0;
+    }
     cudaLaunchConfig_t cfg{};
-    cfg.gridDim = dim3(kCL);
+    cfg.gridDim = dim3(CL);
     cfg.blockDim = dim3(kFT);
     cfg.dynamicSmemBytes = kSmemBytes;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = CL;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
     int n = 0;
-    if (cudaOccupancyMaxActiveClusters(&n, mlp_fused_kernel, &cfg) != cudaSuccess) n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, mlp_fused_kernel<CL>, &cfg) != cudaSuccess) {
+        (void)cudaGetLastError();
+        n = 0;
+    }
     return cached = n;
+}
+
+template <int CL>
+cudaError_t launch_cl(const FusedNet& net, const PointSrc& src, int64_t p0, int64_t m,
+                      const Calib& calib, const Map& map0, const Map& map1, const Epilogue& epi,
+                      int64_t grid_cl, cudaStream_t stream) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3((unsigned)(grid_cl * CL));
+    cfg.blockDim = dim3(kFT);
+    cfg.dynamicSmemBytes = kSmemBytes;
+    cfg.stream = stream;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = CL;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, mlp_fused_kernel<CL>, net, src, p0, m, calib, map0, map1, epi);
+}
+
+// The hidden widths split into 16 slices of at least kNJ neurons.
+bool wide_ok(const FusedNet& n) {
+    for (int l = 0; l + 1 < n.nl; ++l) {
+        const int S = n.L[l].n_out / kCLWide;
+        if (n.L[l].n_out % kCLWide || S < kNJ || (S & (S - 1))) return false;
+    }
+    return true;
 }
 
 }  // namespace
@@ -272,17 +324,22 @@ cudaError_t launch_mlp_fused(const FusedNet& net, const PointSrc& src, int64_t p
                              const Calib& calib, const Map& map0, const Map& map1,
                              const Epilogue& epi, cudaStream_t stream) {
     if (m <= 0) return cudaSuccess;
-    const int ncl = max_clusters();
+    const int ncl = max_clusters<kCL>();
     if (ncl <= 0) return cudaErrorInvalidConfiguration;
     const int64_t tiles = (m + kFP - 1) / kFP;
+    if (!src.count && wide_ok(net)) {
+        // a host-sized batch that 16-CTA clusters take in one round
+        const int nwide = max_clusters<kCLWide>();
+        if (tiles <= nwide) {
+            const cudaError_t e =
+                launch_cl<kCLWide>(net, src, p0, m, calib, map0, map1, epi, tiles, stream);
+            if (e == cudaSuccess) return e;
+            (void)cudaGetLastError();   // a refused launch configuration: use 8-CTA clusters
+        }
+    }
     // a device-resident count gets every co-resident cluster (persistent loop)
     const int64_t grid_cl = src.count ? ncl : std::min<int64_t>(tiles, ncl);
-    cudaLaunchConfig_t cfg{};
-    cfg.gridDim = dim3((unsigned)(grid_cl * kCL));
-    cfg.blockDim = dim3(kFT);
-    cfg.dynamicSmemBytes = kSmemBytes;
-    cfg.stream = stream;
-    return cudaLaunchKernelEx(&cfg, mlp_fused_kernel, net, src, p0, m, calib, map0, map1, epi);
+    return launch_cl<kCL>(net, src, p0, m, calib, map0, map1, epi, grid_cl, stream);
 }
 
 }  // namespace pifu
