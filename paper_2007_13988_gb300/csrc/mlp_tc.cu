@@ -58,12 +58,39 @@ constexpr int kEpiWarps = 8;
 constexpr int kThreads = 64 + 32 * kEpiWarps;
 
 constexpr int kFuseFloats = 4 * 256 + 2 * 4 * TBM + 16;   // last-layer W, exchange, flags
+constexpr int kStageRowBytes = 64;                          // store staging: 64 B per row
+constexpr int kStageBytes = kEpiWarps * 32 * kStageRowBytes; // 32 rows per epilogue warp
 
 __host__ __device__ constexpr uint32_t tc_smem_bytes(int BN) {
     // operand ring + 1024-byte alignment slack + barriers + staged bias and
-    // column scales + fused last layer
+    // column scales + fused last layer + output staging
     return (uint32_t)TSTAGES * (TBM * TBK * 2 + BN * TBK * 2) + 1024 + 256 + 2 * kMaxN * 4 +
-           kFuseFloats * 4;
+           kFuseFloats * 4 + kStageBytes;
+}
+static_assert(tc_smem_bytes(256) <= 227 * 1024, "shared memory of the widest tile");
+
+// Store a warp's 32 rows x 64 bytes (lane l holds row l's four 16-byte
+// pieces v[0..3]) to dst(row) + 16 j: through the warp's shared-memory
+// staging area so that each global store instruction writes 8 rows x 64
+// contiguous bytes (full 32-byte sectors) instead of 32 rows x 16 bytes.
+// Pieces are XOR-swizzled by row so both the write and the read-back take the
+// minimum number of shared-memory wavefronts.  Rows with !live skip the store.
+__device__ __forceinline__ void store_rows64(uint4* stage, const uint4 (&v)[4], int lane,
+                                             uint8_t* row_base, int64_t row_stride, int row0,
+                                             int M) {
+    const int sw = (lane >> 1) & 3;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) stage[lane * 4 + (j ^ sw)] = v[j];
+    __syncwarp();
+    const int j = lane & 3;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int r = (lane >> 2) + 8 * i;
+        const uint4 x = stage[r * 4 + (j ^ ((r >> 1) & 3))];
+        if (row0 + r < M)
+            *reinterpret_cast<uint4*>(row_base + (int64_t)(row0 + r) * row_stride + 16 * j) = x;
+    }
+    __syncwarp();
 }
 
 // 64 consecutive TMEM columns of the warp's 32 lanes: four x16 loads, one wait.
@@ -117,6 +144,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_linear_kernel(
     float* sW5 = scol + kMaxN;               // fused last layer: [4][BN]
     float* sxch = sW5 + 4 * 256;             // [2 buffers][4 outputs][128 rows] partial sums
     volatile uint32_t* sflag = reinterpret_cast<volatile uint32_t*>(sxch + 2 * 4 * TBM);  // [2][4]
+    uint4* sstage = reinterpret_cast<uint4*>(reinterpret_cast<uint8_t*>(sxch + 2 * 4 * TBM) + 64);
 
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
@@ -269,9 +297,9 @@ __global__ void __launch_bounds__(kThreads, 1) tc_linear_kernel(
                         for (int jo = 0; jo < 4; ++jo)
                             if (jo < fl.n_out) part[jo] = fmaf(a, sW5[jo * BN + c0 + cc], part[jo]);
                     }
-                } else if (row < M && MODE == TC_E4M3_E4M3) {
-                    uint8_t* out8 = static_cast<uint8_t*>(out_raw);
-                    uint4* dst = reinterpret_cast<uint4*>(out8 + (int64_t)row * ldo + n0 + c0);
+                } else if (MODE == TC_E4M3_E4M3) {
+                    // 64 E4M3 values = 64 bytes of the row: one staged pass
+                    uint4 pk4[4];
 #pragma unroll
                     for (int v = 0; v < NC / 16; ++v) {
                         uint32_t pk[4];
@@ -287,31 +315,46 @@ __global__ void __launch_bounds__(kThreads, 1) tc_linear_kernel(
                             }
                             pk[jj] = pack_e4m3x4(e[0], e[1], e[2], e[3]);
                         }
-                        dst[v] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                        pk4[v] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
                     }
-                } else if (row < M) {
-                    __nv_bfloat16* out = static_cast<__nv_bfloat16*>(out_raw);
-                    uint4* dst = reinterpret_cast<uint4*>(out + (int64_t)row * ldo + n0 + c0);
+                    if (NC == 64)
+                        store_rows64(sstage + (warp - 2) * 32 * 4, pk4, lane,
+                                     static_cast<uint8_t*>(out_raw) + n0 + c0, ldo, m0 + q * 32, M);
+                    else if (row < M)
 #pragma unroll
-                    for (int v = 0; v < NC / 8; ++v) {
-                        uint32_t pk[4];
+                        for (int v = 0; v < NC / 16; ++v)
+                            reinterpret_cast<uint4*>(static_cast<uint8_t*>(out_raw) +
+                                                     (int64_t)row * ldo + n0 + c0)[v] = pk4[v];
+                } else {
+                    // 64 BF16 values = 128 bytes of the row: two staged passes of 64 bytes
 #pragma unroll
-                        for (int jj = 0; jj < 4; ++jj) {
-                            const int cc = v * 8 + 2 * jj;
-                            float a, c;
-                            if (MODE == TC_BF16) {
-                                a = __uint_as_float(r[cc]) + bb[c0 + cc];
-                                c = __uint_as_float(r[cc + 1]) + bb[c0 + cc + 1];
-                            } else {
-                                a = fmaf(__uint_as_float(r[cc]), sc[c0 + cc], bb[c0 + cc]);
-                                c = fmaf(__uint_as_float(r[cc + 1]), sc[c0 + cc + 1],
-                                         bb[c0 + cc + 1]);
+                    for (int hb = 0; hb < NC / 32; ++hb) {
+                        uint4 pk4[4];
+#pragma unroll
+                        for (int v = 0; v < 4; ++v) {
+                            uint32_t pk[4];
+#pragma unroll
+                            for (int jj = 0; jj < 4; ++jj) {
+                                const int cc = hb * 32 + v * 8 + 2 * jj;
+                                float a, c;
+                                if (MODE == TC_BF16) {
+                                    a = __uint_as_float(r[cc]) + bb[c0 + cc];
+                                    c = __uint_as_float(r[cc + 1]) + bb[c0 + cc + 1];
+                                } else {
+                                    a = fmaf(__uint_as_float(r[cc]), sc[c0 + cc], bb[c0 + cc]);
+                                    c = fmaf(__uint_as_float(r[cc + 1]), sc[c0 + cc + 1],
+                                             bb[c0 + cc + 1]);
+                                }
+                                a = a >= 0.f ? a : slope * a;
+                                c = c >= 0.f ? c : slope * c;
+                                pk[jj] = pack_bf16x2(a, c);
                             }
-                            a = a >= 0.f ? a : slope * a;
-                            c = c >= 0.f ? c : slope * c;
-                            pk[jj] = pack_bf16x2(a, c);
+                            pk4[v] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
                         }
-                        dst[v] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                        store_rows64(sstage + (warp - 2) * 32 * 4, pk4, lane,
+                                     reinterpret_cast<uint8_t*>(static_cast<__nv_bfloat16*>(out_raw) +
+                                                                n0 + c0 + 32 * hb),
+                                     (int64_t)ldo * 2, m0 + q * 32, M);
                     }
                 }
             }
