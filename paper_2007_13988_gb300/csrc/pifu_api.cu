@@ -255,7 +255,7 @@ struct BatchWs {
     int* list = nullptr;               // [cap] keys frame * slot_nodes + node
     int* recheck = nullptr;            // [cap]
     int* squeue = nullptr;             // [cap]
-    int* col_top = nullptr;            // [B][(N+1)^2]
+    int* col_top = nullptr;            // [B][2][(N+1)^2]: column top, then bottom
     float* hit_xyz = nullptr;          // [B npix][3]
     int* hit_pix = nullptr;            // [B npix]
     Map* d_maps0 = nullptr;            // [kMaxBatch] device
@@ -313,7 +313,7 @@ struct pifu_ctx {
     float* hit_xyz = nullptr;
     int* hit_pix = nullptr;
     int64_t hit_cap = 0;
-    int* col_top = nullptr;       // render: per node column, highest non-empty depth
+    int* col_top = nullptr;       // render: per node column, highest and lowest non-empty depth
     // view-culled final level: candidate keys and their occupancies
     int* cull_list = nullptr;
     float* cull_values = nullptr;
@@ -984,7 +984,7 @@ int ensure_level_ws(pifu_ctx* ctx, int N) {
     CK(dev_alloc(&ctx->values, nodes));
     CK(dev_alloc(&ctx->list, nodes));
     dev_free(ctx->col_top);
-    CK(dev_alloc(&ctx->col_top, (int64_t)(N + 1) * (N + 1)));
+    CK(dev_alloc(&ctx->col_top, 2 * (int64_t)(N + 1) * (N + 1)));
     if (nodes > ctx->recheck_cap) {
         dev_free(ctx->recheck);
         dev_free(ctx->squeue);
@@ -2134,7 +2134,7 @@ int batch_ensure(pifu_ctx* ctx, int B, int N, int64_t npix) {
     CK(dev_alloc(&b.list, cap));
     CK(dev_alloc(&b.recheck, cap));
     CK(dev_alloc(&b.squeue, cap));
-    CK(dev_alloc(&b.col_top, (int64_t)(N + 1) * (N + 1) * Bn));
+    CK(dev_alloc(&b.col_top, 2 * (int64_t)(N + 1) * (N + 1) * Bn));
     CK(dev_alloc(&b.hit_xyz, 3 * np * Bn));
     CK(dev_alloc(&b.hit_pix, np * Bn));
     b.B = Bn;

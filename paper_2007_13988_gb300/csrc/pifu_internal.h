@@ -393,7 +393,8 @@ struct RenderArgs {
     float* hit_xyz;       // [width*height][3] surface points of hits
     int* hit_pix;         // pixel index per hit
     unsigned int* hit_count;
-    int* top;             // [(N+1)^2] scratch: highest non-empty depth node per column
+    int* top;             // [2][(N+1)^2] scratch per frame: highest non-empty depth node
+                          // per column, then N - the lowest
     // Several frames (lockstep form): frame f's volume starts f slot_nodes
     // values / f slot_words words further, its outputs f width*height pixels
     // further, and its hits carry pixel keys f width*height + pixel.

@@ -22,16 +22,20 @@ namespace {
 // Highest depth-node index k (z index, 0..N) at which node column (i, j) has
 // any evaluated or inside node: one thread per bitset word (k, j, word), one
 // atomicMax per set bit into top[j][i], which starts at -1 (empty column).
+// With `bot`, also N - (lowest such k) into bot[j][i] (also from -1): the
+// last ray sample index from the observer at which the column is non-empty.
 __global__ void __launch_bounds__(256) column_top_kernel(int N, int row_words,
                                                          const uint32_t* __restrict__ eval,
                                                          const uint32_t* __restrict__ bin,
-                                                         int* __restrict__ top, int64_t slot_words) {
+                                                         int* __restrict__ top, int* __restrict__ bot,
+                                                         int64_t slot_words, int64_t slot_top) {
     const int n1 = N + 1;
     {
         const int64_t f = blockIdx.y;   // frame of a lockstep batch
         eval += f * slot_words;
         bin += f * slot_words;
-        top += f * (int64_t)n1 * n1;
+        top += f * slot_top;
+        if (bot) bot += f * slot_top;
     }
     const int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (w >= (int64_t)n1 * n1 * row_words) return;
@@ -42,10 +46,12 @@ __global__ void __launch_bounds__(256) column_top_kernel(int N, int row_words,
     const int j = (int)(row % n1);
     const int k = (int)(row / n1);
     int* t = top + (int64_t)j * n1 + wx * 32;
+    int* u = bot ? bot + (int64_t)j * n1 + wx * 32 : nullptr;
     while (bits) {
         const int b = __ffs(bits) - 1;
         bits &= bits - 1u;
         atomicMax(t + b, k);
+        if (u) atomicMax(u + b, N - k);
     }
 }
 
@@ -80,7 +86,7 @@ __global__ void __launch_bounds__(256) render_rays_kernel(RenderArgs a) {
         a.values += frame * a.slot_nodes;
         a.eval += frame * a.slot_words;
         a.bin += frame * a.slot_words;
-        a.top += frame * (int64_t)(a.N + 1) * (a.N + 1);
+        a.top += frame * 2 * (int64_t)(a.N + 1) * (a.N + 1);
         if (a.depth) a.depth += frame * npix;
         if (a.mask) a.mask += frame * npix;
         if (a.rgb) a.rgb += frame * npix * 3;
@@ -105,8 +111,11 @@ __global__ void __launch_bounds__(256) render_rays_kernel(RenderArgs a) {
         const int64_t c0 = (int64_t)iy0 * n1 + ix0;
         const int ktop = max(max(a.top[c0], a.top[c0 + 1]), max(a.top[c0 + n1], a.top[c0 + n1 + 1]));
         const int kstart = ktop < 0 ? a.N + 1 : a.N - ktop;
+        // and the samples farther than every node of the four columns are 0
+        const int* bt = a.top + (int64_t)n1 * n1;
+        const int kend = max(max(bt[c0], bt[c0 + 1]), max(bt[c0 + n1], bt[c0 + n1 + 1]));
         float vprev = 0.f;
-        for (int k = kstart; k <= a.N; ++k) {
+        for (int k = kstart; k <= kend; ++k) {
             const int iz = a.N - k;
             const int64_t row0 = (int64_t)iz * n1 + iy0;
             const int64_t row1 = row0 + 1;
@@ -166,12 +175,13 @@ cudaError_t launch_render_rays(const RenderArgs& a, cudaStream_t stream) {
     const int64_t n1 = a.N + 1;
     const int slots = a.slots > 1 ? a.slots : 1;
     if (slots > 65535 || (int64_t)slots * npix > 2147483647LL) return cudaErrorInvalidValue;
+    // per frame: top [(N+1)^2] then bottom [(N+1)^2], both from -1
     cudaError_t e =
-        cudaMemsetAsync(a.top, 0xff, (size_t)(n1 * n1 * slots) * sizeof(int), stream);   // -1
+        cudaMemsetAsync(a.top, 0xff, (size_t)(2 * n1 * n1 * slots) * sizeof(int), stream);
     if (e != cudaSuccess) return e;
     const int64_t nt = n1 * n1 * a.row_words;
     column_top_kernel<<<dim3((unsigned)((nt + 255) / 256), (unsigned)slots), 256, 0, stream>>>(
-        a.N, a.row_words, a.eval, a.bin, a.top, a.slot_words);
+        a.N, a.row_words, a.eval, a.bin, a.top, a.top + n1 * n1, a.slot_words, 2 * n1 * n1);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     render_rays_kernel<<<dim3((unsigned)((npix + 255) / 256), (unsigned)slots), 256, 0, stream>>>(a);
@@ -359,7 +369,7 @@ cudaError_t launch_cull_select(const CullArgs& a, cudaStream_t stream) {
     if (e != cudaSuccess) return e;
     const int64_t nt = n1 * n1 * a.row_words;
     column_top_kernel<<<dim3((unsigned)((nt + 255) / 256), 1u), 256, 0, stream>>>(
-        a.Nc, a.row_words, a.bin, a.bin, a.top, 0);
+        a.Nc, a.row_words, a.bin, a.bin, a.top, nullptr, 0, 0);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     cull_select_kernel<<<(unsigned)((npix + 255) / 256), 256, 0, stream>>>(a);
