@@ -176,8 +176,8 @@ typedef struct {
  * a = ReLU((Gg c + gg) (h - mu) / sqrt(var + eps) + Gb c + gb), h = W a + b,
  * and O = sigmoid(h).  Limits: C and K multiples of 8, n_z >= 2,
  * n_blocks 1 .. 8.  Such a context serves pifu_query, pifu_query_ex (FP32,
- * BF16, MIXED), pifu_localize and pifu_render (FP32, BF16, MIXED, no
- * surrogate); the FP8 forms, the surrogate and the graph forms return
+ * BF16, MIXED), pifu_localize, pifu_render, pifu_frame and pifu_frames
+ * (BF16, MIXED); the FP8 forms and the surrogate return
  * PIFU_ERR_UNSUPPORTED.  The blob is validated completely on the
  * host before any CUDA call.  Errors: PIFU_ERR_FORMAT, PIFU_ERR_UNSUPPORTED
  * (hidden width not a multiple of 8), PIFU_ERR_OOM, PIFU_ERR_CUDA,

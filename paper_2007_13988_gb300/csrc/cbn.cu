@@ -276,6 +276,11 @@ bool cbn_f32_ok(const CbnF32& net) {
     return slice <= 4 * kPf * kThreads && smem_bytes(net) <= 227 * 1024;
 }
 
+cudaError_t cbn_f32_prepare(const CbnF32& net) {
+    if (!cbn_f32_ok(net)) return cudaErrorInvalidValue;
+    return max_clusters(net) > 0 ? cudaSuccess : cudaErrorInvalidConfiguration;
+}
+
 cudaError_t launch_cbn_f32(const CbnF32& net, const PointSrc& src, int64_t m, const Calib& calib,
                            const Map& map, const Epilogue& epi, cudaStream_t stream) {
     if (m <= 0) return cudaSuccess;

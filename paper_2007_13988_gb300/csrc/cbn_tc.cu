@@ -148,7 +148,7 @@ __global__ void __launch_bounds__(kThreads, 1) cbn_tc_kernel(
     const uint32_t tmem = *tslot;
     const uint32_t tm_g = tmem;
     const uint32_t tm_h = tmem + K2;
-    const int M = p.M;
+    const int M = p.m_dev ? min(p.M, (int)*p.m_dev) : p.M;   // a device-resident count
     const int n_tiles = (M + TM - 1) / TM;
 
     bool ok = true;
@@ -371,7 +371,8 @@ __global__ void __launch_bounds__(256) cbn_gather_kernel(PointSrc src, int64_t p
                                                          float* __restrict__ z) {
     const uint32_t nq = (uint32_t)C / 4 + 1;          // feature quads + the depth quad
     const uint32_t ng = (nq + 3) / 4;
-    const int64_t total = m * ng;   // < 2^32: at most 2^20 rows of at most 257 groups
+    if (src.count) m = min(m, (int64_t)*src.count);
+    const int64_t total = m * ng;   // < 2^32: at most 2^22 rows of at most 257 groups
     const Map none{nullptr, 0, 0, 0, 0};
     for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < total;
          w += (int64_t)gridDim.x * blockDim.x) {
@@ -399,12 +400,14 @@ __global__ void __launch_bounds__(256) cbn_gather_kernel(PointSrc src, int64_t p
 // allows so far (raised when a larger network needs more).
 uint32_t g_attr[2][64] = {};
 
+int g_sms[64] = {};
+
 template <int K>
-cudaError_t launch_k(const CbnTcMaps& mp, const CbnTcArgs& a, cudaStream_t s) {
-    int dev = 0, sms = 0;
+cudaError_t prepare_k(int C, int nb, int* sms_out) {
+    int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
-    const Layout L = layout_of(a.C, K, a.nb);
+    const Layout L = layout_of(C, K, nb);
     const int idx = K == 128 ? 1 : 0;
     if (!(dev >= 0 && dev < 64 && g_attr[idx][dev] >= L.total)) {
         e = cudaFuncSetAttribute(cbn_tc_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -412,8 +415,21 @@ cudaError_t launch_k(const CbnTcMaps& mp, const CbnTcArgs& a, cudaStream_t s) {
         if (e != cudaSuccess) return e;
         if (dev >= 0 && dev < 64) g_attr[idx][dev] = L.total;
     }
-    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (dev >= 0 && dev < 64 && g_sms[dev] > 0) {
+        *sms_out = g_sms[dev];
+        return cudaSuccess;
+    }
+    e = cudaDeviceGetAttribute(sms_out, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess && dev >= 0 && dev < 64) g_sms[dev] = *sms_out;
+    return e;
+}
+
+template <int K>
+cudaError_t launch_k(const CbnTcMaps& mp, const CbnTcArgs& a, cudaStream_t s) {
+    int sms = 0;
+    cudaError_t e = prepare_k<K>(a.C, a.nb, &sms);
     if (e != cudaSuccess) return e;
+    const Layout L = layout_of(a.C, K, a.nb);
     const int tiles = (a.M + TM - 1) / TM;
     const int grid = tiles < sms ? tiles : sms;
     cbn_tc_kernel<K><<<grid, kThreads, L.total, s>>>(*mp.tmX, *mp.tmG, *mp.tmW, a);
@@ -432,9 +448,16 @@ cudaError_t launch_cbn_gather(const PointSrc& src, int64_t p0, int64_t m, const 
                               cudaStream_t stream) {
     if (m <= 0) return cudaSuccess;
     const int64_t total = m * ((C / 4 + 1 + 3) / 4);
+    // a device-resident count gets a fixed, SM-filling grid that strides
     const int64_t blocks = std::min<int64_t>((total + 255) / 256, 152 * 16);
     cbn_gather_kernel<<<(unsigned)blocks, 256, 0, stream>>>(src, p0, m, calib, map, X, C, z);
     return cudaGetLastError();
+}
+
+cudaError_t cbn_tc_prepare(int C, int K, int nb) {
+    if (!cbn_tc_ok(C, K, nb)) return cudaErrorInvalidValue;
+    int sms = 0;
+    return K == 128 ? prepare_k<128>(C, nb, &sms) : prepare_k<64>(C, nb, &sms);
 }
 
 cudaError_t launch_cbn_tc(const CbnTcMaps& mp, const CbnTcArgs& a, cudaStream_t s) {

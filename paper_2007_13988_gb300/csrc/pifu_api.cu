@@ -1052,13 +1052,13 @@ bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
 // m_dev (optional): the batch size is device-resident, at most m <= kChunkTC
 // (graph form); m is then only the capacity the launches are sized for.
 int run_cbn_tc(pifu_ctx* ctx, const PointSrc& src, int64_t m, const Map& map, const Calib& calib,
-               const Epilogue& epi, cudaStream_t s);
+               const Epilogue& epi, cudaStream_t s, const unsigned int* m_dev);
 int run_mlp_tc(pifu_ctx* ctx, const DevNet& net, const PointSrc& src_in, int64_t m,
                const Map& map0, const Map& map1, const Calib& calib, const Epilogue& epi,
                cudaStream_t s, const unsigned int* m_dev = nullptr, bool f8 = false) {
     if (net.kind == kNetCbn) {
-        if (f8 || m_dev) return PIFU_ERR_UNSUPPORTED;
-        return run_cbn_tc(ctx, src_in, m, map0, calib, epi, s);
+        if (f8) return PIFU_ERR_UNSUPPORTED;
+        return run_cbn_tc(ctx, src_in, m, map0, calib, epi, s, m_dev);
     }
     if (!net.tc_ok) return PIFU_ERR_UNSUPPORTED;
     if (f8 && !net.f8_ok) return PIFU_ERR_STATE;
@@ -1157,22 +1157,29 @@ int run_mlp_tc(pifu_ctx* ctx, const DevNet& net, const PointSrc& src_in, int64_t
 // The CBN + SoftZ network on the tensor cores over a host-sized batch, in
 // passes of at most kChunkTC points: gather (BF16 features, FP32 depth), then
 // the whole network in one launch.
-int run_cbn_tc(pifu_ctx* ctx, const PointSrc& src, int64_t m, const Map& map, const Calib& calib,
-               const Epilogue& epi, cudaStream_t s) {
+int run_cbn_tc(pifu_ctx* ctx, const PointSrc& src_in, int64_t m, const Map& map,
+               const Calib& calib, const Epilogue& epi, cudaStream_t s,
+               const unsigned int* m_dev) {
     CbnDev& d = ctx->cbn;
     if (!d.tc_ok) return PIFU_ERR_UNSUPPORTED;
     const CbnF32& f = d.f32;
+    // a device-resident count is one pass of capacity m (the graph forms
+    // reserve its rows before capture)
+    const int64_t chunk = m_dev ? std::max<int64_t>(m, 1) : kChunkTC;
+    if (m_dev && m > kTcRowsMax) return PIFU_ERR_ARG;
     {
-        const int st = ensure_tc_rows(ctx, std::min<int64_t>(m, kChunkTC));
+        const int st = ensure_tc_rows(ctx, std::min<int64_t>(m, chunk));
         if (st != PIFU_OK) return st;
     }
+    PointSrc src = src_in;
+    src.count = m_dev;
     float* zbuf = reinterpret_cast<float*>(ctx->Hb[0]);
     const CbnTcMaps maps{&d.tmX, &d.tmG, &d.tmW};
     Profiler& pr = ctx->prof;
     const double flops_pt = 2.0 * ((double)f.n_z * f.K + 2.0 * f.nb * f.C * f.K +
                                    (double)(f.nb - 1) * f.K * f.K + f.K);
-    for (int64_t p0 = 0; p0 < m; p0 += kChunkTC) {
-        const int64_t mc = std::min<int64_t>(kChunkTC, m - p0);
+    for (int64_t p0 = 0; p0 < m; p0 += chunk) {
+        const int64_t mc = std::min<int64_t>(chunk, m - p0);
         cudaEvent_t ev = pr.begin(s);
         CK(launch_cbn_gather(src, p0, mc, calib, map, ctx->Xb, f.C, zbuf, s));
         pr.end(PIFU_K_GATHER, ev, s, 0.0, (double)mc * (4.0 * 4.0 * map.C + 2.0 * f.C + 4.0));
@@ -1189,6 +1196,7 @@ int run_cbn_tc(pifu_ctx* ctx, const PointSrc& src, int64_t m, const Map& map, co
         a.K = f.K;
         a.nb = f.nb;
         a.M = (int)mc;
+        a.m_dev = m_dev;
         a.p0 = p0;
         a.err = ctx->d_count + 1;
         a.epi = epi;
@@ -1207,14 +1215,15 @@ int run_mlp(pifu_ctx* ctx, const DevNet& net, const PointSrc& src_in, int64_t m,
         if (precision != PIFU_PREC_FP32)
             return run_mlp_tc(ctx, net, src_in, m, map0, map1, calib, epi, s, m_dev,
                               precision == PIFU_PREC_FP8);
-        if (m_dev) return PIFU_ERR_UNSUPPORTED;
+        PointSrc srcc = src_in;
+        srcc.count = m_dev;   // a device-resident count: persistent clusters
         const CbnF32& f = ctx->cbn.f32;
         const double flops = 2.0 * (double)m *
                              ((double)f.n_z * f.K + 2.0 * f.nb * f.C * f.K +
                               (double)(f.nb - 1) * f.K * f.K + f.K);
         const double wbytes = 4.0 * ((double)f.n_z * f.K + f.nb * (2.0 * f.C * f.K + f.K * f.K));
         cudaEvent_t ev = ctx->prof.begin(s);
-        CK(launch_cbn_f32(f, src_in, m, calib, map0, epi, s));
+        CK(launch_cbn_f32(f, srcc, m, calib, map0, epi, s));
         ctx->prof.end(PIFU_K_MLP_F32, ev, s, flops, wbytes + (double)m * 4.0 * (4.0 * map0.C + 1));
         return PIFU_OK;
     }
@@ -1785,7 +1794,7 @@ int g_eval(pifu_ctx* ctx, const DevNet& net, const PointSrc& src, int64_t cap,
     e2.list = ctx->recheck;
     // the fused kernel takes any queue length (at most the batch's); the
     // split-K path has a fixed capacity
-    const int64_t rcap = fused_ok(fused_of(net)) ? cap : kRecheckCap;
+    const int64_t rcap = (net.kind == kNetCbn || fused_ok(fused_of(net))) ? cap : kRecheckCap;
     st = run_mlp(ctx, net, s2, rcap, map, Map{}, cal, e2, s, PIFU_PREC_FP32, ctx->d_recheck);
     if (st != PIFU_OK) return st;
     CK(launch_accumulate(rechecked, ctx->d_recheck, (unsigned)rcap, ctx->d_count + 1, s));
@@ -2031,6 +2040,11 @@ int g_build(pifu_ctx* ctx, const FrameKey& k, const Map& occ, const Map& col, co
     }
     if (!ctx->h_gstats) CK(cudaHostAlloc(&ctx->h_gstats, sizeof(GraphStats), cudaHostAllocDefault));
     CK(tc_prepare());
+    if (ctx->net[0].kind == kNetCbn) {
+        const CbnF32& f = ctx->cbn.f32;
+        CK(cbn_f32_prepare(f));
+        if (ctx->cbn.tc_ok) CK(cbn_tc_prepare(f.C, f.K, f.nb));
+    }
     {
         // device-sized batches: the workspaces must hold a whole capacity
         const int st = ensure_tc_rows(ctx, kChunkTC);
@@ -2305,6 +2319,11 @@ int b_build(pifu_ctx* ctx, const BatchKey& k) {
         if (st != PIFU_OK) return st;
     }
     CK(tc_prepare());
+    if (ctx->net[0].kind == kNetCbn) {
+        const CbnF32& f = ctx->cbn.f32;
+        CK(cbn_f32_prepare(f));
+        if (ctx->cbn.tc_ok) CK(cbn_tc_prepare(f.C, f.K, f.nb));
+    }
     {
         const int st = ensure_tc_rows(ctx, std::max<int64_t>(bw.cap, (int64_t)k.B * k.width * k.height));
         if (st != PIFU_OK) return st;
@@ -3002,7 +3021,8 @@ int pifu_frame(pifu_ctx* ctx, const pifu_fmap* occ_map, const pifu_fmap* col_map
         return PIFU_ERR_ARG;
     if (!prec_valid(lv->precision) || lv->precision == PIFU_PREC_FP32) return PIFU_ERR_UNSUPPORTED;
     if (lv->subdivision != PIFU_SUBDIV_METHOD) return PIFU_ERR_UNSUPPORTED;
-    if (ctx->net[0].kind == kNetCbn) return PIFU_ERR_UNSUPPORTED;
+    if (ctx->net[0].kind == kNetCbn && (prec_f8(lv->precision) || lv->use_surrogate))
+        return PIFU_ERR_UNSUPPORTED;
     if (prec_f8(lv->precision) && !ctx->net[0].f8_ok) return PIFU_ERR_STATE;
     if (prec_mixed(lv->precision) && !(lv->margin >= 0.f && lv->margin <= 0.5f))
         return PIFU_ERR_ARG;
@@ -3143,7 +3163,8 @@ int pifu_frames(pifu_ctx* ctx, int B, const pifu_fmap* occ_maps, const pifu_fmap
     if ((int64_t)B * npix > kTcRowsMax) return PIFU_ERR_CAPACITY;
     if (!prec_valid(lv->precision) || lv->precision == PIFU_PREC_FP32) return PIFU_ERR_UNSUPPORTED;
     if (lv->subdivision != PIFU_SUBDIV_METHOD) return PIFU_ERR_UNSUPPORTED;
-    if (ctx->net[0].kind == kNetCbn) return PIFU_ERR_UNSUPPORTED;
+    if (ctx->net[0].kind == kNetCbn && (prec_f8(lv->precision) || lv->use_surrogate))
+        return PIFU_ERR_UNSUPPORTED;
     if (prec_f8(lv->precision) && !ctx->net[0].f8_ok) return PIFU_ERR_STATE;
     if (prec_mixed(lv->precision) && !(lv->margin >= 0.f && lv->margin <= 0.5f))
         return PIFU_ERR_ARG;

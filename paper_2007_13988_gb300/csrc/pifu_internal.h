@@ -344,6 +344,9 @@ struct CbnF32 {
     int C, n_z, K, nb;
 };
 bool cbn_f32_ok(const CbnF32& net);
+// Kernel attributes and the co-resident cluster count, set on the current
+// device (before a stream capture).
+cudaError_t cbn_f32_prepare(const CbnF32& net);
 // Occupancy logits of points 0 .. m - 1 of `src` (src.count: a device-resident
 // m) through the level / store epilogue; the feature is map's bilinear
 // sample, the depth its projection.
@@ -362,7 +365,8 @@ struct CbnTcArgs {
     const float* wlast;   // [K]
     const float* blast;   // [4]
     int C, n_z, K, nb;
-    int M;                // rows of this pass
+    int M;                // rows of this pass (with m_dev: the capacity)
+    const unsigned int* m_dev;   // optional device-resident row count (<= M)
     int64_t p0;           // point number of row 0 (for the epilogue)
     unsigned int* err;    // device error word
     Epilogue epi;
@@ -373,7 +377,10 @@ struct CbnTcMaps {
     const CUtensorMap* tmW;   // BF16 [(nb - 1) K][K] folded linear layers, box 64 x K
 };
 bool cbn_tc_ok(int C, int K, int nb);
-// X[r][0 .. C) = BF16 feature of point p0 + r, z[r] = its projected depth.
+// Kernel attributes on the current device (before a stream capture).
+cudaError_t cbn_tc_prepare(int C, int K, int nb);
+// X[r][0 .. C) = BF16 feature of point p0 + r, z[r] = its projected depth
+// (src.count: a device-resident m).
 cudaError_t launch_cbn_gather(const PointSrc& src, int64_t p0, int64_t m, const Calib& calib,
                               const Map& map, __nv_bfloat16* X, int C, float* z,
                               cudaStream_t stream);

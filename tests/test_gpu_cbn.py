@@ -115,7 +115,7 @@ def test_cbn_refused_forms(tiny):
     m = torch.empty((64, 64), dtype=torch.uint8, device="cuda")
     with pytest.raises(pifu.PifuError) as ei:
         pifu.pifu_frame(tiny.ctx, tiny.occ, tiny.col, w.calib, w.n0, w.num_levels, 64, 64, d, rgb,
-                        m, precision=pifu.PIFU_PREC_MIXED)
+                        m, precision=pifu.PIFU_PREC_FP8_MIXED)
     assert ei.value.status == pifu.PIFU_ERR_UNSUPPORTED
 
 
@@ -247,3 +247,64 @@ def test_cbn_mixed_localization_256(full, full_levels):
     vb = full.localize(precision=BF16)
     bb, _, _ = full.volume_host(vb)
     assert metrics.iou(bb, full_levels[-1].binary) >= 0.97
+
+
+# ---- graph forms -------------------------------------------------------------------
+
+def frame_outputs(B, R):
+    import torch
+    return (torch.empty((B, R, R), dtype=torch.float32, device="cuda"),
+            torch.empty((B, R, R, 3), dtype=torch.float32, device="cuda"),
+            torch.empty((B, R, R), dtype=torch.uint8, device="cuda"))
+
+
+@pytest.mark.parametrize("prec", [BF16, MIXED])
+def test_cbn_graph_frame_equals_host_driven(full, prec):
+    """The per-frame CUDA graph runs the same kernels on the same points as
+    pifu_localize + pifu_render (every point's arithmetic is independent of
+    its batch neighbours), so volume and render are identical."""
+    import torch
+    w = full.w
+    R = 256
+    d, rgb, m = (x[0] for x in frame_outputs(1, R))
+    vol = pifu.pifu_frame(full.ctx, full.occ, full.col, w.calib, w.n0, w.num_levels, R, R, d, rgb,
+                          m, precision=prec)
+    torch.cuda.synchronize()
+    gb, ge, gv = full.volume_host(vol)
+    g = (d.cpu().numpy(), rgb.cpu().numpy(), m.cpu().numpy())
+    n_graph = int(vol.n_eval)
+    hv = full.localize(precision=prec)
+    hb, he, hvv = full.volume_host(hv)
+    h = full.render(R, precision=BF16)
+    print("CBN graph vs host (%s): evaluations %d / %d" % (prec, n_graph, int(hv.n_eval)))
+    assert np.array_equal(gb, hb) and np.array_equal(ge, he)
+    np.testing.assert_array_equal(np.nan_to_num(gv, nan=-1), np.nan_to_num(hvv, nan=-1))
+    assert n_graph == int(hv.n_eval)
+    np.testing.assert_array_equal(g[2].astype(bool), h[2])
+    np.testing.assert_array_equal(np.nan_to_num(g[0], nan=-9), np.nan_to_num(h[0].astype(np.float32), nan=-9))
+    np.testing.assert_array_equal(g[1], h[1].astype(np.float32))
+
+
+def test_cbn_batch_equals_single_frames(full):
+    """Two frames of the animated stream in lockstep make the decisions each
+    makes alone (values to BF16 rounding: a round of at most 256 points runs
+    in FP32 alone and in BF16 + re-check in the batch)."""
+    import torch
+    w = full.w
+    R = 256
+    subj = synth.stream(n_figures=2, frames=64, seed=300)
+    maps = [[torch.from_numpy(x).cuda() for x in s.maps(7 * i)] for i, s in enumerate(subj)]
+    d, rgb, m = frame_outputs(2, R)
+    vols = pifu.pifu_frames(full.ctx, [o for o, _ in maps], [t for _, t in maps], [w.calib] * 2,
+                            w.n0, w.num_levels, R, R, d, rgb, m, precision=MIXED)
+    torch.cuda.synchronize()
+    for f in range(2):
+        bb, be, bv = full.volume_host(vols[f])
+        d1, rgb1, m1 = (x[0] for x in frame_outputs(1, R))
+        v1 = pifu.pifu_frame(full.ctx, maps[f][0], maps[f][1], w.calib, w.n0, w.num_levels, R, R,
+                             d1, rgb1, m1, precision=MIXED)
+        torch.cuda.synchronize()
+        sb, se, sv = full.volume_host(v1)
+        assert np.array_equal(bb, sb) and np.array_equal(be, se), f
+        assert np.max(np.abs(np.nan_to_num(bv, nan=0) - np.nan_to_num(sv, nan=0))) <= 0.03
+        assert np.mean(m[f].cpu().numpy() == m1.cpu().numpy()) >= 0.9999
