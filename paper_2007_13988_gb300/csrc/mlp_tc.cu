@@ -65,7 +65,7 @@ __host__ __device__ constexpr uint32_t tc_smem_bytes(int BN) {
     // operand ring + 1024-byte alignment slack + barriers + staged bias and
     // column scales + fused last layer + output staging
     return (uint32_t)TSTAGES * (TBM * TBK * 2 + BN * TBK * 2) + 1024 + 256 + 2 * kMaxN * 4 +
-           kFuseFloats * 4 + kStageBytes;
+           kFuseFloats * 4 + kStageBytes + 1024;   // + alignment of the staging area
 }
 static_assert(tc_smem_bytes(256) <= 227 * 1024, "shared memory of the widest tile");
 
@@ -121,10 +121,11 @@ __device__ __forceinline__ uint32_t pack_e4m3x4(float a, float b, float c, float
 template <int BN, bool FUSE, int MODE>
 __global__ void __launch_bounds__(kThreads, 1) tc_linear_kernel(
     const __grid_constant__ CUtensorMap tmA1, const __grid_constant__ CUtensorMap tmA2,
-    const __grid_constant__ CUtensorMap tmW, int nk1, int nk2, int M, int N,
-    const float* __restrict__ bias, float slope, void* __restrict__ out_raw, int ldo,
-    unsigned int* __restrict__ err, const unsigned int* __restrict__ m_dev, FuseLast fl,
-    const float* __restrict__ colscale, float out_scale) {
+    const __grid_constant__ CUtensorMap tmW, const __grid_constant__ CUtensorMap tmO, int use_tmo,
+    int nk1, int nk2, int M, int N, const float* __restrict__ bias, float slope,
+    void* __restrict__ out_raw, int ldo, unsigned int* __restrict__ err,
+    const unsigned int* __restrict__ m_dev, FuseLast fl, const float* __restrict__ colscale,
+    float out_scale) {
     static_assert(!(FUSE && MODE != TC_BF16), "the fused last layer reads BF16 activations");
     constexpr int TBKE = MODE == TC_BF16 ? TBK : 2 * TBK;   // elements per 128-byte K-block
     constexpr uint32_t A_BYTES = TBM * TBK * 2;
@@ -144,7 +145,10 @@ __global__ void __launch_bounds__(kThreads, 1) tc_linear_kernel(
     float* sW5 = scol + kMaxN;               // fused last layer: [4][BN]
     float* sxch = sW5 + 4 * 256;             // [2 buffers][4 outputs][128 rows] partial sums
     volatile uint32_t* sflag = reinterpret_cast<volatile uint32_t*>(sxch + 2 * 4 * TBM);  // [2][4]
-    uint4* sstage = reinterpret_cast<uint4*>(reinterpret_cast<uint8_t*>(sxch + 2 * 4 * TBM) + 64);
+    // per-warp store staging, 1024-byte aligned: its XOR pattern is the
+    // 64-byte swizzle, so a TMA store (tmO) can take it as it is
+    uint4* sstage = reinterpret_cast<uint4*>(
+        (reinterpret_cast<uintptr_t>(sxch + 2 * 4 * TBM) + 64 + 1023) & ~static_cast<uintptr_t>(1023));
 
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
@@ -351,10 +355,28 @@ __global__ void __launch_bounds__(kThreads, 1) tc_linear_kernel(
                             }
                             pk4[v] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
                         }
-                        store_rows64(sstage + (warp - 2) * 32 * 4, pk4, lane,
-                                     reinterpret_cast<uint8_t*>(static_cast<__nv_bfloat16*>(out_raw) +
-                                                                n0 + c0 + 32 * hb),
-                                     (int64_t)ldo * 2, m0 + q * 32, M);
+                        uint4* st = sstage + (warp - 2) * 32 * 4;
+                        if (use_tmo) {
+                            // the TMA engine writes the warp's 32 x 32 box (rows past the
+                            // tensor are dropped; rows past M are scratch of this pass)
+                            if (lane == 0) bulk_wait_read();   // the previous box was read
+                            __syncwarp();
+                            const int sw = (lane >> 1) & 3;
+#pragma unroll
+                            for (int jj = 0; jj < 4; ++jj) st[lane * 4 + (jj ^ sw)] = pk4[jj];
+                            fence_async_shared();
+                            __syncwarp();
+                            if (lane == 0) {
+                                tma_store_2d(&tmO, n0 + c0 + 32 * hb, m0 + q * 32, st);
+                                bulk_commit();
+                            }
+                        } else {
+                            store_rows64(st, pk4, lane,
+                                         reinterpret_cast<uint8_t*>(
+                                             static_cast<__nv_bfloat16*>(out_raw) + n0 + c0 +
+                                             32 * hb),
+                                         (int64_t)ldo * 2, m0 + q * 32, M);
+                        }
                     }
                 }
             }
@@ -403,6 +425,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_linear_kernel(
             }
         }
     }
+    if (use_tmo && warp >= 2 && lane == 0) bulk_wait();   // the output is written
     if (!ok) atomicOr(err, 1u);
     tc_fence_before();
     __syncthreads();
@@ -468,23 +491,28 @@ cudaError_t launch_bn(const TcLayerArgs& a, cudaStream_t s) {
     cfg.attrs = at;
     cfg.numAttrs = 1;
     const float* noscale = nullptr;
+    // the TMA-store epilogue needs the output map (BF16 output, not fused)
+    const int use_tmo = a.tmO ? 1 : 0;
+    const CUtensorMap& tmO = a.tmO ? *a.tmO : *a.tmW;
     if (a.fuse) {
         if (a.N != BN || a.fuse->n_out < 1 || a.fuse->n_out > 4) return cudaErrorInvalidValue;
         return cudaLaunchKernelEx(&cfg, tc_linear_kernel<BN, true, TC_BF16>, *a.tmA1, *a.tmA2,
-                                  *a.tmW, a.nk1, a.nk2, a.M, a.N, a.bias, a.slope, a.out, a.ldo,
-                                  a.err, a.m_dev, *a.fuse, noscale, 1.f);
+                                  *a.tmW, tmO, 0, a.nk1, a.nk2, a.M, a.N, a.bias, a.slope, a.out,
+                                  a.ldo, a.err, a.m_dev, *a.fuse, noscale, 1.f);
     }
     if (a.mode == TC_E4M3_E4M3)
         return cudaLaunchKernelEx(&cfg, tc_linear_kernel<BN, false, TC_E4M3_E4M3>, *a.tmA1,
-                                  *a.tmA2, *a.tmW, a.nk1, a.nk2, a.M, a.N, a.bias, a.slope, a.out,
-                                  a.ldo, a.err, a.m_dev, FuseLast{}, a.colscale, a.out_scale);
+                                  *a.tmA2, *a.tmW, tmO, 0, a.nk1, a.nk2, a.M, a.N, a.bias,
+                                  a.slope, a.out, a.ldo, a.err, a.m_dev, FuseLast{}, a.colscale,
+                                  a.out_scale);
     if (a.mode == TC_E4M3_BF16)
         return cudaLaunchKernelEx(&cfg, tc_linear_kernel<BN, false, TC_E4M3_BF16>, *a.tmA1,
-                                  *a.tmA2, *a.tmW, a.nk1, a.nk2, a.M, a.N, a.bias, a.slope, a.out,
-                                  a.ldo, a.err, a.m_dev, FuseLast{}, a.colscale, 1.f);
+                                  *a.tmA2, *a.tmW, tmO, use_tmo, a.nk1, a.nk2, a.M, a.N, a.bias,
+                                  a.slope, a.out, a.ldo, a.err, a.m_dev, FuseLast{}, a.colscale,
+                                  1.f);
     return cudaLaunchKernelEx(&cfg, tc_linear_kernel<BN, false, TC_BF16>, *a.tmA1, *a.tmA2,
-                              *a.tmW, a.nk1, a.nk2, a.M, a.N, a.bias, a.slope, a.out, a.ldo,
-                              a.err, a.m_dev, FuseLast{}, noscale, 1.f);
+                              *a.tmW, tmO, use_tmo, a.nk1, a.nk2, a.M, a.N, a.bias, a.slope,
+                              a.out, a.ldo, a.err, a.m_dev, FuseLast{}, noscale, 1.f);
 }
 
 }  // namespace
@@ -492,7 +520,8 @@ cudaError_t launch_bn(const TcLayerArgs& a, cudaStream_t s) {
 namespace {
 
 bool encode_2d(void* map, CUtensorMapDataType dtype, const void* base, uint64_t cols,
-               uint64_t rows, uint64_t row_stride_bytes, uint32_t box_cols, uint32_t box_rows) {
+               uint64_t rows, uint64_t row_stride_bytes, uint32_t box_cols, uint32_t box_rows,
+               CUtensorMapSwizzle swz = CU_TENSOR_MAP_SWIZZLE_128B) {
     if (!g_encode) {
         cudaDriverEntryPointQueryResult q;
         void* fn = nullptr;
@@ -508,7 +537,7 @@ bool encode_2d(void* map, CUtensorMapDataType dtype, const void* base, uint64_t 
     const cuuint32_t estr[2] = {1, 1};
     const CUresult r = g_encode(static_cast<CUtensorMap*>(map), dtype, 2,
                                 const_cast<void*>(base), dims, strides, box, estr,
-                                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                                CU_TENSOR_MAP_INTERLEAVE_NONE, swz,
                                 CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS;
@@ -520,6 +549,12 @@ bool tc_encode_2d_bf16(void* map, const void* base, uint64_t cols, uint64_t rows
                        uint64_t row_stride_bytes, uint32_t box_cols, uint32_t box_rows) {
     return encode_2d(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, base, cols, rows, row_stride_bytes,
                      box_cols, box_rows);
+}
+
+bool tc_encode_2d_bf16_out(void* map, const void* base, uint64_t cols, uint64_t rows,
+                           uint64_t row_stride_bytes) {
+    return encode_2d(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, base, cols, rows, row_stride_bytes, 32,
+                     32, CU_TENSOR_MAP_SWIZZLE_64B);
 }
 
 bool tc_encode_2d_u8(void* map, const void* base, uint64_t cols, uint64_t rows,

@@ -43,6 +43,8 @@ struct TcLayer {
     int Kw = 0, nk1 = 0, nk2 = 0, BN = 0;
     CUtensorMap tmW{};
     CUtensorMap tmA1{};   // the previous layer's BF16 output (l >= 1)
+    CUtensorMap tmO{};    // this layer's BF16 output, for the epilogue's TMA stores
+    bool tmO_ok = false;
 };
 
 // E4M3 form of one of f_O's leading wide hidden layers: W divided by a
@@ -756,6 +758,13 @@ int encode_act_maps(pifu_ctx* ctx, DevNet& net) {
                                (uint64_t)Ly.K1 * 2, 64, 128))
             return PIFU_ERR_CUDA;
     }
+    for (size_t l = 0; l < net.tc.size(); ++l) {
+        const DevLayer& Ly = net.layers[l];
+        net.tc[l].tmO_ok = tc_encode_2d_bf16_out(&net.tc[l].tmO, ctx->Hb[l % 2],
+                                                 (uint64_t)Ly.n_out, rows,
+                                                 (uint64_t)Ly.n_out * 2);
+        if (!net.tc[l].tmO_ok) return PIFU_ERR_CUDA;
+    }
     if (net.f8_ok) {
         if (!tc_encode_2d_u8(&net.tmX8, ctx->X8, (uint64_t)ctx->ldx8, rows, (uint64_t)ctx->ldx8,
                              128, 128))
@@ -1107,6 +1116,7 @@ int run_mlp_tc(pifu_ctx* ctx, const DevNet& net, const PointSrc& src_in, int64_t
             a.tmA1 = l > 0 ? &T.tmA1 : &net.tmX;
             a.tmA2 = &net.tmX;
             a.tmW = &T.tmW;
+            a.tmO = T.tmO_ok ? &T.tmO : nullptr;
             a.nk1 = T.nk1;
             a.nk2 = T.nk2;
             a.M = (int)mc;

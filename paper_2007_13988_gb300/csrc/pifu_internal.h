@@ -182,6 +182,8 @@ struct TcLayerArgs {
     const CUtensorMap* tmA1;
     const CUtensorMap* tmA2;
     const CUtensorMap* tmW;
+    const CUtensorMap* tmO;       // optional: BF16 output [rows][N], box 32 x 32, 64-byte
+                                  // swizzle (the epilogue then stores with TMA)
     int nk1, nk2, M, N, BN;       // nk1, nk2: 128-byte K-blocks of the two A segments
     const float* bias;
     float slope;
@@ -202,6 +204,10 @@ cudaError_t tc_prepare();
 // Encode a 2-D BF16 tensor map (128-byte swizzle, zero fill out of bounds).
 bool tc_encode_2d_bf16(void* map, const void* base, uint64_t cols, uint64_t rows,
                        uint64_t row_stride_bytes, uint32_t box_cols, uint32_t box_rows);
+// A layer's BF16 output as the epilogue's TMA stores see it: box 32 x 32,
+// 64-byte swizzle.
+bool tc_encode_2d_bf16_out(void* map, const void* base, uint64_t cols, uint64_t rows,
+                           uint64_t row_stride_bytes);
 // The same for 8-bit elements (E4M3 stored as bytes).
 bool tc_encode_2d_u8(void* map, const void* base, uint64_t cols, uint64_t rows,
                      uint64_t row_stride_bytes, uint32_t box_cols, uint32_t box_rows);
