@@ -296,16 +296,30 @@ int pifu_frames(pifu_ctx* ctx, int B, const pifu_fmap* occ_maps, const pifu_fmap
 /* ---- Tile autotuner (not in the paper) ----------------------------------------
  * Times every tensor-core hidden layer of f_O and f_T (and of f_O's E4M3
  * layers once calibrated) on a batch of `rows` points (128 .. 2^22) with each
- * output tile width BN in {64, 128, 256} dividing its width (the layer into
- * whose epilogue the last layer is fused keeps BN = its width), keeps the
- * fastest, and invalidates captured graphs.  The contents of the activation
- * workspaces are whatever they hold (only the timing matters).  Writes the
- * chosen BN and the mean ms per launch of each tuned layer, in order (f_O
- * layers, each E4M3 form before the BF16 form, then f_T), into bn_out /
- * ms_out (up to n_max entries, either may be null) and their number into
- * *n_layers.  Synchronises `stream`. */
+ * tile form allowed for it, keeps the fastest, and invalidates captured
+ * graphs.  A form is given by its tile code:
+ *   64, 128, 256  one CTA per 128-row x BN-column output tile, BN = the code
+ *                 (dividing the layer's width);
+ *   512           the CTA-pair form: two CTAs (a cluster of 2) share a
+ *                 256-row x 256-column tile through cta_group::2 MMAs, each
+ *                 holding half of the tile's operands (BF16 layers whose
+ *                 width 256 divides).
+ * The layer into whose epilogue the last layer is fused keeps its code (BN =
+ * its width).  The contents of the activation workspaces are whatever they
+ * hold (only the timing matters).  Writes the chosen code and the mean ms per
+ * launch of each tuned layer, in order (f_O layers, each E4M3 form before the
+ * BF16 form, then f_T), into bn_out / ms_out (up to n_max entries, either may
+ * be null) and their number into *n_layers.  Synchronises `stream`. */
 int pifu_autotune(pifu_ctx* ctx, int64_t rows, void* stream, int32_t* bn_out, double* ms_out,
                   int n_max, int* n_layers);
+
+/* Sets the tile code of every tuned layer, in pifu_autotune's order: codes[i]
+ * for layer i, n = the number of layers pifu_autotune reports (for instance a
+ * saved autotuner result).  A code must be allowed for its layer as above
+ * (E4M3 forms: 64, 128 or 256); the fused layer must keep its code.  Results
+ * do not depend on the codes.  Invalidates captured graphs; no device work.
+ * Errors: PIFU_ERR_ARG (n or a code not allowed; nothing is changed). */
+int pifu_set_tiles(pifu_ctx* ctx, const int32_t* codes, int n);
 
 /* ---- FP8 form of f_O (not in the paper) --------------------------------------
  * Calibrates and builds the E4M3 layers used by PIFU_PREC_FP8 and

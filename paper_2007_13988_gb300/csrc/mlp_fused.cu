@@ -5,10 +5,13 @@
 // small to fill the GPU, where the chain gather -> one GEMM per layer -> last
 // layer would be ten dependent launches of a few microseconds of work each.
 //
-// Work split: a cluster of CL CTAs owns a tile of kFP points (CL = 8, the
-// portable cluster size, or 16 for host-sized batches of at most as many
-// tiles as 16-CTA clusters fit on the GPU at once: half the arithmetic and
-// weight traffic per SM, so a small batch finishes sooner).  Every CTA
+// Work split: a cluster of CL CTAs owns a tile of kFP points, CL = 16, 8, 4
+// or 2 (16 is a non-portable size).  Larger clusters split each layer's
+// neurons finer, so one tile finishes sooner; smaller ones fit more clusters
+// on the GPU at once (2-CTA clusters: 76 tiles per round instead of 15), so a
+// batch of many tiles takes fewer rounds.  The host picks the size with the
+// fewest latency-weighted rounds (fused_pick; in a graph, a switch node set
+// on the device from the batch size picks among launches of each).  Every CTA
 // assembles the tile's input rows itself (projection + bilinear sample, the
 // same device code as the gather kernel), then for each hidden layer computes
 // its 1/CL share of the output neurons for all kFP points and stores that
@@ -31,6 +34,8 @@
 // same tiles and layers).
 #include <cooperative_groups.h>
 
+#include <algorithm>
+
 #include "epilogue.cuh"
 #include "gather.cuh"
 
@@ -40,18 +45,25 @@ namespace pifu {
 namespace {
 
 constexpr int kFP = 16;     // points per cluster tile
-constexpr int kCL = 8;      // CTAs per cluster (portable cluster size)
-constexpr int kCLWide = 16; // CTAs per cluster for small host-sized batches (non-portable)
+constexpr int kCL = 8;      // CTAs per cluster for a device-resident batch size
 constexpr int kFT = 256;    // threads per CTA
 constexpr int kNW = kFT / 32;
 constexpr int kNJ = 8;      // neurons per warp task
 constexpr int kAcc = kFP * kNJ;
-constexpr int kRed = 4096;  // K-split partial sums: max(kFP * S, kNW * kNJ * kFP)
 constexpr int kMaxLdx = 528;
 constexpr int kMaxHidden = 1024;
 constexpr int kMaxLast = 4096;   // floats of the last layer's weights kept in shared memory
-constexpr size_t kSmemBytes =
-    (size_t)(kFP * kMaxLdx + 2 * kFP * kMaxHidden + kRed + kMaxLast) * 4;
+
+// K-split partial sums: max(kFP * S, kNW * kNJ * kFP) floats, S <= kMaxHidden / CL
+template <int CL>
+__host__ __device__ constexpr int red_floats() {
+    return kFP * (kMaxHidden / CL) > kNW * kNJ * kFP ? kFP * (kMaxHidden / CL) : kNW * kNJ * kFP;
+}
+template <int CL>
+__host__ __device__ constexpr size_t smem_bytes() {
+    return (size_t)(kFP * kMaxLdx + 2 * kFP * kMaxHidden + red_floats<CL>() + kMaxLast) * 4;
+}
+static_assert(smem_bytes<2>() <= 227 * 1024, "shared memory of the 2-CTA form");
 
 __device__ __forceinline__ float lrelu(float v, float s) { return v >= 0.f ? v : s * v; }
 
@@ -178,8 +190,8 @@ __global__ void __launch_bounds__(kFT, 1)
     float* xs = reinterpret_cast<float*>(smem4);   // [kFP][ldx]
     float* hb0 = xs + kFP * net.ldx;               // [kFP][<= max_hidden]
     float* hb1 = hb0 + kFP * net.max_hidden;
-    float* red = hb1 + kFP * net.max_hidden;       // [kRed]
-    float* wl = red + kRed;                        // last layer's weights [n_out][ldw]
+    float* red = hb1 + kFP * net.max_hidden;       // [red_floats<CL>()]
+    float* wl = red + red_floats<CL>();            // last layer's weights [n_out][ldw]
     const FusedLayer& Ll = net.L[net.nl - 1];
     for (int e = threadIdx.x; e < Ll.n_out * Ll.ldw; e += kFT) wl[e] = Ll.W[e];
     __syncthreads();
@@ -240,7 +252,7 @@ int max_clusters() {
     static int cached = -1;
     if (cached >= 0) return cached;
     if (cudaFuncSetAttribute(mlp_fused_kernel<CL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)kSmemBytes) != cudaSuccess)
+                             (int)smem_bytes<CL>()) != cudaSuccess)
         return cached = 0;
     if (CL > 8 && cudaFuncSetAttribute(mlp_fused_kernel<CL>,
                                        cudaFuncAttributeNonPortableClusterSizeAllowed,
@@ -251,7 +263,7 @@ int max_clusters() {
     cudaLaunchConfig_t cfg{};
     cfg.gridDim = dim3(CL);
     cfg.blockDim = dim3(kFT);
-    cfg.dynamicSmemBytes = kSmemBytes;
+    cfg.dynamicSmemBytes = smem_bytes<CL>();
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeClusterDimension;
     at[0].val.clusterDim.x = CL;
@@ -274,7 +286,7 @@ cudaError_t launch_cl(const FusedNet& net, const PointSrc& src, int64_t p0, int6
     cudaLaunchConfig_t cfg{};
     cfg.gridDim = dim3((unsigned)(grid_cl * CL));
     cfg.blockDim = dim3(kFT);
-    cfg.dynamicSmemBytes = kSmemBytes;
+    cfg.dynamicSmemBytes = smem_bytes<CL>();
     cfg.stream = stream;
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeClusterDimension;
@@ -286,11 +298,12 @@ cudaError_t launch_cl(const FusedNet& net, const PointSrc& src, int64_t p0, int6
     return cudaLaunchKernelEx(&cfg, mlp_fused_kernel<CL>, net, src, p0, m, calib, map0, map1, epi);
 }
 
-// The hidden widths split into 16 slices of at least kNJ neurons.
-bool wide_ok(const FusedNet& n) {
+// Every hidden width splits into CL slices of a power-of-two number (at least
+// kNJ) of neurons.
+bool cl_ok(const FusedNet& n, int CL) {
     for (int l = 0; l + 1 < n.nl; ++l) {
-        const int S = n.L[l].n_out / kCLWide;
-        if (n.L[l].n_out % kCLWide || S < kNJ || (S & (S - 1))) return false;
+        const int S = n.L[l].n_out / CL;
+        if (n.L[l].n_out % CL || S < kNJ || (S & (S - 1))) return false;
     }
     return true;
 }
@@ -320,26 +333,95 @@ bool fused_ok(const FusedNet& n) {
     return true;
 }
 
-cudaError_t launch_mlp_fused(const FusedNet& net, const PointSrc& src, int64_t p0, int64_t m,
-                             const Calib& calib, const Map& map0, const Map& map1,
-                             const Epilogue& epi, cudaStream_t stream) {
-    if (m <= 0) return cudaSuccess;
-    const int ncl = max_clusters<kCL>();
-    if (ncl <= 0) return cudaErrorInvalidConfiguration;
-    const int64_t tiles = (m + kFP - 1) / kFP;
-    if (!src.count && wide_ok(net)) {
-        // a host-sized batch that 16-CTA clusters take in one round
-        const int nwide = max_clusters<kCLWide>();
-        if (tiles <= nwide) {
-            const cudaError_t e =
-                launch_cl<kCLWide>(net, src, p0, m, calib, map0, map1, epi, tiles, stream);
-            if (e == cudaSuccess) return e;
-            (void)cudaGetLastError();   // a refused launch configuration: use 8-CTA clusters
+namespace {
+
+// Latency of one tile relative to 8-CTA clusters (full-size f_O, GB300: one
+// round of 16-, 8-, 4- and 2-CTA clusters took 32, 36, 60 and 106 us).
+constexpr int kClSizes[4] = {16, 8, 4, 2};
+constexpr float kClLatency[4] = {0.88f, 1.f, 1.67f, 2.94f};
+
+int clusters_of(int CL) {
+    switch (CL) {
+        case 16: return max_clusters<16>();
+        case 8: return max_clusters<8>();
+        case 4: return max_clusters<4>();
+        case 2: return max_clusters<2>();
+        default: return 0;
+    }
+}
+
+// Index in `p` of the size with the fewest latency-weighted rounds for
+// `tiles` tiles; ties go to the larger clusters (lower latency).
+__host__ __device__ int fused_pick(const FusedPlan& p, long long tiles) {
+    int best = 0;
+    float best_cost = 3.0e38f;
+    for (int i = 0; i < p.n; ++i) {
+        const long long rounds = (tiles + p.ncl[i] - 1) / p.ncl[i];
+        const float cost = (float)rounds * p.lat[i];
+        if (cost < best_cost * 0.999f) {
+            best_cost = cost;
+            best = i;
         }
     }
+    return best;
+}
+
+__global__ void fused_switch_kernel(cudaGraphConditionalHandle h, FusedPlan plan,
+                                    const unsigned int* count, unsigned int cap) {
+    const unsigned int c = min(*count, cap);
+    cudaGraphSetConditional(h, c == 0u ? (unsigned)plan.n
+                                       : (unsigned)fused_pick(plan, ((long long)c + kFP - 1) / kFP));
+}
+
+}  // namespace
+
+FusedPlan fused_plan(const FusedNet& net) {
+    FusedPlan p;
+    for (int i = 0; i < 4; ++i) {
+        const int CL = kClSizes[i];
+        const int n = cl_ok(net, CL) ? clusters_of(CL) : 0;
+        if (n <= 0) continue;
+        p.cl[p.n] = CL;
+        p.ncl[p.n] = n;
+        p.lat[p.n] = kClLatency[i];
+        ++p.n;
+    }
+    return p;
+}
+
+cudaError_t launch_fused_switch(cudaGraphConditionalHandle h, const FusedPlan& plan,
+                                const unsigned int* count, unsigned int cap, cudaStream_t stream) {
+    fused_switch_kernel<<<1, 1, 0, stream>>>(h, plan, count, cap);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mlp_fused(const FusedNet& net, const PointSrc& src, int64_t p0, int64_t m,
+                             const Calib& calib, const Map& map0, const Map& map1,
+                             const Epilogue& epi, cudaStream_t stream, int cl) {
+    if (m <= 0) return cudaSuccess;
+    const int64_t tiles = (m + kFP - 1) / kFP;
+    if (cl == 0) {
+        if (src.count) {
+            cl = kCL;
+        } else {
+            const FusedPlan p = fused_plan(net);
+            if (p.n == 0) return cudaErrorInvalidConfiguration;
+            cl = p.cl[fused_pick(p, tiles)];
+        }
+    }
+    const int ncl = cl_ok(net, cl) ? clusters_of(cl) : 0;
+    if (ncl <= 0) return cudaErrorInvalidConfiguration;
     // a device-resident count gets every co-resident cluster (persistent loop)
     const int64_t grid_cl = src.count ? ncl : std::min<int64_t>(tiles, ncl);
-    return launch_cl<kCL>(net, src, p0, m, calib, map0, map1, epi, grid_cl, stream);
+    cudaError_t e = cudaErrorInvalidValue;
+    switch (cl) {
+        case 16: e = launch_cl<16>(net, src, p0, m, calib, map0, map1, epi, grid_cl, stream); break;
+        case 8: e = launch_cl<8>(net, src, p0, m, calib, map0, map1, epi, grid_cl, stream); break;
+        case 4: e = launch_cl<4>(net, src, p0, m, calib, map0, map1, epi, grid_cl, stream); break;
+        case 2: e = launch_cl<2>(net, src, p0, m, calib, map0, map1, epi, grid_cl, stream); break;
+        default: break;
+    }
+    return e;
 }
 
 }  // namespace pifu

@@ -432,6 +432,237 @@ __global__ void __launch_bounds__(kThreads, 1) tc_linear_kernel(
     if (warp == 1) tmem_dealloc(tmem, TMEM_COLS);
 }
 
+// ---- CTA-pair form ------------------------------------------------------------
+//
+// The same layer (BF16 operands and output, no fused last layer) on pairs of
+// CTAs (clusters of 2) issuing cta_group::2 MMAs of M = 256, N = 256.  A pair
+// walks 256 x 256 output tiles.  CTA r of the pair loads A rows m0 + 128 r
+// and W rows n0 + 128 r of each K-block into its own shared memory, so a
+// stage holds 32 KB per CTA instead of 48 KB for the same MMA work per SM:
+// the ring is PS stages deep (more MMA work in flight per byte of shared
+// memory) and each SM fetches a third less operand data from L2.
+//   * Both CTAs' TMA loads complete on the even CTA's `full` barrier, whose
+//     producer announces both CTAs' bytes.
+//   * The even CTA's lane 0 of warp 1 issues the MMAs; its commits arrive on
+//     the `empty` and `accf` barriers of both CTAs (multicast).
+//   * Each CTA's epilogue drains its own 128 rows x 256 columns of tensor
+//     memory and arrives on the even CTA's `acce` barrier.
+// Every wait is bounded as in tc_linear_kernel; before the CTAs leave, the
+// producers wait for the last releases of their stages and the pair meets at
+// a cluster barrier, so no arrival is still on its way to a CTA that exited.
+constexpr int kPairBN = 256;
+
+__host__ __device__ constexpr uint32_t tc_pair_smem_bytes(int PS, int SB) {
+    // operand ring + alignment slack + barriers + staged bias + output staging
+    return (uint32_t)PS * (TBM * TBK * 2 + (kPairBN / 2) * TBK * 2) + 1024 + 256 + kMaxN * 4 +
+           (uint32_t)SB * kStageBytes + 1024;
+}
+
+template <int PS, int SB>
+__global__ void __launch_bounds__(kThreads, 1) tc_pair_kernel(
+    const __grid_constant__ CUtensorMap tmA1, const __grid_constant__ CUtensorMap tmA2,
+    const __grid_constant__ CUtensorMap tmW, const __grid_constant__ CUtensorMap tmO, int use_tmo,
+    int nk1, int nk2, int M, int N, const float* __restrict__ bias, float slope,
+    __nv_bfloat16* __restrict__ out, int ldo, unsigned int* __restrict__ err,
+    const unsigned int* __restrict__ m_dev) {
+    constexpr int BN = kPairBN;
+    constexpr uint32_t A_BYTES = TBM * TBK * 2;          // this CTA's 128 rows
+    constexpr uint32_t B_BYTES = (BN / 2) * TBK * 2;     // this CTA's half of the columns
+    constexpr uint32_t TMEM_COLS = 2 * BN;               // two accumulators of 256 columns
+    static_assert((2 * PS + 4) * 8 + 4 <= 256, "barriers fit in front of the bias");
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* sA = reinterpret_cast<uint8_t*>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+    uint8_t* sB = sA + PS * A_BYTES;
+    uint64_t* full = reinterpret_cast<uint64_t*>(sB + PS * B_BYTES);
+    uint64_t* empty = full + PS;
+    uint64_t* accf = empty + PS;   // [2] accumulator ready (both CTAs)
+    uint64_t* acce = accf + 2;     // [2] accumulator drained (counted in the even CTA)
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(acce + 2);
+    float* sbias = reinterpret_cast<float*>(reinterpret_cast<uint8_t*>(full) + 256);
+    uint4* sstage = reinterpret_cast<uint4*>(
+        (reinterpret_cast<uintptr_t>(sbias + kMaxN) + 1023) & ~static_cast<uintptr_t>(1023));
+
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    const uint32_t rank = cluster_ctarank();   // 0: issues the MMAs
+    const int nk = nk1 + nk2;
+    const int n_tn = N / BN;
+    const int pair = blockIdx.x >> 1;
+    const int n_pairs = gridDim.x >> 1;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < PS; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&accf[b], 1);
+            mbar_init(&acce[b], 2 * kEpiWarps);   // every epilogue warp of both CTAs
+        }
+        fence_mbar_init();
+        if (nk1 > 0) prefetch_tmap(&tmA1);
+        prefetch_tmap(&tmA2);
+        prefetch_tmap(&tmW);
+    }
+    for (int c = threadIdx.x; c < N; c += blockDim.x) sbias[c] = bias[c];
+    // both CTAs' barriers exist before either CTA signals the other's, and
+    // both CTAs run before the pair allocates tensor memory
+    cluster_sync();
+    if (warp == 1) tmem_alloc_pair(tslot, TMEM_COLS);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tslot;
+    griddep_wait();
+    if (m_dev) M = min(M, (int)*m_dev);
+    const int n_tiles = ((M + 2 * TBM - 1) / (2 * TBM)) * n_tn;
+
+    bool ok = true;
+    if (warp == 0) {
+        if (lane == 0) {
+            // TMA producer of this CTA's halves; the bytes of both count on the
+            // even CTA's full barrier
+            uint32_t g = 0;
+            for (int t = pair; t < n_tiles && ok; t += n_pairs) {
+                const int m0 = (t / n_tn) * 2 * TBM + (int)rank * TBM;
+                const int n0 = (t % n_tn) * BN + (int)rank * (BN / 2);
+                for (int kb = 0; kb < nk; ++kb, ++g) {
+                    const uint32_t s = g % PS;
+                    const uint32_t u = g / PS;
+                    if (u > 0 && !mbar_wait(&empty[s], (u - 1) & 1u, kWaitLimit)) {
+                        ok = false;
+                        break;
+                    }
+                    if (rank == 0) mbar_arrive_expect_tx(&full[s], 2 * (A_BYTES + B_BYTES));
+                    const uint32_t fb = mapa_shared(smem_u32(&full[s]), 0);
+                    if (kb < nk1)
+                        tma_load_2d_pair(sA + s * A_BYTES, &tmA1, kb * TBK, m0, fb);
+                    else
+                        tma_load_2d_pair(sA + s * A_BYTES, &tmA2, (kb - nk1) * TBK, m0, fb);
+                    tma_load_2d_pair(sB + s * B_BYTES, &tmW, kb * TBK, n0, fb);
+                }
+            }
+            // the last release of every stage used has arrived here
+            if (ok) {
+                for (uint32_t s = 0; s < (uint32_t)PS && s < g; ++s) {
+                    const uint32_t uses = (g - s + PS - 1) / PS;
+                    if (!mbar_wait(&empty[s], (uses - 1) & 1u, kWaitLimit)) {
+                        ok = false;
+                        break;
+                    }
+                }
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0 && rank == 0) {
+            // MMA issuer of the pair
+            constexpr uint32_t idesc = idesc_bf16_f32(2 * TBM, BN);
+            uint32_t g = 0, i = 0;
+            for (int t = pair; t < n_tiles && ok; t += n_pairs, ++i) {
+                const uint32_t b = i & 1u, j = i >> 1;
+                if (j > 0 && !mbar_wait_cluster(&acce[b], (j - 1) & 1u, kWaitLimit)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t d = tmem + b * BN;
+                for (int kb = 0; kb < nk; ++kb, ++g) {
+                    const uint32_t s = g % PS;
+                    const uint32_t u = g / PS;
+                    if (!mbar_wait(&full[s], u & 1u, kWaitLimit)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t a0 = smem_u32(sA + s * A_BYTES);
+                    const uint32_t b0 = smem_u32(sB + s * B_BYTES);
+#pragma unroll
+                    for (int k = 0; k < 4; ++k)
+                        mma_bf16_pair(d, desc_k_sw128(a0 + k * 32), desc_k_sw128(b0 + k * 32),
+                                      idesc, (kb | k) != 0 ? 1u : 0u);
+                    mma_commit_pair(&empty[s], (uint16_t)3);
+                }
+                mma_commit_pair(&accf[b], (uint16_t)3);   // also after an error
+            }
+        }
+    } else {
+        // epilogue warps 2..9 of each CTA: its rows 32 (warp % 4) .. + 31 of
+        // the pair tile's half, warps 2-5 columns [0, 128), warps 6-9 [128, 256)
+        constexpr int HALF = BN / 2;
+        const int q = warp & 3;
+        const int cbase = ((warp - 2) >> 2) * HALF;
+        const uint32_t acce0 = mapa_shared(smem_u32(&acce[0]), 0);
+        uint4* stw = sstage + (warp - 2) * SB * 32 * 4;   // this warp's SB staging boxes
+        uint32_t i = 0, nbox = 0;
+        for (int t = pair; t < n_tiles; t += n_pairs, ++i) {
+            const uint32_t b = i & 1u, j = i >> 1;
+            const int m0 = (t / n_tn) * 2 * TBM + (int)rank * TBM;
+            const int n0 = (t % n_tn) * BN;
+            if (!__all_sync(0xffffffffu, mbar_wait(&accf[b], j & 1u, kWaitLimit))) {
+                ok = false;
+                break;
+            }
+            tc_fence_after();
+            const uint32_t tl = tmem + ((uint32_t)(q * 32) << 16) + b * BN;
+            const float* bb = sbias + n0;
+#pragma unroll 1
+            for (int c0 = cbase; c0 < cbase + HALF; c0 += 64) {
+                uint32_t r[64];
+                tmem_ld64(tl + (uint32_t)c0, r);
+#pragma unroll
+                for (int hb = 0; hb < 2; ++hb) {
+                    uint4 pk4[4];
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) {
+                        uint32_t pk[4];
+#pragma unroll
+                        for (int jj = 0; jj < 4; ++jj) {
+                            const int cc = hb * 32 + v * 8 + 2 * jj;
+                            float a = __uint_as_float(r[cc]) + bb[c0 + cc];
+                            float c = __uint_as_float(r[cc + 1]) + bb[c0 + cc + 1];
+                            a = a >= 0.f ? a : slope * a;
+                            c = c >= 0.f ? c : slope * c;
+                            pk[jj] = pack_bf16x2(a, c);
+                        }
+                        pk4[v] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                    }
+                    uint4* st = stw + (nbox % SB) * 32 * 4;
+                    ++nbox;
+                    if (use_tmo) {
+                        // at most SB - 1 of this warp's earlier boxes may still be read
+                        if (lane == 0) bulk_wait_read_n<SB - 1>();
+                        __syncwarp();
+                        const int sw = (lane >> 1) & 3;
+#pragma unroll
+                        for (int jj = 0; jj < 4; ++jj) st[lane * 4 + (jj ^ sw)] = pk4[jj];
+                        fence_async_shared();
+                        __syncwarp();
+                        if (lane == 0) {
+                            tma_store_2d(&tmO, n0 + c0 + 32 * hb, m0 + q * 32, st);
+                            bulk_commit();
+                        }
+                    } else {
+                        store_rows64(st, pk4, lane,
+                                     reinterpret_cast<uint8_t*>(out + n0 + c0 + 32 * hb),
+                                     (int64_t)ldo * 2, m0 + q * 32, M);
+                    }
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive_cluster(acce0 + b * 8u);
+        }
+    }
+    if (use_tmo && warp >= 2 && lane == 0) bulk_wait();
+    if (!ok) atomicOr(err, 1u);
+    tc_fence_before();
+    __syncwarp();
+    cluster_sync();
+    tc_fence_after();
+    if (warp == 1) tmem_dealloc_pair(tmem, TMEM_COLS);
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 
 // Per device: kernel attributes set (index by BN: 64, 128, 256) and SM count.
@@ -515,6 +746,83 @@ cudaError_t launch_bn(const TcLayerArgs& a, cudaStream_t s) {
                               a.out, a.ldo, a.err, a.m_dev, FuseLast{}, noscale, 1.f);
 }
 
+// CTA-pair form: ring depth and output staging boxes per epilogue warp.
+constexpr int kPairStages = 6;
+constexpr int kPairStageBufs = 1;
+static_assert(tc_pair_smem_bytes(kPairStages, kPairStageBufs) <= 227 * 1024,
+              "shared memory of the CTA-pair form");
+
+// Co-resident clusters of 2 per device (0: not known yet); finding them also
+// sets the kernel's shared-memory attribute.
+template <int PS, int SB>
+cudaError_t pair_clusters(int dev, int* out) {
+    static int g_pair_clusters[64] = {};
+    if (dev >= 0 && dev < 64 && g_pair_clusters[dev] > 0) {
+        *out = g_pair_clusters[dev];
+        return cudaSuccess;
+    }
+    const uint32_t smem = tc_pair_smem_bytes(PS, SB);
+    cudaError_t e = cudaFuncSetAttribute(tc_pair_kernel<PS, SB>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(2);
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 2;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int n = 0;
+    e = cudaOccupancyMaxActiveClusters(&n, tc_pair_kernel<PS, SB>, &cfg);
+    if (e != cudaSuccess) return e;
+    if (n <= 0) return cudaErrorInvalidConfiguration;
+    if (dev >= 0 && dev < 64) g_pair_clusters[dev] = n;
+    *out = n;
+    return cudaSuccess;
+}
+
+template <int PS, int SB>
+cudaError_t launch_pair_cfg(const TcLayerArgs& a, cudaStream_t s) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    int ncl = 0;
+    e = pair_clusters<PS, SB>(dev, &ncl);
+    if (e != cudaSuccess) return e;
+    const long long tiles = (long long)(a.N / kPairBN) * ((a.M + 2 * TBM - 1) / (2 * TBM));
+    const int clusters = (int)(tiles < ncl ? tiles : ncl);
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3((unsigned)(2 * clusters));
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = tc_pair_smem_bytes(PS, SB);
+    cfg.stream = s;
+    cudaLaunchAttribute at[2];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 2;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    at[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[1].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 2;
+    const int use_tmo = a.tmO ? 1 : 0;
+    const CUtensorMap& tmO = a.tmO ? *a.tmO : *a.tmW;
+    return cudaLaunchKernelEx(&cfg, tc_pair_kernel<PS, SB>, *a.tmA1, *a.tmA2, *a.tmW, tmO, use_tmo,
+                              a.nk1, a.nk2, a.M, a.N, a.bias, a.slope,
+                              static_cast<__nv_bfloat16*>(a.out), a.ldo, a.err, a.m_dev);
+}
+
+cudaError_t launch_pair(const TcLayerArgs& a, cudaStream_t s) {
+    // BF16 in and out, 256-column pair tiles, no fused last layer
+    if (a.BN != kPairBN || a.mode != TC_BF16 || a.fuse || a.N % kPairBN != 0)
+        return cudaErrorInvalidValue;
+    return launch_pair_cfg<kPairStages, kPairStageBufs>(a, s);
+}
+
 }  // namespace
 
 namespace {
@@ -564,18 +872,20 @@ bool tc_encode_2d_u8(void* map, const void* base, uint64_t cols, uint64_t rows,
 }
 
 cudaError_t tc_prepare() {
-    int dev = 0, sms = 0;
+    int dev = 0, sms = 0, ncl = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = ensure_attr<64>(dev);
     if (e == cudaSuccess) e = ensure_attr<128>(dev);
     if (e == cudaSuccess) e = ensure_attr<256>(dev);
     if (e == cudaSuccess) e = sm_count(dev, &sms);
+    if (e == cudaSuccess) e = pair_clusters<kPairStages, kPairStageBufs>(dev, &ncl);
     return e;
 }
 
 cudaError_t launch_tc_linear(const TcLayerArgs& a, cudaStream_t s) {
     if (a.M <= 0) return cudaSuccess;
     if (a.N > kMaxN) return cudaErrorInvalidValue;
+    if (a.pair) return launch_pair(a, s);
     switch (a.BN) {
         case 256: return launch_bn<256>(a, s);
         case 128: return launch_bn<128>(a, s);

@@ -41,6 +41,7 @@ struct DevLayer {
 struct TcLayer {
     __nv_bfloat16* W = nullptr;
     int Kw = 0, nk1 = 0, nk2 = 0, BN = 0;
+    bool pair = false;    // CTA-pair form (BN = 256; tmW's box is then 128 rows)
     CUtensorMap tmW{};
     CUtensorMap tmA1{};   // the previous layer's BF16 output (l >= 1)
     CUtensorMap tmO{};    // this layer's BF16 output, for the epilogue's TMA stores
@@ -370,6 +371,7 @@ struct pifu_ctx {
     cudaStream_t cap_stream = nullptr;    // capture of the frame
     cudaStream_t cap_stream2 = nullptr;   // capture of the loop bodies
     cudaStream_t cap_stream3 = nullptr;   // capture of conditional branches
+    cudaStream_t cap_stream4 = nullptr;   // capture of the FP32 cluster-size switch's bodies
     int* clist = nullptr;                 // graph form: conflicts of a round (keys)
     unsigned int* d_ccount = nullptr;
     int64_t clist_cap = 0;
@@ -827,7 +829,10 @@ int build_tc(pifu_ctx* ctx, const HostNet& hn, DevNet& net) {
         T.nk1 = Ly.K1 / 64;
         T.nk2 = has_x ? k2pad / 64 : 0;
         T.Kw = Ly.K1 + (has_x ? k2pad : 0);
+        // single-CTA tiles by default (pifu_autotune / pifu_set_tiles may
+        // choose the CTA-pair form)
         T.BN = Ly.n_out % 256 == 0 ? 256 : (Ly.n_out % 128 == 0 ? 128 : 64);
+        T.pair = false;
         std::vector<__nv_bfloat16> wb((size_t)Ly.n_out * T.Kw, __float2bfloat16(0.f));
         const std::vector<float>& wf = hn.W[l];   // [n_out][K1 | ldx]
         for (int o = 0; o < Ly.n_out; ++o) {
@@ -841,7 +846,7 @@ int build_tc(pifu_ctx* ctx, const HostNet& hn, DevNet& net) {
         CK(dev_alloc(&T.W, (int64_t)wb.size()));
         CK(cudaMemcpy(T.W, wb.data(), wb.size() * sizeof(__nv_bfloat16), cudaMemcpyHostToDevice));
         if (!tc_encode_2d_bf16(&T.tmW, T.W, (uint64_t)T.Kw, (uint64_t)Ly.n_out, (uint64_t)T.Kw * 2,
-                               64, (uint32_t)T.BN))
+                               64, (uint32_t)(T.pair ? T.BN / 2 : T.BN)))
             return PIFU_ERR_CUDA;
     }
     net.tc_ok = true;
@@ -1098,7 +1103,7 @@ int run_mlp_tc(pifu_ctx* ctx, const DevNet& net, const PointSrc& src_in, int64_t
         // the last layer rides in the last hidden layer's epilogue when that
         // layer is one tile wide and the last layer reads only its output
         const DevLayer& Ll = net.layers[L - 1];
-        const bool fuse = L > 1 && Ll.K2 == 0 && Ll.n_out <= 4 &&
+        const bool fuse = L > 1 && Ll.K2 == 0 && Ll.n_out <= 4 && !net.tc[L - 2].pair &&
                           net.tc[L - 2].BN == net.layers[L - 2].n_out;
         FuseLast fl{};
         if (fuse) {
@@ -1122,6 +1127,7 @@ int run_mlp_tc(pifu_ctx* ctx, const DevNet& net, const PointSrc& src_in, int64_t
             a.M = (int)mc;
             a.N = Ly.n_out;
             a.BN = T.BN;
+            a.pair = T.pair ? 1 : 0;
             a.bias = Ly.b;
             a.slope = net.slope;
             a.out = ctx->Hb[l % 2];
@@ -1139,6 +1145,7 @@ int run_mlp_tc(pifu_ctx* ctx, const DevNet& net, const PointSrc& src_in, int64_t
                 a.nk1 = Q.nk1;
                 a.nk2 = Q.nk2;
                 a.BN = Q.BN;
+                a.pair = 0;
                 a.mode = l + 1 < F ? TC_E4M3_E4M3 : TC_E4M3_BF16;
                 a.colscale = Q.colscale;
                 a.out_scale = Q.out_scale;
@@ -1220,7 +1227,8 @@ int run_cbn_tc(pifu_ctx* ctx, const PointSrc& src_in, int64_t m, const Map& map,
 
 int run_mlp(pifu_ctx* ctx, const DevNet& net, const PointSrc& src_in, int64_t m, const Map& map0,
             const Map& map1, const Calib& calib, const Epilogue& epi, cudaStream_t s,
-            int precision = PIFU_PREC_FP32, const unsigned int* m_dev = nullptr) {
+            int precision = PIFU_PREC_FP32, const unsigned int* m_dev = nullptr,
+            int fused_cl = 0) {
     if (net.kind == kNetCbn) {
         if (precision != PIFU_PREC_FP32)
             return run_mlp_tc(ctx, net, src_in, m, map0, map1, calib, epi, s, m_dev,
@@ -1253,7 +1261,7 @@ int run_mlp(pifu_ctx* ctx, const DevNet& net, const PointSrc& src_in, int64_t m,
             wbytes += 4.0 * (double)Ly.n_out * (Ly.fan_in + 1);
         }
         cudaEvent_t ev = pr.begin(s);
-        CK(launch_mlp_fused(fz, src, 0, m, calib, map0, map1, epi, s));
+        CK(launch_mlp_fused(fz, src, 0, m, calib, map0, map1, epi, s, fused_cl));
         pr.end(PIFU_K_MLP_F32, ev, s, flops,
                wbytes + (double)m * 4.0 * (4.0 * (map0.C + map1.C) + net.layers[L - 1].n_out));
         return PIFU_OK;
@@ -1727,6 +1735,50 @@ void sur_unpack(const pifu_ctx* ctx, const float* in, std::vector<float>& padded
 int g_add_cond(pifu_ctx* ctx, cudaStream_t s, cudaGraphConditionalHandle h,
                cudaGraphConditionalNodeType type, cudaGraph_t* body);
 
+int g_add_switch(pifu_ctx* ctx, cudaStream_t s, cudaGraphConditionalHandle h, int n,
+                 cudaGraph_t* bodies);
+int64_t launches_now(const pifu_ctx* ctx);
+
+// The FP32 pass over a device-sized queue in the graph.  With the fused
+// kernel, a switch node set on the device from the queue length launches it
+// with the cluster size that length calls for (few points: large clusters,
+// the lowest latency per tile; many: small clusters, more tiles per round).
+int g_recheck(pifu_ctx* ctx, const DevNet& net, const PointSrc& src, int64_t cap,
+              const Map& map, const Calib& cal, const Epilogue& epi, cudaStream_t s,
+              const unsigned int* m_dev) {
+    const FusedNet fz = fused_of(net);
+    const bool sw = net.kind != kNetCbn && ctx->cap_stream4 && s != ctx->cap_stream4 &&
+                    fused_ok(fz);
+    const FusedPlan plan = sw ? fused_plan(fz) : FusedPlan{};
+    if (plan.n <= 1)
+        return run_mlp(ctx, net, src, cap, map, Map{}, cal, epi, s, PIFU_PREC_FP32, m_dev);
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t cg = nullptr;
+    CK(cudaStreamGetCaptureInfo(s, &cs, nullptr, &cg, nullptr, nullptr, nullptr));
+    cudaGraphConditionalHandle h;
+    CK(cudaGraphConditionalHandleCreate(&h, cg, 0, 0));
+    CK(launch_fused_switch(h, plan, m_dev, (unsigned)cap, s));
+    cudaGraph_t bodies[4] = {};
+    int st = g_add_switch(ctx, s, h, plan.n, bodies);
+    if (st != PIFU_OK) return st;
+    cudaStream_t s4 = ctx->cap_stream4;
+    const int64_t before = launches_now(ctx);
+    for (int i = 0; i < plan.n; ++i) {
+        CK(cudaStreamBeginCaptureToGraph(s4, bodies[i], nullptr, nullptr, 0,
+                                         cudaStreamCaptureModeThreadLocal));
+        st = run_mlp(ctx, net, src, cap, map, Map{}, cal, epi, s4, PIFU_PREC_FP32, m_dev,
+                     plan.cl[i]);
+        cudaGraph_t out = nullptr;
+        const cudaError_t ee = cudaStreamEndCapture(s4, &out);
+        if (st != PIFU_OK) return st;
+        if (ee != cudaSuccess) return fail_cuda(ctx, ee);
+    }
+    // one body runs per replay: count its launches once
+    const int64_t per_body = (launches_now(ctx) - before) / plan.n;
+    ctx->prof.k[PIFU_K_MLP_F32].launches -= (launches_now(ctx) - before) - per_body;
+    return PIFU_OK;
+}
+
 // One evaluation batch in the graph: BF16 on the tensor cores, and for MIXED
 // the FP32 re-evaluation of the queued near-0.5 occupancies (device-sized).
 // With `sur`, f_S runs first and f_O takes the occupancies f_S put within
@@ -1777,7 +1829,7 @@ int g_eval(pifu_ctx* ctx, const DevNet& net, const PointSrc& src, int64_t cap,
             CK(cudaStreamBeginCaptureToGraph(s3, body, nullptr, nullptr, 0,
                                              cudaStreamCaptureModeThreadLocal));
             if (br == 0)
-                st = run_mlp(ctx, net, src, cap, map, Map{}, cal, epi, s3, PIFU_PREC_FP32, m_dev);
+                st = g_recheck(ctx, net, src, cap, map, cal, epi, s3, m_dev);
             else
                 st = g_eval(ctx, net, src, cap, m_dev, map, cal, epi, prec, margin, rechecked, s3);
             cudaGraph_t out = nullptr;
@@ -1805,7 +1857,7 @@ int g_eval(pifu_ctx* ctx, const DevNet& net, const PointSrc& src, int64_t cap,
     // the fused kernel takes any queue length (at most the batch's); the
     // split-K path has a fixed capacity
     const int64_t rcap = (net.kind == kNetCbn || fused_ok(fused_of(net))) ? cap : kRecheckCap;
-    st = run_mlp(ctx, net, s2, rcap, map, Map{}, cal, e2, s, PIFU_PREC_FP32, ctx->d_recheck);
+    st = g_recheck(ctx, net, s2, rcap, map, cal, e2, s, ctx->d_recheck);
     if (st != PIFU_OK) return st;
     CK(launch_accumulate(rechecked, ctx->d_recheck, (unsigned)rcap, ctx->d_count + 1, s));
     return PIFU_OK;
@@ -1840,6 +1892,29 @@ int g_add_cond(pifu_ctx* ctx, cudaStream_t s, cudaGraphConditionalHandle h,
     cudaGraphNode_t node;
     CK(cudaGraphAddNode(&node, cg, deps, edata, ndeps, &np));
     *body = np.conditional.phGraph_out[0];
+    CK(cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+    return PIFU_OK;
+}
+
+// Appends a SWITCH node with n bodies to the capture of `s`; the condition
+// is set by the kernel that was captured last (launch_fused_switch).
+int g_add_switch(pifu_ctx* ctx, cudaStream_t s, cudaGraphConditionalHandle h, int n,
+                 cudaGraph_t* bodies) {
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t cg = nullptr;
+    const cudaGraphNode_t* deps = nullptr;
+    const cudaGraphEdgeData* edata = nullptr;
+    size_t ndeps = 0;
+    CK(cudaStreamGetCaptureInfo(s, &cs, nullptr, &cg, &deps, &edata, &ndeps));
+    if (cs != cudaStreamCaptureStatusActive) return PIFU_ERR_STATE;
+    cudaGraphNodeParams np{};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = h;
+    np.conditional.type = cudaGraphCondTypeSwitch;
+    np.conditional.size = (unsigned)n;
+    cudaGraphNode_t node;
+    CK(cudaGraphAddNode(&node, cg, deps, edata, ndeps, &np));
+    for (int i = 0; i < n; ++i) bodies[i] = np.conditional.phGraph_out[i];
     CK(cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
     return PIFU_OK;
 }
@@ -2043,6 +2118,7 @@ int g_build(pifu_ctx* ctx, const FrameKey& k, const Map& occ, const Map& col, co
     if (!ctx->cap_stream) CK(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
     if (!ctx->cap_stream2) CK(cudaStreamCreateWithFlags(&ctx->cap_stream2, cudaStreamNonBlocking));
     if (!ctx->cap_stream3) CK(cudaStreamCreateWithFlags(&ctx->cap_stream3, cudaStreamNonBlocking));
+    if (!ctx->cap_stream4) CK(cudaStreamCreateWithFlags(&ctx->cap_stream4, cudaStreamNonBlocking));
     if (!ctx->d_gstats) CK(dev_alloc(&ctx->d_gstats, 1));
     {
         const int st = ensure_clist(ctx, kChunkTC);
@@ -2324,6 +2400,7 @@ int b_build(pifu_ctx* ctx, const BatchKey& k) {
     if (!ctx->cap_stream) CK(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
     if (!ctx->cap_stream2) CK(cudaStreamCreateWithFlags(&ctx->cap_stream2, cudaStreamNonBlocking));
     if (!ctx->cap_stream3) CK(cudaStreamCreateWithFlags(&ctx->cap_stream3, cudaStreamNonBlocking));
+    if (!ctx->cap_stream4) CK(cudaStreamCreateWithFlags(&ctx->cap_stream4, cudaStreamNonBlocking));
     {
         const int st = ensure_clist(ctx, bw.cap);
         if (st != PIFU_OK) return st;
@@ -2386,27 +2463,36 @@ int b_build(pifu_ctx* ctx, const BatchKey& k) {
 // chosen tile changes the weight tensor map's box, so captured graphs are
 // invalidated.
 
-int tune_layer(pifu_ctx* ctx, const TcLayerArgs& base, int n_out, bool fp8, CUtensorMap* tmW,
-               void* Wdev, int Kw, int* BN, cudaStream_t s, double* best_ms) {
-    const int cands[3] = {64, 128, 256};
-    int best = *BN;
+// Tile codes: 64, 128, 256 = BN of the single-CTA 128 x BN tile; kPairCode =
+// the CTA-pair form (two CTAs on a 256 x 256 tile, BF16 layers only).
+constexpr int kPairCode = 512;
+
+bool encode_w(bool fp8, CUtensorMap* tmW, void* Wdev, int Kw, int n_out, int code) {
+    const uint32_t box = (uint32_t)(code == kPairCode ? 128 : code);
+    return fp8 ? tc_encode_2d_u8(tmW, Wdev, (uint64_t)Kw, (uint64_t)n_out, (uint64_t)Kw, 128, box)
+               : tc_encode_2d_bf16(tmW, Wdev, (uint64_t)Kw, (uint64_t)n_out, (uint64_t)Kw * 2, 64,
+                                   box);
+}
+
+int tune_layer(pifu_ctx* ctx, const TcLayerArgs& base, int n_out, bool fp8, bool allow_pair,
+               CUtensorMap* tmW, void* Wdev, int Kw, int* code, cudaStream_t s, double* best_ms) {
+    const int cands[4] = {64, 128, 256, kPairCode};
+    int best = *code;
     double best_t = 1e30;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
     int st = PIFU_OK;
     for (int c : cands) {
-        if (n_out % c != 0 || st != PIFU_OK) continue;
-        const bool ok = fp8 ? tc_encode_2d_u8(tmW, Wdev, (uint64_t)Kw, (uint64_t)n_out, (uint64_t)Kw,
-                                              128, (uint32_t)c)
-                            : tc_encode_2d_bf16(tmW, Wdev, (uint64_t)Kw, (uint64_t)n_out,
-                                                (uint64_t)Kw * 2, 64, (uint32_t)c);
-        if (!ok) {
+        const bool pair = c == kPairCode;
+        if (st != PIFU_OK || (pair ? !allow_pair || n_out % 256 != 0 : n_out % c != 0)) continue;
+        if (!encode_w(fp8, tmW, Wdev, Kw, n_out, c)) {
             st = PIFU_ERR_CUDA;
             break;
         }
         TcLayerArgs a = base;
-        a.BN = c;
+        a.BN = pair ? 256 : c;
+        a.pair = pair ? 1 : 0;
         a.tmW = tmW;
         float ms = 0.f;
         cudaError_t e = launch_tc_linear(a, s);   // warm-up
@@ -2428,12 +2514,8 @@ int tune_layer(pifu_ctx* ctx, const TcLayerArgs& base, int n_out, bool fp8, CUte
     cudaEventDestroy(e1);
     if (st != PIFU_OK) return st;
     *best_ms = best_t / 3.0;
-    *BN = best;
-    const bool ok = fp8 ? tc_encode_2d_u8(tmW, Wdev, (uint64_t)Kw, (uint64_t)n_out, (uint64_t)Kw, 128,
-                                          (uint32_t)best)
-                        : tc_encode_2d_bf16(tmW, Wdev, (uint64_t)Kw, (uint64_t)n_out,
-                                            (uint64_t)Kw * 2, 64, (uint32_t)best);
-    return ok ? PIFU_OK : PIFU_ERR_CUDA;
+    *code = best;
+    return encode_w(fp8, tmW, Wdev, Kw, n_out, best) ? PIFU_OK : PIFU_ERR_CUDA;
 }
 
 int autotune(pifu_ctx* ctx, int64_t rows, cudaStream_t s, int32_t* bn_out, double* ms_out,
@@ -2477,7 +2559,7 @@ int autotune(pifu_ctx* ctx, int64_t rows, cudaStream_t s, int32_t* bn_out, doubl
                 a.colscale = Q.colscale;
                 a.out_scale = Q.out_scale;
                 double ms = 0.0;
-                st = tune_layer(ctx, a, Ly.n_out, true, &Q.tmW, Q.W, Q.Kw, &Q.BN, s, &ms);
+                st = tune_layer(ctx, a, Ly.n_out, true, false, &Q.tmW, Q.W, Q.Kw, &Q.BN, s, &ms);
                 if (st != PIFU_OK) return st;
                 record(Q.BN, ms);
             }
@@ -2494,15 +2576,76 @@ int autotune(pifu_ctx* ctx, int64_t rows, cudaStream_t s, int32_t* bn_out, doubl
             a.colscale = nullptr;
             a.out_scale = 1.f;
             double ms = 0.0;
-            st = tune_layer(ctx, a, Ly.n_out, false, &T.tmW, T.W, T.Kw, &T.BN, s, &ms);
+            int code = T.pair ? kPairCode : T.BN;
+            st = tune_layer(ctx, a, Ly.n_out, false, true, &T.tmW, T.W, T.Kw, &code, s, &ms);
             if (st != PIFU_OK) return st;
-            record(T.BN, ms);
+            T.pair = code == kPairCode;
+            T.BN = T.pair ? 256 : code;
+            record(code, ms);
         }
     }
     ctx->g_valid = false;
     ctx->batch.g_valid = false;
     if (n_done) *n_done = n;
     return PIFU_OK;
+}
+
+// The tuned layers in pifu_autotune's order; visit(q, t, n_out, fused_last)
+// gets the E4M3 form (q != nullptr) or the BF16 form (t != nullptr).
+template <typename F>
+void for_each_tuned_layer(pifu_ctx* ctx, F&& visit) {
+    for (int which = 0; which < 2; ++which) {
+        DevNet& net = ctx->net[which];
+        if (!net.tc_ok) continue;
+        const int L = (int)net.layers.size();
+        for (int l = 0; l + 1 < L; ++l) {
+            const int n_out = net.layers[(size_t)l].n_out;
+            const bool fused_last = l == L - 2 && net.layers[(size_t)L - 1].K2 == 0 &&
+                                    net.layers[(size_t)L - 1].n_out <= 4;
+            if (net.f8_ok && l < (int)net.f8.size())
+                visit(&net.f8[(size_t)l], (TcLayer*)nullptr, n_out, false);
+            visit((Fp8Layer*)nullptr, &net.tc[(size_t)l], n_out, fused_last);
+        }
+    }
+}
+
+int set_tiles(pifu_ctx* ctx, const int32_t* codes, int n) {
+    // validate everything first, so that a refused call changes nothing
+    int i = 0;
+    bool valid = true;
+    for_each_tuned_layer(ctx, [&](Fp8Layer* q, TcLayer* t, int n_out, bool fused_last) {
+        if (i >= n) {
+            valid = false;
+            ++i;
+            return;
+        }
+        const int c = codes[i++];
+        if (q)
+            valid = valid && (c == 64 || c == 128 || c == 256) && n_out % c == 0;
+        else if (fused_last)
+            valid = valid && c == (t->pair ? kPairCode : t->BN);
+        else if (c == kPairCode)
+            valid = valid && n_out % 256 == 0;
+        else
+            valid = valid && (c == 64 || c == 128 || c == 256) && n_out % c == 0;
+    });
+    if (!valid || i != n) return PIFU_ERR_ARG;
+    i = 0;
+    bool ok = true;
+    for_each_tuned_layer(ctx, [&](Fp8Layer* q, TcLayer* t, int n_out, bool) {
+        const int c = codes[i++];
+        if (q) {
+            q->BN = c;
+            ok = ok && encode_w(true, &q->tmW, q->W, q->Kw, n_out, c);
+        } else {
+            t->pair = c == kPairCode;
+            t->BN = t->pair ? 256 : c;
+            ok = ok && encode_w(false, &t->tmW, t->W, t->Kw, n_out, c);
+        }
+    });
+    ctx->g_valid = false;
+    ctx->batch.g_valid = false;
+    return ok ? PIFU_OK : PIFU_ERR_CUDA;
 }
 
 }  // namespace
@@ -2634,6 +2777,7 @@ void pifu_destroy(pifu_ctx* ctx) {
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     if (ctx->cap_stream2) cudaStreamDestroy(ctx->cap_stream2);
     if (ctx->cap_stream3) cudaStreamDestroy(ctx->cap_stream3);
+    if (ctx->cap_stream4) cudaStreamDestroy(ctx->cap_stream4);
     dev_free(ctx->clist);
     dev_free(ctx->d_ccount);
     dev_free(ctx->d_gstats);
@@ -3279,6 +3423,13 @@ int pifu_autotune(pifu_ctx* ctx, int64_t rows, void* stream, int32_t* bn_out, do
     DeviceGuard g(ctx->device);
     if (!g.ok) return PIFU_ERR_CUDA;
     return autotune(ctx, rows, static_cast<cudaStream_t>(stream), bn_out, ms_out, n_max, n_layers);
+}
+
+int pifu_set_tiles(pifu_ctx* ctx, const int32_t* codes, int n) {
+    if (!ctx || n < 0 || (n > 0 && !codes)) return PIFU_ERR_ARG;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return PIFU_ERR_CUDA;
+    return set_tiles(ctx, codes, n);
 }
 
 int pifu_surrogate_init(pifu_ctx* ctx, int h1, int h2, uint64_t seed) {

@@ -185,6 +185,8 @@ struct TcLayerArgs {
     const CUtensorMap* tmO;       // optional: BF16 output [rows][N], box 32 x 32, 64-byte
                                   // swizzle (the epilogue then stores with TMA)
     int nk1, nk2, M, N, BN;       // nk1, nk2: 128-byte K-blocks of the two A segments
+    int pair;                     // 1: CTA-pair form (BN = 256, TC_BF16, no fuse); tmW's
+                                  // box is then 128 rows (each CTA loads half of a tile's W)
     const float* bias;
     float slope;
     void* out;                    // [M][ldo] of the mode's output type
@@ -325,10 +327,28 @@ struct FusedNet {
 };
 // Whether the network's shape fits the fused kernel.
 bool fused_ok(const FusedNet& n);
-// Points p0 .. p0 + m - 1 of `src` (src.count: a device-resident m).
+// The cluster sizes the fused kernel can use for a network, with the number
+// of clusters of each size that fit on the device at once and the latency of
+// one tile relative to 8-CTA clusters.
+struct FusedPlan {
+    int n = 0;
+    int cl[4] = {};
+    int ncl[4] = {};
+    float lat[4] = {};
+};
+FusedPlan fused_plan(const FusedNet& n);
+// Points p0 .. p0 + m - 1 of `src` (src.count: a device-resident m, at most
+// m).  cl = 0: the cluster size of fewest latency-weighted rounds for a
+// host-known m, 8-CTA clusters for a device-resident one; else that size
+// (one of the plan's).
 cudaError_t launch_mlp_fused(const FusedNet& net, const PointSrc& src, int64_t p0, int64_t m,
                              const Calib& calib, const Map& map0, const Map& map1,
-                             const Epilogue& epi, cudaStream_t stream);
+                             const Epilogue& epi, cudaStream_t stream, int cl = 0);
+// Graph form: sets the switch `h` to the index (in `plan`) of the cluster
+// size the device-resident batch size min(*count, cap) calls for, or to
+// plan.n (no branch) when it is 0.
+cudaError_t launch_fused_switch(cudaGraphConditionalHandle h, const FusedPlan& plan,
+                                const unsigned int* count, unsigned int cap, cudaStream_t stream);
 
 // --- cbn.cu --------------------------------------------------------------
 // The CBN + SoftZ occupancy network (Appendix, Eq. 7 and Eq. 8) in FP32, with

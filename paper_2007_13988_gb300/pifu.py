@@ -45,7 +45,7 @@ EXPORTS = ("pifu_create", "pifu_destroy", "pifu_query", "pifu_query_colour", "pi
            "pifu_surrogate_train", "pifu_surrogate_params", "pifu_surrogate_query",
            "pifu_calibrate_fp8", "pifu_frames", "pifu_autotune", "pifu_surrogate_ohem_init",
            "pifu_surrogate_ohem_weights", "pifu_surrogate_ohem_sample",
-           "pifu_surrogate_train_ohem")
+           "pifu_surrogate_train_ohem", "pifu_set_tiles")
 
 KERNEL_CLASSES = ("gather", "mlp_hidden", "mlp_last", "level", "select", "render", "mlp_f32",
                   "cbn_tc")
@@ -143,6 +143,8 @@ def _lib():
     lib.pifu_autotune.argtypes = [P, I64, P, ctypes.POINTER(ctypes.c_int32),
                                   ctypes.POINTER(ctypes.c_double), I, ctypes.POINTER(I)]
     lib.pifu_autotune.restype = I
+    lib.pifu_set_tiles.argtypes = [P, ctypes.POINTER(ctypes.c_int32), I]
+    lib.pifu_set_tiles.restype = I
     lib.pifu_calibrate_fp8.argtypes = [P, ctypes.POINTER(pifu_fmap), ctypes.POINTER(F), I, P]
     lib.pifu_calibrate_fp8.restype = I
     lib.pifu_surrogate_init.argtypes = [P, I, I, U64]
@@ -376,14 +378,25 @@ def pifu_frames(ctx, occ_maps, col_maps, calibs, n0, num_levels, width, height, 
     return list(vols)
 
 
+# Tile code of the CTA-pair form (two CTAs on a 256 x 256 tile).
+PIFU_TILE_PAIR = 512
+
+
 def pifu_autotune(ctx, rows, stream=None, n_max=32):
-    """Tile widths chosen per tensor-core layer: list of (BN, ms per launch)."""
+    """Tile codes chosen per tensor-core layer: list of (code, ms per launch);
+    code = BN of a single-CTA 128 x BN tile, or PIFU_TILE_PAIR."""
     bn = (ctypes.c_int32 * n_max)()
     ms = (ctypes.c_double * n_max)()
     n = ctypes.c_int(0)
     _check(_lib().pifu_autotune(ctx, int(rows), _stream(stream), bn, ms, n_max, ctypes.byref(n)),
            "pifu_autotune", ctx)
     return [(int(bn[i]), float(ms[i])) for i in range(min(n.value, n_max))]
+
+
+def pifu_set_tiles(ctx, codes):
+    """Set every tuned layer's tile code (pifu_autotune's order and codes)."""
+    arr = (ctypes.c_int32 * max(len(codes), 1))(*[int(c) for c in codes])
+    _check(_lib().pifu_set_tiles(ctx, arr, len(codes)), "pifu_set_tiles", ctx)
 
 
 def pifu_surrogate_ohem_init(ctx, m):

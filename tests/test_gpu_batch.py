@@ -157,7 +157,7 @@ def test_autotune_keeps_results(ctx):
     rgb_b = rgb.cpu().numpy()
     chosen = pifu.pifu_autotune(ctx.ctx, 65536)
     print("autotune (BN, ms):", chosen)
-    assert chosen and all(bn in (64, 128, 256) for bn, _ in chosen)
+    assert chosen and all(bn in (64, 128, 256, pifu.PIFU_TILE_PAIR) for bn, _ in chosen)
     after = pifu.pifu_frame(ctx.ctx, ctx.occ, ctx.col, w.calib, w.n0, w.num_levels, R, R, d[0],
                             rgb[0], m[0])
     torch().cuda.synchronize()

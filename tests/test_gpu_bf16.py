@@ -89,6 +89,76 @@ def test_tc_layers_match_bf16_emulation(m):
         c.close()
 
 
+def pair_workload(m, seed=11):
+    """A hand-sized f_O whose first three hidden layers are multiples of 256
+    wide (so the CTA-pair form applies to them) on BF16-exact inputs."""
+    C = 60
+    occ_net = make_net(C, (512, 256, 256, 128, 1), (1, 2, 3), seed=seed)
+    w = synth.tiny(0)
+    rng = np.random.default_rng(seed + 1)
+    H = W = 32
+    fmap = bf16_round(rng.standard_normal((H, W, C))).astype(np.float32)
+    w.occ_map = np.ascontiguousarray(fmap)
+    w.occ_net = occ_net
+    w.col_net = synth.colour_net(C + 1, (64, 3), (), 5)
+    i = rng.integers(0, W, m)
+    j = rng.integers(0, H, m)
+    z = rng.integers(-64, 65, m) / 64.0
+    P = np.stack([(2 * i + 1) / W - 1, (2 * j + 1) / H - 1, z], 1).astype(np.float32)
+    X = np.concatenate([fmap[j, i].astype(np.float64), z[:, None]], 1)
+    return w, P, X
+
+
+# tuned layers of pair_workload's nets, in the autotuner's order: f_O's four
+# hidden layers (the last one carries the fused last layer), then f_T's one
+SINGLE = [256, 256, 256, 128, 64]
+
+
+# m: one row; the odd CTA's half holds one row; whole 256-row pair tiles plus
+# a tail only the even CTA covers; a tail both cover; several waves
+@pytest.mark.parametrize("m", [1, 129, 256 * 40 + 100, 256 * 40 + 200, 70001])
+def test_pair_form_matches_single_cta_form(m):
+    """The CTA-pair form (two CTAs on a 256 x 256 tile, cta_group::2 MMAs)
+    adds the same products in the same K order as the single-CTA form, so
+    the outputs are equal bit for bit; both stay within the emulation bound."""
+    from paper_2007_13988_gb300 import pifu
+    w, P, X = pair_workload(m)
+    want = emulate(w.occ_net, X)
+    c = Ctx(w)
+    try:
+        pair = [pifu.PIFU_TILE_PAIR] * 3 + SINGLE[3:]
+        got = {}
+        for name, codes in (("single", SINGLE), ("pair", pair), ("mixed", [512, 256, 512, 128, 64])):
+            pifu.pifu_set_tiles(c.ctx, codes)
+            got[name] = c.query(P, precision=BF16)
+            assert np.max(np.abs(got[name] - want)) <= 2e-3, name
+        np.testing.assert_array_equal(got["pair"], got["single"])
+        np.testing.assert_array_equal(got["mixed"], got["single"])
+    finally:
+        c.close()
+
+
+def test_set_tiles_refusals():
+    from paper_2007_13988_gb300 import pifu
+    w, P, _ = pair_workload(300)
+    c = Ctx(w)
+    try:
+        before = c.query(P, precision=BF16)
+        bad = [SINGLE[:-1],                       # one layer short
+               SINGLE + [64],                     # one too many
+               [96] + SINGLE[1:],                 # not a tile code
+               [256, 256, 256, 512, 64],          # the pair form on the 128-wide layer
+               [256, 256, 256, 64, 64],           # the fused layer must keep its code
+               [256, 256, 256, 128, 512]]         # the pair form on a 64-wide layer
+        for codes in bad:
+            with pytest.raises(pifu.PifuError) as e:
+                pifu.pifu_set_tiles(c.ctx, codes)
+            assert e.value.status == pifu.PIFU_ERR_ARG
+        np.testing.assert_array_equal(c.query(P, precision=BF16), before)
+    finally:
+        c.close()
+
+
 @pytest.fixture(scope="module")
 def full():
     c = Ctx(synth.full(0))

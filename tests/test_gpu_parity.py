@@ -49,6 +49,18 @@ def test_query_full_random_points(full):
     assert err <= OCC_TOL, err
 
 
+# FP32 batches of up to 2048 points run in one fused launch whose cluster
+# size follows the batch (16-CTA clusters for one tile up to 2-CTA clusters
+# for about 76 tiles and more): one batch per regime, ragged tails included.
+@pytest.mark.parametrize("m", [16, 130, 300, 700, 1216, 2048])
+def test_query_full_fused_cluster_sizes(full, m):
+    P = synth.query_points(m, seed=300 + m)
+    got = full.query(P)
+    want = occ_oracle(full.w, P)
+    err = np.max(np.abs(got - want))
+    assert err <= OCC_TOL, err
+
+
 def test_query_full_near_surface_points(full):
     # points on the finest grid next to the figure, where o changes fastest
     w = full.w
