@@ -61,6 +61,8 @@ def parse_args():
     ap.add_argument("--no-octree", action="store_true",
                     help="skip the Fig. 3 comparison with the two octree baselines")
     ap.add_argument("--form", choices=("graph", "host"), default="graph")
+    ap.add_argument("--schedule", choices=("chained", "per_layer"), default="per_layer",
+                    help="tensor-core hidden layers: one launch per batch, or one per layer")
     ap.add_argument("--query-points", type=int, default=1 << 20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
@@ -271,12 +273,15 @@ DTYPE = {"fp32": "f32", "bf16": "bf16", "mixed": "bf16+f32", "fp8_mixed": "e4m3+
 class Frame:
     """One workload on one device: context, resident inputs and outputs."""
 
-    def __init__(self, dev, stream):
+    def __init__(self, dev, stream, schedule="per_layer"):
         import torch
         from paper_2007_13988_gb300 import pifu, synth
         self.pifu = pifu
         self.w = w = synth.full(0)
         self.ctx = pifu.pifu_create(pifu.blob_from_nets(w.occ_net, w.col_net))
+        self.schedule = (pifu.PIFU_SCHED_CHAINED if schedule == "chained"
+                         else pifu.PIFU_SCHED_PER_LAYER)
+        pifu.pifu_set_schedule(self.ctx, self.schedule)
         self.stream = stream
         self.dev = dev
         R = w.render
@@ -430,6 +435,7 @@ def cbn_form(fr, args, world):
     p = fr.pifu
     wc = synth.full_cbn(0)
     ctx = p.pifu_create(p.blob_from_nets(wc.occ_net, wc.col_net))
+    p.pifu_set_schedule(ctx, fr.schedule)
     saved = fr.ctx, fr.w
     fr.ctx, fr.w = ctx, wc
     try:
@@ -648,7 +654,7 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     stream = torch.cuda.Stream(device=dev)
-    fr = Frame(dev, stream)
+    fr = Frame(dev, stream, args.schedule)
     pifu = fr.pifu
     w = fr.w
     R = w.render
@@ -825,6 +831,7 @@ def run_ours(args, rank, world, local_rank):
                         "max": max(head["step_ms"])}}
     line["config"]["form"] = ("one CUDA graph per frame (pifu_frame)" if form == "graph"
                               else "host-driven (pifu_localize + pifu_render)")
+    line["config"]["layer_schedule"] = args.schedule
     if form == "graph":
         line["host_driven"] = {"value": prof_run["value"], "ms_per_step": prof_run["ms_per_step"]}
     if prec in (2, 3):

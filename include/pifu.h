@@ -313,6 +313,20 @@ int pifu_frames(pifu_ctx* ctx, int B, const pifu_fmap* occ_maps, const pifu_fmap
 int pifu_autotune(pifu_ctx* ctx, int64_t rows, void* stream, int32_t* bn_out, double* ms_out,
                   int n_max, int* n_layers);
 
+/* ---- Layer schedule (not in the paper) ----------------------------------------
+ * PIFU_SCHED_PER_LAYER (the default): one launch per tensor-core hidden
+ * layer.  PIFU_SCHED_CHAINED: a BF16 batch runs all hidden layers of the
+ * network, with the last layer fused, in ONE persistent cooperative launch.
+ * Rows move through the layers in groups of 128-row blocks, so a layer reads
+ * activations the layer before wrote shortly earlier, and the tiles of one
+ * layer fill the last wave of another.  It applies when the last layer can be
+ * fused, the network has at most 4 hidden layers whose widths sum to at most
+ * 2048, and no layer uses the CTA-pair form; otherwise the per-layer
+ * launches run.  The results are the same bits either way.  Invalidates
+ * captured graphs; no device work.  Errors: PIFU_ERR_ARG. */
+enum pifu_schedule { PIFU_SCHED_PER_LAYER = 0, PIFU_SCHED_CHAINED = 1 };
+int pifu_set_schedule(pifu_ctx* ctx, int schedule);
+
 /* Sets the tile code of every tuned layer, in pifu_autotune's order: codes[i]
  * for layer i, n = the number of layers pifu_autotune reports (for instance a
  * saved autotuner result).  A code must be allowed for its layer as above

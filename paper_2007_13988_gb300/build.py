@@ -21,7 +21,7 @@ LIB = os.path.join(PKG, "libpifu.so")
 
 SOURCES = ["pifu_api.cu", "gather.cu", "mlp_f32.cu", "mlp_tc.cu", "localize.cu", "render.cu",
            "query_noalloc.cu", "train.cu", "mlp_fused.cu", "cbn.cu",
-           "cbn_tc.cu"]
+           "cbn_tc.cu", "mlp_chain.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
                 "-I" + INCLUDE, "-I" + CSRC]

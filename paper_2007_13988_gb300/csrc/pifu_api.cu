@@ -69,6 +69,10 @@ struct DevNet {
     std::vector<DevLayer> layers;
     bool tc_ok = false;             // shapes allow the tensor-core form
     std::vector<TcLayer> tc;        // hidden layers only
+    // chained form (all hidden layers in one launch): shapes and buffers
+    // allow it; chain_tmA1[l] reads layer l-1's output in its chain buffer
+    bool chain_ok = false;
+    std::vector<CUtensorMap> chain_tmA1;
     CUtensorMap tmX{};              // BF16 gather rows as the A operand
     // FP8 form (pifu_calibrate_fp8): the first f8.size() hidden layers
     bool f8_ok = false;
@@ -289,6 +293,8 @@ struct pifu_ctx {
     int64_t X_cap = 0, H_cap = 0;   // elements
     __nv_bfloat16* Xb = nullptr;
     __nv_bfloat16* Hb[2] = {nullptr, nullptr};
+    unsigned int* chain_dep = nullptr;   // [kChainMaxLayers][tc_rows / 128] tile-part counters + 1
+    bool chain_on = false;               // pifu_set_schedule
     int64_t tc_rows = 0;            // rows of Xb, Hb[], X8 (grown on demand up to kChunkTC)
     uint8_t* X8 = nullptr;          // [tc_rows][ldx8] E4M3 gather rows (FP8 forms):
     int ldx8 = 0;                   //   x_hi at [0, kx8), x_lo at [kx8, 2 kx8)
@@ -748,6 +754,14 @@ int ensure_mlp_ws(pifu_ctx* ctx) {
 // widths are not multiples of 64 keep tc_ok = false.
 // TMA maps of a network's activation operands (gather rows, previous layer
 // outputs) over the current tensor-core workspaces of tc_rows rows.
+// Output buffer of hidden layer l in the chained form: [tc_rows][n_out_l].
+__nv_bfloat16* chain_out(pifu_ctx* ctx, const DevNet& net, int l) {
+    if (l == 0) return ctx->Hb[0];
+    int64_t off = 0;
+    for (int k = 1; k < l; ++k) off += net.layers[k].n_out;
+    return ctx->Hb[1] + off * ctx->tc_rows;
+}
+
 int encode_act_maps(pifu_ctx* ctx, DevNet& net) {
     if (!net.tc_ok || ctx->tc_rows == 0 || net.kind == kNetCbn) return PIFU_OK;
     const uint64_t rows = (uint64_t)ctx->tc_rows;
@@ -766,6 +780,26 @@ int encode_act_maps(pifu_ctx* ctx, DevNet& net) {
                                                  (uint64_t)Ly.n_out, rows,
                                                  (uint64_t)Ly.n_out * 2);
         if (!net.tc[l].tmO_ok) return PIFU_ERR_CUDA;
+    }
+    // chained form: layer 0 writes Hb[0], layers 1 .. nl-2 write consecutive
+    // column blocks of Hb[1] (the last hidden layer carries the fused last
+    // layer and writes nothing)
+    {
+        const int nl = (int)net.tc.size();
+        int64_t hcap = 8;
+        for (const DevNet& n : ctx->net) hcap = std::max<int64_t>(hcap, std::max(n.max_hidden, 8));
+        int sum_n = 0, sum_mid = 0;
+        for (int l = 0; l < nl; ++l) sum_n += net.layers[l].n_out;
+        for (int l = 1; l + 1 < nl; ++l) sum_mid += net.layers[l].n_out;
+        net.chain_ok = nl >= 1 && nl <= kChainMaxLayers && sum_n <= kChainBiasFloats &&
+                       net.layers[0].n_out <= hcap && sum_mid <= hcap;
+        net.chain_tmA1.assign((size_t)std::max(nl, 1), CUtensorMap{});
+        for (int l = 1; net.chain_ok && l < nl; ++l) {
+            const int K1 = net.layers[l].K1;
+            if (!tc_encode_2d_bf16(&net.chain_tmA1[l], chain_out(ctx, net, l - 1), (uint64_t)K1,
+                                   rows, (uint64_t)K1 * 2, 64, 128))
+                return PIFU_ERR_CUDA;
+        }
     }
     if (net.f8_ok) {
         if (!tc_encode_2d_u8(&net.tmX8, ctx->X8, (uint64_t)ctx->ldx8, rows, (uint64_t)ctx->ldx8,
@@ -803,7 +837,9 @@ int ensure_tc_rows(pifu_ctx* ctx, int64_t rows) {
     dev_free(ctx->Hb[0]);
     dev_free(ctx->Hb[1]);
     dev_free(ctx->X8);
+    dev_free(ctx->chain_dep);
     ctx->tc_rows = 0;
+    CK(dev_alloc(&ctx->chain_dep, (int64_t)kChainMaxLayers * (cap / 128) + 1));
     CK(dev_alloc(&ctx->Xb, need_x * cap));
     CK(dev_alloc(&ctx->Hb[0], need_h * cap));
     CK(dev_alloc(&ctx->Hb[1], need_h * cap));
@@ -1067,6 +1103,15 @@ bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
 // (graph form); m is then only the capacity the launches are sized for.
 int run_cbn_tc(pifu_ctx* ctx, const PointSrc& src, int64_t m, const Map& map, const Calib& calib,
                const Epilogue& epi, cudaStream_t s, const unsigned int* m_dev);
+// The chained form applies to this network now: its shapes and buffers
+// allow it, it is switched on, and no layer uses the CTA-pair form.
+bool chain_usable(const pifu_ctx* ctx, const DevNet& net) {
+    if (!ctx->chain_on || !net.chain_ok || net.kind == kNetCbn) return false;
+    for (const TcLayer& T : net.tc)
+        if (T.pair || T.BN > 256) return false;
+    return true;
+}
+
 int run_mlp_tc(pifu_ctx* ctx, const DevNet& net, const PointSrc& src_in, int64_t m,
                const Map& map0, const Map& map1, const Calib& calib, const Epilogue& epi,
                cudaStream_t s, const unsigned int* m_dev = nullptr, bool f8 = false) {
@@ -1113,6 +1158,49 @@ int run_mlp_tc(pifu_ctx* ctx, const DevNet& net, const PointSrc& src_in, int64_t
             fl.n_out = Ll.n_out;
             fl.p0 = p0;
             fl.epi = epi;
+        }
+        if (F == 0 && fuse && chain_usable(ctx, net)) {
+            // all hidden layers (and the fused last layer) in one launch
+            ChainArgs ca{};
+            double flops = 2.0 * mc * Ll.fan_in * Ll.n_out, bytes = 0.0;
+            int sum_tiles = 0, boff = 0;
+            ca.nl = L - 1;
+            for (int l = 0; l + 1 < L; ++l) {
+                const DevLayer& Ly = net.layers[l];
+                const TcLayer& T = net.tc[l];
+                ChainLayer& C = ca.L[l];
+                C.tmA1 = l > 0 ? net.chain_tmA1[l] : net.tmX;
+                C.tmA2 = net.tmX;
+                C.tmW = T.tmW;
+                C.nk1 = T.nk1;
+                C.nk2 = T.nk2;
+                C.N = Ly.n_out;
+                C.BN = T.BN;
+                C.bias = Ly.b;
+                C.out = l + 2 < L ? chain_out(ctx, net, l) : nullptr;
+                C.ldo = Ly.n_out;
+                ca.boff[l] = boff;
+                boff += Ly.n_out;
+                sum_tiles += Ly.n_out / T.BN;
+                flops += 2.0 * mc * Ly.fan_in * Ly.n_out;
+                bytes += 2.0 * ((double)mc * (Ly.fan_in + Ly.n_out) + (double)Ly.n_out * Ly.fan_in);
+            }
+            CK(chain_prepare());
+            ca.M = (int)mc;
+            ca.m_dev = m_dev;
+            ca.err = ctx->d_count + 1;
+            ca.dep = ctx->chain_dep;
+            ca.max_mb = (int)(ctx->tc_rows / 128);
+            ca.next_tile = ca.dep + (size_t)ca.nl * ca.max_mb;
+            ca.lag = 4;
+            // a row group: about one wave of tiles over all layers
+            ca.group = std::max(1, chain_grid() / std::max(1, sum_tiles));
+            ca.slope = net.slope;
+            ca.fl = fl;
+            ev = pr.begin(s);
+            CK(launch_tc_chain(ca, s));
+            pr.end(PIFU_K_MLP_HIDDEN, ev, s, flops, bytes);
+            continue;
         }
         for (int l = 0; l + 1 < L; ++l) {
             const DevLayer& Ly = net.layers[l];
@@ -2126,6 +2214,7 @@ int g_build(pifu_ctx* ctx, const FrameKey& k, const Map& occ, const Map& col, co
     }
     if (!ctx->h_gstats) CK(cudaHostAlloc(&ctx->h_gstats, sizeof(GraphStats), cudaHostAllocDefault));
     CK(tc_prepare());
+    CK(chain_prepare());
     if (ctx->net[0].kind == kNetCbn) {
         const CbnF32& f = ctx->cbn.f32;
         CK(cbn_f32_prepare(f));
@@ -2406,6 +2495,7 @@ int b_build(pifu_ctx* ctx, const BatchKey& k) {
         if (st != PIFU_OK) return st;
     }
     CK(tc_prepare());
+    CK(chain_prepare());
     if (ctx->net[0].kind == kNetCbn) {
         const CbnF32& f = ctx->cbn.f32;
         CK(cbn_f32_prepare(f));
@@ -2523,6 +2613,7 @@ int autotune(pifu_ctx* ctx, int64_t rows, cudaStream_t s, int32_t* bn_out, doubl
     int st = ensure_tc_rows(ctx, rows);
     if (st != PIFU_OK) return st;
     CK(tc_prepare());
+    CK(chain_prepare());
     int n = 0;
     auto record = [&](int bn, double ms) {
         if (n < n_max) {
@@ -2754,6 +2845,7 @@ void pifu_destroy(pifu_ctx* ctx) {
     dev_free(ctx->Hb[0]);
     dev_free(ctx->Hb[1]);
     dev_free(ctx->X8);
+    dev_free(ctx->chain_dep);
     dev_free(ctx->part);
     uint32_t** bitsets[] = {&ctx->cand, &ctx->tent, &ctx->bin[0], &ctx->bin[1],
                             &ctx->eval, &ctx->conf[0], &ctx->conf[1]};
@@ -3423,6 +3515,15 @@ int pifu_autotune(pifu_ctx* ctx, int64_t rows, void* stream, int32_t* bn_out, do
     DeviceGuard g(ctx->device);
     if (!g.ok) return PIFU_ERR_CUDA;
     return autotune(ctx, rows, static_cast<cudaStream_t>(stream), bn_out, ms_out, n_max, n_layers);
+}
+
+int pifu_set_schedule(pifu_ctx* ctx, int schedule) {
+    if (!ctx || (schedule != PIFU_SCHED_CHAINED && schedule != PIFU_SCHED_PER_LAYER))
+        return PIFU_ERR_ARG;
+    ctx->chain_on = schedule == PIFU_SCHED_CHAINED;
+    ctx->g_valid = false;
+    ctx->batch.g_valid = false;
+    return PIFU_OK;
 }
 
 int pifu_set_tiles(pifu_ctx* ctx, const int32_t* codes, int n) {

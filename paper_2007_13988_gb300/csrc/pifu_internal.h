@@ -203,6 +203,43 @@ cudaError_t launch_tc_linear(const TcLayerArgs& a, cudaStream_t stream);
 // stream capture: launches inside a capture then make no attribute calls).
 cudaError_t tc_prepare();
 
+// --- mlp_chain.cu ------------------------------------------------------------
+// All hidden layers of one BF16 batch in one persistent cooperative launch
+// (rows move through the layers in groups; per-row-block counters order a
+// layer after the one it reads).
+constexpr int kChainMaxLayers = 4;
+constexpr int kChainBiasFloats = 2048;   // sum of the hidden widths
+struct ChainLayer {
+    CUtensorMap tmA1;       // layer l-1's output [rows][K1] (l >= 1, nk1 > 0)
+    CUtensorMap tmA2;       // the input rows x [rows][ldx]
+    CUtensorMap tmW;        // [N][Kw] BF16, box BN x 64
+    int nk1, nk2, N, BN;    // 128-byte K-blocks of the two segments; BN | N, BN <= 256
+    const float* bias;      // [N]
+    __nv_bfloat16* out;     // [rows][ldo] (unused by a layer carrying the fused last layer)
+    int ldo;
+};
+struct ChainArgs {
+    ChainLayer L[kChainMaxLayers];
+    int boff[kChainMaxLayers];   // offsets of the layers' biases in shared memory
+    int nl;
+    int M;                       // rows (capacity when m_dev is given)
+    const unsigned int* m_dev;   // optional device-resident row count (<= M)
+    unsigned int* err;
+    unsigned int* dep;           // [nl][max_mb] tile-part counters, zeroed by the launch
+    unsigned int* next_tile;     // = dep + nl * max_mb: the tile counter, zeroed with them
+    int max_mb;                  // >= ceil(M / 128)
+    int group;                   // 128-row blocks per row group
+    int lag;                     // steps between a layer and the next on one row group
+    float slope;
+    FuseLast fl;                 // fl.n_out > 0: the last layer rides in layer nl-1
+};
+// Sets the kernel's attributes on the current device (call before a capture).
+cudaError_t chain_prepare();
+// CTAs of one chained launch (one per SM; 0 before chain_prepare).
+int chain_grid();
+// Zeroes a.dep and the tile counter and launches (cooperative, one CTA per SM).
+cudaError_t launch_tc_chain(const ChainArgs& a, cudaStream_t stream);
+
 // Encode a 2-D BF16 tensor map (128-byte swizzle, zero fill out of bounds).
 bool tc_encode_2d_bf16(void* map, const void* base, uint64_t cols, uint64_t rows,
                        uint64_t row_stride_bytes, uint32_t box_cols, uint32_t box_rows);

@@ -45,7 +45,7 @@ EXPORTS = ("pifu_create", "pifu_destroy", "pifu_query", "pifu_query_colour", "pi
            "pifu_surrogate_train", "pifu_surrogate_params", "pifu_surrogate_query",
            "pifu_calibrate_fp8", "pifu_frames", "pifu_autotune", "pifu_surrogate_ohem_init",
            "pifu_surrogate_ohem_weights", "pifu_surrogate_ohem_sample",
-           "pifu_surrogate_train_ohem", "pifu_set_tiles")
+           "pifu_surrogate_train_ohem", "pifu_set_tiles", "pifu_set_schedule")
 
 KERNEL_CLASSES = ("gather", "mlp_hidden", "mlp_last", "level", "select", "render", "mlp_f32",
                   "cbn_tc")
@@ -145,6 +145,8 @@ def _lib():
     lib.pifu_autotune.restype = I
     lib.pifu_set_tiles.argtypes = [P, ctypes.POINTER(ctypes.c_int32), I]
     lib.pifu_set_tiles.restype = I
+    lib.pifu_set_schedule.argtypes = [P, I]
+    lib.pifu_set_schedule.restype = I
     lib.pifu_calibrate_fp8.argtypes = [P, ctypes.POINTER(pifu_fmap), ctypes.POINTER(F), I, P]
     lib.pifu_calibrate_fp8.restype = I
     lib.pifu_surrogate_init.argtypes = [P, I, I, U64]
@@ -391,6 +393,15 @@ def pifu_autotune(ctx, rows, stream=None, n_max=32):
     _check(_lib().pifu_autotune(ctx, int(rows), _stream(stream), bn, ms, n_max, ctypes.byref(n)),
            "pifu_autotune", ctx)
     return [(int(bn[i]), float(ms[i])) for i in range(min(n.value, n_max))]
+
+
+PIFU_SCHED_PER_LAYER = 0
+PIFU_SCHED_CHAINED = 1
+
+
+def pifu_set_schedule(ctx, schedule):
+    """Per-layer launches (default) or chained (all hidden layers in one launch)."""
+    _check(_lib().pifu_set_schedule(ctx, int(schedule)), "pifu_set_schedule", ctx)
 
 
 def pifu_set_tiles(ctx, codes):

@@ -1,0 +1,120 @@
+"""The chained schedule (all hidden layers of a BF16 batch, with the fused
+last layer, in one persistent cooperative launch; per-row-block counters
+order a layer after the one it reads) against the per-layer launches.
+
+Both add the same products in the same K order and round every stored
+activation the same way, so every output is the same bits.  The per-layer
+form is itself checked against a BF16 emulation and the FP64 oracle in
+test_gpu_bf16.py.
+"""
+import numpy as np
+import pytest
+
+from oracle import field, localize
+from paper_2007_13988_gb300 import pifu, synth
+
+from gpu_common import OCC_TOL, Ctx, torch
+from test_gpu_bf16 import BF16, emulate, pair_workload
+
+pytestmark = pytest.mark.gpu
+
+MIXED = pifu.PIFU_PREC_MIXED
+
+
+def both_schedules(c, fn):
+    out = {}
+    for name, sched in (("chained", pifu.PIFU_SCHED_CHAINED),
+                        ("per_layer", pifu.PIFU_SCHED_PER_LAYER)):
+        pifu.pifu_set_schedule(c.ctx, sched)
+        out[name] = fn()
+    pifu.pifu_set_schedule(c.ctx, pifu.PIFU_SCHED_PER_LAYER)
+    return out["chained"], out["per_layer"]
+
+
+# m: one row; one partial row block; 40 row blocks + a tail (several row
+# groups); many groups with a ragged last one
+@pytest.mark.parametrize("m", [1, 100, 128 * 40 + 77, 70001])
+def test_chained_query_equals_per_layer(m):
+    w, P, X = pair_workload(m)
+    want = emulate(w.occ_net, X)
+    c = Ctx(w)
+    try:
+        a, b = both_schedules(c, lambda: c.query(P, precision=BF16))
+        np.testing.assert_array_equal(a, b)
+        assert np.max(np.abs(a - want)) <= 2e-3
+    finally:
+        c.close()
+
+
+@pytest.fixture(scope="module")
+def full():
+    c = Ctx(synth.full(0))
+    yield c
+    c.close()
+
+
+def test_chained_full_query_against_oracle(full):
+    # nodes of the finest grid next to the figure (occupancies across the
+    # band around 0.5) and uniform points
+    w = full.w
+    c = localize.node_coords(256)
+    rng = np.random.default_rng(41)
+    G = np.stack([c[rng.integers(0, 257, 40000)] for _ in range(3)], 1)
+    o = field.occupancy(w.occ_net, w.occ_map, w.calib, G)
+    P = np.concatenate([G[np.abs(o - 0.5) < 0.3][:6000],
+                        synth.query_points(6000, seed=41)]).astype(np.float32)
+    a, b = both_schedules(full, lambda: full.query(P, precision=MIXED))
+    np.testing.assert_array_equal(a, b)
+    want = field.occupancy(w.occ_net, w.occ_map, w.calib, P)
+    # MIXED: FP32 values within the margin of 0.5 (few: the field is steep);
+    # elsewhere BF16 values, whose error reaches about 0.03 here, so only the
+    # decisions of occupancies farther than 0.05 from 0.5 are compared
+    near = np.abs(want - 0.5) < 0.01
+    if near.any():
+        assert np.max(np.abs(a[near] - want[near])) <= OCC_TOL
+    far = np.abs(want - 0.5) > 0.05
+    assert np.array_equal(a[far] >= 0.5, want[far] >= 0.5)
+
+
+def test_chained_localization_and_render_equal(full):
+    w = full.w
+
+    def frame():
+        vol = full.localize(precision=MIXED)
+        b, e, v = full.volume_host(vol)
+        d, rgb, m = full.render(256)
+        return b, e, np.nan_to_num(v, nan=-1.0), d, rgb, m
+
+    A, B = both_schedules(full, frame)
+    for x, y in zip(A, B):
+        np.testing.assert_array_equal(x, y)
+
+
+def test_chained_graph_frame_equal(full):
+    t = torch()
+    w = full.w
+    R = 256
+
+    def frame():
+        d = t.empty((R, R), dtype=t.float32, device="cuda")
+        rgb = t.empty((R, R, 3), dtype=t.float32, device="cuda")
+        m = t.empty((R, R), dtype=t.uint8, device="cuda")
+        vol = pifu.pifu_frame(full.ctx, full.occ, full.col, w.calib, w.n0, w.num_levels, R, R,
+                              d, rgb, m, precision=MIXED)
+        t.cuda.synchronize()
+        b, e, v = full.volume_host(vol)
+        return b, np.nan_to_num(v, nan=-1.0), d.cpu().numpy(), rgb.cpu().numpy(), m.cpu().numpy()
+
+    A, B = both_schedules(full, frame)
+    for x, y in zip(A, B):
+        np.testing.assert_array_equal(x, y)
+
+
+def test_set_schedule_refuses_unknown():
+    c = Ctx(synth.tiny(0))
+    try:
+        with pytest.raises(pifu.PifuError) as e:
+            pifu.pifu_set_schedule(c.ctx, 7)
+        assert e.value.status == pifu.PIFU_ERR_ARG
+    finally:
+        c.close()
