@@ -35,6 +35,15 @@ __device__ __forceinline__ uint64_t coarse_segment(const uint32_t* row, int row_
     return (lo | (hi << 32)) >> ((wx & 1) * 16);
 }
 
+// Bits 0..15 of x moved to the even bits 0, 2, .., 30.
+__device__ __forceinline__ uint32_t spread16(uint32_t x) {
+    x = (x | (x << 8)) & 0x00FF00FFu;
+    x = (x | (x << 4)) & 0x0F0F0F0Fu;
+    x = (x | (x << 2)) & 0x33333333u;
+    x = (x | (x << 1)) & 0x55555555u;
+    return x;
+}
+
 // Tentative value of a fine node = tri-linear interpolation of the binarized
 // coarse level = mean of its 1, 2, 4 or 8 coarse corners (a fine index i sits
 // on coarse node i/2 when even, between (i-1)/2 and (i+1)/2 when odd).
@@ -78,21 +87,39 @@ __global__ void __launch_bounds__(256) classify_kernel(const uint32_t* __restric
             const int jc = b ? jc1 : jc0;
             seg[nrows++] = coarse_segment(coarse + ((int64_t)kc * (Nc + 1) + jc) * rwc, rwc, wx);
         }
-    uint32_t c_word = 0u, t_word = 0u;
-    const uint32_t vm = valid_mask(N, wx);
-    for (int bpos = 0; bpos < 32; ++bpos) {
-        if (!((vm >> bpos) & 1u)) break;
-        const int cx = bpos >> 1;      // coarse x relative to 16 wx
-        const int oddx = bpos & 1;
-        int cnt = 0;
-        for (int r = 0; r < nrows; ++r) {
-            cnt += (int)((seg[r] >> cx) & 1u);
-            if (oddx) cnt += (int)((seg[r] >> (cx + 1)) & 1u);
-        }
-        const int ncorner = nrows * (oddx ? 2 : 1);
-        if (cnt > 0 && cnt < ncorner) c_word |= 1u << bpos;
-        if (2 * cnt >= ncorner) t_word |= 1u << bpos;
+    // Bit-parallel over the word's 32 fine nodes: fine bit 2c (even x) sits
+    // on coarse bit c, fine bit 2c+1 (odd x) between coarse bits c and c+1.
+    // Per coarse row r: X_r = the first corner of every fine bit, Y_r = the
+    // second corner of the odd ones (0 at even bits).
+    constexpr uint32_t EV = 0x55555555u, OD = 0xAAAAAAAAu;
+    uint32_t any = 0u, all = 0xffffffffu;
+    uint32_t b0 = 0u, b1 = 0u, b2 = 0u, b3 = 0u;   // bit-sliced corner count
+    auto add = [&](uint32_t v) {
+        uint32_t c = v, t;
+        t = b0 & c; b0 ^= c; c = t;
+        t = b1 & c; b1 ^= c; c = t;
+        t = b2 & c; b2 ^= c; c = t;
+        b3 ^= c;
+    };
+    for (int r = 0; r < nrows; ++r) {
+        const uint32_t e = spread16((uint32_t)seg[r] & 0xffffu);          // bit 2c = coarse c
+        const uint32_t e1 = spread16((uint32_t)(seg[r] >> 1) & 0xffffu);  // bit 2c = coarse c+1
+        const uint32_t X = e | (e << 1);                                  // even: c; odd: c
+        const uint32_t Y = (e1 << 1) & OD;                                // odd: c+1
+        any |= X | Y;
+        all &= X & (Y | EV);
+        add(X);
+        add(Y);
     }
+    // corners per fine bit: nrows (even x) or 2 nrows (odd x); tent: 2 cnt >= corners
+    const uint32_t ge1 = b0 | b1 | b2 | b3;
+    const uint32_t ge2 = b1 | b2 | b3;
+    const uint32_t ge4 = b2 | b3;
+    const uint32_t t_even = nrows == 4 ? ge2 : ge1;                      // cnt >= ceil(nrows / 2)
+    const uint32_t t_odd = nrows == 1 ? ge1 : (nrows == 2 ? ge2 : ge4);   // cnt >= nrows
+    const uint32_t vm = valid_mask(N, wx);
+    const uint32_t c_word = any & ~all & vm;
+    const uint32_t t_word = ((t_even & EV) | (t_odd & OD)) & vm;
     cand[w] = c_word;
     tent[w] = t_word;
     bin[w] = t_word;
