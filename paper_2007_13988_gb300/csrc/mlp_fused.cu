@@ -98,7 +98,7 @@ __device__ __forceinline__ void load_wq(float4 (&w)[kNJ], const float* __restric
 template <int CL>
 __device__ __forceinline__ void fused_layer(const FusedLayer& Ly, float slope,
                                             const float* __restrict__ in,
-                                            const float* __restrict__ xs, int ldx,
+                                            const float* __restrict__ xs, int ldx, int d_in,
                                             float* out, float* __restrict__ red, unsigned rank,
                                             cg::cluster_group& cl) {
     const int S = Ly.n_out / CL;
@@ -106,7 +106,10 @@ __device__ __forceinline__ void fused_layer(const FusedLayer& Ly, float slope,
     const int KW = groups >= kNW ? 1 : kNW / groups;
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
-    const int Kq = (Ly.K1 + Ly.K2) >> 2;
+    // whole quads of real columns; the x segment's last d_in % 4 columns
+    // (quad Kq) are added one by one, and its padding to ldx not at all
+    const int Kq = (Ly.K1 + (Ly.K2 > 0 ? (d_in & ~3) : 0)) >> 2;
+    const int tail = Ly.K2 > 0 ? (d_in & 3) : 0;
     const int pitch = kFP * S;
     for (int task = warp; task < groups * KW; task += kNW) {
         const int g = task % groups;
@@ -135,6 +138,21 @@ __device__ __forceinline__ void fused_layer(const FusedLayer& Ly, float slope,
             }
 #pragma unroll
             for (int j = 0; j < kNJ; ++j) w[j] = wn[j];
+        }
+        if (tail && lane == (Kq & 31) && ksw == (Kq >> 5) % KW) {
+            // the lane whose turn quad Kq is (the order of the 4-wide loop)
+            const int k = 4 * Kq;
+            for (int e = 0; e < tail; ++e) {
+                float wv[kNJ];
+#pragma unroll
+                for (int j = 0; j < kNJ; ++j) wv[j] = __ldg(wrow + (int64_t)j * Ly.ldw + k + e);
+#pragma unroll
+                for (int p = 0; p < kFP; ++p) {
+                    const float x = xs[p * ldx + (k - Ly.K1) + e];
+#pragma unroll
+                    for (int j = 0; j < kNJ; ++j) acc[p * kNJ + j] = fmaf(x, wv[j], acc[p * kNJ + j]);
+                }
+            }
         }
         // sum over the lanes: value v = p * kNJ + j ends in lane v / 4
 #pragma unroll
@@ -219,7 +237,7 @@ __global__ void __launch_bounds__(kFT, 1)
         const float* in = nullptr;
         for (int l = 0; l + 1 < net.nl; ++l) {
             float* out = (l & 1) ? hb1 : hb0;
-            fused_layer<CL>(net.L[l], net.slope, in, xs, net.ldx, out, red, rank, cl);
+            fused_layer<CL>(net.L[l], net.slope, in, xs, net.ldx, net.d_in, out, red, rank, cl);
             in = out;
         }
         // last layer and epilogue: CTA `rank` takes points rank, rank + CL, ...

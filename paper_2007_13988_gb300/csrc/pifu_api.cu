@@ -110,6 +110,7 @@ FusedNet fused_of(const DevNet& n) {
     if (n.layers.size() > (size_t)kFusedMaxLayers) return f;
     f.nl = (int)n.layers.size();
     f.ldx = n.ldx;
+    f.d_in = n.d_in;
     f.max_hidden = round_up(std::max(n.max_hidden, 8), 4);
     f.slope = n.slope;
     for (int l = 0; l < f.nl; ++l) {

@@ -360,6 +360,7 @@ struct FusedLayer {
 struct FusedNet {
     FusedLayer L[kFusedMaxLayers];
     int nl, ldx, max_hidden;
+    int d_in;         // input row width before the padding to ldx
     float slope;
 };
 // Whether the network's shape fits the fused kernel.
