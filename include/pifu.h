@@ -316,7 +316,7 @@ int pifu_autotune(pifu_ctx* ctx, int64_t rows, void* stream, int32_t* bn_out, do
 /* ---- Layer schedule (not in the paper) ----------------------------------------
  * PIFU_SCHED_PER_LAYER (the default): one launch per tensor-core hidden
  * layer.  PIFU_SCHED_CHAINED: a BF16 batch runs all hidden layers of the
- * network, with the last layer fused, in ONE persistent cooperative launch.
+ * network, with the last layer fused, in ONE persistent launch.
  * Rows move through the layers in groups of 128-row blocks, so a layer reads
  * activations the layer before wrote shortly earlier, and the tiles of one
  * layer fill the last wave of another.  It applies when the last layer can be

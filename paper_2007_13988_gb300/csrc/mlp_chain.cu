@@ -21,13 +21,15 @@
 // dep[l][row block] (release), and the TMA producer waits for the full count
 // of layer l-1 on its row block (acquire) before loading that operand.
 //
-// Deadlock freedom: tiles are handed out in increasing order and a tile
-// waits only on tiles with a smaller index, which were handed out before it.
-// With all CTAs resident at once (a cooperative launch), the smallest tile
-// any CTA is waiting on has all its inputs finished, so some CTA always
-// moves.  A tile's count is published when its own stores are done, never
-// later, so no wait goes from a tile to a larger one.  Every wait is bounded
-// anyway; one that gives up sets *err and the CTA stops.
+// Deadlock freedom: tiles are handed out in increasing order, only to CTAs
+// that are running, and a tile waits only on tiles with a smaller index,
+// which were handed out before it to running CTAs.  The smallest tile any CTA
+// is waiting on therefore has all its inputs finished, so some CTA always
+// moves; the CTAs need not be resident all at once.  A tile's count is
+// published when its own stores are done, never later, so no wait goes from
+// a tile to a larger one.  Every wait is bounded anyway; one that gives up
+// sets *err and the CTA stops.  The counters start at zero (set when the
+// buffer is made) and the last CTA to finish zeroes them again.
 //
 // The producer passes each tile index to the MMA warp and the epilogue warps
 // through an 8-slot queue in shared memory (full/empty mbarriers).
@@ -486,6 +488,23 @@ __global__ void __launch_bounds__(kCThreads, 1) tc_chain_kernel(const __grid_con
     tc_fence_before();
     __syncthreads();
     if (warp == 1) tmem_dealloc(tmem, 2 * kAccCols);
+    // The last CTA to finish sets every counter back to zero for the next
+    // launch (all others have made their last count before counting out).
+    __shared__ int s_last;
+    if (threadIdx.x == 0) {
+        __threadfence();
+        s_last = atomicAdd(a.done, 1u) == gridDim.x - 1 ? 1 : 0;
+    }
+    __syncthreads();
+    if (s_last) {
+        __threadfence();
+        for (int l = 0; l < nl; ++l)
+            for (int i = threadIdx.x; i < n_mb; i += blockDim.x) a.dep[l * a.max_mb + i] = 0u;
+        if (threadIdx.x == 0) {
+            *a.next_tile = 0u;
+            *a.done = 0u;
+        }
+    }
 }
 
 int g_chain_attr[64] = {};   // per device: 1 once the shared-memory attribute is set
@@ -528,18 +547,20 @@ cudaError_t launch_tc_chain(const ChainArgs& a, cudaStream_t s) {
     if (e != cudaSuccess) return e;
     const int grid = chain_grid();
     if (grid <= 0) return cudaErrorInvalidConfiguration;
-    if (a.next_tile != a.dep + (size_t)a.nl * a.max_mb) return cudaErrorInvalidValue;
-    e = cudaMemsetAsync(a.dep, 0, sizeof(unsigned int) * ((size_t)a.nl * a.max_mb + 1), s);
-    if (e != cudaSuccess) return e;
-    // all CTAs resident at once: the tiles of one CTA wait on those of others
+    if (a.next_tile != a.dep + (size_t)a.nl * a.max_mb || a.done != a.next_tile + 1)
+        return cudaErrorInvalidValue;
+    // Only running CTAs take tiles, and a tile waits only on tiles taken
+    // before it, so the CTAs need not all be resident at once: a plain launch,
+    // whose prologue may overlap the previous kernel (programmatic dependent
+    // launch; the counters are read only after griddepcontrol.wait).
     cudaLaunchConfig_t cfg{};
     cfg.gridDim = dim3((unsigned)grid);
     cfg.blockDim = dim3(kCThreads);
     cfg.dynamicSmemBytes = chain_smem_bytes();
     cfg.stream = s;
     cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeCooperative;
-    at[0].val.cooperative = 1;
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, tc_chain_kernel, a);

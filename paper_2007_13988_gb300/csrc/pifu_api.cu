@@ -294,7 +294,8 @@ struct pifu_ctx {
     int64_t X_cap = 0, H_cap = 0;   // elements
     __nv_bfloat16* Xb = nullptr;
     __nv_bfloat16* Hb[2] = {nullptr, nullptr};
-    unsigned int* chain_dep = nullptr;   // [kChainMaxLayers][tc_rows / 128] tile-part counters + 1
+    unsigned int* chain_dep = nullptr;   // [kChainMaxLayers][tc_rows / 128] tile-part counters,
+                                         // the tile counter and the finished-CTA counter
     bool chain_on = false;               // pifu_set_schedule
     int64_t tc_rows = 0;            // rows of Xb, Hb[], X8 (grown on demand up to kChunkTC)
     uint8_t* X8 = nullptr;          // [tc_rows][ldx8] E4M3 gather rows (FP8 forms):
@@ -840,7 +841,8 @@ int ensure_tc_rows(pifu_ctx* ctx, int64_t rows) {
     dev_free(ctx->X8);
     dev_free(ctx->chain_dep);
     ctx->tc_rows = 0;
-    CK(dev_alloc(&ctx->chain_dep, (int64_t)kChainMaxLayers * (cap / 128) + 1));
+    CK(dev_alloc(&ctx->chain_dep, (int64_t)kChainMaxLayers * (cap / 128) + 2));
+    CK(cudaMemset(ctx->chain_dep, 0, sizeof(unsigned int) * ((size_t)kChainMaxLayers * (cap / 128) + 2)));
     CK(dev_alloc(&ctx->Xb, need_x * cap));
     CK(dev_alloc(&ctx->Hb[0], need_h * cap));
     CK(dev_alloc(&ctx->Hb[1], need_h * cap));
@@ -1193,6 +1195,7 @@ int run_mlp_tc(pifu_ctx* ctx, const DevNet& net, const PointSrc& src_in, int64_t
             ca.dep = ctx->chain_dep;
             ca.max_mb = (int)(ctx->tc_rows / 128);
             ca.next_tile = ca.dep + (size_t)ca.nl * ca.max_mb;
+            ca.done = ca.next_tile + 1;
             ca.lag = 4;
             // a row group: about one wave of tiles over all layers
             ca.group = std::max(1, chain_grid() / std::max(1, sum_tiles));

@@ -204,9 +204,9 @@ cudaError_t launch_tc_linear(const TcLayerArgs& a, cudaStream_t stream);
 cudaError_t tc_prepare();
 
 // --- mlp_chain.cu ------------------------------------------------------------
-// All hidden layers of one BF16 batch in one persistent cooperative launch
-// (rows move through the layers in groups; per-row-block counters order a
-// layer after the one it reads).
+// All hidden layers of one BF16 batch in one persistent launch (rows move
+// through the layers in groups; per-row-block counters order a layer after
+// the one it reads).
 constexpr int kChainMaxLayers = 4;
 constexpr int kChainBiasFloats = 2048;   // sum of the hidden widths
 struct ChainLayer {
@@ -225,8 +225,9 @@ struct ChainArgs {
     int M;                       // rows (capacity when m_dev is given)
     const unsigned int* m_dev;   // optional device-resident row count (<= M)
     unsigned int* err;
-    unsigned int* dep;           // [nl][max_mb] tile-part counters, zeroed by the launch
-    unsigned int* next_tile;     // = dep + nl * max_mb: the tile counter, zeroed with them
+    unsigned int* dep;           // [nl][max_mb] tile-part counters, zero at launch
+    unsigned int* next_tile;     // = dep + nl * max_mb: the tile counter
+    unsigned int* done;          // = next_tile + 1: CTAs finished (the last one zeroes all)
     int max_mb;                  // >= ceil(M / 128)
     int group;                   // 128-row blocks per row group
     int lag;                     // steps between a layer and the next on one row group
@@ -237,7 +238,8 @@ struct ChainArgs {
 cudaError_t chain_prepare();
 // CTAs of one chained launch (one per SM; 0 before chain_prepare).
 int chain_grid();
-// Zeroes a.dep and the tile counter and launches (cooperative, one CTA per SM).
+// Launches one CTA per SM (programmatic dependent launch); the counters must
+// be zero, and are zero again when the kernel ends.
 cudaError_t launch_tc_chain(const ChainArgs& a, cudaStream_t stream);
 
 // Encode a 2-D BF16 tensor map (128-byte swizzle, zero fill out of bounds).

@@ -1,6 +1,6 @@
 """The chained schedule (all hidden layers of a BF16 batch, with the fused
-last layer, in one persistent cooperative launch; per-row-block counters
-order a layer after the one it reads) against the per-layer launches.
+last layer, in one persistent launch; per-row-block counters order a layer
+after the one it reads) against the per-layer launches.
 
 Both add the same products in the same K order and round every stored
 activation the same way, so every output is the same bits.  The per-layer
