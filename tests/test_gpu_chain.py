@@ -118,3 +118,28 @@ def test_set_schedule_refuses_unknown():
         assert e.value.status == pifu.PIFU_ERR_ARG
     finally:
         c.close()
+
+
+def test_chained_lockstep_batch_equal(full):
+    """B frames in lockstep (one device-sized key list per round, one chained
+    launch per round for all frames) under both schedules."""
+    from test_gpu_batch import host_volume, outputs, stream_frames
+    t = torch()
+    w = full.w
+    B = 2
+    _, maps = stream_frames(B)
+
+    def batch():
+        d, rgb, m = outputs(B)
+        vols = pifu.pifu_frames(full.ctx, [o for o, _ in maps], [c for _, c in maps],
+                                [w.calib] * B, w.n0, w.num_levels, 256, 256, d, rgb, m,
+                                precision=MIXED)
+        t.cuda.synchronize()
+        out = []
+        for f, v in enumerate(vols):
+            out.extend(host_volume(full, v))
+        return out + [d.cpu().numpy(), rgb.cpu().numpy(), m.cpu().numpy()]
+
+    A, Bv = both_schedules(full, batch)
+    for x, y in zip(A, Bv):
+        np.testing.assert_array_equal(x, y)
