@@ -20,7 +20,8 @@
 // output tiles (tile t covers rows 128 (t / (N/BN)), columns BN (t % (N/BN)),
 // so the CTAs working at one moment share A rows through L2).  10 warps:
 //   warp 0 lane 0   TMA producer: A (128 x 64) and W (BN x 64) tiles into a
-//                   4-stage ring of 128B-swizzled shared-memory buffers;
+//                   ring of 128B-swizzled shared-memory buffers, 4 stages
+//                   deep for BN = 256, 6 for 128, 8 for 64 (the same 192 KB);
 //   warp 1          allocates 2 x BN TMEM columns; lane 0 issues 4 x
 //                   tcgen05.mma (K = 16) per stage into the accumulator of
 //                   the current tile (two accumulators, used alternately),
@@ -62,12 +63,21 @@ constexpr int kFuseFloats = 4 * 256 + 2 * 4 * TBM + 16;   // last-layer W, excha
 constexpr int kStageRowBytes = 64;                          // store staging: 64 B per row
 constexpr int kStageBytes = kEpiWarps * 32 * kStageRowBytes; // 32 rows per epilogue warp
 
+// Ring depth of a tile width: narrower W tiles make smaller stages, so the
+// same 192 KB holds more of them (BN 256: 4, 128: 6, 64: 8) and more operand
+// bytes stay in flight per MMA cycle.
+__host__ __device__ constexpr int tc_stages(int BN) {
+    return TSTAGES * (TBM * TBK * 2 + 256 * TBK * 2) / (TBM * TBK * 2 + BN * TBK * 2);
+}
+
 __host__ __device__ constexpr uint32_t tc_smem_bytes(int BN) {
     // operand ring + 1024-byte alignment slack + barriers + staged bias and
     // column scales + fused last layer + output staging
-    return (uint32_t)TSTAGES * (TBM * TBK * 2 + BN * TBK * 2) + 1024 + 256 + 2 * kMaxN * 4 +
+    return (uint32_t)tc_stages(BN) * (TBM * TBK * 2 + BN * TBK * 2) + 1024 + 256 + 2 * kMaxN * 4 +
            kFuseFloats * 4 + kStageBytes + 1024;   // + alignment of the staging area
 }
+static_assert(tc_stages(256) == 4 && tc_stages(128) == 6 && tc_stages(64) == 8, "ring depths");
+static_assert(2 * tc_stages(64) * 8 + 4 * 8 + 4 <= 256, "barriers fit in front of the bias");
 static_assert(tc_smem_bytes(256) <= 227 * 1024, "shared memory of the widest tile");
 
 // Four values rounded to E4M3 (saturating), first value in the lowest byte.
@@ -90,13 +100,14 @@ __global__ void __launch_bounds__(kThreads, 1) tc_linear_kernel(
     constexpr uint32_t A_BYTES = TBM * TBK * 2;
     constexpr uint32_t B_BYTES = BN * TBK * 2;
     constexpr uint32_t TMEM_COLS = 2 * BN;   // two accumulators; 128, 256 or 512
+    constexpr int NST = tc_stages(BN);
     extern __shared__ uint8_t smem_raw[];
     uint8_t* sA = reinterpret_cast<uint8_t*>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
-    uint8_t* sB = sA + TSTAGES * A_BYTES;
-    uint64_t* full = reinterpret_cast<uint64_t*>(sB + TSTAGES * B_BYTES);
-    uint64_t* empty = full + TSTAGES;
-    uint64_t* accf = empty + TSTAGES;   // [2] accumulator ready for the epilogue
+    uint8_t* sB = sA + NST * A_BYTES;
+    uint64_t* full = reinterpret_cast<uint64_t*>(sB + NST * B_BYTES);
+    uint64_t* empty = full + NST;
+    uint64_t* accf = empty + NST;   // [2] accumulator ready for the epilogue
     uint64_t* acce = accf + 2;          // [2] accumulator drained by the epilogue
     uint32_t* tslot = reinterpret_cast<uint32_t*>(acce + 2);
     float* sbias = reinterpret_cast<float*>(reinterpret_cast<uint8_t*>(full) + 256);
@@ -117,7 +128,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_linear_kernel(
     // Prologue: everything here depends only on the weights, so with a
     // programmatic dependent launch it overlaps the previous kernel's tail.
     if (threadIdx.x == 0) {
-        for (int s = 0; s < TSTAGES; ++s) {
+        for (int s = 0; s < NST; ++s) {
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
@@ -158,8 +169,8 @@ __global__ void __launch_bounds__(kThreads, 1) tc_linear_kernel(
                 const int m0 = (t / n_tn) * TBM;
                 const int n0 = (t % n_tn) * BN;
                 for (int kb = 0; kb < nk; ++kb, ++g) {
-                    const uint32_t s = g % TSTAGES;
-                    const uint32_t u = g / TSTAGES;
+                    const uint32_t s = g % NST;
+                    const uint32_t u = g / NST;
                     if (u > 0 && !mbar_wait(&empty[s], (u - 1) & 1u, kWaitLimit)) {
                         ok = false;
                         break;
@@ -188,8 +199,8 @@ __global__ void __launch_bounds__(kThreads, 1) tc_linear_kernel(
                 tc_fence_after();
                 const uint32_t d = tmem + b * BN;
                 for (int kb = 0; kb < nk; ++kb, ++g) {
-                    const uint32_t s = g % TSTAGES;
-                    const uint32_t u = g / TSTAGES;
+                    const uint32_t s = g % NST;
+                    const uint32_t u = g / NST;
                     if (!mbar_wait(&full[s], u & 1u, kWaitLimit)) {
                         ok = false;
                         break;
