@@ -74,6 +74,9 @@ def test_null_arguments_are_rejected_on_the_host():
     assert lib.pifu_localize(None, None, calib, None, None, None) == pifu.PIFU_ERR_ARG
     assert lib.pifu_render(None, None, None, None, calib, None, None, None, None) == pifu.PIFU_ERR_ARG
     assert lib.pifu_sync_stats(None, None) == pifu.PIFU_ERR_ARG
+    codes = (ctypes.c_int32 * 1)(256)
+    assert lib.pifu_set_tiles(None, codes, 1) == pifu.PIFU_ERR_ARG
+    assert lib.pifu_set_schedule(None, pifu.PIFU_SCHED_CHAINED) == pifu.PIFU_ERR_ARG
     lib.pifu_destroy(None)
 
 
