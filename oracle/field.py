@@ -22,9 +22,10 @@ Readings where the paper is silent (each also listed in the design notes):
 
 Pins: tests/test_oracle_field.py (texel-centre sampling returns stored values,
 a map linear in (u, v) is reproduced exactly, border clamping, MLP against an
-explicit per-neuron loop, the Table A1 flop count; SoftZ closed forms,
-batch-normalization statistics, a hand-built CBN network, the constructed
-CBN network's closed form).
+explicit per-neuron loop, the Table A1 flop count; the colour mapping, input
+order and a constructed colour network's closed form end to end; SoftZ
+closed forms, batch-normalization statistics, a hand-built CBN network, the
+constructed CBN network's closed form).
 """
 from __future__ import annotations
 

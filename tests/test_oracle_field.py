@@ -209,6 +209,64 @@ def test_colour_input_order():
     np.testing.assert_allclose(rgb[0], (np.tanh([0.25, -0.5, 0.75]) + 1) / 2, atol=1e-15)
 
 
+def _passthrough_colour_net(d, n_hidden, width, A, c, slope, alpha):
+    """A colour MLP whose hidden layers carry the input x unchanged in the
+    pair form [x, -x] through leaky-ReLU (lrelu(x) - lrelu(-x) = (1 + s) x),
+    each skip layer rebuilding it from h_{l-1} (weight alpha) and from its x
+    segment (weight 1 - alpha), and whose last layer (also a skip layer)
+    outputs A x + c.  So f_T(x) = A x + c exactly, whatever the depth."""
+    assert width >= 2 * d
+    inv = 1.0 / (1.0 + slope)
+    Ws, bs = [], []
+    for l in range(n_hidden + 1):
+        last = l == n_hidden
+        n_out = A.shape[0] if last else width
+        fan_h = d if l == 0 else width
+        Wh = np.zeros((n_out, fan_h))
+        Wx = np.zeros((n_out, d))
+        T = A if last else np.vstack([np.eye(d), -np.eye(d)])   # the map applied to x
+        if l == 0:
+            Wh[:T.shape[0], :d] = T   # layer 0 reads x only
+        else:
+            # x = (h[:d] - h[d:2d]) / (1 + s)
+            rebuild = np.hstack([np.eye(d), -np.eye(d)]) * inv
+            Wh[:T.shape[0], :2 * d] = alpha * (T @ rebuild)
+            Wx[:T.shape[0], :] = (1.0 - alpha) * T
+        Ws.append(Wh if l == 0 else np.hstack([Wh, Wx]))
+        bs.append(c.copy() if last else np.zeros(n_out))
+    return _Net(d, Ws, bs, skip=tuple(range(1, n_hidden + 1)), slope=slope)
+
+
+@pytest.mark.parametrize("n_hidden,alpha", [(1, 0.5), (4, 0.25)])
+def test_colour_end_to_end_closed_form_at_texel_centres(n_hidden, alpha):
+    # T(P) = (tanh(A [phi_T, phi_O, P_z] + c) + 1) / 2 for a network built to
+    # compute A x + c (above), sampled at texel centres where phi is the
+    # stored texel: pins the input order, the skip concatenation [h, x] in
+    # every layer including the last, the leaky-ReLU slope and the tanh
+    # mapping, end to end through projection and sampling.
+    rng = np.random.default_rng(11)
+    H = W = 8
+    CT, CO = 3, 4
+    T = rng.standard_normal((H, W, CT)).astype(np.float32)
+    O = rng.standard_normal((H, W, CO)).astype(np.float32)
+    d = CT + CO + 1
+    A = rng.uniform(-0.5, 0.5, (3, d))
+    c = rng.uniform(-0.2, 0.2, 3)
+    net = _passthrough_colour_net(d, n_hidden, 2 * d + 3, A, c, slope=0.2, alpha=alpha)
+    i = rng.integers(0, W, 200)
+    j = rng.integers(0, H, 200)
+    z = rng.uniform(-1, 1, 200)
+    u, v = texel_uv(i, j, W, H)
+    P = np.stack([u, v, z], 1)
+    x = np.concatenate([T[j, i].astype(np.float64), O[j, i].astype(np.float64), z[:, None]], 1)
+    want = (np.tanh(x @ A.T + c) + 1.0) / 2.0
+    got = field.colour(net, O, T, synth.calib_identity(), P)
+    np.testing.assert_allclose(got, want, rtol=0, atol=1e-12)
+    # a plausible mistake fails: phi_O before phi_T
+    swapped = np.concatenate([x[:, CT:CT + CO], x[:, :CT], x[:, -1:]], 1)
+    assert np.max(np.abs((np.tanh(swapped @ A.T + c) + 1) / 2 - got)) > 1e-3
+
+
 # ---- CBN + SoftZ (Appendix, Eq. 7 and Eq. 8) ------------------------------------
 
 def test_soft_z_closed_forms():
