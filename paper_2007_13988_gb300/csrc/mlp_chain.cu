@@ -46,6 +46,7 @@
 #include "pifu_internal.h"
 #include "sm100.cuh"
 #include "tc_common.cuh"
+#include "chain_order.cuh"
 
 namespace pifu {
 namespace {
@@ -71,55 +72,9 @@ constexpr uint32_t chain_smem_bytes() {
            kFuseFloats * 4 + kStageBytes + 1024;
 }
 static_assert(chain_smem_bytes() <= 227 * 1024, "shared memory of the chain kernel");
-
-// Position in the tile order: step s, layer slot j (layer nl-1-j), tile pos
-// of the segment (s, j), whose length is len.
-struct ChainPos {
-    int s, j, pos, len;
-};
+static_assert(kChainMaxLayers <= kChainOrderMaxLayers, "tile order of every chain");
 
 constexpr int kTQ = 8;   // tile queue slots (the producer runs at most 6 tiles ahead)
-
-__device__ __forceinline__ int seg_len(const ChainArgs& a, int n_mb, int n_g, int s, int j) {
-    const int l = a.nl - 1 - j;
-    const int gi = s - a.lag * l;
-    if (gi < 0 || gi >= n_g) return 0;
-    const int mb0 = gi * a.group;
-    const int nmb = min(a.group, n_mb - mb0);
-    return nmb * (a.L[l].N / a.L[l].BN);
-}
-
-// Moves k tiles forward; false past the last tile.
-__device__ bool chain_advance(const ChainArgs& a, int n_mb, int n_g, ChainPos& p, long long k) {
-    const int n_steps = n_g + a.lag * (a.nl - 1);
-    while (p.s < n_steps) {
-        if ((long long)p.pos + k < (long long)p.len) {
-            p.pos += (int)k;
-            return true;
-        }
-        k -= p.len - p.pos;
-        if (++p.j == a.nl) {
-            p.j = 0;
-            ++p.s;
-        }
-        p.pos = 0;
-        p.len = p.s < n_steps ? seg_len(a, n_mb, n_g, p.s, p.j) : 0;
-    }
-    return false;
-}
-
-struct ChainTile {
-    int l, mb, nt;
-};
-
-__device__ __forceinline__ ChainTile chain_decode(const ChainArgs& a, const ChainPos& p) {
-    ChainTile t;
-    t.l = a.nl - 1 - p.j;
-    const int ntn = a.L[t.l].N / a.L[t.l].BN;
-    t.mb = (p.s - a.lag * t.l) * a.group + p.pos / ntn;
-    t.nt = p.pos % ntn;
-    return t;
-}
 
 __device__ __forceinline__ bool wait_dep(const unsigned int* p, unsigned int target) {
     for (uint32_t it = 0; it < kDepWait; ++it) {
@@ -205,18 +160,25 @@ __global__ void __launch_bounds__(kCThreads, 1) tc_chain_kernel(const __grid_con
     const int n_mb = (M + CBM - 1) / CBM;
     const int n_g = (n_mb + a.group - 1) / a.group;
 
+    ChainShape shape{};
+    shape.nl = nl;
+    shape.lag = a.lag;
+    shape.group = a.group;
     long long total = 0;
-    for (int l = 0; l < nl; ++l) total += (long long)n_mb * (a.L[l].N / a.L[l].BN);
+    for (int l = 0; l < nl; ++l) {
+        shape.ntn[l] = a.L[l].N / a.L[l].BN;
+        total += (long long)n_mb * shape.ntn[l];
+    }
 
     bool ok = true;
     // each role walks the same increasing tile indices with its own cursor
-    ChainPos p{0, 0, 0, n_g > 0 ? seg_len(a, n_mb, n_g, 0, 0) : 0};
-    if (n_g > 0) chain_advance(a, n_mb, n_g, p, 0);
+    ChainPos p = chain_begin(shape, n_mb, n_g);
+    if (n_g > 0) chain_advance(shape, n_mb, n_g, p, 0);
     long long at = 0;
     auto seek = [&](long long t) {
-        chain_advance(a, n_mb, n_g, p, t - at);
+        chain_advance(shape, n_mb, n_g, p, t - at);
         at = t;
-        return chain_decode(a, p);
+        return chain_decode(shape, p);
     };
 
     if (warp == 0) {
