@@ -33,6 +33,23 @@ def test_library_exports_every_declared_symbol():
     assert set(pifu.EXPORTS) == names
 
 
+def test_binding_constants_match_the_header():
+    # every enumerator or #define of the header that the binding names
+    # carries the same value there
+    src = open(os.path.join(ROOT, "include", "pifu.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    pairs = re.findall(r"\b(PIFU_[A-Z0-9_]+)\s*=\s*(-?\d+)", src)
+    pairs += re.findall(r"#define\s+(PIFU_[A-Z0-9_]+)\s+\(?(-?\d+)\)?", src)
+    checked = 0
+    for name, value in pairs:
+        if hasattr(pifu, name):
+            assert getattr(pifu, name) == int(value), name
+            checked += 1
+    assert checked >= 10
+    for name in ("PIFU_SCHED_PER_LAYER", "PIFU_SCHED_CHAINED", "PIFU_PREC_MIXED", "PIFU_ERR_ARG"):
+        assert name in dict(pairs), name
+
+
 def test_status_strings():
     assert pifu.pifu_status_string(0) == "ok"
     assert "converge" in pifu.pifu_status_string(pifu.PIFU_ERR_NOT_CONVERGED)
