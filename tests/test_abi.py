@@ -48,6 +48,11 @@ def test_binding_constants_match_the_header():
     assert checked >= 10
     for name in ("PIFU_SCHED_PER_LAYER", "PIFU_SCHED_CHAINED", "PIFU_PREC_MIXED", "PIFU_ERR_ARG"):
         assert name in dict(pairs), name
+    # the profiler classes: the binding's names in the header's order
+    classes = {n[len("PIFU_K_"):].lower(): int(v) for n, v in pairs if n.startswith("PIFU_K_")}
+    assert len(pifu.KERNEL_CLASSES) == classes.pop("count")
+    for name, idx in classes.items():
+        assert pifu.KERNEL_CLASSES[idx] == name, (name, idx)
 
 
 def test_status_strings():
