@@ -475,10 +475,15 @@ int pifu_profile_read(pifu_ctx* ctx, pifu_kernel_stats* out);
  * points for the 257-1024-512-256-128-1 network, 14,169 for 33-128-64-1);
  * a larger m returns PIFU_ERR_ARG before any work is enqueued.
  * All calls share the array: calls that overlap on the GPU (other streams,
- * other threads) race and must be serialised by the caller.  The first call
- * on a device looks the array's device address up (cudaGetSymbolAddress)
- * with that device current; make that first call before any stream capture.
- * No call allocates memory, host or device.
+ * other threads) race and must be serialised by the caller.  Each call looks
+ * the array's device address up (cudaGetSymbolAddress) on the current device
+ * (inside a stream capture: the address its last call outside one found);
+ * make the first call on a device before any stream capture.  With CUDA's
+ * lazy module loading (the default), the first call on a device also loads
+ * the library's device code and its static arrays there, the 16 MiB array
+ * included: make it while that much device memory is still free (for
+ * instance before the application's allocator reserves the rest).  Apart
+ * from that one-time load no call allocates memory, host or device.
  * Errors: PIFU_ERR_ARG, PIFU_ERR_FORMAT, PIFU_ERR_UNSUPPORTED (bf16 map),
  * PIFU_ERR_CUDA. */
 int pifu_query_noalloc(const void* weight_blob, size_t bytes, const void* weight_blob_dev,

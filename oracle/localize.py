@@ -211,33 +211,41 @@ def corner_mean_deviation(coarse_vals):
     return mean, dev
 
 
+def refine_binarized(field, coarse: Level):
+    """One finer level of the binarized-octree baseline."""
+    N = 2 * coarse.N
+    T = upsample_tentative(coarse.values >= 0.5)
+    ev = (T > 0.0) & (T < 1.0)
+    values = T.copy()
+    n = evaluate_mask(field, N, ev, values)
+    return Level(N=N, values=values, evaluated=ev, tentative=T, selected=ev,
+                 n_eval=n, conflict_rounds=0)
+
+
 def octree_binarized(field, n0, num_levels):
     """Binarized-octree baseline; returns the levels."""
     levels = [dense(field, n0)]
     for _ in range(num_levels - 1):
-        coarse = levels[-1]
-        N = 2 * coarse.N
-        T = upsample_tentative(coarse.values >= 0.5)
-        ev = (T > 0.0) & (T < 1.0)
-        values = T.copy()
-        n = evaluate_mask(field, N, ev, values)
-        levels.append(Level(N=N, values=values, evaluated=ev, tentative=T, selected=ev,
-                            n_eval=n, conflict_rounds=0))
+        levels.append(refine_binarized(field, levels[-1]))
     return levels
+
+
+def refine_threshold(field, coarse: Level, threshold):
+    """One finer level of the threshold-subdivision baseline."""
+    N = 2 * coarse.N
+    mean, dev = corner_mean_deviation(coarse.values)
+    ev = dev > threshold
+    values = mean.copy()
+    n = evaluate_mask(field, N, ev, values)
+    return Level(N=N, values=values, evaluated=ev, tentative=mean, selected=ev,
+                 n_eval=n, conflict_rounds=0)
 
 
 def octree_threshold(field, n0, num_levels, threshold):
     """Threshold-subdivision baseline; returns the levels."""
     levels = [dense(field, n0)]
     for _ in range(num_levels - 1):
-        coarse = levels[-1]
-        N = 2 * coarse.N
-        mean, dev = corner_mean_deviation(coarse.values)
-        ev = dev > threshold
-        values = mean.copy()
-        n = evaluate_mask(field, N, ev, values)
-        levels.append(Level(N=N, values=values, evaluated=ev, tentative=mean, selected=ev,
-                            n_eval=n, conflict_rounds=0))
+        levels.append(refine_threshold(field, levels[-1], threshold))
     return levels
 
 

@@ -33,16 +33,27 @@ constexpr int kMaxLayers = 16;
 
 static __device__ __align__(256) float g_scratch[kScratchFloats];
 
-// Device address of g_scratch, looked up once per device.  In host code the
-// name g_scratch is only a host-side stand-in, never a device address.
+// Device address of g_scratch on the current device.  In host code the name
+// g_scratch is only a host-side stand-in, never a device address.  Outside a
+// stream capture the address is looked up on every call (cheap), so that a
+// module reloaded after cudaDeviceReset, or another context made current on
+// the same device, is followed; inside a capture the address of the last
+// lookup on this device is used (the first call on a device has to come
+// before any capture).  The first lookup in a process also loads the
+// library's device code and its static arrays onto the device when CUDA loads
+// modules lazily (the default since CUDA 12.2): that load allocates the
+// 16 MiB array, which is why the first call must come while that much device
+// memory is still free.
 std::mutex g_mu;
 float* g_scratch_dev[kMaxDevices] = {};
 
-int scratch_address(float** out) {
+int scratch_address(cudaStream_t s, float** out) {
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return PIFU_ERR_CUDA;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) return PIFU_ERR_CUDA;
     std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_scratch_dev[dev]) {
+    if (cs == cudaStreamCaptureStatusNone || !g_scratch_dev[dev]) {
         void* p = nullptr;
         const cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
         if (e != cudaSuccess || !p) return PIFU_ERR_CUDA;
@@ -211,13 +222,13 @@ extern "C" int pifu_query_noalloc(const void* weight_blob, size_t bytes, const v
     const int64_t m_max = kScratchFloats / per_point;
     if (m > m_max) return PIFU_ERR_ARG;
 
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
     float* scratch = nullptr;
-    st = scratch_address(&scratch);
+    st = scratch_address(s, &scratch);
     if (st != PIFU_OK) return st;
     float* X = scratch;
     float* H[2] = {scratch + m * ldx, scratch + m * (ldx + max_hidden)};
 
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
     const char* wdev = static_cast<const char*>(weight_blob_dev);
     Calib cal;
     std::memcpy(cal.c, calib, sizeof(cal.c));

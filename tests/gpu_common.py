@@ -3,9 +3,10 @@ library context, and the comparison rules of the plain FP32 path.
 
 Tolerances (plain FP32 form against the FP64 oracle):
 * occupancy: max-abs error <= 1e-4;
-* binarized decisions and evaluated sets: identical, except where an
-  oracle value lies within 1e-4 of 0.5 (such points are counted and the
-  comparison then only bounds the difference);
+* localization: evaluated sets, binarized volumes, evaluation counts and
+  conflict rounds identical at every level to the oracle's, where the oracle
+  follows the library's side of 0.5 at the nodes whose exact occupancy lies
+  within 1e-4 of it (tests/parity_rules.py; such nodes are counted);
 * depth: within 1e-3 of the volume extent (2), i.e. 2e-3 in NDC, on rays
   whose samples up to the crossing stay 1e-4 away from 0.5;
 * colour: max-abs error <= 1e-3.
@@ -14,10 +15,51 @@ from __future__ import annotations
 
 import numpy as np
 
-OCC_TOL = 1e-4
-NEAR_HALF = 1e-4
+import parity_rules as pr
+from parity_rules import NEAR_HALF, OCC_TOL
 DEPTH_TOL = 1e-3 * 2.0
 COLOUR_TOL = 1e-3
+
+
+def depth_step(N):
+    """One depth interval of a ray sampled at the depth nodes of an N-cell
+    level, 2 / N in NDC.  Two renders that agree on a ray's first inside
+    sample put its crossing in the same interval, so their depths differ by
+    less than this whatever the error of the samples.  This bounds the
+    tensor-core forms, whose occupancies away from the FP32 re-check band
+    keep their BF16 rounding (up to a few 1e-2), which the linear crossing
+    solve passes on to the depth in proportion to the interval."""
+    return 2.0 / N
+
+
+def check_mixed_values(c, vol, base, field, margin=0.02, sure=0.06):
+    """MIXED forms at the finest level: every stored occupancy within `margin`
+    of 0.5 was evaluated again in FP32, so it is within OCC_TOL of the
+    oracle's; and every decision at a node whose exact occupancy is more than
+    `sure` from 0.5 (about twice the largest BF16 error seen) is the
+    oracle's.  Returns the figures."""
+    b, e, v = c.volume_host(vol)
+    fine = base[-1]
+    idx = np.flatnonzero(e.ravel())
+    o = np.empty(len(idx))
+    have = fine.evaluated.ravel()[idx]
+    o[have] = fine.values.ravel()[idx[have]]
+    if (~have).any():
+        from oracle import localize
+        n1 = vol.n + 1
+        q = idx[~have]
+        cc = localize.node_coords(vol.n)
+        P = np.stack([cc[q % n1], cc[(q // n1) % n1], cc[q // (n1 * n1)]], 1)
+        o[~have] = field(P)
+    g = v.ravel()[idx]
+    band = np.abs(g - 0.5) < margin
+    far = np.abs(o - 0.5) > sure
+    res = {"in_band": int(band.sum()),
+           "band_err": float(np.max(np.abs(g[band] - o[band]))) if band.any() else 0.0,
+           "far_flips": int(np.count_nonzero((g[far] >= 0.5) != (o[far] >= 0.5)))}
+    assert res["band_err"] <= OCC_TOL, res
+    assert res["far_flips"] == 0, res
+    return res
 
 
 def torch():
@@ -102,44 +144,73 @@ class Ctx:
 
 def near_half_count(levels):
     """Oracle-evaluated values within NEAR_HALF of 0.5 over all levels."""
-    n = 0
-    for l in levels:
-        v = l.values[l.evaluated]
-        n += int(np.count_nonzero(np.abs(v - 0.5) < NEAR_HALF))
-    return n
+    return pr.near_decisions(levels)
 
 
-def compare_volume(gpu_b, gpu_e, gpu_v, levels, stats):
-    """Check a GPU-localized finest level against the oracle's levels.
+def eval_level(c, vol, l, full_values=False):
+    """The finest level of a localization as the comparison rules take it
+    (l: its index in the schedule, for the per-level counters)."""
+    occ, ev, val = c.pifu.volume_tensors(vol)
+    n, rw = vol.n, vol.row_words
+    b = c.pifu.unpack_bits(occ.cpu().numpy(), n, rw)
+    e = c.pifu.unpack_bits(ev.cpu().numpy(), n, rw)
+    v = val.cpu().numpy().astype(np.float64).reshape((n + 1,) * 3)
+    if not full_values:
+        v = np.where(e, v, np.nan)
+    return pr.EvalLevel(n, b, e, v, int(vol.evals_per_level[l]), int(vol.conflict_rounds[l]))
 
-    Returns a dict of the figures.  Exact set equality is required when no
-    oracle value lies within NEAR_HALF of 0.5; otherwise the differences are
-    reported and bounded."""
-    fine = levels[-1]
-    near = near_half_count(levels)
-    both = gpu_e & fine.evaluated
-    err = float(np.max(np.abs(gpu_v[both] - fine.values[both]))) if both.any() else 0.0
-    res = {
-        "near_half": near,
-        "eval_symdiff": int(np.count_nonzero(gpu_e ^ fine.evaluated)),
-        "bin_diff": int(np.count_nonzero(gpu_b ^ fine.binary)),
-        "max_abs_err": err,
-        "evals_gpu": [int(stats.evals_per_level[i]) for i in range(len(levels))],
-        "evals_oracle": [int(l.n_eval) for l in levels],
-        "rounds_gpu": [int(stats.conflict_rounds[i]) for i in range(len(levels))],
-        "rounds_oracle": [int(l.conflict_rounds) for l in levels],
-    }
-    assert err <= OCC_TOL, res
+
+def check_localization(c, base, field, n0=None, levels=None, calib=None, kind="method",
+                       threshold=None, **kw):
+    """Localize through the library and compare with the oracle exactly
+    (tests/parity_rules.py): every level's evaluated set, binarized volume,
+    evaluation count and conflict rounds equal the flip-aware oracle's, and
+    every evaluated value is within OCC_TOL of the oracle's.
+
+    base: the plain oracle levels of this schedule; field: the oracle's field
+    (evaluated only at nodes base did not evaluate).  When some oracle
+    decision is within rounding of its threshold, the library's levels are
+    taken one by one from localizations with 1, 2, ... levels (the first
+    levels of a schedule do not depend on the later ones), so that the
+    oracle follows the library's side of each such decision.
+    Returns (the figures, the flip-aware oracle levels, the last volume)."""
+    w = c.w
+    n0 = w.n0 if n0 is None else n0
+    L = w.num_levels if levels is None else levels
+    if kind == "binarized":
+        kw["subdivision"] = c.pifu.PIFU_SUBDIV_BINARIZED
+    elif kind == "threshold":
+        kw["subdivision"] = c.pifu.PIFU_SUBDIV_THRESHOLD
+        kw["threshold"] = threshold
+    full_values = kind == "threshold"
+    near = pr.near_decisions(base, threshold)
+    theirs = []
+    if near > 0:
+        for l in range(L - 1):
+            v = c.localize(n0=n0, levels=l + 1, calib=calib, **kw)
+            theirs.append(eval_level(c, v, l, full_values))
+    # the full schedule last: it stays the context's volume for a render
+    vol = c.localize(n0=n0, levels=L, calib=calib, **kw)
+    final = eval_level(c, vol, L - 1, full_values)
+    # the counters of every level
+    counts = [int(vol.evals_per_level[l]) for l in range(L)]
+    rounds = [int(vol.conflict_rounds[l]) for l in range(L)]
     if near == 0:
-        assert res["eval_symdiff"] == 0, res
-        assert res["bin_diff"] == 0, res
-        assert res["evals_gpu"] == res["evals_oracle"], res
-        assert res["rounds_gpu"] == res["rounds_oracle"], res
+        theirs = [None] * (L - 1) + [final]
+        got = base
+        trues = [np.where(lv.evaluated, lv.values, np.nan) for lv in base]
+        stats = {"substituted": 0, "flipped": 0}
     else:
-        # a flip at a near-0.5 point may shift the refinement locally
-        assert res["bin_diff"] <= 64 * near, res
-        assert res["eval_symdiff"] <= 4096 * near, res
-    return res
+        theirs.append(final)
+        got, trues, stats = pr.flip_aware(field, n0, theirs, base=base, kind=kind,
+                                          threshold=threshold)
+    res = pr.compare(theirs, got, trues, rounds=kind == "method", threshold=threshold)
+    res.update(near=near, **stats)
+    res["evals"] = (counts, [int(lv.n_eval) for lv in got])
+    res["rounds"] = (rounds, [int(lv.conflict_rounds) for lv in got])
+    assert res["evals"][0] == res["evals"][1], res
+    assert res["rounds"][0] == res["rounds"][1], res
+    return res, got, vol
 
 
 def ambiguous_rays(values, R):

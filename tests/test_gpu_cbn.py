@@ -1,15 +1,16 @@
 """The paper's final occupancy network, CBN + SoftZ (Appendix, Eq. 7 and
 Eq. 8), through the C ABI against the FP64 oracle: the field at ragged batch
 sizes, the coarse-to-fine localization and the render, at the plain FP32
-parity bar (occupancy <= 1e-4; sets, volumes and counts identical unless an
-oracle value lies within 1e-4 of 0.5), and the forms a CBN context refuses."""
+parity bar (occupancy <= 1e-4; sets, volumes, counts and rounds identical at
+every level, with the oracle following the library's side of 0.5 where its
+own value lies within 1e-4 of it), and the forms a CBN context refuses."""
 import numpy as np
 import pytest
 
 from oracle import field, localize, render
 from paper_2007_13988_gb300 import pifu, synth
 
-from gpu_common import COLOUR_TOL, DEPTH_TOL, OCC_TOL, Ctx, ambiguous_rays, compare_volume
+from gpu_common import COLOUR_TOL, DEPTH_TOL, OCC_TOL, Ctx, ambiguous_rays, check_localization
 
 pytestmark = pytest.mark.gpu
 
@@ -70,25 +71,22 @@ def tiny_levels(tiny):
 
 
 def test_cbn_localize_tiny(tiny, tiny_levels):
-    vol = tiny.localize()
-    b, e, v = tiny.volume_host(vol)
-    res = compare_volume(b, e, v, tiny_levels, vol)
+    res, _, _ = check_localization(tiny, tiny_levels, lambda P: occ_oracle(tiny.w, P))
     print("CBN tiny localization:", res)
 
 
 def test_cbn_localize_full_128(full):
     w = full.w
-    lv = localize.hierarchical(lambda P: occ_oracle(w, P), 32, 3)
-    vol = full.localize(n0=32, levels=3)
-    b, e, v = full.volume_host(vol)
-    res = compare_volume(b, e, v, lv, vol)
+    f = lambda P: occ_oracle(w, P)
+    lv = localize.hierarchical(f, 32, 3)
+    res, _, _ = check_localization(full, lv, f, n0=32, levels=3)
     print("CBN full 32^3 -> 128^3:", res)
 
 
 def test_cbn_render_tiny(tiny, tiny_levels):
     w = tiny.w
-    tiny.localize()
-    fine = tiny_levels[-1]
+    _, lv, _ = check_localization(tiny, tiny_levels, lambda P: occ_oracle(w, P))
+    fine = lv[-1]
     R = 64
     o_rgb, o_depth, o_hit = render.render(fine.values, R, w.col_net, w.occ_map, w.col_map, w.calib)
     depth, rgb, mask = tiny.render(R)

@@ -8,7 +8,7 @@ import pytest
 from oracle import field, localize, metrics, render
 from paper_2007_13988_gb300 import pifu, synth
 
-from gpu_common import COLOUR_TOL, DEPTH_TOL, Ctx, ambiguous_rays
+from gpu_common import Ctx, ambiguous_rays, check_mixed_values, depth_step
 
 pytestmark = pytest.mark.gpu
 
@@ -41,7 +41,7 @@ def full_oracle(full):
                                  w.n0, w.num_levels)
 
 
-def check_against_oracle(c, vol, depth, rgb, mask, levels, R, iou_min, rgb_tol):
+def check_against_oracle(c, vol, depth, rgb, mask, levels, R, iou_min, rgb_tol, steps=1):
     w = c.w
     b, e, v = c.volume_host(vol)
     fine = levels[-1]
@@ -52,19 +52,24 @@ def check_against_oracle(c, vol, depth, rgb, mask, levels, R, iou_min, rgb_tol):
     agree = np.count_nonzero(mask[ok] == o_hit[ok]) / np.count_nonzero(ok)
     assert agree >= 0.999, agree
     both = ok & o_hit & mask
-    assert np.max(np.abs(depth[both] - o_depth[both])) <= DEPTH_TOL * 10
+    derr = float(np.max(np.abs(depth[both] - o_depth[both])))
+    assert derr <= steps * depth_step(vol.n), derr
     d = rgb[both] - o_rgb[both]
     psnr = 10 * np.log10(1.0 / np.mean(d * d))
     assert np.max(np.abs(d)) <= rgb_tol
-    return iou, agree, psnr
+    return iou, agree, psnr, derr
 
 
 def test_graph_frame_mixed_matches_oracle(full, full_oracle):
     vol, depth, rgb, mask = run_frame(full, 512)
-    iou, agree, psnr = check_against_oracle(full, vol, depth, rgb, mask, full_oracle, 512,
-                                            0.999, 0.05)
-    print("graph mixed: IoU %.6f, mask agreement %.6f, colour PSNR %.1f dB, evals %d, rounds %s"
-          % (iou, agree, psnr, vol.n_eval, list(vol.conflict_rounds)[:4]))
+    iou, agree, psnr, derr = check_against_oracle(full, vol, depth, rgb, mask, full_oracle, 512,
+                                                  0.999, 0.05)
+    w = full.w
+    mv = check_mixed_values(full, vol, full_oracle,
+                            lambda P: field.occupancy(w.occ_net, w.occ_map, w.calib, P))
+    print("graph mixed: IoU %.6f, mask agreement %.6f, depth max %.2e, colour PSNR %.1f dB, "
+          "evals %d, rounds %s, %s" % (iou, agree, derr, psnr, vol.n_eval,
+                                       list(vol.conflict_rounds)[:4], mv))
     assert psnr >= 40.0
     # the device-side counters are those of the method: evaluations within
     # the near-0.5 set differences of the oracle's
@@ -81,8 +86,10 @@ def test_graph_frame_relaunch_is_deterministic(full):
 
 
 def test_graph_frame_bf16(full, full_oracle):
+    # no FP32 re-check: a BF16 decision near 0.5 may move a ray's first
+    # inside sample by a node, and its crossing by up to two intervals
     vol, depth, rgb, mask = run_frame(full, 512, precision=pifu.PIFU_PREC_BF16)
-    check_against_oracle(full, vol, depth, rgb, mask, full_oracle, 512, 0.99, 0.05)
+    check_against_oracle(full, vol, depth, rgb, mask, full_oracle, 512, 0.99, 0.05, steps=2)
 
 
 def test_graph_frame_follows_new_inputs(full):

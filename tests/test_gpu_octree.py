@@ -2,23 +2,23 @@
 subdivision) through pifu_localize, against the FP64 oracle's
 octree_binarized / octree_threshold, and the Fig. 3 trade-off at full size.
 
-Rules (plain FP32 form): evaluated values within OCC_TOL; for the threshold
-form, when no decision is ambiguous, also the interpolated values at the
-other nodes (convex combinations of values within OCC_TOL).  Evaluated sets, binarized results and per-level
-counts are identical unless some decision of the oracle is ambiguous: a
-value within NEAR_HALF of 0.5, or (threshold form) a corner deviation within
-DEV_TOL of the threshold; then the differences are bounded."""
+Rules (plain FP32 form, tests/parity_rules.py): evaluated values within
+OCC_TOL; for the threshold form also the interpolated values at the other
+nodes (convex combinations of values within OCC_TOL).  Evaluated sets,
+binarized results and per-level counts are identical at every level to the
+oracle's, where the oracle follows the library's decision wherever its own is
+within rounding: a value within NEAR_HALF of 0.5, or (threshold form) a
+corner deviation within DEV_TOL of the threshold (where the binarized value
+of an interpolated node within NEAR_HALF of 0.5 may also go either way)."""
 import numpy as np
 import pytest
 
 from oracle import field, localize, metrics
 from paper_2007_13988_gb300 import pifu, synth
 
-from gpu_common import NEAR_HALF, OCC_TOL, Ctx
+from gpu_common import Ctx, check_localization
 
 pytestmark = pytest.mark.gpu
-
-DEV_TOL = 4 * OCC_TOL      # a deviation is a difference of two values within OCC_TOL
 
 
 @pytest.fixture(scope="module")
@@ -39,17 +39,6 @@ def oracle_field(w):
     return lambda P: field.occupancy(w.occ_net, w.occ_map, w.calib, P)
 
 
-def ambiguous(levels, threshold=None):
-    """Oracle decisions that FP32 arithmetic may take the other way."""
-    n = 0
-    for l, lv in enumerate(levels):
-        n += int(np.count_nonzero(np.abs(lv.values - 0.5) < NEAR_HALF))
-        if threshold is not None and l > 0:
-            _, dev = localize.corner_mean_deviation(levels[l - 1].values)
-            n += int(np.count_nonzero(np.abs(dev - threshold) < DEV_TOL))
-    return n
-
-
 def gpu_volume(c, vol):
     occ, ev, val = pifu.volume_tensors(vol)
     n, rw = vol.n, vol.row_words
@@ -59,38 +48,17 @@ def gpu_volume(c, vol):
     return b, e, v
 
 
-def compare(c, vol, levels, threshold=None):
-    b, e, v = gpu_volume(c, vol)
-    fine = levels[-1]
-    amb = ambiguous(levels, threshold)
-    both = e & fine.evaluated
-    res = {
-        "ambiguous": amb,
-        "eval_symdiff": int(np.count_nonzero(e ^ fine.evaluated)),
-        "bin_diff": int(np.count_nonzero(b ^ fine.binary)),
-        "evals_gpu": [int(vol.evals_per_level[i]) for i in range(len(levels))],
-        "evals_oracle": [int(l.n_eval) for l in levels],
-        "max_err_evaluated": float(np.max(np.abs(v[both] - fine.values[both]))) if both.any() else 0.0,
-    }
-    if threshold is not None and amb == 0:
-        same = ~(e ^ fine.evaluated)
-        res["max_err_all"] = float(np.max(np.abs(v[same] - fine.values[same])))
-        assert res["max_err_all"] <= OCC_TOL + 1e-6, res
-    assert res["max_err_evaluated"] <= OCC_TOL, res
+def check(c, levels, kind, threshold=None, **kw):
+    res, _, vol = check_localization(c, levels, oracle_field(c.w), kind=kind, threshold=threshold,
+                                     **kw)
     assert all(r == 0 for r in vol.conflict_rounds[:len(levels)])
-    if amb == 0:
-        assert res["eval_symdiff"] == 0 and res["bin_diff"] == 0, res
-        assert res["evals_gpu"] == res["evals_oracle"], res
-    else:
-        assert res["bin_diff"] <= 64 * amb and res["eval_symdiff"] <= 4096 * amb, res
     return res
 
 
 @pytest.mark.parametrize("n0,levels", [(16, 3), (8, 4), (2, 3)])
 def test_binarized_octree_matches_oracle(tiny, n0, levels):
     lv = localize.octree_binarized(oracle_field(tiny.w), n0, levels)
-    vol = tiny.localize(n0=n0, levels=levels, subdivision=pifu.PIFU_SUBDIV_BINARIZED)
-    res = compare(tiny, vol, lv)
+    res = check(tiny, lv, "binarized", n0=n0, levels=levels)
     print("binarized octree %d -> %d: %s" % (n0, n0 << (levels - 1), res))
 
 
@@ -98,21 +66,19 @@ def test_binarized_octree_matches_oracle(tiny, n0, levels):
 def test_threshold_octree_matches_oracle(tiny, threshold):
     w = tiny.w
     lv = localize.octree_threshold(oracle_field(w), w.n0, w.num_levels, threshold)
-    vol = tiny.localize(subdivision=pifu.PIFU_SUBDIV_THRESHOLD, threshold=threshold)
-    res = compare(tiny, vol, lv, threshold)
+    res = check(tiny, lv, "threshold", threshold)
     print("threshold octree thr %.2f: %s" % (threshold, res))
     if threshold == 1.0:           # no deviation of values in [0, 1] exceeds 1
-        assert res["evals_gpu"][1:] == [0] * (w.num_levels - 1)
+        assert res["evals"][0][1:] == [0] * (w.num_levels - 1)
 
 
 def test_octrees_full_shapes_128(full):
     w = full.w
     f = oracle_field(w)
     lv = localize.octree_binarized(f, 32, 3)
-    compare(full, full.localize(n0=32, levels=3, subdivision=pifu.PIFU_SUBDIV_BINARIZED), lv)
+    check(full, lv, "binarized", n0=32, levels=3)
     lv = localize.octree_threshold(f, 32, 3, 0.08)
-    compare(full, full.localize(n0=32, levels=3, subdivision=pifu.PIFU_SUBDIV_THRESHOLD,
-                                threshold=0.08), lv, 0.08)
+    check(full, lv, "threshold", 0.08, n0=32, levels=3)
 
 
 def main_body(b, cell):

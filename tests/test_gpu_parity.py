@@ -7,8 +7,7 @@ import pytest
 from oracle import field, localize, render
 from paper_2007_13988_gb300 import synth
 
-from gpu_common import (COLOUR_TOL, DEPTH_TOL, OCC_TOL, Ctx, ambiguous_rays, compare_volume,
-                        near_half_count)
+from gpu_common import COLOUR_TOL, DEPTH_TOL, OCC_TOL, Ctx, ambiguous_rays, check_localization
 
 pytestmark = pytest.mark.gpu
 
@@ -113,29 +112,25 @@ def tiny_oracle(tiny):
 
 
 def test_localize_tiny_matches_oracle(tiny, tiny_oracle):
-    vol = tiny.localize()
-    b, e, v = tiny.volume_host(vol)
-    res = compare_volume(b, e, v, tiny_oracle, vol)
+    res, _, vol = check_localization(tiny, tiny_oracle, lambda P: occ_oracle(tiny.w, P))
     assert vol.n == 64 and vol.num_levels == 3
-    assert res["max_abs_err"] <= OCC_TOL
+    print("tiny localization:", res)
 
 
 @pytest.mark.parametrize("n0,levels", [(2, 1), (8, 1), (2, 4), (8, 3), (32, 2)])
 def test_localize_tiny_schedules(tiny, n0, levels):
     w = tiny.w
-    lv = localize.hierarchical(lambda P: occ_oracle(w, P), n0, levels)
-    vol = tiny.localize(n0=n0, levels=levels)
-    b, e, v = tiny.volume_host(vol)
-    compare_volume(b, e, v, lv, vol)
+    f = lambda P: occ_oracle(w, P)
+    lv = localize.hierarchical(f, n0, levels)
+    check_localization(tiny, lv, f, n0=n0, levels=levels)
 
 
 def test_localize_tiny_yaw(tiny):
     w = tiny.w
     cal = synth.calib_yaw(30.0)
-    lv = localize.hierarchical(lambda P: occ_oracle(w, P, cal), w.n0, w.num_levels)
-    vol = tiny.localize(calib=cal)
-    b, e, v = tiny.volume_host(vol)
-    compare_volume(b, e, v, lv, vol)
+    f = lambda P: occ_oracle(w, P, cal)
+    lv = localize.hierarchical(f, w.n0, w.num_levels)
+    check_localization(tiny, lv, f, calib=cal)
 
 
 @pytest.fixture(scope="module")
@@ -145,9 +140,7 @@ def full_oracle_128(full):
 
 
 def test_localize_full_shapes_128(full, full_oracle_128):
-    vol = full.localize(n0=32, levels=3)
-    b, e, v = full.volume_host(vol)
-    compare_volume(b, e, v, full_oracle_128, vol)
+    check_localization(full, full_oracle_128, lambda P: occ_oracle(full.w, P), n0=32, levels=3)
 
 
 @pytest.fixture(scope="module")
@@ -158,10 +151,8 @@ def full_oracle_256(full):
 
 def test_localize_full_size_256(full, full_oracle_256):
     # the full-size workload: 32^3 -> 256^3 with the 257-1024-512-256-128-1 MLP
-    vol = full.localize()
+    res, _, vol = check_localization(full, full_oracle_256, lambda P: occ_oracle(full.w, P))
     assert vol.n == 256
-    b, e, v = full.volume_host(vol)
-    res = compare_volume(b, e, v, full_oracle_256, vol)
     print("full-size localization:", res)
 
 
@@ -204,21 +195,25 @@ def check_render(c, levels, R, calib=None, bg=(0.0, 0.0, 0.0)):
             "rgb_err": float(np.max(np.abs(rgb[ok] - o_rgb[ok])))}
 
 
+def localized(c, base):
+    """Localize (checked against the oracle) and return the oracle's levels
+    that follow the library's side of 0.5 at near-0.5 nodes."""
+    _, lv, _ = check_localization(c, base, lambda P: occ_oracle(c.w, P))
+    return lv
+
+
 def test_render_tiny(tiny, tiny_oracle):
-    tiny.localize()
-    res = check_render(tiny, tiny_oracle, 64, bg=(0.25, 0.5, 0.75))
+    res = check_render(tiny, localized(tiny, tiny_oracle), 64, bg=(0.25, 0.5, 0.75))
     print("tiny render:", res)
 
 
 @pytest.mark.parametrize("R", [32, 96, 128])
 def test_render_tiny_other_sizes(tiny, tiny_oracle, R):
-    tiny.localize()
-    check_render(tiny, tiny_oracle, R)
+    check_render(tiny, localized(tiny, tiny_oracle), R)
 
 
 def test_render_full_size_512(full, full_oracle_256):
-    full.localize()
-    res = check_render(full, full_oracle_256, 512)
+    res = check_render(full, localized(full, full_oracle_256), 512)
     print("full render:", res)
 
 
