@@ -48,10 +48,10 @@ def gpu_volume(c, vol):
     return b, e, v
 
 
-def check(c, levels, kind, threshold=None, **kw):
-    res, _, vol = check_localization(c, levels, oracle_field(c.w), kind=kind, threshold=threshold,
+def check(c, base, kind, threshold=None, **kw):
+    res, _, vol = check_localization(c, base, oracle_field(c.w), kind=kind, threshold=threshold,
                                      **kw)
-    assert all(r == 0 for r in vol.conflict_rounds[:len(levels)])
+    assert all(r == 0 for r in vol.conflict_rounds[:len(base)])
     return res
 
 

@@ -113,14 +113,14 @@ def test_stream_batch_mixed_matches_oracle(ctx, frames, oracle_frames):
 
 @pytest.fixture(scope="module")
 def fp8_surrogate(ctx, frames):
-    """FP8 scales from the first frame, and a surrogate distilled as the bench
-    does it (fewer tuples and steps)."""
+    """FP8 scales from the first frame, and a surrogate distilled as the
+    surrogate tests do it."""
     w = ctx.w
     pifu.pifu_calibrate_fp8(ctx.ctx, frames[0]["occ"], w.calib, w.n0)
-    x, y = distill.build_samples(ctx.ctx, n_figures=8, per_figure=150000, seed0=1000)
-    distill.train(ctx.ctx, x, y, steps=3000, batch=4096, lr=3e-3)
-    margin, _ = distill.calibrate_margin(ctx.ctx, seeds=[2000, 2001], per_figure=100000,
-                                         quantile=0.999)
+    x, y = distill.build_samples(ctx.ctx, n_figures=12, per_figure=200000, seed0=1000)
+    distill.train(ctx.ctx, x, y, steps=4000, batch=4096, lr=3e-3)
+    margin, _ = distill.calibrate_margin(ctx.ctx, seeds=[2000, 2001], per_figure=100000)
+    assert margin < 0.5     # the surrogate decides some points itself
     return margin
 
 
