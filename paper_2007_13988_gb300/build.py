@@ -19,9 +19,9 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libpifu.so")
 
-SOURCES = ["pifu_api.cu", "gather.cu", "mlp_f32.cu", "mlp_tc.cu", "localize.cu", "render.cu",
-           "query_noalloc.cu", "train.cu", "mlp_fused.cu", "cbn.cu",
-           "cbn_tc.cu", "mlp_chain.cu"]
+SOURCES = ["pifu_api.cu", "ctx.cu", "mlp_run.cu", "graph.cu", "batch.cu", "tune.cu",
+           "surrogate_api.cu", "gather.cu", "mlp_f32.cu", "mlp_tc.cu", "localize.cu", "render.cu",
+           "query_noalloc.cu", "train.cu", "mlp_fused.cu", "cbn.cu", "cbn_tc.cu", "mlp_chain.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
                 "-I" + INCLUDE, "-I" + CSRC]
@@ -65,7 +65,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
             print(r.stdout + r.stderr)
         return obj
 
-    with cf.ThreadPoolExecutor(max_workers=min(8, len(SOURCES))) as ex:
+    with cf.ThreadPoolExecutor(max_workers=min(os.cpu_count() or 8, len(SOURCES))) as ex:
         objs = list(ex.map(compile_one, SOURCES))
     tmp = LIB + ".tmp"
     r = subprocess.run([cc, *ARCH, "-shared", "-o", tmp, *objs], capture_output=True, text=True)
