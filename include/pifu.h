@@ -293,6 +293,62 @@ int pifu_frames(pifu_ctx* ctx, int B, const pifu_fmap* occ_maps, const pifu_fmap
                 void* stream, float* depth_dev, float* rgb_dev, uint8_t* mask_dev,
                 pifu_volume* out);
 
+/* ---- Stream of frames through a device work queue (not in the paper) ---------
+ * Localization + render of F independent frames (1 <= F <= 4096), held in
+ * `slots` concurrent frame slots (1 <= slots <= 16, slots x width x height
+ * <= 2^22), in ONE graph launch.  On the device the graph loops over rounds;
+ * in each round every slot takes one step of the method (Sec. 3.2) for the
+ * frame it holds: a frame taken from the queue evaluates its dense level 0;
+ * a level whose frontier is empty advances to the next level (binarize,
+ * interpolate, candidates, their 26-ring) or, at the finest level, to the
+ * render (Eq. 3) and colour (Eq. 2) of the frame, after which the slot takes
+ * the next frame of the queue; otherwise the level runs its next conflict
+ * round.  All slots' points of a round -- whatever level each slot is at --
+ * go through one gather and one persistent tensor-core launch per MLP layer.
+ * So every frame makes the decisions, and runs the conflict rounds, it makes
+ * alone (its binarized volume and evaluated set equal pifu_frame's), and a
+ * frame that needs few rounds does not wait for the slowest one.
+ *   occ_maps[f], col_maps[f]  frame f's maps (device; one shape and type for
+ *                             all f; col_maps may be null)
+ *   calibs                    F x 12 floats (host)
+ *   depth_dev, rgb_dev, mask_dev  [F][height][width] (rgb x3) device
+ *                             outputs, each may be null
+ *   occ_bits_dev              optional [F][(n+1)^2 row_words] words: each
+ *                             frame's binarized finest level (the bitset
+ *                             layout of pifu_volume)
+ *   out                       F volumes (may be null): per-level evaluation
+ *                             and candidate counts and conflict rounds of
+ *                             each frame; rechecked_per_level[0] and
+ *                             fallback_per_level[0] hold the stream's
+ *                             totals; the bitset and value views show the
+ *                             last frame each slot held (valid until the
+ *                             next pifu_stream) and are null for the others
+ *   times                     F entries (may be null): when each frame was
+ *                             taken from the queue and when its render
+ *                             ended, in ms after the first frame was taken
+ *                             (device clock), the slot that held it and the
+ *                             rounds the whole stream ran
+ * The graph is captured per argument set (F, slots, the maps' shapes and
+ * types, levels, camera, output pointers); the map pointers and calibrations
+ * are read on the device, so later calls with new maps relaunch it.
+ * Synchronises `stream` once.  Precisions as pifu_frame; the CBN + SoftZ
+ * network and final_level 1 return PIFU_ERR_UNSUPPORTED.  Errors:
+ * PIFU_ERR_ARG, PIFU_ERR_CAPACITY (a round's points beyond the key list,
+ * max(2^20, slots x 2^18) rounded up to a power of two), PIFU_ERR_NOT_CONVERGED
+ * (a level over max_rounds), PIFU_ERR_STATE, PIFU_ERR_OOM, PIFU_ERR_CUDA. */
+typedef struct {
+    float admit_ms;          /* taken from the queue, after the first frame was  */
+    float done_ms;           /* render finished, after the first frame was taken */
+    int32_t slot;            /* the slot that held the frame                     */
+    int32_t stream_rounds;   /* rounds the whole stream ran (same for all)        */
+} pifu_frame_time;
+
+int pifu_stream(pifu_ctx* ctx, int F, const pifu_fmap* occ_maps, const pifu_fmap* col_maps,
+                const float* calibs, int slots, const pifu_levels* levels,
+                const pifu_camera* cam, void* stream, float* depth_dev, float* rgb_dev,
+                uint8_t* mask_dev, uint32_t* occ_bits_dev, pifu_volume* out,
+                pifu_frame_time* times);
+
 /* ---- Tile autotuner (not in the paper) ----------------------------------------
  * Times every tensor-core hidden layer of f_O and f_T (and of f_O's E4M3
  * layers once calibrated) on a batch of `rows` points (128 .. 2^22) with each

@@ -267,11 +267,13 @@ int ensure_mlp_ws(pifu_ctx* ctx) {
         need_h = std::max<int64_t>(need_h, std::max(n.max_hidden, 8));
     }
     if (need_x > ctx->X_cap) {   // per-point widths; FP32 rows are kChunk points
+        invalidate_graphs(ctx);
         dev_free(ctx->X);
         CK(dev_alloc(&ctx->X, need_x * kChunk));
         ctx->X_cap = need_x;
     }
     if (need_h > ctx->H_cap) {
+        invalidate_graphs(ctx);
         dev_free(ctx->HA);
         dev_free(ctx->HB);
         CK(dev_alloc(&ctx->HA, need_h * kChunk));
@@ -287,6 +289,7 @@ int ensure_mlp_ws(pifu_ctx* ctx) {
                                                    std::max<int64_t>(kSplitMaxM, kRecheckCap) *
                                                    L.n_out);
     if (need_p > ctx->part_cap) {
+        invalidate_graphs(ctx);
         dev_free(ctx->part);
         CK(dev_alloc(&ctx->part, need_p));
         ctx->part_cap = need_p;
@@ -377,7 +380,7 @@ int ensure_tc_rows(pifu_ctx* ctx, int64_t rows) {
         need_x = std::max<int64_t>(need_x, n.ldx);
         need_h = std::max<int64_t>(need_h, std::max(n.max_hidden, 8));
     }
-    ctx->g_valid = false;
+    invalidate_graphs(ctx);
     dev_free(ctx->Xb);
     dev_free(ctx->Hb[0]);
     dev_free(ctx->Hb[1]);
@@ -513,6 +516,7 @@ int calibrate_fp8(pifu_ctx* ctx, const Map& map, const Calib& cal, int n0, cudaS
     int st0 = ensure_tc_rows(ctx, 1);
     if (st0 != PIFU_OK) return st0;
     if (!ctx->X8 || ctx->ldx8 != 2 * kx8) {
+        invalidate_graphs(ctx);
         dev_free(ctx->X8);
         ctx->ldx8 = ctx->kx8 = 0;
         CK(dev_alloc(&ctx->X8, (int64_t)2 * kx8 * ctx->tc_rows));
@@ -564,6 +568,7 @@ int calibrate_fp8(pifu_ctx* ctx, const Map& map, const Calib& cal, int n0, cudaS
 
 int ensure_level_ws(pifu_ctx* ctx, int N) {
     if (N <= ctx->ws_N) return PIFU_OK;
+    invalidate_graphs(ctx);
     uint32_t** bitsets[] = {&ctx->cand, &ctx->tent, &ctx->bin[0], &ctx->bin[1],
                             &ctx->eval, &ctx->conf[0], &ctx->conf[1]};
     for (auto b : bitsets) dev_free(*b);
@@ -595,6 +600,7 @@ int ensure_level_ws(pifu_ctx* ctx, int N) {
 
 int ensure_prev_values(pifu_ctx* ctx, int64_t n) {
     if (n <= ctx->prev_cap) return PIFU_OK;
+    invalidate_graphs(ctx);
     dev_free(ctx->prev_values);
     ctx->prev_cap = 0;
     CK(dev_alloc(&ctx->prev_values, n));
@@ -604,6 +610,7 @@ int ensure_prev_values(pifu_ctx* ctx, int64_t n) {
 
 int ensure_hit_ws(pifu_ctx* ctx, int64_t npix) {
     if (npix <= ctx->hit_cap) return PIFU_OK;
+    invalidate_graphs(ctx);
     dev_free(ctx->hit_xyz);
     dev_free(ctx->hit_pix);
     ctx->hit_cap = 0;

@@ -21,7 +21,13 @@ __device__ __forceinline__ void last_epilogue(const Epilogue& epi, int64_t p, in
     if (epi.recheck) {
         // mixed precision: defer occupancies close to the decision threshold
         const float o = apply_act(ACT_SIGMOID, t[0] + bias[0]);
-        if (fabsf(o - kHalf) < epi.margin) {
+        bool defer = fabsf(o - kHalf) < epi.margin;
+        if (!defer && epi.finest_to_queue && epi.mode == EPI_LEVEL && epi.lv.sv) {
+            // frame stream, surrogate pass: a slot at its finest level runs f_O
+            const int64_t key = epi.list ? (int64_t)epi.list[p] : epi.base + p;
+            defer = epi.lv.sv[key / epi.lv.key_div].finest != 0;
+        }
+        if (defer) {
             const unsigned pos = atomicAdd(epi.recheck_count, 1u);
             epi.recheck[pos] = (epi.mode == EPI_LEVEL || epi.mode == EPI_COLUMN)
                                    ? (epi.list ? epi.list[p] : (int)(epi.base + p))
@@ -50,22 +56,34 @@ __device__ __forceinline__ void last_epilogue(const Epilogue& epi, int64_t p, in
         const uint32_t* tent = lv.tent;
         uint32_t* bin = lv.bin;
         uint32_t* conf = lv.conf;
+        int N = lv.N, row_words = lv.row_words, first_level = lv.first_level;
         if (lv.key_div) {   // several frames: key = frame * key_div + node
             const int64_t f = idx / lv.key_div;
             idx -= f * lv.key_div;
-            values += f * lv.slot_nodes;
-            tent += f * lv.slot_words;
-            bin += f * lv.slot_words;
-            conf += f * lv.slot_words;
+            if (lv.sv) {    // frame stream: the slot's arrays and level
+                const SlotView& v = lv.sv[f];
+                values = v.values;
+                tent = v.tent;
+                bin = v.bin;
+                conf = v.conf;
+                N = v.N;
+                row_words = row_words_of(N);
+                first_level = v.first_level;
+            } else {
+                values += f * lv.slot_nodes;
+                tent += f * lv.slot_words;
+                bin += f * lv.slot_words;
+                conf += f * lv.slot_words;
+            }
         }
         values[idx] = o;
-        const int64_t n1 = lv.N + 1;
+        const int64_t n1 = N + 1;
         const int64_t row = idx / n1;            // k (N+1) + j
         const int i = (int)(idx - row * n1);
-        const int64_t w = row * lv.row_words + (i >> 5);
+        const int64_t w = row * row_words + (i >> 5);
         const uint32_t bit = 1u << (i & 31);
         const bool ob = o >= kHalf;
-        if (lv.first_level) {
+        if (first_level) {
             if (ob) atomicOr(&bin[w], bit);
         } else {
             const bool tb = (tent[w] & bit) != 0u;

@@ -85,18 +85,20 @@ __device__ __forceinline__ int point_xyz(const PointSrc& src, int64_t p, float& 
     }
     uint32_t idx = (src.mode == PTS_LIST) ? (uint32_t)src.list[p] : (uint32_t)(src.base + p);
     int f = 0;
+    int N = src.N;
     if (src.maps0) {
         const uint32_t sd = (uint32_t)src.slot_div;
         f = (int)(idx / sd);
         idx -= (uint32_t)f * sd;
+        if (src.sv) N = src.sv[f].N;   // frame stream: the slot's level
     }
-    const uint32_t n1 = (uint32_t)src.N + 1u;
+    const uint32_t n1 = (uint32_t)N + 1u;
     const uint32_t row = idx / n1;             // k (N + 1) + j
     const int i = (int)(idx - row * n1);
     const uint32_t kk = row / n1;
     const int j = (int)(row - kk * n1);
     const int k = (int)kk;
-    const float h = 2.0f / (float)src.N;   // exact for power-of-two N
+    const float h = 2.0f / (float)N;   // exact for power-of-two N
     x = __fmaf_rn((float)i, h, -1.0f);
     y = __fmaf_rn((float)j, h, -1.0f);
     z = __fmaf_rn((float)k, h, -1.0f);

@@ -64,6 +64,7 @@ int g_eval(pifu_ctx* ctx, const DevNet& net, const PointSrc& src, int64_t cap,
         es.recheck = ctx->squeue;
         es.recheck_count = ctx->d_squeue;
         es.margin = sur_margin;
+        es.finest_to_queue = 1;   // frame stream: a slot at its finest level runs f_O
         int st = run_mlp_tc(ctx, ctx->snet, src, cap, map, Map{}, cal, es, s, m_dev);
         if (st != PIFU_OK) return st;
         // a queue longer than one device-sized batch latches a capacity error

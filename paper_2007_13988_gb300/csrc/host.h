@@ -290,6 +290,74 @@ struct BatchWs {
 using namespace pifu;
 using namespace pifu_host;
 
+namespace pifu_host {
+
+// Everything a captured stream graph depends on besides the frames' map
+// pointers and calibrations (read on the device).
+struct StreamKey {
+    int F, S;
+    int oH, oW, oC, odt, cH, cW, cC, cdt;
+    int n0, num_levels, precision, max_rounds;
+    float margin;
+    int use_surrogate;
+    float sur_margin;
+    uint64_t sur_version;
+    uint64_t f8_version;
+    int width, height;
+    float bg[3];
+    float* depth;
+    float* rgb;
+    uint8_t* mask;
+    uint32_t* bits_out;
+};
+
+// Work-queue stream of frames (pifu_stream): S slots of the finest level's
+// size, the frames' inputs and results, and the graph.
+struct StreamWs {
+    int S = 0, N = 0, F = 0;           // allocated for S slots, finest N, F frames
+    int64_t npix = 0;
+    int64_t slot_words = 0, slot_nodes = 0, slot_top = 0, cap = 0;
+    uint32_t* cand = nullptr;
+    uint32_t* tent = nullptr;
+    uint32_t* bin[2] = {nullptr, nullptr};
+    uint32_t* eval = nullptr;
+    uint32_t* conf = nullptr;
+    float* values = nullptr;
+    int* top = nullptr;
+    int* list = nullptr;               // [cap] keys slot * slot_nodes + node
+    int* recheck = nullptr;            // [cap]
+    int* squeue = nullptr;             // [cap]
+    float* hit_xyz = nullptr;          // [S npix][3]
+    int* hit_pix = nullptr;            // [S npix] keys frame * npix + pixel
+    unsigned int* d_hits = nullptr;
+    SlotView* sv = nullptr;            // [S]
+    StreamSlot* st = nullptr;          // [S]
+    unsigned int* pend = nullptr;      // [2 S]: keys in the round's evaluation, keys queued next
+    unsigned long long* cands = nullptr;   // [S]
+    Map* slot_maps0 = nullptr;         // [S]
+    Map* slot_maps1 = nullptr;
+    Calib* slot_calibs = nullptr;
+    Map* frame_maps0 = nullptr;        // [F] device
+    Map* frame_maps1 = nullptr;
+    Calib* frame_calibs = nullptr;
+    Map* h_maps0 = nullptr;            // [F] pinned staging
+    Map* h_maps1 = nullptr;
+    Calib* h_calibs = nullptr;
+    StreamFrameStats* d_fs = nullptr;  // [F]
+    StreamFrameStats* h_fs = nullptr;  // pinned
+    StreamCtl* d_ctl = nullptr;
+    StreamCtl* h_ctl = nullptr;        // pinned
+    bool g_valid = false;
+    StreamKey key{};
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int64_t launches_fixed = 0;
+    int64_t launches_body = 0;
+    int64_t launches_colour = 0;
+};
+
+}  // namespace pifu_host
+
 struct pifu_ctx {
     int device = 0;
     DevNet net[2];
@@ -397,10 +465,21 @@ struct pifu_ctx {
     int64_t g_launches_body[8] = {};      // kernel launches per loop iteration
     // lockstep frame batches (pifu_frames)
     BatchWs batch;
+    // work-queue stream of frames (pifu_stream)
+    StreamWs stream;
 };
 
 namespace pifu_host {
 
+
+// Every captured graph (frame, lockstep batch, stream) holds the addresses
+// of the workspaces it was captured with: a workspace that moves makes them
+// invalid, and the next call recaptures.
+inline void invalidate_graphs(pifu_ctx* ctx) {
+    ctx->g_valid = false;
+    ctx->batch.g_valid = false;
+    ctx->stream.g_valid = false;
+}
 
 struct DeviceGuard {
     int prev = -1;
@@ -586,5 +665,6 @@ int tune_layer(pifu_ctx* ctx, const TcLayerArgs& base, int n_out, bool fp8, bool
 int autotune(pifu_ctx* ctx, int64_t rows, cudaStream_t s, int32_t* bn_out, double* ms_out,
              int n_max, int* n_done);
 int set_tiles(pifu_ctx* ctx, const int32_t* codes, int n);
+void stream_free(pifu_ctx* ctx);
 
 }  // namespace pifu_host

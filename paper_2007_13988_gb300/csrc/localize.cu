@@ -14,6 +14,8 @@
 // Several frames in lockstep: blockIdx.y is the frame; its bitsets start
 // `fslot` words (coarse: `cslot`) further, and the node keys it appends are
 // frame * slot_nodes + node, into one list for all frames.
+#include <algorithm>
+
 #include "pifu_internal.h"
 
 namespace pifu {
@@ -47,30 +49,14 @@ __device__ __forceinline__ uint32_t spread16(uint32_t x) {
 // Tentative value of a fine node = tri-linear interpolation of the binarized
 // coarse level = mean of its 1, 2, 4 or 8 coarse corners (a fine index i sits
 // on coarse node i/2 when even, between (i-1)/2 and (i+1)/2 when odd).
-// cand: 0 < mean < 1.  tent: mean >= 1/2.
-__global__ void __launch_bounds__(256) classify_kernel(const uint32_t* __restrict__ coarse, int N,
-                                                       uint32_t* __restrict__ cand,
-                                                       uint32_t* __restrict__ tent,
-                                                       uint32_t* __restrict__ bin,
-                                                       uint32_t* __restrict__ eval,
-                                                       uint32_t* __restrict__ conf0,
-                                                       int64_t cslot, int64_t fslot) {
-    {
-        const int64_t f = blockIdx.y;
-        coarse += f * cslot;
-        cand += f * fslot;
-        tent += f * fslot;
-        bin += f * fslot;
-        eval += f * fslot;
-        conf0 += f * fslot;
-    }
+// cand: 0 < mean < 1.  tent: mean >= 1/2.  For bitset word w of an N-cell
+// level (w below words_of(N)).
+__device__ __forceinline__ void classify_word(const uint32_t* __restrict__ coarse, int N, int64_t w,
+                                              uint32_t& c_word, uint32_t& t_word) {
     const int n1 = N + 1;
     const int rw = row_words_of(N);
     const int Nc = N / 2;
     const int rwc = row_words_of(Nc);
-    const int64_t total = (int64_t)n1 * n1 * rw;
-    const int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (w >= total) return;
     const int wx = (int)(w % rw);
     const int64_t rowid = w / rw;
     const int j = (int)(rowid % n1);
@@ -118,8 +104,30 @@ __global__ void __launch_bounds__(256) classify_kernel(const uint32_t* __restric
     const uint32_t t_even = nrows == 4 ? ge2 : ge1;                      // cnt >= ceil(nrows / 2)
     const uint32_t t_odd = nrows == 1 ? ge1 : (nrows == 2 ? ge2 : ge4);   // cnt >= nrows
     const uint32_t vm = valid_mask(N, wx);
-    const uint32_t c_word = any & ~all & vm;
-    const uint32_t t_word = ((t_even & EV) | (t_odd & OD)) & vm;
+    c_word = any & ~all & vm;
+    t_word = ((t_even & EV) | (t_odd & OD)) & vm;
+}
+
+__global__ void __launch_bounds__(256) classify_kernel(const uint32_t* __restrict__ coarse, int N,
+                                                       uint32_t* __restrict__ cand,
+                                                       uint32_t* __restrict__ tent,
+                                                       uint32_t* __restrict__ bin,
+                                                       uint32_t* __restrict__ eval,
+                                                       uint32_t* __restrict__ conf0,
+                                                       int64_t cslot, int64_t fslot) {
+    {
+        const int64_t f = blockIdx.y;
+        coarse += f * cslot;
+        cand += f * fslot;
+        tent += f * fslot;
+        bin += f * fslot;
+        eval += f * fslot;
+        conf0 += f * fslot;
+    }
+    const int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= words_of(N)) return;
+    uint32_t c_word, t_word;
+    classify_word(coarse, N, w, c_word, t_word);
     cand[w] = c_word;
     tent[w] = t_word;
     bin[w] = t_word;
@@ -143,6 +151,32 @@ __global__ void __launch_bounds__(256) dense_setup_kernel(int N, uint32_t* __res
     bin[w] = 0u;
     conf0[w] = 0u;
     eval[w] = valid_mask(N, (int)((w - (int64_t)blockIdx.y * fslot) % rw));
+}
+
+// Word w of dilate26(src), restricted to the grid: the OR of the nine node
+// rows around it, each with its bits shifted by -1, 0 and +1.
+__device__ __forceinline__ uint32_t dilate_word(const uint32_t* __restrict__ src, int N, int64_t w) {
+    const int n1 = N + 1;
+    const int rw = row_words_of(N);
+    const int wx = (int)(w % rw);
+    const int64_t row = w / rw;
+    const int j = (int)(row % n1);
+    const int k = (int)(row / n1);
+    uint32_t acc = 0u;
+    for (int dk = -1; dk <= 1; ++dk) {
+        const int kk = k + dk;
+        if (kk < 0 || kk > N) continue;
+        for (int dj = -1; dj <= 1; ++dj) {
+            const int jj = j + dj;
+            if (jj < 0 || jj > N) continue;
+            const uint32_t* r = src + ((int64_t)kk * n1 + jj) * rw;
+            const uint32_t c = r[wx];
+            const uint32_t l = wx > 0 ? r[wx - 1] : 0u;
+            const uint32_t h = wx + 1 < rw ? r[wx + 1] : 0u;
+            acc |= c | (c << 1) | (c >> 1) | (l >> 31) | (h << 31);
+        }
+    }
+    return acc & valid_mask(N, wx);
 }
 
 // sel = dilate26(src) & ~eval, restricted to the grid; eval |= sel; compact.
@@ -171,23 +205,7 @@ __global__ void __launch_bounds__(256) dilate_select_kernel(const uint32_t* __re
     if (w < total) {
         wx = (int)(w % rw);
         row = w / rw;
-        const int j = (int)(row % n1);
-        const int k = (int)(row / n1);
-        uint32_t acc = radius ? 0u : src[w];
-        for (int dk = -radius; dk <= radius; ++dk) {
-            const int kk = k + dk;
-            if (kk < 0 || kk > N) continue;
-            for (int dj = -1; dj <= 1 && radius; ++dj) {
-                const int jj = j + dj;
-                if (jj < 0 || jj > N) continue;
-                const uint32_t* r = src + ((int64_t)kk * n1 + jj) * rw;
-                const uint32_t c = r[wx];
-                const uint32_t l = wx > 0 ? r[wx - 1] : 0u;
-                const uint32_t h = wx + 1 < rw ? r[wx + 1] : 0u;
-                acc |= c | (c << 1) | (c >> 1) | (l >> 31) | (h << 31);
-            }
-        }
-        acc &= valid_mask(N, wx);
+        const uint32_t acc = radius ? dilate_word(src, N, w) : src[w] & valid_mask(N, wx);
         const uint32_t e = eval[w];
         sel = acc & ~e;
         if (sel) eval[w] = e | sel;
@@ -316,14 +334,15 @@ __global__ void loop_control_kernel(cudaGraphConditionalHandle h, const unsigned
 }
 
 // One thread per (conflict, neighbour) pair; warp-aggregated append.
+// Frame stream (sv set): a key's slot gives the level and the evaluated
+// bitset, and slot_count[slot] counts the keys appended for it.
 __global__ void __launch_bounds__(256) expand_conflicts_kernel(
     const int* __restrict__ clist, const unsigned int* __restrict__ ccount, unsigned int max_c,
-    int N, uint32_t* __restrict__ eval, int64_t key_div, int64_t slot_words,
+    int N0, uint32_t* __restrict__ eval0, int64_t key_div, int64_t slot_words,
     int* __restrict__ list, unsigned int* __restrict__ count, unsigned int cap,
-    unsigned int* __restrict__ err) {
+    unsigned int* __restrict__ err, const SlotView* __restrict__ sv,
+    unsigned int* __restrict__ slot_count) {
     const unsigned int nc = min(*ccount, max_c);
-    const int n1 = N + 1;
-    const int rw = row_words_of(N);
     const int lane = threadIdx.x & 31;
     const int64_t total = (int64_t)nc * 26;
     // whole warps iterate together (ballots below)
@@ -343,19 +362,28 @@ __global__ void __launch_bounds__(256) expand_conflicts_kernel(
                 f = key / key_div;
                 key -= f * key_div;
             }
+            int N = N0;
+            uint32_t* eval = eval0 + f * slot_words;
+            if (sv) {
+                N = sv[f].N;
+                eval = sv[f].eval;
+            }
+            const int n1 = N + 1;
+            const int rw = row_words_of(N);
             const int64_t row = key / n1;           // k (N+1) + j
             const int i = (int)(key - row * n1) + dx;
             const int j = (int)(row % n1) + dy;
             const int k = (int)(row / n1) + dz;
             if (i >= 0 && i <= N && j >= 0 && j <= N && k >= 0 && k <= N) {
                 const int64_t r2 = (int64_t)k * n1 + j;
-                uint32_t* wptr = eval + f * slot_words + r2 * rw + (i >> 5);
+                uint32_t* wptr = eval + r2 * rw + (i >> 5);
                 const uint32_t bit = 1u << (i & 31);
                 if (!(*wptr & bit)) {
                     const uint32_t old = atomicOr(wptr, bit);
                     fresh = !(old & bit);
                 }
                 nkey = f * (key_div ? key_div : 0) + r2 * n1 + i;
+                if (fresh && slot_count) atomicAdd(slot_count + f, 1u);
             }
         }
         const unsigned ballot = __ballot_sync(0xffffffffu, fresh);
@@ -369,6 +397,101 @@ __global__ void __launch_bounds__(256) expand_conflicts_kernel(
             else atomicOr(err, kErrCapacity);
         }
     }
+}
+
+// ---- frame stream: the set-up and selection of every slot in one launch each ----
+//
+// Grid (x: enough blocks for the finest level's words, striding; y: slot).
+// A slot whose round op is START gets level 0 set up (every node evaluated,
+// nothing else set); ADVANCE runs the classify step from its coarser level.
+
+__global__ void __launch_bounds__(256) stream_setup_kernel(const SlotView* __restrict__ sv) {
+    const SlotView v = sv[blockIdx.y];
+    if (v.op != SLOT_START && v.op != SLOT_ADVANCE) return;
+    const int N = v.N;
+    const int rw = row_words_of(N);
+    const int64_t total = words_of(N);
+    for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < total;
+         w += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t c_word = 0u, t_word = 0u, e_word = 0u;
+        if (v.op == SLOT_START)
+            e_word = valid_mask(N, (int)(w % rw));
+        else
+            classify_word(v.coarse, N, w, c_word, t_word);
+        v.cand[w] = c_word;
+        v.tent[w] = t_word;
+        v.bin[w] = t_word;
+        v.eval[w] = e_word;
+        v.conf[w] = 0u;
+    }
+}
+
+// Queues the nodes a slot evaluates first in its new level, as keys
+// slot * slot_nodes + node appended at *count (beyond cap the error word gets
+// kErrCapacity): START every node of level 0; ADVANCE the 26-ring of the
+// boundary candidates (dilate26(cand) & ~eval, then eval |= it), whose number
+// goes to cands[slot].  pend[slot] += the keys queued for the slot.
+__global__ void __launch_bounds__(256) stream_select_kernel(
+    const SlotView* __restrict__ sv, int64_t slot_nodes, int* __restrict__ list,
+    unsigned int* __restrict__ count, unsigned int cap, unsigned int* __restrict__ err,
+    unsigned int* __restrict__ pend, unsigned long long* __restrict__ cands) {
+    const int slot = blockIdx.y;
+    const SlotView v = sv[slot];
+    if (v.op != SLOT_START && v.op != SLOT_ADVANCE) return;
+    const int N = v.N;
+    const int n1 = N + 1;
+    const int rw = row_words_of(N);
+    const int64_t total = words_of(N);
+    const int lane = threadIdx.x & 31;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    unsigned long long ncand = 0;
+    // whole warps iterate together (shuffles below)
+    for (int64_t base_w = (int64_t)blockIdx.x * blockDim.x; base_w < total; base_w += stride) {
+        const int64_t w = base_w + threadIdx.x;
+        uint32_t sel = 0u;
+        int64_t node0 = 0;
+        if (w < total) {
+            const int wx = (int)(w % rw);
+            node0 = (w / rw) * n1 + (int64_t)wx * 32;
+            if (v.op == SLOT_START) {
+                sel = valid_mask(N, wx);   // level-0 set-up marked them evaluated
+            } else {
+                ncand += __popc(v.cand[w]);
+                const uint32_t e = v.eval[w];
+                sel = dilate_word(v.cand, N, w) & ~e;
+                if (sel) v.eval[w] = e | sel;
+            }
+        }
+        const int n = __popc(sel);
+        int incl = n;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        const int warp_total = __shfl_sync(0xffffffffu, incl, 31);
+        unsigned int base = 0u;
+        if (lane == 31 && warp_total > 0) {
+            base = atomicAdd(count, (unsigned int)warp_total);
+            atomicAdd(pend + slot, (unsigned int)warp_total);
+        }
+        base = __shfl_sync(0xffffffffu, base, 31);
+        if (n) {
+            unsigned int pos = base + (unsigned int)(incl - n);
+            const int64_t key0 = node0 + (int64_t)slot * slot_nodes;
+            uint32_t s = sel;
+            while (s) {
+                const int b = __ffs(s) - 1;
+                s &= s - 1u;
+                if (pos < cap) list[pos] = (int)(key0 + b);
+                else atomicOr(err, kErrCapacity);
+                ++pos;
+            }
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) ncand += __shfl_xor_sync(0xffffffffu, ncand, o);
+    if (lane == 0 && ncand) atomicAdd(cands + slot, ncand);
 }
 
 // Graph form: picks one of two conditional branches from a device-resident
@@ -446,12 +569,32 @@ cudaError_t launch_loop_control(cudaGraphConditionalHandle h, const unsigned int
 cudaError_t launch_expand_conflicts(const int* clist, const unsigned int* ccount,
                                     unsigned int max_c, int N, uint32_t* eval, int64_t key_div,
                                     int64_t slot_words, int* list, unsigned int* count,
-                                    unsigned int cap, unsigned int* err, cudaStream_t stream) {
+                                    unsigned int cap, unsigned int* err, cudaStream_t stream,
+                                    const SlotView* sv, unsigned int* slot_count) {
     if (max_c == 0) return cudaSuccess;
     const int64_t total = (int64_t)max_c * 26;
     const int64_t blocks = std::min<int64_t>((total + 255) / 256, 152 * 8);
     expand_conflicts_kernel<<<(unsigned)blocks, 256, 0, stream>>>(
-        clist, ccount, max_c, N, eval, key_div, slot_words, list, count, cap, err);
+        clist, ccount, max_c, N, eval, key_div, slot_words, list, count, cap, err, sv,
+        slot_count);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_stream_setup(const SlotView* sv, int slots, int N_fine, cudaStream_t stream) {
+    if (slots < 1 || slots > 65535) return cudaErrorInvalidValue;
+    const unsigned gx = (unsigned)std::min<int64_t>(blocks_for(words_of(N_fine)), 152 * 2);
+    stream_setup_kernel<<<dim3(gx, (unsigned)slots), 256, 0, stream>>>(sv);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_stream_select(const SlotView* sv, int slots, int N_fine, int64_t slot_nodes,
+                                 int* list, unsigned int* count, unsigned int cap,
+                                 unsigned int* err, unsigned int* pend,
+                                 unsigned long long* cands, cudaStream_t stream) {
+    if (slots < 1 || slots > 65535) return cudaErrorInvalidValue;
+    const unsigned gx = (unsigned)std::min<int64_t>(blocks_for(words_of(N_fine)), 152 * 2);
+    stream_select_kernel<<<dim3(gx, (unsigned)slots), 256, 0, stream>>>(
+        sv, slot_nodes, list, count, cap, err, pend, cands);
     return cudaGetLastError();
 }
 

@@ -384,12 +384,14 @@ int ensure_cull_ws(pifu_ctx* ctx, int64_t npix, int Nc) {
     const int64_t cap = npix * 16;
     const int64_t vals = npix * (2 * (int64_t)Nc + 1);
     if (cap > ctx->cull_cap) {
+        invalidate_graphs(ctx);
         dev_free(ctx->cull_list);
         ctx->cull_cap = 0;
         CK(dev_alloc(&ctx->cull_list, cap));
         ctx->cull_cap = cap;
     }
     if (vals > ctx->cull_vals_cap) {
+        invalidate_graphs(ctx);
         dev_free(ctx->cull_values);
         ctx->cull_vals_cap = 0;
         CK(dev_alloc(&ctx->cull_values, vals));
@@ -413,6 +415,7 @@ int eval_batch(pifu_ctx* ctx, const PointSrc& src, int64_t n, const Map& map, co
 int ensure_clist(pifu_ctx* ctx, int64_t cap) {
     if (!ctx->d_ccount) CK(dev_alloc(&ctx->d_ccount, 1));
     if (cap > ctx->clist_cap) {
+        invalidate_graphs(ctx);
         dev_free(ctx->clist);
         ctx->clist_cap = 0;
         CK(dev_alloc(&ctx->clist, cap));

@@ -7,6 +7,8 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include "stream_sched.cuh"
+
 namespace pifu {
 
 constexpr float kHalf = 0.5f;
@@ -26,6 +28,32 @@ struct Map {
     const void* data;
     int H, W, C;
     int dtype;  // 0 f32, 1 bf16
+};
+
+// ---- frame stream (work-queue form): slot ops and the scheduling step ---------
+
+// One slot of the frame stream as the kernels of a round see it (written by
+// the scheduler kernel between rounds).  Its arrays are the slot's, sized for
+// the finest level; the current level uses their first words.
+struct SlotView {
+    int op;                  // SlotOp of this round
+    int frame;               // the stream frame the slot holds (-1: none)
+    int level;               // level index
+    int N;                   // cells per axis of the level
+    int first_level;         // 1 at level 0: no tentative values, no conflicts
+    int finest;              // 1 at the last level
+    const uint32_t* coarse;  // SLOT_ADVANCE: the binarized coarser level
+    uint32_t* cand;
+    uint32_t* tent;
+    uint32_t* bin;
+    uint32_t* eval;
+    uint32_t* conf;
+    float* values;           // dense store of the level's occupancies
+    int* top;                // render scratch [2][(N+1)^2]
+    float* depth;            // the frame's outputs (each may be null)
+    float* rgb;
+    uint8_t* mask;
+    uint32_t* bits_out;      // optional copy of the frame's binarized finest level
 };
 
 // Where the points of an MLP batch come from.
@@ -57,6 +85,9 @@ struct PointSrc {
     const int* keys;      // PTS_XYZ
     int64_t slot_div;
     int width;            // PTS_COLUMN: pixels per image side
+    // Frame stream: the grid modes' key / slot_div is a slot, whose level
+    // resolution replaces N.
+    const SlotView* sv;
 };
 
 // What the last MLP layer does with its output.
@@ -89,6 +120,9 @@ struct LevelBits {
     unsigned int* ccount;
     unsigned int ccap;      // beyond it the error word gets kErrCapacity
     unsigned int* err;
+    // Frame stream: key / key_div is a slot whose arrays, resolution and
+    // first-level flag replace the ones above.
+    const SlotView* sv;
 };
 
 struct Epilogue {
@@ -105,6 +139,9 @@ struct Epilogue {
     int* recheck;
     unsigned int* recheck_count;
     float margin;
+    // Frame stream, surrogate pass: the points of slots at their finest level
+    // are queued whatever their occupancy (that level always runs f_O).
+    int finest_to_queue;
 };
 
 // --- gather.cu -------------------------------------------------------------
@@ -333,10 +370,81 @@ cudaError_t launch_loop_control(cudaGraphConditionalHandle h, const unsigned int
 // is appended to list at *count (at most cap; beyond it kErrCapacity).  The
 // same set as dilate26(conflicts) & ~evaluated, in work proportional to the
 // conflicts.  Launched for up to max_c conflicts (a device-resident count).
+// Frame stream: sv gives every key's slot level and evaluated bitset (N and
+// eval are then unused) and slot_count[slot] counts the keys appended.
 cudaError_t launch_expand_conflicts(const int* clist, const unsigned int* ccount,
                                     unsigned int max_c, int N, uint32_t* eval, int64_t key_div,
                                     int64_t slot_words, int* list, unsigned int* count,
-                                    unsigned int cap, unsigned int* err, cudaStream_t stream);
+                                    unsigned int cap, unsigned int* err, cudaStream_t stream,
+                                    const SlotView* sv = nullptr,
+                                    unsigned int* slot_count = nullptr);
+
+// Frame stream: everything the scheduler kernel reads and writes.
+struct StreamCtl {
+    unsigned int next_frame;          // the queue's next frame
+    unsigned int rounds;              // rounds run
+    unsigned long long rechecked;     // MIXED: evaluations redone in FP32, all frames
+    unsigned long long fallback;      // surrogate: evaluations redone by f_O, all frames
+    unsigned long long t_start;       // device clock (ns) of the first admission
+    unsigned int render_rounds;       // rounds in which a slot rendered
+    unsigned int err;                 // the error word when the loop stopped
+};
+struct StreamArgs {
+    SlotView* sv;                     // [S] this round's views (written here)
+    StreamSlot* st;                   // [S] persistent slot state
+    StreamFrameStats* fs;             // [F]
+    StreamCtl* ctl;
+    unsigned int* pend_eval;          // [S] keys of the slot in the round's evaluation
+    unsigned int* pend_next;          // [S] keys its conflict expansion queued
+    unsigned long long* cands;        // [S] candidates its selection counted
+    int S, F, L, n0, max_rounds;
+    unsigned int max_total_rounds;    // beyond it: kErrNotConverged
+    // the slots' arrays: slot s at s * slot_words / slot_nodes / slot_top
+    uint32_t* cand;
+    uint32_t* tent;
+    uint32_t* bin0;
+    uint32_t* bin1;
+    uint32_t* eval;
+    uint32_t* conf;
+    float* values;
+    int* top;
+    int64_t slot_words, slot_nodes, slot_top;
+    // the frames' inputs (copied to a slot's entries when it takes a frame)
+    const Map* frame_maps0;
+    const Map* frame_maps1;           // may be null
+    const Calib* frame_calibs;
+    Map* slot_maps0;
+    Map* slot_maps1;
+    Calib* slot_calibs;
+    // the frames' outputs, frame f at f * npix pixels / f * out_words words
+    float* depth;
+    float* rgb;
+    uint8_t* mask;
+    uint32_t* bits_out;
+    int64_t npix, out_words;
+    unsigned int* err;
+    cudaGraphConditionalHandle h;     // the loop's condition: another round
+    int init;                         // 1: reset the stream and admit its first frames
+};
+// One thread: every slot's scheduling step (stream_step), the views of the
+// next round, and the loop condition (another round while a slot holds a
+// frame or the queue holds one, and no error is latched).
+cudaError_t launch_stream_sched(const StreamArgs& a, cudaStream_t stream);
+// h = (*count > 0).
+cudaError_t launch_set_if(cudaGraphConditionalHandle h, const unsigned int* count,
+                          cudaStream_t stream);
+
+// Frame stream: the level set-up (op START: level 0 with every node
+// evaluated; op ADVANCE: the classify step) of every slot whose round op asks
+// for one, and the first selection of those slots' level (START: every node;
+// ADVANCE: the candidates' 26-ring), appended as keys slot * slot_nodes +
+// node at *count (at most cap; beyond it kErrCapacity); pend[slot] += keys
+// queued, cands[slot] += boundary candidates.  N_fine sizes the grid.
+cudaError_t launch_stream_setup(const SlotView* sv, int slots, int N_fine, cudaStream_t stream);
+cudaError_t launch_stream_select(const SlotView* sv, int slots, int N_fine, int64_t slot_nodes,
+                                 int* list, unsigned int* count, unsigned int cap,
+                                 unsigned int* err, unsigned int* pend,
+                                 unsigned long long* cands, cudaStream_t stream);
 
 // Graph form: set hs for 1 .. threshold points in *count, hl above.
 cudaError_t launch_branch(cudaGraphConditionalHandle hs, cudaGraphConditionalHandle hl,
@@ -475,6 +583,12 @@ struct RenderArgs {
     int64_t slot_nodes, slot_words;
 };
 cudaError_t launch_render_rays(const RenderArgs& a, cudaStream_t stream);
+// Frame stream: the render of every slot whose round op is RENDER, from the
+// slot's arrays into its frame's outputs (SlotView); a supplies the image
+// size, the background and the hit list, whose keys are frame * width *
+// height + pixel.  N_fine sizes the grid.
+cudaError_t launch_stream_render(const SlotView* sv, int slots, int N_fine, const RenderArgs& a,
+                                 cudaStream_t stream);
 
 // View-culled final level (Sec. 3.2): the render's pixel columns at the N_f =
 // 2 N_c depth nodes of the level after the last localized one (N_c cells,

@@ -14,10 +14,33 @@
 // for the colour MLP; misses get the background of Eq. 3.
 #include <math.h>
 
+#include <algorithm>
+
 #include "pifu_internal.h"
 
 namespace pifu {
 namespace {
+
+// The set bits of word w of eval | bin raise the column tops (and bottoms).
+__device__ __forceinline__ void column_top_word(int N, int row_words, const uint32_t* __restrict__ eval,
+                                                const uint32_t* __restrict__ bin, int* top,
+                                                int* bot, int64_t w) {
+    const int n1 = N + 1;
+    uint32_t bits = __ldg(eval + w) | __ldg(bin + w);
+    if (!bits) return;
+    const int wx = (int)(w % row_words);
+    const int64_t row = w / row_words;   // k (N+1) + j
+    const int j = (int)(row % n1);
+    const int k = (int)(row / n1);
+    int* t = top + (int64_t)j * n1 + wx * 32;
+    int* u = bot ? bot + (int64_t)j * n1 + wx * 32 : nullptr;
+    while (bits) {
+        const int b = __ffs(bits) - 1;
+        bits &= bits - 1u;
+        atomicMax(t + b, k);
+        if (u) atomicMax(u + b, N - k);
+    }
+}
 
 // Highest depth-node index k (z index, 0..N) at which node column (i, j) has
 // any evaluated or inside node: one thread per bitset word (k, j, word), one
@@ -39,20 +62,7 @@ __global__ void __launch_bounds__(256) column_top_kernel(int N, int row_words,
     }
     const int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (w >= (int64_t)n1 * n1 * row_words) return;
-    uint32_t bits = __ldg(eval + w) | __ldg(bin + w);
-    if (!bits) return;
-    const int wx = (int)(w % row_words);
-    const int64_t row = w / row_words;   // k (N+1) + j
-    const int j = (int)(row % n1);
-    const int k = (int)(row / n1);
-    int* t = top + (int64_t)j * n1 + wx * 32;
-    int* u = bot ? bot + (int64_t)j * n1 + wx * 32 : nullptr;
-    while (bits) {
-        const int b = __ffs(bits) - 1;
-        bits &= bits - 1u;
-        atomicMax(t + b, k);
-        if (u) atomicMax(u + b, N - k);
-    }
+    column_top_word(N, row_words, eval, bin, top, bot, w);
 }
 
 // bits ix and ix+1 of a bitset row as bits 0 and 1 (ix + 1 <= N is in the row)
@@ -77,10 +87,97 @@ __device__ __forceinline__ void pixel_node(int i, int R, int N, int& i0, float& 
     w = (float)r / (float)den;
 }
 
+// The first crossing of pixel pix's ray through one frame's volume (the
+// arrays of `a`): true on a hit, with its depth zs; (px, py) is the pixel
+// centre in NDC.
+__device__ __forceinline__ bool ray_crossing(const RenderArgs& a, int64_t pix, float& zs,
+                                             float& px, float& py) {
+    bool hit = false;
+    zs = 0.f;
+    const int i = (int)(pix % a.width);
+    const int j = (int)(pix / a.width);
+    int ix0, iy0;
+    float wx, wy;
+    pixel_node(i, a.width, a.N, ix0, wx);
+    pixel_node(j, a.height, a.N, iy0, wy);
+    px = __fmaf_rn((float)(2 * i + 1), 1.0f / (float)a.width, -1.0f);
+    py = __fmaf_rn((float)(2 * j + 1), 1.0f / (float)a.height, -1.0f);
+    const int n1 = a.N + 1;
+    const int rw = a.row_words;
+    const float w00 = (1.f - wx) * (1.f - wy), w10 = wx * (1.f - wy);
+    const float w01 = (1.f - wx) * wy, w11 = wx * wy;
+    const float h = 2.0f / (float)a.N;
+    // samples nearer the observer than every node of the four columns are 0
+    const int64_t c0 = (int64_t)iy0 * n1 + ix0;
+    const int ktop = max(max(a.top[c0], a.top[c0 + 1]), max(a.top[c0 + n1], a.top[c0 + n1 + 1]));
+    const int kstart = ktop < 0 ? a.N + 1 : a.N - ktop;
+    // and the samples farther than every node of the four columns are 0
+    const int* bt = a.top + (int64_t)n1 * n1;
+    const int kend = max(max(bt[c0], bt[c0 + 1]), max(bt[c0 + n1], bt[c0 + n1 + 1]));
+    float vprev = 0.f;
+    for (int k = kstart; k <= kend; ++k) {
+        const int iz = a.N - k;
+        const int64_t row0 = (int64_t)iz * n1 + iy0;
+        const int64_t row1 = row0 + 1;
+        const uint32_t e0 = two_bits(a.eval + row0 * rw, ix0);
+        const uint32_t e1 = two_bits(a.eval + row1 * rw, ix0);
+        const uint32_t b0 = two_bits(a.bin + row0 * rw, ix0);
+        const uint32_t b1 = two_bits(a.bin + row1 * rw, ix0);
+        float v = 0.f;
+        if (e0 | e1 | b0 | b1) {
+            const float v00 = (e0 & 1u) ? a.values[row0 * n1 + ix0] : (float)(b0 & 1u);
+            const float v10 = (e0 & 2u) ? a.values[row0 * n1 + ix0 + 1] : (float)(b0 >> 1);
+            const float v01 = (e1 & 1u) ? a.values[row1 * n1 + ix0] : (float)(b1 & 1u);
+            const float v11 = (e1 & 2u) ? a.values[row1 * n1 + ix0 + 1] : (float)(b1 >> 1);
+            v = fmaf(w11, v11, fmaf(w01, v01, fmaf(w10, v10, w00 * v00)));
+        }
+        if (v >= kHalf) {
+            hit = true;
+            if (k == 0) {
+                zs = 1.0f;
+            } else {
+                const float t = (kHalf - vprev) / (v - vprev);
+                const float zprev = __fmaf_rn(-(float)(k - 1), h, 1.0f);
+                zs = zprev - t * h;
+            }
+            break;
+        }
+        vprev = v;
+    }
+    return hit;
+}
+
+// Writes a pixel's depth, mask and (on a miss) background colour, and
+// appends its hit with key `hit_key` (warp-aggregated; the whole warp calls).
+__device__ __forceinline__ void ray_outputs(const RenderArgs& a, int64_t pix, bool valid, bool hit,
+                                            float zs, float px, float py, int hit_key) {
+    const int lane = threadIdx.x & 31;
+    if (valid) {
+        if (a.depth) a.depth[pix] = hit ? zs : __int_as_float(0x7fc00000);
+        if (a.mask) a.mask[pix] = hit ? 1 : 0;
+        if (a.rgb && !hit) {
+            a.rgb[pix * 3 + 0] = a.bg[0];
+            a.rgb[pix * 3 + 1] = a.bg[1];
+            a.rgb[pix * 3 + 2] = a.bg[2];
+        }
+    }
+    const unsigned ballot = __ballot_sync(0xffffffffu, hit);
+    if (ballot == 0u) return;
+    unsigned base = 0u;
+    if (lane == 0) base = atomicAdd(a.hit_count, (unsigned)__popc(ballot));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (hit) {
+        const unsigned pos = base + __popc(ballot & ((1u << lane) - 1u));
+        a.hit_xyz[3 * (int64_t)pos + 0] = px;
+        a.hit_xyz[3 * (int64_t)pos + 1] = py;
+        a.hit_xyz[3 * (int64_t)pos + 2] = zs;
+        a.hit_pix[pos] = hit_key;
+    }
+}
+
 __global__ void __launch_bounds__(256) render_rays_kernel(RenderArgs a) {
     const int64_t npix = (int64_t)a.width * a.height;
     const int64_t pix = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int lane = threadIdx.x & 31;
     const int64_t frame = blockIdx.y;   // frame of a lockstep batch (0: one frame)
     if (frame > 0) {
         a.values += frame * a.slot_nodes;
@@ -93,77 +190,65 @@ __global__ void __launch_bounds__(256) render_rays_kernel(RenderArgs a) {
     }
     bool hit = false;
     float zs = 0.f, px = 0.f, py = 0.f;
-    if (pix < npix) {
-        const int i = (int)(pix % a.width);
-        const int j = (int)(pix / a.width);
-        int ix0, iy0;
-        float wx, wy;
-        pixel_node(i, a.width, a.N, ix0, wx);
-        pixel_node(j, a.height, a.N, iy0, wy);
-        px = __fmaf_rn((float)(2 * i + 1), 1.0f / (float)a.width, -1.0f);
-        py = __fmaf_rn((float)(2 * j + 1), 1.0f / (float)a.height, -1.0f);
-        const int n1 = a.N + 1;
-        const int rw = a.row_words;
-        const float w00 = (1.f - wx) * (1.f - wy), w10 = wx * (1.f - wy);
-        const float w01 = (1.f - wx) * wy, w11 = wx * wy;
-        const float h = 2.0f / (float)a.N;
-        // samples nearer the observer than every node of the four columns are 0
-        const int64_t c0 = (int64_t)iy0 * n1 + ix0;
-        const int ktop = max(max(a.top[c0], a.top[c0 + 1]), max(a.top[c0 + n1], a.top[c0 + n1 + 1]));
-        const int kstart = ktop < 0 ? a.N + 1 : a.N - ktop;
-        // and the samples farther than every node of the four columns are 0
-        const int* bt = a.top + (int64_t)n1 * n1;
-        const int kend = max(max(bt[c0], bt[c0 + 1]), max(bt[c0 + n1], bt[c0 + n1 + 1]));
-        float vprev = 0.f;
-        for (int k = kstart; k <= kend; ++k) {
-            const int iz = a.N - k;
-            const int64_t row0 = (int64_t)iz * n1 + iy0;
-            const int64_t row1 = row0 + 1;
-            const uint32_t e0 = two_bits(a.eval + row0 * rw, ix0);
-            const uint32_t e1 = two_bits(a.eval + row1 * rw, ix0);
-            const uint32_t b0 = two_bits(a.bin + row0 * rw, ix0);
-            const uint32_t b1 = two_bits(a.bin + row1 * rw, ix0);
-            float v = 0.f;
-            if (e0 | e1 | b0 | b1) {
-                const float v00 = (e0 & 1u) ? a.values[row0 * n1 + ix0] : (float)(b0 & 1u);
-                const float v10 = (e0 & 2u) ? a.values[row0 * n1 + ix0 + 1] : (float)(b0 >> 1);
-                const float v01 = (e1 & 1u) ? a.values[row1 * n1 + ix0] : (float)(b1 & 1u);
-                const float v11 = (e1 & 2u) ? a.values[row1 * n1 + ix0 + 1] : (float)(b1 >> 1);
-                v = fmaf(w11, v11, fmaf(w01, v01, fmaf(w10, v10, w00 * v00)));
-            }
-            if (v >= kHalf) {
-                hit = true;
-                if (k == 0) {
-                    zs = 1.0f;
-                } else {
-                    const float t = (kHalf - vprev) / (v - vprev);
-                    const float zprev = __fmaf_rn(-(float)(k - 1), h, 1.0f);
-                    zs = zprev - t * h;
-                }
-                break;
-            }
-            vprev = v;
-        }
-        if (a.depth) a.depth[pix] = hit ? zs : __int_as_float(0x7fc00000);
-        if (a.mask) a.mask[pix] = hit ? 1 : 0;
-        if (a.rgb && !hit) {
-            a.rgb[pix * 3 + 0] = a.bg[0];
-            a.rgb[pix * 3 + 1] = a.bg[1];
-            a.rgb[pix * 3 + 2] = a.bg[2];
-        }
+    const bool valid = pix < npix;
+    if (valid) hit = ray_crossing(a, pix, zs, px, py);
+    ray_outputs(a, pix, valid, hit, zs, px, py, (int)(frame * npix + pix));
+}
+
+// ---- frame stream: the render of the slots whose finest level converged ----
+//
+// Grid y = slot; only slots whose round op is RENDER do anything.
+
+// Column tops and bottoms back to -1 (empty), in [2][(N+1)^2] ints.
+__global__ void __launch_bounds__(256) stream_top_reset_kernel(const SlotView* __restrict__ sv) {
+    const SlotView v = sv[blockIdx.y];
+    if (v.op != SLOT_RENDER) return;
+    const int64_t n = 2 * (int64_t)(v.N + 1) * (v.N + 1);
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n;
+         q += (int64_t)gridDim.x * blockDim.x)
+        v.top[q] = -1;
+}
+
+// Column tops and bottoms of the slot's volume, and the copy of its
+// binarized finest level into the frame's place of bits_out.
+__global__ void __launch_bounds__(256) stream_column_top_kernel(const SlotView* __restrict__ sv) {
+    const SlotView v = sv[blockIdx.y];
+    if (v.op != SLOT_RENDER) return;
+    const int n1 = v.N + 1;
+    const int rw = row_words_of(v.N);
+    const int64_t total = words_of(v.N);
+    for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < total;
+         w += (int64_t)gridDim.x * blockDim.x) {
+        column_top_word(v.N, rw, v.eval, v.bin, v.top, v.top + (int64_t)n1 * n1, w);
+        if (v.bits_out) v.bits_out[w] = v.bin[w];
     }
-    // warp-aggregated append of the hits
-    const unsigned ballot = __ballot_sync(0xffffffffu, hit);
-    if (ballot == 0u) return;
-    unsigned base = 0u;
-    if (lane == 0) base = atomicAdd(a.hit_count, (unsigned)__popc(ballot));
-    base = __shfl_sync(0xffffffffu, base, 0);
-    if (hit) {
-        const unsigned pos = base + __popc(ballot & ((1u << lane) - 1u));
-        a.hit_xyz[3 * (int64_t)pos + 0] = px;
-        a.hit_xyz[3 * (int64_t)pos + 1] = py;
-        a.hit_xyz[3 * (int64_t)pos + 2] = zs;
-        a.hit_pix[pos] = (int)(frame * npix + pix);
+}
+
+// Rays of the slot's frame: its depth, mask and background into the frame's
+// outputs, its hits appended with keys frame * width * height + pixel.
+__global__ void __launch_bounds__(256) stream_rays_kernel(const SlotView* __restrict__ sv,
+                                                          RenderArgs a) {
+    const SlotView v = sv[blockIdx.y];
+    if (v.op != SLOT_RENDER) return;
+    a.N = v.N;
+    a.row_words = row_words_of(v.N);
+    a.values = v.values;
+    a.eval = v.eval;
+    a.bin = v.bin;
+    a.top = v.top;
+    a.depth = v.depth;
+    a.rgb = v.rgb;
+    a.mask = v.mask;
+    const int64_t npix = (int64_t)a.width * a.height;
+    // whole warps iterate together (the hit append is warp-aggregated)
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < npix;
+         base += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t pix = base + threadIdx.x;
+        bool hit = false;
+        float zs = 0.f, px = 0.f, py = 0.f;
+        const bool valid = pix < npix;
+        if (valid) hit = ray_crossing(a, pix, zs, px, py);
+        ray_outputs(a, pix, valid, hit, zs, px, py, (int)((int64_t)v.frame * npix + pix));
     }
 }
 
@@ -185,6 +270,24 @@ cudaError_t launch_render_rays(const RenderArgs& a, cudaStream_t stream) {
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     render_rays_kernel<<<dim3((unsigned)((npix + 255) / 256), (unsigned)slots), 256, 0, stream>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_stream_render(const SlotView* sv, int slots, int N_fine, const RenderArgs& a,
+                                 cudaStream_t stream) {
+    const int64_t npix = (int64_t)a.width * a.height;
+    if (slots < 1 || slots > 65535 || npix <= 0) return cudaErrorInvalidValue;
+    const int64_t n1 = N_fine + 1;
+    const unsigned gt = (unsigned)std::min<int64_t>((2 * n1 * n1 + 255) / 256, 152 * 2);
+    stream_top_reset_kernel<<<dim3(gt, (unsigned)slots), 256, 0, stream>>>(sv);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const unsigned gw = (unsigned)std::min<int64_t>((words_of(N_fine) + 255) / 256, 152 * 2);
+    stream_column_top_kernel<<<dim3(gw, (unsigned)slots), 256, 0, stream>>>(sv);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const unsigned gp = (unsigned)std::min<int64_t>((npix + 255) / 256, 152 * 4);
+    stream_rays_kernel<<<dim3(gp, (unsigned)slots), 256, 0, stream>>>(sv, a);
     return cudaGetLastError();
 }
 

@@ -136,6 +136,7 @@ int autotune(pifu_ctx* ctx, int64_t rows, cudaStream_t s, int32_t* bn_out, doubl
     }
     ctx->g_valid = false;
     ctx->batch.g_valid = false;
+    ctx->stream.g_valid = false;
     if (n_done) *n_done = n;
     return PIFU_OK;
 }
@@ -195,6 +196,7 @@ int set_tiles(pifu_ctx* ctx, const int32_t* codes, int n) {
     });
     ctx->g_valid = false;
     ctx->batch.g_valid = false;
+    ctx->stream.g_valid = false;
     return ok ? PIFU_OK : PIFU_ERR_CUDA;
 }
 
@@ -219,6 +221,7 @@ int pifu_set_schedule(pifu_ctx* ctx, int schedule) {
     ctx->chain_on = schedule == PIFU_SCHED_CHAINED;
     ctx->g_valid = false;
     ctx->batch.g_valid = false;
+    ctx->stream.g_valid = false;
     return PIFU_OK;
 }
 

@@ -45,7 +45,7 @@ EXPORTS = ("pifu_create", "pifu_destroy", "pifu_query", "pifu_query_colour", "pi
            "pifu_surrogate_train", "pifu_surrogate_params", "pifu_surrogate_query",
            "pifu_calibrate_fp8", "pifu_frames", "pifu_autotune", "pifu_surrogate_ohem_init",
            "pifu_surrogate_ohem_weights", "pifu_surrogate_ohem_sample",
-           "pifu_surrogate_train_ohem", "pifu_set_tiles", "pifu_set_schedule")
+           "pifu_surrogate_train_ohem", "pifu_set_tiles", "pifu_set_schedule", "pifu_stream")
 
 KERNEL_CLASSES = ("gather", "mlp_hidden", "mlp_last", "level", "select", "render", "mlp_f32",
                   "cbn_tc")
@@ -80,6 +80,11 @@ class pifu_volume(ctypes.Structure):
                 ("rechecked_per_level", ctypes.c_int64 * 8),
                 ("fallback_per_level", ctypes.c_int64 * 8),
                 ("conflict_rounds", ctypes.c_int32 * 8)]
+
+
+class pifu_frame_time(ctypes.Structure):
+    _fields_ = [("admit_ms", ctypes.c_float), ("done_ms", ctypes.c_float),
+                ("slot", ctypes.c_int32), ("stream_rounds", ctypes.c_int32)]
 
 
 class pifu_kernel_stats(ctypes.Structure):
@@ -140,6 +145,11 @@ def _lib():
                                 ctypes.POINTER(F), ctypes.POINTER(pifu_levels),
                                 ctypes.POINTER(pifu_camera), P, P, P, P, ctypes.POINTER(pifu_volume)]
     lib.pifu_frames.restype = I
+    lib.pifu_stream.argtypes = [P, I, ctypes.POINTER(pifu_fmap), ctypes.POINTER(pifu_fmap),
+                                ctypes.POINTER(F), I, ctypes.POINTER(pifu_levels),
+                                ctypes.POINTER(pifu_camera), P, P, P, P, P,
+                                ctypes.POINTER(pifu_volume), ctypes.POINTER(pifu_frame_time)]
+    lib.pifu_stream.restype = I
     lib.pifu_autotune.argtypes = [P, I64, P, ctypes.POINTER(ctypes.c_int32),
                                   ctypes.POINTER(ctypes.c_double), I, ctypes.POINTER(I)]
     lib.pifu_autotune.restype = I
@@ -378,6 +388,33 @@ def pifu_frames(ctx, occ_maps, col_maps, calibs, n0, num_levels, width, height, 
                             _stream(stream), _ptr(depth), _ptr(rgb), _ptr(mask), vols)
     _check(st, "pifu_frames", ctx)
     return list(vols)
+
+
+def pifu_stream(ctx, occ_maps, col_maps, calibs, slots, n0, num_levels, width, height, depth=None,
+                rgb=None, mask=None, occ_bits=None, precision=PIFU_PREC_MIXED, margin=0.02,
+                max_rounds=0, background=(0.0, 0.0, 0.0), stream=None, use_surrogate=False,
+                surrogate_margin=0.0):
+    """F frames through `slots` frame slots fed by a device work queue, as one
+    (cached) CUDA graph; returns (F volumes, F pifu_frame_time).
+    occ_maps / col_maps: sequences of device tensors (col_maps may be None),
+    calibs: F calibrations; depth/rgb/mask: [F][H][W](x3) device tensors;
+    occ_bits: optional [F][words] int32 device tensor for each frame's
+    binarized finest level."""
+    F = len(occ_maps)
+    fo = (pifu_fmap * F)(*[fmap(m) for m in occ_maps])
+    fc = (pifu_fmap * F)(*[fmap(m) for m in col_maps]) if col_maps is not None else None
+    cal = np.ascontiguousarray(np.asarray(calibs, np.float32).reshape(F, 12))
+    cal_p = cal.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+    lv = pifu_levels(n0, num_levels, precision, max_rounds, margin, int(bool(use_surrogate)),
+                     surrogate_margin)
+    cam = pifu_camera(width, height, (ctypes.c_float * 3)(*background), PIFU_PREC_BF16)
+    vols = (pifu_volume * F)()
+    times = (pifu_frame_time * F)()
+    st = _lib().pifu_stream(ctx, F, fo, fc, cal_p, int(slots), ctypes.byref(lv),
+                            ctypes.byref(cam), _stream(stream), _ptr(depth), _ptr(rgb), _ptr(mask),
+                            _ptr(occ_bits), vols, times)
+    _check(st, "pifu_stream", ctx)
+    return list(vols), list(times)
 
 
 # Tile code of the CTA-pair form (two CTAs on a 256 x 256 tile).

@@ -1,8 +1,12 @@
-"""The batched video-stream form (config 4: animated subjects of different
-scales, BF16 feature maps, frames evaluated together) against the FP64
-oracle, frame by frame: each frame of a batch is compared with the oracle's
-coarse-to-fine localization (Sec. 3.2) and render (Eq. 3) on the same
-BF16-rounded maps.
+"""The batched video-stream forms (config 4: animated subjects of different
+scales, BF16 feature maps, frames evaluated together): the lockstep batch
+(pifu_frames) and the stream through a device work queue (pifu_stream),
+against the FP64 oracle frame by frame: each frame is compared with the
+oracle's coarse-to-fine localization (Sec. 3.2) and render (Eq. 3) on the
+same BF16-rounded maps.  The work-queue stream is also checked against the
+frames run alone: in BF16 (each MLP row's arithmetic does not depend on its
+batch) bit for bit, with the same evaluations and conflict rounds per level,
+and its number of rounds against the schedule its frames' own steps give.
 
 Bars: occupancy IoU >= 0.995 and colour PSNR >= 40 dB for every precision
 (the benchmark spec's); in MIXED also every stored occupancy within the 0.02
@@ -82,9 +86,12 @@ def run_batch(c, frames, precision, **kw):
         m.cpu().numpy().astype(bool)
 
 
-def check_frame(c, vol, depth, rgb, mask, ofr, mixed):
+def check_frame(c, vol, depth, rgb, mask, ofr, mixed, binary=None):
+    """binary: the frame's binarized finest level when the volume views are
+    not available (work-queue frames whose slot took a later frame)."""
     f, lv, o_rgb, o_depth, o_hit = ofr
-    b, e, v = c.volume_host(vol)
+    has_view = bool(vol.occ_bits_dev)
+    b = c.volume_host(vol)[0] if has_view else binary
     fine = lv[-1]
     iou = metrics.iou(b, fine.binary)
     ok = ~ambiguous_rays(fine.values, R)
@@ -98,7 +105,8 @@ def check_frame(c, vol, depth, rgb, mask, ofr, mixed):
     assert iou >= 0.995, res
     assert psnr >= 40.0, res
     if mixed:
-        res.update(check_mixed_values(c, vol, lv, f))
+        if has_view:
+            res.update(check_mixed_values(c, vol, lv, f))
         assert derr <= depth_step(vol.n), res
     return res
 
@@ -132,3 +140,132 @@ def test_stream_batch_fp8_mixed_surrogate_matches_oracle(ctx, frames, oracle_fra
         res = check_frame(ctx, vols[k], depth[k], rgb[k], mask[k], ofr, mixed=False)
         print("stream FP8_MIXED + surrogate (margin %.3f) subject %d (scale %.2f) frame %d: %s"
               % (fp8_surrogate, fr["subject"], fr["scale"], fr["t"], res))
+
+
+# ---- the work-queue stream (pifu_stream) -------------------------------------------
+
+def bits_words(n):
+    return (n + 1) * (n + 1) * ((n + 1 + 31) // 32)
+
+
+def run_stream(c, frames, slots, precision, R_=R, **kw):
+    t = torch()
+    F = len(frames)
+    w = c.w
+    n = w.n0 << (w.num_levels - 1)
+    d = t.empty((F, R_, R_), dtype=t.float32, device="cuda")
+    rgb = t.empty((F, R_, R_, 3), dtype=t.float32, device="cuda")
+    m = t.empty((F, R_, R_), dtype=t.uint8, device="cuda")
+    bits = t.zeros((F, bits_words(n)), dtype=t.int32, device="cuda")
+    vols, times = pifu.pifu_stream(c.ctx, [fr["occ"] for fr in frames],
+                                   [fr["col"] for fr in frames], [w.calib] * F, slots, w.n0,
+                                   w.num_levels, R_, R_, d, rgb, m, bits, precision=precision,
+                                   **kw)
+    t.cuda.synchronize()
+    binary = [pifu.unpack_bits(bits[f].cpu().numpy(), n, (n + 1 + 31) // 32) for f in range(F)]
+    return (vols, times, d.cpu().numpy().astype(np.float64), rgb.cpu().numpy().astype(np.float64),
+            m.cpu().numpy().astype(bool), binary)
+
+
+def schedule_rounds(steps, slots):
+    """Rounds a stream of frames taking steps[f] rounds each runs on `slots`
+    slots, frames taken in order by the first free slot (lowest index first)."""
+    free_at = [0] * slots
+    for d in steps:
+        s = min(range(slots), key=lambda i: (free_at[i], i))
+        free_at[s] += d
+    return max(free_at)
+
+
+@pytest.fixture(scope="module")
+def many_frames():
+    """Five frames of four subjects of different scales (small and large
+    surfaces), BF16 maps."""
+    t = torch()
+    subj = synth.stream(n_figures=8, frames=64, seed=100)
+    order = np.argsort([s.scale for s in subj])
+    out = []
+    for i, tt in ((order[0], 3), (order[-1], 9), (order[3], 20), (order[-1], 33), (order[1], 50)):
+        g_o, g_t = subj[int(i)].maps(tt)
+        out.append({"subject": int(i), "scale": subj[int(i)].scale, "t": tt,
+                    "occ": t.from_numpy(g_o).cuda().to(t.bfloat16).contiguous(),
+                    "col": t.from_numpy(g_t).cuda().to(t.bfloat16).contiguous()})
+    return out
+
+
+def test_stream_bf16_equals_frames_alone(ctx, many_frames):
+    """Five frames through two slots (each slot takes several frames): every
+    frame's binarized volume, evaluations and conflict rounds per level,
+    depth, mask and colour equal those of the frame run alone, bit for bit."""
+    t = torch()
+    w = ctx.w
+    R2 = 256
+    L = w.num_levels
+    vols, times, d, rgb, m, binary = run_stream(ctx, many_frames, 2, pifu.PIFU_PREC_BF16, R_=R2)
+    steps = []
+    for f, fr in enumerate(many_frames):
+        d1 = t.empty((R2, R2), dtype=t.float32, device="cuda")
+        rgb1 = t.empty((R2, R2, 3), dtype=t.float32, device="cuda")
+        m1 = t.empty((R2, R2), dtype=t.uint8, device="cuda")
+        v1 = pifu.pifu_frame(ctx.ctx, fr["occ"], fr["col"], w.calib, w.n0, L, R2, R2, d1, rgb1,
+                             m1, precision=pifu.PIFU_PREC_BF16)
+        t.cuda.synchronize()
+        b1 = ctx.volume_host(v1)[0]
+        assert np.array_equal(binary[f], b1), f
+        for l in range(L):
+            assert int(vols[f].evals_per_level[l]) == int(v1.evals_per_level[l]), (f, l)
+            assert int(vols[f].conflict_rounds[l]) == int(v1.conflict_rounds[l]), (f, l)
+            assert int(vols[f].candidates_per_level[l]) == int(v1.candidates_per_level[l]), (f, l)
+        np.testing.assert_array_equal(m[f], m1.cpu().numpy().astype(bool))
+        np.testing.assert_array_equal(np.nan_to_num(d[f], nan=-9.0),
+                                      np.nan_to_num(d1.cpu().numpy().astype(np.float64), nan=-9.0))
+        np.testing.assert_array_equal(rgb[f][m[f]], rgb1.cpu().numpy().astype(np.float64)[m[f]])
+        steps.append(L + 1 + sum(int(v1.conflict_rounds[l]) for l in range(L)))
+        assert times[f].done_ms > times[f].admit_ms
+    # the device's rounds are those of the frames' own steps on two slots
+    rounds = int(times[0].stream_rounds)
+    assert rounds == schedule_rounds(steps, 2), (rounds, steps)
+    print("stream BF16: 5 frames on 2 slots, steps per frame %s, stream rounds %d, "
+          "slots %s" % (steps, rounds, [tm.slot for tm in times]))
+
+
+def test_stream_mixed_matches_oracle(ctx, frames, oracle_frames):
+    # one slot: the second frame takes the slot the first one leaves
+    vols, times, depth, rgb, mask, binary = run_stream(ctx, frames, 1, pifu.PIFU_PREC_MIXED)
+    assert [tm.slot for tm in times] == [0, 0]
+    assert times[1].admit_ms >= times[0].done_ms
+    for k, (fr, ofr) in enumerate(zip(frames, oracle_frames)):
+        res = check_frame(ctx, vols[k], depth[k], rgb[k], mask[k], ofr, mixed=True,
+                          binary=binary[k])
+        print("work-queue stream MIXED subject %d (scale %.2f) frame %d: %s"
+              % (fr["subject"], fr["scale"], fr["t"], res))
+
+
+def test_stream_fp8_mixed_surrogate_matches_oracle(ctx, frames, oracle_frames, fp8_surrogate):
+    vols, times, depth, rgb, mask, binary = run_stream(
+        ctx, frames, 2, pifu.PIFU_PREC_FP8_MIXED, use_surrogate=True,
+        surrogate_margin=fp8_surrogate)
+    for k, (fr, ofr) in enumerate(zip(frames, oracle_frames)):
+        res = check_frame(ctx, vols[k], depth[k], rgb[k], mask[k], ofr, mixed=False,
+                          binary=binary[k])
+        print("work-queue stream FP8_MIXED + surrogate subject %d (scale %.2f) frame %d: %s"
+              % (fr["subject"], fr["scale"], fr["t"], res))
+
+
+def test_stream_arguments(ctx, many_frames):
+    w = ctx.w
+    fr = many_frames[:2]
+    with pytest.raises(pifu.PifuError) as ei:
+        run_stream(ctx, fr, 0, pifu.PIFU_PREC_MIXED)
+    assert ei.value.status == pifu.PIFU_ERR_ARG
+    with pytest.raises(pifu.PifuError) as ei:
+        run_stream(ctx, fr, 17, pifu.PIFU_PREC_MIXED)
+    assert ei.value.status == pifu.PIFU_ERR_ARG
+    with pytest.raises(pifu.PifuError) as ei:
+        run_stream(ctx, fr, 2, pifu.PIFU_PREC_FP32)
+    assert ei.value.status == pifu.PIFU_ERR_UNSUPPORTED
+    with pytest.raises(pifu.PifuError) as ei:
+        run_stream(ctx, fr, 2, pifu.PIFU_PREC_MIXED, max_rounds=1)
+    assert ei.value.status == pifu.PIFU_ERR_NOT_CONVERGED
+    run_stream(ctx, fr, 2, pifu.PIFU_PREC_MIXED)   # usable afterwards
+    del w
