@@ -388,6 +388,7 @@ struct StreamCtl {
     unsigned long long t_start;       // device clock (ns) of the first admission
     unsigned int render_rounds;       // rounds in which a slot rendered
     unsigned int err;                 // the error word when the loop stopped
+    unsigned int colour_passes;       // deferred colour passes inside the loop
 };
 struct StreamArgs {
     SlotView* sv;                     // [S] this round's views (written here)
@@ -433,6 +434,11 @@ cudaError_t launch_stream_sched(const StreamArgs& a, cudaStream_t stream);
 // h = (*count > 0).
 cudaError_t launch_set_if(cudaGraphConditionalHandle h, const unsigned int* count,
                           cudaStream_t stream);
+// Frame stream: h = (*hits + npix x the slots rendering this round > cap),
+// i.e. the hit list could not take this round's renders; *passes += h.
+cudaError_t launch_colour_cond(cudaGraphConditionalHandle h, const unsigned int* hits,
+                               const SlotView* sv, int S, int64_t npix, unsigned int cap,
+                               unsigned int* passes, cudaStream_t stream);
 
 // Frame stream: the level set-up (op START: level 0 with every node
 // evaluated; op ADVANCE: the classify step) of every slot whose round op asks

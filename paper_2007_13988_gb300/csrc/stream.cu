@@ -25,6 +25,7 @@ __global__ void stream_sched_kernel(StreamArgs a) {
         ctl->fallback = 0ull;
         ctl->t_start = now;
         ctl->render_rounds = 0u;
+        ctl->colour_passes = 0u;
         for (int s = 0; s < a.S; ++s) {
             a.st[s] = StreamSlot{-1, 0, 0, 0};
             a.sv[s].op = SLOT_IDLE;
@@ -92,6 +93,16 @@ __global__ void set_if_kernel(cudaGraphConditionalHandle h, const unsigned int* 
     cudaGraphSetConditional(h, *count > 0u ? 1u : 0u);
 }
 
+__global__ void colour_cond_kernel(cudaGraphConditionalHandle h, const unsigned int* hits,
+                                   const SlotView* sv, int S, int64_t npix, unsigned int cap,
+                                   unsigned int* passes) {
+    int renders = 0;
+    for (int s = 0; s < S; ++s) renders += sv[s].op == SLOT_RENDER ? 1 : 0;
+    const bool go = (int64_t)*hits + (int64_t)renders * npix > (int64_t)cap;
+    if (go) *passes += 1u;
+    cudaGraphSetConditional(h, go ? 1u : 0u);
+}
+
 }  // namespace
 
 cudaError_t launch_stream_sched(const StreamArgs& a, cudaStream_t stream) {
@@ -102,6 +113,13 @@ cudaError_t launch_stream_sched(const StreamArgs& a, cudaStream_t stream) {
 cudaError_t launch_set_if(cudaGraphConditionalHandle h, const unsigned int* count,
                           cudaStream_t stream) {
     set_if_kernel<<<1, 1, 0, stream>>>(h, count);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_colour_cond(cudaGraphConditionalHandle h, const unsigned int* hits,
+                               const SlotView* sv, int S, int64_t npix, unsigned int cap,
+                               unsigned int* passes, cudaStream_t stream) {
+    colour_cond_kernel<<<1, 1, 0, stream>>>(h, hits, sv, S, npix, cap, passes);
     return cudaGetLastError();
 }
 

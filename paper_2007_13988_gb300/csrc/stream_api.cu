@@ -194,6 +194,28 @@ int g_enqueue_stream(pifu_ctx* ctx, const StreamKey& k) {
     a.err = err;
     a.h = h;
     a.init = 1;
+    CK(cudaMemsetAsync(w.d_hits, 0, sizeof(unsigned int), s));
+    // the hit list holds the hits of every render since the last colour pass
+    const int64_t hcap = std::min<int64_t>((int64_t)w.S * w.npix, cap);
+    // the colour MLP over the hit list, then the list emptied
+    auto colour_pass = [&](cudaStream_t cs) -> int {
+        PointSrc hs{PTS_XYZ, w.hit_xyz, nullptr, 0, 0, nullptr};
+        const bool col = k.cC > 0;
+        hs.maps0 = col ? w.frame_maps1 : w.frame_maps0;   // colour maps first (Eq. 2)
+        hs.maps1 = col ? w.frame_maps0 : nullptr;
+        hs.calibs = w.frame_calibs;
+        hs.keys = w.hit_pix;
+        hs.slot_div = npix;
+        Epilogue he{};
+        he.mode = EPI_PIXELS;
+        he.act = ACT_TANH01;
+        he.out = k.rgb;
+        he.pix = w.hit_pix;
+        int r = run_mlp_tc(ctx, ctx->net[1], hs, hcap, Map{}, Map{}, Calib{}, he, cs, w.d_hits);
+        if (r == PIFU_OK && cudaMemsetAsync(w.d_hits, 0, sizeof(unsigned int), cs) != cudaSuccess)
+            r = PIFU_ERR_CUDA;
+        return r;
+    };
     CK(launch_stream_sched(a, s));   // admits the first frames, sets the condition
     cudaGraph_t body = nullptr;
     st = g_add_while(ctx, s, h, &body);
@@ -240,7 +262,10 @@ int g_enqueue_stream(pifu_ctx* ctx, const StreamKey& k) {
                                     (unsigned)cap, err, sb, w.sv, a.pend_next) != cudaSuccess)
             st = PIFU_ERR_CUDA;
         ctx->prof.k[PIFU_K_SELECT].launches += 1;
-        // 4. render of the converged slots, colour of their hits
+        // 4. colour of the hits gathered so far, when the hit list could not
+        //    take this round's renders; then the render of the converged slots.
+        //    The colour pass is deferred so that it runs on many frames' hits
+        //    at once (the rest run after the loop).
         RenderArgs ra{};
         ra.width = k.width;
         ra.height = k.height;
@@ -248,11 +273,6 @@ int g_enqueue_stream(pifu_ctx* ctx, const StreamKey& k) {
         ra.hit_xyz = w.hit_xyz;
         ra.hit_pix = w.hit_pix;
         ra.hit_count = w.d_hits;
-        if (st == PIFU_OK && cudaMemsetAsync(w.d_hits, 0, sizeof(unsigned int), sb) != cudaSuccess)
-            st = PIFU_ERR_CUDA;
-        if (st == PIFU_OK && launch_stream_render(w.sv, S, N_fine, ra, sb) != cudaSuccess)
-            st = PIFU_ERR_CUDA;
-        ctx->prof.k[PIFU_K_RENDER].launches += 3;
         if (st == PIFU_OK && k.rgb) {
             cudaStreamCaptureStatus cs2;
             cudaGraph_t cgb = nullptr;
@@ -260,7 +280,8 @@ int g_enqueue_stream(pifu_ctx* ctx, const StreamKey& k) {
             if (cudaStreamGetCaptureInfo(sb, &cs2, nullptr, &cgb, nullptr, nullptr, nullptr) !=
                     cudaSuccess ||
                 cudaGraphConditionalHandleCreate(&hc, cgb, 0, 0) != cudaSuccess ||
-                launch_set_if(hc, w.d_hits, sb) != cudaSuccess)
+                launch_colour_cond(hc, w.d_hits, w.sv, S, npix, (unsigned)hcap, &w.d_ctl->colour_passes,
+                                   sb) != cudaSuccess)
                 st = PIFU_ERR_CUDA;
             cudaGraph_t cbody = nullptr;
             if (st == PIFU_OK) st = g_add_cond(ctx, sb, hc, cudaGraphCondTypeIf, &cbody);
@@ -271,26 +292,19 @@ int g_enqueue_stream(pifu_ctx* ctx, const StreamKey& k) {
                 st = PIFU_ERR_CUDA;
             const int64_t before_colour = launches_now(ctx);
             if (st == PIFU_OK) {
-                PointSrc hs{PTS_XYZ, w.hit_xyz, nullptr, 0, 0, nullptr};
-                const bool col = k.cC > 0;
-                hs.maps0 = col ? w.frame_maps1 : w.frame_maps0;   // colour maps first (Eq. 2)
-                hs.maps1 = col ? w.frame_maps0 : nullptr;
-                hs.calibs = w.frame_calibs;
-                hs.keys = w.hit_pix;
-                hs.slot_div = npix;
-                Epilogue he{};
-                he.mode = EPI_PIXELS;
-                he.act = ACT_TANH01;
-                he.out = k.rgb;
-                he.pix = w.hit_pix;
-                st = run_mlp_tc(ctx, ctx->net[1], hs, (int64_t)S * npix, Map{}, Map{}, Calib{}, he,
-                                s3, w.d_hits);
+                st = colour_pass(s3);
                 cudaGraph_t out = nullptr;
                 const cudaError_t ee = cudaStreamEndCapture(s3, &out);
                 if (st == PIFU_OK && ee != cudaSuccess) st = PIFU_ERR_CUDA;
             }
             w.launches_colour = launches_now(ctx) - before_colour;
+        } else if (st == PIFU_OK &&
+                   cudaMemsetAsync(w.d_hits, 0, sizeof(unsigned int), sb) != cudaSuccess) {
+            st = PIFU_ERR_CUDA;   // no colour: the hit list starts empty every round
         }
+        if (st == PIFU_OK && launch_stream_render(w.sv, S, N_fine, ra, sb) != cudaSuccess)
+            st = PIFU_ERR_CUDA;
+        ctx->prof.k[PIFU_K_RENDER].launches += 3;
         // 5. every slot one step further; the loop condition
         a.init = 0;
         if (st == PIFU_OK && launch_stream_sched(a, sb) != cudaSuccess) st = PIFU_ERR_CUDA;
@@ -300,6 +314,11 @@ int g_enqueue_stream(pifu_ctx* ctx, const StreamKey& k) {
     if (st != PIFU_OK) return st;
     if (ee != cudaSuccess) return fail_cuda(ctx, ee);
     w.launches_body = launches_now(ctx) - before - w.launches_colour;
+    if (k.rgb) {
+        // the colour of the hits the loop left
+        st = colour_pass(s);
+        if (st != PIFU_OK) return st;
+    }
     CK(cudaMemcpyAsync(w.h_ctl, w.d_ctl, sizeof(StreamCtl), cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(w.h_fs, w.d_fs, sizeof(StreamFrameStats) * (size_t)k.F,
                        cudaMemcpyDeviceToHost, s));
@@ -471,10 +490,10 @@ int pifu_stream(pifu_ctx* ctx, int F, const pifu_fmap* occ_maps, const pifu_fmap
     CK(cudaGraphLaunch(w.exec, s));
     CK(cudaStreamSynchronize(s));
     const StreamCtl& ctl = *w.h_ctl;
-    // graph: counted in one class; the colour pass runs in the rounds with hits
+    // graph: counted in one class; the deferred colour pass runs when it fired
     ctx->prof.k[PIFU_K_MLP_HIDDEN].launches += w.launches_fixed +
                                               w.launches_body * (int64_t)ctl.rounds +
-                                              w.launches_colour * (int64_t)ctl.render_rounds;
+                                              w.launches_colour * (int64_t)ctl.colour_passes;
     // the last frame each slot held keeps its volume there
     std::vector<int> last(slots, -1);
     for (int f = 0; f < F; ++f) {
