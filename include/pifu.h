@@ -63,11 +63,12 @@ typedef enum { PIFU_F32 = 0, PIFU_BF16 = 1 } pifu_dtype;
  * tensor cores, BF16 weights and activations, FP32 accumulation.  MIXED:
  * BF16, then every occupancy within `margin` of 0.5 evaluated again in FP32
  * (the decision threshold is where low precision can change a result).
- * FP8: as BF16, but f_O's leading hidden layers with at least 512 outputs
- * (at full size the 1024- and 512-wide layers, 78% of its arithmetic) take
- * E4M3 operands with per-output-channel weight scales and per-tensor
- * activation scales (kind::f8f6f4, FP32 accumulation); needs
- * pifu_calibrate_fp8 first.  FP8_MIXED: FP8, then the FP32 re-evaluation of
+ * FP8: as BF16, but among f_O's leading hidden layers with at least 512
+ * outputs (at full size the 1024- and 512-wide layers, 78% of its
+ * arithmetic) the first writes its output in E4M3 (per-tensor scale), and
+ * each later one reads it as E4M3 operands against E4M3 weights
+ * (per-output-channel scales; kind::f8f6f4) while its input-row columns stay
+ * BF16, all with FP32 accumulation; needs pifu_calibrate_fp8 first.  FP8_MIXED: FP8, then the FP32 re-evaluation of
  * MIXED.  The colour MLP runs in BF16 in the FP8 forms. */
 typedef enum {
     PIFU_PREC_FP32 = 0,
@@ -392,18 +393,19 @@ int pifu_set_schedule(pifu_ctx* ctx, int schedule);
 int pifu_set_tiles(pifu_ctx* ctx, const int32_t* codes, int n);
 
 /* ---- FP8 form of f_O (not in the paper) --------------------------------------
- * Calibrates and builds the E4M3 layers used by PIFU_PREC_FP8 and
- * PIFU_PREC_FP8_MIXED: f_O's input rows x and first hidden outputs are
+ * Calibrates and builds the FP8 layers used by PIFU_PREC_FP8 and
+ * PIFU_PREC_FP8_MIXED: f_O's hidden outputs that an E4M3 layer reads are
  * evaluated in FP32 at the (n0+1)^3 nodes of the dense coarsest grid of this
- * feature map and calibration; the activation scales are their absolute
- * maxima / 448 (the largest E4M3 value; larger values saturate), the weight
- * scales the per-output-channel absolute maxima / 448 (the x columns of a
- * layer that also reads h are first multiplied by s_x / s_h so that both
- * segments share one accumulator scale).  The scales stay with the context
- * until the next call.  Synchronises `stream`.
+ * feature map and calibration; their activation scales are their absolute
+ * maxima / 448 (the largest E4M3 value; larger values saturate).  A later
+ * layer's E4M3 weights are divided by their per-output-channel absolute
+ * maxima / 448 (s_w), its BF16 input-row weights by s_w times the scale of
+ * its E4M3 input, so that both segments share one accumulator, multiplied
+ * back in the epilogue.  The scales stay with the context until the next
+ * call.  Synchronises `stream`.
  * Errors: PIFU_ERR_ARG (map/calibration/n0), PIFU_ERR_UNSUPPORTED (f_O has no
- * tensor-core form, or no leading hidden layer with >= 512 outputs whose
- * widths are multiples of 128), PIFU_ERR_CUDA / PIFU_ERR_OOM. */
+ * tensor-core form, or fewer than two leading hidden layers with >= 512
+ * outputs whose widths are multiples of 128), PIFU_ERR_CUDA / PIFU_ERR_OOM. */
 int pifu_calibrate_fp8(pifu_ctx* ctx, const pifu_fmap* occ_map, const float calib[12], int n0,
                        void* stream);
 

@@ -350,9 +350,6 @@ int encode_act_maps(pifu_ctx* ctx, DevNet& net) {
         }
     }
     if (net.f8_ok) {
-        if (!tc_encode_2d_u8(&net.tmX8, ctx->X8, (uint64_t)ctx->ldx8, rows, (uint64_t)ctx->ldx8,
-                             128, 128))
-            return PIFU_ERR_CUDA;
         for (size_t l = 1; l < net.f8.size(); ++l) {
             const DevLayer& Ly = net.layers[l];
             if (!tc_encode_2d_u8(&net.f8[l].tmA1, ctx->Hb[(l - 1) % 2], (uint64_t)Ly.K1, rows,
@@ -384,7 +381,6 @@ int ensure_tc_rows(pifu_ctx* ctx, int64_t rows) {
     dev_free(ctx->Xb);
     dev_free(ctx->Hb[0]);
     dev_free(ctx->Hb[1]);
-    dev_free(ctx->X8);
     dev_free(ctx->chain_dep);
     ctx->tc_rows = 0;
     CK(dev_alloc(&ctx->chain_dep, (int64_t)kChainMaxLayers * (cap / 128) + 2));
@@ -392,10 +388,6 @@ int ensure_tc_rows(pifu_ctx* ctx, int64_t rows) {
     CK(dev_alloc(&ctx->Xb, need_x * cap));
     CK(dev_alloc(&ctx->Hb[0], need_h * cap));
     CK(dev_alloc(&ctx->Hb[1], need_h * cap));
-    if (ctx->ldx8 > 0) {
-        CK(dev_alloc(&ctx->X8, (int64_t)ctx->ldx8 * cap));
-        CK(cudaMemset(ctx->X8, 0, (size_t)ctx->ldx8 * cap));
-    }
     ctx->tc_rows = cap;
     return encode_all_act_maps(ctx);
 }
@@ -444,26 +436,33 @@ uint8_t e4m3_byte(float v) {
     return (uint8_t)__nv_cvt_float_to_fp8(v, __NV_SATFINITE, __NV_E4M3);
 }
 
-// The E4M3 layers 0 .. F-1 of `net` from its FP32 weights (read back from the
-// device) and the activation scales: net.s_x for the input rows, s_h[l] for
-// h_l (the output of layer l, l < F-1).  The input rows enter as two E4M3
-// terms (x / s_x ~ hi + lo / 16), so a layer's x columns appear twice: once
-// against hi and once, divided by 16, against lo.
+// The FP8 layers 0 .. F-1 of `net` (F >= 2; Fp8Layer), from its FP32 and
+// BF16 weights and the activation scales s_h[l] of h_l, l < F-1.
 int build_fp8(pifu_ctx* ctx, DevNet& net, int F, const std::vector<float>& s_h) {
     free_f8(net);
-    const int kx8 = ctx->kx8;
-    const int nk2 = 2 * kx8 / 128;
     net.f8.assign((size_t)F, Fp8Layer{});
     for (int l = 0; l < F; ++l) {
         const DevLayer& Ly = net.layers[(size_t)l];
+        const TcLayer& T = net.tc[(size_t)l];
         Fp8Layer& Q = net.f8[(size_t)l];
+        Q.BN = T.BN;
+        Q.out_scale = l + 1 < F ? 1.f / s_h[(size_t)l] : 1.f;
+        Q.nk2 = T.nk2;
+        if (l == 0) {
+            // the BF16 operands of the tensor-core form, its own tile map
+            Q.bf16_in = true;
+            Q.nk1 = T.nk1;
+            Q.Kw = T.Kw;
+            Q.Wmap = T.W;
+            if (!tc_encode_2d_bf16(&Q.tmW, T.W, (uint64_t)T.Kw, (uint64_t)Ly.n_out,
+                                   (uint64_t)T.Kw * 2, 64, (uint32_t)Q.BN))
+                return PIFU_ERR_CUDA;
+            continue;
+        }
         const bool has_x = Ly.K2 > 0;
         Q.nk1 = Ly.K1 / 128;
-        Q.nk2 = has_x ? nk2 : 0;
-        Q.Kw = Ly.K1 + (has_x ? 2 * kx8 : 0);
-        Q.BN = net.tc[(size_t)l].BN;
-        const float s_a = l == 0 ? net.s_x : s_h[(size_t)l - 1];
-        const float xf = has_x ? net.s_x / s_a : 0.f;   // x columns in units of s_a
+        Q.Kw = Ly.K1 + Q.nk2 * 128;   // bytes
+        const float s_a = s_h[(size_t)l - 1];
         std::vector<float> wf((size_t)Ly.n_out * Ly.ldw);
         CK(cudaMemcpy(wf.data(), Ly.W, wf.size() * 4, cudaMemcpyDeviceToHost));
         std::vector<uint8_t> w8((size_t)Ly.n_out * Q.Kw, 0);
@@ -472,16 +471,13 @@ int build_fp8(pifu_ctx* ctx, DevNet& net, int F, const std::vector<float>& s_h) 
             const float* row = &wf[(size_t)o * Ly.ldw];
             float amax = 0.f;
             for (int k = 0; k < Ly.K1; ++k) amax = std::max(amax, std::fabs(row[k]));
-            if (has_x)
-                for (int k = 0; k < net.d_in; ++k)
-                    amax = std::max(amax, std::fabs(row[Ly.K1 + k] * xf));
             const float sw = amax > 0.f ? amax / 448.f : 1.f;
             uint8_t* dst = &w8[(size_t)o * Q.Kw];
             for (int k = 0; k < Ly.K1; ++k) dst[k] = e4m3_byte(row[k] / sw);
             if (has_x)
                 for (int k = 0; k < net.d_in; ++k) {
-                    dst[Ly.K1 + k] = e4m3_byte(row[Ly.K1 + k] * xf / sw);
-                    dst[Ly.K1 + kx8 + k] = e4m3_byte(row[Ly.K1 + k] * xf / (16.f * sw));
+                    const __nv_bfloat16 v = __float2bfloat16(row[Ly.K1 + k] / (s_a * sw));
+                    std::memcpy(dst + Ly.K1 + 2 * k, &v, 2);
                 }
             cs[(size_t)o] = sw * s_a;
         }
@@ -489,10 +485,10 @@ int build_fp8(pifu_ctx* ctx, DevNet& net, int F, const std::vector<float>& s_h) 
         CK(dev_alloc(&Q.colscale, (int64_t)cs.size()));
         CK(cudaMemcpy(Q.W, w8.data(), w8.size(), cudaMemcpyHostToDevice));
         CK(cudaMemcpy(Q.colscale, cs.data(), cs.size() * 4, cudaMemcpyHostToDevice));
+        Q.Wmap = Q.W;
         if (!tc_encode_2d_u8(&Q.tmW, Q.W, (uint64_t)Q.Kw, (uint64_t)Ly.n_out, (uint64_t)Q.Kw, 128,
                              (uint32_t)Q.BN))
             return PIFU_ERR_CUDA;
-        Q.out_scale = l + 1 < F ? 1.f / s_h[(size_t)l] : 1.f;
     }
     net.f8_ok = true;
     ++net.f8_version;
@@ -509,21 +505,9 @@ int calibrate_fp8(pifu_ctx* ctx, const Map& map, const Calib& cal, int n0, cudaS
     while (F + 1 < L && net.layers[(size_t)F].n_out >= 512 &&
            net.layers[(size_t)F].n_out % 128 == 0 && net.layers[(size_t)F].K1 % 128 == 0)
         ++F;
-    if (F == 0) return PIFU_ERR_UNSUPPORTED;
-    // [x_hi | x_lo], each padded to whole 128-byte K-blocks; the padding
-    // stays zero (the gather writes only the first ldx bytes of each half)
-    const int kx8 = round_up(std::max(net.d_in, net.ldx), 128);
+    if (F < 2) return PIFU_ERR_UNSUPPORTED;   // a first layer and one that reads it in E4M3
     int st0 = ensure_tc_rows(ctx, 1);
     if (st0 != PIFU_OK) return st0;
-    if (!ctx->X8 || ctx->ldx8 != 2 * kx8) {
-        invalidate_graphs(ctx);
-        dev_free(ctx->X8);
-        ctx->ldx8 = ctx->kx8 = 0;
-        CK(dev_alloc(&ctx->X8, (int64_t)2 * kx8 * ctx->tc_rows));
-        CK(cudaMemset(ctx->X8, 0, (size_t)2 * kx8 * ctx->tc_rows));
-        ctx->ldx8 = 2 * kx8;
-        ctx->kx8 = kx8;
-    }
     unsigned int* d_amax = nullptr;
     CK(cudaMalloc(&d_amax, sizeof(unsigned int) * (size_t)F));
     cudaError_t e = cudaMemsetAsync(d_amax, 0, sizeof(unsigned int) * (size_t)F, s);

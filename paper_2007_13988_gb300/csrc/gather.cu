@@ -54,38 +54,6 @@ __global__ void __launch_bounds__(256) gather_kernel(PointSrc src, int64_t p0, i
     }
 }
 
-// The same rows twice: BF16 into X, and as two E4M3 terms into X8: with
-// v = x / s (times inv_s), hi = e4m3(v) at byte c and lo = e4m3(16 (v - hi))
-// at byte lo_off + c, so that x ~ s (hi + lo / 16) keeps about twice the
-// mantissa bits of one E4M3 value (row stride ldx8 >= lo_off + ldx bytes).
-__global__ void __launch_bounds__(256) gather_dual_kernel(PointSrc src, int64_t p0, int64_t m,
-                                                          Calib calib, Map map0, Map map1,
-                                                          __nv_bfloat16* __restrict__ X, int ldx,
-                                                          uint8_t* __restrict__ X8, int ldx8,
-                                                          int lo_off, float inv_s) {
-    const uint32_t nq = (uint32_t)ldx >> 2;
-    if (src.count) m = min(m, (int64_t)*src.count);
-    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < m * nq;
-         t += (int64_t)gridDim.x * blockDim.x) {
-        const uint32_t lp = (uint32_t)t / nq;
-        const int c = (int)((uint32_t)t - lp * nq) * 4;
-        const float4 r = gather_quad(src, p0 + lp, calib, map0, map1, c);
-        store4(X + (int64_t)lp * ldx + c, r);
-        const float v[4] = {r.x * inv_s, r.y * inv_s, r.z * inv_s, r.w * inv_s};
-        uint32_t hw = 0, lw = 0;
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const __nv_fp8_e4m3 h(v[j]);   // round to nearest, saturating
-            const __nv_fp8_e4m3 l(16.f * (v[j] - static_cast<float>(h)));
-            hw |= (uint32_t)h.__x << (8 * j);
-            lw |= (uint32_t)l.__x << (8 * j);
-        }
-        uint8_t* row = X8 + (int64_t)lp * ldx8;
-        *reinterpret_cast<uint32_t*>(row + c) = hw;
-        *reinterpret_cast<uint32_t*>(row + lo_off + c) = lw;
-    }
-}
-
 // One thread per (point, 4 channels); a device-resident count gets a fixed,
 // SM-filling grid that strides over whatever the count turns out to be.
 inline unsigned gather_blocks(const PointSrc& src, int64_t total) {
@@ -112,19 +80,6 @@ cudaError_t launch_gather_bf16(const PointSrc& src, int64_t p0, int64_t m, const
     const int64_t total = m * ((ldx / 4 + kQPT - 1) / kQPT);
     gather_kernel<__nv_bfloat16><<<gather_blocks(src, total), 256, 0, stream>>>(src, p0, m, calib,
                                                                                map0, map1, X, ldx);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_gather_dual(const PointSrc& src, int64_t p0, int64_t m, const Calib& calib,
-                               const Map& map0, const Map& map1, __nv_bfloat16* X, int ldx,
-                               uint8_t* X8, int ldx8, int lo_off, float inv_s,
-                               cudaStream_t stream) {
-    if (m <= 0) return cudaSuccess;
-    if (lo_off < ldx || ldx8 < lo_off + ldx || ldx8 % 16 || lo_off % 16)
-        return cudaErrorInvalidValue;
-    const int64_t total = m * (ldx / 4);
-    gather_dual_kernel<<<gather_blocks(src, total), 256, 0, stream>>>(
-        src, p0, m, calib, map0, map1, X, ldx, X8, ldx8, lo_off, inv_s);
     return cudaGetLastError();
 }
 

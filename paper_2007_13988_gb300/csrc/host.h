@@ -52,13 +52,20 @@ struct TcLayer {
     bool tmO_ok = false;
 };
 
-// E4M3 form of one of f_O's leading wide hidden layers: W divided by a
-// per-output-channel scale s_w[n] (the x columns first multiplied by
-// s_x / s_a), the accumulator multiplied back by colscale[n] = s_w[n] s_a.
+// FP8 form of one of f_O's leading wide hidden layers.  Layer 0 keeps the
+// BF16 operands of the tensor-core form and rounds its output to E4M3
+// (multiplied by out_scale = 1 / s of the next layer's input).  A later layer
+// reads that E4M3 output against E4M3 weights W_h / s_w[n] (s_w[n]: the
+// per-output-channel absolute maximum / 448) and the BF16 input rows against
+// BF16 weights W_x / (s_a s_w[n]), into one FP32 accumulator that the
+// epilogue multiplies by colscale[n] = s_w[n] s_a (s_a: the per-tensor scale
+// of its E4M3 input).
 struct Fp8Layer {
-    uint8_t* W = nullptr;        // [n_out][Kw] E4M3 bytes, x segment zero-padded
-    float* colscale = nullptr;   // [n_out]
-    int Kw = 0, nk1 = 0, nk2 = 0, BN = 0;
+    bool bf16_in = false;        // layer 0: W and tmW are over the BF16 weights
+    uint8_t* W = nullptr;        // later layers: [n_out][Kw] bytes, E4M3 h part then BF16 x part
+    const void* Wmap = nullptr;  // the weights tmW covers
+    float* colscale = nullptr;   // [n_out] (later layers)
+    int Kw = 0, nk1 = 0, nk2 = 0, BN = 0;   // Kw: row width in the map's elements
     float out_scale = 1.f;       // E4M3 output: 1 / s of the next layer's input
     CUtensorMap tmW{};
     CUtensorMap tmA1{};          // the previous layer's E4M3 output (layer >= 1)
@@ -81,9 +88,8 @@ struct DevNet {
     // FP8 form (pifu_calibrate_fp8): the first f8.size() hidden layers
     bool f8_ok = false;
     std::vector<Fp8Layer> f8;
-    float s_x = 0.f;                // per-tensor scale of the input rows
+    float s_x = 0.f;                // per-tensor scale of the input rows (reported)
     uint64_t f8_version = 0;        // bumped by every calibration
-    CUtensorMap tmX8{};             // E4M3 gather rows as the A operand
 };
 
 constexpr int kNetCbn = 2;   // DevNet.kind of the CBN + SoftZ occupancy network
@@ -373,10 +379,7 @@ struct pifu_ctx {
     unsigned int* chain_dep = nullptr;   // [kChainMaxLayers][tc_rows / 128] tile-part counters,
                                          // the tile counter and the finished-CTA counter
     bool chain_on = false;               // pifu_set_schedule
-    int64_t tc_rows = 0;            // rows of Xb, Hb[], X8 (grown on demand up to kChunkTC)
-    uint8_t* X8 = nullptr;          // [tc_rows][ldx8] E4M3 gather rows (FP8 forms):
-    int ldx8 = 0;                   //   x_hi at [0, kx8), x_lo at [kx8, 2 kx8)
-    int kx8 = 0;
+    int64_t tc_rows = 0;            // rows of Xb, Hb[] (grown on demand up to kChunkTC)
     float* part = nullptr;            // split-K partial sums of small FP32 batches
     int64_t part_cap = 0;
     // level workspace, sized for ws_N

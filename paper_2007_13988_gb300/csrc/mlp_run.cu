@@ -44,13 +44,9 @@ int run_mlp_tc(pifu_ctx* ctx, const DevNet& net, const PointSrc& src_in, int64_t
     for (int64_t p0 = 0; p0 < m; p0 += chunk) {
         const int64_t mc = std::min<int64_t>(chunk, m - p0);
         cudaEvent_t ev = pr.begin(s);
-        if (F > 0)
-            CK(launch_gather_dual(src, p0, mc, calib, map0, map1, ctx->Xb, net.ldx, ctx->X8,
-                                  ctx->ldx8, ctx->kx8, 1.f / net.s_x, s));
-        else
-            CK(launch_gather_bf16(src, p0, mc, calib, map0, map1, ctx->Xb, net.ldx, s));
+        CK(launch_gather_bf16(src, p0, mc, calib, map0, map1, ctx->Xb, net.ldx, s));
         pr.end(PIFU_K_GATHER, ev, s, 0.0,
-               (double)mc * (4.0 * 4.0 * (map0.C + map1.C) + (F > 0 ? 3.0 : 2.0) * net.ldx));
+               (double)mc * (4.0 * 4.0 * (map0.C + map1.C) + 2.0 * net.ldx));
         // the last layer rides in the last hidden layer's epilogue when that
         // layer is one tile wide and the last layer reads only its output
         const DevLayer& Ll = net.layers[L - 1];
@@ -132,16 +128,18 @@ int run_mlp_tc(pifu_ctx* ctx, const DevNet& net, const PointSrc& src_in, int64_t
             a.fuse = (fuse && l == L - 2) ? &fl : nullptr;
             a.mode = TC_BF16;
             if (l < F) {
-                // E4M3 operands; the last E4M3 layer hands BF16 to the next one
+                // the FP8 form (Fp8Layer): layer 0 BF16 in, E4M3 out; later
+                // layers E4M3 h and BF16 x into one accumulator, E4M3 out but
+                // for the last, which hands BF16 to the next layer
                 const Fp8Layer& Q = net.f8[(size_t)l];
-                a.tmA1 = l > 0 ? &Q.tmA1 : &net.tmX8;
-                a.tmA2 = &net.tmX8;
+                a.tmA1 = l > 0 ? &Q.tmA1 : &net.tmX;
+                a.tmA2 = &net.tmX;
                 a.tmW = &Q.tmW;
                 a.nk1 = Q.nk1;
                 a.nk2 = Q.nk2;
                 a.BN = Q.BN;
                 a.pair = 0;
-                a.mode = l + 1 < F ? TC_E4M3_E4M3 : TC_E4M3_BF16;
+                a.mode = l == 0 ? TC_BF16_E4M3 : (l + 1 < F ? TC_MIX_E4M3 : TC_MIX_BF16);
                 a.colscale = Q.colscale;
                 a.out_scale = Q.out_scale;
                 if (a.fuse) return PIFU_ERR_UNSUPPORTED;

@@ -5,11 +5,14 @@
 //
 //   out[M][N] = lrelu( s[n] ([H | X][M][K] * W[N][K]^T) + b )
 //
-// BF16 mode: s = 1, BF16 out.  E4M3 modes (kind::f8f6f4): the operands are
-// stored divided by their scales (per-tensor for activations, per output
-// channel for weights), s[n] multiplies the two back, and the output is BF16
-// or E4M3 again (multiplied by the next layer's inverse activation scale).
-// One K-block is 128 bytes of a row in both: 64 BF16 or 128 E4M3 values.
+// BF16 modes: s = 1, BF16 operands, BF16 or E4M3 out (the latter multiplied
+// by the next layer's inverse activation scale).  Mixed modes (the FP8 form's
+// later layers): H in E4M3 against E4M3 weights (kind::f8f6f4), both stored
+// divided by their scales (per tensor for H, per output channel for W), then
+// X in BF16 against BF16 weights divided by the same two scales (kind::f16),
+// all into one FP32 accumulator that s[n] multiplies back; BF16 or E4M3 out.
+// One K-block is 128 bytes of a row in every mode: 64 BF16 or 128 E4M3
+// values.
 //
 // The skip concatenation [h_{l-1}, x] is fused as two K segments: the TMA
 // producer fetches A tiles from the H tensor map for the first nk1 K-blocks
@@ -96,7 +99,13 @@ __global__ void __launch_bounds__(kThreads, 1) tc_linear_kernel(
     const unsigned int* __restrict__ m_dev, FuseLast fl, const float* __restrict__ colscale,
     float out_scale) {
     static_assert(!(FUSE && MODE != TC_BF16), "the fused last layer reads BF16 activations");
-    constexpr int TBKE = MODE == TC_BF16 ? TBK : 2 * TBK;   // elements per 128-byte K-block
+    constexpr bool MIX = MODE == TC_MIX_E4M3 || MODE == TC_MIX_BF16;
+    constexpr bool OUT8 = MODE == TC_BF16_E4M3 || MODE == TC_MIX_E4M3;
+    // elements per 128-byte K-block: A1 (E4M3 in the mixed modes), A2 (BF16),
+    // W (a byte matrix in the mixed modes)
+    constexpr int E1 = MIX ? 2 * TBK : TBK;
+    constexpr int E2 = TBK;
+    constexpr int EW = MIX ? 2 * TBK : TBK;
     constexpr uint32_t A_BYTES = TBM * TBK * 2;
     constexpr uint32_t B_BYTES = BN * TBK * 2;
     constexpr uint32_t TMEM_COLS = 2 * BN;   // two accumulators; 128, 256 or 512
@@ -143,7 +152,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_linear_kernel(
     }
     for (int c = threadIdx.x; c < N; c += blockDim.x) {
         sbias[c] = bias[c];
-        scol[c] = MODE == TC_BF16 ? 1.f : colscale[c];
+        scol[c] = MIX ? colscale[c] : 1.f;
     }
     if (FUSE) {
         for (int c = threadIdx.x; c < fl.n_out * BN; c += blockDim.x)
@@ -177,18 +186,18 @@ __global__ void __launch_bounds__(kThreads, 1) tc_linear_kernel(
                     }
                     mbar_arrive_expect_tx(&full[s], A_BYTES + B_BYTES);
                     if (kb < nk1)
-                        tma_load_2d(sA + s * A_BYTES, &tmA1, kb * TBKE, m0, &full[s]);
+                        tma_load_2d(sA + s * A_BYTES, &tmA1, kb * E1, m0, &full[s]);
                     else
-                        tma_load_2d(sA + s * A_BYTES, &tmA2, (kb - nk1) * TBKE, m0, &full[s]);
-                    tma_load_2d(sB + s * B_BYTES, &tmW, kb * TBKE, n0, &full[s]);
+                        tma_load_2d(sA + s * A_BYTES, &tmA2, (kb - nk1) * E2, m0, &full[s]);
+                    tma_load_2d(sB + s * B_BYTES, &tmW, kb * EW, n0, &full[s]);
                 }
             }
         }
     } else if (warp == 1) {
         if (lane == 0) {
             // MMA issuer
-            constexpr uint32_t idesc =
-                MODE == TC_BF16 ? idesc_bf16_f32(TBM, BN) : idesc_e4m3_f32(TBM, BN);
+            constexpr uint32_t idesc16 = idesc_bf16_f32(TBM, BN);
+            constexpr uint32_t idesc8 = idesc_e4m3_f32(TBM, BN);
             uint32_t g = 0, i = 0;
             for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x, ++i) {
                 const uint32_t b = i & 1u, j = i >> 1;
@@ -209,14 +218,15 @@ __global__ void __launch_bounds__(kThreads, 1) tc_linear_kernel(
                     const uint32_t a0 = smem_u32(sA + s * A_BYTES);
                     const uint32_t b0 = smem_u32(sB + s * B_BYTES);
                     // 4 MMAs of 32 bytes of K each (16 BF16 or 32 E4M3 values)
+                    const bool f8 = MIX && kb < nk1;
 #pragma unroll
                     for (int k = 0; k < 4; ++k) {
-                        if (MODE == TC_BF16)
-                            mma_bf16(d, desc_k_sw128(a0 + k * 32), desc_k_sw128(b0 + k * 32),
-                                     idesc, (kb | k) != 0 ? 1u : 0u);
-                        else
+                        if (f8)
                             mma_e4m3(d, desc_k_sw128(a0 + k * 32), desc_k_sw128(b0 + k * 32),
-                                     idesc, (kb | k) != 0 ? 1u : 0u);
+                                     idesc8, (kb | k) != 0 ? 1u : 0u);
+                        else
+                            mma_bf16(d, desc_k_sw128(a0 + k * 32), desc_k_sw128(b0 + k * 32),
+                                     idesc16, (kb | k) != 0 ? 1u : 0u);
                     }
                     mma_commit(&empty[s]);
                 }
@@ -271,7 +281,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_linear_kernel(
                         for (int jo = 0; jo < 4; ++jo)
                             if (jo < fl.n_out) part[jo] = fmaf(a, sW5[jo * BN + c0 + cc], part[jo]);
                     }
-                } else if (MODE == TC_E4M3_E4M3) {
+                } else if (OUT8) {
                     // 64 E4M3 values = 64 bytes of the row: one staged pass
                     uint4 pk4[4];
 #pragma unroll
@@ -311,7 +321,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_linear_kernel(
                             for (int jj = 0; jj < 4; ++jj) {
                                 const int cc = hb * 32 + v * 8 + 2 * jj;
                                 float a, c;
-                                if (MODE == TC_BF16) {
+                                if (!MIX) {
                                     a = __uint_as_float(r[cc]) + bb[c0 + cc];
                                     c = __uint_as_float(r[cc + 1]) + bb[c0 + cc + 1];
                                 } else {
@@ -649,9 +659,11 @@ cudaError_t ensure_attr(int dev) {
     cudaError_t e = cudaFuncSetAttribute(tc_linear_kernel<BN, false, TC_BF16>, at, bytes);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(tc_linear_kernel<BN, true, TC_BF16>, at, bytes);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(tc_linear_kernel<BN, false, TC_E4M3_E4M3>, at, bytes);
+        e = cudaFuncSetAttribute(tc_linear_kernel<BN, false, TC_BF16_E4M3>, at, bytes);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(tc_linear_kernel<BN, false, TC_E4M3_BF16>, at, bytes);
+        e = cudaFuncSetAttribute(tc_linear_kernel<BN, false, TC_MIX_E4M3>, at, bytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(tc_linear_kernel<BN, false, TC_MIX_BF16>, at, bytes);
     if (e == cudaSuccess && dev >= 0 && dev < 64) g_attr_set[bn_index(BN)][dev] = true;
     return e;
 }
@@ -679,7 +691,9 @@ cudaError_t launch_bn(const TcLayerArgs& a, cudaStream_t s) {
     const long long tiles = (long long)(a.N / BN) * ((a.M + TBM - 1) / TBM);
     const int grid = (int)(tiles < sms ? tiles : sms);
     const uint32_t smem = tc_smem_bytes(BN);
-    if (a.mode != TC_BF16 && (a.fuse || !a.colscale)) return cudaErrorInvalidValue;
+    if (a.mode != TC_BF16 && a.fuse) return cudaErrorInvalidValue;
+    if ((a.mode == TC_MIX_E4M3 || a.mode == TC_MIX_BF16) && !a.colscale)
+        return cudaErrorInvalidValue;
     // programmatic dependent launch: the prologue overlaps the previous kernel
     cudaLaunchConfig_t cfg{};
     cfg.gridDim = dim3((unsigned)grid);
@@ -701,13 +715,18 @@ cudaError_t launch_bn(const TcLayerArgs& a, cudaStream_t s) {
                                   *a.tmW, tmO, 0, a.nk1, a.nk2, a.M, a.N, a.bias, a.slope, a.out,
                                   a.ldo, a.err, a.m_dev, *a.fuse, noscale, 1.f);
     }
-    if (a.mode == TC_E4M3_E4M3)
-        return cudaLaunchKernelEx(&cfg, tc_linear_kernel<BN, false, TC_E4M3_E4M3>, *a.tmA1,
+    if (a.mode == TC_BF16_E4M3)
+        return cudaLaunchKernelEx(&cfg, tc_linear_kernel<BN, false, TC_BF16_E4M3>, *a.tmA1,
+                                  *a.tmA2, *a.tmW, tmO, 0, a.nk1, a.nk2, a.M, a.N, a.bias,
+                                  a.slope, a.out, a.ldo, a.err, a.m_dev, FuseLast{}, noscale,
+                                  a.out_scale);
+    if (a.mode == TC_MIX_E4M3)
+        return cudaLaunchKernelEx(&cfg, tc_linear_kernel<BN, false, TC_MIX_E4M3>, *a.tmA1,
                                   *a.tmA2, *a.tmW, tmO, 0, a.nk1, a.nk2, a.M, a.N, a.bias,
                                   a.slope, a.out, a.ldo, a.err, a.m_dev, FuseLast{}, a.colscale,
                                   a.out_scale);
-    if (a.mode == TC_E4M3_BF16)
-        return cudaLaunchKernelEx(&cfg, tc_linear_kernel<BN, false, TC_E4M3_BF16>, *a.tmA1,
+    if (a.mode == TC_MIX_BF16)
+        return cudaLaunchKernelEx(&cfg, tc_linear_kernel<BN, false, TC_MIX_BF16>, *a.tmA1,
                                   *a.tmA2, *a.tmW, tmO, use_tmo, a.nk1, a.nk2, a.M, a.N, a.bias,
                                   a.slope, a.out, a.ldo, a.err, a.m_dev, FuseLast{}, a.colscale,
                                   1.f);

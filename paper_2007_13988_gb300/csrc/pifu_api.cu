@@ -107,7 +107,6 @@ void pifu_destroy(pifu_ctx* ctx) {
     dev_free(ctx->Xb);
     dev_free(ctx->Hb[0]);
     dev_free(ctx->Hb[1]);
-    dev_free(ctx->X8);
     dev_free(ctx->chain_dep);
     dev_free(ctx->part);
     uint32_t** bitsets[] = {&ctx->cand, &ctx->tent, &ctx->bin[0], &ctx->bin[1],

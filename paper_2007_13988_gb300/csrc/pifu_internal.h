@@ -151,15 +151,9 @@ cudaError_t launch_gather(const PointSrc& src, int64_t p0, int64_t m, const Cali
                           const Map& map0, const Map& map1, float* X, int ldx,
                           cudaStream_t stream);
 
-// Same rows in BF16 (the tensor-core MLP's A operand); ldx a multiple of 8.
-// BF16 rows into X and, as two E4M3 terms of x inv_s (hi at byte c, lo =
-// 16 x the remainder at byte lo_off + c), into X8.
-cudaError_t launch_gather_dual(const PointSrc& src, int64_t p0, int64_t m, const Calib& calib,
-                               const Map& map0, const Map& map1, __nv_bfloat16* X, int ldx,
-                               uint8_t* X8, int ldx8, int lo_off, float inv_s,
-                               cudaStream_t stream);
 // *out = max(*out, max_i |p[i]|) with *out holding float bits.
 cudaError_t launch_amax(const float* p, int64_t n, unsigned int* out, cudaStream_t stream);
+// Same rows in BF16 (the tensor-core MLP's A operand); ldx a multiple of 8.
 cudaError_t launch_gather_bf16(const PointSrc& src, int64_t p0, int64_t m, const Calib& calib,
                                const Map& map0, const Map& map1, __nv_bfloat16* X, int ldx,
                                cudaStream_t stream);
@@ -212,8 +206,15 @@ struct FuseLast {
 // Operand and output types of one tensor-core layer.
 enum TcMode : int {
     TC_BF16 = 0,       // BF16 A and W, BF16 out
-    TC_E4M3_E4M3 = 1,  // E4M3 A and W, E4M3 out (scaled by out_scale)
-    TC_E4M3_BF16 = 2,  // E4M3 A and W, BF16 out
+    TC_BF16_E4M3 = 1,  // BF16 A and W, E4M3 out (multiplied by out_scale first)
+    // Mixed layers: the A1 segment (the previous layer's output) in E4M3
+    // against E4M3 weights (kind::f8f6f4), then the A2 segment (the input
+    // rows x) in BF16 against BF16 weights (kind::f16), both into the same
+    // FP32 accumulator, which the epilogue multiplies by colscale[n].  W is a
+    // byte matrix: per row the E4M3 part (nk1 x 128 bytes), then the BF16
+    // part (nk2 x 64 values), each 128-byte K-block one TMA box.
+    TC_MIX_E4M3 = 2,   // E4M3 out (multiplied by out_scale first)
+    TC_MIX_BF16 = 3,   // BF16 out
 };
 struct TcLayerArgs {
     const CUtensorMap* tmA1;
@@ -233,7 +234,7 @@ struct TcLayerArgs {
     const FuseLast* fuse;        // optional: last layer fused (requires N == BN, TC_BF16)
     int mode;                    // TcMode
     const float* colscale;       // E4M3 modes: accumulator scale per output column
-    float out_scale;             // TC_E4M3_E4M3: output multiplied by this before rounding
+    float out_scale;             // E4M3 outputs: multiplied by this before rounding
 };
 cudaError_t launch_tc_linear(const TcLayerArgs& a, cudaStream_t stream);
 // Set the tensor-core kernels' attributes on the current device (before a

@@ -101,15 +101,17 @@ int autotune(pifu_ctx* ctx, int64_t rows, cudaStream_t s, int32_t* bn_out, doubl
             const bool f8 = net.f8_ok && l < (int)net.f8.size();
             if (f8) {
                 Fp8Layer& Q = net.f8[(size_t)l];
-                a.tmA1 = l > 0 ? &Q.tmA1 : &net.tmX8;
-                a.tmA2 = &net.tmX8;
+                const int F = (int)net.f8.size();
+                a.tmA1 = l > 0 ? &Q.tmA1 : &net.tmX;
+                a.tmA2 = &net.tmX;
                 a.nk1 = Q.nk1;
                 a.nk2 = Q.nk2;
-                a.mode = l + 1 < (int)net.f8.size() ? TC_E4M3_E4M3 : TC_E4M3_BF16;
+                a.mode = l == 0 ? TC_BF16_E4M3 : (l + 1 < F ? TC_MIX_E4M3 : TC_MIX_BF16);
                 a.colscale = Q.colscale;
                 a.out_scale = Q.out_scale;
                 double ms = 0.0;
-                st = tune_layer(ctx, a, Ly.n_out, true, false, &Q.tmW, Q.W, Q.Kw, &Q.BN, s, &ms);
+                st = tune_layer(ctx, a, Ly.n_out, !Q.bf16_in, false, &Q.tmW,
+                                const_cast<void*>(Q.Wmap), Q.Kw, &Q.BN, s, &ms);
                 if (st != PIFU_OK) return st;
                 record(Q.BN, ms);
             }
@@ -187,7 +189,8 @@ int set_tiles(pifu_ctx* ctx, const int32_t* codes, int n) {
         const int c = codes[i++];
         if (q) {
             q->BN = c;
-            ok = ok && encode_w(true, &q->tmW, q->W, q->Kw, n_out, c);
+            ok = ok && encode_w(!q->bf16_in, &q->tmW, const_cast<void*>(q->Wmap), q->Kw, n_out,
+                                c);
         } else {
             t->pair = c == kPairCode;
             t->BN = t->pair ? 256 : c;

@@ -83,7 +83,7 @@ def test_mixed_512_graph_frame(full, oracle512):
     assert psnr >= 40.0
 
 
-# ---- FP8 form: the 1024- and 512-wide layers in E4M3 ------------------------
+# ---- FP8 form: the 1024-wide layer's output and the 512-wide layer in E4M3 --
 
 @pytest.fixture(scope="module")
 def fp8(full):
@@ -96,11 +96,10 @@ def fp8(full):
 
 
 def test_fp8_query_error_is_bounded(fp8):
-    """E4M3 operands (3 mantissa bits) in the two widest layers, the input
-    rows as two E4M3 terms: the error of the occupancy against FP64 is bounded
-    in distribution (a CPU emulation of the same rounding gives p99 0.026 on
-    the localization's points; with x as one E4M3 term it was 0.09), and the
-    FP32 re-evaluation of FP8_MIXED restores the plain tolerance near 0.5."""
+    """E4M3 (3 mantissa bits) for the 1024-wide layer's output and the
+    512-wide layer's weights on it, the input rows in BF16: the error of the
+    occupancy against FP64 is bounded in distribution, and the FP32
+    re-evaluation of FP8_MIXED restores the plain tolerance near 0.5."""
     w = fp8.w
     P = synth.distill_points(w.fig, 20000, 99)
     o = field.occupancy(w.occ_net, w.occ_map, w.calib, P)
