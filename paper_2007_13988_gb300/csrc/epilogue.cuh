@@ -21,13 +21,7 @@ __device__ __forceinline__ void last_epilogue(const Epilogue& epi, int64_t p, in
     if (epi.recheck) {
         // mixed precision: defer occupancies close to the decision threshold
         const float o = apply_act(ACT_SIGMOID, t[0] + bias[0]);
-        bool defer = fabsf(o - kHalf) < epi.margin;
-        if (!defer && epi.finest_to_queue && epi.mode == EPI_LEVEL && epi.lv.sv) {
-            // frame stream, surrogate pass: a slot at its finest level runs f_O
-            const int64_t key = epi.list ? (int64_t)epi.list[p] : epi.base + p;
-            defer = epi.lv.sv[key / epi.lv.key_div].finest != 0;
-        }
-        if (defer) {
+        if (fabsf(o - kHalf) < epi.margin) {
             const unsigned pos = atomicAdd(epi.recheck_count, 1u);
             epi.recheck[pos] = (epi.mode == EPI_LEVEL || epi.mode == EPI_COLUMN)
                                    ? (epi.list ? epi.list[p] : (int)(epi.base + p))

@@ -57,18 +57,19 @@ int g_recheck(pifu_ctx* ctx, const DevNet& net, const PointSrc& src, int64_t cap
 int g_eval(pifu_ctx* ctx, const DevNet& net, const PointSrc& src, int64_t cap,
            const unsigned int* m_dev, const Map& map, const Calib& cal, const Epilogue& epi,
            int prec, float margin, unsigned long long* rechecked, cudaStream_t s,
-           bool sur, float sur_margin, unsigned long long* fallback) {
+           bool sur, float sur_margin, unsigned long long* fallback, int64_t qcap_in) {
     if (sur) {
-        CK(cudaMemsetAsync(ctx->d_squeue, 0, sizeof(unsigned int), s));
+        // qcap_in > 0: the f_O queue already holds keys (the frame stream's
+        // finest-level keys), f_S's fall-backs are appended after them
+        if (qcap_in <= 0) CK(cudaMemsetAsync(ctx->d_squeue, 0, sizeof(unsigned int), s));
         Epilogue es = epi;
         es.recheck = ctx->squeue;
         es.recheck_count = ctx->d_squeue;
         es.margin = sur_margin;
-        es.finest_to_queue = 1;   // frame stream: a slot at its finest level runs f_O
         int st = run_mlp_tc(ctx, ctx->snet, src, cap, map, Map{}, cal, es, s, m_dev);
         if (st != PIFU_OK) return st;
         // a queue longer than one device-sized batch latches a capacity error
-        const int64_t qcap = std::min<int64_t>(cap, kTcRowsMax);
+        const int64_t qcap = std::min<int64_t>(qcap_in > 0 ? qcap_in : cap, kTcRowsMax);
         CK(launch_accumulate(fallback, ctx->d_squeue, (unsigned)qcap, ctx->d_count + 1, s));
         PointSrc sf = src;   // keeps the frames' maps of a lockstep batch
         sf.mode = PTS_LIST;

@@ -651,7 +651,8 @@ int g_recheck(pifu_ctx* ctx, const DevNet& net, const PointSrc& src, int64_t cap
 int g_eval(pifu_ctx* ctx, const DevNet& net, const PointSrc& src, int64_t cap,
            const unsigned int* m_dev, const Map& map, const Calib& cal, const Epilogue& epi,
            int prec, float margin, unsigned long long* rechecked, cudaStream_t s,
-           bool sur = false, float sur_margin = 0.f, unsigned long long* fallback = nullptr);
+           bool sur = false, float sur_margin = 0.f, unsigned long long* fallback = nullptr,
+           int64_t qcap_in = 0);
 int g_add_while(pifu_ctx* ctx, cudaStream_t s, cudaGraphConditionalHandle h, cudaGraph_t* body);
 int g_enqueue_frame(pifu_ctx* ctx, const FrameKey& k, const Map& occ, const Map& col,
                     const Calib& cal);

@@ -341,7 +341,8 @@ __global__ void __launch_bounds__(256) expand_conflicts_kernel(
     int N0, uint32_t* __restrict__ eval0, int64_t key_div, int64_t slot_words,
     int* __restrict__ list, unsigned int* __restrict__ count, unsigned int cap,
     unsigned int* __restrict__ err, const SlotView* __restrict__ sv,
-    unsigned int* __restrict__ slot_count) {
+    unsigned int* __restrict__ slot_count, int* __restrict__ list_f,
+    unsigned int* __restrict__ count_f) {
     const unsigned int nc = min(*ccount, max_c);
     const int lane = threadIdx.x & 31;
     const int64_t total = (int64_t)nc * 26;
@@ -350,6 +351,7 @@ __global__ void __launch_bounds__(256) expand_conflicts_kernel(
          base_t += (int64_t)gridDim.x * blockDim.x) {
         const int64_t t = base_t + threadIdx.x;
         bool fresh = false;
+        bool to_f = false;   // frame stream: a key of a slot at its finest level
         int64_t nkey = 0;
         if (t < total) {
             const int64_t c = t / 26;
@@ -367,6 +369,7 @@ __global__ void __launch_bounds__(256) expand_conflicts_kernel(
             if (sv) {
                 N = sv[f].N;
                 eval = sv[f].eval;
+                to_f = list_f != nullptr && sv[f].finest != 0;
             }
             const int n1 = N + 1;
             const int rw = row_words_of(N);
@@ -386,15 +389,23 @@ __global__ void __launch_bounds__(256) expand_conflicts_kernel(
                 if (fresh && slot_count) atomicAdd(slot_count + f, 1u);
             }
         }
-        const unsigned ballot = __ballot_sync(0xffffffffu, fresh);
-        if (ballot == 0u) continue;
-        unsigned int b = 0u;
-        if (lane == 0) b = atomicAdd(count, (unsigned int)__popc(ballot));
-        b = __shfl_sync(0xffffffffu, b, 0);
-        if (fresh) {
-            const unsigned int pos = b + __popc(ballot & ((1u << lane) - 1u));
-            if (pos < cap) list[pos] = (int)nkey;
-            else atomicOr(err, kErrCapacity);
+        // two warp-aggregated appends: the first list, and the second one
+        // (frame stream: keys of slots at their finest level)
+#pragma unroll
+        for (int which = 0; which < 2; ++which) {
+            const bool mine = fresh && (to_f == (which == 1));
+            const unsigned ballot = __ballot_sync(0xffffffffu, mine);
+            if (ballot == 0u) continue;
+            unsigned int* cnt = which ? count_f : count;
+            int* lst = which ? list_f : list;
+            unsigned int b = 0u;
+            if (lane == 0) b = atomicAdd(cnt, (unsigned int)__popc(ballot));
+            b = __shfl_sync(0xffffffffu, b, 0);
+            if (mine) {
+                const unsigned int pos = b + __popc(ballot & ((1u << lane) - 1u));
+                if (pos < cap) lst[pos] = (int)nkey;
+                else atomicOr(err, kErrCapacity);
+            }
         }
     }
 }
@@ -434,10 +445,15 @@ __global__ void __launch_bounds__(256) stream_setup_kernel(const SlotView* __res
 __global__ void __launch_bounds__(256) stream_select_kernel(
     const SlotView* __restrict__ sv, int64_t slot_nodes, int* __restrict__ list,
     unsigned int* __restrict__ count, unsigned int cap, unsigned int* __restrict__ err,
-    unsigned int* __restrict__ pend, unsigned long long* __restrict__ cands) {
+    unsigned int* __restrict__ pend, unsigned long long* __restrict__ cands,
+    int* __restrict__ list_f, unsigned int* __restrict__ count_f) {
     const int slot = blockIdx.y;
     const SlotView v = sv[slot];
     if (v.op != SLOT_START && v.op != SLOT_ADVANCE) return;
+    if (list_f && v.finest) {   // the finest level's keys go to the second list
+        list = list_f;
+        count = count_f;
+    }
     const int N = v.N;
     const int n1 = N + 1;
     const int rw = row_words_of(N);
@@ -570,13 +586,14 @@ cudaError_t launch_expand_conflicts(const int* clist, const unsigned int* ccount
                                     unsigned int max_c, int N, uint32_t* eval, int64_t key_div,
                                     int64_t slot_words, int* list, unsigned int* count,
                                     unsigned int cap, unsigned int* err, cudaStream_t stream,
-                                    const SlotView* sv, unsigned int* slot_count) {
+                                    const SlotView* sv, unsigned int* slot_count, int* list_f,
+                                    unsigned int* count_f) {
     if (max_c == 0) return cudaSuccess;
     const int64_t total = (int64_t)max_c * 26;
     const int64_t blocks = std::min<int64_t>((total + 255) / 256, 152 * 8);
     expand_conflicts_kernel<<<(unsigned)blocks, 256, 0, stream>>>(
         clist, ccount, max_c, N, eval, key_div, slot_words, list, count, cap, err, sv,
-        slot_count);
+        slot_count, list_f, count_f);
     return cudaGetLastError();
 }
 
@@ -590,11 +607,12 @@ cudaError_t launch_stream_setup(const SlotView* sv, int slots, int N_fine, cudaS
 cudaError_t launch_stream_select(const SlotView* sv, int slots, int N_fine, int64_t slot_nodes,
                                  int* list, unsigned int* count, unsigned int cap,
                                  unsigned int* err, unsigned int* pend,
-                                 unsigned long long* cands, cudaStream_t stream) {
+                                 unsigned long long* cands, cudaStream_t stream, int* list_f,
+                                 unsigned int* count_f) {
     if (slots < 1 || slots > 65535) return cudaErrorInvalidValue;
     const unsigned gx = (unsigned)std::min<int64_t>(blocks_for(words_of(N_fine)), 152 * 2);
     stream_select_kernel<<<dim3(gx, (unsigned)slots), 256, 0, stream>>>(
-        sv, slot_nodes, list, count, cap, err, pend, cands);
+        sv, slot_nodes, list, count, cap, err, pend, cands, list_f, count_f);
     return cudaGetLastError();
 }
 

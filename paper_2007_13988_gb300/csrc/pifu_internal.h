@@ -139,9 +139,6 @@ struct Epilogue {
     int* recheck;
     unsigned int* recheck_count;
     float margin;
-    // Frame stream, surrogate pass: the points of slots at their finest level
-    // are queued whatever their occupancy (that level always runs f_O).
-    int finest_to_queue;
 };
 
 // --- gather.cu -------------------------------------------------------------
@@ -372,13 +369,16 @@ cudaError_t launch_loop_control(cudaGraphConditionalHandle h, const unsigned int
 // same set as dilate26(conflicts) & ~evaluated, in work proportional to the
 // conflicts.  Launched for up to max_c conflicts (a device-resident count).
 // Frame stream: sv gives every key's slot level and evaluated bitset (N and
-// eval are then unused) and slot_count[slot] counts the keys appended.
+// eval are then unused) and slot_count[slot] counts the keys appended; with
+// list_f, the keys of slots at their finest level go to list_f at *count_f
+// instead (each list at most cap).
 cudaError_t launch_expand_conflicts(const int* clist, const unsigned int* ccount,
                                     unsigned int max_c, int N, uint32_t* eval, int64_t key_div,
                                     int64_t slot_words, int* list, unsigned int* count,
                                     unsigned int cap, unsigned int* err, cudaStream_t stream,
                                     const SlotView* sv = nullptr,
-                                    unsigned int* slot_count = nullptr);
+                                    unsigned int* slot_count = nullptr, int* list_f = nullptr,
+                                    unsigned int* count_f = nullptr);
 
 // Frame stream: everything the scheduler kernel reads and writes.
 struct StreamCtl {
@@ -446,12 +446,14 @@ cudaError_t launch_colour_cond(cudaGraphConditionalHandle h, const unsigned int*
 // for one, and the first selection of those slots' level (START: every node;
 // ADVANCE: the candidates' 26-ring), appended as keys slot * slot_nodes +
 // node at *count (at most cap; beyond it kErrCapacity); pend[slot] += keys
-// queued, cands[slot] += boundary candidates.  N_fine sizes the grid.
+// queued, cands[slot] += boundary candidates.  With list_f, a slot at its
+// finest level appends to list_f at *count_f instead.  N_fine sizes the grid.
 cudaError_t launch_stream_setup(const SlotView* sv, int slots, int N_fine, cudaStream_t stream);
 cudaError_t launch_stream_select(const SlotView* sv, int slots, int N_fine, int64_t slot_nodes,
                                  int* list, unsigned int* count, unsigned int cap,
                                  unsigned int* err, unsigned int* pend,
-                                 unsigned long long* cands, cudaStream_t stream);
+                                 unsigned long long* cands, cudaStream_t stream,
+                                 int* list_f = nullptr, unsigned int* count_f = nullptr);
 
 // Graph form: set hs for 1 .. threshold points in *count, hl above.
 cudaError_t launch_branch(cudaGraphConditionalHandle hs, cudaGraphConditionalHandle hl,

@@ -96,8 +96,9 @@ int stream_ensure(pifu_ctx* ctx, int S, int N, int F, int64_t npix) {
     CK(dev_alloc(&w.values, nodes * Sn));
     CK(dev_alloc(&w.top, top * Sn));
     CK(dev_alloc(&w.list, cap));
-    CK(dev_alloc(&w.recheck, cap));
-    CK(dev_alloc(&w.squeue, cap));
+    CK(dev_alloc(&w.recheck, 2 * cap));   // a surrogate round's f_O pass takes up to 2 cap
+    // the surrogate's f_O queue: the finest-level keys, then f_S's fall-backs
+    CK(dev_alloc(&w.squeue, 2 * cap));
     CK(dev_alloc(&w.hit_xyz, 3 * np * Sn));
     CK(dev_alloc(&w.hit_pix, np * Sn));
     CK(dev_alloc(&w.d_hits, 1));
@@ -195,6 +196,7 @@ int g_enqueue_stream(pifu_ctx* ctx, const StreamKey& k) {
     a.h = h;
     a.init = 1;
     CK(cudaMemsetAsync(w.d_hits, 0, sizeof(unsigned int), s));
+    CK(cudaMemsetAsync(ctx->d_squeue, 0, sizeof(unsigned int), s));
     // the hit list holds the hits of every render since the last colour pass
     const int64_t hcap = std::min<int64_t>((int64_t)w.S * w.npix, cap);
     // the colour MLP over the hit list, then the list emptied
@@ -223,10 +225,17 @@ int g_enqueue_stream(pifu_ctx* ctx, const StreamKey& k) {
     const int64_t before = launches_now(ctx);
     CK(cudaStreamBeginCaptureToGraph(sb, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
     {
+        // With the surrogate, the keys of slots at their finest level go
+        // straight to f_O's queue (that level always runs f_O); f_S runs on
+        // the coarse levels' keys and appends its fall-backs after them.
+        const bool sur = k.use_surrogate != 0;
+        int* list_f = sur ? w.squeue : nullptr;
+        unsigned int* count_f = sur ? ctx->d_squeue : nullptr;
         // 1. set-up and first selection of the starting and advancing slots
         if (launch_stream_setup(w.sv, S, N_fine, sb) != cudaSuccess ||
             launch_stream_select(w.sv, S, N_fine, w.slot_nodes, w.list, ctx->d_count,
-                                 (unsigned)cap, err, a.pend_eval, w.cands, sb) != cudaSuccess)
+                                 (unsigned)cap, err, a.pend_eval, w.cands, sb, list_f,
+                                 count_f) != cudaSuccess)
             st = PIFU_ERR_CUDA;
         ctx->prof.k[PIFU_K_LEVEL].launches += 1;
         ctx->prof.k[PIFU_K_SELECT].launches += 1;
@@ -251,15 +260,19 @@ int g_enqueue_stream(pifu_ctx* ctx, const StreamKey& k) {
             st = PIFU_ERR_CUDA;
         if (st == PIFU_OK)
             st = g_eval(ctx, net, src, cap, ctx->d_count, Map{}, Calib{}, epi, k.precision,
-                        k.margin, &w.d_ctl->rechecked, sb, k.use_surrogate != 0, k.sur_margin,
-                        &w.d_ctl->fallback);
+                        k.margin, &w.d_ctl->rechecked, sb, sur, k.sur_margin,
+                        &w.d_ctl->fallback, sur ? std::min<int64_t>(2 * cap, kTcRowsMax) : 0);
+        if (st == PIFU_OK && sur &&
+            cudaMemsetAsync(ctx->d_squeue, 0, sizeof(unsigned int), sb) != cudaSuccess)
+            st = PIFU_ERR_CUDA;
         // 3. the next round's keys: the unevaluated ring of this round's conflicts
         if (st == PIFU_OK && cudaMemsetAsync(ctx->d_count, 0, sizeof(unsigned int), sb) != cudaSuccess)
             st = PIFU_ERR_CUDA;
         if (st == PIFU_OK &&
             launch_expand_conflicts(ctx->clist, ctx->d_ccount, (unsigned)ctx->clist_cap, N_fine,
                                     w.eval, w.slot_nodes, w.slot_words, w.list, ctx->d_count,
-                                    (unsigned)cap, err, sb, w.sv, a.pend_next) != cudaSuccess)
+                                    (unsigned)cap, err, sb, w.sv, a.pend_next, list_f,
+                                    count_f) != cudaSuccess)
             st = PIFU_ERR_CUDA;
         ctx->prof.k[PIFU_K_SELECT].launches += 1;
         // 4. colour of the hits gathered so far, when the hit list could not
@@ -338,13 +351,16 @@ int s_build(pifu_ctx* ctx, const StreamKey& k) {
     if (!ctx->cap_stream3) CK(cudaStreamCreateWithFlags(&ctx->cap_stream3, cudaStreamNonBlocking));
     if (!ctx->cap_stream4) CK(cudaStreamCreateWithFlags(&ctx->cap_stream4, cudaStreamNonBlocking));
     {
-        const int st = ensure_clist(ctx, w.cap);
+        const int st = ensure_clist(ctx, 2 * w.cap);
         if (st != PIFU_OK) return st;
     }
     CK(tc_prepare());
     CK(chain_prepare());
     {
-        const int st = ensure_tc_rows(ctx, w.cap);
+        // the surrogate's f_O pass takes up to twice a round's list (its
+        // finest-level keys and the fall-backs)
+        const int64_t rows = k.use_surrogate ? std::min<int64_t>(2 * w.cap, kTcRowsMax) : w.cap;
+        const int st = ensure_tc_rows(ctx, rows);
         if (st != PIFU_OK) return st;
     }
     // g_eval's queues are the context's; point them at the stream's for the capture
@@ -502,6 +518,10 @@ int pifu_stream(pifu_ctx* ctx, int F, const pifu_fmap* occ_maps, const pifu_fmap
             last[sl] = f;
     }
     const int cur = (lv->num_levels - 1) & 1;   // the finest level's binarized bitset
+    // f_O's queue also took every finest-level key: the fall-backs are the rest
+    int64_t fallback = (int64_t)ctl.fallback;
+    if (lv->use_surrogate)
+        for (int f = 0; f < F; ++f) fallback -= (int64_t)w.h_fs[f].evals[lv->num_levels - 1];
     for (int f = 0; f < F; ++f) {
         const StreamFrameStats& fs = w.h_fs[f];
         if (out) {
@@ -522,7 +542,7 @@ int pifu_stream(pifu_ctx* ctx, int F, const pifu_fmap* occ_maps, const pifu_fmap
                 vs.conflict_rounds[l] = (int32_t)fs.rounds[l];
             }
             vs.rechecked_per_level[0] = (int64_t)ctl.rechecked;
-            vs.fallback_per_level[0] = (int64_t)ctl.fallback;
+            vs.fallback_per_level[0] = fallback;
             out[f] = vs;
         }
         if (times) {
