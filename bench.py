@@ -786,6 +786,18 @@ def run_ours(args, rank, world, local_rank):
             if PREC[name] != prec:
                 r = time_form(fr, PREC[name], side_steps, 2, world, form=form)
                 others[name] = (r, snapshot(fr, r["vol"]))
+    # ---- the headline form with the FP32 SIMT re-check (the default re-check
+    # is the split-TF32 pass on the tensor cores) ----------------------------
+    simt_rc = None
+    if prec in (2, 3):
+        pp = fr.pifu
+        pp.pifu_set_recheck(fr.ctx, pp.PIFU_RECHECK_SIMT)
+        try:
+            r = time_form(fr, prec, side_steps, 2, world, form=form)
+            rh = time_form(fr, prec, side_steps, 1, world, form="host") if form == "graph" else r
+        finally:
+            pp.pifu_set_recheck(fr.ctx, pp.PIFU_RECHECK_TENSOR)
+        simt_rc = (r, rh)
     # ---- the plain FP32 form on the same GPU, for the speedup ---------------
     plain = None
     if prec != 0 and not args.no_plain:
@@ -1067,6 +1079,23 @@ def run_ours(args, rank, world, local_rank):
                    "speedup_over_headline": r["value"] / head["value"],
                    "speedup_over_plain_fp32": r["value"] / plain["value"] if plain else None}
             for name, (r, _) in others.items()}
+    if simt_rc is not None:
+        r, rh = simt_rc
+        nr = max(1, len(rh["step_ms"]))
+        line["recheck_forms"] = {
+            "note": "the FP32-accurate pass of the MIXED forms (re-check of occupancies within "
+                    "the margin of 0.5, batches of <= 256 points): passes of more than 512 "
+                    "points in split TF32 on the tensor cores (hi*hi + hi*lo + lo*hi, FP32 "
+                    "accumulation), smaller ones on the FP32 SIMT network (the headline), "
+                    "against every pass on the FP32 SIMT network; ms per frame of that class "
+                    "on the host-driven form (its host launch gaps included)",
+            "tensor": {"value": head["value"], "ms_per_step": head["ms_per_step"],
+                       "pass_ms_per_frame": prof["mlp_f32"]["ms"] / nprof,
+                       "pass_launches_per_frame": prof["mlp_f32"]["launches"] // nprof},
+            "simt": {"value": r["value"], "ms_per_step": r["ms_per_step"],
+                     "pass_ms_per_frame": rh["prof"]["mlp_f32"]["ms"] / nr,
+                     "pass_launches_per_frame": rh["prof"]["mlp_f32"]["launches"] // nr,
+                     "rechecked_per_frame": r["rechecked"]}}
     if head["clocks"] is not None:
         line["clocks"] = head["clocks"]
     if world == 1 and not args.no_cpu_baseline:

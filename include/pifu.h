@@ -384,6 +384,28 @@ int pifu_autotune(pifu_ctx* ctx, int64_t rows, void* stream, int32_t* bn_out, do
 enum pifu_schedule { PIFU_SCHED_PER_LAYER = 0, PIFU_SCHED_CHAINED = 1 };
 int pifu_set_schedule(pifu_ctx* ctx, int schedule);
 
+/* Arithmetic of the MIXED forms' FP32 passes: the re-evaluation of
+ * occupancies within the margin of 0.5 and batches of at most 256 points
+ * (not in the paper, which evaluates every point once; Sec. 3.2 needs only
+ * the decision at 0.5 to be the network's).
+ *   PIFU_RECHECK_TENSOR (default): a pass of more than 512 points runs f_O's
+ *     hidden layers on the tensor cores with every FP32 operand split into
+ *     two TF32 values, hi = tf32(v) and lo = tf32(v - hi), and each product
+ *     formed as hi*hi + hi*lo + lo*hi (Ootomo and Yokota's split-TF32
+ *     method), FP32 accumulation and an FP32 last layer: within about 2e-5
+ *     of the FP64 network in occupancy (the FP32 SIMT network: about 1e-6).
+ *     Smaller passes run the FP32 SIMT network, whose one launch has the
+ *     lower latency there.  Needs hidden widths that are multiples of 128,
+ *     the last one 128 wide, and a last layer of at most 4 outputs reading
+ *     only it; other networks (and the CBN network) use the SIMT form.  The
+ *     first MIXED call of a context reserves its workspace: 16,384 points x
+ *     (2 d_in + 4 widest hidden width) floats plus 16 MB.
+ *   PIFU_RECHECK_SIMT: the FP32 SIMT network (FFMA) for every pass, as the
+ *     FP32 form.
+ * Invalidates captured graphs; no device work.  Errors: PIFU_ERR_ARG. */
+enum pifu_recheck { PIFU_RECHECK_TENSOR = 0, PIFU_RECHECK_SIMT = 1 };
+int pifu_set_recheck(pifu_ctx* ctx, int form);
+
 /* Sets the tile code of every tuned layer, in pifu_autotune's order: codes[i]
  * for layer i, n = the number of layers pifu_autotune reports (for instance a
  * saved autotuner result).  A code must be allowed for its layer as above

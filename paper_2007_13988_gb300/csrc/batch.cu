@@ -250,7 +250,9 @@ int b_build(pifu_ctx* ctx, const BatchKey& k) {
         if (ctx->cbn.tc_ok) CK(cbn_tc_prepare(f.C, f.K, f.nb));
     }
     {
-        const int st = ensure_tc_rows(ctx, std::max<int64_t>(bw.cap, (int64_t)k.B * k.width * k.height));
+        int st = ensure_tc_rows(ctx, std::max<int64_t>(bw.cap, (int64_t)k.B * k.width * k.height));
+        if (st == PIFU_OK && (k.precision == PIFU_PREC_MIXED || k.precision == PIFU_PREC_FP8_MIXED))
+            st = ensure_x3(ctx);
         if (st != PIFU_OK) return st;
     }
     // g_eval's queues are the context's; point them at the batch's for the capture

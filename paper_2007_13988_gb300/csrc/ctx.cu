@@ -253,9 +253,12 @@ void free_net(DevNet& net) {
         dev_free(L.b);
     }
     for (auto& T : net.tc) dev_free(T.W);
+    for (auto& X : net.x3) dev_free(X.W);
     free_f8(net);
     net.layers.clear();
     net.tc.clear();
+    net.x3.clear();
+    net.x3_ok = false;
 }
 
 // ---- workspaces -------------------------------------------------------------
@@ -428,6 +431,90 @@ int build_tc(pifu_ctx* ctx, const HostNet& hn, DevNet& net) {
     }
     net.tc_ok = true;
     return encode_act_maps(ctx, net);
+}
+
+// ---- split-TF32 form (FP32-accurate passes on the tensor cores) -------------
+
+// Weights of the split-TF32 layers: per hidden layer [n_out][2 KP], the TF32
+// value hi = tf32(w) of every weight in columns [0, KP) and lo = tf32(w - hi)
+// in [KP, 2 KP), the h part first, then the x part zero-padded to KX.  Nets
+// of other shapes keep x3_ok = false (their FP32 passes use the SIMT kernels).
+int build_x3(pifu_ctx* ctx, const HostNet& hn, DevNet& net) {
+    (void)ctx;
+    net.x3_ok = false;
+    const int L = (int)net.layers.size();
+    if (net.kind == kNetCbn || L < 2) return PIFU_OK;
+    for (int l = 0; l + 1 < L; ++l) {
+        const DevLayer& Ly = net.layers[(size_t)l];
+        if (Ly.n_out % kX3Tile != 0 || (l == 0) != (Ly.K1 == 0)) return PIFU_OK;
+    }
+    const DevLayer& Ll = net.layers[(size_t)L - 1];
+    if (net.layers[(size_t)L - 2].n_out != kX3Tile || Ll.K2 != 0 || Ll.n_out < 1 || Ll.n_out > 4)
+        return PIFU_OK;
+    const int KX = round_up(net.d_in, 32);
+    net.x3.assign((size_t)L - 1, X3Layer{});
+    for (int l = 0; l + 1 < L; ++l) {
+        const DevLayer& Ly = net.layers[(size_t)l];
+        X3Layer& X = net.x3[(size_t)l];
+        X.KH = Ly.K1;
+        X.KX = Ly.K2 > 0 ? KX : 0;
+        X.KP = X.KH + X.KX;
+        if (X.KP == 0) return PIFU_OK;
+        const size_t row = 2 * (size_t)X.KP;
+        std::vector<float> w((size_t)Ly.n_out * row, 0.f);
+        const std::vector<float>& wf = hn.W[(size_t)l];   // [n_out][K1 | ldx]
+        for (int o = 0; o < Ly.n_out; ++o) {
+            auto put = [&](int k, float v) {
+                const float hi = tf32_round(v);
+                w[(size_t)o * row + (size_t)k] = hi;
+                w[(size_t)o * row + (size_t)X.KP + (size_t)k] = tf32_round(v - hi);
+            };
+            for (int k = 0; k < Ly.K1; ++k) put(k, wf[(size_t)o * Ly.ldw + k]);
+            if (Ly.K2 > 0)
+                for (int k = 0; k < net.d_in; ++k) put(X.KH + k, wf[(size_t)o * Ly.ldw + Ly.K1 + k]);
+        }
+        CK(dev_alloc(&X.W, (int64_t)w.size()));
+        CK(cudaMemcpy(X.W, w.data(), w.size() * sizeof(float), cudaMemcpyHostToDevice));
+        if (!x3_encode_2d(&X.tmW, X.W, row, (uint64_t)Ly.n_out, row * 4, 32, 128))
+            return PIFU_ERR_CUDA;
+    }
+    net.x3_KX = KX;
+    net.x3_ok = true;
+    return PIFU_OK;
+}
+
+// The split-TF32 workspaces (kX3Rows points) and the tensor maps over them,
+// once per context.  Called before any capture (a graph holds the maps).
+int ensure_x3(pifu_ctx* ctx) {
+    if (ctx->x3_ready) return PIFU_OK;
+    int64_t kx = 0, h = 0;
+    for (const DevNet& n : ctx->net) {
+        if (!n.x3_ok) continue;
+        kx = std::max<int64_t>(kx, n.x3_KX);
+        for (size_t l = 0; l + 1 < n.layers.size(); ++l) h = std::max<int64_t>(h, n.layers[l].n_out);
+    }
+    if (kx == 0) return PIFU_OK;
+    CK(x3_prepare());
+    CK(dev_alloc(&ctx->X3, kX3Rows * 2 * kx));
+    CK(dev_alloc(&ctx->H3[0], kX3Rows * 2 * h));
+    CK(dev_alloc(&ctx->H3[1], kX3Rows * 2 * h));
+    CK(dev_alloc(&ctx->x3_part, (int64_t)kX3MaxUnits * kX3Tile * kX3Tile));
+    CK(dev_alloc(&ctx->x3_ctr, 2 * (int64_t)kX3MaxUnits));
+    CK(cudaMemset(ctx->x3_ctr, 0, sizeof(unsigned int) * 2 * kX3MaxUnits));
+    for (DevNet& n : ctx->net) {
+        if (!n.x3_ok) continue;
+        const uint64_t rx = 2 * (uint64_t)n.x3_KX;
+        if (!x3_encode_2d(&n.tmX3, ctx->X3, rx, (uint64_t)kX3Rows, rx * 4, 32, 32))
+            return PIFU_ERR_CUDA;
+        for (size_t l = 1; l < n.x3.size(); ++l) {
+            const uint64_t rh = 2 * (uint64_t)n.x3[l].KH;
+            if (!x3_encode_2d(&n.x3[l].tmH, ctx->H3[(l - 1) % 2], rh, (uint64_t)kX3Rows, rh * 4, 32,
+                              32))
+                return PIFU_ERR_CUDA;
+        }
+    }
+    ctx->x3_ready = true;
+    return PIFU_OK;
 }
 
 // ---- FP8 form of f_O ----------------------------------------------------------

@@ -13,7 +13,10 @@ int64_t launches_now(const pifu_ctx* ctx);
 // The FP32 pass over a device-sized queue in the graph.  With the fused
 // kernel, a switch node set on the device from the queue length launches it
 // with the cluster size that length calls for (few points: large clusters,
-// the lowest latency per tile; many: small clusters, more tiles per round).
+// the lowest latency per tile; many: small clusters, more tiles per round),
+// or, when the split-TF32 network is usable (x3_usable) and the queue holds
+// more than kX3MinRows and at most kX3Rows points, that network (one more
+// body of the same switch).  An empty queue launches nothing.
 int g_recheck(pifu_ctx* ctx, const DevNet& net, const PointSrc& src, int64_t cap,
               const Map& map, const Calib& cal, const Epilogue& epi, cudaStream_t s,
               const unsigned int* m_dev) {
@@ -21,31 +24,40 @@ int g_recheck(pifu_ctx* ctx, const DevNet& net, const PointSrc& src, int64_t cap
     const bool sw = net.kind != kNetCbn && ctx->cap_stream4 && s != ctx->cap_stream4 &&
                     fused_ok(fz);
     const FusedPlan plan = sw ? fused_plan(fz) : FusedPlan{};
-    if (plan.n <= 1)
+    const bool x3 = sw && plan.n >= 1 && x3_usable(ctx, net) && cap > kX3MinRows;
+    if (plan.n <= 1 && !x3)
         return run_mlp(ctx, net, src, cap, map, Map{}, cal, epi, s, PIFU_PREC_FP32, m_dev);
     cudaStreamCaptureStatus cs;
     cudaGraph_t cg = nullptr;
     CK(cudaStreamGetCaptureInfo(s, &cs, nullptr, &cg, nullptr, nullptr, nullptr));
     cudaGraphConditionalHandle h;
     CK(cudaGraphConditionalHandleCreate(&h, cg, 0, 0));
-    CK(launch_fused_switch(h, plan, m_dev, (unsigned)cap, s));
-    cudaGraph_t bodies[4] = {};
-    int st = g_add_switch(ctx, s, h, plan.n, bodies);
+    CK(launch_fused_switch(h, plan, m_dev, (unsigned)cap, s, x3 ? (unsigned)kX3MinRows : 0u,
+                           x3 ? (unsigned)kX3Rows : 0u));
+    const int nb = plan.n + (x3 ? 1 : 0);
+    cudaGraph_t bodies[5] = {};
+    int st = g_add_switch(ctx, s, h, nb, bodies);
     if (st != PIFU_OK) return st;
     cudaStream_t s4 = ctx->cap_stream4;
     const int64_t before = launches_now(ctx);
-    for (int i = 0; i < plan.n; ++i) {
+    int64_t fused_launches = 0;
+    for (int i = 0; i < nb; ++i) {
         CK(cudaStreamBeginCaptureToGraph(s4, bodies[i], nullptr, nullptr, 0,
                                          cudaStreamCaptureModeThreadLocal));
-        st = run_mlp(ctx, net, src, cap, map, Map{}, cal, epi, s4, PIFU_PREC_FP32, m_dev,
-                     plan.cl[i]);
+        if (i < plan.n)
+            st = run_mlp(ctx, net, src, cap, map, Map{}, cal, epi, s4, PIFU_PREC_FP32, m_dev,
+                         plan.cl[i]);
+        else
+            st = run_mlp_x3(ctx, net, src, std::min<int64_t>(cap, kX3Rows), map, Map{}, cal, epi,
+                            s4, m_dev);
         cudaGraph_t out = nullptr;
         const cudaError_t ee = cudaStreamEndCapture(s4, &out);
         if (st != PIFU_OK) return st;
         if (ee != cudaSuccess) return fail_cuda(ctx, ee);
+        if (i + 1 == plan.n) fused_launches = launches_now(ctx) - before;
     }
-    // one body runs per replay: count its launches once
-    const int64_t per_body = (launches_now(ctx) - before) / plan.n;
+    // one body runs per replay: count one fused body's launches
+    const int64_t per_body = plan.n > 0 ? fused_launches / plan.n : 0;
     ctx->prof.k[PIFU_K_MLP_F32].launches -= (launches_now(ctx) - before) - per_body;
     return PIFU_OK;
 }
@@ -407,7 +419,9 @@ int g_build(pifu_ctx* ctx, const FrameKey& k, const Map& occ, const Map& col, co
     }
     {
         // device-sized batches: the workspaces must hold a whole capacity
-        const int st = ensure_tc_rows(ctx, kChunkTC);
+        int st = ensure_tc_rows(ctx, kChunkTC);
+        auto mixed = [](int p) { return p == PIFU_PREC_MIXED || p == PIFU_PREC_FP8_MIXED; };
+        if (st == PIFU_OK && (mixed(k.precision) || mixed(k.cam_precision))) st = ensure_x3(ctx);
         if (st != PIFU_OK) return st;
     }
     const bool prof_on = ctx->prof.on;

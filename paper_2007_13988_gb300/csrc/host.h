@@ -29,6 +29,9 @@ constexpr int kMaxBatch = 64;           // frames of a lockstep batch
 constexpr int64_t kRecheckCap = 8192; // graph form: FP32 re-checks per batch (split-K path)
 constexpr int64_t kFusedMaxM = 2048;   // host-sized FP32 batches up to this size: fused kernel
 constexpr int64_t kTinyBatch = 256; // mixed precision: batches this small run in FP32
+constexpr int64_t kX3Rows = 16384;   // points per pass of the split-TF32 network (its workspace rows)
+constexpr int64_t kX3MinRows = 512;  // FP32 passes of more points run it (fewer: the one-launch
+                                     // SIMT network, whose latency is lower there)
 
 struct DevLayer {
     int n_out = 0;
@@ -71,6 +74,16 @@ struct Fp8Layer {
     CUtensorMap tmA1{};          // the previous layer's E4M3 output (layer >= 1)
 };
 
+// Split-TF32 form of a hidden layer (mlp_x3.cu): W as [n_out][2 KP] FP32,
+// hi values then lo values, KP = KH + KX (the h part, then the x part
+// zero-padded to 32 values), and its tensor maps.
+struct X3Layer {
+    float* W = nullptr;
+    int KH = 0, KX = 0, KP = 0;
+    CUtensorMap tmW{};
+    CUtensorMap tmH{};   // the previous layer's output planes (l >= 1)
+};
+
 struct DevNet {
     int kind = 0;       // 0 occupancy (sigmoid), 1 colour (tanh01)
     int d_in = 0;
@@ -90,6 +103,13 @@ struct DevNet {
     std::vector<Fp8Layer> f8;
     float s_x = 0.f;                // per-tensor scale of the input rows (reported)
     uint64_t f8_version = 0;        // bumped by every calibration
+    // split-TF32 form (the MIXED forms' FP32-accurate passes): hidden widths
+    // multiples of 128, the last hidden one 128 wide, a last layer of <= 4
+    // outputs reading only it
+    bool x3_ok = false;
+    std::vector<X3Layer> x3;
+    int x3_KX = 0;                  // x part of a plane row: d_in rounded up to 32
+    CUtensorMap tmX3{};             // the input-row planes [kX3Rows][2 x3_KX]
 };
 
 constexpr int kNetCbn = 2;   // DevNet.kind of the CBN + SoftZ occupancy network
@@ -380,6 +400,14 @@ struct pifu_ctx {
                                          // the tile counter and the finished-CTA counter
     bool chain_on = false;               // pifu_set_schedule
     int64_t tc_rows = 0;            // rows of Xb, Hb[] (grown on demand up to kChunkTC)
+    // split-TF32 passes: input-row planes, two output-plane buffers, split-K
+    // partial tiles and their arrival counters (allocated on first use)
+    float* X3 = nullptr;
+    float* H3[2] = {nullptr, nullptr};
+    float* x3_part = nullptr;
+    unsigned int* x3_ctr = nullptr;
+    bool x3_ready = false;
+    int recheck_form = 0;             // pifu_set_recheck
     float* part = nullptr;            // split-K partial sums of small FP32 batches
     int64_t part_cap = 0;
     // level workspace, sized for ws_N
@@ -596,6 +624,19 @@ int encode_act_maps(pifu_ctx* ctx, DevNet& net);
 int encode_all_act_maps(pifu_ctx* ctx);
 int ensure_tc_rows(pifu_ctx* ctx, int64_t rows);
 int build_tc(pifu_ctx* ctx, const HostNet& hn, DevNet& net);
+int build_x3(pifu_ctx* ctx, const HostNet& hn, DevNet& net);
+int ensure_x3(pifu_ctx* ctx);
+// The FP32-accurate pass of the MIXED forms (re-checks, tiny batches): the
+// split-TF32 network when the context's re-check form is the tensor cores and
+// the net allows it (m points, or a device-sized batch of at most m), else
+// the FP32 SIMT network.
+bool x3_usable(const pifu_ctx* ctx, const DevNet& net);
+int run_mlp_x3(pifu_ctx* ctx, const DevNet& net, const PointSrc& src_in, int64_t m,
+               const Map& map0, const Map& map1, const Calib& calib, const Epilogue& epi,
+               cudaStream_t s, const unsigned int* m_dev);
+int run_recheck(pifu_ctx* ctx, const DevNet& net, const PointSrc& src, int64_t m,
+                const Map& map0, const Map& map1, const Calib& calib, const Epilogue& epi,
+                cudaStream_t s);
 uint8_t e4m3_byte(float v);
 int build_fp8(pifu_ctx* ctx, DevNet& net, int F, const std::vector<float>& s_h);
 int calibrate_fp8(pifu_ctx* ctx, const Map& map, const Calib& cal, int n0, cudaStream_t s);

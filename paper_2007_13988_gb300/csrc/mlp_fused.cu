@@ -385,10 +385,14 @@ __host__ __device__ int fused_pick(const FusedPlan& p, long long tiles) {
 }
 
 __global__ void fused_switch_kernel(cudaGraphConditionalHandle h, FusedPlan plan,
-                                    const unsigned int* count, unsigned int cap) {
+                                    const unsigned int* count, unsigned int cap, unsigned int x3_lo,
+                                    unsigned int x3_hi) {
     const unsigned int c = min(*count, cap);
-    cudaGraphSetConditional(h, c == 0u ? (unsigned)plan.n
-                                       : (unsigned)fused_pick(plan, ((long long)c + kFP - 1) / kFP));
+    unsigned int i;
+    if (c == 0u) i = (unsigned)plan.n + 1u;
+    else if (c > x3_lo && c <= x3_hi) i = (unsigned)plan.n;
+    else i = (unsigned)fused_pick(plan, ((long long)c + kFP - 1) / kFP);
+    cudaGraphSetConditional(h, i);
 }
 
 }  // namespace
@@ -408,8 +412,9 @@ FusedPlan fused_plan(const FusedNet& net) {
 }
 
 cudaError_t launch_fused_switch(cudaGraphConditionalHandle h, const FusedPlan& plan,
-                                const unsigned int* count, unsigned int cap, cudaStream_t stream) {
-    fused_switch_kernel<<<1, 1, 0, stream>>>(h, plan, count, cap);
+                                const unsigned int* count, unsigned int cap, cudaStream_t stream,
+                                unsigned int x3_lo, unsigned int x3_hi) {
+    fused_switch_kernel<<<1, 1, 0, stream>>>(h, plan, count, cap, x3_lo, x3_hi);
     return cudaGetLastError();
 }
 

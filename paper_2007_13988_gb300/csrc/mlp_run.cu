@@ -292,6 +292,79 @@ int run_mlp(pifu_ctx* ctx, const DevNet& net, const PointSrc& src_in, int64_t m,
     return PIFU_OK;
 }
 
+// ---- the FP32-accurate pass on the tensor cores (split TF32, mlp_x3.cu) -------
+
+bool x3_usable(const pifu_ctx* ctx, const DevNet& net) {
+    return net.x3_ok && ctx->x3_ready && ctx->recheck_form == PIFU_RECHECK_TENSOR;
+}
+
+// Gather into hi/lo planes, then one launch per hidden layer, the last one
+// with the last layer and the epilogue; passes of at most kX3Rows points (a
+// device-sized batch is one pass of at most m <= kX3Rows).
+int run_mlp_x3(pifu_ctx* ctx, const DevNet& net, const PointSrc& src_in, int64_t m,
+               const Map& map0, const Map& map1, const Calib& calib, const Epilogue& epi,
+               cudaStream_t s, const unsigned int* m_dev) {
+    if (!x3_usable(ctx, net)) return PIFU_ERR_UNSUPPORTED;
+    if (m_dev && m > kX3Rows) return PIFU_ERR_ARG;
+    PointSrc src = src_in;
+    src.count = m_dev;
+    const int L = (int)net.layers.size();
+    const DevLayer& Ll = net.layers[(size_t)L - 1];
+    Profiler& pr = ctx->prof;
+    for (int64_t p0 = 0; p0 < m; p0 += kX3Rows) {
+        const int64_t mc = std::min<int64_t>(kX3Rows, m - p0);
+        cudaEvent_t ev = pr.begin(s);
+        CK(launch_gather_x3(src, p0, mc, calib, map0, map1, ctx->X3, net.x3_KX, s));
+        pr.end(PIFU_K_GATHER, ev, s, 0.0,
+               (double)mc * (4.0 * 4.0 * (map0.C + map1.C) + 8.0 * net.x3_KX));
+        FuseLast fl{};
+        fl.W = Ll.W;
+        fl.ldw = Ll.ldw;
+        fl.bias = Ll.b;
+        fl.n_out = Ll.n_out;
+        fl.p0 = p0;
+        fl.epi = epi;
+        for (int l = 0; l + 1 < L; ++l) {
+            const DevLayer& Ly = net.layers[(size_t)l];
+            const X3Layer& X = net.x3[(size_t)l];
+            X3LayerArgs a{};
+            a.tmW = &X.tmW;
+            a.tmH = l > 0 ? &X.tmH : nullptr;
+            a.tmX = &net.tmX3;
+            a.nk1 = X.KH / 32;
+            a.nk2 = X.KX / 32;
+            a.KH = X.KH;
+            a.KX = X.KX;
+            a.KP = X.KP;
+            a.M = (int)mc;
+            a.N = Ly.n_out;
+            a.m_dev = m_dev;
+            a.bias = Ly.b;
+            a.slope = net.slope;
+            a.out = l + 2 < L ? ctx->H3[l % 2] : nullptr;
+            a.fuse = l + 2 == L ? &fl : nullptr;
+            a.part = ctx->x3_part;
+            a.ctr = ctx->x3_ctr;
+            a.err = ctx->d_count + 1;
+            double flops = 3.0 * 2.0 * mc * Ly.fan_in * Ly.n_out;
+            if (a.fuse) flops += 2.0 * mc * Ll.fan_in * Ll.n_out;
+            ev = pr.begin(s);
+            CK(launch_x3_layer(a, s));
+            pr.end(PIFU_K_MLP_F32, ev, s, flops,
+                   8.0 * ((double)mc * (X.KP + Ly.n_out) + (double)Ly.n_out * X.KP));
+        }
+    }
+    return PIFU_OK;
+}
+
+int run_recheck(pifu_ctx* ctx, const DevNet& net, const PointSrc& src, int64_t m,
+                const Map& map0, const Map& map1, const Calib& calib, const Epilogue& epi,
+                cudaStream_t s) {
+    if (m > kX3MinRows && x3_usable(ctx, net))
+        return run_mlp_x3(ctx, net, src, m, map0, map1, calib, epi, s, nullptr);
+    return run_mlp(ctx, net, src, m, map0, map1, calib, epi, s, PIFU_PREC_FP32);
+}
+
 // Mixed precision over one batch: the tensor-core BF16 pass commits every
 // occupancy farther than `margin` from 0.5 and queues the others (node
 // indices for a level, point numbers otherwise) on ctx->recheck; the queued
@@ -303,9 +376,13 @@ int run_mlp_mixed(pifu_ctx* ctx, const DevNet& net, const PointSrc& src, int64_t
                   const Map& map0, const Map& map1, const Calib& calib, const Epilogue& epi,
                   float margin, cudaStream_t s, int64_t* rechecked, bool f8) {
     if (m > ctx->recheck_cap) return PIFU_ERR_ARG;
+    {
+        const int st = ensure_x3(ctx);
+        if (st != PIFU_OK) return st;
+    }
     // A tiny batch costs less in FP32 outright than in BF16 plus a re-check
     // pass (both are latency-bound there); FP32 is the re-check's arithmetic.
-    if (m <= kTinyBatch) return run_mlp(ctx, net, src, m, map0, map1, calib, epi, s, PIFU_PREC_FP32);
+    if (m <= kTinyBatch) return run_recheck(ctx, net, src, m, map0, map1, calib, epi, s);
     CK(cudaMemsetAsync(ctx->d_recheck, 0, sizeof(unsigned int), s));
     Epilogue e1 = epi;
     e1.recheck = ctx->recheck;
@@ -331,7 +408,7 @@ int run_mlp_mixed(pifu_ctx* ctx, const DevNet& net, const PointSrc& src, int64_t
         s2.list = ctx->recheck;
         e2.pix = ctx->recheck;
     }
-    return run_mlp(ctx, net, s2, n, map0, map1, calib, e2, s, PIFU_PREC_FP32);
+    return run_recheck(ctx, net, s2, n, map0, map1, calib, e2, s);
 }
 
 int read_recheck(pifu_ctx* ctx, cudaStream_t s, unsigned int* out) {

@@ -1,0 +1,557 @@
+// FP32-accurate hidden MLP layers on the tensor cores, for the small batches
+// of the MIXED forms: the re-evaluation of occupancies that the BF16 pass put
+// near Sec. 3.2's decision threshold 0.5, and batches too small for a BF16
+// pass plus a re-check.  These batches hold a few to a few thousand points;
+// in FP32 FFMA they are latency-bound on a few SMs.
+//
+// Arithmetic (the split-TF32 method of Ootomo and Yokota, 2022, restated):
+// each FP32 value v is held as two TF32 values, hi = tf32(v) and
+// lo = tf32(v - hi), so v = hi + lo to about 2^-22 |v|; a product a b is
+// formed as a_hi b_hi + a_hi b_lo + a_lo b_hi (the dropped a_lo b_lo is below
+// 2^-22 |a b|), three kind::tf32 tcgen05 MMAs into one FP32 accumulator.  The
+// result is within a few FP32 roundings of the FP32 network's.
+//
+// Layout: a layer's weights are [N][2 KP] FP32 rows, hi values in columns
+// [0, KP) and lo values in [KP, 2 KP), KP = KH + KX (the h part, then the x
+// part zero-padded to whole 32-value K-blocks); activations the same way,
+// [rows][2 K].
+//
+// Swapped operands: the MMA's A operand is 128 neurons of W and its B
+// operand up to 128 points, so a batch of 20 points costs MMAs of N = 32, not
+// 128-row tiles.  A work unit is (128 points, 128 neurons, a range of
+// K-blocks).  When the batch has fewer (point, neuron) tiles than the grid
+// has CTAs, the K-blocks of each tile are split over several units (one per
+// CTA then, all CTAs co-resident); each unit writes its partial tile, counts
+// itself in at the tile's counter, waits (bounded) until all splits have,
+// and finishes its share of the tile's columns: the partials summed in split
+// order (the same sums whichever CTA takes a column), the bias, the leaky
+// ReLU, and the hi/lo planes written -- or, in the last hidden layer, the
+// last layer in FP32 and the network's epilogue.  Without a split the unit
+// finishes from tensor memory.
+//
+// Persistent, warp-specialised: warp 0 lane 0 loads W and point tiles by TMA
+// into a 3-stage ring (64 KB a stage: hi and lo of both operands), warp 1
+// lane 0 issues the MMAs into one of two TMEM accumulators, warps 2-5 (one
+// TMEM lane quadrant each, one neuron per thread) run the epilogue of one
+// unit while the next unit's MMAs run.  Every mbarrier wait is bounded; a
+// wait that gives up sets *err and the roles stop.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include "epilogue.cuh"
+#include "gather.cuh"
+#include "pifu_internal.h"
+#include "sm100.cuh"
+
+namespace pifu {
+namespace {
+
+using namespace sm100;
+
+constexpr int XP = kX3Tile;                         // points per unit (MMA N <= 128)
+constexpr int XK = 32;                              // FP32 values per 128-byte K-block
+constexpr int XNST = 3;                             // ring stages
+constexpr uint32_t W_PLANE = 128 * 128;             // 128 neuron rows x 128 bytes
+constexpr uint32_t P_PLANE = XP * 128;              // 128 point rows x 128 bytes
+constexpr uint32_t P_BOX = 32 * 128;                // one 32-row TMA box of points
+constexpr uint32_t STAGE_BYTES = 2 * W_PLANE + 2 * P_PLANE;
+constexpr int kThreads = 192;
+constexpr uint32_t kTmemCols = 2 * XP;              // two accumulators
+constexpr uint32_t kWaitLimit = 1u << 20;           // polls; legitimate waits are microseconds
+constexpr int kMaxSplits = 8;
+constexpr uint32_t kSmemBytes = XNST * STAGE_BYTES + 1024 + 256 + 4 * XP * 4 * 4;
+static_assert(kSmemBytes <= 227 * 1024, "shared memory");
+static_assert(XP == 128, "one TMEM lane per neuron, 128 columns per accumulator");
+
+struct X3Params {
+    int nk1, nk2, KH, KX, KP, M, N, fuse;
+    const unsigned int* m_dev;
+    const float* bias;
+    float slope;
+    float* out;
+    float* part;
+    unsigned int* ctr;
+    unsigned int* err;
+};
+
+// The unit decomposition of one launch, the same in every CTA.
+struct Units {
+    int count, n_tiles, pairs, splits, units, nk;
+};
+
+__device__ __forceinline__ Units units_of(const X3Params& p) {
+    Units u;
+    u.count = p.M;
+    if (p.m_dev) u.count = min(u.count, (int)*p.m_dev);
+    u.count = max(u.count, 0);
+    u.n_tiles = p.N / 128;
+    u.pairs = ((u.count + XP - 1) / XP) * u.n_tiles;
+    u.nk = p.nk1 + p.nk2;
+    const int G = (int)gridDim.x;
+    u.splits = 1;
+    // split the K-blocks (at least two per split, at most kMaxSplits: the
+    // finishing unit reads every split's partial tile) while tiles are fewer
+    // than CTAs; then units = pairs x splits <= G <= kX3MaxUnits
+    if (u.pairs > 0 && u.pairs < G)
+        u.splits = max(1, min(min(G / u.pairs, u.nk / 2), kMaxSplits));
+    u.units = u.pairs * u.splits;
+    return u;
+}
+
+// Unit `t`: its tile (consecutive units share the points, so the CTAs working
+// at one moment read the same point rows through L2) and K range.
+struct Unit {
+    int pair, split, n0, p0, pcount, pn, kb0, kb1;
+};
+
+__device__ __forceinline__ Unit unit_of(const Units& us, int t) {
+    Unit w;
+    w.pair = t / us.splits;
+    w.split = t - w.pair * us.splits;
+    w.n0 = (w.pair % us.n_tiles) * 128;
+    w.p0 = (w.pair / us.n_tiles) * XP;
+    w.pcount = min(XP, us.count - w.p0);
+    w.pn = (w.pcount + 31) / 32;
+    w.kb0 = (int)((long long)w.split * us.nk / us.splits);
+    w.kb1 = (int)((long long)(w.split + 1) * us.nk / us.splits);
+    return w;
+}
+
+__device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+
+__device__ __forceinline__ float warp_sum(float x) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+}
+
+// Finishes column c (point p0 + c of the unit) of this thread's neuron n from
+// its accumulated sum a: bias, leaky ReLU, then the hi/lo planes of the
+// output, or (fuse) the point's contribution to the last layer summed over
+// the warp's 32 neurons into sred[q][c][j].  c is warp-uniform.
+__device__ __forceinline__ void finish_one(float a, int c, bool live, const Unit& w,
+                                           const X3Params& p, int n, float bn,
+                                           const float (&w5)[4], int n_out, int q, int lane,
+                                           float* sred) {
+    float h = a + bn;
+    h = h >= 0.f ? h : p.slope * h;
+    if (!p.fuse) {
+        if (live) {
+            const float hi = tf32_round(h);
+            const float lo = tf32_round(h - hi);
+            float* row = p.out + (int64_t)(w.p0 + c) * (2 * p.N);
+            __stcg(row + n, hi);
+            __stcg(row + p.N + n, lo);
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            if (j < n_out) {
+                const float t = warp_sum(h * w5[j]);
+                if (lane == 0) sred[(q * XP + c) * 4 + j] = t;
+            }
+        }
+    }
+}
+
+// Global word read with acquire semantics at GPU scope.
+__device__ __forceinline__ unsigned int ld_acquire(const unsigned int* a) {
+    unsigned int v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(a) : "memory");
+    return v;
+}
+
+__global__ void __launch_bounds__(kThreads, 1) x3_layer_kernel(
+    const __grid_constant__ CUtensorMap tmW, const __grid_constant__ CUtensorMap tmH,
+    const __grid_constant__ CUtensorMap tmX, const X3Params p, const FuseLast fl) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* ring = reinterpret_cast<uint8_t*>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+    uint64_t* full = reinterpret_cast<uint64_t*>(ring + XNST * STAGE_BYTES);
+    uint64_t* empty = full + XNST;
+    uint64_t* accf = empty + XNST;   // [2] accumulator ready for the epilogue
+    uint64_t* acce = accf + 2;       // [2] accumulator drained by the epilogue
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(acce + 2);
+    volatile uint32_t* sflag = tslot + 1;   // [0] accumulator ready, [1] last split of the tile
+    float* sred = reinterpret_cast<float*>(ring + XNST * STAGE_BYTES + 256);   // [4][XP][4]
+
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+
+    // prologue: depends on nothing earlier kernels write (overlaps their tail)
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < XNST; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&accf[b], 1);
+            mbar_init(&acce[b], 4);   // one arrival per epilogue warp
+        }
+        fence_mbar_init();
+        prefetch_tmap(&tmW);
+        if (p.nk1 > 0) prefetch_tmap(&tmH);
+        if (p.nk2 > 0) prefetch_tmap(&tmX);
+    }
+    if (warp == 1) tmem_alloc(tslot, kTmemCols);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tslot;
+    griddep_wait();   // the input planes and the point count come from earlier kernels
+    const Units us = units_of(p);
+    const int G = (int)gridDim.x;
+
+    bool ok = true;
+    if (warp == 0) {
+        if (lane == 0) {
+            // TMA producer: per K-block, W hi and lo (128 rows) and the unit's
+            // point rows in 32-row boxes, hi and lo
+            uint32_t g = 0;
+            for (int t = blockIdx.x; t < us.units && ok; t += G) {
+                const Unit w = unit_of(us, t);
+                for (int kb = w.kb0; kb < w.kb1; ++kb, ++g) {
+                    const uint32_t s = g % XNST;
+                    const uint32_t u = g / XNST;
+                    if (u > 0 && !mbar_wait(&empty[s], (u - 1) & 1u, kWaitLimit)) {
+                        ok = false;
+                        break;
+                    }
+                    uint8_t* st = ring + s * STAGE_BYTES;
+                    mbar_arrive_expect_tx(&full[s], 2 * W_PLANE + 2 * (uint32_t)w.pn * P_BOX);
+                    tma_load_2d(st, &tmW, kb * XK, w.n0, &full[s]);
+                    tma_load_2d(st + W_PLANE, &tmW, p.KP + kb * XK, w.n0, &full[s]);
+                    const bool from_h = kb < p.nk1;
+                    const CUtensorMap* mb = from_h ? &tmH : &tmX;
+                    const int x = from_h ? kb * XK : (kb - p.nk1) * XK;
+                    const int xl = x + (from_h ? p.KH : p.KX);
+                    for (int j = 0; j < w.pn; ++j) {
+                        tma_load_2d(st + 2 * W_PLANE + j * P_BOX, mb, x, w.p0 + 32 * j, &full[s]);
+                        tma_load_2d(st + 2 * W_PLANE + P_PLANE + j * P_BOX, mb, xl, w.p0 + 32 * j,
+                                    &full[s]);
+                    }
+                }
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // MMA issuer: per K-block 4 steps of K = 8, three products each
+            uint32_t g = 0, i = 0;
+            for (int t = blockIdx.x; t < us.units && ok; t += G, ++i) {
+                const Unit w = unit_of(us, t);
+                const uint32_t b = i & 1u, j = i >> 1;
+                if (j > 0 && !mbar_wait(&acce[b], (j - 1) & 1u, kWaitLimit)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t d = tmem + b * XP;
+                const uint32_t idesc = idesc_tf32_f32(128, 32 * w.pn);
+                for (int kb = w.kb0; kb < w.kb1; ++kb, ++g) {
+                    const uint32_t s = g % XNST;
+                    const uint32_t u = g / XNST;
+                    if (!mbar_wait(&full[s], u & 1u, kWaitLimit)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t ah = smem_u32(ring + s * STAGE_BYTES);
+                    const uint32_t al = ah + W_PLANE;
+                    const uint32_t bh = ah + 2 * W_PLANE;
+                    const uint32_t bl = bh + P_PLANE;
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const uint32_t acc = (kb != w.kb0 || k != 0) ? 1u : 0u;
+                        mma_tf32(d, desc_k_sw128(ah + k * 32), desc_k_sw128(bh + k * 32), idesc, acc);
+                        mma_tf32(d, desc_k_sw128(ah + k * 32), desc_k_sw128(bl + k * 32), idesc, 1u);
+                        mma_tf32(d, desc_k_sw128(al + k * 32), desc_k_sw128(bh + k * 32), idesc, 1u);
+                    }
+                    mma_commit(&empty[s]);
+                }
+                mma_commit(&accf[b]);   // also after an error, so the epilogue is released
+            }
+        }
+    } else {
+        // epilogue warps 2..5: TMEM lane quadrant q = neurons 32 q .. 32 q + 31
+        const int q = warp & 3;
+        const int nl = q * 32 + lane;
+        const int et = (int)threadIdx.x - 64;   // 0 .. 127
+        const int n_out = p.fuse ? fl.n_out : 0;
+        float w5[4] = {0.f, 0.f, 0.f, 0.f};
+        if (p.fuse)
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (j < n_out) w5[j] = fl.W[(int64_t)j * fl.ldw + nl];
+        uint32_t i = 0;
+        for (int t = blockIdx.x; t < us.units; t += G, ++i) {
+            const Unit w = unit_of(us, t);
+            const uint32_t b = i & 1u, j = i >> 1;
+            // one thread waits, the four warps take its answer (they stay together
+            // at the named barriers below)
+            if (et == 0) sflag[0] = mbar_wait(&accf[b], j & 1u, kWaitLimit) ? 1u : 0u;
+            epi_bar();
+            const bool got = sflag[0] != 0u;
+            if (!got) {
+                ok = false;
+                break;
+            }
+            tc_fence_after();
+            const uint32_t tl = tmem + ((uint32_t)(q * 32) << 16) + b * XP;
+            const int n = w.n0 + nl;
+            const float bn = p.bias[n];
+            bool finish = us.splits == 1;
+            int cs = 0, ce = w.pcount;   // the columns this unit finishes
+            if (finish) {
+                for (int c0 = 0; c0 < 32 * w.pn; c0 += 32) {
+                    uint32_t r[32];
+                    uint32_t(&r0)[16] = *reinterpret_cast<uint32_t(*)[16]>(&r[0]);
+                    uint32_t(&r1)[16] = *reinterpret_cast<uint32_t(*)[16]>(&r[16]);
+                    tmem_ld16(tl + (uint32_t)c0, r0);
+                    tmem_ld16(tl + (uint32_t)c0 + 16, r1);
+                    tmem_ld_wait();
+#pragma unroll
+                    for (int cc = 0; cc < 32; ++cc)
+                        finish_one(__uint_as_float(r[cc]), c0 + cc, c0 + cc < w.pcount, w, p, n,
+                                   bn, w5, n_out, q, lane, sred);
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&acce[b]);
+            } else {
+                // this split's partial tile [c][nl], then the arrival count of the tile
+                float* dst = p.part + (int64_t)t * XP * 128;
+                for (int c0 = 0; c0 < 32 * w.pn; c0 += 32) {
+                    uint32_t r[32];
+                    uint32_t(&r0)[16] = *reinterpret_cast<uint32_t(*)[16]>(&r[0]);
+                    uint32_t(&r1)[16] = *reinterpret_cast<uint32_t(*)[16]>(&r[16]);
+                    tmem_ld16(tl + (uint32_t)c0, r0);
+                    tmem_ld16(tl + (uint32_t)c0 + 16, r1);
+                    tmem_ld_wait();
+#pragma unroll
+                    for (int cc = 0; cc < 32; ++cc)
+                        if (c0 + cc < w.pcount) __stcg(dst + (c0 + cc) * 128 + nl, __uint_as_float(r[cc]));
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&acce[b]);
+                // every split of the tile finishes its own share of the columns,
+                // once all the tile's partial tiles are written (one unit per CTA
+                // here, and the grid is co-resident: the wait ends)
+                __threadfence();
+                epi_bar();
+                if (et == 0) {
+                    atomicAdd(&p.ctr[w.pair], 1u);
+                    uint32_t it = 0;
+                    while (ld_acquire(&p.ctr[w.pair]) < (unsigned)us.splits && ++it < kWaitLimit) {
+                    }
+                    sflag[1] = it < kWaitLimit ? 1u : 0u;
+                }
+                epi_bar();
+                if (sflag[1] == 0u) {
+                    ok = false;
+                    break;
+                }
+                __threadfence();
+                cs = (int)((long long)w.split * w.pcount / us.splits);
+                ce = (int)((long long)(w.split + 1) * w.pcount / us.splits);
+                const float* src = p.part + (int64_t)w.pair * us.splits * XP * 128 + nl;
+                // four columns at a time, every split's value loaded before the
+                // sums, which run in split order
+                for (int c = cs; c < ce; c += 4) {
+                    float v[4] = {0.f, 0.f, 0.f, 0.f};
+                    float t2[kMaxSplits][4];
+#pragma unroll
+                    for (int s2 = 0; s2 < kMaxSplits; ++s2)
+#pragma unroll
+                        for (int j = 0; j < 4; ++j)
+                            t2[s2][j] = (s2 < us.splits && c + j < ce)
+                                            ? __ldcg(src + ((int64_t)s2 * XP + c + j) * 128)
+                                            : 0.f;
+#pragma unroll
+                    for (int s2 = 0; s2 < kMaxSplits; ++s2)
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) v[j] += t2[s2][j];
+#pragma unroll
+                    for (int j = 0; j < 4; ++j)
+                        if (c + j < ce)
+                            finish_one(v[j], c + j, true, w, p, n, bn, w5, n_out, q, lane, sred);
+                }
+                finish = true;
+                // the last split out resets the tile's counters for the next launch
+                epi_bar();
+                if (et == 0) {
+                    const unsigned int prev = atomicAdd(&p.ctr[kX3MaxUnits + w.pair], 1u);
+                    if (prev + 1u == (unsigned)us.splits) {
+                        p.ctr[w.pair] = 0u;
+                        p.ctr[kX3MaxUnits + w.pair] = 0u;
+                    }
+                }
+            }
+            if (p.fuse && finish) {
+                // the last layer: the four quadrants' sums per point, in order
+                epi_bar();
+                if (et >= cs && et < ce) {
+                    float tt[4];
+#pragma unroll
+                    for (int jo = 0; jo < 4; ++jo) {
+                        tt[jo] = 0.f;
+                        if (jo < n_out)
+                            for (int qq = 0; qq < 4; ++qq) tt[jo] += sred[(qq * XP + et) * 4 + jo];
+                    }
+                    last_epilogue(fl.epi, fl.p0 + w.p0 + et, n_out, tt, fl.bias);
+                }
+            }
+            epi_bar();   // sflag and sred are free for the next unit
+        }
+    }
+    if (!ok) atomicOr(p.err, 1u);
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) tmem_dealloc(tmem, kTmemCols);
+}
+
+// One thread per (point, group of 8 quads of the row): hi and lo planes.
+constexpr int kQG = 8;
+
+__global__ void __launch_bounds__(256) gather_x3_kernel(PointSrc src, int64_t p0, int64_t m,
+                                                        Calib calib, Map map0, Map map1,
+                                                        float* __restrict__ X, int KX) {
+    const uint32_t nq = (uint32_t)KX >> 2;
+    const uint32_t ng = (nq + kQG - 1) / kQG;
+    if (src.count) m = min(m, (int64_t)*src.count);
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < m * ng;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t lp = (uint32_t)(t / ng);
+        const uint32_t q0 = ((uint32_t)t - lp * ng) * kQG;
+        const PointSample ps = sample_point(src, p0 + lp, calib, map0, map1);
+        float* row = X + (int64_t)lp * 2 * KX;
+#pragma unroll
+        for (uint32_t j = 0; j < kQG; ++j) {
+            if (q0 + j >= nq) break;
+            const float4 v = sample_quad(ps, 4 * (int)(q0 + j));
+            float4 hi, lo;
+            hi.x = tf32_round(v.x);
+            hi.y = tf32_round(v.y);
+            hi.z = tf32_round(v.z);
+            hi.w = tf32_round(v.w);
+            lo.x = tf32_round(v.x - hi.x);
+            lo.y = tf32_round(v.y - hi.y);
+            lo.z = tf32_round(v.z - hi.z);
+            lo.w = tf32_round(v.w - hi.w);
+            *reinterpret_cast<float4*>(row + 4 * (q0 + j)) = hi;
+            *reinterpret_cast<float4*>(row + KX + 4 * (q0 + j)) = lo;
+        }
+    }
+}
+
+bool g_attr_set[64] = {};
+int g_n_sm[64] = {};
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+
+cudaError_t ensure_attr(int dev, int* sms) {
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (!g_attr_set[dev]) {
+        cudaError_t e = cudaFuncSetAttribute(x3_layer_kernel,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)kSmemBytes);
+        if (e == cudaSuccess)
+            e = cudaDeviceGetAttribute(&g_n_sm[dev], cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return e;
+        g_attr_set[dev] = true;
+    }
+    *sms = g_n_sm[dev];
+    return cudaSuccess;
+}
+
+}  // namespace
+
+bool x3_encode_2d(void* map, const void* base, uint64_t cols, uint64_t rows,
+                  uint64_t row_stride_bytes, uint32_t box_cols, uint32_t box_rows) {
+    if (!g_encode) {
+        cudaDriverEntryPointQueryResult q;
+        void* fn = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
+                                             &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess || !fn)
+            return false;
+        g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    }
+    const cuuint64_t dims[2] = {cols, rows};
+    const cuuint64_t strides[1] = {row_stride_bytes};
+    const cuuint32_t box[2] = {box_cols, box_rows};
+    const cuuint32_t estr[2] = {1, 1};
+    return g_encode(static_cast<CUtensorMap*>(map), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
+                    const_cast<void*>(base), dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+cudaError_t x3_prepare() {
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = ensure_attr(dev, &sms);
+    return e;
+}
+
+cudaError_t launch_x3_layer(const X3LayerArgs& a, cudaStream_t s) {
+    if (a.M <= 0) return cudaSuccess;
+    if (a.N <= 0 || a.N % 128 != 0 || a.KH % XK != 0 || a.KX % XK != 0 ||
+        a.KP != a.KH + a.KX || a.nk1 * XK != a.KH || a.nk2 * XK != a.KX || a.nk1 + a.nk2 < 1 ||
+        (a.nk1 > 0 && !a.tmH) || (a.nk2 > 0 && !a.tmX) || !a.tmW || !a.bias || !a.part ||
+        !a.ctr || !a.err)
+        return cudaErrorInvalidValue;
+    if (a.fuse ? (a.N != 128 || a.fuse->n_out < 1 || a.fuse->n_out > 4) : !a.out)
+        return cudaErrorInvalidValue;
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = ensure_attr(dev, &sms);
+    if (e != cudaSuccess) return e;
+    X3Params p{};
+    p.nk1 = a.nk1;
+    p.nk2 = a.nk2;
+    p.KH = a.KH;
+    p.KX = a.KX;
+    p.KP = a.KP;
+    p.M = a.M;
+    p.N = a.N;
+    p.fuse = a.fuse ? 1 : 0;
+    p.m_dev = a.m_dev;
+    p.bias = a.bias;
+    p.slope = a.slope;
+    p.out = a.out;
+    p.part = a.part;
+    p.ctr = a.ctr;
+    p.err = a.err;
+    const FuseLast fl = a.fuse ? *a.fuse : FuseLast{};
+    // one CTA per SM (the ring takes 192 KB); at most kX3MaxUnits, which bounds
+    // the split-K partial tiles
+    const int grid = sms < kX3MaxUnits ? sms : kX3MaxUnits;
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = kSmemBytes;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    const CUtensorMap& mh = a.nk1 > 0 ? *a.tmH : *a.tmW;
+    const CUtensorMap& mx = a.nk2 > 0 ? *a.tmX : *a.tmW;
+    return cudaLaunchKernelEx(&cfg, x3_layer_kernel, *a.tmW, mh, mx, p, fl);
+}
+
+cudaError_t launch_gather_x3(const PointSrc& src, int64_t p0, int64_t m, const Calib& calib,
+                             const Map& map0, const Map& map1, float* X, int KX,
+                             cudaStream_t stream) {
+    if (m <= 0) return cudaSuccess;
+    if (KX <= 0 || KX % 32 != 0) return cudaErrorInvalidValue;
+    const int64_t total = m * ((KX / 4 + kQG - 1) / kQG);
+    const int64_t exact = (total + 255) / 256;
+    const unsigned blocks = (unsigned)(src.count ? (exact < 152 * 8 ? exact : 152 * 8) : exact);
+    gather_x3_kernel<<<blocks, 256, 0, stream>>>(src, p0, m, calib, map0, map1, X, KX);
+    return cudaGetLastError();
+}
+
+}  // namespace pifu

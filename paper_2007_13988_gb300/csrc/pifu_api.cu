@@ -55,6 +55,7 @@ int pifu_create(const void* weight_blob, size_t bytes, pifu_ctx** out) {
     if (st == PIFU_OK) st = upload_net(ctx, hn[1], ctx->net[1]);
     if (st == PIFU_OK) st = ensure_mlp_ws(ctx);
     if (st == PIFU_OK && !cbn) st = build_tc(ctx, hn[0], ctx->net[0]);
+    if (st == PIFU_OK && !cbn) st = build_x3(ctx, hn[0], ctx->net[0]);
     if (st == PIFU_OK) st = build_tc(ctx, hn[1], ctx->net[1]);
     if (st == PIFU_OK) {
         cudaError_t e = cudaMalloc(&ctx->d_count, 2 * sizeof(unsigned int));
@@ -109,6 +110,11 @@ void pifu_destroy(pifu_ctx* ctx) {
     dev_free(ctx->Hb[1]);
     dev_free(ctx->chain_dep);
     dev_free(ctx->part);
+    dev_free(ctx->X3);
+    dev_free(ctx->H3[0]);
+    dev_free(ctx->H3[1]);
+    dev_free(ctx->x3_part);
+    dev_free(ctx->x3_ctr);
     uint32_t** bitsets[] = {&ctx->cand, &ctx->tent, &ctx->bin[0], &ctx->bin[1],
                             &ctx->eval, &ctx->conf[0], &ctx->conf[1]};
     for (auto b : bitsets) dev_free(*b);

@@ -3,6 +3,7 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <cstring>
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -237,6 +238,60 @@ cudaError_t launch_tc_linear(const TcLayerArgs& a, cudaStream_t stream);
 // Set the tensor-core kernels' attributes on the current device (before a
 // stream capture: launches inside a capture then make no attribute calls).
 cudaError_t tc_prepare();
+
+// --- mlp_x3.cu ---------------------------------------------------------------
+// FP32-accurate hidden layers on the tensor cores for small batches: each
+// FP32 value v is held as two TF32 values, hi = tf32(v) and
+// lo = tf32(v - hi), and each product as a_hi b_hi + a_hi b_lo + a_lo b_hi.
+//
+// v rounded to TF32 (10 explicit mantissa bits, ties away from zero): the
+// 13 low bits of the FP32 encoding cleared after adding half of their range
+// (sign-magnitude, so the same for both signs).  Finite v only.
+__host__ __device__ __forceinline__ float tf32_round(float v) {
+    uint32_t u;
+    memcpy(&u, &v, 4);
+    u = (u + 0x1000u) & 0xFFFFE000u;
+    float r;
+    memcpy(&r, &u, 4);
+    return r;
+}
+
+constexpr int kX3MaxUnits = 256;   // work units of one launch that hold split-K partials
+constexpr int kX3Tile = 128;       // points and neurons per work unit
+
+// One hidden layer over [H | X] (split planes: a row of K values is stored
+// as 2 K floats, the hi values then the lo values):
+//   out[p][n] = lrelu(b[n] + sum_k W[n][k] [H | X][p][k]),
+// written back as hi/lo planes [rows][2 N], or, with `fuse`, handed to the
+// last layer (FP32) and its epilogue.  N a multiple of 128 (fuse: N = 128).
+struct X3LayerArgs {
+    const CUtensorMap* tmW;      // [N][2 KP] FP32, box 32 x 128, 128-byte swizzle
+    const CUtensorMap* tmH;      // [rows][2 KH] previous layer's planes, box 32 x 32
+    const CUtensorMap* tmX;      // [rows][2 KX] input-row planes, box 32 x 32
+    int nk1, nk2;                // 32-value K-blocks from H, then from X
+    int KH, KX, KP;              // lo-plane column offsets (KP = KH + KX)
+    int M, N;                    // points (a capacity with m_dev), neurons
+    const unsigned int* m_dev;   // optional device-resident point count (<= M)
+    const float* bias;
+    float slope;
+    float* out;                  // [rows][2 N] (null with fuse)
+    const FuseLast* fuse;        // optional: last layer (N = 128, n_out <= 4)
+    float* part;                 // [kX3MaxUnits][128][128] split-K partial tiles
+    unsigned int* ctr;           // [2][kX3MaxUnits] arrivals and departures per tile, zero
+                                 // between launches
+    unsigned int* err;
+};
+cudaError_t launch_x3_layer(const X3LayerArgs& a, cudaStream_t stream);
+// X[p][0 .. 2 KX) = hi and lo planes of the gather row of point p0 + p
+// (KX a multiple of 32, columns past d_in zero).
+cudaError_t launch_gather_x3(const PointSrc& src, int64_t p0, int64_t m, const Calib& calib,
+                             const Map& map0, const Map& map1, float* X, int KX,
+                             cudaStream_t stream);
+cudaError_t x3_prepare();
+// Tensor map of an FP32 matrix [rows][cols] (row stride in bytes), box
+// box_cols x box_rows, 128-byte swizzle.
+bool x3_encode_2d(void* map, const void* base, uint64_t cols, uint64_t rows,
+                  uint64_t row_stride_bytes, uint32_t box_cols, uint32_t box_rows);
 
 // --- mlp_chain.cu ------------------------------------------------------------
 // All hidden layers of one BF16 batch in one persistent launch (rows move
@@ -502,10 +557,12 @@ cudaError_t launch_mlp_fused(const FusedNet& net, const PointSrc& src, int64_t p
                              const Calib& calib, const Map& map0, const Map& map1,
                              const Epilogue& epi, cudaStream_t stream, int cl = 0);
 // Graph form: sets the switch `h` to the index (in `plan`) of the cluster
-// size the device-resident batch size min(*count, cap) calls for, or to
-// plan.n (no branch) when it is 0.
+// size the device-resident batch size c = min(*count, cap) calls for; to
+// plan.n when x3_lo < c <= x3_hi (the split-TF32 body, if the switch has
+// one: x3_hi > 0); to a value past every body (no branch) when c is 0.
 cudaError_t launch_fused_switch(cudaGraphConditionalHandle h, const FusedPlan& plan,
-                                const unsigned int* count, unsigned int cap, cudaStream_t stream);
+                                const unsigned int* count, unsigned int cap, cudaStream_t stream,
+                                unsigned int x3_lo = 0, unsigned int x3_hi = 0);
 
 // --- cbn.cu --------------------------------------------------------------
 // The CBN + SoftZ occupancy network (Appendix, Eq. 7 and Eq. 8) in FP32, with

@@ -360,7 +360,9 @@ int s_build(pifu_ctx* ctx, const StreamKey& k) {
         // the surrogate's f_O pass takes up to twice a round's list (its
         // finest-level keys and the fall-backs)
         const int64_t rows = k.use_surrogate ? std::min<int64_t>(2 * w.cap, kTcRowsMax) : w.cap;
-        const int st = ensure_tc_rows(ctx, rows);
+        int st = ensure_tc_rows(ctx, rows);
+        if (st == PIFU_OK && (k.precision == PIFU_PREC_MIXED || k.precision == PIFU_PREC_FP8_MIXED))
+            st = ensure_x3(ctx);
         if (st != PIFU_OK) return st;
     }
     // g_eval's queues are the context's; point them at the stream's for the capture

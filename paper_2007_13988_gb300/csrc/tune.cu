@@ -228,6 +228,15 @@ int pifu_set_schedule(pifu_ctx* ctx, int schedule) {
     return PIFU_OK;
 }
 
+int pifu_set_recheck(pifu_ctx* ctx, int form) {
+    if (!ctx || (form != PIFU_RECHECK_TENSOR && form != PIFU_RECHECK_SIMT)) return PIFU_ERR_ARG;
+    ctx->recheck_form = form;
+    ctx->g_valid = false;
+    ctx->batch.g_valid = false;
+    ctx->stream.g_valid = false;
+    return PIFU_OK;
+}
+
 int pifu_set_tiles(pifu_ctx* ctx, const int32_t* codes, int n) {
     if (!ctx || n < 0 || (n > 0 && !codes)) return PIFU_ERR_ARG;
     DeviceGuard g(ctx->device);

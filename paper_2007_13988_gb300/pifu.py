@@ -45,7 +45,8 @@ EXPORTS = ("pifu_create", "pifu_destroy", "pifu_query", "pifu_query_colour", "pi
            "pifu_surrogate_train", "pifu_surrogate_params", "pifu_surrogate_query",
            "pifu_calibrate_fp8", "pifu_frames", "pifu_autotune", "pifu_surrogate_ohem_init",
            "pifu_surrogate_ohem_weights", "pifu_surrogate_ohem_sample",
-           "pifu_surrogate_train_ohem", "pifu_set_tiles", "pifu_set_schedule", "pifu_stream")
+           "pifu_surrogate_train_ohem", "pifu_set_tiles", "pifu_set_schedule", "pifu_stream",
+           "pifu_set_recheck")
 
 KERNEL_CLASSES = ("gather", "mlp_hidden", "mlp_last", "level", "select", "render", "mlp_f32",
                   "cbn_tc")
@@ -157,6 +158,8 @@ def _lib():
     lib.pifu_set_tiles.restype = I
     lib.pifu_set_schedule.argtypes = [P, I]
     lib.pifu_set_schedule.restype = I
+    lib.pifu_set_recheck.argtypes = [P, I]
+    lib.pifu_set_recheck.restype = I
     lib.pifu_calibrate_fp8.argtypes = [P, ctypes.POINTER(pifu_fmap), ctypes.POINTER(F), I, P]
     lib.pifu_calibrate_fp8.restype = I
     lib.pifu_surrogate_init.argtypes = [P, I, I, U64]
@@ -439,6 +442,16 @@ PIFU_SCHED_CHAINED = 1
 def pifu_set_schedule(ctx, schedule):
     """Per-layer launches (default) or chained (all hidden layers in one launch)."""
     _check(_lib().pifu_set_schedule(ctx, int(schedule)), "pifu_set_schedule", ctx)
+
+
+PIFU_RECHECK_TENSOR = 0
+PIFU_RECHECK_SIMT = 1
+
+
+def pifu_set_recheck(ctx, form):
+    """Arithmetic of the MIXED forms' FP32 passes: split TF32 on the tensor
+    cores (default) or the FP32 SIMT network."""
+    _check(_lib().pifu_set_recheck(ctx, int(form)), "pifu_set_recheck", ctx)
 
 
 def pifu_set_tiles(ctx, codes):
