@@ -396,7 +396,7 @@ int pifu_set_schedule(pifu_ctx* ctx, int schedule);
  *     of the FP64 network in occupancy (the FP32 SIMT network: about 1e-6).
  *     Smaller passes run the FP32 SIMT network, whose one launch has the
  *     lower latency there.  Needs hidden widths that are multiples of 128,
- *     the last one 128 wide, and a last layer of at most 4 outputs reading
+ *     the last one 128 wide, and a one-output last layer reading
  *     only it; other networks (and the CBN network) use the SIMT form.  The
  *     first MIXED call of a context reserves its workspace: 16,384 points x
  *     (2 d_in + 4 widest hidden width) floats plus 16 MB.

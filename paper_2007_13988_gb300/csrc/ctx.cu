@@ -438,7 +438,9 @@ int build_tc(pifu_ctx* ctx, const HostNet& hn, DevNet& net) {
 // Weights of the split-TF32 layers: per hidden layer [n_out][2 KP], the TF32
 // value hi = tf32(w) of every weight in columns [0, KP) and lo = tf32(w - hi)
 // in [KP, 2 KP), the h part first, then the x part zero-padded to KX.  Nets
-// of other shapes keep x3_ok = false (their FP32 passes use the SIMT kernels).
+// of other shapes (hidden widths not multiples of 128, a last hidden layer
+// other than 128 wide, a last layer of more than one output or reading x)
+// keep x3_ok = false: their FP32 passes use the SIMT kernels.
 int build_x3(pifu_ctx* ctx, const HostNet& hn, DevNet& net) {
     (void)ctx;
     net.x3_ok = false;
@@ -449,8 +451,7 @@ int build_x3(pifu_ctx* ctx, const HostNet& hn, DevNet& net) {
         if (Ly.n_out % kX3Tile != 0 || (l == 0) != (Ly.K1 == 0)) return PIFU_OK;
     }
     const DevLayer& Ll = net.layers[(size_t)L - 1];
-    if (net.layers[(size_t)L - 2].n_out != kX3Tile || Ll.K2 != 0 || Ll.n_out < 1 || Ll.n_out > 4)
-        return PIFU_OK;
+    if (net.layers[(size_t)L - 2].n_out != kX3Tile || Ll.K2 != 0 || Ll.n_out != 1) return PIFU_OK;
     const int KX = round_up(net.d_in, 32);
     net.x3.assign((size_t)L - 1, X3Layer{});
     for (int l = 0; l + 1 < L; ++l) {

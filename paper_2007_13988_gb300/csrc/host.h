@@ -104,8 +104,8 @@ struct DevNet {
     float s_x = 0.f;                // per-tensor scale of the input rows (reported)
     uint64_t f8_version = 0;        // bumped by every calibration
     // split-TF32 form (the MIXED forms' FP32-accurate passes): hidden widths
-    // multiples of 128, the last hidden one 128 wide, a last layer of <= 4
-    // outputs reading only it
+    // multiples of 128, the last hidden one 128 wide, a one-output last layer
+    // reading only it
     bool x3_ok = false;
     std::vector<X3Layer> x3;
     int x3_KX = 0;                  // x part of a plane row: d_in rounded up to 32

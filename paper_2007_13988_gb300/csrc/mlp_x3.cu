@@ -26,14 +26,14 @@
 // and finishes its share of the tile's columns: the partials summed in split
 // order (the same sums whichever CTA takes a column), the bias, the leaky
 // ReLU, and the hi/lo planes written -- or, in the last hidden layer, the
-// last layer in FP32 and the network's epilogue.  Without a split the unit
+// one-output last layer in FP32 and the network's epilogue.  Without a split the unit
 // finishes from tensor memory.
 //
 // Persistent, warp-specialised: warp 0 lane 0 loads W and point tiles by TMA
 // into a 3-stage ring (64 KB a stage: hi and lo of both operands), warp 1
-// lane 0 issues the MMAs into one of two TMEM accumulators, warps 2-5 (one
-// TMEM lane quadrant each, one neuron per thread) run the epilogue of one
-// unit while the next unit's MMAs run.  Every mbarrier wait is bounded; a
+// lane 0 issues the MMAs into one of two TMEM accumulators, warps 2-9 (two
+// per TMEM lane quadrant, one neuron per thread) run the epilogue of one unit
+// while the next unit's MMAs run.  Every mbarrier wait is bounded; a
 // wait that gives up sets *err and the roles stop.
 #include <cuda.h>
 #include <cudaTypedefs.h>
@@ -55,11 +55,11 @@ constexpr uint32_t W_PLANE = 128 * 128;             // 128 neuron rows x 128 byt
 constexpr uint32_t P_PLANE = XP * 128;              // 128 point rows x 128 bytes
 constexpr uint32_t P_BOX = 32 * 128;                // one 32-row TMA box of points
 constexpr uint32_t STAGE_BYTES = 2 * W_PLANE + 2 * P_PLANE;
-constexpr int kThreads = 192;
+constexpr int kThreads = 320;                       // 2 role warps + 8 epilogue warps
 constexpr uint32_t kTmemCols = 2 * XP;              // two accumulators
 constexpr uint32_t kWaitLimit = 1u << 20;           // polls; legitimate waits are microseconds
 constexpr int kMaxSplits = 8;
-constexpr uint32_t kSmemBytes = XNST * STAGE_BYTES + 1024 + 256 + 4 * XP * 4 * 4;
+constexpr uint32_t kSmemBytes = XNST * STAGE_BYTES + 1024 + 256 + 4 * XP * 4;
 static_assert(kSmemBytes <= 227 * 1024, "shared memory");
 static_assert(XP == 128, "one TMEM lane per neuron, 128 columns per accumulator");
 
@@ -117,7 +117,7 @@ __device__ __forceinline__ Unit unit_of(const Units& us, int t) {
     return w;
 }
 
-__device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+__device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
 
 __device__ __forceinline__ float warp_sum(float x) {
 #pragma unroll
@@ -127,15 +127,15 @@ __device__ __forceinline__ float warp_sum(float x) {
 
 // Finishes column c (point p0 + c of the unit) of this thread's neuron n from
 // its accumulated sum a: bias, leaky ReLU, then the hi/lo planes of the
-// output, or (fuse) the point's contribution to the last layer summed over
-// the warp's 32 neurons into sred[q][c][j].  c is warp-uniform.
+// output, or (FUSE) the point's contribution to the one-output last layer,
+// summed over the warp's 32 neurons into sred[q][c].  c is warp-uniform.
+template <bool FUSE>
 __device__ __forceinline__ void finish_one(float a, int c, bool live, const Unit& w,
-                                           const X3Params& p, int n, float bn,
-                                           const float (&w5)[4], int n_out, int q, int lane,
-                                           float* sred) {
+                                           const X3Params& p, int n, float bn, float w5, int q,
+                                           int lane, float* sred) {
     float h = a + bn;
     h = h >= 0.f ? h : p.slope * h;
-    if (!p.fuse) {
+    if (!FUSE) {
         if (live) {
             const float hi = tf32_round(h);
             const float lo = tf32_round(h - hi);
@@ -144,13 +144,8 @@ __device__ __forceinline__ void finish_one(float a, int c, bool live, const Unit
             __stcg(row + p.N + n, lo);
         }
     } else {
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            if (j < n_out) {
-                const float t = warp_sum(h * w5[j]);
-                if (lane == 0) sred[(q * XP + c) * 4 + j] = t;
-            }
-        }
+        const float t = warp_sum(h * w5);
+        if (lane == 0) sred[q * XP + c] = t;
     }
 }
 
@@ -161,6 +156,7 @@ __device__ __forceinline__ unsigned int ld_acquire(const unsigned int* a) {
     return v;
 }
 
+template <bool FUSE>
 __global__ void __launch_bounds__(kThreads, 1) x3_layer_kernel(
     const __grid_constant__ CUtensorMap tmW, const __grid_constant__ CUtensorMap tmH,
     const __grid_constant__ CUtensorMap tmX, const X3Params p, const FuseLast fl) {
@@ -173,7 +169,7 @@ __global__ void __launch_bounds__(kThreads, 1) x3_layer_kernel(
     uint64_t* acce = accf + 2;       // [2] accumulator drained by the epilogue
     uint32_t* tslot = reinterpret_cast<uint32_t*>(acce + 2);
     volatile uint32_t* sflag = tslot + 1;   // [0] accumulator ready, [1] last split of the tile
-    float* sred = reinterpret_cast<float*>(ring + XNST * STAGE_BYTES + 256);   // [4][XP][4]
+    float* sred = reinterpret_cast<float*>(ring + XNST * STAGE_BYTES + 256);   // [4][XP]
 
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
@@ -186,7 +182,7 @@ __global__ void __launch_bounds__(kThreads, 1) x3_layer_kernel(
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&accf[b], 1);
-            mbar_init(&acce[b], 4);   // one arrival per epilogue warp
+            mbar_init(&acce[b], 8);   // one arrival per epilogue warp
         }
         fence_mbar_init();
         prefetch_tmap(&tmW);
@@ -272,22 +268,23 @@ __global__ void __launch_bounds__(kThreads, 1) x3_layer_kernel(
             }
         }
     } else {
-        // epilogue warps 2..5: TMEM lane quadrant q = neurons 32 q .. 32 q + 31
+        // epilogue warps 2..9: TMEM lane quadrant q = neurons 32 q .. 32 q + 31,
+        // one neuron per thread; the quadrant's two warps (half 0: warps 2-5,
+        // half 1: warps 6-9) take alternate groups of columns.  The epilogue
+        // runs once or twice per CTA and launch, from a cold instruction
+        // cache, and a TMEM load takes hundreds of cycles: 16 columns per
+        // load, the next group's load in flight while this one is finished.
         const int q = warp & 3;
+        const int half = (warp - 2) >> 2;
         const int nl = q * 32 + lane;
-        const int et = (int)threadIdx.x - 64;   // 0 .. 127
-        const int n_out = p.fuse ? fl.n_out : 0;
-        float w5[4] = {0.f, 0.f, 0.f, 0.f};
-        if (p.fuse)
-#pragma unroll
-            for (int j = 0; j < 4; ++j)
-                if (j < n_out) w5[j] = fl.W[(int64_t)j * fl.ldw + nl];
+        const int et = (int)threadIdx.x - 64;   // 0 .. 255
+        const float w5 = FUSE ? fl.W[nl] : 0.f;   // the last layer's weight of this neuron
         uint32_t i = 0;
         for (int t = blockIdx.x; t < us.units; t += G, ++i) {
             const Unit w = unit_of(us, t);
             const uint32_t b = i & 1u, j = i >> 1;
-            // one thread waits, the four warps take its answer (they stay together
-            // at the named barriers below)
+            // one thread waits, the eight warps take its answer (they stay
+            // together at the named barriers below)
             if (et == 0) sflag[0] = mbar_wait(&accf[b], j & 1u, kWaitLimit) ? 1u : 0u;
             epi_bar();
             const bool got = sflag[0] != 0u;
@@ -299,41 +296,49 @@ __global__ void __launch_bounds__(kThreads, 1) x3_layer_kernel(
             const uint32_t tl = tmem + ((uint32_t)(q * 32) << 16) + b * XP;
             const int n = w.n0 + nl;
             const float bn = p.bias[n];
-            bool finish = us.splits == 1;
+            const bool direct = us.splits == 1;
+            float* dst = p.part + (int64_t)t * XP * 128;   // this split's partial tile [c][nl]
+            {
+                const int ng = (w.pcount + 15) >> 4;   // 16-column groups: g = half, half + 2, ..
+                uint32_t ra[16], rb[16];
+                int g = half;
+                if (g < ng) tmem_ld16(tl + (uint32_t)(16 * g), ra);
+                tmem_ld_wait();
+                // two loops, each with one short body (the instruction cache)
+                if (direct) {
+                    while (g < ng) {
+                        const int gn = g + 2;
+                        if (gn < ng) tmem_ld16(tl + (uint32_t)(16 * gn), rb);
+#pragma unroll
+                        for (int cc = 0; cc < 16; ++cc)
+                            finish_one<FUSE>(__uint_as_float(ra[cc]), 16 * g + cc,
+                                             16 * g + cc < w.pcount, w, p, n, bn, w5, q, lane,
+                                             sred);
+                        tmem_ld_wait();
+#pragma unroll
+                        for (int cc = 0; cc < 16; ++cc) ra[cc] = rb[cc];
+                        g = gn;
+                    }
+                } else {
+                    while (g < ng) {
+                        const int gn = g + 2;
+                        if (gn < ng) tmem_ld16(tl + (uint32_t)(16 * gn), rb);
+#pragma unroll
+                        for (int cc = 0; cc < 16; ++cc)
+                            if (16 * g + cc < w.pcount)
+                                __stcg(dst + (16 * g + cc) * 128 + nl, __uint_as_float(ra[cc]));
+                        tmem_ld_wait();
+#pragma unroll
+                        for (int cc = 0; cc < 16; ++cc) ra[cc] = rb[cc];
+                        g = gn;
+                    }
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&acce[b]);
+            }
             int cs = 0, ce = w.pcount;   // the columns this unit finishes
-            if (finish) {
-                for (int c0 = 0; c0 < 32 * w.pn; c0 += 32) {
-                    uint32_t r[32];
-                    uint32_t(&r0)[16] = *reinterpret_cast<uint32_t(*)[16]>(&r[0]);
-                    uint32_t(&r1)[16] = *reinterpret_cast<uint32_t(*)[16]>(&r[16]);
-                    tmem_ld16(tl + (uint32_t)c0, r0);
-                    tmem_ld16(tl + (uint32_t)c0 + 16, r1);
-                    tmem_ld_wait();
-#pragma unroll
-                    for (int cc = 0; cc < 32; ++cc)
-                        finish_one(__uint_as_float(r[cc]), c0 + cc, c0 + cc < w.pcount, w, p, n,
-                                   bn, w5, n_out, q, lane, sred);
-                }
-                tc_fence_before();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&acce[b]);
-            } else {
-                // this split's partial tile [c][nl], then the arrival count of the tile
-                float* dst = p.part + (int64_t)t * XP * 128;
-                for (int c0 = 0; c0 < 32 * w.pn; c0 += 32) {
-                    uint32_t r[32];
-                    uint32_t(&r0)[16] = *reinterpret_cast<uint32_t(*)[16]>(&r[0]);
-                    uint32_t(&r1)[16] = *reinterpret_cast<uint32_t(*)[16]>(&r[16]);
-                    tmem_ld16(tl + (uint32_t)c0, r0);
-                    tmem_ld16(tl + (uint32_t)c0 + 16, r1);
-                    tmem_ld_wait();
-#pragma unroll
-                    for (int cc = 0; cc < 32; ++cc)
-                        if (c0 + cc < w.pcount) __stcg(dst + (c0 + cc) * 128 + nl, __uint_as_float(r[cc]));
-                }
-                tc_fence_before();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&acce[b]);
+            if (!direct) {
                 // every split of the tile finishes its own share of the columns,
                 // once all the tile's partial tiles are written (one unit per CTA
                 // here, and the grid is co-resident: the wait ends)
@@ -355,28 +360,31 @@ __global__ void __launch_bounds__(kThreads, 1) x3_layer_kernel(
                 cs = (int)((long long)w.split * w.pcount / us.splits);
                 ce = (int)((long long)(w.split + 1) * w.pcount / us.splits);
                 const float* src = p.part + (int64_t)w.pair * us.splits * XP * 128 + nl;
-                // four columns at a time, every split's value loaded before the
-                // sums, which run in split order
-                for (int c = cs; c < ce; c += 4) {
+                // four columns at a time (alternate fours per half), every split's
+                // value loaded before the sums, which run in split order; loads
+                // from clamped (valid) addresses, masked afterwards, so that no
+                // branch stands between them
+                for (int c = cs + 4 * half; c < ce; c += 8) {
                     float v[4] = {0.f, 0.f, 0.f, 0.f};
                     float t2[kMaxSplits][4];
 #pragma unroll
                     for (int s2 = 0; s2 < kMaxSplits; ++s2)
 #pragma unroll
-                        for (int j = 0; j < 4; ++j)
-                            t2[s2][j] = (s2 < us.splits && c + j < ce)
-                                            ? __ldcg(src + ((int64_t)s2 * XP + c + j) * 128)
-                                            : 0.f;
+                        for (int jj = 0; jj < 4; ++jj) {
+                            const int sc = s2 < us.splits ? s2 : 0;
+                            const int cj = min(c + jj, ce - 1);
+                            const float x = __ldcg(src + ((int64_t)sc * XP + cj) * 128);
+                            t2[s2][jj] = (s2 < us.splits && c + jj < ce) ? x : 0.f;
+                        }
 #pragma unroll
                     for (int s2 = 0; s2 < kMaxSplits; ++s2)
 #pragma unroll
-                        for (int j = 0; j < 4; ++j) v[j] += t2[s2][j];
+                        for (int jj = 0; jj < 4; ++jj) v[jj] += t2[s2][jj];
 #pragma unroll
-                    for (int j = 0; j < 4; ++j)
-                        if (c + j < ce)
-                            finish_one(v[j], c + j, true, w, p, n, bn, w5, n_out, q, lane, sred);
+                    for (int jj = 0; jj < 4; ++jj)
+                        if (c + jj < ce)
+                            finish_one<FUSE>(v[jj], c + jj, true, w, p, n, bn, w5, q, lane, sred);
                 }
-                finish = true;
                 // the last split out resets the tile's counters for the next launch
                 epi_bar();
                 if (et == 0) {
@@ -387,18 +395,13 @@ __global__ void __launch_bounds__(kThreads, 1) x3_layer_kernel(
                     }
                 }
             }
-            if (p.fuse && finish) {
+            if (FUSE) {
                 // the last layer: the four quadrants' sums per point, in order
                 epi_bar();
                 if (et >= cs && et < ce) {
-                    float tt[4];
-#pragma unroll
-                    for (int jo = 0; jo < 4; ++jo) {
-                        tt[jo] = 0.f;
-                        if (jo < n_out)
-                            for (int qq = 0; qq < 4; ++qq) tt[jo] += sred[(qq * XP + et) * 4 + jo];
-                    }
-                    last_epilogue(fl.epi, fl.p0 + w.p0 + et, n_out, tt, fl.bias);
+                    float tt[4] = {0.f, 0.f, 0.f, 0.f};
+                    for (int qq = 0; qq < 4; ++qq) tt[0] += sred[qq * XP + et];
+                    last_epilogue(fl.epi, fl.p0 + w.p0 + et, 1, tt, fl.bias);
                 }
             }
             epi_bar();   // sflag and sred are free for the next unit
@@ -451,9 +454,12 @@ PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 cudaError_t ensure_attr(int dev, int* sms) {
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
     if (!g_attr_set[dev]) {
-        cudaError_t e = cudaFuncSetAttribute(x3_layer_kernel,
+        cudaError_t e = cudaFuncSetAttribute(x3_layer_kernel<false>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)kSmemBytes);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(x3_layer_kernel<true>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
         if (e == cudaSuccess)
             e = cudaDeviceGetAttribute(&g_n_sm[dev], cudaDevAttrMultiProcessorCount, dev);
         if (e != cudaSuccess) return e;
@@ -501,7 +507,7 @@ cudaError_t launch_x3_layer(const X3LayerArgs& a, cudaStream_t s) {
         (a.nk1 > 0 && !a.tmH) || (a.nk2 > 0 && !a.tmX) || !a.tmW || !a.bias || !a.part ||
         !a.ctr || !a.err)
         return cudaErrorInvalidValue;
-    if (a.fuse ? (a.N != 128 || a.fuse->n_out < 1 || a.fuse->n_out > 4) : !a.out)
+    if (a.fuse ? (a.N != 128 || a.fuse->n_out != 1) : !a.out)
         return cudaErrorInvalidValue;
     int dev = 0, sms = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -539,7 +545,8 @@ cudaError_t launch_x3_layer(const X3LayerArgs& a, cudaStream_t s) {
     cfg.numAttrs = 1;
     const CUtensorMap& mh = a.nk1 > 0 ? *a.tmH : *a.tmW;
     const CUtensorMap& mx = a.nk2 > 0 ? *a.tmX : *a.tmW;
-    return cudaLaunchKernelEx(&cfg, x3_layer_kernel, *a.tmW, mh, mx, p, fl);
+    if (a.fuse) return cudaLaunchKernelEx(&cfg, x3_layer_kernel<true>, *a.tmW, mh, mx, p, fl);
+    return cudaLaunchKernelEx(&cfg, x3_layer_kernel<false>, *a.tmW, mh, mx, p, fl);
 }
 
 cudaError_t launch_gather_x3(const PointSrc& src, int64_t p0, int64_t m, const Calib& calib,

@@ -248,12 +248,16 @@ cudaError_t tc_prepare();
 // 13 low bits of the FP32 encoding cleared after adding half of their range
 // (sign-magnitude, so the same for both signs).  Finite v only.
 __host__ __device__ __forceinline__ float tf32_round(float v) {
+#if defined(__CUDA_ARCH__)
+    return __uint_as_float((__float_as_uint(v) + 0x1000u) & 0xFFFFE000u);
+#else
     uint32_t u;
     memcpy(&u, &v, 4);
     u = (u + 0x1000u) & 0xFFFFE000u;
     float r;
     memcpy(&r, &u, 4);
     return r;
+#endif
 }
 
 constexpr int kX3MaxUnits = 256;   // work units of one launch that hold split-K partials
@@ -263,7 +267,8 @@ constexpr int kX3Tile = 128;       // points and neurons per work unit
 // as 2 K floats, the hi values then the lo values):
 //   out[p][n] = lrelu(b[n] + sum_k W[n][k] [H | X][p][k]),
 // written back as hi/lo planes [rows][2 N], or, with `fuse`, handed to the
-// last layer (FP32) and its epilogue.  N a multiple of 128 (fuse: N = 128).
+// one-output last layer (FP32) and its epilogue.  N a multiple of 128 (fuse:
+// N = 128).
 struct X3LayerArgs {
     const CUtensorMap* tmW;      // [N][2 KP] FP32, box 32 x 128, 128-byte swizzle
     const CUtensorMap* tmH;      // [rows][2 KH] previous layer's planes, box 32 x 32
@@ -275,7 +280,7 @@ struct X3LayerArgs {
     const float* bias;
     float slope;
     float* out;                  // [rows][2 N] (null with fuse)
-    const FuseLast* fuse;        // optional: last layer (N = 128, n_out <= 4)
+    const FuseLast* fuse;        // optional: last layer (N = 128, n_out = 1)
     float* part;                 // [kX3MaxUnits][128][128] split-K partial tiles
     unsigned int* ctr;           // [2][kX3MaxUnits] arrivals and departures per tile, zero
                                  // between launches
