@@ -406,6 +406,18 @@ int pifu_set_schedule(pifu_ctx* ctx, int schedule);
 enum pifu_recheck { PIFU_RECHECK_TENSOR = 0, PIFU_RECHECK_SIMT = 1 };
 int pifu_set_recheck(pifu_ctx* ctx, int form);
 
+/* Test hook for the bounded device waits (not in the paper).  With starve =
+ * 1, the split-TF32 kernels' cross-CTA wait (the split-K units of a tile
+ * waiting for each other's partial tiles; no bulk copy or MMA is in flight
+ * there) waits for one arrival more than there are, gives up after a few
+ * thousand polls and latches the context's error word; the next
+ * synchronising call returns PIFU_ERR_TIMEOUT and puts the kernels' tile
+ * counters back, so the context stays usable.  starve = 0 (the default)
+ * restores normal operation.  Results computed while starving are not
+ * meaningful.  Invalidates captured graphs; no device work.  Errors:
+ * PIFU_ERR_ARG. */
+int pifu_test_starve_wait(pifu_ctx* ctx, int starve);
+
 /* Sets the tile code of every tuned layer, in pifu_autotune's order: codes[i]
  * for layer i, n = the number of layers pifu_autotune reports (for instance a
  * saved autotuner result).  A code must be allowed for its layer as above

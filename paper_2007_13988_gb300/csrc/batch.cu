@@ -424,7 +424,10 @@ int pifu_frames(pifu_ctx* ctx, int B, const pifu_fmap* occ_maps, const pifu_fmap
         }
         out[f] = vs;
     }
-    if (gs.err) return decode_err(gs.err);
+    if (gs.err) {
+        const int st = reset_after_error(ctx, s);
+        return st != PIFU_OK ? st : decode_err(gs.err);
+    }
     return PIFU_OK;
 }
 

@@ -568,7 +568,10 @@ int pifu_frame(pifu_ctx* ctx, const pifu_fmap* occ_map, const pifu_fmap* col_map
     if (cam->final_level && lv->num_levels < kMaxLevels)
         vs.evals_per_level[lv->num_levels] = (int64_t)gs.culled;   // the culled final level
     if (out) *out = vs;
-    if (gs.err) return decode_err(gs.err);
+    if (gs.err) {
+        const int st = reset_after_error(ctx, s);
+        return st != PIFU_OK ? st : decode_err(gs.err);
+    }
     ctx->stats = vs;
     ctx->have_volume = true;
     ctx->vol_N = (int)n_fine;

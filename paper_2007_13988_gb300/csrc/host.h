@@ -408,6 +408,7 @@ struct pifu_ctx {
     unsigned int* x3_ctr = nullptr;
     bool x3_ready = false;
     int recheck_form = 0;             // pifu_set_recheck
+    unsigned int x3_starve = 0;       // pifu_test_starve_wait
     float* part = nullptr;            // split-K partial sums of small FP32 batches
     int64_t part_cap = 0;
     // level workspace, sized for ws_N
@@ -669,6 +670,10 @@ int eval_batch(pifu_ctx* ctx, const PointSrc& src, int64_t n, const Map& map, co
 int ensure_clist(pifu_ctx* ctx, int64_t cap);
 int ohem_ensure(pifu_ctx* ctx, int64_t m, int B, bool reset);
 int decode_err(unsigned int e);
+// After a device error word was read: clears it and puts back what a kernel
+// that stopped early may have left behind (the split-TF32 tile counters), so
+// the context stays usable.
+int reset_after_error(pifu_ctx* ctx, cudaStream_t s);
 int read_count(pifu_ctx* ctx, cudaStream_t s, unsigned int* out);
 uint64_t splitmix64(uint64_t& x);
 void sur_free(pifu_ctx* ctx);

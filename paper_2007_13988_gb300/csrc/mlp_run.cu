@@ -346,6 +346,7 @@ int run_mlp_x3(pifu_ctx* ctx, const DevNet& net, const PointSrc& src_in, int64_t
             a.part = ctx->x3_part;
             a.ctr = ctx->x3_ctr;
             a.err = ctx->d_count + 1;
+            a.wait_extra = ctx->x3_starve;
             double flops = 3.0 * 2.0 * mc * Ly.fan_in * Ly.n_out;
             if (a.fuse) flops += 2.0 * mc * Ll.fan_in * Ll.n_out;
             ev = pr.begin(s);
@@ -545,8 +546,16 @@ int read_count(pifu_ctx* ctx, cudaStream_t s, unsigned int* out) {
     if (ctx->h_count[1] != 0u) {
         const unsigned int e = ctx->h_count[1];
         CK(cudaMemsetAsync(ctx->d_count + 1, 0, sizeof(unsigned int), s));
-        return decode_err(e);
+        const int st = reset_after_error(ctx, s);
+        return st != PIFU_OK ? st : decode_err(e);
     }
+    return PIFU_OK;
+}
+
+int reset_after_error(pifu_ctx* ctx, cudaStream_t s) {
+    CK(cudaMemsetAsync(ctx->d_count + 1, 0, sizeof(unsigned int), s));
+    if (ctx->x3_ctr)
+        CK(cudaMemsetAsync(ctx->x3_ctr, 0, sizeof(unsigned int) * 2 * kX3MaxUnits, s));
     return PIFU_OK;
 }
 

@@ -58,6 +58,7 @@ constexpr uint32_t STAGE_BYTES = 2 * W_PLANE + 2 * P_PLANE;
 constexpr int kThreads = 320;                       // 2 role warps + 8 epilogue warps
 constexpr uint32_t kTmemCols = 2 * XP;              // two accumulators
 constexpr uint32_t kWaitLimit = 1u << 20;           // polls; legitimate waits are microseconds
+constexpr uint32_t kTestWaitLimit = 1u << 12;
 constexpr int kMaxSplits = 8;
 constexpr uint32_t kSmemBytes = XNST * STAGE_BYTES + 1024 + 256 + 4 * XP * 4;
 static_assert(kSmemBytes <= 227 * 1024, "shared memory");
@@ -65,6 +66,7 @@ static_assert(XP == 128, "one TMEM lane per neuron, 128 columns per accumulator"
 
 struct X3Params {
     int nk1, nk2, KH, KX, KP, M, N, fuse;
+    unsigned int wait_extra;   // test hook: arrivals the split-K wait needs beyond the splits
     const unsigned int* m_dev;
     const float* bias;
     float slope;
@@ -346,10 +348,14 @@ __global__ void __launch_bounds__(kThreads, 1) x3_layer_kernel(
                 epi_bar();
                 if (et == 0) {
                     atomicAdd(&p.ctr[w.pair], 1u);
+                    // wait_extra > 0 (a test): an arrival that never comes, and a
+                    // shorter limit
+                    const unsigned int need = (unsigned)us.splits + p.wait_extra;
+                    const uint32_t lim = p.wait_extra ? kTestWaitLimit : kWaitLimit;
                     uint32_t it = 0;
-                    while (ld_acquire(&p.ctr[w.pair]) < (unsigned)us.splits && ++it < kWaitLimit) {
+                    while (ld_acquire(&p.ctr[w.pair]) < need && ++it < lim) {
                     }
-                    sflag[1] = it < kWaitLimit ? 1u : 0u;
+                    sflag[1] = it < lim ? 1u : 0u;
                 }
                 epi_bar();
                 if (sflag[1] == 0u) {
@@ -522,6 +528,7 @@ cudaError_t launch_x3_layer(const X3LayerArgs& a, cudaStream_t s) {
     p.M = a.M;
     p.N = a.N;
     p.fuse = a.fuse ? 1 : 0;
+    p.wait_extra = a.wait_extra;
     p.m_dev = a.m_dev;
     p.bias = a.bias;
     p.slope = a.slope;

@@ -285,6 +285,8 @@ struct X3LayerArgs {
     unsigned int* ctr;           // [2][kX3MaxUnits] arrivals and departures per tile, zero
                                  // between launches
     unsigned int* err;
+    unsigned int wait_extra;     // test hook (0): the split-K arrival wait needs this many
+                                 // arrivals more than there are, so it runs out
 };
 cudaError_t launch_x3_layer(const X3LayerArgs& a, cudaStream_t stream);
 // X[p][0 .. 2 KX) = hi and lo planes of the gather row of point p0 + p

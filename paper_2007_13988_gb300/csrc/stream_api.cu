@@ -556,7 +556,8 @@ int pifu_stream(pifu_ctx* ctx, int F, const pifu_fmap* occ_maps, const pifu_fmap
     }
     if (ctl.err) {
         CK(cudaMemsetAsync(ctx->d_count + 1, 0, sizeof(unsigned int), s));
-        return decode_err(ctl.err);
+        const int st = reset_after_error(ctx, s);
+        return st != PIFU_OK ? st : decode_err(ctl.err);
     }
     for (int f = 0; f < F; ++f)
         if (!w.h_fs[f].done) return PIFU_ERR_NOT_CONVERGED;

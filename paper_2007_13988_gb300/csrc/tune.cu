@@ -237,6 +237,15 @@ int pifu_set_recheck(pifu_ctx* ctx, int form) {
     return PIFU_OK;
 }
 
+int pifu_test_starve_wait(pifu_ctx* ctx, int starve) {
+    if (!ctx || (starve != 0 && starve != 1)) return PIFU_ERR_ARG;
+    ctx->x3_starve = (unsigned int)starve;
+    ctx->g_valid = false;
+    ctx->batch.g_valid = false;
+    ctx->stream.g_valid = false;
+    return PIFU_OK;
+}
+
 int pifu_set_tiles(pifu_ctx* ctx, const int32_t* codes, int n) {
     if (!ctx || n < 0 || (n > 0 && !codes)) return PIFU_ERR_ARG;
     DeviceGuard g(ctx->device);

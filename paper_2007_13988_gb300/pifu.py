@@ -46,7 +46,7 @@ EXPORTS = ("pifu_create", "pifu_destroy", "pifu_query", "pifu_query_colour", "pi
            "pifu_calibrate_fp8", "pifu_frames", "pifu_autotune", "pifu_surrogate_ohem_init",
            "pifu_surrogate_ohem_weights", "pifu_surrogate_ohem_sample",
            "pifu_surrogate_train_ohem", "pifu_set_tiles", "pifu_set_schedule", "pifu_stream",
-           "pifu_set_recheck")
+           "pifu_set_recheck", "pifu_test_starve_wait")
 
 KERNEL_CLASSES = ("gather", "mlp_hidden", "mlp_last", "level", "select", "render", "mlp_f32",
                   "cbn_tc")
@@ -160,6 +160,8 @@ def _lib():
     lib.pifu_set_schedule.restype = I
     lib.pifu_set_recheck.argtypes = [P, I]
     lib.pifu_set_recheck.restype = I
+    lib.pifu_test_starve_wait.argtypes = [P, I]
+    lib.pifu_test_starve_wait.restype = I
     lib.pifu_calibrate_fp8.argtypes = [P, ctypes.POINTER(pifu_fmap), ctypes.POINTER(F), I, P]
     lib.pifu_calibrate_fp8.restype = I
     lib.pifu_surrogate_init.argtypes = [P, I, I, U64]
@@ -452,6 +454,11 @@ def pifu_set_recheck(ctx, form):
     """Arithmetic of the MIXED forms' FP32 passes: split TF32 on the tensor
     cores (default) or the FP32 SIMT network."""
     _check(_lib().pifu_set_recheck(ctx, int(form)), "pifu_set_recheck", ctx)
+
+
+def pifu_test_starve_wait(ctx, starve):
+    """Test hook: the split-TF32 kernels' cross-CTA wait runs out (1) or not (0)."""
+    _check(_lib().pifu_test_starve_wait(ctx, int(starve)), "pifu_test_starve_wait", ctx)
 
 
 def pifu_set_tiles(ctx, codes):

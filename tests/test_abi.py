@@ -100,6 +100,7 @@ def test_null_arguments_are_rejected_on_the_host():
     assert lib.pifu_set_tiles(None, codes, 1) == pifu.PIFU_ERR_ARG
     assert lib.pifu_set_schedule(None, pifu.PIFU_SCHED_CHAINED) == pifu.PIFU_ERR_ARG
     assert lib.pifu_set_recheck(None, pifu.PIFU_RECHECK_SIMT) == pifu.PIFU_ERR_ARG
+    assert lib.pifu_test_starve_wait(None, 1) == pifu.PIFU_ERR_ARG
     lib.pifu_destroy(None)
 
 

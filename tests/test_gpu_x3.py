@@ -115,3 +115,40 @@ def test_mixed_localization_band_values(full, oracle256, form):
 def test_set_recheck_rejects_unknown_form(full):
     with pytest.raises(Exception):
         full.pifu.pifu_set_recheck(full.ctx, 7)
+
+
+def test_starved_wait_reports_timeout_and_context_recovers(full, oracle256):
+    # The split-K units of a tile wait for each other's partial tiles (a
+    # cross-CTA flag wait, no bulk copy or MMA in flight).  The test hook makes
+    # that wait need an arrival that never comes: it gives up after its poll
+    # limit, the kernel returns, and the call reports PIFU_ERR_TIMEOUT; then
+    # the same context localizes correctly again, host-driven and as a graph.
+    import torch
+    pifu = full.pifu
+    w = full.w
+    R = 256
+    depth = torch.empty((R, R), dtype=torch.float32, device="cuda")
+    rgb = torch.empty((R, R, 3), dtype=torch.float32, device="cuda")
+    mask = torch.empty((R, R), dtype=torch.uint8, device="cuda")
+
+    def frame():
+        v = pifu.pifu_frame(full.ctx, full.occ, full.col, w.calib, w.n0, w.num_levels, R, R,
+                            depth, rgb, mask, precision=MIXED)
+        torch.cuda.synchronize()
+        return v
+
+    pifu.pifu_test_starve_wait(full.ctx, 1)
+    try:
+        with pytest.raises(pifu.PifuError) as e1:
+            full.localize(precision=MIXED)
+        assert e1.value.status == pifu.PIFU_ERR_TIMEOUT
+        with pytest.raises(pifu.PifuError) as e2:
+            frame()
+        assert e2.value.status == pifu.PIFU_ERR_TIMEOUT
+    finally:
+        pifu.pifu_test_starve_wait(full.ctx, 0)
+    field_fn = lambda P: occ_oracle(w, P)
+    res = check_mixed_values(full, full.localize(precision=MIXED), oracle256, field_fn)
+    assert res["in_band"] > 0
+    res = check_mixed_values(full, frame(), oracle256, field_fn)
+    assert res["in_band"] > 0
