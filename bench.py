@@ -1084,7 +1084,7 @@ def run_ours(args, rank, world, local_rank):
         nr = max(1, len(rh["step_ms"]))
         line["recheck_forms"] = {
             "note": "the FP32-accurate pass of the MIXED forms (re-check of occupancies within "
-                    "the margin of 0.5, batches of <= 256 points): passes of more than 512 "
+                    "the margin of 0.5, batches of <= 256 points): passes of more than 192 "
                     "points in split TF32 on the tensor cores (hi*hi + hi*lo + lo*hi, FP32 "
                     "accumulation), smaller ones on the FP32 SIMT network (the headline), "
                     "against every pass on the FP32 SIMT network; ms per frame of that class "

@@ -388,22 +388,24 @@ int pifu_set_schedule(pifu_ctx* ctx, int schedule);
  * occupancies within the margin of 0.5 and batches of at most 256 points
  * (not in the paper, which evaluates every point once; Sec. 3.2 needs only
  * the decision at 0.5 to be the network's).
- *   PIFU_RECHECK_TENSOR (default): a pass of more than 512 points runs f_O's
+ *   PIFU_RECHECK_TENSOR (default): a pass of more than 192 points runs f_O's
  *     hidden layers on the tensor cores with every FP32 operand split into
  *     two TF32 values, hi = tf32(v) and lo = tf32(v - hi), and each product
  *     formed as hi*hi + hi*lo + lo*hi (Ootomo and Yokota's split-TF32
  *     method), FP32 accumulation and an FP32 last layer: within about 2e-5
  *     of the FP64 network in occupancy (the FP32 SIMT network: about 1e-6).
- *     Smaller passes run the FP32 SIMT network, whose one launch has the
- *     lower latency there.  Needs hidden widths that are multiples of 128,
+ *     The whole network is one cooperative launch.  Smaller passes run the
+ *     FP32 SIMT network, whose latency is lower there.  Needs hidden widths that are multiples of 128,
  *     the last one 128 wide, and a one-output last layer reading
  *     only it; other networks (and the CBN network) use the SIMT form.  The
  *     first MIXED call of a context reserves its workspace: 16,384 points x
  *     (2 d_in + 4 widest hidden width) floats plus 16 MB.
  *   PIFU_RECHECK_SIMT: the FP32 SIMT network (FFMA) for every pass, as the
  *     FP32 form.
+ *   PIFU_RECHECK_TENSOR_ALL: the split-TF32 network for every pass, small
+ *     ones included (where PIFU_RECHECK_TENSOR allows it).
  * Invalidates captured graphs; no device work.  Errors: PIFU_ERR_ARG. */
-enum pifu_recheck { PIFU_RECHECK_TENSOR = 0, PIFU_RECHECK_SIMT = 1 };
+enum pifu_recheck { PIFU_RECHECK_TENSOR = 0, PIFU_RECHECK_SIMT = 1, PIFU_RECHECK_TENSOR_ALL = 2 };
 int pifu_set_recheck(pifu_ctx* ctx, int form);
 
 /* Test hook for the bounded device waits (not in the paper).  With starve =

@@ -500,8 +500,9 @@ int ensure_x3(pifu_ctx* ctx) {
     CK(dev_alloc(&ctx->H3[0], kX3Rows * 2 * h));
     CK(dev_alloc(&ctx->H3[1], kX3Rows * 2 * h));
     CK(dev_alloc(&ctx->x3_part, (int64_t)kX3MaxUnits * kX3Tile * kX3Tile));
-    CK(dev_alloc(&ctx->x3_ctr, 2 * (int64_t)kX3MaxUnits));
-    CK(cudaMemset(ctx->x3_ctr, 0, sizeof(unsigned int) * 2 * kX3MaxUnits));
+    // tile counters [2][kX3MaxUnits], then the grid barrier's words
+    CK(dev_alloc(&ctx->x3_ctr, (int64_t)kX3CtrWords));
+    CK(cudaMemset(ctx->x3_ctr, 0, sizeof(unsigned int) * kX3CtrWords));
     for (DevNet& n : ctx->net) {
         if (!n.x3_ok) continue;
         const uint64_t rx = 2 * (uint64_t)n.x3_KX;

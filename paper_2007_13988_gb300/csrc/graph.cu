@@ -15,7 +15,7 @@ int64_t launches_now(const pifu_ctx* ctx);
 // with the cluster size that length calls for (few points: large clusters,
 // the lowest latency per tile; many: small clusters, more tiles per round),
 // or, when the split-TF32 network is usable (x3_usable) and the queue holds
-// more than kX3MinRows and at most kX3Rows points, that network (one more
+// more than x3_min_rows and at most kX3Rows points, that network (one more
 // body of the same switch).  An empty queue launches nothing.
 int g_recheck(pifu_ctx* ctx, const DevNet& net, const PointSrc& src, int64_t cap,
               const Map& map, const Calib& cal, const Epilogue& epi, cudaStream_t s,
@@ -24,7 +24,8 @@ int g_recheck(pifu_ctx* ctx, const DevNet& net, const PointSrc& src, int64_t cap
     const bool sw = net.kind != kNetCbn && ctx->cap_stream4 && s != ctx->cap_stream4 &&
                     fused_ok(fz);
     const FusedPlan plan = sw ? fused_plan(fz) : FusedPlan{};
-    const bool x3 = sw && plan.n >= 1 && x3_usable(ctx, net) && cap > kX3MinRows;
+    const int64_t x3_lo = x3_min_rows(ctx);
+    const bool x3 = sw && plan.n >= 1 && x3_usable(ctx, net) && cap > x3_lo;
     if (plan.n <= 1 && !x3)
         return run_mlp(ctx, net, src, cap, map, Map{}, cal, epi, s, PIFU_PREC_FP32, m_dev);
     cudaStreamCaptureStatus cs;
@@ -32,7 +33,7 @@ int g_recheck(pifu_ctx* ctx, const DevNet& net, const PointSrc& src, int64_t cap
     CK(cudaStreamGetCaptureInfo(s, &cs, nullptr, &cg, nullptr, nullptr, nullptr));
     cudaGraphConditionalHandle h;
     CK(cudaGraphConditionalHandleCreate(&h, cg, 0, 0));
-    CK(launch_fused_switch(h, plan, m_dev, (unsigned)cap, s, x3 ? (unsigned)kX3MinRows : 0u,
+    CK(launch_fused_switch(h, plan, m_dev, (unsigned)cap, s, x3 ? (unsigned)x3_lo : 0u,
                            x3 ? (unsigned)kX3Rows : 0u));
     const int nb = plan.n + (x3 ? 1 : 0);
     cudaGraph_t bodies[5] = {};

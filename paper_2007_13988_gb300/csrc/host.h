@@ -30,7 +30,7 @@ constexpr int64_t kRecheckCap = 8192; // graph form: FP32 re-checks per batch (s
 constexpr int64_t kFusedMaxM = 2048;   // host-sized FP32 batches up to this size: fused kernel
 constexpr int64_t kTinyBatch = 256; // mixed precision: batches this small run in FP32
 constexpr int64_t kX3Rows = 16384;   // points per pass of the split-TF32 network (its workspace rows)
-constexpr int64_t kX3MinRows = 512;  // FP32 passes of more points run it (fewer: the one-launch
+constexpr int64_t kX3MinRows = 192;  // FP32 passes of more points run it (fewer: the one-launch
                                      // SIMT network, whose latency is lower there)
 
 struct DevLayer {
@@ -632,6 +632,8 @@ int ensure_x3(pifu_ctx* ctx);
 // the net allows it (m points, or a device-sized batch of at most m), else
 // the FP32 SIMT network.
 bool x3_usable(const pifu_ctx* ctx, const DevNet& net);
+// Passes of more points than this run the split-TF32 network (when usable).
+int64_t x3_min_rows(const pifu_ctx* ctx);
 int run_mlp_x3(pifu_ctx* ctx, const DevNet& net, const PointSrc& src_in, int64_t m,
                const Map& map0, const Map& map1, const Calib& calib, const Epilogue& epi,
                cudaStream_t s, const unsigned int* m_dev);

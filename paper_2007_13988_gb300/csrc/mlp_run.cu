@@ -295,65 +295,73 @@ int run_mlp(pifu_ctx* ctx, const DevNet& net, const PointSrc& src_in, int64_t m,
 // ---- the FP32-accurate pass on the tensor cores (split TF32, mlp_x3.cu) -------
 
 bool x3_usable(const pifu_ctx* ctx, const DevNet& net) {
-    return net.x3_ok && ctx->x3_ready && ctx->recheck_form == PIFU_RECHECK_TENSOR;
+    return net.x3_ok && ctx->x3_ready && ctx->recheck_form != PIFU_RECHECK_SIMT;
 }
 
-// Gather into hi/lo planes, then one launch per hidden layer, the last one
-// with the last layer and the epilogue; passes of at most kX3Rows points (a
-// device-sized batch is one pass of at most m <= kX3Rows).
+int64_t x3_min_rows(const pifu_ctx* ctx) {
+    return ctx->recheck_form == PIFU_RECHECK_TENSOR_ALL ? 0 : kX3MinRows;
+}
+
+// The whole network (gather into hi/lo planes, every hidden layer, the last
+// layer and the epilogue) in one cooperative launch per pass of at most
+// kX3Rows points (a device-sized batch is one pass of at most m <= kX3Rows).
 int run_mlp_x3(pifu_ctx* ctx, const DevNet& net, const PointSrc& src_in, int64_t m,
                const Map& map0, const Map& map1, const Calib& calib, const Epilogue& epi,
                cudaStream_t s, const unsigned int* m_dev) {
     if (!x3_usable(ctx, net)) return PIFU_ERR_UNSUPPORTED;
     if (m_dev && m > kX3Rows) return PIFU_ERR_ARG;
-    PointSrc src = src_in;
-    src.count = m_dev;
     const int L = (int)net.layers.size();
+    if (L - 1 > kX3MaxLayers) return PIFU_ERR_UNSUPPORTED;
     const DevLayer& Ll = net.layers[(size_t)L - 1];
     Profiler& pr = ctx->prof;
     for (int64_t p0 = 0; p0 < m; p0 += kX3Rows) {
         const int64_t mc = std::min<int64_t>(kX3Rows, m - p0);
-        cudaEvent_t ev = pr.begin(s);
-        CK(launch_gather_x3(src, p0, mc, calib, map0, map1, ctx->X3, net.x3_KX, s));
-        pr.end(PIFU_K_GATHER, ev, s, 0.0,
-               (double)mc * (4.0 * 4.0 * (map0.C + map1.C) + 8.0 * net.x3_KX));
-        FuseLast fl{};
-        fl.W = Ll.W;
-        fl.ldw = Ll.ldw;
-        fl.bias = Ll.b;
-        fl.n_out = Ll.n_out;
-        fl.p0 = p0;
-        fl.epi = epi;
+        X3NetArgs a{};
+        double flops = 2.0 * mc * Ll.fan_in * Ll.n_out, bytes = 0.0;
         for (int l = 0; l + 1 < L; ++l) {
             const DevLayer& Ly = net.layers[(size_t)l];
             const X3Layer& X = net.x3[(size_t)l];
-            X3LayerArgs a{};
-            a.tmW = &X.tmW;
-            a.tmH = l > 0 ? &X.tmH : nullptr;
-            a.tmX = &net.tmX3;
-            a.nk1 = X.KH / 32;
-            a.nk2 = X.KX / 32;
-            a.KH = X.KH;
-            a.KX = X.KX;
-            a.KP = X.KP;
-            a.M = (int)mc;
-            a.N = Ly.n_out;
-            a.m_dev = m_dev;
-            a.bias = Ly.b;
-            a.slope = net.slope;
-            a.out = l + 2 < L ? ctx->H3[l % 2] : nullptr;
-            a.fuse = l + 2 == L ? &fl : nullptr;
-            a.part = ctx->x3_part;
-            a.ctr = ctx->x3_ctr;
-            a.err = ctx->d_count + 1;
-            a.wait_extra = ctx->x3_starve;
-            double flops = 3.0 * 2.0 * mc * Ly.fan_in * Ly.n_out;
-            if (a.fuse) flops += 2.0 * mc * Ll.fan_in * Ll.n_out;
-            ev = pr.begin(s);
-            CK(launch_x3_layer(a, s));
-            pr.end(PIFU_K_MLP_F32, ev, s, flops,
-                   8.0 * ((double)mc * (X.KP + Ly.n_out) + (double)Ly.n_out * X.KP));
+            X3NetLayer& A = a.L[l];
+            A.tmW = X.tmW;
+            if (l > 0) A.tmH = X.tmH;
+            A.nk1 = X.KH / 32;
+            A.nk2 = X.KX / 32;
+            A.KH = X.KH;
+            A.KX = X.KX;
+            A.KP = X.KP;
+            A.N = Ly.n_out;
+            A.bias = Ly.b;
+            A.out = l + 2 < L ? ctx->H3[l % 2] : nullptr;
+            flops += 3.0 * 2.0 * mc * Ly.fan_in * Ly.n_out;
+            bytes += 8.0 * ((double)mc * (X.KP + Ly.n_out) + (double)Ly.n_out * X.KP);
         }
+        a.tmX = net.tmX3;
+        a.nl = L - 1;
+        a.M = (int)mc;
+        a.m_dev = m_dev;
+        a.slope = net.slope;
+        a.src = src_in;
+        a.src.count = nullptr;   // the count is m_dev, read by the kernel
+        a.p0 = p0;
+        a.calib = calib;
+        a.map0 = map0;
+        a.map1 = map1;
+        a.X = ctx->X3;
+        a.KX = net.x3_KX;
+        a.fl.W = Ll.W;
+        a.fl.ldw = Ll.ldw;
+        a.fl.bias = Ll.b;
+        a.fl.n_out = Ll.n_out;
+        a.fl.p0 = p0;
+        a.fl.epi = epi;
+        a.part = ctx->x3_part;
+        a.ctr = ctx->x3_ctr;
+        a.err = ctx->d_count + 1;
+        a.wait_extra = ctx->x3_starve;
+        cudaEvent_t ev = pr.begin(s);
+        CK(launch_x3_net(a, s));
+        pr.end(PIFU_K_MLP_F32, ev, s, flops,
+               bytes + (double)mc * (4.0 * 4.0 * (map0.C + map1.C) + 8.0 * net.x3_KX));
     }
     return PIFU_OK;
 }
@@ -361,7 +369,7 @@ int run_mlp_x3(pifu_ctx* ctx, const DevNet& net, const PointSrc& src_in, int64_t
 int run_recheck(pifu_ctx* ctx, const DevNet& net, const PointSrc& src, int64_t m,
                 const Map& map0, const Map& map1, const Calib& calib, const Epilogue& epi,
                 cudaStream_t s) {
-    if (m > kX3MinRows && x3_usable(ctx, net))
+    if (m > x3_min_rows(ctx) && x3_usable(ctx, net))
         return run_mlp_x3(ctx, net, src, m, map0, map1, calib, epi, s, nullptr);
     return run_mlp(ctx, net, src, m, map0, map1, calib, epi, s, PIFU_PREC_FP32);
 }
@@ -555,7 +563,7 @@ int read_count(pifu_ctx* ctx, cudaStream_t s, unsigned int* out) {
 int reset_after_error(pifu_ctx* ctx, cudaStream_t s) {
     CK(cudaMemsetAsync(ctx->d_count + 1, 0, sizeof(unsigned int), s));
     if (ctx->x3_ctr)
-        CK(cudaMemsetAsync(ctx->x3_ctr, 0, sizeof(unsigned int) * 2 * kX3MaxUnits, s));
+        CK(cudaMemsetAsync(ctx->x3_ctr, 0, sizeof(unsigned int) * kX3CtrWords, s));
     return PIFU_OK;
 }
 

@@ -263,37 +263,50 @@ __host__ __device__ __forceinline__ float tf32_round(float v) {
 constexpr int kX3MaxUnits = 256;   // work units of one launch that hold split-K partials
 constexpr int kX3Tile = 128;       // points and neurons per work unit
 
-// One hidden layer over [H | X] (split planes: a row of K values is stored
-// as 2 K floats, the hi values then the lo values):
-//   out[p][n] = lrelu(b[n] + sum_k W[n][k] [H | X][p][k]),
-// written back as hi/lo planes [rows][2 N], or, with `fuse`, handed to the
-// one-output last layer (FP32) and its epilogue.  N a multiple of 128 (fuse:
-// N = 128).
-struct X3LayerArgs {
-    const CUtensorMap* tmW;      // [N][2 KP] FP32, box 32 x 128, 128-byte swizzle
-    const CUtensorMap* tmH;      // [rows][2 KH] previous layer's planes, box 32 x 32
-    const CUtensorMap* tmX;      // [rows][2 KX] input-row planes, box 32 x 32
+// The whole network over a batch in one cooperative launch: the gather into
+// the input-row planes, then every hidden layer over [H | X] (split planes: a
+// row of K values is stored as 2 K floats, the hi values then the lo values),
+//   h_l[p][n] = lrelu(b[n] + sum_k W[n][k] [h_{l-1} | x][p][k]),
+// written back as hi/lo planes [rows][2 N], the last hidden layer (N = 128)
+// handed to the one-output last layer (FP32) and its epilogue.  A grid-wide
+// barrier (bounded waits) separates the phases.
+constexpr int kX3MaxLayers = 4;
+constexpr int kX3CtrWords = 2 * kX3MaxUnits + kX3MaxLayers + 2;
+struct X3NetLayer {
+    CUtensorMap tmW;             // [N][2 KP] FP32, box 32 x 128, 128-byte swizzle
+    CUtensorMap tmH;             // [rows][2 KH] previous layer's planes, box 32 x 32 (l >= 1)
     int nk1, nk2;                // 32-value K-blocks from H, then from X
     int KH, KX, KP;              // lo-plane column offsets (KP = KH + KX)
-    int M, N;                    // points (a capacity with m_dev), neurons
-    const unsigned int* m_dev;   // optional device-resident point count (<= M)
+    int N;                       // neurons, a multiple of 128
     const float* bias;
+    float* out;                  // [rows][2 N] (unused by the last hidden layer)
+};
+struct X3NetArgs {
+    X3NetLayer L[kX3MaxLayers];
+    CUtensorMap tmX;             // [rows][2 KX] input-row planes, box 32 x 32
+    int nl;                      // hidden layers
+    int M;                       // points (a capacity with m_dev)
+    const unsigned int* m_dev;   // optional device-resident point count (<= M)
     float slope;
-    float* out;                  // [rows][2 N] (null with fuse)
-    const FuseLast* fuse;        // optional: last layer (N = 128, n_out = 1)
+    // gather: points p0 .. p0 + count - 1 of src into X
+    PointSrc src;
+    int64_t p0;
+    Calib calib;
+    Map map0, map1;
+    float* X;
+    int KX;
+    FuseLast fl;                 // the last layer (n_out = 1) and its epilogue
     float* part;                 // [kX3MaxUnits][128][128] split-K partial tiles
-    unsigned int* ctr;           // [2][kX3MaxUnits] arrivals and departures per tile, zero
-                                 // between launches
+    unsigned int* ctr;           // [2][kX3MaxUnits] arrivals and departures per tile, then
+                                 // [kX3MaxLayers + 2] grid barrier counters per phase and
+                                 // CTA departures (kX3CtrWords); all zero at launch and
+                                 // zero again at exit
     unsigned int* err;
     unsigned int wait_extra;     // test hook (0): the split-K arrival wait needs this many
                                  // arrivals more than there are, so it runs out
 };
-cudaError_t launch_x3_layer(const X3LayerArgs& a, cudaStream_t stream);
-// X[p][0 .. 2 KX) = hi and lo planes of the gather row of point p0 + p
-// (KX a multiple of 32, columns past d_in zero).
-cudaError_t launch_gather_x3(const PointSrc& src, int64_t p0, int64_t m, const Calib& calib,
-                             const Map& map0, const Map& map1, float* X, int KX,
-                             cudaStream_t stream);
+// One cooperative launch (every CTA resident: one per SM).
+cudaError_t launch_x3_net(const X3NetArgs& a, cudaStream_t stream);
 cudaError_t x3_prepare();
 // Tensor map of an FP32 matrix [rows][cols] (row stride in bytes), box
 // box_cols x box_rows, 128-byte swizzle.

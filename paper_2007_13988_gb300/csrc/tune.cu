@@ -229,7 +229,9 @@ int pifu_set_schedule(pifu_ctx* ctx, int schedule) {
 }
 
 int pifu_set_recheck(pifu_ctx* ctx, int form) {
-    if (!ctx || (form != PIFU_RECHECK_TENSOR && form != PIFU_RECHECK_SIMT)) return PIFU_ERR_ARG;
+    if (!ctx || (form != PIFU_RECHECK_TENSOR && form != PIFU_RECHECK_SIMT &&
+                 form != PIFU_RECHECK_TENSOR_ALL))
+        return PIFU_ERR_ARG;
     ctx->recheck_form = form;
     ctx->g_valid = false;
     ctx->batch.g_valid = false;

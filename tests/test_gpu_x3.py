@@ -7,8 +7,10 @@ a MIXED query goes through that pass, so the query's values are the pass's
 own: they must meet the oracle within the occupancy tolerance, at batch
 sizes that cover ragged 128-point tiles, the split-K forms (fewer tiles than
 SMs) and the unsplit ones, and more than one 16,384-point pass.  Passes of
-at most 512 points run the SIMT network in either form; the SIMT form
-(PIFU_RECHECK_SIMT) stays covered for the large passes too."""
+at most 192 points run the SIMT network in the default form and the
+split-TF32 network with PIFU_RECHECK_TENSOR_ALL (tested here at small
+sizes); the SIMT form (PIFU_RECHECK_SIMT) stays covered for the large passes
+too."""
 import numpy as np
 import pytest
 
@@ -60,7 +62,7 @@ def near_surface(oracle256):
     return np.concatenate([P, extra]).astype(np.float32)
 
 
-# Passes of more than 512 points run the split-TF32 network (fewer: the
+# Passes of more than 192 points run the split-TF32 network (fewer: the
 # SIMT network).  513 and 545: four full 128-point tiles and a ragged one of
 # 1 or 33 points; 700-2305: split K (fewer (point, neuron) tiles than SMs in
 # some layers); 5000: layers 1-2 unsplit; 16384 + 129: two passes.
@@ -68,10 +70,27 @@ def near_surface(oracle256):
 def test_tensor_recheck_matches_oracle(full, near_surface, m):
     P = near_surface[:m]
     want = occ_oracle(full.w, P)
-    assert np.count_nonzero(np.abs(want - 0.5) < 0.45) > 512   # a split-TF32 pass
+    assert np.count_nonzero(np.abs(want - 0.5) < 0.45) > 192   # a split-TF32 pass
     got = full.query(P, precision=MIXED, margin=0.5)
     err = np.max(np.abs(got - want))
     print("m = %d: max |error| %.2e" % (m, err))
+    assert err <= OCC_TOL, err
+
+
+# Every pass on the split-TF32 network, the small ones included: one 32-point
+# group, either side of a group, a ragged second tile, and every layer split.
+@pytest.mark.parametrize("m", [1, 31, 33, 100, 129, 192])
+def test_tensor_all_small_batches_match_oracle(full, near_surface, m):
+    pifu = full.pifu
+    P = near_surface[:m]
+    pifu.pifu_set_recheck(full.ctx, pifu.PIFU_RECHECK_TENSOR_ALL)
+    try:
+        got = full.query(P, precision=MIXED, margin=0.5)
+    finally:
+        pifu.pifu_set_recheck(full.ctx, pifu.PIFU_RECHECK_TENSOR)
+    want = occ_oracle(full.w, P)
+    err = np.max(np.abs(got - want))
+    print("all-tensor m = %d: max |error| %.2e" % (m, err))
     assert err <= OCC_TOL, err
 
 
@@ -97,7 +116,7 @@ def test_tensor_and_simt_forms_agree(full, near_surface):
 @pytest.mark.parametrize("form", ["tensor", "simt"])
 def test_mixed_localization_band_values(full, oracle256, form):
     # a MIXED localization (32^3 -> 256^3; the finest level re-checks more
-    # than 512 points at once) with either re-check form: every stored
+    # than 192 points at once) with either re-check form: every stored
     # occupancy within 0.02 of 0.5 meets the oracle within OCC_TOL
     pifu = full.pifu
     if form == "simt":
@@ -109,7 +128,7 @@ def test_mixed_localization_band_values(full, oracle256, form):
         pifu.pifu_set_recheck(full.ctx, pifu.PIFU_RECHECK_TENSOR)
     print("%s re-check: %s, rechecked %s" % (form, res, list(vol.rechecked_per_level)[:4]))
     assert res["in_band"] > 0
-    assert max(vol.rechecked_per_level[i] for i in range(vol.num_levels)) > 512
+    assert max(vol.rechecked_per_level[i] for i in range(vol.num_levels)) > 192
 
 
 def test_set_recheck_rejects_unknown_form(full):
