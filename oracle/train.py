@@ -16,8 +16,12 @@ db_l = column sums of dZ_l, dH_{l-1} = dZ_l W_l, dZ_{l-1} = dH_{l-1} * g'(Z).
 Adam (Kingma & Ba): m = b1 m + (1-b1) g, v = b2 v + (1-b2) g^2,
 w -= lr (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps).
 
-Pins: tests/test_oracle_train.py (central finite differences of the loss;
-a hand-computed Adam step; BCE closed forms).
+The concatenation MLP with skip layers (the full f_O's family, fitted once to
+the figures by tests/golden/fit_occupancy.py) has its own forward and
+backward below.
+
+Pins: tests/test_oracle_train.py (central finite differences of the loss,
+with and without skips; a hand-computed Adam step; BCE closed forms).
 """
 from __future__ import annotations
 
@@ -70,6 +74,53 @@ def loss_and_grads(Ws, bs, X, y, slope):
         dbs[l] = dz.sum(axis=0)
         if l > 0:
             dh = dz @ np.asarray(Ws[l], F64)
+            dz = dh * leaky_grad(Z[l - 1], slope)
+    return loss, dWs, dbs
+
+
+# ---- the concatenation MLP with skips (Sec. 3.1, f_O of the "MLP" variant) ----
+#
+# Layer l reads z_l = [h_{l-1}, x] when l is a skip layer (l > 0), else
+# h_{l-1} (h_{-1} = x); Z_l = z_l W_l^T + b_l, h_l = g(Z_l) but for the last
+# layer, whose Z is the logit.  Backward: dZ_l gives dW_l = dZ_l^T z_l and
+# db_l = column sums of dZ_l; dz_l = dZ_l W_l, whose first columns are
+# dh_{l-1} (the trailing d_in columns of a skip layer are the gradient with
+# respect to x, which no parameter needs), and dZ_{l-1} = dh_{l-1} * g'(Z_{l-1}).
+
+
+def forward_concat(Ws, bs, X, slope, skip):
+    """Pre-activations Z_l and layer inputs z_l of the concatenation MLP."""
+    X = np.asarray(X, F64)
+    h = X
+    Z, zin = [], []
+    L = len(Ws)
+    for l in range(L):
+        z = np.concatenate([h, X], axis=1) if (l in skip and l > 0) else h
+        zin.append(z)
+        pre = z @ np.asarray(Ws[l], F64).T + np.asarray(bs[l], F64)
+        Z.append(pre)
+        if l < L - 1:
+            h = leaky(pre, slope)
+    return Z, zin
+
+
+def loss_and_grads_concat(Ws, bs, X, y, slope, skip):
+    """Mean BCE loss and its gradients (dW_l, db_l) of the concatenation MLP."""
+    Z, zin = forward_concat(Ws, bs, X, slope, skip)
+    t = Z[-1][:, 0]
+    B = len(t)
+    loss = bce_with_logits(t, y)
+    s = 1.0 / (1.0 + np.exp(-t))
+    dz = ((s - np.asarray(y, F64)) / B)[:, None]
+    L = len(Ws)
+    dWs = [None] * L
+    dbs = [None] * L
+    for l in range(L - 1, -1, -1):
+        dWs[l] = dz.T @ zin[l]
+        dbs[l] = dz.sum(axis=0)
+        if l > 0:
+            width_prev = np.asarray(Ws[l - 1]).shape[0]
+            dh = (dz @ np.asarray(Ws[l], F64))[:, :width_prev]
             dz = dh * leaky_grad(Z[l - 1], slope)
     return loss, dWs, dbs
 

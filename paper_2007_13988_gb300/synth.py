@@ -31,6 +31,8 @@ from __future__ import annotations
 import dataclasses
 import math
 
+import os
+
 import numpy as np
 
 LEAKY_SLOPE = 0.01
@@ -719,6 +721,39 @@ def full(seed: int = 0, calib=None, num_levels: int = 4, n0: int = 32, render: i
     return Workload(f"full {n0}^3->{n_fine}^3, {render}^2 render, C=256 FP32", fig, occ, col,
                     calib_identity() if calib is None else calib, onet, cnet,
                     n0=n0, num_levels=num_levels, render=render)
+
+
+def fitted_occupancy_net(which: str, base: Net) -> Net:
+    """f_O of the ``which`` ("tiny" or "full") workload fitted to its seed-0
+    figure: the architecture of ``base``, the stored weights of
+    tests/golden/fitted_occ_<which>.npz (written once by
+    tests/golden/fit_occupancy.py: 2000 Adam steps of BCE on 65,536 points
+    against the capsules' occupancy)."""
+    path = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "tests",
+                        "golden", "fitted_occ_%s.npz" % which)
+    z = np.load(path)
+    L = len(base.widths)
+    W = [np.ascontiguousarray(z["W%d" % l], dtype=np.float32) for l in range(L)]
+    b = [np.ascontiguousarray(z["b%d" % l], dtype=np.float32) for l in range(L)]
+    for l in range(L):
+        assert W[l].shape == (base.widths[l], base.fan_in(l)), (which, l, W[l].shape)
+    return Net(base.d_in, base.widths, base.skip, W, b, base.out_act, base.slope)
+
+
+def tiny_fitted(calib=None) -> Workload:
+    """The tiny workload (seed 0) with its fitted f_O."""
+    w = tiny(0, calib)
+    w.occ_net = fitted_occupancy_net("tiny", w.occ_net)
+    w.name = "tiny 16^3->64^3, 64^2 render, C=32 FP32, fitted f_O"
+    return w
+
+
+def full_fitted(calib=None, num_levels: int = 4, n0: int = 32, render: int = 512) -> Workload:
+    """The full-size workload (seed 0) with its fitted f_O."""
+    w = full(0, calib, num_levels=num_levels, n0=n0, render=render)
+    w.occ_net = fitted_occupancy_net("full", w.occ_net)
+    w.name = w.name + ", fitted f_O"
+    return w
 
 
 def tiny_cbn(seed: int = 0, calib=None) -> Workload:

@@ -16,6 +16,7 @@ from __future__ import annotations
 import numpy as np
 
 import parity_rules as pr
+from oracle import field, render
 from parity_rules import NEAR_HALF, OCC_TOL
 DEPTH_TOL = 1e-3 * 2.0
 COLOUR_TOL = 1e-3
@@ -224,3 +225,31 @@ def ambiguous_rays(values, R):
     ks = np.arange(V.shape[2])[None, None, :]
     upto = ks <= k[..., None]
     return ((np.abs(V - 0.5) < NEAR_HALF) & upto).any(axis=2)
+
+
+def check_render(c, levels, R, calib=None, bg=(0.0, 0.0, 0.0)):
+    w = c.w
+    fine = levels[-1]
+    o_rgb, o_depth, o_hit = render.render(fine.values, R, w.col_net, w.occ_map, w.col_map,
+                                          w.calib if calib is None else calib, background=bg)
+    depth, rgb, mask = c.render(R, calib=calib, background=bg)
+    amb = ambiguous_rays(fine.values, R)
+    ok = ~amb
+    assert np.array_equal(mask[ok], o_hit[ok])
+    hit = ok & o_hit
+    assert hit.sum() > 0
+    assert np.max(np.abs(depth[hit] - o_depth[hit])) <= DEPTH_TOL
+    assert np.all(np.isnan(depth[ok & ~o_hit]))
+    assert np.max(np.abs(rgb[ok] - o_rgb[ok])) <= COLOUR_TOL
+    return {"hits": int(o_hit.sum()), "ambiguous": int(amb.sum()),
+            "depth_err": float(np.max(np.abs(depth[hit] - o_depth[hit]))),
+            "rgb_err": float(np.max(np.abs(rgb[ok] - o_rgb[ok])))}
+
+
+def localized(c, base):
+    """Localize (checked against the oracle) and return the oracle's levels
+    that follow the library's side of 0.5 at near-0.5 nodes."""
+    w = c.w
+    _, lv, _ = check_localization(c, base,
+                                  lambda P: field.occupancy(w.occ_net, w.occ_map, w.calib, P))
+    return lv

@@ -7,7 +7,8 @@ import pytest
 from oracle import field, localize, render
 from paper_2007_13988_gb300 import synth
 
-from gpu_common import COLOUR_TOL, DEPTH_TOL, OCC_TOL, Ctx, ambiguous_rays, check_localization
+from gpu_common import (COLOUR_TOL, DEPTH_TOL, OCC_TOL, Ctx, ambiguous_rays, check_localization,
+                        check_render, localized)
 
 pytestmark = pytest.mark.gpu
 
@@ -175,32 +176,6 @@ def test_localize_rejects_bad_arguments(tiny):
 
 
 # --------------------------------------------------------------- render ------
-
-def check_render(c, levels, R, calib=None, bg=(0.0, 0.0, 0.0)):
-    w = c.w
-    fine = levels[-1]
-    o_rgb, o_depth, o_hit = render.render(fine.values, R, w.col_net, w.occ_map, w.col_map,
-                                          w.calib if calib is None else calib, background=bg)
-    depth, rgb, mask = c.render(R, calib=calib, background=bg)
-    amb = ambiguous_rays(fine.values, R)
-    ok = ~amb
-    assert np.array_equal(mask[ok], o_hit[ok])
-    hit = ok & o_hit
-    assert hit.sum() > 0
-    assert np.max(np.abs(depth[hit] - o_depth[hit])) <= DEPTH_TOL
-    assert np.all(np.isnan(depth[ok & ~o_hit]))
-    assert np.max(np.abs(rgb[ok] - o_rgb[ok])) <= COLOUR_TOL
-    return {"hits": int(o_hit.sum()), "ambiguous": int(amb.sum()),
-            "depth_err": float(np.max(np.abs(depth[hit] - o_depth[hit]))),
-            "rgb_err": float(np.max(np.abs(rgb[ok] - o_rgb[ok])))}
-
-
-def localized(c, base):
-    """Localize (checked against the oracle) and return the oracle's levels
-    that follow the library's side of 0.5 at near-0.5 nodes."""
-    _, lv, _ = check_localization(c, base, lambda P: occ_oracle(c.w, P))
-    return lv
-
 
 def test_render_tiny(tiny, tiny_oracle):
     res = check_render(tiny, localized(tiny, tiny_oracle), 64, bg=(0.25, 0.5, 0.75))

@@ -85,3 +85,71 @@ def test_ohem_sampling_frequencies():
     freq = np.bincount(idx, minlength=len(w)) / len(idx)
     np.testing.assert_allclose(freq, w / w.sum(), atol=0.015)
     assert freq[3] == 0.0
+
+
+def skip_net(seed=3, d_in=6, widths=(5, 4, 3, 1), skip=(1, 2)):
+    rng = np.random.default_rng(seed)
+    Ws, bs = [], []
+    prev = d_in
+    for l, w in enumerate(widths):
+        fan = prev + (d_in if (l in skip and l > 0) else 0)
+        Ws.append(rng.standard_normal((w, fan)) * 0.6)
+        bs.append(rng.standard_normal(w) * 0.1)
+        prev = w
+    return Ws, bs
+
+
+def test_concat_gradients_match_central_differences():
+    # every weight and bias of a net whose layers 1 and 2 read [h, x]
+    Ws, bs = skip_net()
+    skip = (1, 2)
+    rng = np.random.default_rng(4)
+    X = rng.standard_normal((11, 6))
+    y = (rng.uniform(0, 1, 11) > 0.5).astype(float)
+    slope = 0.01
+    _, dWs, dbs = train.loss_and_grads_concat(Ws, bs, X, y, slope, skip)
+    h = 1e-6
+
+    def loss(Ws_, bs_):
+        return train.loss_and_grads_concat(Ws_, bs_, X, y, slope, skip)[0]
+
+    for l in range(len(Ws)):
+        for idx in np.ndindex(*Ws[l].shape):
+            Wp = [w.copy() for w in Ws]
+            Wm = [w.copy() for w in Ws]
+            Wp[l][idx] += h
+            Wm[l][idx] -= h
+            num = (loss(Wp, bs) - loss(Wm, bs)) / (2 * h)
+            assert abs(num - dWs[l][idx]) < 1e-8, (l, idx)
+        for k in range(len(bs[l])):
+            bp = [b.copy() for b in bs]
+            bm = [b.copy() for b in bs]
+            bp[l][k] += h
+            bm[l][k] -= h
+            num = (loss(Ws, bp) - loss(Ws, bm)) / (2 * h)
+            assert abs(num - dbs[l][k]) < 1e-8, (l, k)
+
+
+def test_concat_forward_is_the_field_mlp():
+    # the trainer's logit is the inference network's (oracle.field.mlp, the
+    # same concatenation family written for Eq. 1)
+    from types import SimpleNamespace
+
+    from oracle import field
+    Ws, bs = skip_net(seed=5)
+    X = np.random.default_rng(6).standard_normal((8, 6))
+    net = SimpleNamespace(W=Ws, b=bs, skip=(1, 2), slope=0.01)
+    Z, _ = train.forward_concat(Ws, bs, X, 0.01, (1, 2))
+    assert np.allclose(Z[-1], field.mlp(net, X), rtol=0, atol=1e-13)
+
+
+def test_concat_without_skips_is_the_plain_trainer():
+    Ws, bs = small_net(7)
+    X = np.random.default_rng(8).standard_normal((5, 7))
+    y = np.random.default_rng(9).uniform(0, 1, 5)
+    a = train.loss_and_grads(Ws, bs, X, y, 0.01)
+    b = train.loss_and_grads_concat(Ws, bs, X, y, 0.01, ())
+    assert abs(a[0] - b[0]) < 1e-15
+    for l in range(len(Ws)):
+        assert np.allclose(a[1][l], b[1][l], rtol=0, atol=1e-15)
+        assert np.allclose(a[2][l], b[2][l], rtol=0, atol=1e-15)
