@@ -1113,11 +1113,13 @@ def run_ours(args, rank, world, local_rank):
         nr = max(1, len(rh["step_ms"]))
         line["recheck_forms"] = {
             "note": "the FP32-accurate pass of the MIXED forms (re-check of occupancies within "
-                    "the margin of 0.5, batches of <= 256 points): passes of more than 192 "
-                    "points in split TF32 on the tensor cores (hi*hi + hi*lo + lo*hi, FP32 "
-                    "accumulation), smaller ones on the FP32 SIMT network (the headline), "
-                    "against every pass on the FP32 SIMT network; ms per frame of that class "
-                    "on the host-driven form (its host launch gaps included)",
+                    "the margin of 0.5, batches of <= 256 points) in the headline: passes of "
+                    "more than 192 points in split TF32 on the tensor cores (hi*hi + hi*lo + "
+                    "lo*hi, FP32 accumulation), passes of at most 64 points in FP32 FFMA as "
+                    "one cooperative launch over every SM, the others on the FP32 form's "
+                    "cluster network; against every pass on that cluster network; ms per "
+                    "frame of that class on the host-driven form (its host launch gaps "
+                    "included)",
             "tensor": {"value": head["value"], "ms_per_step": head["ms_per_step"],
                        "pass_ms_per_frame": prof["mlp_f32"]["ms"] / nprof,
                        "pass_launches_per_frame": prof["mlp_f32"]["launches"] // nprof},

@@ -394,14 +394,19 @@ int pifu_set_schedule(pifu_ctx* ctx, int schedule);
  *     formed as hi*hi + hi*lo + lo*hi (Ootomo and Yokota's split-TF32
  *     method), FP32 accumulation and an FP32 last layer: within about 2e-5
  *     of the FP64 network in occupancy (the FP32 SIMT network: about 1e-6).
- *     The whole network is one cooperative launch.  Smaller passes run the
- *     FP32 SIMT network, whose latency is lower there.  Needs hidden widths that are multiples of 128,
- *     the last one 128 wide, and a one-output last layer reading
- *     only it; other networks (and the CBN network) use the SIMT form.  The
- *     first MIXED call of a context reserves its workspace: 16,384 points x
- *     (2 d_in + 4 widest hidden width) floats plus 16 MB.
- *   PIFU_RECHECK_SIMT: the FP32 SIMT network (FFMA) for every pass, as the
- *     FP32 form.
+ *     The whole network is one cooperative launch.  Needs hidden widths
+ *     that are multiples of 128, the last one 128 wide, and a one-output
+ *     last layer reading only it.  A pass of at most 64 points runs the
+ *     network in FP32 FFMA as one cooperative launch over every SM (each
+ *     hidden layer's neurons split over the SMs, a grid barrier between
+ *     layers), whose latency is the lowest there; passes between the two
+ *     sizes, and networks neither form takes (and the CBN network), use
+ *     the FP32 form's SIMT network.
+ *     The first MIXED call of a context reserves its workspace: 16,384
+ *     points x (2 d_in + 4 widest hidden width) floats, 256 points x 2
+ *     widest hidden width floats, plus 17 MB.
+ *   PIFU_RECHECK_SIMT: the FP32 form's SIMT network (FFMA, clusters of
+ *     CTAs) for every pass.
  *   PIFU_RECHECK_TENSOR_ALL: the split-TF32 network for every pass, small
  *     ones included (where PIFU_RECHECK_TENSOR allows it).
  * Invalidates captured graphs; no device work.  Errors: PIFU_ERR_ARG. */
@@ -409,12 +414,14 @@ enum pifu_recheck { PIFU_RECHECK_TENSOR = 0, PIFU_RECHECK_SIMT = 1, PIFU_RECHECK
 int pifu_set_recheck(pifu_ctx* ctx, int form);
 
 /* Test hook for the bounded device waits (not in the paper).  With starve =
- * 1, the split-TF32 kernels' cross-CTA wait (the split-K units of a tile
- * waiting for each other's partial tiles; no bulk copy or MMA is in flight
- * there) waits for one arrival more than there are, gives up after a few
- * thousand polls and latches the context's error word; the next
- * synchronising call returns PIFU_ERR_TIMEOUT and puts the kernels' tile
- * counters back, so the context stays usable.  starve = 0 (the default)
+ * 1, two cross-CTA waits each wait for one arrival more than there are: the
+ * split-TF32 kernels' split-K wait (the units of a tile waiting for each
+ * other's partial tiles) and the whole-GPU FP32 kernel's grid barrier (which
+ * then issues each layer's weight copies after the barrier, so no bulk copy
+ * or MMA is in flight at either wait).  Each gives up after a few thousand
+ * polls and latches the context's error word; the next synchronising call
+ * returns PIFU_ERR_TIMEOUT and puts the kernels' counters back, so the
+ * context stays usable.  starve = 0 (the default)
  * restores normal operation.  Results computed while starving are not
  * meaningful.  Invalidates captured graphs; no device work.  Errors:
  * PIFU_ERR_ARG. */

@@ -22,7 +22,7 @@ LIB = os.path.join(PKG, "libpifu.so")
 SOURCES = ["pifu_api.cu", "ctx.cu", "mlp_run.cu", "graph.cu", "batch.cu", "tune.cu",
            "surrogate_api.cu", "stream_api.cu", "stream.cu", "gather.cu", "mlp_f32.cu", "mlp_tc.cu", "localize.cu", "render.cu",
            "query_noalloc.cu", "train.cu", "mlp_fused.cu", "cbn.cu", "cbn_tc.cu", "mlp_chain.cu",
-           "mlp_x3.cu"]
+           "mlp_x3.cu", "mlp_grid.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
                 "-I" + INCLUDE, "-I" + CSRC]

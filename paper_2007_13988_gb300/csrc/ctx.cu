@@ -486,7 +486,29 @@ int build_x3(pifu_ctx* ctx, const HostNet& hn, DevNet& net) {
 
 // The split-TF32 workspaces (kX3Rows points) and the tensor maps over them,
 // once per context.  Called before any capture (a graph holds the maps).
+// The whole-GPU FP32 network's buffers, and each concatenation network's
+// largest batch for it.
+int ensure_grid(pifu_ctx* ctx) {
+    if (ctx->grid_ctr) return PIFU_OK;
+    int64_t h = 0;
+    for (DevNet& n : ctx->net) {
+        n.grid_rows = n.kind == kNetCbn ? 0 : grid_max_rows(fused_of(n));
+        if (n.grid_rows > 0) h = std::max<int64_t>(h, n.max_hidden);
+    }
+    if (h == 0) return PIFU_OK;
+    CK(dev_alloc(&ctx->grid_H[0], kGridMaxRows * h));
+    CK(dev_alloc(&ctx->grid_H[1], kGridMaxRows * h));
+    CK(dev_alloc(&ctx->grid_part, (int64_t)kGridMaxRows * kGridMaxCtas * 4));
+    CK(dev_alloc(&ctx->grid_ctr, (int64_t)kGridCtrWords));
+    CK(cudaMemset(ctx->grid_ctr, 0, sizeof(unsigned int) * kGridCtrWords));
+    return PIFU_OK;
+}
+
+// The FP32-accurate passes' workspaces: the whole-GPU FP32 network's and the
+// split-TF32 network's.
 int ensure_x3(pifu_ctx* ctx) {
+    const int st = ensure_grid(ctx);
+    if (st != PIFU_OK) return st;
     if (ctx->x3_ready) return PIFU_OK;
     int64_t kx = 0, h = 0;
     for (const DevNet& n : ctx->net) {

@@ -13,10 +13,12 @@ int64_t launches_now(const pifu_ctx* ctx);
 // The FP32 pass over a device-sized queue in the graph.  With the fused
 // kernel, a switch node set on the device from the queue length launches it
 // with the cluster size that length calls for (few points: large clusters,
-// the lowest latency per tile; many: small clusters, more tiles per round),
-// or, when the split-TF32 network is usable (x3_usable) and the queue holds
-// more than x3_min_rows and at most kX3Rows points, that network (one more
-// body of the same switch).  An empty queue launches nothing.
+// the lowest latency per tile; many: small clusters, more tiles per round);
+// in the default re-check form a queue of at most grid_rows points runs the
+// whole-GPU FP32 network instead, and, when the split-TF32 network is usable
+// (x3_usable), a queue of more than x3_min_rows and at most kX3Rows points
+// runs that network (one more body each of the same switch).  An empty queue
+// launches nothing.
 int g_recheck(pifu_ctx* ctx, const DevNet& net, const PointSrc& src, int64_t cap,
               const Map& map, const Calib& cal, const Epilogue& epi, cudaStream_t s,
               const unsigned int* m_dev) {
@@ -26,7 +28,8 @@ int g_recheck(pifu_ctx* ctx, const DevNet& net, const PointSrc& src, int64_t cap
     const FusedPlan plan = sw ? fused_plan(fz) : FusedPlan{};
     const int64_t x3_lo = x3_min_rows(ctx);
     const bool x3 = sw && plan.n >= 1 && x3_usable(ctx, net) && cap > x3_lo;
-    if (plan.n <= 1 && !x3)
+    const int64_t ghi = sw && plan.n >= 1 ? std::min<int64_t>(grid_rows(ctx, net), cap) : 0;
+    if (plan.n <= 1 && !x3 && ghi <= 0)
         return run_mlp(ctx, net, src, cap, map, Map{}, cal, epi, s, PIFU_PREC_FP32, m_dev);
     cudaStreamCaptureStatus cs;
     cudaGraph_t cg = nullptr;
@@ -34,32 +37,31 @@ int g_recheck(pifu_ctx* ctx, const DevNet& net, const PointSrc& src, int64_t cap
     cudaGraphConditionalHandle h;
     CK(cudaGraphConditionalHandleCreate(&h, cg, 0, 0));
     CK(launch_fused_switch(h, plan, m_dev, (unsigned)cap, s, x3 ? (unsigned)x3_lo : 0u,
-                           x3 ? (unsigned)kX3Rows : 0u));
-    const int nb = plan.n + (x3 ? 1 : 0);
-    cudaGraph_t bodies[5] = {};
+                           x3 ? (unsigned)kX3Rows : 0u, ghi > 0 ? (unsigned)ghi : 0u));
+    const int nb = plan.n + (x3 ? 1 : 0) + (ghi > 0 ? 1 : 0);
+    cudaGraph_t bodies[6] = {};
     int st = g_add_switch(ctx, s, h, nb, bodies);
     if (st != PIFU_OK) return st;
     cudaStream_t s4 = ctx->cap_stream4;
     const int64_t before = launches_now(ctx);
-    int64_t fused_launches = 0;
     for (int i = 0; i < nb; ++i) {
         CK(cudaStreamBeginCaptureToGraph(s4, bodies[i], nullptr, nullptr, 0,
                                          cudaStreamCaptureModeThreadLocal));
         if (i < plan.n)
             st = run_mlp(ctx, net, src, cap, map, Map{}, cal, epi, s4, PIFU_PREC_FP32, m_dev,
                          plan.cl[i]);
-        else
+        else if (x3 && i == plan.n)
             st = run_mlp_x3(ctx, net, src, std::min<int64_t>(cap, kX3Rows), map, Map{}, cal, epi,
                             s4, m_dev);
+        else
+            st = run_mlp_grid(ctx, net, src, ghi, map, Map{}, cal, epi, s4, m_dev);
         cudaGraph_t out = nullptr;
         const cudaError_t ee = cudaStreamEndCapture(s4, &out);
         if (st != PIFU_OK) return st;
         if (ee != cudaSuccess) return fail_cuda(ctx, ee);
-        if (i + 1 == plan.n) fused_launches = launches_now(ctx) - before;
     }
-    // one body runs per replay: count one fused body's launches
-    const int64_t per_body = plan.n > 0 ? fused_launches / plan.n : 0;
-    ctx->prof.k[PIFU_K_MLP_F32].launches -= (launches_now(ctx) - before) - per_body;
+    // one body, one launch, runs per replay
+    ctx->prof.k[PIFU_K_MLP_F32].launches -= (launches_now(ctx) - before) - 1;
     return PIFU_OK;
 }
 

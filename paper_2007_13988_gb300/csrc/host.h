@@ -30,6 +30,9 @@ constexpr int64_t kRecheckCap = 8192; // graph form: FP32 re-checks per batch (s
 constexpr int64_t kFusedMaxM = 2048;   // host-sized FP32 batches up to this size: fused kernel
 constexpr int64_t kTinyBatch = 256; // mixed precision: batches this small run in FP32
 constexpr int64_t kX3Rows = 16384;   // points per pass of the split-TF32 network (its workspace rows)
+constexpr int64_t kGridPreferRows = 64;  // FP32 passes of at most this many points (and
+                                         // at most DevNet::grid_rows) run the whole-GPU
+                                         // network, where its latency is the lowest
 constexpr int64_t kX3MinRows = 192;  // FP32 passes of more points run it (fewer: the one-launch
                                      // SIMT network, whose latency is lower there)
 
@@ -110,6 +113,9 @@ struct DevNet {
     std::vector<X3Layer> x3;
     int x3_KX = 0;                  // x part of a plane row: d_in rounded up to 32
     CUtensorMap tmX3{};             // the input-row planes [kX3Rows][2 x3_KX]
+    // whole-GPU FP32 form of small passes (mlp_grid.cu): the largest batch
+    // one launch takes (0: not usable), set by ensure_x3
+    int grid_rows = 0;
 };
 
 constexpr int kNetCbn = 2;   // DevNet.kind of the CBN + SoftZ occupancy network
@@ -407,6 +413,11 @@ struct pifu_ctx {
     float* x3_part = nullptr;
     unsigned int* x3_ctr = nullptr;
     bool x3_ready = false;
+    // whole-GPU FP32 passes: hidden activations, last-layer partial sums,
+    // barrier counters (allocated with the split-TF32 buffers)
+    float* grid_H[2] = {nullptr, nullptr};
+    float* grid_part = nullptr;
+    unsigned int* grid_ctr = nullptr;
     int recheck_form = 0;             // pifu_set_recheck
     unsigned int x3_starve = 0;       // pifu_test_starve_wait
     float* part = nullptr;            // split-K partial sums of small FP32 batches
@@ -640,6 +651,12 @@ int run_mlp_x3(pifu_ctx* ctx, const DevNet& net, const PointSrc& src_in, int64_t
 int run_recheck(pifu_ctx* ctx, const DevNet& net, const PointSrc& src, int64_t m,
                 const Map& map0, const Map& map1, const Calib& calib, const Epilogue& epi,
                 cudaStream_t s);
+// Passes of at most this many points run the whole-GPU FP32 network
+// (mlp_grid.cu) in the default re-check form; 0: not usable.
+int64_t grid_rows(const pifu_ctx* ctx, const DevNet& net);
+int run_mlp_grid(pifu_ctx* ctx, const DevNet& net, const PointSrc& src, int64_t m,
+                 const Map& map0, const Map& map1, const Calib& calib, const Epilogue& epi,
+                 cudaStream_t s, const unsigned int* m_dev);
 uint8_t e4m3_byte(float v);
 int build_fp8(pifu_ctx* ctx, DevNet& net, int F, const std::vector<float>& s_h);
 int calibrate_fp8(pifu_ctx* ctx, const Map& map, const Calib& cal, int n0, cudaStream_t s);

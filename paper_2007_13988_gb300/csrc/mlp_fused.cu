@@ -384,13 +384,18 @@ __host__ __device__ int fused_pick(const FusedPlan& p, long long tiles) {
     return best;
 }
 
+// Bodies: the plan's cluster sizes, then the split-TF32 network (x3_hi > 0),
+// then the whole-GPU network (grid_hi > 0); an index past them runs nothing.
 __global__ void fused_switch_kernel(cudaGraphConditionalHandle h, FusedPlan plan,
                                     const unsigned int* count, unsigned int cap, unsigned int x3_lo,
-                                    unsigned int x3_hi) {
+                                    unsigned int x3_hi, unsigned int grid_hi) {
     const unsigned int c = min(*count, cap);
+    const unsigned int x3_idx = (unsigned)plan.n;
+    const unsigned int grid_idx = x3_idx + (x3_hi > 0u ? 1u : 0u);
     unsigned int i;
-    if (c == 0u) i = (unsigned)plan.n + 1u;
-    else if (c > x3_lo && c <= x3_hi) i = (unsigned)plan.n;
+    if (c == 0u) i = grid_idx + (grid_hi > 0u ? 1u : 0u);
+    else if (c <= grid_hi) i = grid_idx;
+    else if (c > x3_lo && c <= x3_hi) i = x3_idx;
     else i = (unsigned)fused_pick(plan, ((long long)c + kFP - 1) / kFP);
     cudaGraphSetConditional(h, i);
 }
@@ -413,8 +418,8 @@ FusedPlan fused_plan(const FusedNet& net) {
 
 cudaError_t launch_fused_switch(cudaGraphConditionalHandle h, const FusedPlan& plan,
                                 const unsigned int* count, unsigned int cap, cudaStream_t stream,
-                                unsigned int x3_lo, unsigned int x3_hi) {
-    fused_switch_kernel<<<1, 1, 0, stream>>>(h, plan, count, cap, x3_lo, x3_hi);
+                                unsigned int x3_lo, unsigned int x3_hi, unsigned int grid_hi) {
+    fused_switch_kernel<<<1, 1, 0, stream>>>(h, plan, count, cap, x3_lo, x3_hi, grid_hi);
     return cudaGetLastError();
 }
 

@@ -366,9 +366,55 @@ int run_mlp_x3(pifu_ctx* ctx, const DevNet& net, const PointSrc& src_in, int64_t
     return PIFU_OK;
 }
 
+// ---- the FP32 pass over the whole GPU (mlp_grid.cu) -------------------------------
+
+int64_t grid_rows(const pifu_ctx* ctx, const DevNet& net) {
+    if (ctx->recheck_form != PIFU_RECHECK_TENSOR || !ctx->grid_ctr) return 0;
+    return std::min<int64_t>(net.grid_rows, kGridPreferRows);
+}
+
+// The whole network (input rows, every hidden layer, the last layer and the
+// epilogue) in one cooperative launch of one CTA per SM, for m <= grid_rows
+// points (a device-sized batch: at most m of them).
+int run_mlp_grid(pifu_ctx* ctx, const DevNet& net, const PointSrc& src, int64_t m,
+                 const Map& map0, const Map& map1, const Calib& calib, const Epilogue& epi,
+                 cudaStream_t s, const unsigned int* m_dev) {
+    if (m <= 0) return PIFU_OK;
+    if (m > net.grid_rows || !ctx->grid_ctr) return PIFU_ERR_UNSUPPORTED;
+    GridArgs a{};
+    a.net = fused_of(net);
+    a.src = src;
+    a.src.count = nullptr;   // the count is m_dev, read by the kernel
+    a.p0 = 0;
+    a.M = (int)m;
+    a.m_dev = m_dev;
+    a.calib = calib;
+    a.map0 = map0;
+    a.map1 = map1;
+    a.epi = epi;
+    a.H[0] = ctx->grid_H[0];
+    a.H[1] = ctx->grid_H[1];
+    a.part = ctx->grid_part;
+    a.ctr = ctx->grid_ctr;
+    a.err = ctx->d_count + 1;
+    a.wait_extra = ctx->x3_starve;
+    double flops = 0.0, wbytes = 0.0;
+    for (const DevLayer& Ly : net.layers) {
+        flops += 2.0 * (double)m * Ly.fan_in * Ly.n_out;
+        wbytes += 4.0 * (double)Ly.n_out * (Ly.fan_in + 1);
+    }
+    cudaEvent_t ev = ctx->prof.begin(s);
+    CK(launch_mlp_grid(a, s));
+    ctx->prof.end(PIFU_K_MLP_F32, ev, s, flops,
+                  wbytes + (double)m * 4.0 * (4.0 * (map0.C + map1.C) + net.layers.back().n_out));
+    return PIFU_OK;
+}
+
 int run_recheck(pifu_ctx* ctx, const DevNet& net, const PointSrc& src, int64_t m,
                 const Map& map0, const Map& map1, const Calib& calib, const Epilogue& epi,
                 cudaStream_t s) {
+    if (m <= grid_rows(ctx, net))
+        return run_mlp_grid(ctx, net, src, m, map0, map1, calib, epi, s, nullptr);
     if (m > x3_min_rows(ctx) && x3_usable(ctx, net))
         return run_mlp_x3(ctx, net, src, m, map0, map1, calib, epi, s, nullptr);
     return run_mlp(ctx, net, src, m, map0, map1, calib, epi, s, PIFU_PREC_FP32);
@@ -564,6 +610,8 @@ int reset_after_error(pifu_ctx* ctx, cudaStream_t s) {
     CK(cudaMemsetAsync(ctx->d_count + 1, 0, sizeof(unsigned int), s));
     if (ctx->x3_ctr)
         CK(cudaMemsetAsync(ctx->x3_ctr, 0, sizeof(unsigned int) * kX3CtrWords, s));
+    if (ctx->grid_ctr)
+        CK(cudaMemsetAsync(ctx->grid_ctr, 0, sizeof(unsigned int) * kGridCtrWords, s));
     return PIFU_OK;
 }
 

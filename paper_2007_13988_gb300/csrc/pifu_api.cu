@@ -115,6 +115,10 @@ void pifu_destroy(pifu_ctx* ctx) {
     dev_free(ctx->H3[1]);
     dev_free(ctx->x3_part);
     dev_free(ctx->x3_ctr);
+    dev_free(ctx->grid_H[0]);
+    dev_free(ctx->grid_H[1]);
+    dev_free(ctx->grid_part);
+    dev_free(ctx->grid_ctr);
     uint32_t** bitsets[] = {&ctx->cand, &ctx->tent, &ctx->bin[0], &ctx->bin[1],
                             &ctx->eval, &ctx->conf[0], &ctx->conf[1]};
     for (auto b : bitsets) dev_free(*b);
@@ -240,6 +244,7 @@ int pifu_localize(pifu_ctx* ctx, const pifu_fmap* occ_map, const float calib[12]
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     ctx->have_volume = false;
     int st = ensure_level_ws(ctx, (int)n_fine);
+    if (st == PIFU_OK && subdiv == PIFU_SUBDIV_METHOD) st = ensure_clist(ctx, kChunkTC);
     if (st != PIFU_OK) return st;
 
     pifu_volume vs{};
@@ -339,8 +344,23 @@ int pifu_localize(pifu_ctx* ctx, const pifu_fmap* occ_map, const float calib[12]
         Epilogue epi{};
         epi.mode = EPI_LEVEL;
         epi.list = ctx->list;
+        const int64_t level_nodes = (int64_t)(N + 1) * (N + 1) * (N + 1);
         while (n > 0) {
+            // The round's conflicts also go to a key list when it can hold
+            // them all (at most n): the next frontier, their unevaluated
+            // 26-neighbours, is then found in work proportional to them.
+            // Otherwise the conflict bitset conf[q] is dilated over the whole
+            // grid (stale bits of earlier list rounds add nothing: their
+            // neighbours are evaluated).
+            const bool sparse = (int64_t)n <= ctx->clist_cap;
             epi.lv = LevelBits{ctx->values, ctx->tent, ctx->bin[cur], ctx->conf[q], N, rw, 0};
+            if (sparse) {
+                epi.lv.clist = ctx->clist;
+                epi.lv.ccount = ctx->d_ccount;
+                epi.lv.ccap = (unsigned)ctx->clist_cap;
+                epi.lv.err = ctx->d_count + 1;
+                CK(cudaMemsetAsync(ctx->d_ccount, 0, sizeof(unsigned int), s));
+            }
             st = eval_level_batch(ctx, src, n, map, cal, epi, prec, lv->margin,
                                   use_sur && l < lv->num_levels - 1, lv->surrogate_margin, s,
                                   &vs.rechecked_per_level[l], &vs.fallback_per_level[l]);
@@ -349,9 +369,16 @@ int pifu_localize(pifu_ctx* ctx, const pifu_fmap* occ_map, const float calib[12]
             // unevaluated 1-ring of this evaluation's conflicts
             CK(cudaMemsetAsync(ctx->d_count, 0, sizeof(unsigned int), s));
             ev = ctx->prof.begin(s);
-            CK(launch_dilate_select(ctx->conf[q], ctx->eval, ctx->conf[1 - q], N, ctx->list,
-                                    ctx->d_count, s));
-            ctx->prof.end(PIFU_K_SELECT, ev, s, 0.0, 4.0 * wbytes);
+            if (sparse)
+                CK(launch_expand_conflicts(ctx->clist, ctx->d_ccount, n, N, ctx->eval, 0, 0,
+                                           ctx->list, ctx->d_count, (unsigned)level_nodes,
+                                           ctx->d_count + 1, s));
+            else
+                CK(launch_dilate_select(ctx->conf[q], ctx->eval, ctx->conf[1 - q], N, ctx->list,
+                                        ctx->d_count, s));
+            // the list expansion reads a few bytes per conflict, counted
+            // with the list it writes (below)
+            ctx->prof.end(PIFU_K_SELECT, ev, s, 0.0, sparse ? 0.0 : 4.0 * wbytes);
             st = read_count(ctx, s, &n);
             if (st != PIFU_OK) return st;
             ctx->prof.k[PIFU_K_SELECT].bytes += 4.0 * n;

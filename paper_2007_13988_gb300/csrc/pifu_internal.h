@@ -582,7 +582,41 @@ cudaError_t launch_mlp_fused(const FusedNet& net, const PointSrc& src, int64_t p
 // one: x3_hi > 0); to a value past every body (no branch) when c is 0.
 cudaError_t launch_fused_switch(cudaGraphConditionalHandle h, const FusedPlan& plan,
                                 const unsigned int* count, unsigned int cap, cudaStream_t stream,
-                                unsigned int x3_lo = 0, unsigned int x3_hi = 0);
+                                unsigned int x3_lo = 0, unsigned int x3_hi = 0,
+                                unsigned int grid_hi = 0);
+
+// --- mlp_grid.cu -----------------------------------------------------------
+// The whole network in FP32 for a batch of at most kGridMaxRows points in one
+// cooperative launch over every SM: each hidden layer's neurons split over
+// the CTAs, a bounded grid barrier between layers (mlp_grid.cu).
+constexpr int kGridMaxRows = 256;    // points per launch
+constexpr int kGridMaxCtas = 256;    // CTAs per launch (one per SM)
+constexpr int kGridMaxGroups = 64;   // point groups per launch
+// [kFusedMaxLayers] grid barrier counters (one per hidden layer), [1] CTA
+// departures, [kGridMaxGroups] last-layer arrivals per point group
+constexpr int kGridCtrWords = kFusedMaxLayers + 1 + kGridMaxGroups;
+struct GridArgs {
+    FusedNet net;
+    PointSrc src;                // points p0 .. p0 + min(M, *m_dev) - 1
+    int64_t p0;
+    int M;                       // <= kGridMaxRows
+    const unsigned int* m_dev;   // device-resident batch size, or null
+    Calib calib;
+    Map map0, map1;
+    Epilogue epi;
+    float* H[2];                 // [kGridMaxRows][max_hidden] hidden activations, ping-pong
+    float* part;                 // [kGridMaxRows][kGridMaxCtas][4] last-layer partial sums
+    unsigned int* ctr;           // kGridCtrWords, zero at launch and again at exit
+    unsigned int* err;           // device error word (kErrTimeout, kErrCapacity)
+    unsigned int wait_extra;     // test hook (0): the grid barrier needs this many more arrivals
+};
+// Whether the network's shape fits the kernel (hidden widths and ldw
+// multiples of 4, 16-byte aligned weights, at most 4 outputs, >= 1 hidden layer).
+bool grid_ok(const FusedNet& n);
+// The largest batch one launch takes for this network on the current device
+// (0: the network does not fit or the device cannot hold the grid).
+int grid_max_rows(const FusedNet& n);
+cudaError_t launch_mlp_grid(const GridArgs& a, cudaStream_t stream);
 
 // --- cbn.cu --------------------------------------------------------------
 // The CBN + SoftZ occupancy network (Appendix, Eq. 7 and Eq. 8) in FP32, with

@@ -111,6 +111,18 @@ __device__ __forceinline__ void griddep_wait() {
 
 // ---- TMA ----------------------------------------------------------------------
 
+// Contiguous bulk copy of `bytes` from global to this CTA's shared memory,
+// completion counted in bytes on `bar`.  Both addresses 16-byte aligned,
+// bytes a multiple of 16.
+__device__ __forceinline__ void bulk_load_1d(void* dst, const void* src, uint32_t bytes,
+                                             uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+        ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes),
+        "r"(smem_u32(bar))
+        : "memory");
+}
+
 // 2-D tiled bulk tensor load into shared memory, completion counted in bytes
 // on `bar`.  x (innermost) must be a multiple of 16 bytes' worth of elements.
 __device__ __forceinline__ void tma_load_2d(void* dst, const void* tmap, int x, int y,

@@ -453,7 +453,7 @@ PIFU_RECHECK_TENSOR_ALL = 2
 
 def pifu_set_recheck(ctx, form):
     """Arithmetic of the MIXED forms' FP32 passes: split TF32 on the tensor
-    cores above 512 points (default), the FP32 SIMT network, or split TF32
+    cores above 192 points (default), the FP32 SIMT network, or split TF32
     for every pass."""
     _check(_lib().pifu_set_recheck(ctx, int(form)), "pifu_set_recheck", ctx)
 
