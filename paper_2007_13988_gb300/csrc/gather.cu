@@ -3,8 +3,9 @@
 //
 // Layout: feature maps are channel-last [H][W][C], so the C channels of one
 // texel are one contiguous run; a thread owns one point and 16 channels and
-// issues four 16-byte loads per bilinear tap, and consecutive threads of a
-// warp read consecutive 64-byte pieces of the same texel row (coalesced).
+// issues four 16-byte loads per bilinear tap (two for a BF16 map), and
+// consecutive threads of a warp read consecutive pieces of the same texel
+// row (coalesced).
 // The 16.8 MB full-size map stays resident in the 129 MB L2 across a frame.
 //
 // Projection and sampling arithmetic: gather.cuh.
@@ -49,8 +50,19 @@ __global__ void __launch_bounds__(256) gather_kernel(PointSrc src, int64_t p0, i
         const PointSample ps = sample_point(src, p0 + lp, calib, map0, map1);
         OutT* row = X + (int64_t)lp * ldx;
 #pragma unroll
-        for (uint32_t j = 0; j < kQPT; ++j)
-            if (q0 + j < nq) store4(row + 4 * (q0 + j), sample_quad(ps, 4 * (int)(q0 + j)));
+        for (uint32_t j = 0; j < kQPT; j += 2) {
+            const int c = 4 * (int)(q0 + j);
+            if (q0 + j + 1 < nq && oct_bf16(ps, c)) {
+                // two quads of a BF16 map: 16-byte taps
+                float4 lo, hi;
+                sample_oct_bf16(ps, c, lo, hi);
+                store4(row + c, lo);
+                store4(row + c + 4, hi);
+            } else {
+                if (q0 + j < nq) store4(row + c, sample_quad(ps, c));
+                if (q0 + j + 1 < nq) store4(row + c + 4, sample_quad(ps, c + 4));
+            }
+        }
     }
 }
 

@@ -115,6 +115,16 @@ __device__ __forceinline__ float4 tap4(const Map& mp, int64_t e) {
     return ld4(static_cast<const float*>(mp.data) + e);
 }
 
+// Eight consecutive channels of a BF16 texel as floats: one 16-byte load
+// (e a multiple of 8, the map 16-byte aligned).
+__device__ __forceinline__ void tap8_bf16(const Map& mp, int64_t e, float4& lo, float4& hi) {
+    const uint4 v = __ldg(reinterpret_cast<const uint4*>(static_cast<const uint16_t*>(mp.data) + e));
+    lo = make_float4(__uint_as_float(v.x << 16), __uint_as_float(v.x & 0xffff0000u),
+                     __uint_as_float(v.y << 16), __uint_as_float(v.y & 0xffff0000u));
+    hi = make_float4(__uint_as_float(v.z << 16), __uint_as_float(v.z & 0xffff0000u),
+                     __uint_as_float(v.w << 16), __uint_as_float(v.w & 0xffff0000u));
+}
+
 // A point's projection, the frame's maps and the four bilinear taps of
 // each map: everything its channels share.
 struct PointSample {
@@ -187,6 +197,38 @@ __device__ __forceinline__ float4 sample_quad(const PointSample& ps, int c) {
     r.z = fmaf(w11, f11.z, fmaf(w01, f01.z, fmaf(w10, f10.z, w00 * f00.z)));
     r.w = fmaf(w11, f11.w, fmaf(w01, f01.w, fmaf(w10, f10.w, w00 * f00.w)));
     return r;
+}
+
+// Whether channels c..c+7 of the sampled point's row lie in one BF16 map at
+// a multiple of 8 of its channels (then sample_oct_bf16 reads them with one
+// 16-byte load per tap).
+__device__ __forceinline__ bool oct_bf16(const PointSample& ps, int c) {
+    const int C0 = ps.map0.C, C1 = ps.map1.C;
+    if (c + 8 <= C0) return ps.map0.dtype == 1 && (C0 & 7) == 0 && (c & 7) == 0;
+    return c >= C0 && c + 8 <= C0 + C1 && ps.map1.dtype == 1 && (C1 & 7) == 0 &&
+           ((c - C0) & 7) == 0;
+}
+
+// Channels c..c+7 of the sampled point's row when oct_bf16(ps, c): the
+// same bilinear arithmetic as sample_quad, per channel.
+__device__ __forceinline__ void sample_oct_bf16(const PointSample& ps, int c, float4& lo,
+                                                float4& hi) {
+    const bool first = c < ps.map0.C;
+    const Map& mp = first ? ps.map0 : ps.map1;
+    const int64_t cc = first ? c : c - ps.map0.C;
+    float4 a[4], b[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) tap8_bf16(mp, (first ? ps.e0[t] : ps.e1[t]) + cc, a[t], b[t]);
+    const float w00 = first ? ps.w0[0] : ps.w1[0], w10 = first ? ps.w0[1] : ps.w1[1];
+    const float w01 = first ? ps.w0[2] : ps.w1[2], w11 = first ? ps.w0[3] : ps.w1[3];
+    lo.x = fmaf(w11, a[3].x, fmaf(w01, a[2].x, fmaf(w10, a[1].x, w00 * a[0].x)));
+    lo.y = fmaf(w11, a[3].y, fmaf(w01, a[2].y, fmaf(w10, a[1].y, w00 * a[0].y)));
+    lo.z = fmaf(w11, a[3].z, fmaf(w01, a[2].z, fmaf(w10, a[1].z, w00 * a[0].z)));
+    lo.w = fmaf(w11, a[3].w, fmaf(w01, a[2].w, fmaf(w10, a[1].w, w00 * a[0].w)));
+    hi.x = fmaf(w11, b[3].x, fmaf(w01, b[2].x, fmaf(w10, b[1].x, w00 * b[0].x)));
+    hi.y = fmaf(w11, b[3].y, fmaf(w01, b[2].y, fmaf(w10, b[1].y, w00 * b[0].y)));
+    hi.z = fmaf(w11, b[3].z, fmaf(w01, b[2].z, fmaf(w10, b[1].z, w00 * b[0].z)));
+    hi.w = fmaf(w11, b[3].w, fmaf(w01, b[2].w, fmaf(w10, b[1].w, w00 * b[0].w)));
 }
 
 // Channels c..c+3 of the MLP input row of point p (one quad on its own,
