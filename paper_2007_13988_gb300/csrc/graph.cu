@@ -69,10 +69,21 @@ int g_recheck(pifu_ctx* ctx, const DevNet& net, const PointSrc& src, int64_t cap
 // the FP32 re-evaluation of the queued near-0.5 occupancies (device-sized).
 // With `sur`, f_S runs first and f_O takes the occupancies f_S put within
 // `sur_margin` of 0.5 (a device-sized queue; *fallback += its length).
+// rs (a conflict round's start, m_dev its batch size): the round's statistics
+// and the zeroing of its conflict count, merged into the launch that sets
+// the tiny/large branch where the batch takes that branch, else launched
+// before the batch.
 int g_eval(pifu_ctx* ctx, const DevNet& net, const PointSrc& src, int64_t cap,
            const unsigned int* m_dev, const Map& map, const Calib& cal, const Epilogue& epi,
            int prec, float margin, unsigned long long* rechecked, cudaStream_t s,
-           bool sur, float sur_margin, unsigned long long* fallback, int64_t qcap_in) {
+           bool sur, float sur_margin, unsigned long long* fallback, int64_t qcap_in,
+           const RoundStart* rs) {
+    const bool branch = !sur && prec != PIFU_PREC_BF16 && prec != PIFU_PREC_FP8 && m_dev &&
+                        ctx->cap_stream3 && s != ctx->cap_stream3;
+    if (rs && !branch) {
+        CK(launch_accumulate(rs->evals, m_dev, rs->cap, rs->err, s));
+        CK(cudaMemsetAsync(rs->zero, 0, sizeof(unsigned int), s));
+    }
     if (sur) {
         // qcap_in > 0: the f_O queue already holds keys (the frame stream's
         // finest-level keys), f_S's fall-backs are appended after them
@@ -98,7 +109,7 @@ int g_eval(pifu_ctx* ctx, const DevNet& net, const PointSrc& src, int64_t cap,
     if (prec == PIFU_PREC_BF16 || prec == PIFU_PREC_FP8)
         return run_mlp_tc(ctx, net, src, cap, map, Map{}, cal, epi, s, m_dev,
                           prec == PIFU_PREC_FP8);
-    if (m_dev && ctx->cap_stream3 && s != ctx->cap_stream3) {
+    if (branch) {
         // A device-sized batch of at most kTinyBatch points goes straight to
         // FP32 (one fused launch), as in the host-driven form; the tensor-core
         // pass and its re-check run above that.  Two IF nodes, set on the device.
@@ -108,7 +119,8 @@ int g_eval(pifu_ctx* ctx, const DevNet& net, const PointSrc& src, int64_t cap,
         cudaGraphConditionalHandle hs, hl;
         CK(cudaGraphConditionalHandleCreate(&hs, cg, 0, 0));
         CK(cudaGraphConditionalHandleCreate(&hl, cg, 0, 0));
-        CK(launch_branch(hs, hl, m_dev, (unsigned)kTinyBatch, s));
+        if (rs) CK(launch_round_start(hs, hl, m_dev, (unsigned)kTinyBatch, *rs, s));
+        else CK(launch_branch(hs, hl, m_dev, (unsigned)kTinyBatch, s));
         cudaStream_t s3 = ctx->cap_stream3;
         for (int br = 0; br < 2; ++br) {
             cudaGraph_t body = nullptr;
@@ -242,18 +254,20 @@ int g_enqueue_frame(pifu_ctx* ctx, const FrameKey& k, const Map& occ, const Map&
         const int prev = cur;
         cur ^= 1;
         N *= 2;
-        CK(launch_classify(ctx->bin[prev], N, ctx->cand, ctx->tent, ctx->bin[cur], ctx->eval,
-                           ctx->conf[0], s));
-        CK(launch_popcount(ctx->cand, words_of(N), &gs->cands[l], s));
-        CK(cudaMemsetAsync(ctx->d_count, 0, sizeof(unsigned int), s));
-        CK(launch_dilate_select(ctx->cand, ctx->eval, nullptr, N, ctx->list, ctx->d_count, s));
         cudaStreamCaptureStatus cs;
         cudaGraph_t cg = nullptr;
         CK(cudaStreamGetCaptureInfo(s, &cs, nullptr, &cg, nullptr, nullptr, nullptr));
         cudaGraphConditionalHandle h;
         CK(cudaGraphConditionalHandleCreate(&h, cg, 0, 0));
-        CK(launch_loop_control(h, ctx->d_count, (unsigned)kChunkTC, &gs->rounds[l], 0, k.max_rounds,
-                               err, s));
+        // the level's set-up (candidate count and the list count's zeroing in
+        // the same launch), then its first selection, whose last CTA decides
+        // whether the loop runs
+        CK(launch_classify(ctx->bin[prev], N, ctx->cand, ctx->tent, ctx->bin[cur], ctx->eval,
+                           ctx->conf[0], s, 1, 0, 0, &gs->cands[l], ctx->d_count));
+        const LoopTail first{h, ctx->d_tail, (unsigned)kChunkTC, &gs->rounds[l], 0, k.max_rounds,
+                             err};
+        CK(launch_dilate_select(ctx->cand, ctx->eval, nullptr, N, ctx->list, ctx->d_count, s, 1, 0,
+                                0, &first));
         cudaGraph_t body = nullptr;
         st = g_add_while(ctx, s, h, &body);
         if (st != PIFU_OK) return st;
@@ -273,26 +287,21 @@ int g_enqueue_frame(pifu_ctx* ctx, const FrameKey& k, const Map& occ, const Map&
             epi.lv.ccount = ctx->d_ccount;
             epi.lv.ccap = (unsigned)ctx->clist_cap;
             epi.lv.err = err;
-            st = launch_accumulate(&gs->evals[l], ctx->d_count, (unsigned)kChunkTC, err, sb) == cudaSuccess
-                     ? PIFU_OK : PIFU_ERR_CUDA;
-            if (st == PIFU_OK &&
-                cudaMemsetAsync(ctx->d_ccount, 0, sizeof(unsigned int), sb) != cudaSuccess)
-                st = PIFU_ERR_CUDA;
-            if (st == PIFU_OK)
-                st = g_eval(ctx, net, src, kChunkTC, ctx->d_count, occ, cal, epi, k.precision,
-                            k.margin, &gs->rechecked[l], sb,
-                            k.use_surrogate && l < k.num_levels - 1, k.sur_margin,
-                            &gs->fallback[l]);
+            // the round's statistics and the zeroing of its conflict count
+            // ride in the launch that picks the batch's branch; the expansion's
+            // last CTA decides whether another round runs
+            const RoundStart rs{&gs->evals[l], (unsigned)kChunkTC, err, ctx->d_ccount};
+            st = g_eval(ctx, net, src, kChunkTC, ctx->d_count, occ, cal, epi, k.precision,
+                        k.margin, &gs->rechecked[l], sb, k.use_surrogate && l < k.num_levels - 1,
+                        k.sur_margin, &gs->fallback[l], 0, &rs);
             if (st == PIFU_OK && cudaMemsetAsync(ctx->d_count, 0, sizeof(unsigned int), sb) != cudaSuccess)
                 st = PIFU_ERR_CUDA;
+            const LoopTail next{h, ctx->d_tail + 1, (unsigned)kChunkTC, &gs->rounds[l], 1,
+                                k.max_rounds, err};
             if (st == PIFU_OK &&
                 launch_expand_conflicts(ctx->clist, ctx->d_ccount, (unsigned)kChunkTC, N, ctx->eval,
-                                        0, 0, ctx->list, ctx->d_count, (unsigned)kChunkTC, err,
-                                        sb) != cudaSuccess)
-                st = PIFU_ERR_CUDA;
-            if (st == PIFU_OK && launch_loop_control(h, ctx->d_count, (unsigned)kChunkTC,
-                                                     &gs->rounds[l], 1, k.max_rounds, err,
-                                                     sb) != cudaSuccess)
+                                        0, 0, ctx->list, ctx->d_count, (unsigned)kChunkTC, err, sb,
+                                        nullptr, nullptr, nullptr, nullptr, &next) != cudaSuccess)
                 st = PIFU_ERR_CUDA;
         }
         cudaGraph_t body_out = nullptr;
@@ -408,6 +417,10 @@ int g_build(pifu_ctx* ctx, const FrameKey& k, const Map& occ, const Map& col, co
     if (!ctx->cap_stream3) CK(cudaStreamCreateWithFlags(&ctx->cap_stream3, cudaStreamNonBlocking));
     if (!ctx->cap_stream4) CK(cudaStreamCreateWithFlags(&ctx->cap_stream4, cudaStreamNonBlocking));
     if (!ctx->d_gstats) CK(dev_alloc(&ctx->d_gstats, 1));
+    if (!ctx->d_tail) {
+        CK(dev_alloc(&ctx->d_tail, 2));
+        CK(cudaMemset(ctx->d_tail, 0, 2 * sizeof(unsigned int)));
+    }
     {
         const int st = ensure_clist(ctx, kChunkTC);
         if (st != PIFU_OK) return st;

@@ -504,6 +504,7 @@ struct pifu_ctx {
     int64_t clist_cap = 0;
     GraphStats* d_gstats = nullptr;
     GraphStats* h_gstats = nullptr;       // pinned
+    unsigned int* d_tail = nullptr;       // graph form: the loop tails' CTA counters [2]
     int64_t g_launches_fixed = 0;         // kernel launches outside the loops
     int64_t g_launches_body[8] = {};      // kernel launches per loop iteration
     // lockstep frame batches (pifu_frames)
@@ -717,7 +718,7 @@ int g_eval(pifu_ctx* ctx, const DevNet& net, const PointSrc& src, int64_t cap,
            const unsigned int* m_dev, const Map& map, const Calib& cal, const Epilogue& epi,
            int prec, float margin, unsigned long long* rechecked, cudaStream_t s,
            bool sur = false, float sur_margin = 0.f, unsigned long long* fallback = nullptr,
-           int64_t qcap_in = 0);
+           int64_t qcap_in = 0, const RoundStart* rs = nullptr);
 int g_add_while(pifu_ctx* ctx, cudaStream_t s, cudaGraphConditionalHandle h, cudaGraph_t* body);
 int g_enqueue_frame(pifu_ctx* ctx, const FrameKey& k, const Map& occ, const Map& col,
                     const Calib& cal);

@@ -108,13 +108,17 @@ __device__ __forceinline__ void classify_word(const uint32_t* __restrict__ coars
     t_word = ((t_even & EV) | (t_odd & OD)) & vm;
 }
 
+// cands (optional, one frame): += the number of candidate bits; zero
+// (optional): set to 0 (the list count the selection after it appends to).
 __global__ void __launch_bounds__(256) classify_kernel(const uint32_t* __restrict__ coarse, int N,
                                                        uint32_t* __restrict__ cand,
                                                        uint32_t* __restrict__ tent,
                                                        uint32_t* __restrict__ bin,
                                                        uint32_t* __restrict__ eval,
                                                        uint32_t* __restrict__ conf0,
-                                                       int64_t cslot, int64_t fslot) {
+                                                       int64_t cslot, int64_t fslot,
+                                                       unsigned long long* __restrict__ cands,
+                                                       unsigned int* __restrict__ zero) {
     {
         const int64_t f = blockIdx.y;
         coarse += f * cslot;
@@ -124,15 +128,53 @@ __global__ void __launch_bounds__(256) classify_kernel(const uint32_t* __restric
         eval += f * fslot;
         conf0 += f * fslot;
     }
+    if (zero && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) *zero = 0u;
     const int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (w >= words_of(N)) return;
-    uint32_t c_word, t_word;
-    classify_word(coarse, N, w, c_word, t_word);
-    cand[w] = c_word;
-    tent[w] = t_word;
-    bin[w] = t_word;
-    eval[w] = 0u;
-    conf0[w] = 0u;
+    uint32_t c_word = 0u;
+    if (w < words_of(N)) {
+        uint32_t t_word;
+        classify_word(coarse, N, w, c_word, t_word);
+        cand[w] = c_word;
+        tent[w] = t_word;
+        bin[w] = t_word;
+        eval[w] = 0u;
+        conf0[w] = 0u;
+    }
+    if (cands) {
+        unsigned int n = __popc(c_word);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) n += __shfl_xor_sync(0xffffffffu, n, o);
+        if ((threadIdx.x & 31) == 0 && n) atomicAdd(cands, (unsigned long long)n);
+    }
+}
+
+// The conflict loop's decision (loop_control_kernel's) taken by the last CTA
+// of the kernel that wrote the frontier count, instead of a launch of its
+// own.  Every thread of the kernel calls it once, at its end.
+__device__ __forceinline__ void loop_tail(const LoopTail& t, const unsigned int* count) {
+    if (!t.done) return;
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    __threadfence();
+    const unsigned int ctas = gridDim.x * gridDim.y;
+    if (atomicAdd(t.done, 1u) + 1u != ctas) return;
+    __threadfence();
+    const unsigned int c = *reinterpret_cast<const volatile unsigned int*>(count);
+    bool go = c > 0u;
+    if (go && c > t.cap) {
+        atomicOr(t.err, kErrCapacity);
+        go = false;
+    }
+    if (go && t.count_round) {
+        const unsigned int r = *t.rounds + 1u;
+        *t.rounds = r;
+        if ((int)r > t.max_rounds) {
+            atomicOr(t.err, kErrNotConverged);
+            go = false;
+        }
+    }
+    *t.done = 0u;
+    cudaGraphSetConditional(t.h, go ? 1u : 0u);
 }
 
 __global__ void __launch_bounds__(256) dense_setup_kernel(int N, uint32_t* __restrict__ cand,
@@ -187,7 +229,7 @@ __global__ void __launch_bounds__(256) dilate_select_kernel(const uint32_t* __re
                                                             int* __restrict__ list,
                                                             unsigned int* __restrict__ count,
                                                             int64_t fslot, int64_t slot_nodes,
-                                                            int radius) {
+                                                            int radius, LoopTail tail) {
     {
         const int64_t f = blockIdx.y;
         src += f * fslot;
@@ -233,6 +275,7 @@ __global__ void __launch_bounds__(256) dilate_select_kernel(const uint32_t* __re
             list[pos++] = (int)(node0 + b);
         }
     }
+    loop_tail(tail, count);
 }
 
 // Threshold subdivision, the second octree baseline of Fig. 3: every fine
@@ -342,7 +385,7 @@ __global__ void __launch_bounds__(256) expand_conflicts_kernel(
     int* __restrict__ list, unsigned int* __restrict__ count, unsigned int cap,
     unsigned int* __restrict__ err, const SlotView* __restrict__ sv,
     unsigned int* __restrict__ slot_count, int* __restrict__ list_f,
-    unsigned int* __restrict__ count_f) {
+    unsigned int* __restrict__ count_f, LoopTail tail) {
     const unsigned int nc = min(*ccount, max_c);
     const int lane = threadIdx.x & 31;
     const int64_t total = (int64_t)nc * 26;
@@ -408,6 +451,7 @@ __global__ void __launch_bounds__(256) expand_conflicts_kernel(
             }
         }
     }
+    loop_tail(tail, count);
 }
 
 // ---- frame stream: the set-up and selection of every slot in one launch each ----
@@ -527,16 +571,31 @@ __global__ void accumulate_kernel(unsigned long long* dst, const unsigned int* s
     if (v > cap) atomicOr(err, kErrCapacity);
 }
 
+// The start of a conflict round in the graph: accumulate_kernel's statistics,
+// *zero = 0, and branch_kernel's two conditions, in one launch.
+__global__ void round_start_kernel(cudaGraphConditionalHandle hs, cudaGraphConditionalHandle hl,
+                                   const unsigned int* count, unsigned int threshold,
+                                   unsigned long long* evals, unsigned int cap, unsigned int* err,
+                                   unsigned int* zero) {
+    const unsigned int c = *count;
+    *evals += c;
+    if (c > cap) atomicOr(err, kErrCapacity);
+    *zero = 0u;
+    cudaGraphSetConditional(hs, (c > 0u && c <= threshold) ? 1u : 0u);
+    cudaGraphSetConditional(hl, c > threshold ? 1u : 0u);
+}
+
 inline unsigned blocks_for(int64_t n) { return (unsigned)((n + 255) / 256); }
 
 }  // namespace
 
 cudaError_t launch_classify(const uint32_t* coarse_bin, int N, uint32_t* cand, uint32_t* tent,
                             uint32_t* bin, uint32_t* eval, uint32_t* conf0, cudaStream_t stream,
-                            int slots, int64_t cslot, int64_t fslot) {
-    if (slots < 1 || slots > 65535) return cudaErrorInvalidValue;
+                            int slots, int64_t cslot, int64_t fslot, unsigned long long* cands,
+                            unsigned int* zero) {
+    if (slots < 1 || slots > 65535 || (cands && slots != 1)) return cudaErrorInvalidValue;
     classify_kernel<<<dim3(blocks_for(words_of(N)), (unsigned)slots), 256, 0, stream>>>(
-        coarse_bin, N, cand, tent, bin, eval, conf0, cslot, fslot);
+        coarse_bin, N, cand, tent, bin, eval, conf0, cslot, fslot, cands, zero);
     return cudaGetLastError();
 }
 
@@ -551,17 +610,17 @@ cudaError_t launch_dense_setup(int N, uint32_t* cand, uint32_t* tent, uint32_t* 
 
 cudaError_t launch_dilate_select(const uint32_t* src, uint32_t* eval, uint32_t* clear, int N,
                                  int* list, unsigned int* count, cudaStream_t stream, int slots,
-                                 int64_t fslot, int64_t slot_nodes) {
+                                 int64_t fslot, int64_t slot_nodes, const LoopTail* tail) {
     if (slots < 1 || slots > 65535) return cudaErrorInvalidValue;
     dilate_select_kernel<<<dim3(blocks_for(words_of(N)), (unsigned)slots), 256, 0, stream>>>(
-        src, eval, clear, N, list, count, fslot, slot_nodes, 1);
+        src, eval, clear, N, list, count, fslot, slot_nodes, 1, tail ? *tail : LoopTail{});
     return cudaGetLastError();
 }
 
 cudaError_t launch_select(const uint32_t* src, uint32_t* eval, int N, int* list,
                           unsigned int* count, cudaStream_t stream) {
     dilate_select_kernel<<<blocks_for(words_of(N)), 256, 0, stream>>>(src, eval, nullptr, N, list,
-                                                                    count, 0, 0, 0);
+                                                                    count, 0, 0, 0, LoopTail{});
     return cudaGetLastError();
 }
 
@@ -587,13 +646,13 @@ cudaError_t launch_expand_conflicts(const int* clist, const unsigned int* ccount
                                     int64_t slot_words, int* list, unsigned int* count,
                                     unsigned int cap, unsigned int* err, cudaStream_t stream,
                                     const SlotView* sv, unsigned int* slot_count, int* list_f,
-                                    unsigned int* count_f) {
-    if (max_c == 0) return cudaSuccess;
+                                    unsigned int* count_f, const LoopTail* tail) {
+    if (max_c == 0) return tail ? cudaErrorInvalidValue : cudaSuccess;
     const int64_t total = (int64_t)max_c * 26;
     const int64_t blocks = std::min<int64_t>((total + 255) / 256, 152 * 8);
     expand_conflicts_kernel<<<(unsigned)blocks, 256, 0, stream>>>(
         clist, ccount, max_c, N, eval, key_div, slot_words, list, count, cap, err, sv,
-        slot_count, list_f, count_f);
+        slot_count, list_f, count_f, tail ? *tail : LoopTail{});
     return cudaGetLastError();
 }
 
@@ -625,6 +684,14 @@ cudaError_t launch_branch(cudaGraphConditionalHandle hs, cudaGraphConditionalHan
 cudaError_t launch_accumulate(unsigned long long* dst, const unsigned int* src, unsigned int cap,
                               unsigned int* err, cudaStream_t stream) {
     accumulate_kernel<<<1, 1, 0, stream>>>(dst, src, cap, err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_round_start(cudaGraphConditionalHandle hs, cudaGraphConditionalHandle hl,
+                               const unsigned int* count, unsigned int threshold,
+                               const RoundStart& rs, cudaStream_t stream) {
+    round_start_kernel<<<1, 1, 0, stream>>>(hs, hl, count, threshold, rs.evals, rs.cap, rs.err,
+                                            rs.zero);
     return cudaGetLastError();
 }
 

@@ -612,6 +612,7 @@ int reset_after_error(pifu_ctx* ctx, cudaStream_t s) {
         CK(cudaMemsetAsync(ctx->x3_ctr, 0, sizeof(unsigned int) * kX3CtrWords, s));
     if (ctx->grid_ctr)
         CK(cudaMemsetAsync(ctx->grid_ctr, 0, sizeof(unsigned int) * kGridCtrWords, s));
+    if (ctx->d_tail) CK(cudaMemsetAsync(ctx->d_tail, 0, 2 * sizeof(unsigned int), s));
     return PIFU_OK;
 }
 

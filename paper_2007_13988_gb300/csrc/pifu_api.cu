@@ -119,6 +119,7 @@ void pifu_destroy(pifu_ctx* ctx) {
     dev_free(ctx->grid_H[1]);
     dev_free(ctx->grid_part);
     dev_free(ctx->grid_ctr);
+    dev_free(ctx->d_tail);
     uint32_t** bitsets[] = {&ctx->cand, &ctx->tent, &ctx->bin[0], &ctx->bin[1],
                             &ctx->eval, &ctx->conf[0], &ctx->conf[1]};
     for (auto b : bitsets) dev_free(*b);

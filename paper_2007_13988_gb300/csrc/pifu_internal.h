@@ -402,9 +402,25 @@ __host__ __device__ inline int64_t words_of(int N) {
 // candidate bits; clears eval, conf0 and the working bits (= tentative).
 // Several frames: `slots` of them, bitsets cslot (coarse) / fslot (fine)
 // words apart.
+// One frame: cands (optional) += the candidates' count, zero (optional) = 0.
 cudaError_t launch_classify(const uint32_t* coarse_bin, int N, uint32_t* cand, uint32_t* tent,
                             uint32_t* bin, uint32_t* eval, uint32_t* conf0, cudaStream_t stream,
-                            int slots = 1, int64_t cslot = 0, int64_t fslot = 0);
+                            int slots = 1, int64_t cslot = 0, int64_t fslot = 0,
+                            unsigned long long* cands = nullptr, unsigned int* zero = nullptr);
+
+// Graph form: the conflict loop's decision (launch_loop_control's, on the
+// kernel's own list count) taken by the last CTA of the kernel that builds
+// the frontier.  done: a CTA counter, zero between launches.  done = null:
+// no decision.
+struct LoopTail {
+    cudaGraphConditionalHandle h;
+    unsigned int* done;
+    unsigned int cap;
+    unsigned int* rounds;
+    int count_round;
+    int max_rounds;
+    unsigned int* err;
+};
 
 // Level-0 set-up: everything empty except eval = all nodes.
 cudaError_t launch_dense_setup(int N, uint32_t* cand, uint32_t* tent, uint32_t* bin,
@@ -416,7 +432,8 @@ cudaError_t launch_dense_setup(int N, uint32_t* cand, uint32_t* tent, uint32_t* 
 // Several frames: one list for all, keys frame * slot_nodes + node.
 cudaError_t launch_dilate_select(const uint32_t* src, uint32_t* eval, uint32_t* clear, int N,
                                  int* list, unsigned int* count, cudaStream_t stream,
-                                 int slots = 1, int64_t fslot = 0, int64_t slot_nodes = 0);
+                                 int slots = 1, int64_t fslot = 0, int64_t slot_nodes = 0,
+                                 const LoopTail* tail = nullptr);
 
 // src & ~eval (no dilation); eval |= it; append the node indices to list.
 cudaError_t launch_select(const uint32_t* src, uint32_t* eval, int N, int* list,
@@ -453,7 +470,8 @@ cudaError_t launch_expand_conflicts(const int* clist, const unsigned int* ccount
                                     unsigned int cap, unsigned int* err, cudaStream_t stream,
                                     const SlotView* sv = nullptr,
                                     unsigned int* slot_count = nullptr, int* list_f = nullptr,
-                                    unsigned int* count_f = nullptr);
+                                    unsigned int* count_f = nullptr,
+                                    const LoopTail* tail = nullptr);
 
 // Frame stream: everything the scheduler kernel reads and writes.
 struct StreamCtl {
@@ -536,6 +554,17 @@ cudaError_t launch_branch(cudaGraphConditionalHandle hs, cudaGraphConditionalHan
 // *dst += *src; capacity error bit if *src > cap.
 cudaError_t launch_accumulate(unsigned long long* dst, const unsigned int* src, unsigned int cap,
                               unsigned int* err, cudaStream_t stream);
+// A conflict round's start in one launch: *evals += *count (capacity error
+// bit if above cap), *zero = 0, then launch_branch's two conditions.
+struct RoundStart {
+    unsigned long long* evals;
+    unsigned int cap;
+    unsigned int* err;
+    unsigned int* zero;
+};
+cudaError_t launch_round_start(cudaGraphConditionalHandle hs, cudaGraphConditionalHandle hl,
+                               const unsigned int* count, unsigned int threshold,
+                               const RoundStart& rs, cudaStream_t stream);
 
 // Population count of a bitset (for statistics) added into *count.
 // Several frames: count[f] += popcount of frame f's bitset.
