@@ -80,10 +80,8 @@ int g_eval(pifu_ctx* ctx, const DevNet& net, const PointSrc& src, int64_t cap,
            const RoundStart* rs) {
     const bool branch = !sur && prec != PIFU_PREC_BF16 && prec != PIFU_PREC_FP8 && m_dev &&
                         ctx->cap_stream3 && s != ctx->cap_stream3;
-    if (rs && !branch) {
-        CK(launch_accumulate(rs->evals, m_dev, rs->cap, rs->err, s));
-        CK(cudaMemsetAsync(rs->zero, 0, sizeof(unsigned int), s));
-    }
+    if (rs && !branch)
+        CK(launch_round_start(0, 0, false, const_cast<unsigned int*>(m_dev), 0u, *rs, s));
     if (sur) {
         // qcap_in > 0: the f_O queue already holds keys (the frame stream's
         // finest-level keys), f_S's fall-backs are appended after them
@@ -119,7 +117,9 @@ int g_eval(pifu_ctx* ctx, const DevNet& net, const PointSrc& src, int64_t cap,
         cudaGraphConditionalHandle hs, hl;
         CK(cudaGraphConditionalHandleCreate(&hs, cg, 0, 0));
         CK(cudaGraphConditionalHandleCreate(&hl, cg, 0, 0));
-        if (rs) CK(launch_round_start(hs, hl, m_dev, (unsigned)kTinyBatch, *rs, s));
+        if (rs)
+            CK(launch_round_start(hs, hl, true, const_cast<unsigned int*>(m_dev),
+                                  (unsigned)kTinyBatch, *rs, s));
         else CK(launch_branch(hs, hl, m_dev, (unsigned)kTinyBatch, s));
         cudaStream_t s3 = ctx->cap_stream3;
         for (int br = 0; br < 2; ++br) {
@@ -262,12 +262,14 @@ int g_enqueue_frame(pifu_ctx* ctx, const FrameKey& k, const Map& occ, const Map&
         // the level's set-up (candidate count and the list count's zeroing in
         // the same launch), then its first selection, whose last CTA decides
         // whether the loop runs
+        // (the frontier counts in d_count2: each round's start moves it to
+        // d_count, the size its passes read)
         CK(launch_classify(ctx->bin[prev], N, ctx->cand, ctx->tent, ctx->bin[cur], ctx->eval,
-                           ctx->conf[0], s, 1, 0, 0, &gs->cands[l], ctx->d_count));
+                           ctx->conf[0], s, 1, 0, 0, &gs->cands[l], ctx->d_count2));
         const LoopTail first{h, ctx->d_tail, (unsigned)kChunkTC, &gs->rounds[l], 0, k.max_rounds,
                              err};
-        CK(launch_dilate_select(ctx->cand, ctx->eval, nullptr, N, ctx->list, ctx->d_count, s, 1, 0,
-                                0, &first));
+        CK(launch_dilate_select(ctx->cand, ctx->eval, nullptr, N, ctx->list, ctx->d_count2, s, 1,
+                                0, 0, &first));
         cudaGraph_t body = nullptr;
         st = g_add_while(ctx, s, h, &body);
         if (st != PIFU_OK) return st;
@@ -290,18 +292,17 @@ int g_enqueue_frame(pifu_ctx* ctx, const FrameKey& k, const Map& occ, const Map&
             // the round's statistics and the zeroing of its conflict count
             // ride in the launch that picks the batch's branch; the expansion's
             // last CTA decides whether another round runs
-            const RoundStart rs{&gs->evals[l], (unsigned)kChunkTC, err, ctx->d_ccount};
+            const RoundStart rs{&gs->evals[l], (unsigned)kChunkTC, err, ctx->d_ccount,
+                                ctx->d_count2};
             st = g_eval(ctx, net, src, kChunkTC, ctx->d_count, occ, cal, epi, k.precision,
                         k.margin, &gs->rechecked[l], sb, k.use_surrogate && l < k.num_levels - 1,
                         k.sur_margin, &gs->fallback[l], 0, &rs);
-            if (st == PIFU_OK && cudaMemsetAsync(ctx->d_count, 0, sizeof(unsigned int), sb) != cudaSuccess)
-                st = PIFU_ERR_CUDA;
             const LoopTail next{h, ctx->d_tail + 1, (unsigned)kChunkTC, &gs->rounds[l], 1,
                                 k.max_rounds, err};
             if (st == PIFU_OK &&
                 launch_expand_conflicts(ctx->clist, ctx->d_ccount, (unsigned)kChunkTC, N, ctx->eval,
-                                        0, 0, ctx->list, ctx->d_count, (unsigned)kChunkTC, err, sb,
-                                        nullptr, nullptr, nullptr, nullptr, &next) != cudaSuccess)
+                                        0, 0, ctx->list, ctx->d_count2, (unsigned)kChunkTC, err,
+                                        sb, nullptr, nullptr, nullptr, nullptr, &next) != cudaSuccess)
                 st = PIFU_ERR_CUDA;
         }
         cudaGraph_t body_out = nullptr;
@@ -418,8 +419,10 @@ int g_build(pifu_ctx* ctx, const FrameKey& k, const Map& occ, const Map& col, co
     if (!ctx->cap_stream4) CK(cudaStreamCreateWithFlags(&ctx->cap_stream4, cudaStreamNonBlocking));
     if (!ctx->d_gstats) CK(dev_alloc(&ctx->d_gstats, 1));
     if (!ctx->d_tail) {
-        CK(dev_alloc(&ctx->d_tail, 2));
-        CK(cudaMemset(ctx->d_tail, 0, 2 * sizeof(unsigned int)));
+        // the loop tails' CTA counters [2], then the frontier count
+        CK(dev_alloc(&ctx->d_tail, 3));
+        CK(cudaMemset(ctx->d_tail, 0, 3 * sizeof(unsigned int)));
+        ctx->d_count2 = ctx->d_tail + 2;
     }
     {
         const int st = ensure_clist(ctx, kChunkTC);

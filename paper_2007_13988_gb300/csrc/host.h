@@ -505,6 +505,7 @@ struct pifu_ctx {
     GraphStats* d_gstats = nullptr;
     GraphStats* h_gstats = nullptr;       // pinned
     unsigned int* d_tail = nullptr;       // graph form: the loop tails' CTA counters [2]
+    unsigned int* d_count2 = nullptr;     // graph form: the frontier count (in d_tail's block)
     int64_t g_launches_fixed = 0;         // kernel launches outside the loops
     int64_t g_launches_body[8] = {};      // kernel launches per loop iteration
     // lockstep frame batches (pifu_frames)

@@ -571,18 +571,23 @@ __global__ void accumulate_kernel(unsigned long long* dst, const unsigned int* s
     if (v > cap) atomicOr(err, kErrCapacity);
 }
 
-// The start of a conflict round in the graph: accumulate_kernel's statistics,
-// *zero = 0, and branch_kernel's two conditions, in one launch.
+// The start of a conflict round in the graph: the round's size moved from
+// the frontier count to the batch count, accumulate_kernel's statistics,
+// *zero = 0, and (set) branch_kernel's two conditions, in one launch.
 __global__ void round_start_kernel(cudaGraphConditionalHandle hs, cudaGraphConditionalHandle hl,
-                                   const unsigned int* count, unsigned int threshold,
+                                   int set, unsigned int* count, unsigned int threshold,
                                    unsigned long long* evals, unsigned int cap, unsigned int* err,
-                                   unsigned int* zero) {
-    const unsigned int c = *count;
+                                   unsigned int* zero, unsigned int* next) {
+    const unsigned int c = *next;
+    *count = c;
+    *next = 0u;
     *evals += c;
     if (c > cap) atomicOr(err, kErrCapacity);
     *zero = 0u;
-    cudaGraphSetConditional(hs, (c > 0u && c <= threshold) ? 1u : 0u);
-    cudaGraphSetConditional(hl, c > threshold ? 1u : 0u);
+    if (set) {
+        cudaGraphSetConditional(hs, (c > 0u && c <= threshold) ? 1u : 0u);
+        cudaGraphSetConditional(hl, c > threshold ? 1u : 0u);
+    }
 }
 
 inline unsigned blocks_for(int64_t n) { return (unsigned)((n + 255) / 256); }
@@ -688,10 +693,10 @@ cudaError_t launch_accumulate(unsigned long long* dst, const unsigned int* src, 
 }
 
 cudaError_t launch_round_start(cudaGraphConditionalHandle hs, cudaGraphConditionalHandle hl,
-                               const unsigned int* count, unsigned int threshold,
+                               bool set, unsigned int* count, unsigned int threshold,
                                const RoundStart& rs, cudaStream_t stream) {
-    round_start_kernel<<<1, 1, 0, stream>>>(hs, hl, count, threshold, rs.evals, rs.cap, rs.err,
-                                            rs.zero);
+    round_start_kernel<<<1, 1, 0, stream>>>(hs, hl, set ? 1 : 0, count, threshold, rs.evals,
+                                            rs.cap, rs.err, rs.zero, rs.next);
     return cudaGetLastError();
 }
 

@@ -554,16 +554,20 @@ cudaError_t launch_branch(cudaGraphConditionalHandle hs, cudaGraphConditionalHan
 // *dst += *src; capacity error bit if *src > cap.
 cudaError_t launch_accumulate(unsigned long long* dst, const unsigned int* src, unsigned int cap,
                               unsigned int* err, cudaStream_t stream);
-// A conflict round's start in one launch: *evals += *count (capacity error
-// bit if above cap), *zero = 0, then launch_branch's two conditions.
+// A conflict round's start in one launch: the round's size c = *next (the
+// frontier count the previous selection or expansion appended to) becomes
+// *count, the batch size its passes read, and *next = 0 for the next
+// expansion; *evals += c (capacity error bit if above cap), *zero = 0, and,
+// with handles, launch_branch's two conditions on c.
 struct RoundStart {
     unsigned long long* evals;
     unsigned int cap;
     unsigned int* err;
     unsigned int* zero;
+    unsigned int* next;
 };
 cudaError_t launch_round_start(cudaGraphConditionalHandle hs, cudaGraphConditionalHandle hl,
-                               const unsigned int* count, unsigned int threshold,
+                               bool set, unsigned int* count, unsigned int threshold,
                                const RoundStart& rs, cudaStream_t stream);
 
 // Population count of a bitset (for statistics) added into *count.
