@@ -302,13 +302,11 @@ int pifu_localize(pifu_ctx* ctx, const pifu_fmap* occ_map, const float calib[12]
                           4.0 * nc + 4.0 * (double)(N + 1) * (N + 1) * (N + 1) + 4.0 * wbytes);
             CK(launch_popcount(ctx->eval, words_of(N), ctx->d_pop + l, s));
         } else {
+            // the level's set-up; the candidates are counted in the same launch
             ev = ctx->prof.begin(s);
             CK(launch_classify(ctx->bin[prev], N, ctx->cand, ctx->tent, ctx->bin[cur], ctx->eval,
-                               ctx->conf[0], s));
+                               ctx->conf[0], s, 1, 0, 0, ctx->d_pop + l, nullptr));
             ctx->prof.end(PIFU_K_LEVEL, ev, s, 0.0, 4.0 * words_of(N / 2) + 5.0 * wbytes);
-            ev = ctx->prof.begin(s);
-            CK(launch_popcount(ctx->cand, words_of(N), ctx->d_pop + l, s));
-            ctx->prof.end(PIFU_K_LEVEL, ev, s, 0.0, wbytes);
             CK(cudaMemsetAsync(ctx->d_count, 0, sizeof(unsigned int), s));
             ev = ctx->prof.begin(s);
             if (subdiv == PIFU_SUBDIV_BINARIZED)   // the candidates alone
