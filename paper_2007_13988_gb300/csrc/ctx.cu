@@ -409,6 +409,10 @@ int build_tc(pifu_ctx* ctx, const HostNet& hn, DevNet& net) {
         T.nk1 = Ly.K1 / 64;
         T.nk2 = has_x ? k2pad / 64 : 0;
         T.Kw = Ly.K1 + (has_x ? k2pad : 0);
+        // the x part ends at K1 + d_in: the map reads no further, and the
+        // last K-block's MMA steps past d_in (zeros on both sides) are skipped
+        T.Kmap = has_x ? Ly.K1 + net.d_in : T.Kw;
+        T.klast = has_x ? (net.d_in - 64 * (T.nk2 - 1) + 15) / 16 : 4;
         // single-CTA tiles by default (pifu_autotune / pifu_set_tiles may
         // choose the CTA-pair form)
         T.BN = Ly.n_out % 256 == 0 ? 256 : (Ly.n_out % 128 == 0 ? 128 : 64);
@@ -425,8 +429,8 @@ int build_tc(pifu_ctx* ctx, const HostNet& hn, DevNet& net) {
         }
         CK(dev_alloc(&T.W, (int64_t)wb.size()));
         CK(cudaMemcpy(T.W, wb.data(), wb.size() * sizeof(__nv_bfloat16), cudaMemcpyHostToDevice));
-        if (!tc_encode_2d_bf16(&T.tmW, T.W, (uint64_t)T.Kw, (uint64_t)Ly.n_out, (uint64_t)T.Kw * 2,
-                               64, (uint32_t)(T.pair ? T.BN / 2 : T.BN)))
+        if (!tc_encode_2d_bf16(&T.tmW, T.W, (uint64_t)T.Kmap, (uint64_t)Ly.n_out,
+                               (uint64_t)T.Kw * 2, 64, (uint32_t)(T.pair ? T.BN / 2 : T.BN)))
             return PIFU_ERR_CUDA;
     }
     net.tc_ok = true;
@@ -559,13 +563,15 @@ int build_fp8(pifu_ctx* ctx, DevNet& net, int F, const std::vector<float>& s_h) 
         Q.BN = T.BN;
         Q.out_scale = l + 1 < F ? 1.f / s_h[(size_t)l] : 1.f;
         Q.nk2 = T.nk2;
+        Q.klast = T.klast;
         if (l == 0) {
             // the BF16 operands of the tensor-core form, its own tile map
             Q.bf16_in = true;
             Q.nk1 = T.nk1;
             Q.Kw = T.Kw;
+            Q.Kmap = T.Kmap;
             Q.Wmap = T.W;
-            if (!tc_encode_2d_bf16(&Q.tmW, T.W, (uint64_t)T.Kw, (uint64_t)Ly.n_out,
+            if (!tc_encode_2d_bf16(&Q.tmW, T.W, (uint64_t)Q.Kmap, (uint64_t)Ly.n_out,
                                    (uint64_t)T.Kw * 2, 64, (uint32_t)Q.BN))
                 return PIFU_ERR_CUDA;
             continue;
@@ -573,6 +579,7 @@ int build_fp8(pifu_ctx* ctx, DevNet& net, int F, const std::vector<float>& s_h) 
         const bool has_x = Ly.K2 > 0;
         Q.nk1 = Ly.K1 / 128;
         Q.Kw = Ly.K1 + Q.nk2 * 128;   // bytes
+        Q.Kmap = has_x ? Ly.K1 + 2 * net.d_in : Q.Kw;
         const float s_a = s_h[(size_t)l - 1];
         std::vector<float> wf((size_t)Ly.n_out * Ly.ldw);
         CK(cudaMemcpy(wf.data(), Ly.W, wf.size() * 4, cudaMemcpyDeviceToHost));
@@ -597,7 +604,7 @@ int build_fp8(pifu_ctx* ctx, DevNet& net, int F, const std::vector<float>& s_h) 
         CK(cudaMemcpy(Q.W, w8.data(), w8.size(), cudaMemcpyHostToDevice));
         CK(cudaMemcpy(Q.colscale, cs.data(), cs.size() * 4, cudaMemcpyHostToDevice));
         Q.Wmap = Q.W;
-        if (!tc_encode_2d_u8(&Q.tmW, Q.W, (uint64_t)Q.Kw, (uint64_t)Ly.n_out, (uint64_t)Q.Kw, 128,
+        if (!tc_encode_2d_u8(&Q.tmW, Q.W, (uint64_t)Q.Kmap, (uint64_t)Ly.n_out, (uint64_t)Q.Kw, 128,
                              (uint32_t)Q.BN))
             return PIFU_ERR_CUDA;
     }

@@ -267,10 +267,14 @@ __global__ void __launch_bounds__(kCThreads, 1) tc_chain_kernel(const __grid_con
                     tc_fence_after();
                     const uint32_t a0 = smem_u32(sA + s * kABytes);
                     const uint32_t b0 = smem_u32(sB + s * kBBytes);
+                    // the last K-block stops after its last real column
+                    const int ksteps = kb == nk - 1 ? Ly.klast : 4;
 #pragma unroll
-                    for (int k = 0; k < 4; ++k)
+                    for (int k = 0; k < 4; ++k) {
+                        if (k >= ksteps) break;
                         mma_bf16(d, desc_k_sw128(a0 + k * 32), desc_k_sw128(b0 + k * 32), idesc,
                                  (kb | k) != 0 ? 1u : 0u);
+                    }
                     mma_commit(&empty[s]);
                 }
                 mma_commit(&accf[b]);   // also after an error, so the epilogue is released

@@ -76,6 +76,7 @@ int run_mlp_tc(pifu_ctx* ctx, const DevNet& net, const PointSrc& src_in, int64_t
                 C.tmW = T.tmW;
                 C.nk1 = T.nk1;
                 C.nk2 = T.nk2;
+                C.klast = T.klast;
                 C.N = Ly.n_out;
                 C.BN = T.BN;
                 C.bias = Ly.b;
@@ -115,6 +116,7 @@ int run_mlp_tc(pifu_ctx* ctx, const DevNet& net, const PointSrc& src_in, int64_t
             a.tmO = T.tmO_ok ? &T.tmO : nullptr;
             a.nk1 = T.nk1;
             a.nk2 = T.nk2;
+            a.klast = T.klast;
             a.M = (int)mc;
             a.N = Ly.n_out;
             a.BN = T.BN;
@@ -137,6 +139,7 @@ int run_mlp_tc(pifu_ctx* ctx, const DevNet& net, const PointSrc& src_in, int64_t
                 a.tmW = &Q.tmW;
                 a.nk1 = Q.nk1;
                 a.nk2 = Q.nk2;
+                a.klast = Q.klast;
                 a.BN = Q.BN;
                 a.pair = 0;
                 a.mode = l == 0 ? TC_BF16_E4M3 : (l + 1 < F ? TC_MIX_E4M3 : TC_MIX_BF16);

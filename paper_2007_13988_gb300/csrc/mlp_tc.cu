@@ -83,6 +83,11 @@ static_assert(tc_stages(256) == 4 && tc_stages(128) == 6 && tc_stages(64) == 8, 
 static_assert(2 * tc_stages(64) * 8 + 4 * 8 + 4 <= 256, "barriers fit in front of the bias");
 static_assert(tc_smem_bytes(256) <= 227 * 1024, "shared memory of the widest tile");
 
+// Four consecutive floats of shared memory (16-byte aligned) in one load.
+__device__ __forceinline__ float4 lds4(const float* p) {
+    return *reinterpret_cast<const float4*>(p);
+}
+
 // Four values rounded to E4M3 (saturating), first value in the lowest byte.
 __device__ __forceinline__ uint32_t pack_e4m3x4(float a, float b, float c, float d) {
     const uint32_t lo = __nv_cvt_float2_to_fp8x2(make_float2(a, b), __NV_SATFINITE, __NV_E4M3);
@@ -94,7 +99,7 @@ template <int BN, bool FUSE, int MODE>
 __global__ void __launch_bounds__(kThreads, 1) tc_linear_kernel(
     const __grid_constant__ CUtensorMap tmA1, const __grid_constant__ CUtensorMap tmA2,
     const __grid_constant__ CUtensorMap tmW, const __grid_constant__ CUtensorMap tmO, int use_tmo,
-    int nk1, int nk2, int M, int N, const float* __restrict__ bias, float slope,
+    int nk1, int nk2, int klast, int M, int N, const float* __restrict__ bias, float slope,
     void* __restrict__ out_raw, int ldo, unsigned int* __restrict__ err,
     const unsigned int* __restrict__ m_dev, FuseLast fl, const float* __restrict__ colscale,
     float out_scale) {
@@ -217,10 +222,13 @@ __global__ void __launch_bounds__(kThreads, 1) tc_linear_kernel(
                     tc_fence_after();
                     const uint32_t a0 = smem_u32(sA + s * A_BYTES);
                     const uint32_t b0 = smem_u32(sB + s * B_BYTES);
-                    // 4 MMAs of 32 bytes of K each (16 BF16 or 32 E4M3 values)
+                    // 4 MMAs of 32 bytes of K each (16 BF16 or 32 E4M3 values);
+                    // the last K-block stops after its last real column
                     const bool f8 = MIX && kb < nk1;
+                    const int ksteps = kb == nk - 1 ? klast : 4;
 #pragma unroll
                     for (int k = 0; k < 4; ++k) {
+                        if (k >= ksteps) break;
                         if (f8)
                             mma_e4m3(d, desc_k_sw128(a0 + k * 32), desc_k_sw128(b0 + k * 32),
                                      idesc8, (kb | k) != 0 ? 1u : 0u);
@@ -271,15 +279,28 @@ __global__ void __launch_bounds__(kThreads, 1) tc_linear_kernel(
                 constexpr int NC = HALF >= 64 ? 64 : HALF;
                 if (FUSE) {
                     // h rounded to BF16 (as the unfused path stores it), dotted
-                    // with the last layer's rows
+                    // with the last layer's rows; shared-memory operands in
+                    // 16-byte loads (the same values, in the same order)
 #pragma unroll
-                    for (int cc = 0; cc < NC; ++cc) {
-                        float a = __uint_as_float(r[cc]) + bb[c0 + cc];
-                        a = a >= 0.f ? a : slope * a;
-                        a = __bfloat162float(__float2bfloat16_rn(a));
+                    for (int c4 = 0; c4 < NC; c4 += 4) {
+                        const float4 b4 = lds4(bb + c0 + c4);
+                        const float bv[4] = {b4.x, b4.y, b4.z, b4.w};
+                        float h[4];
+#pragma unroll
+                        for (int t4 = 0; t4 < 4; ++t4) {
+                            float a = __uint_as_float(r[c4 + t4]) + bv[t4];
+                            a = a >= 0.f ? a : slope * a;
+                            h[t4] = __bfloat162float(__float2bfloat16_rn(a));
+                        }
 #pragma unroll
                         for (int jo = 0; jo < 4; ++jo)
-                            if (jo < fl.n_out) part[jo] = fmaf(a, sW5[jo * BN + c0 + cc], part[jo]);
+                            if (jo < fl.n_out) {
+                                const float4 w4 = lds4(sW5 + jo * BN + c0 + c4);
+                                part[jo] = fmaf(h[0], w4.x, part[jo]);
+                                part[jo] = fmaf(h[1], w4.y, part[jo]);
+                                part[jo] = fmaf(h[2], w4.z, part[jo]);
+                                part[jo] = fmaf(h[3], w4.w, part[jo]);
+                            }
                     }
                 } else if (OUT8) {
                     // 64 E4M3 values = 64 bytes of the row: one staged pass
@@ -289,11 +310,15 @@ __global__ void __launch_bounds__(kThreads, 1) tc_linear_kernel(
                         uint32_t pk[4];
 #pragma unroll
                         for (int jj = 0; jj < 4; ++jj) {
+                            const int cq = v * 16 + 4 * jj;
+                            const float4 b4 = lds4(bb + c0 + cq);
+                            const float4 s4 = lds4(sc + c0 + cq);
+                            const float bv[4] = {b4.x, b4.y, b4.z, b4.w};
+                            const float sv[4] = {s4.x, s4.y, s4.z, s4.w};
                             float e[4];
 #pragma unroll
                             for (int t4 = 0; t4 < 4; ++t4) {
-                                const int cc = v * 16 + 4 * jj + t4;
-                                float a = fmaf(__uint_as_float(r[cc]), sc[c0 + cc], bb[c0 + cc]);
+                                float a = fmaf(__uint_as_float(r[cq + t4]), sv[t4], bv[t4]);
                                 a = a >= 0.f ? a : slope * a;
                                 e[t4] = a * out_scale;
                             }
@@ -316,18 +341,31 @@ __global__ void __launch_bounds__(kThreads, 1) tc_linear_kernel(
                         uint4 pk4[4];
 #pragma unroll
                         for (int v = 0; v < 4; ++v) {
+                            // the 8 columns' bias (and scales) in two 16-byte loads
+                            const int c8 = hb * 32 + v * 8;
+                            const float4 b4a = lds4(bb + c0 + c8);
+                            const float4 b4b = lds4(bb + c0 + c8 + 4);
+                            const float bv[8] = {b4a.x, b4a.y, b4a.z, b4a.w,
+                                                 b4b.x, b4b.y, b4b.z, b4b.w};
+                            float sv[8];
+                            if (MIX) {
+                                const float4 s4a = lds4(sc + c0 + c8);
+                                const float4 s4b = lds4(sc + c0 + c8 + 4);
+                                sv[0] = s4a.x; sv[1] = s4a.y; sv[2] = s4a.z; sv[3] = s4a.w;
+                                sv[4] = s4b.x; sv[5] = s4b.y; sv[6] = s4b.z; sv[7] = s4b.w;
+                            }
                             uint32_t pk[4];
 #pragma unroll
                             for (int jj = 0; jj < 4; ++jj) {
-                                const int cc = hb * 32 + v * 8 + 2 * jj;
+                                const int cc = c8 + 2 * jj;
                                 float a, c;
                                 if (!MIX) {
-                                    a = __uint_as_float(r[cc]) + bb[c0 + cc];
-                                    c = __uint_as_float(r[cc + 1]) + bb[c0 + cc + 1];
+                                    a = __uint_as_float(r[cc]) + bv[2 * jj];
+                                    c = __uint_as_float(r[cc + 1]) + bv[2 * jj + 1];
                                 } else {
-                                    a = fmaf(__uint_as_float(r[cc]), sc[c0 + cc], bb[c0 + cc]);
-                                    c = fmaf(__uint_as_float(r[cc + 1]), sc[c0 + cc + 1],
-                                             bb[c0 + cc + 1]);
+                                    a = fmaf(__uint_as_float(r[cc]), sv[2 * jj], bv[2 * jj]);
+                                    c = fmaf(__uint_as_float(r[cc + 1]), sv[2 * jj + 1],
+                                             bv[2 * jj + 1]);
                                 }
                                 a = a >= 0.f ? a : slope * a;
                                 c = c >= 0.f ? c : slope * c;
@@ -442,7 +480,7 @@ template <int PS, int SB>
 __global__ void __launch_bounds__(kThreads, 1) tc_pair_kernel(
     const __grid_constant__ CUtensorMap tmA1, const __grid_constant__ CUtensorMap tmA2,
     const __grid_constant__ CUtensorMap tmW, const __grid_constant__ CUtensorMap tmO, int use_tmo,
-    int nk1, int nk2, int M, int N, const float* __restrict__ bias, float slope,
+    int nk1, int nk2, int klast, int M, int N, const float* __restrict__ bias, float slope,
     __nv_bfloat16* __restrict__ out, int ldo, unsigned int* __restrict__ err,
     const unsigned int* __restrict__ m_dev) {
     constexpr int BN = kPairBN;
@@ -557,10 +595,13 @@ __global__ void __launch_bounds__(kThreads, 1) tc_pair_kernel(
                     tc_fence_after();
                     const uint32_t a0 = smem_u32(sA + s * A_BYTES);
                     const uint32_t b0 = smem_u32(sB + s * B_BYTES);
+                    const int ksteps = kb == nk - 1 ? klast : 4;
 #pragma unroll
-                    for (int k = 0; k < 4; ++k)
+                    for (int k = 0; k < 4; ++k) {
+                        if (k >= ksteps) break;
                         mma_bf16_pair(d, desc_k_sw128(a0 + k * 32), desc_k_sw128(b0 + k * 32),
                                       idesc, (kb | k) != 0 ? 1u : 0u);
+                    }
                     mma_commit_pair(&empty[s], (uint16_t)3);
                 }
                 mma_commit_pair(&accf[b], (uint16_t)3);   // also after an error
@@ -706,32 +747,33 @@ cudaError_t launch_bn(const TcLayerArgs& a, cudaStream_t s) {
     cfg.attrs = at;
     cfg.numAttrs = 1;
     const float* noscale = nullptr;
+    const int kl = a.klast >= 1 && a.klast <= 4 ? a.klast : 4;
     // the TMA-store epilogue needs the output map (BF16 output, not fused)
     const int use_tmo = a.tmO ? 1 : 0;
     const CUtensorMap& tmO = a.tmO ? *a.tmO : *a.tmW;
     if (a.fuse) {
         if (a.N != BN || a.fuse->n_out < 1 || a.fuse->n_out > 4) return cudaErrorInvalidValue;
         return cudaLaunchKernelEx(&cfg, tc_linear_kernel<BN, true, TC_BF16>, *a.tmA1, *a.tmA2,
-                                  *a.tmW, tmO, 0, a.nk1, a.nk2, a.M, a.N, a.bias, a.slope, a.out,
+                                  *a.tmW, tmO, 0, a.nk1, a.nk2, kl, a.M, a.N, a.bias, a.slope, a.out,
                                   a.ldo, a.err, a.m_dev, *a.fuse, noscale, 1.f);
     }
     if (a.mode == TC_BF16_E4M3)
         return cudaLaunchKernelEx(&cfg, tc_linear_kernel<BN, false, TC_BF16_E4M3>, *a.tmA1,
-                                  *a.tmA2, *a.tmW, tmO, 0, a.nk1, a.nk2, a.M, a.N, a.bias,
+                                  *a.tmA2, *a.tmW, tmO, 0, a.nk1, a.nk2, kl, a.M, a.N, a.bias,
                                   a.slope, a.out, a.ldo, a.err, a.m_dev, FuseLast{}, noscale,
                                   a.out_scale);
     if (a.mode == TC_MIX_E4M3)
         return cudaLaunchKernelEx(&cfg, tc_linear_kernel<BN, false, TC_MIX_E4M3>, *a.tmA1,
-                                  *a.tmA2, *a.tmW, tmO, 0, a.nk1, a.nk2, a.M, a.N, a.bias,
+                                  *a.tmA2, *a.tmW, tmO, 0, a.nk1, a.nk2, kl, a.M, a.N, a.bias,
                                   a.slope, a.out, a.ldo, a.err, a.m_dev, FuseLast{}, a.colscale,
                                   a.out_scale);
     if (a.mode == TC_MIX_BF16)
         return cudaLaunchKernelEx(&cfg, tc_linear_kernel<BN, false, TC_MIX_BF16>, *a.tmA1,
-                                  *a.tmA2, *a.tmW, tmO, use_tmo, a.nk1, a.nk2, a.M, a.N, a.bias,
+                                  *a.tmA2, *a.tmW, tmO, use_tmo, a.nk1, a.nk2, kl, a.M, a.N, a.bias,
                                   a.slope, a.out, a.ldo, a.err, a.m_dev, FuseLast{}, a.colscale,
                                   1.f);
     return cudaLaunchKernelEx(&cfg, tc_linear_kernel<BN, false, TC_BF16>, *a.tmA1, *a.tmA2,
-                              *a.tmW, tmO, use_tmo, a.nk1, a.nk2, a.M, a.N, a.bias, a.slope,
+                              *a.tmW, tmO, use_tmo, a.nk1, a.nk2, kl, a.M, a.N, a.bias, a.slope,
                               a.out, a.ldo, a.err, a.m_dev, FuseLast{}, noscale, 1.f);
 }
 
@@ -800,8 +842,9 @@ cudaError_t launch_pair_cfg(const TcLayerArgs& a, cudaStream_t s) {
     cfg.numAttrs = 2;
     const int use_tmo = a.tmO ? 1 : 0;
     const CUtensorMap& tmO = a.tmO ? *a.tmO : *a.tmW;
+    const int kl = a.klast >= 1 && a.klast <= 4 ? a.klast : 4;
     return cudaLaunchKernelEx(&cfg, tc_pair_kernel<PS, SB>, *a.tmA1, *a.tmA2, *a.tmW, tmO, use_tmo,
-                              a.nk1, a.nk2, a.M, a.N, a.bias, a.slope,
+                              a.nk1, a.nk2, kl, a.M, a.N, a.bias, a.slope,
                               static_cast<__nv_bfloat16*>(a.out), a.ldo, a.err, a.m_dev);
 }
 

@@ -221,6 +221,9 @@ struct TcLayerArgs {
     const CUtensorMap* tmO;       // optional: BF16 output [rows][N], box 32 x 32, 64-byte
                                   // swizzle (the epilogue then stores with TMA)
     int nk1, nk2, M, N, BN;       // nk1, nk2: 128-byte K-blocks of the two A segments
+    int klast;                    // MMA steps (16 BF16 values each) of the last K-block
+                                  // that hold real columns, 1..4 (0: all 4); the rest of
+                                  // that block is zero padding in both operands
     int pair;                     // 1: CTA-pair form (BN = 256, TC_BF16, no fuse); tmW's
                                   // box is then 128 rows (each CTA loads half of a tile's W)
     const float* bias;
@@ -324,6 +327,7 @@ struct ChainLayer {
     CUtensorMap tmA2;       // the input rows x [rows][ldx]
     CUtensorMap tmW;        // [N][Kw] BF16, box BN x 64
     int nk1, nk2, N, BN;    // 128-byte K-blocks of the two segments; BN | N, BN <= 256
+    int klast;              // as in TcLayerArgs
     const float* bias;      // [N]
     __nv_bfloat16* out;     // [rows][ldo] (unused by a layer carrying the fused last layer)
     int ldo;
