@@ -314,16 +314,20 @@ class Frame:
         # scales of the FP8 form from the frame's own dense coarsest grid
         pifu.pifu_calibrate_fp8(self.ctx, self.occ, w.calib, w.n0, stream=stream)
 
-    def run(self, prec, form="graph", margin=0.02, sur_margin=None, levels=None, final_level=0):
+    def run(self, prec, form="graph", margin=0.02, sur_margin=None, levels=None, final_level=0,
+            wait=True):
+        """One frame.  Graph form: pifu_frame, or with wait=False
+        pifu_frame_async (the host does not wait; pifu_frame_wait later)."""
         w, p = self.w, self.pifu
         L = w.num_levels if levels is None else levels
         sur = {} if sur_margin is None else {"use_surrogate": True, "surrogate_margin": sur_margin}
         if form == "graph" and prec != 0:
             # one CUDA graph per frame (captured on the first call)
-            return p.pifu_frame(self.ctx, self.occ, self.col, w.calib, w.n0, L,
-                                w.render, w.render, self.depth, self.rgb, self.mask,
-                                precision=prec, margin=margin, stream=self.stream,
-                                final_level=final_level, **sur)
+            call = p.pifu_frame if wait else p.pifu_frame_async
+            return call(self.ctx, self.occ, self.col, w.calib, w.n0, L,
+                        w.render, w.render, self.depth, self.rgb, self.mask,
+                        precision=prec, margin=margin, stream=self.stream,
+                        final_level=final_level, **sur)
         vol = p.pifu_localize(self.ctx, self.occ, w.calib, w.n0, L, precision=prec,
                               margin=margin, stream=self.stream, **sur)
         p.pifu_render(self.ctx, w.render, w.render, self.occ, self.col, w.calib, self.depth,
@@ -336,7 +340,7 @@ class Frame:
 
 
 def time_form(fr, prec, steps, warmup, world, clocks=None, form="graph", sur_margin=None,
-              levels=None, final_level=0):
+              levels=None, final_level=0, asynchronous=True):
     """Device-timed frames of one precision form; returns a dict."""
     import torch
     vol = None
@@ -349,12 +353,20 @@ def time_form(fr, prec, steps, warmup, world, clocks=None, form="graph", sur_mar
         torch.distributed.barrier()
     torch.cuda.synchronize()
     fr.pifu.pifu_profile(fr.ctx, True)
+    # graph form: the frames go out through pifu_frame_async, so the host
+    # never waits between steps and each step's events bracket its device
+    # work only (with pifu_frame the host's wait and relaunch would sit
+    # between the events); pifu_frame_wait reports their errors at the end
+    graph = form == "graph" and prec != 0 and asynchronous
     for i in range(steps):
         with torch.cuda.stream(fr.stream):
             fr.flush.zero_()
         ev[i][0].record(fr.stream)
-        vol = fr.run(prec, form, sur_margin=sur_margin, levels=levels, final_level=final_level)
+        vol = fr.run(prec, form, sur_margin=sur_margin, levels=levels, final_level=final_level,
+                     wait=not graph)
         ev[i][1].record(fr.stream)
+    if graph:
+        vol = fr.pifu.pifu_frame_wait(fr.ctx, fr.stream)
     torch.cuda.synchronize()
     prof = fr.pifu.pifu_profile_read(fr.ctx)
     fr.pifu.pifu_profile(fr.ctx, False)
@@ -796,8 +808,11 @@ def run_ours(args, rank, world, local_rank):
     # ---- per-kernel timing: a graph has no per-launch events, so the kernel
     # classes of the same frame are timed on its host-driven form ------------
     prof_run = head
+    sync_call = None
     if form == "graph":
         prof_run = time_form(fr, prec, max(3, min(args.steps, 10)), 1, world, form="host")
+        # the same graph through pifu_frame, which waits for each frame
+        sync_call = time_form(fr, prec, args.steps, 2, world, form="graph", asynchronous=False)
     # ---- the same form with the learned surrogate at the coarse levels -------
     sur = None
     if sur_margin is not None:
@@ -920,7 +935,10 @@ def run_ours(args, rank, world, local_rank):
         # frame i runs, step i+1's maps come in from pinned host memory and
         # step i-1's outputs go out, through device staging buffers (one
         # device-to-device copy each way on the frame's stream, so the
-        # frame's own buffers and graph stay the same).
+        # frame's own buffers and graph stay the same).  Graph frames go out
+        # through pifu_frame_async: the host enqueues step i+1 while frame i
+        # runs, and pifu_frame_wait at the end reports the frames' errors.
+        graph = form == "graph" and prec != 0
         cs = torch.cuda.Stream(device=dev)
         s_occ, s_col = torch.empty_like(fr.occ), torch.empty_like(fr.col)
         s_depth, s_rgb, s_mask = (torch.empty_like(fr.depth), torch.empty_like(fr.rgb),
@@ -952,7 +970,7 @@ def run_ours(args, rank, world, local_rank):
                     h_rgb.copy_(s_rgb, non_blocking=True)
                     h_mask.copy_(s_mask, non_blocking=True)
                     ev_d2h.record(cs)
-            fr.run(prec, form)
+            fr.run(prec, form, wait=not graph)
             with torch.cuda.stream(stream):
                 if i > 0:
                     stream.wait_event(ev_d2h)               # staging free again
@@ -966,6 +984,8 @@ def run_ours(args, rank, world, local_rank):
             h_depth.copy_(s_depth, non_blocking=True)
             h_rgb.copy_(s_rgb, non_blocking=True)
             h_mask.copy_(s_mask, non_blocking=True)
+        if graph:
+            fr.pifu.pifu_frame_wait(fr.ctx, stream)
         cs.synchronize()
         return time.perf_counter() - t0
 
@@ -1062,18 +1082,26 @@ def run_ours(args, rank, world, local_rank):
                     "d2h_bytes_per_step": d2h, "steps": e2e_steps,
                     "form": "pipelined: step i+1's maps in and step i-1's outputs out on a "
                             "second stream during frame i (pinned host memory, device "
-                            "staging), every step's copies inside the timed loop",
+                            "staging), every step's copies inside the timed loop; frames "
+                            "through pifu_frame_async, errors read by pifu_frame_wait inside "
+                            "the timed region",
                     "serial": {"value": e2e_serial_value,
                                "form": "copy in, frame, copy out, wait: one step at a time"}},
             "gpu_launches": launches, "roofline": roofline, "kernels": kernels,
             "bookkeeping_roofline": book,
             "step_ms": {"min": min(head["step_ms"]), "median": statistics.median(head["step_ms"]),
                         "max": max(head["step_ms"])}}
-    line["config"]["form"] = ("one CUDA graph per frame (pifu_frame)" if form == "graph"
+    line["config"]["form"] = ("one CUDA graph per frame, enqueued by pifu_frame_async (the host "
+                              "does not wait between frames; pifu_frame_wait after the timed "
+                              "steps)" if form == "graph"
                               else "host-driven (pifu_localize + pifu_render)")
     line["config"]["layer_schedule"] = args.schedule
     if form == "graph":
         line["host_driven"] = {"value": prof_run["value"], "ms_per_step": prof_run["ms_per_step"]}
+        line["sync_call"] = {"value": sync_call["value"], "ms_per_step": sync_call["ms_per_step"],
+                             "form": "the same graph through pifu_frame, which waits for each "
+                                     "frame: the events then also hold the host's wait and "
+                                     "relaunch"}
     if prec in (2, 3):
         line["config"]["margin"] = 0.02
         line["config"]["rechecked_per_frame"] = head["rechecked"]

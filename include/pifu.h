@@ -260,6 +260,36 @@ int pifu_frame(pifu_ctx* ctx, const pifu_fmap* occ_map, const pifu_fmap* col_map
                void* stream, float* depth_dev, float* rgb_dev, uint8_t* mask_dev,
                pifu_volume* out);
 
+/* pifu_frame without the host waiting on it (Sec. 3.2's frame, one graph
+ * launch; Sec. 4 keeps frames flowing through its pipeline, and this lets a
+ * caller enqueue frame i+1 -- and the copies around it -- while frame i
+ * runs).  Arguments, the graph, its capture rule and the host-side checks
+ * are pifu_frame's; `out` is read by pifu_frame_wait instead.
+ * The call returns once the frame's graph is enqueued on `stream`: it does
+ * not synchronise the stream and reads no counter.  (The first call with a
+ * new argument set still captures the graph; with frames in flight it then
+ * waits for them first.)  The frame's device-side errors (a capacity, the
+ * round cap, a bounded wait that gave up) are latched on the device and
+ * reported by pifu_frame_wait; frames enqueued after a failing one have
+ * undefined outputs.  The frames of one context share its workspaces, so
+ * they must all go to one stream (stream order serialises them), and no
+ * other call may use the context until pifu_frame_wait (pifu_frame returns
+ * PIFU_ERR_STATE meanwhile).  Returns PIFU_OK or a host-detected error, in
+ * which case nothing was enqueued. */
+int pifu_frame_async(pifu_ctx* ctx, const pifu_fmap* occ_map, const pifu_fmap* col_map,
+                     const float calib[12], const pifu_levels* levels, const pifu_camera* cam,
+                     void* stream, float* depth_dev, float* rgb_dev, uint8_t* mask_dev);
+
+/* Waits for the frames pifu_frame_async enqueued on `stream` since the last
+ * wait.  If any of them latched a device-side error, returns the code
+ * pifu_frame gives for the union of their error bits (PIFU_ERR_CAPACITY
+ * before PIFU_ERR_NOT_CONVERGED before PIFU_ERR_TIMEOUT) and clears them (the
+ * device counters are reset, as after a failed pifu_frame); otherwise PIFU_OK.
+ * *out (may be NULL) receives the last frame's volume view and counters, as
+ * from pifu_frame, and that volume is then available to pifu_render and
+ * pifu_sync_stats.  PIFU_ERR_STATE when no frame is pending. */
+int pifu_frame_wait(pifu_ctx* ctx, void* stream, pifu_volume* out);
+
 /* ---- Lockstep batch of frames (not in the paper) ------------------------------
  * Localization + render of B independent frames (1 <= B <= 64) that advance
  * together.  Every level's set-up, dilation and compaction runs over all B

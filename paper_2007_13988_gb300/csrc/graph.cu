@@ -472,15 +472,14 @@ int g_build(pifu_ctx* ctx, const FrameKey& k, const Map& occ, const Map& col, co
 }
 
 
-}  // namespace pifu_host
-
-using namespace pifu_host;
-
-extern "C" {
-
-int pifu_frame(pifu_ctx* ctx, const pifu_fmap* occ_map, const pifu_fmap* col_map,
-               const float calib[12], const pifu_levels* lv, const pifu_camera* cam, void* stream,
-               float* depth_dev, float* rgb_dev, uint8_t* mask_dev, pifu_volume* out) {
+// The validation, the graph (captured when the argument set is new) and its
+// launch on `stream` of pifu_frame and pifu_frame_async; *kout: the frame's
+// key.  Nothing is enqueued when an argument or a host-known capacity is
+// refused.
+int frame_enqueue(pifu_ctx* ctx, const pifu_fmap* occ_map, const pifu_fmap* col_map,
+                  const float calib[12], const pifu_levels* lv, const pifu_camera* cam,
+                  void* stream, float* depth_dev, float* rgb_dev, uint8_t* mask_dev,
+                  FrameKey* kout) {
     if (!ctx || !calib || !lv || !cam || !map_ok(occ_map) || (col_map && !map_ok(col_map)))
         return PIFU_ERR_ARG;
     if (!is_pow2(lv->n0) || lv->n0 < 2 || lv->num_levels < 1 || lv->num_levels > kMaxLevels)
@@ -554,19 +553,30 @@ int pifu_frame(pifu_ctx* ctx, const pifu_fmap* occ_map, const pifu_fmap* col_map
         if (st != PIFU_OK) return st;
     }
     if (!ctx->g_valid || std::memcmp(&k, &ctx->gkey, sizeof(k)) != 0) {
+        // frames in flight use the workspaces and the graph being replaced
+        if (ctx->async_frames > 0) CK(cudaStreamSynchronize(s));
         st = g_build(ctx, k, to_map(occ_map), to_map(col_map), to_calib(calib));
         if (st != PIFU_OK) return st;
     }
     ctx->have_volume = false;
     CK(cudaGraphLaunch(ctx->gexec, s));
-    CK(cudaStreamSynchronize(s));
+    *kout = k;
+    return PIFU_OK;
+}
+
+// The volume and counters of the last frame launched with key k (its
+// counters in ctx->h_gstats, the graph's last copy), after the stream has
+// been synchronised; `frames` frames ran (launch accounting); err: their
+// error word (nonzero: the device counters are reset and the error decoded).
+int frame_readout(pifu_ctx* ctx, const FrameKey& k, int64_t frames, unsigned int err,
+                  cudaStream_t s, pifu_volume* out) {
     const GraphStats& gs = *ctx->h_gstats;
     pifu_volume vs{};
-    vs.num_levels = lv->num_levels;
-    vs.evals_per_level[0] = (int64_t)(lv->n0 + 1) * (lv->n0 + 1) * (lv->n0 + 1);
+    vs.num_levels = k.num_levels;
+    vs.evals_per_level[0] = (int64_t)(k.n0 + 1) * (k.n0 + 1) * (k.n0 + 1);
     vs.n_eval = vs.evals_per_level[0];
     int64_t launches = ctx->g_launches_fixed;
-    for (int l = 0; l < lv->num_levels; ++l) {
+    for (int l = 0; l < k.num_levels; ++l) {
         if (l > 0) {
             vs.evals_per_level[l] = (int64_t)gs.evals[l];
             vs.n_eval += (int64_t)gs.evals[l];
@@ -577,27 +587,90 @@ int pifu_frame(pifu_ctx* ctx, const pifu_fmap* occ_map, const pifu_fmap* col_map
         vs.rechecked_per_level[l] = (int64_t)gs.rechecked[l];
         vs.fallback_per_level[l] = (int64_t)gs.fallback[l];
     }
-    ctx->prof.k[PIFU_K_MLP_HIDDEN].launches += launches;   // graph: counted in one class
-    const int cur = (lv->num_levels - 1) & 1;
+    ctx->prof.k[PIFU_K_MLP_HIDDEN].launches += launches * frames;   // graph: counted in one class
+    const int cur = (k.num_levels - 1) & 1;
+    const int64_t n_fine = (int64_t)k.n0 << (k.num_levels - 1);
     vs.n = (int32_t)n_fine;
     vs.row_words = row_words_of((int)n_fine);
     vs.occ_bits_dev = ctx->bin[cur];
     vs.eval_bits_dev = ctx->eval;
     vs.values_dev = ctx->values;
-    if (cam->final_level && lv->num_levels < kMaxLevels)
-        vs.evals_per_level[lv->num_levels] = (int64_t)gs.culled;   // the culled final level
+    if (k.final_level && k.num_levels < kMaxLevels)
+        vs.evals_per_level[k.num_levels] = (int64_t)gs.culled;   // the culled final level
     if (out) *out = vs;
-    if (gs.err) {
+    if (err) {
         const int st = reset_after_error(ctx, s);
-        return st != PIFU_OK ? st : decode_err(gs.err);
+        return st != PIFU_OK ? st : decode_err(err);
     }
     ctx->stats = vs;
     ctx->have_volume = true;
     ctx->vol_N = (int)n_fine;
     ctx->vol_bin = cur;
-    ctx->vol_prec = lv->precision;
-    ctx->vol_margin = lv->margin;
+    ctx->vol_prec = k.precision;
+    ctx->vol_margin = k.margin;
     return PIFU_OK;
+}
+
+
+}  // namespace pifu_host
+
+using namespace pifu_host;
+
+extern "C" {
+
+int pifu_frame(pifu_ctx* ctx, const pifu_fmap* occ_map, const pifu_fmap* col_map,
+               const float calib[12], const pifu_levels* lv, const pifu_camera* cam, void* stream,
+               float* depth_dev, float* rgb_dev, uint8_t* mask_dev, pifu_volume* out) {
+    if (ctx && ctx->async_frames > 0) return PIFU_ERR_STATE;   // pifu_frame_wait first
+    FrameKey k;
+    int st = frame_enqueue(ctx, occ_map, col_map, calib, lv, cam, stream, depth_dev, rgb_dev,
+                           mask_dev, &k);
+    if (st != PIFU_OK) return st;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return PIFU_ERR_CUDA;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    CK(cudaStreamSynchronize(s));
+    return frame_readout(ctx, k, 1, ctx->h_gstats->err, s, out);
+}
+
+int pifu_frame_async(pifu_ctx* ctx, const pifu_fmap* occ_map, const pifu_fmap* col_map,
+                     const float calib[12], const pifu_levels* lv, const pifu_camera* cam,
+                     void* stream, float* depth_dev, float* rgb_dev, uint8_t* mask_dev) {
+    if (!ctx) return PIFU_ERR_ARG;
+    {
+        DeviceGuard g(ctx->device);
+        if (!g.ok) return PIFU_ERR_CUDA;
+        if (!ctx->d_sticky) {
+            CK(dev_alloc(&ctx->d_sticky, 1));
+            CK(cudaMemset(ctx->d_sticky, 0, sizeof(unsigned int)));
+        }
+    }
+    FrameKey k;
+    const int st = frame_enqueue(ctx, occ_map, col_map, calib, lv, cam, stream, depth_dev, rgb_dev,
+                                 mask_dev, &k);
+    if (st != PIFU_OK) return st;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return PIFU_ERR_CUDA;
+    CK(launch_latch_err(ctx->d_count + 1, ctx->d_sticky, static_cast<cudaStream_t>(stream)));
+    ctx->prof.k[PIFU_K_MLP_HIDDEN].launches += 1;   // counted with the graph's launches
+    ctx->async_key = k;
+    ++ctx->async_frames;
+    return PIFU_OK;
+}
+
+int pifu_frame_wait(pifu_ctx* ctx, void* stream, pifu_volume* out) {
+    if (!ctx) return PIFU_ERR_ARG;
+    if (ctx->async_frames <= 0) return PIFU_ERR_STATE;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return PIFU_ERR_CUDA;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    CK(cudaStreamSynchronize(s));
+    unsigned int sticky = 0;
+    CK(cudaMemcpy(&sticky, ctx->d_sticky, sizeof(sticky), cudaMemcpyDeviceToHost));
+    if (sticky) CK(cudaMemset(ctx->d_sticky, 0, sizeof(unsigned int)));
+    const int64_t n = ctx->async_frames;
+    ctx->async_frames = 0;
+    return frame_readout(ctx, ctx->async_key, n, sticky, s, out);
 }
 
 }  // extern "C"

@@ -513,6 +513,10 @@ struct pifu_ctx {
     unsigned int* d_count2 = nullptr;     // graph form: the frontier count (in d_tail's block)
     int64_t g_launches_fixed = 0;         // kernel launches outside the loops
     int64_t g_launches_body[8] = {};      // kernel launches per loop iteration
+    // asynchronous frames (pifu_frame_async / pifu_frame_wait)
+    unsigned int* d_sticky = nullptr;     // the enqueued frames' errors, ORed; host-cleared
+    int64_t async_frames = 0;             // enqueued since the last wait
+    FrameKey async_key{};                 // the last enqueued frame's arguments
     // lockstep frame batches (pifu_frames)
     BatchWs batch;
     // work-queue stream of frames (pifu_stream)

@@ -571,6 +571,13 @@ __global__ void accumulate_kernel(unsigned long long* dst, const unsigned int* s
     if (v > cap) atomicOr(err, kErrCapacity);
 }
 
+// An enqueued frame's error word ORed into a word that only the host clears
+// (the asynchronous frame call: the next frame's graph zeroes its own word).
+__global__ void latch_err_kernel(const unsigned int* err, unsigned int* sticky) {
+    const unsigned int e = *err;
+    if (e) atomicOr(sticky, e);
+}
+
 // The start of a conflict round in the graph: the round's size moved from
 // the frontier count to the batch count, accumulate_kernel's statistics,
 // *zero = 0, and (set) branch_kernel's two conditions, in one launch.
@@ -689,6 +696,11 @@ cudaError_t launch_branch(cudaGraphConditionalHandle hs, cudaGraphConditionalHan
 cudaError_t launch_accumulate(unsigned long long* dst, const unsigned int* src, unsigned int cap,
                               unsigned int* err, cudaStream_t stream) {
     accumulate_kernel<<<1, 1, 0, stream>>>(dst, src, cap, err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_latch_err(const unsigned int* err, unsigned int* sticky, cudaStream_t stream) {
+    latch_err_kernel<<<1, 1, 0, stream>>>(err, sticky);
     return cudaGetLastError();
 }
 

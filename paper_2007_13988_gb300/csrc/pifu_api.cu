@@ -146,6 +146,7 @@ void pifu_destroy(pifu_ctx* ctx) {
     dev_free(ctx->clist);
     dev_free(ctx->d_ccount);
     dev_free(ctx->d_gstats);
+    dev_free(ctx->d_sticky);
     if (ctx->h_gstats) cudaFreeHost(ctx->h_gstats);
     if (ctx->h_count) cudaFreeHost(ctx->h_count);
     if (ctx->h_pop) cudaFreeHost(ctx->h_pop);

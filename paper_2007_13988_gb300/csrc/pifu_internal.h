@@ -558,6 +558,8 @@ cudaError_t launch_branch(cudaGraphConditionalHandle hs, cudaGraphConditionalHan
 // *dst += *src; capacity error bit if *src > cap.
 cudaError_t launch_accumulate(unsigned long long* dst, const unsigned int* src, unsigned int cap,
                               unsigned int* err, cudaStream_t stream);
+// *sticky |= *err (one thread): an enqueued frame's error kept for the host.
+cudaError_t launch_latch_err(const unsigned int* err, unsigned int* sticky, cudaStream_t stream);
 // A conflict round's start in one launch: the round's size c = *next (the
 // frontier count the previous selection or expansion appended to) becomes
 // *count, the batch size its passes read, and *next = 0 for the next

@@ -46,7 +46,7 @@ EXPORTS = ("pifu_create", "pifu_destroy", "pifu_query", "pifu_query_colour", "pi
            "pifu_calibrate_fp8", "pifu_frames", "pifu_autotune", "pifu_surrogate_ohem_init",
            "pifu_surrogate_ohem_weights", "pifu_surrogate_ohem_sample",
            "pifu_surrogate_train_ohem", "pifu_set_tiles", "pifu_set_schedule", "pifu_stream",
-           "pifu_set_recheck", "pifu_test_starve_wait")
+           "pifu_set_recheck", "pifu_test_starve_wait", "pifu_frame_async", "pifu_frame_wait")
 
 KERNEL_CLASSES = ("gather", "mlp_hidden", "mlp_last", "level", "select", "render", "mlp_f32",
                   "cbn_tc")
@@ -141,6 +141,12 @@ def _lib():
                                ctypes.POINTER(F), ctypes.POINTER(pifu_levels),
                                ctypes.POINTER(pifu_camera), P, P, P, P, ctypes.POINTER(pifu_volume)]
     lib.pifu_frame.restype = I
+    lib.pifu_frame_async.argtypes = [P, ctypes.POINTER(pifu_fmap), ctypes.POINTER(pifu_fmap),
+                                     ctypes.POINTER(F), ctypes.POINTER(pifu_levels),
+                                     ctypes.POINTER(pifu_camera), P, P, P, P]
+    lib.pifu_frame_async.restype = I
+    lib.pifu_frame_wait.argtypes = [P, P, ctypes.POINTER(pifu_volume)]
+    lib.pifu_frame_wait.restype = I
     U64, D = ctypes.c_uint64, ctypes.c_double
     lib.pifu_frames.argtypes = [P, I, ctypes.POINTER(pifu_fmap), ctypes.POINTER(pifu_fmap),
                                 ctypes.POINTER(F), ctypes.POINTER(pifu_levels),
@@ -370,6 +376,33 @@ def pifu_frame(ctx, occ_map, col_map, calib, n0, num_levels, width, height, dept
                            ctypes.byref(lv), ctypes.byref(cam), _stream(stream), _ptr(depth),
                            _ptr(rgb), _ptr(mask), ctypes.byref(vol))
     _check(st, "pifu_frame", ctx)
+    return vol
+
+
+def pifu_frame_async(ctx, occ_map, col_map, calib, n0, num_levels, width, height, depth=None,
+                     rgb=None, mask=None, precision=PIFU_PREC_MIXED, margin=0.02, max_rounds=0,
+                     background=(0.0, 0.0, 0.0), stream=None, use_surrogate=False,
+                     surrogate_margin=0.0, final_level=0) -> None:
+    """pifu_frame enqueued on `stream` without waiting for it; errors and the
+    volume come from pifu_frame_wait."""
+    fo = fmap(occ_map)
+    fc = fmap(col_map)
+    lv = pifu_levels(n0, num_levels, precision, max_rounds, margin, int(bool(use_surrogate)),
+                     surrogate_margin)
+    cam = pifu_camera(width, height, (ctypes.c_float * 3)(*background), PIFU_PREC_BF16,
+                      final_level)
+    st = _lib().pifu_frame_async(ctx, ctypes.byref(fo), ctypes.byref(fc) if fc else None,
+                                 _calib(calib), ctypes.byref(lv), ctypes.byref(cam),
+                                 _stream(stream), _ptr(depth), _ptr(rgb), _ptr(mask))
+    _check(st, "pifu_frame_async", ctx)
+
+
+def pifu_frame_wait(ctx, stream=None) -> pifu_volume:
+    """Waits for the frames pifu_frame_async enqueued; raises the error any of
+    them latched; returns the last frame's volume."""
+    vol = pifu_volume()
+    st = _lib().pifu_frame_wait(ctx, _stream(stream), ctypes.byref(vol))
+    _check(st, "pifu_frame_wait", ctx)
     return vol
 
 

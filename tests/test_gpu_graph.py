@@ -85,6 +85,32 @@ def test_graph_frame_relaunch_is_deterministic(full):
     assert v1.n_eval == v2.n_eval
 
 
+def test_async_frames_equal_the_synchronous_frame(full):
+    # pifu_frame_async launches the same graph without waiting: three frames
+    # back to back, then pifu_frame_wait, give pifu_frame's outputs bit for bit
+    import torch
+    v1, d1, r1, m1 = run_frame(full, 512)
+    R = 512
+    depth = torch.empty((R, R), dtype=torch.float32, device="cuda")
+    rgb = torch.empty((R, R, 3), dtype=torch.float32, device="cuda")
+    mask = torch.empty((R, R), dtype=torch.uint8, device="cuda")
+    w = full.w
+    args = (full.ctx, full.occ, full.col, w.calib, w.n0, w.num_levels, R, R, depth, rgb, mask)
+    vs = pifu.pifu_frame(*args, precision=pifu.PIFU_PREC_MIXED)   # captures this output set
+    for _ in range(3):
+        pifu.pifu_frame_async(*args, precision=pifu.PIFU_PREC_MIXED)
+    va = pifu.pifu_frame_wait(full.ctx, torch.cuda.current_stream())
+    d2 = depth.cpu().numpy().astype(np.float64)
+    assert np.array_equal(mask.cpu().numpy().astype(bool), m1)
+    assert np.array_equal(np.nan_to_num(d2, nan=-9), np.nan_to_num(d1, nan=-9))
+    assert np.array_equal(rgb.cpu().numpy().astype(np.float64), r1)
+    assert va.n_eval == v1.n_eval == vs.n_eval
+    assert list(va.conflict_rounds)[:4] == list(v1.conflict_rounds)[:4]
+    b1, e1, _ = full.volume_host(v1)
+    ba, ea, _ = full.volume_host(va)
+    assert np.array_equal(b1, ba) and np.array_equal(e1, ea)
+
+
 def test_graph_frame_bf16(full, full_oracle):
     # no FP32 re-check: a BF16 decision near 0.5 may move a ray's first
     # inside sample by a node, and its crossing by up to two intervals
