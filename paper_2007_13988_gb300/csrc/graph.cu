@@ -81,7 +81,7 @@ int g_eval(pifu_ctx* ctx, const DevNet& net, const PointSrc& src, int64_t cap,
     const bool branch = !sur && prec != PIFU_PREC_BF16 && prec != PIFU_PREC_FP8 && m_dev &&
                         ctx->cap_stream3 && s != ctx->cap_stream3;
     if (rs && !branch)
-        CK(launch_round_start(0, 0, false, const_cast<unsigned int*>(m_dev), 0u, *rs, s));
+        CK(launch_round_start(const_cast<unsigned int*>(m_dev), *rs, s));
     if (sur) {
         // qcap_in > 0: the f_O queue already holds keys (the frame stream's
         // finest-level keys), f_S's fall-backs are appended after them
@@ -109,34 +109,58 @@ int g_eval(pifu_ctx* ctx, const DevNet& net, const PointSrc& src, int64_t cap,
                           prec == PIFU_PREC_FP8);
     if (branch) {
         // A device-sized batch of at most kTinyBatch points goes straight to
-        // FP32 (one fused launch), as in the host-driven form; the tensor-core
-        // pass and its re-check run above that.  Two IF nodes, set on the device.
+        // FP32, as in the host-driven form; the tensor-core pass and its
+        // re-check run above that.  One SWITCH, set on the device (with a
+        // conflict round's start in the same launch): its first bodies are
+        // g_recheck's FP32 forms for the small batch, its last the
+        // tensor-core pass; an empty batch runs none.
         cudaStreamCaptureStatus cs;
         cudaGraph_t cg = nullptr;
         CK(cudaStreamGetCaptureInfo(s, &cs, nullptr, &cg, nullptr, nullptr, nullptr));
-        cudaGraphConditionalHandle hs, hl;
-        CK(cudaGraphConditionalHandleCreate(&hs, cg, 0, 0));
-        CK(cudaGraphConditionalHandleCreate(&hl, cg, 0, 0));
-        if (rs)
-            CK(launch_round_start(hs, hl, true, const_cast<unsigned int*>(m_dev),
-                                  (unsigned)kTinyBatch, *rs, s));
-        else CK(launch_branch(hs, hl, m_dev, (unsigned)kTinyBatch, s));
+        cudaGraphConditionalHandle h;
+        CK(cudaGraphConditionalHandleCreate(&h, cg, 0, 0));
         cudaStream_t s3 = ctx->cap_stream3;
-        for (int br = 0; br < 2; ++br) {
-            cudaGraph_t body = nullptr;
-            int st = g_add_cond(ctx, s, br == 0 ? hs : hl, cudaGraphCondTypeIf, &body);
-            if (st != PIFU_OK) return st;
-            CK(cudaStreamBeginCaptureToGraph(s3, body, nullptr, nullptr, 0,
+        // the FP32 forms g_recheck would switch between for this capacity
+        const FusedNet fz = fused_of(net);
+        const bool sw = net.kind != kNetCbn && ctx->cap_stream4 && fused_ok(fz);
+        const FusedPlan plan = sw ? fused_plan(fz) : FusedPlan{};
+        const int64_t x3_lo = x3_min_rows(ctx);
+        const bool x3 = sw && plan.n >= 1 && x3_usable(ctx, net) && cap > x3_lo;
+        const int64_t ghi = sw && plan.n >= 1 ? std::min<int64_t>(grid_rows(ctx, net), cap) : 0;
+        const bool single = plan.n <= 1 && !x3 && ghi <= 0;
+        const int nt = single ? 1 : plan.n + (x3 ? 1 : 0) + (ghi > 0 ? 1 : 0);
+        CK(launch_batch_switch(h, plan, const_cast<unsigned int*>(m_dev), (unsigned)cap,
+                               (unsigned)kTinyBatch, nt, single, x3 ? (unsigned)x3_lo : 0u,
+                               x3 ? (unsigned)kX3Rows : 0u, ghi > 0 ? (unsigned)ghi : 0u, rs, s));
+        cudaGraph_t bodies[8] = {};
+        int st = g_add_switch(ctx, s, h, nt + 1, bodies);
+        if (st != PIFU_OK) return st;
+        const int64_t before = launches_now(ctx);
+        int64_t small = 0;
+        for (int i = 0; i <= nt; ++i) {
+            CK(cudaStreamBeginCaptureToGraph(s3, bodies[i], nullptr, nullptr, 0,
                                              cudaStreamCaptureModeThreadLocal));
-            if (br == 0)
-                st = g_recheck(ctx, net, src, cap, map, cal, epi, s3, m_dev);
-            else
+            if (i == nt)
                 st = g_eval(ctx, net, src, cap, m_dev, map, cal, epi, prec, margin, rechecked, s3);
+            else if (single)
+                st = run_mlp(ctx, net, src, cap, map, Map{}, cal, epi, s3, PIFU_PREC_FP32, m_dev);
+            else if (i < plan.n)
+                st = run_mlp(ctx, net, src, cap, map, Map{}, cal, epi, s3, PIFU_PREC_FP32, m_dev,
+                             plan.cl[i]);
+            else if (x3 && i == plan.n)
+                st = run_mlp_x3(ctx, net, src, std::min<int64_t>(cap, kX3Rows), map, Map{}, cal,
+                                epi, s3, m_dev);
+            else
+                st = run_mlp_grid(ctx, net, src, ghi, map, Map{}, cal, epi, s3, m_dev);
             cudaGraph_t out = nullptr;
             const cudaError_t ee = cudaStreamEndCapture(s3, &out);
             if (st != PIFU_OK) return st;
             if (ee != cudaSuccess) return fail_cuda(ctx, ee);
+            if (i + 1 == nt) small = launches_now(ctx) - before;
         }
+        // one small body, one launch, runs per replay (the large body's
+        // launches stay counted, as the branch that does the work)
+        ctx->prof.k[PIFU_K_MLP_F32].launches -= small - 1;
         return PIFU_OK;
     }
     CK(cudaMemsetAsync(ctx->d_recheck, 0, sizeof(unsigned int), s));

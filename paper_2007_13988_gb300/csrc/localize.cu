@@ -554,15 +554,6 @@ __global__ void __launch_bounds__(256) stream_select_kernel(
     if (lane == 0 && ncand) atomicAdd(cands + slot, ncand);
 }
 
-// Graph form: picks one of two conditional branches from a device-resident
-// batch size: hs for 1 .. threshold points, hl above.
-__global__ void branch_kernel(cudaGraphConditionalHandle hs, cudaGraphConditionalHandle hl,
-                              const unsigned int* count, unsigned int threshold) {
-    const unsigned int c = *count;
-    cudaGraphSetConditional(hs, (c > 0u && c <= threshold) ? 1u : 0u);
-    cudaGraphSetConditional(hl, c > threshold ? 1u : 0u);
-}
-
 // *dst += *src, flagging a capacity error when *src exceeds cap.
 __global__ void accumulate_kernel(unsigned long long* dst, const unsigned int* src,
                                   unsigned int cap, unsigned int* err) {
@@ -579,22 +570,18 @@ __global__ void latch_err_kernel(const unsigned int* err, unsigned int* sticky) 
 }
 
 // The start of a conflict round in the graph: the round's size moved from
-// the frontier count to the batch count, accumulate_kernel's statistics,
-// *zero = 0, and (set) branch_kernel's two conditions, in one launch.
-__global__ void round_start_kernel(cudaGraphConditionalHandle hs, cudaGraphConditionalHandle hl,
-                                   int set, unsigned int* count, unsigned int threshold,
-                                   unsigned long long* evals, unsigned int cap, unsigned int* err,
-                                   unsigned int* zero, unsigned int* next) {
+// the frontier count to the batch count, accumulate_kernel's statistics and
+// *zero = 0, in one launch (batch_switch_kernel does the same for a batch
+// that also picks its branch).
+__global__ void round_start_kernel(unsigned int* count, unsigned long long* evals,
+                                   unsigned int cap, unsigned int* err, unsigned int* zero,
+                                   unsigned int* next) {
     const unsigned int c = *next;
     *count = c;
     *next = 0u;
     *evals += c;
     if (c > cap) atomicOr(err, kErrCapacity);
     *zero = 0u;
-    if (set) {
-        cudaGraphSetConditional(hs, (c > 0u && c <= threshold) ? 1u : 0u);
-        cudaGraphSetConditional(hl, c > threshold ? 1u : 0u);
-    }
 }
 
 inline unsigned blocks_for(int64_t n) { return (unsigned)((n + 255) / 256); }
@@ -687,12 +674,6 @@ cudaError_t launch_stream_select(const SlotView* sv, int slots, int N_fine, int6
     return cudaGetLastError();
 }
 
-cudaError_t launch_branch(cudaGraphConditionalHandle hs, cudaGraphConditionalHandle hl,
-                          const unsigned int* count, unsigned int threshold, cudaStream_t stream) {
-    branch_kernel<<<1, 1, 0, stream>>>(hs, hl, count, threshold);
-    return cudaGetLastError();
-}
-
 cudaError_t launch_accumulate(unsigned long long* dst, const unsigned int* src, unsigned int cap,
                               unsigned int* err, cudaStream_t stream) {
     accumulate_kernel<<<1, 1, 0, stream>>>(dst, src, cap, err);
@@ -704,11 +685,8 @@ cudaError_t launch_latch_err(const unsigned int* err, unsigned int* sticky, cuda
     return cudaGetLastError();
 }
 
-cudaError_t launch_round_start(cudaGraphConditionalHandle hs, cudaGraphConditionalHandle hl,
-                               bool set, unsigned int* count, unsigned int threshold,
-                               const RoundStart& rs, cudaStream_t stream) {
-    round_start_kernel<<<1, 1, 0, stream>>>(hs, hl, set ? 1 : 0, count, threshold, rs.evals,
-                                            rs.cap, rs.err, rs.zero, rs.next);
+cudaError_t launch_round_start(unsigned int* count, const RoundStart& rs, cudaStream_t stream) {
+    round_start_kernel<<<1, 1, 0, stream>>>(count, rs.evals, rs.cap, rs.err, rs.zero, rs.next);
     return cudaGetLastError();
 }
 

@@ -386,17 +386,50 @@ __host__ __device__ int fused_pick(const FusedPlan& p, long long tiles) {
 
 // Bodies: the plan's cluster sizes, then the split-TF32 network (x3_hi > 0),
 // then the whole-GPU network (grid_hi > 0); an index past them runs nothing.
+__device__ __forceinline__ unsigned int fused_index(const FusedPlan& plan, unsigned int c,
+                                                    unsigned int x3_lo, unsigned int x3_hi,
+                                                    unsigned int grid_hi) {
+    const unsigned int x3_idx = (unsigned)plan.n;
+    const unsigned int grid_idx = x3_idx + (x3_hi > 0u ? 1u : 0u);
+    if (c == 0u) return grid_idx + (grid_hi > 0u ? 1u : 0u);
+    if (c <= grid_hi) return grid_idx;
+    if (c > x3_lo && c <= x3_hi) return x3_idx;
+    return (unsigned)fused_pick(plan, ((long long)c + kFP - 1) / kFP);
+}
+
 __global__ void fused_switch_kernel(cudaGraphConditionalHandle h, FusedPlan plan,
                                     const unsigned int* count, unsigned int cap, unsigned int x3_lo,
                                     unsigned int x3_hi, unsigned int grid_hi) {
-    const unsigned int c = min(*count, cap);
-    const unsigned int x3_idx = (unsigned)plan.n;
-    const unsigned int grid_idx = x3_idx + (x3_hi > 0u ? 1u : 0u);
+    cudaGraphSetConditional(h, fused_index(plan, min(*count, cap), x3_lo, x3_hi, grid_hi));
+}
+
+// One batch of the MIXED forms in the graph as one SWITCH: bodies 0 .. nt-1
+// evaluate a batch of 1 .. threshold points in FP32 (single: body 0 alone,
+// else fused_switch_kernel's choice among them), body nt takes a larger
+// batch to the tensor cores, and an empty batch runs no body.  has_rs: the
+// batch is a conflict round, whose size is first moved from the frontier
+// count, with round_start_kernel's statistics and zeroing.
+__global__ void batch_switch_kernel(cudaGraphConditionalHandle h, FusedPlan plan,
+                                    unsigned int* count, unsigned int cap,
+                                    unsigned int threshold, int nt, int single,
+                                    unsigned int x3_lo, unsigned int x3_hi, unsigned int grid_hi,
+                                    RoundStart rs, int has_rs) {
+    unsigned int c;
+    if (has_rs) {
+        c = *rs.next;
+        *count = c;
+        *rs.next = 0u;
+        *rs.evals += c;
+        if (c > rs.cap) atomicOr(rs.err, kErrCapacity);
+        *rs.zero = 0u;
+    } else {
+        c = *count;
+    }
     unsigned int i;
-    if (c == 0u) i = grid_idx + (grid_hi > 0u ? 1u : 0u);
-    else if (c <= grid_hi) i = grid_idx;
-    else if (c > x3_lo && c <= x3_hi) i = x3_idx;
-    else i = (unsigned)fused_pick(plan, ((long long)c + kFP - 1) / kFP);
+    if (c == 0u) i = (unsigned)nt + 1u;
+    else if (c > threshold) i = (unsigned)nt;
+    else if (single) i = 0u;
+    else i = fused_index(plan, min(c, cap), x3_lo, x3_hi, grid_hi);
     cudaGraphSetConditional(h, i);
 }
 
@@ -420,6 +453,16 @@ cudaError_t launch_fused_switch(cudaGraphConditionalHandle h, const FusedPlan& p
                                 const unsigned int* count, unsigned int cap, cudaStream_t stream,
                                 unsigned int x3_lo, unsigned int x3_hi, unsigned int grid_hi) {
     fused_switch_kernel<<<1, 1, 0, stream>>>(h, plan, count, cap, x3_lo, x3_hi, grid_hi);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_switch(cudaGraphConditionalHandle h, const FusedPlan& plan,
+                                unsigned int* count, unsigned int cap, unsigned int threshold,
+                                int nt, bool single, unsigned int x3_lo, unsigned int x3_hi,
+                                unsigned int grid_hi, const RoundStart* rs, cudaStream_t stream) {
+    batch_switch_kernel<<<1, 1, 0, stream>>>(h, plan, count, cap, threshold, nt, single ? 1 : 0,
+                                             x3_lo, x3_hi, grid_hi, rs ? *rs : RoundStart{},
+                                             rs ? 1 : 0);
     return cudaGetLastError();
 }
 

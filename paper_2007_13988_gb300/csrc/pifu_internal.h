@@ -552,9 +552,6 @@ cudaError_t launch_stream_select(const SlotView* sv, int slots, int N_fine, int6
                                  unsigned long long* cands, cudaStream_t stream,
                                  int* list_f = nullptr, unsigned int* count_f = nullptr);
 
-// Graph form: set hs for 1 .. threshold points in *count, hl above.
-cudaError_t launch_branch(cudaGraphConditionalHandle hs, cudaGraphConditionalHandle hl,
-                          const unsigned int* count, unsigned int threshold, cudaStream_t stream);
 // *dst += *src; capacity error bit if *src > cap.
 cudaError_t launch_accumulate(unsigned long long* dst, const unsigned int* src, unsigned int cap,
                               unsigned int* err, cudaStream_t stream);
@@ -563,8 +560,7 @@ cudaError_t launch_latch_err(const unsigned int* err, unsigned int* sticky, cuda
 // A conflict round's start in one launch: the round's size c = *next (the
 // frontier count the previous selection or expansion appended to) becomes
 // *count, the batch size its passes read, and *next = 0 for the next
-// expansion; *evals += c (capacity error bit if above cap), *zero = 0, and,
-// with handles, launch_branch's two conditions on c.
+// expansion; *evals += c (capacity error bit if above cap), *zero = 0.
 struct RoundStart {
     unsigned long long* evals;
     unsigned int cap;
@@ -572,9 +568,7 @@ struct RoundStart {
     unsigned int* zero;
     unsigned int* next;
 };
-cudaError_t launch_round_start(cudaGraphConditionalHandle hs, cudaGraphConditionalHandle hl,
-                               bool set, unsigned int* count, unsigned int threshold,
-                               const RoundStart& rs, cudaStream_t stream);
+cudaError_t launch_round_start(unsigned int* count, const RoundStart& rs, cudaStream_t stream);
 
 // Population count of a bitset (for statistics) added into *count.
 // Several frames: count[f] += popcount of frame f's bitset.
@@ -623,6 +617,16 @@ cudaError_t launch_fused_switch(cudaGraphConditionalHandle h, const FusedPlan& p
                                 const unsigned int* count, unsigned int cap, cudaStream_t stream,
                                 unsigned int x3_lo = 0, unsigned int x3_hi = 0,
                                 unsigned int grid_hi = 0);
+// Graph form, one evaluation batch of the MIXED forms as one switch `h` of
+// nt + 1 bodies: a device-resident batch of c points, 1 <= c <= threshold,
+// selects an FP32 body (body 0 when single, else launch_fused_switch's index
+// for min(c, cap)); c > threshold selects body nt (the tensor-core pass);
+// c = 0 none.  rs (optional): the batch is a conflict round; c is first
+// moved from *rs->next into *count with round_start's statistics.
+cudaError_t launch_batch_switch(cudaGraphConditionalHandle h, const FusedPlan& plan,
+                                unsigned int* count, unsigned int cap, unsigned int threshold,
+                                int nt, bool single, unsigned int x3_lo, unsigned int x3_hi,
+                                unsigned int grid_hi, const RoundStart* rs, cudaStream_t stream);
 
 // --- mlp_grid.cu -----------------------------------------------------------
 // The whole network in FP32 for a batch of at most kGridMaxRows points in one
