@@ -201,7 +201,6 @@ int g_enqueue_batch(pifu_ctx* ctx, const BatchKey& k) {
     a.slots = B;
     a.slot_nodes = sn;
     a.slot_words = fs;
-    CK(cudaMemsetAsync(ctx->d_count, 0, sizeof(unsigned int), s));
     CK(launch_render_rays(a, s));
     ctx->prof.k[PIFU_K_RENDER].launches += 2;
     if (k.rgb) {

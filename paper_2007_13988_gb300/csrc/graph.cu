@@ -21,7 +21,7 @@ int64_t launches_now(const pifu_ctx* ctx);
 // launches nothing.
 int g_recheck(pifu_ctx* ctx, const DevNet& net, const PointSrc& src, int64_t cap,
               const Map& map, const Calib& cal, const Epilogue& epi, cudaStream_t s,
-              const unsigned int* m_dev) {
+              const unsigned int* m_dev, unsigned long long* stat, unsigned int stat_cap) {
     const FusedNet fz = fused_of(net);
     const bool sw = net.kind != kNetCbn && ctx->cap_stream4 && s != ctx->cap_stream4 &&
                     fused_ok(fz);
@@ -29,15 +29,18 @@ int g_recheck(pifu_ctx* ctx, const DevNet& net, const PointSrc& src, int64_t cap
     const int64_t x3_lo = x3_min_rows(ctx);
     const bool x3 = sw && plan.n >= 1 && x3_usable(ctx, net) && cap > x3_lo;
     const int64_t ghi = sw && plan.n >= 1 ? std::min<int64_t>(grid_rows(ctx, net), cap) : 0;
-    if (plan.n <= 1 && !x3 && ghi <= 0)
+    if (plan.n <= 1 && !x3 && ghi <= 0) {
+        if (stat) CK(launch_accumulate(stat, m_dev, stat_cap, ctx->d_count + 1, s));
         return run_mlp(ctx, net, src, cap, map, Map{}, cal, epi, s, PIFU_PREC_FP32, m_dev);
+    }
     cudaStreamCaptureStatus cs;
     cudaGraph_t cg = nullptr;
     CK(cudaStreamGetCaptureInfo(s, &cs, nullptr, &cg, nullptr, nullptr, nullptr));
     cudaGraphConditionalHandle h;
     CK(cudaGraphConditionalHandleCreate(&h, cg, 0, 0));
     CK(launch_fused_switch(h, plan, m_dev, (unsigned)cap, s, x3 ? (unsigned)x3_lo : 0u,
-                           x3 ? (unsigned)kX3Rows : 0u, ghi > 0 ? (unsigned)ghi : 0u));
+                           x3 ? (unsigned)kX3Rows : 0u, ghi > 0 ? (unsigned)ghi : 0u, stat,
+                           stat_cap, ctx->d_count + 1));
     const int nb = plan.n + (x3 ? 1 : 0) + (ghi > 0 ? 1 : 0);
     cudaGraph_t bodies[6] = {};
     int st = g_add_switch(ctx, s, h, nb, bodies);
@@ -77,7 +80,7 @@ int g_eval(pifu_ctx* ctx, const DevNet& net, const PointSrc& src, int64_t cap,
            const unsigned int* m_dev, const Map& map, const Calib& cal, const Epilogue& epi,
            int prec, float margin, unsigned long long* rechecked, cudaStream_t s,
            bool sur, float sur_margin, unsigned long long* fallback, int64_t qcap_in,
-           const RoundStart* rs) {
+           const RoundStart* rs, bool recheck_zeroed) {
     const bool branch = !sur && prec != PIFU_PREC_BF16 && prec != PIFU_PREC_FP8 && m_dev &&
                         ctx->cap_stream3 && s != ctx->cap_stream3;
     if (rs && !branch)
@@ -131,7 +134,8 @@ int g_eval(pifu_ctx* ctx, const DevNet& net, const PointSrc& src, int64_t cap,
         const int nt = single ? 1 : plan.n + (x3 ? 1 : 0) + (ghi > 0 ? 1 : 0);
         CK(launch_batch_switch(h, plan, const_cast<unsigned int*>(m_dev), (unsigned)cap,
                                (unsigned)kTinyBatch, nt, single, x3 ? (unsigned)x3_lo : 0u,
-                               x3 ? (unsigned)kX3Rows : 0u, ghi > 0 ? (unsigned)ghi : 0u, rs, s));
+                               x3 ? (unsigned)kX3Rows : 0u, ghi > 0 ? (unsigned)ghi : 0u, rs,
+                               ctx->d_recheck, s));
         cudaGraph_t bodies[8] = {};
         int st = g_add_switch(ctx, s, h, nt + 1, bodies);
         if (st != PIFU_OK) return st;
@@ -141,7 +145,8 @@ int g_eval(pifu_ctx* ctx, const DevNet& net, const PointSrc& src, int64_t cap,
             CK(cudaStreamBeginCaptureToGraph(s3, bodies[i], nullptr, nullptr, 0,
                                              cudaStreamCaptureModeThreadLocal));
             if (i == nt)
-                st = g_eval(ctx, net, src, cap, m_dev, map, cal, epi, prec, margin, rechecked, s3);
+                st = g_eval(ctx, net, src, cap, m_dev, map, cal, epi, prec, margin, rechecked, s3,
+                            false, 0.f, nullptr, 0, nullptr, true);
             else if (single)
                 st = run_mlp(ctx, net, src, cap, map, Map{}, cal, epi, s3, PIFU_PREC_FP32, m_dev);
             else if (i < plan.n)
@@ -163,7 +168,7 @@ int g_eval(pifu_ctx* ctx, const DevNet& net, const PointSrc& src, int64_t cap,
         ctx->prof.k[PIFU_K_MLP_F32].launches -= small - 1;
         return PIFU_OK;
     }
-    CK(cudaMemsetAsync(ctx->d_recheck, 0, sizeof(unsigned int), s));
+    if (!recheck_zeroed) CK(cudaMemsetAsync(ctx->d_recheck, 0, sizeof(unsigned int), s));
     Epilogue e1 = epi;
     e1.recheck = ctx->recheck;
     e1.recheck_count = ctx->d_recheck;
@@ -181,10 +186,9 @@ int g_eval(pifu_ctx* ctx, const DevNet& net, const PointSrc& src, int64_t cap,
     // the fused kernel takes any queue length (at most the batch's); the
     // split-K path has a fixed capacity
     const int64_t rcap = (net.kind == kNetCbn || fused_ok(fused_of(net))) ? cap : kRecheckCap;
-    st = g_recheck(ctx, net, s2, rcap, map, cal, e2, s, ctx->d_recheck);
-    if (st != PIFU_OK) return st;
-    CK(launch_accumulate(rechecked, ctx->d_recheck, (unsigned)rcap, ctx->d_count + 1, s));
-    return PIFU_OK;
+    // the re-check count joins the statistics in the launch that picks its form
+    return g_recheck(ctx, net, s2, rcap, map, cal, e2, s, ctx->d_recheck, rechecked,
+                     (unsigned)rcap);
 }
 
 // Appends a WHILE node to the capture of `s` (after everything captured so
@@ -258,11 +262,14 @@ int g_enqueue_frame(pifu_ctx* ctx, const FrameKey& k, const Map& occ, const Map&
     unsigned int* err = ctx->d_count + 1;
     const DevNet& net = ctx->net[0];
     int st = PIFU_OK;
-    CK(cudaMemsetAsync(gs, 0, sizeof(GraphStats), s));
-    CK(cudaMemsetAsync(err, 0, sizeof(unsigned int), s));
-    // level 0: every node
+    // level 0: every node; the set-up launch also zeroes the frame's
+    // statistics, its error word and the re-check queue length
     int N = k.n0, cur = 0;
-    CK(launch_dense_setup(N, ctx->cand, ctx->tent, ctx->bin[cur], ctx->eval, ctx->conf[0], s));
+    static_assert(sizeof(GraphStats) % 4 == 0, "statistics zeroed as words");
+    const ZeroSpans zs{{reinterpret_cast<unsigned int*>(gs), err, ctx->d_recheck},
+                       {(uint32_t)(sizeof(GraphStats) / 4), 1u, 1u}};
+    CK(launch_dense_setup(N, ctx->cand, ctx->tent, ctx->bin[cur], ctx->eval, ctx->conf[0], s, 1,
+                          0, &zs));
     {
         const int64_t nodes = (int64_t)(N + 1) * (N + 1) * (N + 1);
         PointSrc src{PTS_DENSE, nullptr, nullptr, 0, N, nullptr};
@@ -271,7 +278,7 @@ int g_enqueue_frame(pifu_ctx* ctx, const FrameKey& k, const Map& occ, const Map&
         epi.lv = LevelBits{ctx->values, ctx->tent, ctx->bin[cur], ctx->conf[0], N, row_words_of(N), 1};
         st = g_eval(ctx, net, src, nodes, nullptr, occ, cal, epi, k.precision, k.margin,
                     &gs->rechecked[0], s, k.use_surrogate && k.num_levels > 1, k.sur_margin,
-                    &gs->fallback[0]);
+                    &gs->fallback[0], 0, nullptr, true);
         if (st != PIFU_OK) return st;
     }
     for (int l = 1; l < k.num_levels; ++l) {
@@ -406,7 +413,6 @@ int g_enqueue_frame(pifu_ctx* ctx, const FrameKey& k, const Map& occ, const Map&
     a.hit_pix = ctx->hit_pix;
     a.hit_count = ctx->d_count;
     a.top = ctx->col_top;
-    CK(cudaMemsetAsync(ctx->d_count, 0, sizeof(unsigned int), s));
     CK(launch_render_rays(a, s));
     ctx->prof.k[PIFU_K_RENDER].launches += 2;
     if (k.rgb) {

@@ -721,14 +721,17 @@ int g_add_cond(pifu_ctx* ctx, cudaStream_t s, cudaGraphConditionalHandle h,
 int g_add_switch(pifu_ctx* ctx, cudaStream_t s, cudaGraphConditionalHandle h, int n,
                  cudaGraph_t* bodies);
 int64_t launches_now(const pifu_ctx* ctx);
+// stat (optional): *stat += the queue length, capacity error above stat_cap.
 int g_recheck(pifu_ctx* ctx, const DevNet& net, const PointSrc& src, int64_t cap,
               const Map& map, const Calib& cal, const Epilogue& epi, cudaStream_t s,
-              const unsigned int* m_dev);
+              const unsigned int* m_dev, unsigned long long* stat = nullptr,
+              unsigned int stat_cap = 0);
+// recheck_zeroed: a launch before this batch zeroed the re-check queue length.
 int g_eval(pifu_ctx* ctx, const DevNet& net, const PointSrc& src, int64_t cap,
            const unsigned int* m_dev, const Map& map, const Calib& cal, const Epilogue& epi,
            int prec, float margin, unsigned long long* rechecked, cudaStream_t s,
            bool sur = false, float sur_margin = 0.f, unsigned long long* fallback = nullptr,
-           int64_t qcap_in = 0, const RoundStart* rs = nullptr);
+           int64_t qcap_in = 0, const RoundStart* rs = nullptr, bool recheck_zeroed = false);
 int g_add_while(pifu_ctx* ctx, cudaStream_t s, cudaGraphConditionalHandle h, cudaGraph_t* body);
 int g_enqueue_frame(pifu_ctx* ctx, const FrameKey& k, const Map& occ, const Map& col,
                     const Calib& cal);

@@ -182,7 +182,10 @@ __global__ void __launch_bounds__(256) dense_setup_kernel(int N, uint32_t* __res
                                                           uint32_t* __restrict__ bin,
                                                           uint32_t* __restrict__ eval,
                                                           uint32_t* __restrict__ conf0,
-                                                          int64_t fslot) {
+                                                          int64_t fslot, ZeroSpans z) {
+    if (blockIdx.x == 0 && blockIdx.y == 0)
+        for (int q = 0; q < ZeroSpans::kMax; ++q)
+            for (uint32_t i = threadIdx.x; i < z.words[q]; i += blockDim.x) z.p[q][i] = 0u;
     const int n1 = N + 1;
     const int rw = row_words_of(N);
     const int64_t total = (int64_t)n1 * n1 * rw;
@@ -600,10 +603,10 @@ cudaError_t launch_classify(const uint32_t* coarse_bin, int N, uint32_t* cand, u
 
 cudaError_t launch_dense_setup(int N, uint32_t* cand, uint32_t* tent, uint32_t* bin,
                                uint32_t* eval, uint32_t* conf0, cudaStream_t stream, int slots,
-                               int64_t fslot) {
+                               int64_t fslot, const ZeroSpans* zero) {
     if (slots < 1 || slots > 65535) return cudaErrorInvalidValue;
     dense_setup_kernel<<<dim3(blocks_for(words_of(N)), (unsigned)slots), 256, 0, stream>>>(
-        N, cand, tent, bin, eval, conf0, fslot);
+        N, cand, tent, bin, eval, conf0, fslot, zero ? *zero : ZeroSpans{});
     return cudaGetLastError();
 }
 

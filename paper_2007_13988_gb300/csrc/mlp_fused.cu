@@ -399,8 +399,15 @@ __device__ __forceinline__ unsigned int fused_index(const FusedPlan& plan, unsig
 
 __global__ void fused_switch_kernel(cudaGraphConditionalHandle h, FusedPlan plan,
                                     const unsigned int* count, unsigned int cap, unsigned int x3_lo,
-                                    unsigned int x3_hi, unsigned int grid_hi) {
-    cudaGraphSetConditional(h, fused_index(plan, min(*count, cap), x3_lo, x3_hi, grid_hi));
+                                    unsigned int x3_hi, unsigned int grid_hi,
+                                    unsigned long long* stat, unsigned int stat_cap,
+                                    unsigned int* err) {
+    const unsigned int v = *count;
+    if (stat) {
+        *stat += v;
+        if (v > stat_cap) atomicOr(err, kErrCapacity);
+    }
+    cudaGraphSetConditional(h, fused_index(plan, min(v, cap), x3_lo, x3_hi, grid_hi));
 }
 
 // One batch of the MIXED forms in the graph as one SWITCH: bodies 0 .. nt-1
@@ -413,7 +420,8 @@ __global__ void batch_switch_kernel(cudaGraphConditionalHandle h, FusedPlan plan
                                     unsigned int* count, unsigned int cap,
                                     unsigned int threshold, int nt, int single,
                                     unsigned int x3_lo, unsigned int x3_hi, unsigned int grid_hi,
-                                    RoundStart rs, int has_rs) {
+                                    RoundStart rs, int has_rs, unsigned int* zero) {
+    if (zero) *zero = 0u;
     unsigned int c;
     if (has_rs) {
         c = *rs.next;
@@ -451,18 +459,22 @@ FusedPlan fused_plan(const FusedNet& net) {
 
 cudaError_t launch_fused_switch(cudaGraphConditionalHandle h, const FusedPlan& plan,
                                 const unsigned int* count, unsigned int cap, cudaStream_t stream,
-                                unsigned int x3_lo, unsigned int x3_hi, unsigned int grid_hi) {
-    fused_switch_kernel<<<1, 1, 0, stream>>>(h, plan, count, cap, x3_lo, x3_hi, grid_hi);
+                                unsigned int x3_lo, unsigned int x3_hi, unsigned int grid_hi,
+                                unsigned long long* stat, unsigned int stat_cap,
+                                unsigned int* err) {
+    fused_switch_kernel<<<1, 1, 0, stream>>>(h, plan, count, cap, x3_lo, x3_hi, grid_hi, stat,
+                                             stat_cap, err);
     return cudaGetLastError();
 }
 
 cudaError_t launch_batch_switch(cudaGraphConditionalHandle h, const FusedPlan& plan,
                                 unsigned int* count, unsigned int cap, unsigned int threshold,
                                 int nt, bool single, unsigned int x3_lo, unsigned int x3_hi,
-                                unsigned int grid_hi, const RoundStart* rs, cudaStream_t stream) {
+                                unsigned int grid_hi, const RoundStart* rs, unsigned int* zero,
+                                cudaStream_t stream) {
     batch_switch_kernel<<<1, 1, 0, stream>>>(h, plan, count, cap, threshold, nt, single ? 1 : 0,
                                              x3_lo, x3_hi, grid_hi, rs ? *rs : RoundStart{},
-                                             rs ? 1 : 0);
+                                             rs ? 1 : 0, zero);
     return cudaGetLastError();
 }
 

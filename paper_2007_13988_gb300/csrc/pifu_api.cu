@@ -519,7 +519,6 @@ int pifu_render(pifu_ctx* ctx, const pifu_camera* cam, const pifu_fmap* occ_map,
     a.hit_pix = ctx->hit_pix;
     a.hit_count = ctx->d_count;
     a.top = ctx->col_top;
-    CK(cudaMemsetAsync(ctx->d_count, 0, sizeof(unsigned int), s));
     cudaEvent_t ev = ctx->prof.begin(s);
     CK(launch_render_rays(a, s));
     {

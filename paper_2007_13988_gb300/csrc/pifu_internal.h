@@ -426,10 +426,19 @@ struct LoopTail {
     unsigned int* err;
 };
 
-// Level-0 set-up: everything empty except eval = all nodes.
+// Up to kMax device spans of 32-bit words that a kernel zeroes on the way
+// (in the graph forms, in place of memset nodes before it).
+struct ZeroSpans {
+    static constexpr int kMax = 3;
+    unsigned int* p[kMax];
+    uint32_t words[kMax];
+};
+// Level-0 set-up: everything empty except eval = all nodes; the spans of
+// `zero` (optional) are zeroed too.
 cudaError_t launch_dense_setup(int N, uint32_t* cand, uint32_t* tent, uint32_t* bin,
                                uint32_t* eval, uint32_t* conf0, cudaStream_t stream,
-                               int slots = 1, int64_t fslot = 0);
+                               int slots = 1, int64_t fslot = 0,
+                               const ZeroSpans* zero = nullptr);
 
 // sel = dilate26(src) & ~eval; eval |= sel; clear[w] = 0 (if non-null);
 // append the node indices of sel to list at *count.
@@ -613,20 +622,25 @@ cudaError_t launch_mlp_fused(const FusedNet& net, const PointSrc& src, int64_t p
 // size the device-resident batch size c = min(*count, cap) calls for; to
 // plan.n when x3_lo < c <= x3_hi (the split-TF32 body, if the switch has
 // one: x3_hi > 0); to a value past every body (no branch) when c is 0.
+// stat (optional): *stat += *count, capacity error bit in *err when *count
+// exceeds stat_cap (launch_accumulate's work, in the same launch).
 cudaError_t launch_fused_switch(cudaGraphConditionalHandle h, const FusedPlan& plan,
                                 const unsigned int* count, unsigned int cap, cudaStream_t stream,
                                 unsigned int x3_lo = 0, unsigned int x3_hi = 0,
-                                unsigned int grid_hi = 0);
+                                unsigned int grid_hi = 0, unsigned long long* stat = nullptr,
+                                unsigned int stat_cap = 0, unsigned int* err = nullptr);
 // Graph form, one evaluation batch of the MIXED forms as one switch `h` of
 // nt + 1 bodies: a device-resident batch of c points, 1 <= c <= threshold,
 // selects an FP32 body (body 0 when single, else launch_fused_switch's index
 // for min(c, cap)); c > threshold selects body nt (the tensor-core pass);
 // c = 0 none.  rs (optional): the batch is a conflict round; c is first
-// moved from *rs->next into *count with round_start's statistics.
+// moved from *rs->next into *count with round_start's statistics.  *zero = 0
+// (optional: the tensor-core body's re-check queue length).
 cudaError_t launch_batch_switch(cudaGraphConditionalHandle h, const FusedPlan& plan,
                                 unsigned int* count, unsigned int cap, unsigned int threshold,
                                 int nt, bool single, unsigned int x3_lo, unsigned int x3_hi,
-                                unsigned int grid_hi, const RoundStart* rs, cudaStream_t stream);
+                                unsigned int grid_hi, const RoundStart* rs, unsigned int* zero,
+                                cudaStream_t stream);
 
 // --- mlp_grid.cu -----------------------------------------------------------
 // The whole network in FP32 for a batch of at most kGridMaxRows points in one
@@ -736,7 +750,7 @@ struct RenderArgs {
     uint8_t* mask;        // may be null
     float* hit_xyz;       // [width*height][3] surface points of hits
     int* hit_pix;         // pixel index per hit
-    unsigned int* hit_count;
+    unsigned int* hit_count;   // zeroed by the launch (before any hit is appended)
     int* top;             // [2][(N+1)^2] scratch per frame: highest non-empty depth node
                           // per column, then N - the lowest
     // Several frames (lockstep form): frame f's volume starts f slot_nodes

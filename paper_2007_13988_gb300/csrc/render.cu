@@ -51,7 +51,10 @@ __global__ void __launch_bounds__(256) column_top_kernel(int N, int row_words,
                                                          const uint32_t* __restrict__ eval,
                                                          const uint32_t* __restrict__ bin,
                                                          int* __restrict__ top, int* __restrict__ bot,
-                                                         int64_t slot_words, int64_t slot_top) {
+                                                         int64_t slot_words, int64_t slot_top,
+                                                         unsigned int* __restrict__ hits) {
+    // the hit list's length, appended to by render_rays_kernel after this launch
+    if (hits && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) *hits = 0u;
     const int n1 = N + 1;
     {
         const int64_t f = blockIdx.y;   // frame of a lockstep batch
@@ -266,7 +269,8 @@ cudaError_t launch_render_rays(const RenderArgs& a, cudaStream_t stream) {
     if (e != cudaSuccess) return e;
     const int64_t nt = n1 * n1 * a.row_words;
     column_top_kernel<<<dim3((unsigned)((nt + 255) / 256), (unsigned)slots), 256, 0, stream>>>(
-        a.N, a.row_words, a.eval, a.bin, a.top, a.top + n1 * n1, a.slot_words, 2 * n1 * n1);
+        a.N, a.row_words, a.eval, a.bin, a.top, a.top + n1 * n1, a.slot_words, 2 * n1 * n1,
+        a.hit_count);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     render_rays_kernel<<<dim3((unsigned)((npix + 255) / 256), (unsigned)slots), 256, 0, stream>>>(a);
@@ -472,7 +476,7 @@ cudaError_t launch_cull_select(const CullArgs& a, cudaStream_t stream) {
     if (e != cudaSuccess) return e;
     const int64_t nt = n1 * n1 * a.row_words;
     column_top_kernel<<<dim3((unsigned)((nt + 255) / 256), 1u), 256, 0, stream>>>(
-        a.Nc, a.row_words, a.bin, a.bin, a.top, nullptr, 0, 0);
+        a.Nc, a.row_words, a.bin, a.bin, a.top, nullptr, 0, 0, nullptr);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     cull_select_kernel<<<(unsigned)((npix + 255) / 256), 256, 0, stream>>>(a);
