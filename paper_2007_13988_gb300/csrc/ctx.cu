@@ -23,6 +23,7 @@ int parse_net(Reader& rd, HostNet& hn, int want_kind) {
     net.kind = (int)kind;
     net.d_in = (int)d_in;
     net.ldx = round_up((int)d_in, 8);
+    net.ldx_tc = round_up((int)d_in, 64);
     net.slope = slope;
     net.layers.assign(n_layers, DevLayer{});
     net.max_hidden = 0;
@@ -208,6 +209,7 @@ int upload_cbn(pifu_ctx* ctx, const HostCbn& h) {
     net.kind = kNetCbn;
     net.d_in = h.C + 1;
     net.ldx = round_up(h.C + 1, 8);
+    net.ldx_tc = round_up(h.C + 1, 64);
     net.max_hidden = h.K;
     net.tc_ok = d.tc_ok;
     d.ready = true;
@@ -316,8 +318,8 @@ __nv_bfloat16* chain_out(pifu_ctx* ctx, const DevNet& net, int l) {
 int encode_act_maps(pifu_ctx* ctx, DevNet& net) {
     if (!net.tc_ok || ctx->tc_rows == 0 || net.kind == kNetCbn) return PIFU_OK;
     const uint64_t rows = (uint64_t)ctx->tc_rows;
-    if (!tc_encode_2d_bf16(&net.tmX, ctx->Xb, (uint64_t)net.d_in, rows, (uint64_t)net.ldx * 2, 64,
-                           128))
+    if (!tc_encode_2d_bf16(&net.tmX, ctx->Xb, (uint64_t)net.ldx_tc, rows,
+                           (uint64_t)net.ldx_tc * 2, 64, 128))
         return PIFU_ERR_CUDA;
     for (size_t l = 1; l < net.tc.size(); ++l) {
         const DevLayer& Ly = net.layers[l];
@@ -377,7 +379,7 @@ int ensure_tc_rows(pifu_ctx* ctx, int64_t rows) {
     cap = std::min<int64_t>(cap, kTcRowsMax);
     int64_t need_x = 0, need_h = 0;
     for (const DevNet& n : ctx->net) {
-        need_x = std::max<int64_t>(need_x, n.ldx);
+        need_x = std::max<int64_t>(need_x, std::max(n.ldx, n.ldx_tc));
         need_h = std::max<int64_t>(need_h, std::max(n.max_hidden, 8));
     }
     invalidate_graphs(ctx);
@@ -409,9 +411,7 @@ int build_tc(pifu_ctx* ctx, const HostNet& hn, DevNet& net) {
         T.nk1 = Ly.K1 / 64;
         T.nk2 = has_x ? k2pad / 64 : 0;
         T.Kw = Ly.K1 + (has_x ? k2pad : 0);
-        // the x part ends at K1 + d_in: the map reads no further, and the
-        // last K-block's MMA steps past d_in (zeros on both sides) are skipped
-        T.Kmap = has_x ? Ly.K1 + net.d_in : T.Kw;
+        // the last K-block's MMA steps past d_in (zeros on both sides) are skipped
         T.klast = has_x ? (net.d_in - 64 * (T.nk2 - 1) + 15) / 16 : 4;
         // single-CTA tiles by default (pifu_autotune / pifu_set_tiles may
         // choose the CTA-pair form)
@@ -429,8 +429,8 @@ int build_tc(pifu_ctx* ctx, const HostNet& hn, DevNet& net) {
         }
         CK(dev_alloc(&T.W, (int64_t)wb.size()));
         CK(cudaMemcpy(T.W, wb.data(), wb.size() * sizeof(__nv_bfloat16), cudaMemcpyHostToDevice));
-        if (!tc_encode_2d_bf16(&T.tmW, T.W, (uint64_t)T.Kmap, (uint64_t)Ly.n_out,
-                               (uint64_t)T.Kw * 2, 64, (uint32_t)(T.pair ? T.BN / 2 : T.BN)))
+        if (!tc_encode_2d_bf16(&T.tmW, T.W, (uint64_t)T.Kw, (uint64_t)Ly.n_out, (uint64_t)T.Kw * 2,
+                               64, (uint32_t)(T.pair ? T.BN / 2 : T.BN)))
             return PIFU_ERR_CUDA;
     }
     net.tc_ok = true;
@@ -569,9 +569,8 @@ int build_fp8(pifu_ctx* ctx, DevNet& net, int F, const std::vector<float>& s_h) 
             Q.bf16_in = true;
             Q.nk1 = T.nk1;
             Q.Kw = T.Kw;
-            Q.Kmap = T.Kmap;
             Q.Wmap = T.W;
-            if (!tc_encode_2d_bf16(&Q.tmW, T.W, (uint64_t)Q.Kmap, (uint64_t)Ly.n_out,
+            if (!tc_encode_2d_bf16(&Q.tmW, T.W, (uint64_t)T.Kw, (uint64_t)Ly.n_out,
                                    (uint64_t)T.Kw * 2, 64, (uint32_t)Q.BN))
                 return PIFU_ERR_CUDA;
             continue;
@@ -579,7 +578,6 @@ int build_fp8(pifu_ctx* ctx, DevNet& net, int F, const std::vector<float>& s_h) 
         const bool has_x = Ly.K2 > 0;
         Q.nk1 = Ly.K1 / 128;
         Q.Kw = Ly.K1 + Q.nk2 * 128;   // bytes
-        Q.Kmap = has_x ? Ly.K1 + 2 * net.d_in : Q.Kw;
         const float s_a = s_h[(size_t)l - 1];
         std::vector<float> wf((size_t)Ly.n_out * Ly.ldw);
         CK(cudaMemcpy(wf.data(), Ly.W, wf.size() * 4, cudaMemcpyDeviceToHost));
@@ -604,7 +602,7 @@ int build_fp8(pifu_ctx* ctx, DevNet& net, int F, const std::vector<float>& s_h) 
         CK(cudaMemcpy(Q.W, w8.data(), w8.size(), cudaMemcpyHostToDevice));
         CK(cudaMemcpy(Q.colscale, cs.data(), cs.size() * 4, cudaMemcpyHostToDevice));
         Q.Wmap = Q.W;
-        if (!tc_encode_2d_u8(&Q.tmW, Q.W, (uint64_t)Q.Kmap, (uint64_t)Ly.n_out, (uint64_t)Q.Kw, 128,
+        if (!tc_encode_2d_u8(&Q.tmW, Q.W, (uint64_t)Q.Kw, (uint64_t)Ly.n_out, (uint64_t)Q.Kw, 128,
                              (uint32_t)Q.BN))
             return PIFU_ERR_CUDA;
     }

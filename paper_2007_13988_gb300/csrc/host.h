@@ -51,10 +51,7 @@ struct DevLayer {
 struct TcLayer {
     __nv_bfloat16* W = nullptr;
     int Kw = 0, nk1 = 0, nk2 = 0, BN = 0;
-    // tmW's row extent: K1 + d_in with an x part, so the x part's padding
-    // to a whole K-block is the map's zero fill, not bytes read; klast: the
-    // 16-value MMA steps of the last K-block that reach a real column
-    int Kmap = 0, klast = 4;
+    int klast = 4;        // the 16-value MMA steps of the last K-block that reach a real column
     bool pair = false;    // CTA-pair form (BN = 256; tmW's box is then 128 rows)
     CUtensorMap tmW{};
     CUtensorMap tmA1{};   // the previous layer's BF16 output (l >= 1)
@@ -76,7 +73,7 @@ struct Fp8Layer {
     const void* Wmap = nullptr;  // the weights tmW covers
     float* colscale = nullptr;   // [n_out] (later layers)
     int Kw = 0, nk1 = 0, nk2 = 0, BN = 0;   // Kw: row width in the map's elements
-    int Kmap = 0, klast = 4;                // as in TcLayer (Kmap in the map's elements)
+    int klast = 4;                          // as in TcLayer
     float out_scale = 1.f;       // E4M3 output: 1 / s of the next layer's input
     CUtensorMap tmW{};
     CUtensorMap tmA1{};          // the previous layer's E4M3 output (layer >= 1)
@@ -96,6 +93,8 @@ struct DevNet {
     int kind = 0;       // 0 occupancy (sigmoid), 1 colour (tanh01)
     int d_in = 0;
     int ldx = 0;        // gather row width: d_in rounded up to 8
+    int ldx_tc = 0;     // BF16 tensor-core input row width: d_in rounded up to 64 (whole
+                        // K-blocks, the padding zero), so no TMA box reads past a row
     float slope = 0.01f;
     int max_hidden = 0;
     std::vector<DevLayer> layers;
@@ -744,8 +743,7 @@ int g_enqueue_batch(pifu_ctx* ctx, const BatchKey& k);
 int b_build(pifu_ctx* ctx, const BatchKey& k);
 bool encode_w(bool fp8, CUtensorMap* tmW, void* Wdev, int Kw, int n_out, int code);
 int tune_layer(pifu_ctx* ctx, const TcLayerArgs& base, int n_out, bool fp8, bool allow_pair,
-               CUtensorMap* tmW, void* Wdev, int Kw, int Kmap, int* code, cudaStream_t s,
-               double* best_ms);
+               CUtensorMap* tmW, void* Wdev, int Kw, int* code, cudaStream_t s, double* best_ms);
 int autotune(pifu_ctx* ctx, int64_t rows, cudaStream_t s, int32_t* bn_out, double* ms_out,
              int n_max, int* n_done);
 int set_tiles(pifu_ctx* ctx, const int32_t* codes, int n);

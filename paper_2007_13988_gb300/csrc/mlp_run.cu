@@ -44,9 +44,9 @@ int run_mlp_tc(pifu_ctx* ctx, const DevNet& net, const PointSrc& src_in, int64_t
     for (int64_t p0 = 0; p0 < m; p0 += chunk) {
         const int64_t mc = std::min<int64_t>(chunk, m - p0);
         cudaEvent_t ev = pr.begin(s);
-        CK(launch_gather_bf16(src, p0, mc, calib, map0, map1, ctx->Xb, net.ldx, s));
+        CK(launch_gather_bf16(src, p0, mc, calib, map0, map1, ctx->Xb, net.ldx_tc, s));
         pr.end(PIFU_K_GATHER, ev, s, 0.0,
-               (double)mc * (4.0 * 4.0 * (map0.C + map1.C) + 2.0 * net.ldx));
+               (double)mc * (4.0 * 4.0 * (map0.C + map1.C) + 2.0 * net.ldx_tc));
         // the last layer rides in the last hidden layer's epilogue when that
         // layer is one tile wide and the last layer reads only its output
         const DevLayer& Ll = net.layers[L - 1];
@@ -158,7 +158,7 @@ int run_mlp_tc(pifu_ctx* ctx, const DevNet& net, const PointSrc& src_in, int64_t
             const __nv_bfloat16* h = L > 1 ? ctx->Hb[(L - 2) % 2] : nullptr;
             const int hw = L > 1 ? net.layers[L - 2].n_out : 0;
             ev = pr.begin(s);
-            CK(launch_last_layer_bf16(p0, mc, Ll.n_out, h, hw, Ll.K1, ctx->Xb, net.ldx, Ll.K2,
+            CK(launch_last_layer_bf16(p0, mc, Ll.n_out, h, hw, Ll.K1, ctx->Xb, net.ldx_tc, Ll.K2,
                                       Ll.W, Ll.ldw, Ll.b, epi, s, m_dev));
             pr.end(PIFU_K_MLP_LAST, ev, s, 2.0 * mc * Ll.fan_in * Ll.n_out,
                    2.0 * (double)mc * (Ll.fan_in + Ll.n_out));

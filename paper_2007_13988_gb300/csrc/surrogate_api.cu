@@ -61,6 +61,7 @@ void sur_bind(pifu_ctx* ctx) {
     n.kind = 0;
     n.d_in = fo.d_in;
     n.ldx = fo.ldx;
+    n.ldx_tc = fo.ldx_tc;
     n.slope = fo.slope;
     n.max_hidden = std::max(S.h1, S.h2);
     n.layers.assign(3, DevLayer{});

@@ -16,19 +16,15 @@ namespace pifu_host {
 // the CTA-pair form (two CTAs on a 256 x 256 tile, BF16 layers only).
 constexpr int kPairCode = 512;
 
-// Kw: the row pitch in the map's elements; Kmap: the row extent the map
-// reads (the layer's Kmap).
-bool encode_w(bool fp8, CUtensorMap* tmW, void* Wdev, int Kw, int Kmap, int n_out, int code) {
+bool encode_w(bool fp8, CUtensorMap* tmW, void* Wdev, int Kw, int n_out, int code) {
     const uint32_t box = (uint32_t)(code == kPairCode ? 128 : code);
-    return fp8 ? tc_encode_2d_u8(tmW, Wdev, (uint64_t)Kmap, (uint64_t)n_out, (uint64_t)Kw, 128,
-                                 box)
-               : tc_encode_2d_bf16(tmW, Wdev, (uint64_t)Kmap, (uint64_t)n_out, (uint64_t)Kw * 2,
-                                   64, box);
+    return fp8 ? tc_encode_2d_u8(tmW, Wdev, (uint64_t)Kw, (uint64_t)n_out, (uint64_t)Kw, 128, box)
+               : tc_encode_2d_bf16(tmW, Wdev, (uint64_t)Kw, (uint64_t)n_out, (uint64_t)Kw * 2, 64,
+                                   box);
 }
 
 int tune_layer(pifu_ctx* ctx, const TcLayerArgs& base, int n_out, bool fp8, bool allow_pair,
-               CUtensorMap* tmW, void* Wdev, int Kw, int Kmap, int* code, cudaStream_t s,
-               double* best_ms) {
+               CUtensorMap* tmW, void* Wdev, int Kw, int* code, cudaStream_t s, double* best_ms) {
     const int cands[4] = {64, 128, 256, kPairCode};
     int best = *code;
     double best_t = 1e30;
@@ -39,7 +35,7 @@ int tune_layer(pifu_ctx* ctx, const TcLayerArgs& base, int n_out, bool fp8, bool
     for (int c : cands) {
         const bool pair = c == kPairCode;
         if (st != PIFU_OK || (pair ? !allow_pair || n_out % 256 != 0 : n_out % c != 0)) continue;
-        if (!encode_w(fp8, tmW, Wdev, Kw, Kmap, n_out, c)) {
+        if (!encode_w(fp8, tmW, Wdev, Kw, n_out, c)) {
             st = PIFU_ERR_CUDA;
             break;
         }
@@ -68,7 +64,7 @@ int tune_layer(pifu_ctx* ctx, const TcLayerArgs& base, int n_out, bool fp8, bool
     if (st != PIFU_OK) return st;
     *best_ms = best_t / 3.0;
     *code = best;
-    return encode_w(fp8, tmW, Wdev, Kw, Kmap, n_out, best) ? PIFU_OK : PIFU_ERR_CUDA;
+    return encode_w(fp8, tmW, Wdev, Kw, n_out, best) ? PIFU_OK : PIFU_ERR_CUDA;
 }
 
 int autotune(pifu_ctx* ctx, int64_t rows, cudaStream_t s, int32_t* bn_out, double* ms_out,
@@ -116,7 +112,7 @@ int autotune(pifu_ctx* ctx, int64_t rows, cudaStream_t s, int32_t* bn_out, doubl
                 a.out_scale = Q.out_scale;
                 double ms = 0.0;
                 st = tune_layer(ctx, a, Ly.n_out, !Q.bf16_in, false, &Q.tmW,
-                                const_cast<void*>(Q.Wmap), Q.Kw, Q.Kmap, &Q.BN, s, &ms);
+                                const_cast<void*>(Q.Wmap), Q.Kw, &Q.BN, s, &ms);
                 if (st != PIFU_OK) return st;
                 record(Q.BN, ms);
             }
@@ -135,8 +131,7 @@ int autotune(pifu_ctx* ctx, int64_t rows, cudaStream_t s, int32_t* bn_out, doubl
             a.out_scale = 1.f;
             double ms = 0.0;
             int code = T.pair ? kPairCode : T.BN;
-            st = tune_layer(ctx, a, Ly.n_out, false, true, &T.tmW, T.W, T.Kw, T.Kmap, &code, s,
-                            &ms);
+            st = tune_layer(ctx, a, Ly.n_out, false, true, &T.tmW, T.W, T.Kw, &code, s, &ms);
             if (st != PIFU_OK) return st;
             T.pair = code == kPairCode;
             T.BN = T.pair ? 256 : code;
@@ -196,12 +191,12 @@ int set_tiles(pifu_ctx* ctx, const int32_t* codes, int n) {
         const int c = codes[i++];
         if (q) {
             q->BN = c;
-            ok = ok && encode_w(!q->bf16_in, &q->tmW, const_cast<void*>(q->Wmap), q->Kw,
-                                q->Kmap, n_out, c);
+            ok = ok && encode_w(!q->bf16_in, &q->tmW, const_cast<void*>(q->Wmap), q->Kw, n_out,
+                                c);
         } else {
             t->pair = c == kPairCode;
             t->BN = t->pair ? 256 : c;
-            ok = ok && encode_w(false, &t->tmW, t->W, t->Kw, t->Kmap, n_out, c);
+            ok = ok && encode_w(false, &t->tmW, t->W, t->Kw, n_out, c);
         }
     });
     ctx->g_valid = false;
