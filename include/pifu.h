@@ -185,7 +185,8 @@ typedef struct {
  * PIFU_ERR_ARG (null pointers). */
 int pifu_create(const void* weight_blob, size_t bytes, pifu_ctx** out);
 
-/* Release the context and all its device memory.  NULL is a no-op. */
+/* Release the context and all its device memory (after waiting for the
+ * device when pifu_frame_async frames are pending).  NULL is a no-op. */
 void pifu_destroy(pifu_ctx* ctx);
 
 /* Eq. 1 at m arbitrary points: occ_dev[p] = O(pts_dev[3p .. 3p+2]).

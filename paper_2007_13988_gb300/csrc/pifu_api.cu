@@ -87,6 +87,8 @@ int pifu_create(const void* weight_blob, size_t bytes, pifu_ctx** out) {
 void pifu_destroy(pifu_ctx* ctx) {
     if (!ctx) return;
     DeviceGuard g(ctx->device);
+    // frames from pifu_frame_async may still run on the context's buffers
+    if (ctx->async_frames > 0) (void)cudaDeviceSynchronize();
     batch_free(ctx);
     {
         BatchWs& bw = ctx->batch;
