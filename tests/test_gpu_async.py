@@ -131,3 +131,32 @@ def test_async_host_errors_enqueue_nothing(tiny):
     with pytest.raises(pifu.PifuError) as ei:
         pifu.pifu_frame_wait(c.ctx, torch.cuda.current_stream())
     assert ei.value.status == pifu.PIFU_ERR_STATE
+
+
+def test_destroy_with_frames_pending():
+    # pifu_destroy waits for the frames still in flight before it releases
+    # their graph and buffers; a context made afterwards works as before
+    import torch
+    w = synth.tiny(0)
+    c = Ctx(w)
+    depth, rgb, mask = outputs()
+    a, kw = frame_args(c, depth, rgb, mask, precision=pifu.PIFU_PREC_MIXED)
+    vol = pifu.pifu_frame(*a, **kw)
+    torch.cuda.synchronize()
+    ref = (host(depth), host(mask), int(vol.n_eval))
+    for _ in range(3):
+        pifu.pifu_frame_async(*a, **kw)
+    c.close()                                      # frames pending
+    torch.cuda.synchronize()
+    for g, r in zip((host(depth), host(mask)), ref[:2]):
+        assert same(g, r)                          # the frames ran to the end
+    c2 = Ctx(w)
+    try:
+        a2, kw2 = frame_args(c2, depth, rgb, mask, precision=pifu.PIFU_PREC_MIXED)
+        vol = pifu.pifu_frame(*a2, **kw2)
+        torch.cuda.synchronize()
+        assert int(vol.n_eval) == ref[2]
+        assert same(host(depth), ref[0])
+    finally:
+        c2.close()
+
