@@ -197,6 +197,9 @@ __global__ void __launch_bounds__(kThreads, 1) tc_linear_kernel(
                     tma_load_2d(sB + s * B_BYTES, &tmW, kb * EW, n0, &full[s]);
                 }
             }
+            // every load of this CTA is issued: the next layer's CTAs may be
+            // placed (and run their prologue) as SMs free up
+            griddep_launch_dependents();
         }
     } else if (warp == 1) {
         if (lane == 0) {

@@ -109,6 +109,14 @@ __device__ __forceinline__ void griddep_wait() {
     asm volatile("griddepcontrol.wait;" ::: "memory");
 }
 
+// This CTA no longer holds back the kernels launched after it as
+// programmatic dependents: once every CTA of the grid has signalled (or
+// exited) they may be scheduled, and they still wait for this grid's
+// completion in griddep_wait before reading its results.
+__device__ __forceinline__ void griddep_launch_dependents() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // ---- TMA ----------------------------------------------------------------------
 
 // Contiguous bulk copy of `bytes` from global to this CTA's shared memory,
