@@ -10,6 +10,7 @@
 #include <cuda_fp8.h>
 
 #include "gather.cuh"
+#include "sm100.cuh"
 
 namespace pifu {
 namespace {
@@ -44,6 +45,10 @@ template <typename OutT>
 __global__ void __launch_bounds__(256) gather_kernel(PointSrc src, int64_t p0, int64_t m,
                                                      Calib calib, Map map0, Map map1,
                                                      OutT* __restrict__ X, int ldx) {
+    // a programmatic dependent of the kernel before it (which may write the
+    // point list or the hits it reads); its own dependents may be placed now
+    sm100::griddep_wait();
+    sm100::griddep_launch_dependents();
     const int nq = ldx >> 2;
     if (src.count) m = min(m, (int64_t)*src.count);
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < m * kTPP;
@@ -99,9 +104,8 @@ cudaError_t launch_gather(const PointSrc& src, int64_t p0, int64_t m, const Cali
                           cudaStream_t stream) {
     if (m <= 0) return cudaSuccess;
     const int64_t total = m * kTPP;
-    gather_kernel<float><<<gather_blocks(src, total), 256, 0, stream>>>(src, p0, m, calib, map0,
-                                                                       map1, X, ldx);
-    return cudaGetLastError();
+    return launch_pdl(gather_kernel<float>, dim3(gather_blocks(src, total)), dim3(256), 0, stream,
+                      src, p0, m, calib, map0, map1, X, ldx);
 }
 
 cudaError_t launch_gather_bf16(const PointSrc& src, int64_t p0, int64_t m, const Calib& calib,
@@ -109,9 +113,8 @@ cudaError_t launch_gather_bf16(const PointSrc& src, int64_t p0, int64_t m, const
                                cudaStream_t stream) {
     if (m <= 0) return cudaSuccess;
     const int64_t total = m * kTPP;
-    gather_kernel<__nv_bfloat16><<<gather_blocks(src, total), 256, 0, stream>>>(src, p0, m, calib,
-                                                                               map0, map1, X, ldx);
-    return cudaGetLastError();
+    return launch_pdl(gather_kernel<__nv_bfloat16>, dim3(gather_blocks(src, total)), dim3(256), 0,
+                      stream, src, p0, m, calib, map0, map1, X, ldx);
 }
 
 }  // namespace pifu

@@ -17,6 +17,7 @@
 #include <algorithm>
 
 #include "pifu_internal.h"
+#include "sm100.cuh"
 
 namespace pifu {
 namespace {
@@ -119,6 +120,7 @@ __global__ void __launch_bounds__(256) classify_kernel(const uint32_t* __restric
                                                        int64_t cslot, int64_t fslot,
                                                        unsigned long long* __restrict__ cands,
                                                        unsigned int* __restrict__ zero) {
+    sm100::griddep_launch_dependents();   // the selection waits for this grid
     {
         const int64_t f = blockIdx.y;
         coarse += f * cslot;
@@ -183,6 +185,7 @@ __global__ void __launch_bounds__(256) dense_setup_kernel(int N, uint32_t* __res
                                                           uint32_t* __restrict__ eval,
                                                           uint32_t* __restrict__ conf0,
                                                           int64_t fslot, ZeroSpans z) {
+    sm100::griddep_launch_dependents();   // the gather after it waits for this grid
     if (blockIdx.x == 0 && blockIdx.y == 0)
         for (int q = 0; q < ZeroSpans::kMax; ++q)
             for (uint32_t i = threadIdx.x; i < z.words[q]; i += blockDim.x) z.p[q][i] = 0u;
@@ -233,6 +236,7 @@ __global__ void __launch_bounds__(256) dilate_select_kernel(const uint32_t* __re
                                                             unsigned int* __restrict__ count,
                                                             int64_t fslot, int64_t slot_nodes,
                                                             int radius, LoopTail tail) {
+    sm100::griddep_wait();   // a programmatic dependent of the level's classify
     {
         const int64_t f = blockIdx.y;
         src += f * fslot;
@@ -614,16 +618,16 @@ cudaError_t launch_dilate_select(const uint32_t* src, uint32_t* eval, uint32_t* 
                                  int* list, unsigned int* count, cudaStream_t stream, int slots,
                                  int64_t fslot, int64_t slot_nodes, const LoopTail* tail) {
     if (slots < 1 || slots > 65535) return cudaErrorInvalidValue;
-    dilate_select_kernel<<<dim3(blocks_for(words_of(N)), (unsigned)slots), 256, 0, stream>>>(
-        src, eval, clear, N, list, count, fslot, slot_nodes, 1, tail ? *tail : LoopTail{});
-    return cudaGetLastError();
+    return launch_pdl(dilate_select_kernel, dim3(blocks_for(words_of(N)), (unsigned)slots),
+                      dim3(256), 0, stream, src, eval, clear, N, list, count, fslot, slot_nodes, 1,
+                      tail ? *tail : LoopTail{});
 }
 
 cudaError_t launch_select(const uint32_t* src, uint32_t* eval, int N, int* list,
                           unsigned int* count, cudaStream_t stream) {
-    dilate_select_kernel<<<blocks_for(words_of(N)), 256, 0, stream>>>(src, eval, nullptr, N, list,
-                                                                    count, 0, 0, 0, LoopTail{});
-    return cudaGetLastError();
+    return launch_pdl(dilate_select_kernel, dim3(blocks_for(words_of(N))), dim3(256), 0, stream,
+                      src, eval, static_cast<uint32_t*>(nullptr), N, list, count, (int64_t)0,
+                      (int64_t)0, 0, LoopTail{});
 }
 
 cudaError_t launch_threshold_select(const float* coarse, int N, float thr, float* values,

@@ -38,6 +38,7 @@
 
 #include "epilogue.cuh"
 #include "gather.cuh"
+#include "sm100.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -402,6 +403,7 @@ __global__ void fused_switch_kernel(cudaGraphConditionalHandle h, FusedPlan plan
                                     unsigned int x3_hi, unsigned int grid_hi,
                                     unsigned long long* stat, unsigned int stat_cap,
                                     unsigned int* err) {
+    sm100::griddep_wait();   // a programmatic dependent of the pass that fills the queue
     const unsigned int v = *count;
     if (stat) {
         *stat += v;
@@ -462,9 +464,8 @@ cudaError_t launch_fused_switch(cudaGraphConditionalHandle h, const FusedPlan& p
                                 unsigned int x3_lo, unsigned int x3_hi, unsigned int grid_hi,
                                 unsigned long long* stat, unsigned int stat_cap,
                                 unsigned int* err) {
-    fused_switch_kernel<<<1, 1, 0, stream>>>(h, plan, count, cap, x3_lo, x3_hi, grid_hi, stat,
-                                             stat_cap, err);
-    return cudaGetLastError();
+    return launch_pdl(fused_switch_kernel, dim3(1), dim3(1), 0, stream, h, plan, count, cap, x3_lo,
+                      x3_hi, grid_hi, stat, stat_cap, err);
 }
 
 cudaError_t launch_batch_switch(cudaGraphConditionalHandle h, const FusedPlan& plan,

@@ -10,7 +10,29 @@
 
 #include "stream_sched.cuh"
 
+#include <utility>
+
 namespace pifu {
+
+// A launch as a programmatic dependent of the kernel before it on the stream
+// (the launch may be placed before that kernel has finished; the kernel must
+// call griddepcontrol.wait before touching anything the earlier kernel
+// writes or reads).
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                       cudaStream_t stream, Args&&... args) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = stream;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
 
 constexpr float kHalf = 0.5f;
 

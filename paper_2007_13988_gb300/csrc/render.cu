@@ -17,6 +17,7 @@
 #include <algorithm>
 
 #include "pifu_internal.h"
+#include "sm100.cuh"
 
 namespace pifu {
 namespace {
@@ -53,6 +54,7 @@ __global__ void __launch_bounds__(256) column_top_kernel(int N, int row_words,
                                                          int* __restrict__ top, int* __restrict__ bot,
                                                          int64_t slot_words, int64_t slot_top,
                                                          unsigned int* __restrict__ hits) {
+    sm100::griddep_launch_dependents();   // the rays wait for this grid
     // the hit list's length, appended to by render_rays_kernel after this launch
     if (hits && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) *hits = 0u;
     const int n1 = N + 1;
@@ -179,6 +181,10 @@ __device__ __forceinline__ void ray_outputs(const RenderArgs& a, int64_t pix, bo
 }
 
 __global__ void __launch_bounds__(256) render_rays_kernel(RenderArgs a) {
+    // a programmatic dependent of the column table; the colour gather after
+    // it waits for this grid
+    sm100::griddep_wait();
+    sm100::griddep_launch_dependents();
     const int64_t npix = (int64_t)a.width * a.height;
     const int64_t pix = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t frame = blockIdx.y;   // frame of a lockstep batch (0: one frame)
@@ -273,8 +279,8 @@ cudaError_t launch_render_rays(const RenderArgs& a, cudaStream_t stream) {
         a.hit_count);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    render_rays_kernel<<<dim3((unsigned)((npix + 255) / 256), (unsigned)slots), 256, 0, stream>>>(a);
-    return cudaGetLastError();
+    return launch_pdl(render_rays_kernel, dim3((unsigned)((npix + 255) / 256), (unsigned)slots),
+                      dim3(256), 0, stream, a);
 }
 
 cudaError_t launch_stream_render(const SlotView* sv, int slots, int N_fine, const RenderArgs& a,
