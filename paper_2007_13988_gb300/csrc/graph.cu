@@ -19,17 +19,51 @@ int64_t launches_now(const pifu_ctx* ctx);
 // (x3_usable), a queue of more than x3_min_rows and at most kX3Rows points
 // runs that network (one more body each of the same switch).  An empty queue
 // launches nothing.
+// The FP32 forms a device-sized batch of at most `cap` points may take:
+// the plan's cluster sizes, then the split-TF32 network (x3), then the
+// whole-GPU network (ghi > 0: batches of at most ghi points); single: one
+// form only (the cluster network at its default size), so no switch.
+struct Fp32Forms {
+    FusedPlan plan;
+    int64_t x3_lo = 0, ghi = 0;
+    bool x3 = false, single = true;
+    int n = 1;   // bodies of the switch
+};
+
+Fp32Forms fp32_forms(pifu_ctx* ctx, const DevNet& net, int64_t cap) {
+    Fp32Forms f;
+    const FusedNet fz = fused_of(net);
+    const bool sw = net.kind != kNetCbn && ctx->cap_stream4 && fused_ok(fz);
+    if (sw) f.plan = fused_plan(fz);
+    f.x3_lo = x3_min_rows(ctx);
+    f.x3 = sw && f.plan.n >= 1 && x3_usable(ctx, net) && cap > f.x3_lo;
+    f.ghi = sw && f.plan.n >= 1 ? std::min<int64_t>(grid_rows(ctx, net), cap) : 0;
+    f.single = f.plan.n <= 1 && !f.x3 && f.ghi <= 0;
+    f.n = f.single ? 1 : f.plan.n + (f.x3 ? 1 : 0) + (f.ghi > 0 ? 1 : 0);
+    return f;
+}
+
+// Body i of a switch over fp32_forms(ctx, net, cap), captured on s.
+int fp32_form_body(pifu_ctx* ctx, const DevNet& net, const Fp32Forms& f, int i,
+                   const PointSrc& src, int64_t cap, const Map& map, const Calib& cal,
+                   const Epilogue& epi, cudaStream_t s, const unsigned int* m_dev) {
+    if (f.single)
+        return run_mlp(ctx, net, src, cap, map, Map{}, cal, epi, s, PIFU_PREC_FP32, m_dev);
+    if (i < f.plan.n)
+        return run_mlp(ctx, net, src, cap, map, Map{}, cal, epi, s, PIFU_PREC_FP32, m_dev,
+                       f.plan.cl[i]);
+    if (f.x3 && i == f.plan.n)
+        return run_mlp_x3(ctx, net, src, std::min<int64_t>(cap, kX3Rows), map, Map{}, cal, epi, s,
+                          m_dev);
+    return run_mlp_grid(ctx, net, src, f.ghi, map, Map{}, cal, epi, s, m_dev);
+}
+
 int g_recheck(pifu_ctx* ctx, const DevNet& net, const PointSrc& src, int64_t cap,
               const Map& map, const Calib& cal, const Epilogue& epi, cudaStream_t s,
               const unsigned int* m_dev, unsigned long long* stat, unsigned int stat_cap) {
-    const FusedNet fz = fused_of(net);
-    const bool sw = net.kind != kNetCbn && ctx->cap_stream4 && s != ctx->cap_stream4 &&
-                    fused_ok(fz);
-    const FusedPlan plan = sw ? fused_plan(fz) : FusedPlan{};
-    const int64_t x3_lo = x3_min_rows(ctx);
-    const bool x3 = sw && plan.n >= 1 && x3_usable(ctx, net) && cap > x3_lo;
-    const int64_t ghi = sw && plan.n >= 1 ? std::min<int64_t>(grid_rows(ctx, net), cap) : 0;
-    if (plan.n <= 1 && !x3 && ghi <= 0) {
+    Fp32Forms f = fp32_forms(ctx, net, cap);
+    if (s == ctx->cap_stream4) f = Fp32Forms{};   // inside a switch body: one form, no switch
+    if (f.single) {
         if (stat) CK(launch_accumulate(stat, m_dev, stat_cap, ctx->d_count + 1, s));
         return run_mlp(ctx, net, src, cap, map, Map{}, cal, epi, s, PIFU_PREC_FP32, m_dev);
     }
@@ -38,10 +72,10 @@ int g_recheck(pifu_ctx* ctx, const DevNet& net, const PointSrc& src, int64_t cap
     CK(cudaStreamGetCaptureInfo(s, &cs, nullptr, &cg, nullptr, nullptr, nullptr));
     cudaGraphConditionalHandle h;
     CK(cudaGraphConditionalHandleCreate(&h, cg, 0, 0));
-    CK(launch_fused_switch(h, plan, m_dev, (unsigned)cap, s, x3 ? (unsigned)x3_lo : 0u,
-                           x3 ? (unsigned)kX3Rows : 0u, ghi > 0 ? (unsigned)ghi : 0u, stat,
+    CK(launch_fused_switch(h, f.plan, m_dev, (unsigned)cap, s, f.x3 ? (unsigned)f.x3_lo : 0u,
+                           f.x3 ? (unsigned)kX3Rows : 0u, f.ghi > 0 ? (unsigned)f.ghi : 0u, stat,
                            stat_cap, ctx->d_count + 1));
-    const int nb = plan.n + (x3 ? 1 : 0) + (ghi > 0 ? 1 : 0);
+    const int nb = f.n;
     cudaGraph_t bodies[6] = {};
     int st = g_add_switch(ctx, s, h, nb, bodies);
     if (st != PIFU_OK) return st;
@@ -50,14 +84,7 @@ int g_recheck(pifu_ctx* ctx, const DevNet& net, const PointSrc& src, int64_t cap
     for (int i = 0; i < nb; ++i) {
         CK(cudaStreamBeginCaptureToGraph(s4, bodies[i], nullptr, nullptr, 0,
                                          cudaStreamCaptureModeThreadLocal));
-        if (i < plan.n)
-            st = run_mlp(ctx, net, src, cap, map, Map{}, cal, epi, s4, PIFU_PREC_FP32, m_dev,
-                         plan.cl[i]);
-        else if (x3 && i == plan.n)
-            st = run_mlp_x3(ctx, net, src, std::min<int64_t>(cap, kX3Rows), map, Map{}, cal, epi,
-                            s4, m_dev);
-        else
-            st = run_mlp_grid(ctx, net, src, ghi, map, Map{}, cal, epi, s4, m_dev);
+        st = fp32_form_body(ctx, net, f, i, src, cap, map, cal, epi, s4, m_dev);
         cudaGraph_t out = nullptr;
         const cudaError_t ee = cudaStreamEndCapture(s4, &out);
         if (st != PIFU_OK) return st;
@@ -124,17 +151,11 @@ int g_eval(pifu_ctx* ctx, const DevNet& net, const PointSrc& src, int64_t cap,
         CK(cudaGraphConditionalHandleCreate(&h, cg, 0, 0));
         cudaStream_t s3 = ctx->cap_stream3;
         // the FP32 forms g_recheck would switch between for this capacity
-        const FusedNet fz = fused_of(net);
-        const bool sw = net.kind != kNetCbn && ctx->cap_stream4 && fused_ok(fz);
-        const FusedPlan plan = sw ? fused_plan(fz) : FusedPlan{};
-        const int64_t x3_lo = x3_min_rows(ctx);
-        const bool x3 = sw && plan.n >= 1 && x3_usable(ctx, net) && cap > x3_lo;
-        const int64_t ghi = sw && plan.n >= 1 ? std::min<int64_t>(grid_rows(ctx, net), cap) : 0;
-        const bool single = plan.n <= 1 && !x3 && ghi <= 0;
-        const int nt = single ? 1 : plan.n + (x3 ? 1 : 0) + (ghi > 0 ? 1 : 0);
-        CK(launch_batch_switch(h, plan, const_cast<unsigned int*>(m_dev), (unsigned)cap,
-                               (unsigned)kTinyBatch, nt, single, x3 ? (unsigned)x3_lo : 0u,
-                               x3 ? (unsigned)kX3Rows : 0u, ghi > 0 ? (unsigned)ghi : 0u, rs,
+        const Fp32Forms f = fp32_forms(ctx, net, cap);
+        const int nt = f.n;
+        CK(launch_batch_switch(h, f.plan, const_cast<unsigned int*>(m_dev), (unsigned)cap,
+                               (unsigned)kTinyBatch, nt, f.single, f.x3 ? (unsigned)f.x3_lo : 0u,
+                               f.x3 ? (unsigned)kX3Rows : 0u, f.ghi > 0 ? (unsigned)f.ghi : 0u, rs,
                                ctx->d_recheck, s));
         cudaGraph_t bodies[8] = {};
         int st = g_add_switch(ctx, s, h, nt + 1, bodies);
@@ -147,16 +168,8 @@ int g_eval(pifu_ctx* ctx, const DevNet& net, const PointSrc& src, int64_t cap,
             if (i == nt)
                 st = g_eval(ctx, net, src, cap, m_dev, map, cal, epi, prec, margin, rechecked, s3,
                             false, 0.f, nullptr, 0, nullptr, true);
-            else if (single)
-                st = run_mlp(ctx, net, src, cap, map, Map{}, cal, epi, s3, PIFU_PREC_FP32, m_dev);
-            else if (i < plan.n)
-                st = run_mlp(ctx, net, src, cap, map, Map{}, cal, epi, s3, PIFU_PREC_FP32, m_dev,
-                             plan.cl[i]);
-            else if (x3 && i == plan.n)
-                st = run_mlp_x3(ctx, net, src, std::min<int64_t>(cap, kX3Rows), map, Map{}, cal,
-                                epi, s3, m_dev);
             else
-                st = run_mlp_grid(ctx, net, src, ghi, map, Map{}, cal, epi, s3, m_dev);
+                st = fp32_form_body(ctx, net, f, i, src, cap, map, cal, epi, s3, m_dev);
             cudaGraph_t out = nullptr;
             const cudaError_t ee = cudaStreamEndCapture(s3, &out);
             if (st != PIFU_OK) return st;
