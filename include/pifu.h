@@ -16,7 +16,9 @@
  *   Host pointers are read during the call only.
  * - `stream` is a cudaStream_t passed as void* (NULL = legacy default
  *   stream).  Work is enqueued on it; the calls that need a host decision
- *   (pifu_localize, pifu_render) synchronise it internally.
+ *   (pifu_localize, pifu_render) synchronise it internally, the graph forms
+ *   once per call, and pifu_frame_async not at all (its device-side errors
+ *   wait for pifu_frame_wait).
  * - Every call returns a pifu_status.  Errors detectable on the host return
  *   before any work is enqueued.  A CUDA error returns PIFU_ERR_CUDA and
  *   leaves the context usable only if the CUDA context itself survived.
