@@ -45,7 +45,7 @@ namespace cg = cooperative_groups;
 namespace pifu {
 namespace {
 
-constexpr int kFP = 16;     // points per cluster tile
+constexpr int kFP = kFusedTilePoints;   // points per cluster tile (16)
 constexpr int kCL = 8;      // CTAs per cluster for a device-resident batch size
 constexpr int kFT = 256;    // threads per CTA
 constexpr int kNW = kFT / 32;
@@ -369,35 +369,7 @@ int clusters_of(int CL) {
     }
 }
 
-// Index in `p` of the size with the fewest latency-weighted rounds for
-// `tiles` tiles; ties go to the larger clusters (lower latency).
-__host__ __device__ int fused_pick(const FusedPlan& p, long long tiles) {
-    int best = 0;
-    float best_cost = 3.0e38f;
-    for (int i = 0; i < p.n; ++i) {
-        const long long rounds = (tiles + p.ncl[i] - 1) / p.ncl[i];
-        const float cost = (float)rounds * p.lat[i];
-        if (cost < best_cost * 0.999f) {
-            best_cost = cost;
-            best = i;
-        }
-    }
-    return best;
-}
-
-// Bodies: the plan's cluster sizes, then the split-TF32 network (x3_hi > 0),
-// then the whole-GPU network (grid_hi > 0); an index past them runs nothing.
-__device__ __forceinline__ unsigned int fused_index(const FusedPlan& plan, unsigned int c,
-                                                    unsigned int x3_lo, unsigned int x3_hi,
-                                                    unsigned int grid_hi) {
-    const unsigned int x3_idx = (unsigned)plan.n;
-    const unsigned int grid_idx = x3_idx + (x3_hi > 0u ? 1u : 0u);
-    if (c == 0u) return grid_idx + (grid_hi > 0u ? 1u : 0u);
-    if (c <= grid_hi) return grid_idx;
-    if (c > x3_lo && c <= x3_hi) return x3_idx;
-    return (unsigned)fused_pick(plan, ((long long)c + kFP - 1) / kFP);
-}
-
+// fused_pick, fused_index and batch_index: switch_index.cuh.
 __global__ void fused_switch_kernel(cudaGraphConditionalHandle h, FusedPlan plan,
                                     const unsigned int* count, unsigned int cap, unsigned int x3_lo,
                                     unsigned int x3_hi, unsigned int grid_hi,
@@ -435,12 +407,8 @@ __global__ void batch_switch_kernel(cudaGraphConditionalHandle h, FusedPlan plan
     } else {
         c = *count;
     }
-    unsigned int i;
-    if (c == 0u) i = (unsigned)nt + 1u;
-    else if (c > threshold) i = (unsigned)nt;
-    else if (single) i = 0u;
-    else i = fused_index(plan, min(c, cap), x3_lo, x3_hi, grid_hi);
-    cudaGraphSetConditional(h, i);
+    cudaGraphSetConditional(h, batch_index(plan, c, cap, threshold, nt, single != 0, x3_lo, x3_hi,
+                                           grid_hi));
 }
 
 }  // namespace

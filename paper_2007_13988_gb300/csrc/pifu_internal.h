@@ -9,6 +9,7 @@
 #include <cuda_runtime.h>
 
 #include "stream_sched.cuh"
+#include "switch_index.cuh"
 
 #include <utility>
 
@@ -623,15 +624,8 @@ struct FusedNet {
 };
 // Whether the network's shape fits the fused kernel.
 bool fused_ok(const FusedNet& n);
-// The cluster sizes the fused kernel can use for a network, with the number
-// of clusters of each size that fit on the device at once and the latency of
-// one tile relative to 8-CTA clusters.
-struct FusedPlan {
-    int n = 0;
-    int cl[4] = {};
-    int ncl[4] = {};
-    float lat[4] = {};
-};
+// The cluster sizes the fused kernel can use for a network (FusedPlan,
+// switch_index.cuh).
 FusedPlan fused_plan(const FusedNet& n);
 // Points p0 .. p0 + m - 1 of `src` (src.count: a device-resident m, at most
 // m).  cl = 0: the cluster size of fewest latency-weighted rounds for a
